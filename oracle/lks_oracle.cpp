@@ -1,0 +1,1109 @@
+// Oracle for the coupled lattice-kinetic-scheme / rigid-body step and its discrete adjoint.
+//
+// TEST INFRASTRUCTURE ONLY. This file is a plain, slow, single-threaded FP64 CPU statement of
+// what the method computes. Only the tests, the smoke check and the benchmark's CPU-baseline
+// leg may load it. It shares no code, header or constant table with the CUDA library.
+//
+// Paper: "Topology optimization of passively moving rigid bodies in unsteady flows"
+// (arXiv 2601.18272). Citations below name the paper's section / equation.
+//
+// Forward step t (Algorithm 1, inner loops), in the paper's order:
+//   S1  LKS predictor p*, u* from the state at t-1          (Sec. 2.2, Eqs. p_tmp, u_tmp, f^eq)
+//   S2  boundary values prescribed directly                  (Sec. 2.2, last paragraph)
+//   S3  N_itr fixed-point iterations                         (Sec. 3.1)
+//         rigid transform x^ref, u^S,ref                     (Sec. 2.3, Eqs. rigid_body_position/velocity)
+//         spread kappa, u^S onto the analysis grid           (Sec. 2.3, Eqs. kappa_mapping, us_mapping)
+//         Brinkman update u = (u* + kappa u^S)/(1 + kappa)   (Sec. 2.2, Eq. u)
+//         interpolate u^ref to the design points             (Sec. 2.3, Eq. u_mapping)
+//         force / torque sums and explicit Euler EOM         (Sec. 2.4)
+// The adjoint is the exact reverse of that arithmetic (reverse-mode, written out by hand); the
+// paper's continuous-adjoint ALKS (Sec. 2.5) has the same stencil structure (moments of the
+// adjoint distribution gathered from x + c_i) but is a discretised continuous adjoint.
+//
+// Readings where the paper is silent or garbled (each repeated at its use):
+//   lattice units dx = dt = 1, design-cell volume 1; D2Q9/D3Q15 velocity order (rest, axes,
+//   diagonals); f^eq with -3/2|u|^2; velocity gradient by the isotropic central stencil
+//   d_b u_a(y) = sum_j c_jb u_a(y + c_j) / sum_j c_jb^2; weight kernel w(r) = (1 + cos(pi r/2))/4
+//   for |r| < 2 (or bilinear 1 - |r|); design spacing one cell with pivot at the design-grid
+//   centre; DOF^(0) = DOF(t-1), u(t) from the last iteration, DOF(t) = DOF^(N_itr); lever arm
+//   R(theta^(k-1)) r_m; M and I held constant.
+//
+// Templated on the scalar type: double, and std::complex<double> for complex-step derivatives.
+// Every branch (kernel support, floor, bilinear sign) is taken on the real part.
+
+#include <cmath>
+#include <complex>
+#include <cstdint>
+#include <cstring>
+#include <vector>
+
+namespace {
+
+typedef std::complex<double> cplx;
+
+inline double re(double x) { return x; }
+inline double re(const cplx& x) { return x.real(); }
+
+const double kPi = 3.14159265358979323846;
+
+enum { BC_PERIODIC = 0, BC_INFLOW_OUTFLOW = 1, BC_WALL = 2, BC_PRESSURE = 3 };
+enum { W_COS4 = 0, W_BILINEAR = 1 };
+enum { DOF_TX = 1, DOF_TY = 2, DOF_TZ = 4, DOF_ROT = 8 };
+enum { ORC_OK = 0, ORC_ERR_ARG = 1, ORC_ERR_BODY_OUTSIDE = 2, ORC_ERR_NONFINITE = 3, ORC_ERR_UNSTABLE = 4 };
+
+}  // namespace
+
+// The oracle's own problem record (mirrored by oracle/oracle.py with ctypes).
+extern "C" struct OracleProblem {
+  int dim;             // 2 or 3
+  int nx, ny, nz;      // analysis grid (nz = 1 in 2D)
+  int ndx, ndy, ndz;   // design grid (ndz = 1 in 2D)
+  int rot_axis;        // single rotation axis (2 = z in 2D)
+  int dof_mask;        // DOF_TX | DOF_TY | DOF_TZ | DOF_ROT
+  int bc[3];           // boundary kind per axis
+  int weight_kind;     // W_COS4 or W_BILINEAR
+  int n_steps;         // N_t
+  int n_itr;           // N_itr
+  double mass;         // M
+  double inertia;      // I about rot_axis
+  double nu;           // kinematic viscosity; A = 9/2 (1/6 - nu)
+  double u_in;         // inflow speed
+  double dp;           // pressure at the inlet for the pressure-driven boundary
+  double kappa_max;    // kappa_max in the Brinkman interpolation
+  double q;            // convexity parameter
+  double obj_w[8];     // J = sum_d obj_w[d] * s_d(N_t) over (xG, uG, theta, omega)
+};
+
+namespace {
+
+struct Lattice {
+  int d = 2, Q = 9;
+  int c[15][3];
+  double w[15];
+  double cn[3];  // sum_j c_jb^2, the normaliser of the gradient stencil
+};
+
+// Velocity sets and weights (Sec. 2.2). The paper gives the weights by index range; the vectors
+// are drawn only in a figure, so the order used is rest, axis directions, diagonals.
+Lattice make_lattice(int dim) {
+  Lattice L;
+  std::memset(L.c, 0, sizeof(L.c));
+  if (dim == 2) {
+    L.d = 2;
+    L.Q = 9;
+    const int c2[9][2] = {{0, 0}, {1, 0}, {0, 1}, {-1, 0}, {0, -1}, {1, 1}, {-1, 1}, {-1, -1}, {1, -1}};
+    for (int i = 0; i < 9; ++i) {
+      L.c[i][0] = c2[i][0];
+      L.c[i][1] = c2[i][1];
+      L.c[i][2] = 0;
+      L.w[i] = (i == 0) ? 4.0 / 9.0 : (i <= 4 ? 1.0 / 9.0 : 1.0 / 36.0);
+    }
+  } else {
+    L.d = 3;
+    L.Q = 15;
+    const int c3[15][3] = {{0, 0, 0},   {1, 0, 0},   {-1, 0, 0}, {0, 1, 0},  {0, -1, 0},
+                           {0, 0, 1},   {0, 0, -1},  {1, 1, 1},  {-1, 1, 1}, {1, -1, 1},
+                           {-1, -1, 1}, {1, 1, -1},  {-1, 1, -1}, {1, -1, -1}, {-1, -1, -1}};
+    for (int i = 0; i < 15; ++i) {
+      for (int a = 0; a < 3; ++a) L.c[i][a] = c3[i][a];
+      L.w[i] = (i == 0) ? 2.0 / 9.0 : (i <= 6 ? 1.0 / 9.0 : 1.0 / 72.0);
+    }
+  }
+  for (int b = 0; b < 3; ++b) {
+    L.cn[b] = 0;
+    for (int j = 0; j < L.Q; ++j) L.cn[b] += L.c[j][b] * L.c[j][b];
+  }
+  return L;
+}
+
+struct Ctx {
+  OracleProblem P;
+  Lattice L;
+  int d;
+  int n[3];
+  size_t N;
+  int nd[3];
+  size_t ND;
+  double A;       // nu = (1/6 - 2A/9) dx (Sec. 2.2)
+  int support;    // kernel half-width in cells
+  int err = ORC_OK;
+  std::vector<double> r;  // r_m = xi_m - xi^G, [ND][3]
+};
+
+bool make_ctx(const OracleProblem* P, Ctx* C) {
+  C->P = *P;
+  C->d = P->dim;
+  if (C->d != 2 && C->d != 3) return false;
+  C->L = make_lattice(C->d);
+  C->n[0] = P->nx;
+  C->n[1] = P->ny;
+  C->n[2] = (C->d == 3) ? P->nz : 1;
+  C->nd[0] = P->ndx;
+  C->nd[1] = P->ndy;
+  C->nd[2] = (C->d == 3) ? P->ndz : 1;
+  for (int a = 0; a < C->d; ++a)
+    if (C->n[a] < 4 || C->nd[a] < 1) return false;
+  C->N = (size_t)C->n[0] * C->n[1] * C->n[2];
+  C->ND = (size_t)C->nd[0] * C->nd[1] * C->nd[2];
+  if (P->bc[0] == BC_WALL) return false;  // x is periodic or open
+  for (int a = 1; a < 3; ++a)
+    if (P->bc[a] != BC_PERIODIC && P->bc[a] != BC_WALL) return false;
+  if (C->d == 2 && P->rot_axis != 2) return false;
+  if (P->rot_axis < 0 || P->rot_axis > 2) return false;
+  if (P->n_itr < 1 || P->n_steps < 0) return false;
+  C->A = 4.5 * (1.0 / 6.0 - P->nu);
+  C->support = (P->weight_kind == W_BILINEAR) ? 1 : 2;
+  C->r.assign(C->ND * 3, 0.0);
+  for (int k = 0; k < C->nd[2]; ++k)
+    for (int j = 0; j < C->nd[1]; ++j)
+      for (int i = 0; i < C->nd[0]; ++i) {
+        size_t m = (size_t)i + C->nd[0] * ((size_t)j + C->nd[1] * k);
+        C->r[3 * m + 0] = i - (C->nd[0] - 1) / 2.0;
+        C->r[3 * m + 1] = j - (C->nd[1] - 1) / 2.0;
+        C->r[3 * m + 2] = (C->d == 3) ? k - (C->nd[2] - 1) / 2.0 : 0.0;
+      }
+  return true;
+}
+
+inline size_t idx(const Ctx& C, int x, int y, int z) { return (size_t)x + C.n[0] * ((size_t)y + C.n[1] * z); }
+
+inline int wrap(int v, int n) { return ((v % n) + n) % n; }
+
+// Node on a boundary plane of a non-periodic axis?
+inline bool on_boundary(const Ctx& C, int a, int v) {
+  return C.P.bc[a] != BC_PERIODIC && (v == 0 || v == C.n[a] - 1);
+}
+inline bool is_interior(const Ctx& C, const int* x) {
+  for (int a = 0; a < C.d; ++a)
+    if (on_boundary(C, a, x[a])) return false;
+  return true;
+}
+
+// Neighbour for the velocity-gradient stencil, with one ghost layer on non-periodic axes:
+// open boundaries (inflow/outflow, pressure) copy the boundary node; no-slip walls take the odd
+// reflection u(-1) = -u(1) (linear extrapolation through the wall value u = 0).
+inline size_t grad_nbr(const Ctx& C, const int* x, const int* c, double* sgn) {
+  int y[3] = {0, 0, 0};
+  *sgn = 1.0;
+  for (int a = 0; a < 3; ++a) {
+    if (a >= C.d) {
+      y[a] = 0;
+      continue;
+    }
+    int v = x[a] + c[a];
+    int n = C.n[a];
+    int bc = C.P.bc[a];
+    if (bc == BC_PERIODIC) {
+      v = wrap(v, n);
+    } else if (v < 0 || v >= n) {
+      if (bc == BC_WALL) {
+        v = (v < 0) ? 1 : n - 2;
+        *sgn = -*sgn;
+      } else {
+        v = (v < 0) ? 0 : n - 1;
+      }
+    }
+    y[a] = v;
+  }
+  return idx(C, y[0], y[1], y[2]);
+}
+
+// Neighbour x - c_i for an interior node (always inside the grid on non-periodic axes).
+inline size_t shift_nbr(const Ctx& C, const int* x, const int* c, int sign) {
+  int y[3] = {0, 0, 0};
+  for (int a = 0; a < C.d; ++a) y[a] = wrap(x[a] + sign * c[a], C.n[a]);
+  return idx(C, y[0], y[1], y[2]);
+}
+
+inline void coords(const Ctx& C, size_t n, int* x) {
+  x[0] = (int)(n % C.n[0]);
+  x[1] = (int)((n / C.n[0]) % C.n[1]);
+  x[2] = (int)(n / ((size_t)C.n[0] * C.n[1]));
+}
+
+template <class T>
+struct Fields {
+  std::vector<T> p;
+  std::vector<T> u[3];
+  void alloc(const Ctx& C) {
+    p.assign(C.N, T(0));
+    for (int a = 0; a < 3; ++a) u[a].assign(a < C.d ? C.N : 0, T(0));
+  }
+};
+
+// ------------------------------------------------------------------------------------------
+// S1 + S2: LKS predictor and boundary values (Sec. 2.2).
+//   f_i^eq = w_i (3p + 3 c.u + 9/2 (c.u)^2 - 3/2 |u|^2) + w_i A (d_a u_b + d_b u_a) c_ia c_ib
+//   p*(x) = 1/3 sum_i f_i^eq(x - c_i),  u*(x) = sum_i c_i f_i^eq(x - c_i)
+// The paper prints "+3/2 u^2"; only "-3/2 |u|^2" makes sum_i f_i^eq = 3p, i.e. p* = p for a
+// uniform state, which the paper's Eq. p = p* relies on; that sign is used.
+// ------------------------------------------------------------------------------------------
+template <class T>
+void velocity_gradient(const Ctx& C, const Fields<T>& s, std::vector<T>* G) {
+  const int d = C.d;
+  G->assign((size_t)d * d * C.N, T(0));
+  for (size_t n = 0; n < C.N; ++n) {
+    int x[3];
+    coords(C, n, x);
+    for (int a = 0; a < d; ++a)
+      for (int b = 0; b < d; ++b) {
+        T acc = T(0);
+        for (int j = 0; j < C.L.Q; ++j) {
+          if (C.L.c[j][b] == 0) continue;
+          double sg;
+          size_t m = grad_nbr(C, x, C.L.c[j], &sg);
+          acc += (double)C.L.c[j][b] * sg * s.u[a][m];
+        }
+        (*G)[((size_t)a * d + b) * C.N + n] = acc / C.L.cn[b];  // G_ab = d_b u_a
+      }
+  }
+}
+
+template <class T>
+T feq(const Ctx& C, int i, const Fields<T>& s, const std::vector<T>& G, size_t n) {
+  const int d = C.d;
+  const int* c = C.L.c[i];
+  T cu = T(0), uu = T(0), cgc = T(0);
+  for (int a = 0; a < d; ++a) {
+    cu += (double)c[a] * s.u[a][n];
+    uu += s.u[a][n] * s.u[a][n];
+  }
+  for (int a = 0; a < d; ++a)
+    for (int b = 0; b < d; ++b) cgc += (double)(c[a] * c[b]) * G[((size_t)a * d + b) * C.N + n];
+  // A (d_a u_b + d_b u_a) c_a c_b summed over a, b equals 2 A sum_ab G_ab c_a c_b
+  return C.L.w[i] * (3.0 * s.p[n] + 3.0 * cu + 4.5 * cu * cu - 1.5 * uu) + C.L.w[i] * C.A * 2.0 * cgc;
+}
+
+template <class T>
+void apply_boundaries(const Ctx& C, Fields<T>* o) {
+  const int d = C.d;
+  int x[3];
+  // phase 1: y walls, for nodes whose x and z are interior
+  // phase 2: z walls, for nodes whose x is interior
+  for (int wa = 1; wa < d; ++wa) {
+    if (C.P.bc[wa] != BC_WALL) continue;
+    for (size_t n = 0; n < C.N; ++n) {
+      coords(C, n, x);
+      if (!(x[wa] == 0 || x[wa] == C.n[wa] - 1)) continue;
+      if (on_boundary(C, 0, x[0])) continue;
+      if (wa == 1 && d == 3 && on_boundary(C, 2, x[2])) continue;
+      int y[3] = {x[0], x[1], x[2]};
+      y[wa] = (x[wa] == 0) ? 1 : C.n[wa] - 2;
+      o->p[n] = o->p[idx(C, y[0], y[1], y[2])];
+      for (int a = 0; a < d; ++a) o->u[a][n] = T(0);
+    }
+  }
+  // phase 3: open x boundaries, all rows
+  const int bcx = C.P.bc[0];
+  if (bcx == BC_PERIODIC) return;
+  for (size_t n = 0; n < C.N; ++n) {
+    coords(C, n, x);
+    if (!(x[0] == 0 || x[0] == C.n[0] - 1)) continue;
+    bool inlet = (x[0] == 0);
+    size_t nin = idx(C, inlet ? 1 : C.n[0] - 2, x[1], x[2]);
+    if (bcx == BC_INFLOW_OUTFLOW) {
+      if (inlet) {
+        o->p[n] = o->p[nin];  // zero-gradient pressure at the inlet
+        o->u[0][n] = T(C.P.u_in);
+        for (int a = 1; a < d; ++a) o->u[a][n] = T(0);
+      } else {
+        o->p[n] = T(0);  // pressure gauge fixed at the outlet
+        for (int a = 0; a < d; ++a) o->u[a][n] = o->u[a][nin];
+      }
+    } else {  // BC_PRESSURE
+      o->p[n] = inlet ? T(C.P.dp) : T(0);
+      for (int a = 0; a < d; ++a) o->u[a][n] = o->u[a][nin];
+    }
+  }
+}
+
+template <class T>
+void stencil_fwd(const Ctx& C, const Fields<T>& s, Fields<T>* o) {
+  const int d = C.d, Q = C.L.Q;
+  std::vector<T> G;
+  velocity_gradient(C, s, &G);
+  std::vector<T> f((size_t)Q * C.N);
+  for (size_t n = 0; n < C.N; ++n)
+    for (int i = 0; i < Q; ++i) f[(size_t)i * C.N + n] = feq(C, i, s, G, n);
+  o->alloc(C);
+  int x[3];
+  for (size_t n = 0; n < C.N; ++n) {
+    coords(C, n, x);
+    if (!is_interior(C, x)) continue;
+    T ps = T(0);
+    T us[3] = {T(0), T(0), T(0)};
+    for (int i = 0; i < Q; ++i) {
+      T fi = f[(size_t)i * C.N + shift_nbr(C, x, C.L.c[i], -1)];  // f_i^eq(x - c_i)
+      ps += fi;
+      for (int a = 0; a < d; ++a) us[a] += (double)C.L.c[i][a] * fi;
+    }
+    o->p[n] = ps / 3.0;
+    for (int a = 0; a < d; ++a) o->u[a][n] = us[a];
+  }
+  apply_boundaries(C, o);
+}
+
+// Exact transpose of stencil_fwd at the state s (the vector-Jacobian product).
+// In: lps, lus = dJ/d(p*, u*). Out: lp, lu = dJ/d(p, u) at t-1.
+template <class T>
+void stencil_vjp(const Ctx& C, const Fields<T>& s, const Fields<T>& lam_star, Fields<T>* lam) {
+  const int d = C.d, Q = C.L.Q;
+  Fields<T> ls = lam_star;  // working copy, boundary phases reversed in place
+  int x[3];
+  // reverse phase 3 (open x boundaries)
+  const int bcx = C.P.bc[0];
+  if (bcx != BC_PERIODIC) {
+    for (size_t n = 0; n < C.N; ++n) {
+      coords(C, n, x);
+      if (!(x[0] == 0 || x[0] == C.n[0] - 1)) continue;
+      bool inlet = (x[0] == 0);
+      size_t nin = idx(C, inlet ? 1 : C.n[0] - 2, x[1], x[2]);
+      if (bcx == BC_INFLOW_OUTFLOW) {
+        if (inlet) {
+          ls.p[nin] += ls.p[n];
+        } else {
+          for (int a = 0; a < d; ++a) ls.u[a][nin] += ls.u[a][n];
+        }
+      } else {
+        for (int a = 0; a < d; ++a) ls.u[a][nin] += ls.u[a][n];
+      }
+      ls.p[n] = T(0);
+      for (int a = 0; a < d; ++a) ls.u[a][n] = T(0);
+    }
+  }
+  // reverse phase 2 then phase 1 (walls)
+  for (int wa = d - 1; wa >= 1; --wa) {
+    if (C.P.bc[wa] != BC_WALL) continue;
+    for (size_t n = 0; n < C.N; ++n) {
+      coords(C, n, x);
+      if (!(x[wa] == 0 || x[wa] == C.n[wa] - 1)) continue;
+      if (on_boundary(C, 0, x[0])) continue;
+      if (wa == 1 && d == 3 && on_boundary(C, 2, x[2])) continue;
+      int y[3] = {x[0], x[1], x[2]};
+      y[wa] = (x[wa] == 0) ? 1 : C.n[wa] - 2;
+      ls.p[idx(C, y[0], y[1], y[2])] += ls.p[n];
+      ls.p[n] = T(0);
+      for (int a = 0; a < d; ++a) ls.u[a][n] = T(0);
+    }
+  }
+  // interior gather transpose: fbar_i(x - c_i) += lps(x)/3 + c_i . lus(x)
+  std::vector<T> fbar((size_t)Q * C.N, T(0));
+  for (size_t n = 0; n < C.N; ++n) {
+    coords(C, n, x);
+    if (!is_interior(C, x)) continue;
+    for (int i = 0; i < Q; ++i) {
+      T v = ls.p[n] / 3.0;
+      for (int a = 0; a < d; ++a) v += (double)C.L.c[i][a] * ls.u[a][n];
+      fbar[(size_t)i * C.N + shift_nbr(C, x, C.L.c[i], -1)] += v;
+    }
+  }
+  // f^eq transpose (the gradient enters f^eq linearly, so only its adjoint is needed)
+  lam->alloc(C);
+  std::vector<T> lG((size_t)d * d * C.N, T(0));
+  for (size_t n = 0; n < C.N; ++n) {
+    for (int i = 0; i < Q; ++i) {
+      T fb = fbar[(size_t)i * C.N + n];
+      const int* c = C.L.c[i];
+      double wi = C.L.w[i];
+      T cu = T(0);
+      for (int a = 0; a < d; ++a) cu += (double)c[a] * s.u[a][n];
+      lam->p[n] += 3.0 * wi * fb;
+      for (int a = 0; a < d; ++a) lam->u[a][n] += wi * fb * (3.0 * c[a] + 9.0 * cu * (double)c[a] - 3.0 * s.u[a][n]);
+      for (int a = 0; a < d; ++a)
+        for (int b = 0; b < d; ++b) lG[((size_t)a * d + b) * C.N + n] += wi * C.A * 2.0 * (double)(c[a] * c[b]) * fb;
+    }
+  }
+  // velocity-gradient transpose: G_ab(n) = sum_j c_jb sgn u_a(nbr) / cn_b
+  for (size_t n = 0; n < C.N; ++n) {
+    coords(C, n, x);
+    for (int a = 0; a < d; ++a)
+      for (int b = 0; b < d; ++b) {
+        T g = lG[((size_t)a * d + b) * C.N + n];
+        for (int j = 0; j < Q; ++j) {
+          if (C.L.c[j][b] == 0) continue;
+          double sg;
+          size_t m = grad_nbr(C, x, C.L.c[j], &sg);
+          lam->u[a][m] += (double)C.L.c[j][b] * sg * g / C.L.cn[b];
+        }
+      }
+  }
+}
+
+// ------------------------------------------------------------------------------------------
+// Grid separation (Sec. 2.3) and rigid motion.
+// ------------------------------------------------------------------------------------------
+template <class T>
+T wk(int kind, T r) {
+  double a = std::fabs(re(r));
+  if (kind == W_BILINEAR) {
+    if (a >= 1.0) return T(0);
+    return re(r) >= 0.0 ? T(1.0) - r : T(1.0) + r;
+  }
+  if (a >= 2.0) return T(0);
+  return 0.25 * (1.0 + std::cos(kPi * r / 2.0));  // the paper's "1 - cos" read as "1 + cos"
+}
+
+template <class T>
+T dwk(int kind, T r) {  // dw/dr, the branch taken on the real part as in wk
+  double a = std::fabs(re(r));
+  if (kind == W_BILINEAR) {
+    if (a >= 1.0) return T(0);
+    return re(r) >= 0.0 ? T(-1.0) : T(1.0);
+  }
+  if (a >= 2.0) return T(0);
+  return -0.125 * kPi * std::sin(kPi * r / 2.0);
+}
+
+// In-plane axes (b, c) of the rotation about axis a, right-handed.
+inline void plane_axes(int a, int* b, int* c) {
+  *b = (a + 1) % 3;
+  *c = (a + 2) % 3;
+}
+
+// Design-point geometry for one DOF iterate (Eqs. rigid_body_position, rigid_body_velocity).
+template <class T>
+struct Geometry {
+  std::vector<T> xref, usref, lev, dlev;  // [ND][3]; lev = R r, dlev = R' r = d(R r)/d theta
+};
+
+template <class T>
+void transform(const Ctx& C, const T* s, Geometry<T>* g) {
+  const size_t ND = C.ND;
+  g->xref.assign(ND * 3, T(0));
+  g->usref.assign(ND * 3, T(0));
+  g->lev.assign(ND * 3, T(0));
+  g->dlev.assign(ND * 3, T(0));
+  int ax = C.P.rot_axis, b, c;
+  plane_axes(ax, &b, &c);
+  T ct = std::cos(s[6]), st = std::sin(s[6]);
+  for (size_t m = 0; m < ND; ++m) {
+    const double* r = &C.r[3 * m];
+    T l[3], dl[3];
+    l[ax] = T(r[ax]);
+    dl[ax] = T(0);
+    l[b] = ct * r[b] - st * r[c];
+    l[c] = st * r[b] + ct * r[c];
+    dl[b] = -st * r[b] - ct * r[c];
+    dl[c] = ct * r[b] - st * r[c];
+    for (int a = 0; a < 3; ++a) {
+      g->lev[3 * m + a] = l[a];
+      g->dlev[3 * m + a] = dl[a];
+      g->xref[3 * m + a] = (a < C.d) ? s[a] + l[a] : T(0);
+      g->usref[3 * m + a] = (a < C.d) ? s[3 + a] + s[7] * dl[a] : T(0);
+    }
+  }
+}
+
+// Support window of design point m: 2*support nodes per axis starting at floor(xref) - support + 1.
+// Nodes on non-periodic axes must stay at least two cells inside the boundary planes.
+struct WindowNode {
+  size_t n;
+  int off[3];
+};
+
+template <class T>
+void window(Ctx& C, const T* xref, std::vector<WindowNode>* out, std::vector<T>* wv, std::vector<T>* dwv) {
+  out->clear();
+  wv->clear();
+  dwv->clear();
+  const int d = C.d, s = C.support, kind = C.P.weight_kind;
+  int lo[3] = {0, 0, 0}, cnt[3] = {1, 1, 1};
+  for (int a = 0; a < d; ++a) {
+    lo[a] = (int)std::floor(re(xref[a])) - s + 1;
+    cnt[a] = 2 * s;
+  }
+  for (int k = 0; k < cnt[2]; ++k)
+    for (int j = 0; j < cnt[1]; ++j)
+      for (int i = 0; i < cnt[0]; ++i) {
+        int pos[3] = {lo[0] + i, lo[1] + j, lo[2] + k};
+        T w1[3], dw1[3];
+        bool nz = true;
+        for (int a = 0; a < 3; ++a) {
+          if (a < d) {
+            T rr = (double)pos[a] - xref[a];
+            w1[a] = wk(kind, rr);
+            dw1[a] = dwk(kind, rr);
+            if (re(w1[a]) == 0.0 && re(dw1[a]) == 0.0) nz = false;
+          } else {
+            w1[a] = T(1);
+            dw1[a] = T(0);
+          }
+        }
+        if (!nz) continue;
+        int node[3] = {0, 0, 0};
+        for (int a = 0; a < d; ++a) {
+          if (C.P.bc[a] == BC_PERIODIC) {
+            node[a] = wrap(pos[a], C.n[a]);
+          } else {
+            if (pos[a] < 2 || pos[a] > C.n[a] - 3) {
+              C.err = ORC_ERR_BODY_OUTSIDE;
+              node[a] = pos[a] < 2 ? 2 : C.n[a] - 3;
+            } else {
+              node[a] = pos[a];
+            }
+          }
+        }
+        WindowNode wn;
+        wn.n = idx(C, node[0], node[1], node[2]);
+        wn.off[0] = i;
+        wn.off[1] = j;
+        wn.off[2] = k;
+        out->push_back(wn);
+        T W = w1[0] * w1[1] * w1[2];
+        wv->push_back(W);
+        // dW/dxref_e = -w'(x_e - xref_e) prod_{a != e} w(x_a - xref_a)
+        for (int e = 0; e < 3; ++e) {
+          T prod = T(1);
+          for (int a = 0; a < 3; ++a) prod *= (a == e) ? dw1[a] : w1[a];
+          dwv->push_back(e < d ? -prod : T(0));
+        }
+      }
+}
+
+// One coupling iteration's intermediate values (kept for the adjoint).
+template <class T>
+struct IterRecord {
+  std::vector<T> kap, us[3], u[3];  // analysis-grid fields
+  std::vector<T> uref;              // [ND][3]
+  Geometry<T> geo;
+  T F[3], Tq;
+};
+
+template <class T>
+void coupling_iteration(Ctx& C, const std::vector<T>& kref, const T* s_prev_iter, const T* s_step_start,
+                        const Fields<T>& star, IterRecord<T>* rec, T* s_new) {
+  const int d = C.d;
+  const size_t N = C.N, ND = C.ND;
+  transform(C, s_prev_iter, &rec->geo);
+  rec->kap.assign(N, T(0));
+  for (int a = 0; a < 3; ++a) {
+    rec->us[a].assign(a < d ? N : 0, T(0));
+    rec->u[a].assign(a < d ? N : 0, T(0));
+  }
+  std::vector<WindowNode> wn;
+  std::vector<T> wv, dwv;
+  // spread (Eqs. kappa_mapping, us_mapping): scatter each design point over its window
+  for (size_t m = 0; m < ND; ++m) {
+    window(C, &rec->geo.xref[3 * m], &wn, &wv, &dwv);
+    for (size_t q = 0; q < wn.size(); ++q) {
+      rec->kap[wn[q].n] += wv[q] * kref[m];
+      for (int a = 0; a < d; ++a) rec->us[a][wn[q].n] += wv[q] * rec->geo.usref[3 * m + a];
+    }
+  }
+  // Brinkman update (Eq. u); p = p* is untouched
+  for (size_t n = 0; n < N; ++n)
+    for (int a = 0; a < d; ++a) rec->u[a][n] = (star.u[a][n] + rec->kap[n] * rec->us[a][n]) / (1.0 + rec->kap[n]);
+  // interpolation to the design points (Eq. u_mapping)
+  rec->uref.assign(ND * 3, T(0));
+  for (size_t m = 0; m < ND; ++m) {
+    window(C, &rec->geo.xref[3 * m], &wn, &wv, &dwv);
+    for (size_t q = 0; q < wn.size(); ++q)
+      for (int a = 0; a < d; ++a) rec->uref[3 * m + a] += wv[q] * rec->u[a][wn[q].n];
+  }
+  // force and torque from the design-grid sums (Sec. 2.4); lever arm x^ref - x^G = R r
+  int ax = C.P.rot_axis, b, c;
+  plane_axes(ax, &b, &c);
+  T F[3] = {T(0), T(0), T(0)}, Tq = T(0);
+  for (size_t m = 0; m < ND; ++m) {
+    T D[3];
+    for (int a = 0; a < 3; ++a) D[a] = (a < d) ? rec->uref[3 * m + a] - rec->geo.usref[3 * m + a] : T(0);
+    for (int a = 0; a < d; ++a) F[a] += kref[m] * D[a];
+    const T* l = &rec->geo.lev[3 * m];
+    Tq += kref[m] * (l[b] * D[c] - l[c] * D[b]);
+  }
+  for (int a = 0; a < 3; ++a) rec->F[a] = F[a];
+  rec->Tq = Tq;
+  // explicit Euler EOM, velocity first (Eqs. equation_of_motion_*_discretized), masked by the DOFs
+  for (int a = 0; a < 8; ++a) s_new[a] = s_step_start[a];
+  const int mask = C.P.dof_mask;
+  for (int a = 0; a < d; ++a) {
+    if (!(mask & (1 << a))) continue;
+    s_new[3 + a] = s_step_start[3 + a] + F[a] / C.P.mass;
+    s_new[a] = s_step_start[a] + s_new[3 + a];
+  }
+  if (mask & DOF_ROT) {
+    s_new[7] = s_step_start[7] + Tq / C.P.inertia;
+    s_new[6] = s_step_start[6] + s_new[7];
+  }
+}
+
+template <class T>
+void forward_step(Ctx& C, const std::vector<T>& kref, const Fields<T>& prev, const T* s_prev, Fields<T>* next,
+                  T* s_next, std::vector<T>* iters_out) {
+  Fields<T> star;
+  stencil_fwd(C, prev, &star);
+  const int K = C.P.n_itr;
+  std::vector<T> it((size_t)(K + 1) * 8);
+  for (int a = 0; a < 8; ++a) it[a] = s_prev[a];
+  IterRecord<T> rec;
+  for (int k = 1; k <= K; ++k) coupling_iteration(C, kref, &it[(size_t)(k - 1) * 8], s_prev, star, &rec, &it[(size_t)k * 8]);
+  next->p = star.p;
+  for (int a = 0; a < 3; ++a) next->u[a] = rec.u[a];
+  for (int a = 0; a < 8; ++a) s_next[a] = it[(size_t)K * 8 + a];
+  if (iters_out) *iters_out = it;
+}
+
+// Brinkman interpolation (Eq. brinkman_coefficient).
+template <class T>
+std::vector<T> brinkman(const Ctx& C, const T* gamma) {
+  std::vector<T> k(C.ND);
+  for (size_t m = 0; m < C.ND; ++m) k[m] = C.P.kappa_max * C.P.q * gamma[m] / ((1.0 - gamma[m]) + C.P.q);
+  return k;
+}
+
+template <class T>
+void load_fields(const Ctx& C, const T* p, const T* u, Fields<T>* f) {
+  f->alloc(C);
+  for (size_t n = 0; n < C.N; ++n) f->p[n] = p[n];
+  for (int a = 0; a < C.d; ++a)
+    for (size_t n = 0; n < C.N; ++n) f->u[a][n] = u[(size_t)a * C.N + n];
+}
+
+template <class T>
+T objective(const Ctx& C, const T* s) {
+  T J = T(0);
+  for (int a = 0; a < 8; ++a) J += C.P.obj_w[a] * s[a];
+  return J;
+}
+
+bool finite_fields(const Ctx& C, const Fields<double>& f) {
+  for (size_t n = 0; n < C.N; ++n) {
+    if (!std::isfinite(f.p[n])) return false;
+    for (int a = 0; a < C.d; ++a)
+      if (!std::isfinite(f.u[a][n])) return false;
+  }
+  return true;
+}
+
+// ------------------------------------------------------------------------------------------
+// Adjoint of one coupling iteration k (exact reverse of coupling_iteration).
+//   in : lam_sk = dJ/ds^(k) ; lam_uk_ext = dJ/du^(k) from outside the iteration (k = N_itr only)
+//   out: lam_ustar += dJ/du* ; lam_prev += direct EOM part of dJ/ds(t-1) ;
+//        lam_skm1 = dJ/ds^(k-1) through the transform ; dkref += dJ/dkappa^ref
+// ------------------------------------------------------------------------------------------
+void coupling_iteration_vjp(Ctx& C, const std::vector<double>& kref, const IterRecord<double>& rec,
+                            const double* s_km1, const double* lam_sk, const Fields<double>* lam_uk_ext,
+                            Fields<double>* lam_ustar, double* lam_prev, double* lam_skm1, std::vector<double>* dkref) {
+  const int d = C.d;
+  const size_t N = C.N, ND = C.ND;
+  const int mask = C.P.dof_mask;
+  // EOM reverse
+  double lF[3] = {0, 0, 0}, lT = 0;
+  for (int a = 0; a < 3; ++a) {
+    bool free_a = (a < d) && (mask & (1 << a));
+    if (free_a) {
+      double lug = lam_sk[3 + a] + lam_sk[a];
+      lF[a] = lug / C.P.mass;
+      lam_prev[a] += lam_sk[a];
+      lam_prev[3 + a] += lug;
+    } else {
+      lam_prev[a] += lam_sk[a];
+      lam_prev[3 + a] += lam_sk[3 + a];
+    }
+  }
+  if (mask & DOF_ROT) {
+    double lom = lam_sk[7] + lam_sk[6];
+    lT = lom / C.P.inertia;
+    lam_prev[6] += lam_sk[6];
+    lam_prev[7] += lom;
+  } else {
+    lam_prev[6] += lam_sk[6];
+    lam_prev[7] += lam_sk[7];
+  }
+  // force / torque reverse
+  int ax = C.P.rot_axis, b, c;
+  plane_axes(ax, &b, &c);
+  std::vector<double> l_uref(ND * 3, 0.0), l_usref(ND * 3, 0.0), l_lev(ND * 3, 0.0), l_xref(ND * 3, 0.0);
+  for (size_t m = 0; m < ND; ++m) {
+    double D[3];
+    for (int a = 0; a < 3; ++a) D[a] = (a < d) ? rec.uref[3 * m + a] - rec.geo.usref[3 * m + a] : 0.0;
+    const double* l = &rec.geo.lev[3 * m];
+    double lD[3] = {0, 0, 0};
+    for (int a = 0; a < d; ++a) lD[a] += kref[m] * lF[a];
+    lD[c] += kref[m] * lT * l[b];
+    lD[b] -= kref[m] * lT * l[c];
+    for (int a = 0; a < d; ++a) {
+      l_uref[3 * m + a] = lD[a];
+      l_usref[3 * m + a] = -lD[a];
+    }
+    l_lev[3 * m + b] += lT * kref[m] * D[c];
+    l_lev[3 * m + c] -= lT * kref[m] * D[b];
+    double dk = 0;
+    for (int a = 0; a < d; ++a) dk += lF[a] * D[a];
+    dk += lT * (l[b] * D[c] - l[c] * D[b]);
+    (*dkref)[m] += dk;
+  }
+  // interpolation reverse
+  Fields<double> lam_uk;
+  lam_uk.alloc(C);
+  if (lam_uk_ext)
+    for (int a = 0; a < d; ++a) lam_uk.u[a] = lam_uk_ext->u[a];
+  std::vector<WindowNode> wn;
+  std::vector<double> wv, dwv;
+  for (size_t m = 0; m < ND; ++m) {
+    window(C, &rec.geo.xref[3 * m], &wn, &wv, &dwv);
+    for (size_t q = 0; q < wn.size(); ++q) {
+      double ul = 0;
+      for (int a = 0; a < d; ++a) {
+        lam_uk.u[a][wn[q].n] += wv[q] * l_uref[3 * m + a];
+        ul += rec.u[a][wn[q].n] * l_uref[3 * m + a];
+      }
+      for (int e = 0; e < d; ++e) l_xref[3 * m + e] += dwv[3 * q + e] * ul;
+    }
+  }
+  // Brinkman reverse
+  std::vector<double> l_kap(N, 0.0);
+  std::vector<double> l_us[3];
+  for (int a = 0; a < d; ++a) l_us[a].assign(N, 0.0);
+  for (size_t n = 0; n < N; ++n) {
+    double inv = 1.0 / (1.0 + rec.kap[n]);
+    double lk = 0;
+    for (int a = 0; a < d; ++a) {
+      double lu = lam_uk.u[a][n];
+      lam_ustar->u[a][n] += lu * inv;
+      lk += lu * (rec.us[a][n] - rec.u[a][n]) * inv;
+      l_us[a][n] = lu * rec.kap[n] * inv;
+    }
+    l_kap[n] = lk;
+  }
+  // spread reverse
+  for (size_t m = 0; m < ND; ++m) {
+    window(C, &rec.geo.xref[3 * m], &wn, &wv, &dwv);
+    double dk = 0;
+    for (size_t q = 0; q < wn.size(); ++q) {
+      size_t n = wn[q].n;
+      dk += wv[q] * l_kap[n];
+      double su = kref[m] * l_kap[n];
+      for (int a = 0; a < d; ++a) {
+        l_usref[3 * m + a] += wv[q] * l_us[a][n];
+        su += rec.geo.usref[3 * m + a] * l_us[a][n];
+      }
+      for (int e = 0; e < d; ++e) l_xref[3 * m + e] += dwv[3 * q + e] * su;
+    }
+    (*dkref)[m] += dk;
+  }
+  // transform reverse: xref = xG + R r, usref = uG + omega R' r, lev = R r
+  for (int a = 0; a < 8; ++a) lam_skm1[a] = 0.0;
+  const double om = s_km1[7];
+  for (size_t m = 0; m < ND; ++m) {
+    const double* l = &rec.geo.lev[3 * m];
+    const double* dl = &rec.geo.dlev[3 * m];
+    double ddl[3];  // R'' r = -(R r) in the rotation plane, 0 along the axis
+    for (int a = 0; a < 3; ++a) ddl[a] = (a == ax) ? 0.0 : -l[a];
+    for (int a = 0; a < d; ++a) {
+      lam_skm1[a] += l_xref[3 * m + a];
+      lam_skm1[3 + a] += l_usref[3 * m + a];
+    }
+    for (int a = 0; a < 3; ++a) {
+      double lx = (a < d) ? l_xref[3 * m + a] : 0.0;
+      double lus = (a < d) ? l_usref[3 * m + a] : 0.0;
+      lam_skm1[6] += (lx + l_lev[3 * m + a]) * dl[a] + om * lus * ddl[a];
+      lam_skm1[7] += lus * dl[a];
+    }
+  }
+}
+
+// Full forward with every state and DOF iterate stored, then the exact reverse sweep.
+struct Trajectory {
+  std::vector<Fields<double>> states;  // t = 0..N_t
+  std::vector<std::vector<double>> iters;  // per step t = 1..N_t: (K+1)*8
+  std::vector<double> s;               // (N_t+1)*8
+};
+
+int run_forward(Ctx& C, const std::vector<double>& kref, const double* p0, const double* u0, const double* dof0,
+                Trajectory* tr, bool keep) {
+  const int NT = C.P.n_steps;
+  Fields<double> cur;
+  load_fields(C, p0, u0, &cur);
+  tr->s.assign((size_t)(NT + 1) * 8, 0.0);
+  for (int a = 0; a < 8; ++a) tr->s[a] = dof0[a];
+  if (keep) {
+    tr->states.clear();
+    tr->states.push_back(cur);
+    tr->iters.clear();
+  }
+  for (int t = 1; t <= NT; ++t) {
+    Fields<double> nxt;
+    std::vector<double> it;
+    forward_step(C, kref, cur, &tr->s[(size_t)(t - 1) * 8], &nxt, &tr->s[(size_t)t * 8], keep ? &it : nullptr);
+    cur.p.swap(nxt.p);
+    for (int a = 0; a < 3; ++a) cur.u[a].swap(nxt.u[a]);
+    if (keep) {
+      tr->states.push_back(cur);
+      tr->iters.push_back(it);
+    }
+  }
+  if (!keep) {
+    tr->states.clear();
+    tr->states.push_back(cur);
+  }
+  return C.err;
+}
+
+}  // namespace
+
+// ============================================================================================
+// C API (ctypes). Field arrays: p [N], u [dim][N] planes, x fastest. DOF vectors: 8 doubles
+// (xG_x, xG_y, xG_z, uG_x, uG_y, uG_z, theta, omega). Return: 0 ok, else an ORC_ERR_* code.
+// ============================================================================================
+extern "C" {
+
+int oracle_abi_version(void) { return 1; }
+
+int oracle_sizeof_problem(void) { return (int)sizeof(OracleProblem); }
+
+// Forward march: final fields, DOF history [(n_steps+1)*8] (optional), J (optional).
+int oracle_forward(const OracleProblem* P, const double* gamma, const double* p0, const double* u0,
+                   const double* dof0, double* p_out, double* u_out, double* dof_hist, double* J) {
+  Ctx C;
+  if (!make_ctx(P, &C)) return ORC_ERR_ARG;
+  if (P->nu <= 0.0) return ORC_ERR_UNSTABLE;
+  std::vector<double> kref = brinkman(C, gamma);
+  Trajectory tr;
+  run_forward(C, kref, p0, u0, dof0, &tr, false);
+  const Fields<double>& f = tr.states.back();
+  if (p_out)
+    for (size_t n = 0; n < C.N; ++n) p_out[n] = f.p[n];
+  if (u_out)
+    for (int a = 0; a < C.d; ++a)
+      for (size_t n = 0; n < C.N; ++n) u_out[(size_t)a * C.N + n] = f.u[a][n];
+  if (dof_hist) std::memcpy(dof_hist, tr.s.data(), tr.s.size() * sizeof(double));
+  if (J) *J = objective(C, &tr.s[(size_t)P->n_steps * 8]);
+  if (C.err) return C.err;
+  if (!finite_fields(C, f)) return ORC_ERR_NONFINITE;
+  return ORC_OK;
+}
+
+// Forward + exact discrete adjoint with seed dJ = 1. Outputs J, dJ/dgamma [ND] and, when the
+// pointers are non-null, the adjoint of the initial state: dJ/dp0 [N], dJ/du0 [dim][N],
+// dJ/ds0 [8], and dJ/dkappa^ref [ND].
+int oracle_gradient(const OracleProblem* P, const double* gamma, const double* p0, const double* u0,
+                    const double* dof0, double* J, double* dJdgamma, double* lam_p0, double* lam_u0,
+                    double* lam_dof0, double* dJdkref) {
+  Ctx C;
+  if (!make_ctx(P, &C)) return ORC_ERR_ARG;
+  if (P->nu <= 0.0) return ORC_ERR_UNSTABLE;
+  std::vector<double> kref = brinkman(C, gamma);
+  Trajectory tr;
+  run_forward(C, kref, p0, u0, dof0, &tr, true);
+  if (C.err) return C.err;
+  const int NT = P->n_steps, K = P->n_itr, d = C.d;
+  if (J) *J = objective(C, &tr.s[(size_t)NT * 8]);
+  // terminal adjoint: the objective depends on the DOFs only
+  Fields<double> lam;
+  lam.alloc(C);
+  double lam_s[8];
+  for (int a = 0; a < 8; ++a) lam_s[a] = P->obj_w[a];
+  std::vector<double> dk(C.ND, 0.0);
+  for (int t = NT; t >= 1; --t) {
+    const Fields<double>& prev = tr.states[t - 1];
+    const std::vector<double>& it = tr.iters[t - 1];
+    Fields<double> star;
+    stencil_fwd(C, prev, &star);
+    std::vector<IterRecord<double>> recs(K + 1);
+    for (int k = 1; k <= K; ++k) {
+      double tmp[8];
+      coupling_iteration(C, kref, &it[(size_t)(k - 1) * 8], &it[0], star, &recs[k], tmp);
+    }
+    Fields<double> lam_star;
+    lam_star.alloc(C);
+    lam_star.p = lam.p;  // p(t) = p*(t)
+    double lam_prev[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+    double lam_sk[8];
+    for (int a = 0; a < 8; ++a) lam_sk[a] = lam_s[a];
+    for (int k = K; k >= 1; --k) {
+      double lam_skm1[8];
+      coupling_iteration_vjp(C, kref, recs[k], &it[(size_t)(k - 1) * 8], lam_sk, (k == K) ? &lam : nullptr,
+                             &lam_star, lam_prev, lam_skm1, &dk);
+      if (k > 1) {
+        for (int a = 0; a < 8; ++a) lam_sk[a] = lam_skm1[a];
+      } else {
+        for (int a = 0; a < 8; ++a) lam_prev[a] += lam_skm1[a];
+      }
+    }
+    Fields<double> lam_prev_fields;
+    stencil_vjp(C, prev, lam_star, &lam_prev_fields);
+    lam.p.swap(lam_prev_fields.p);
+    for (int a = 0; a < 3; ++a) lam.u[a].swap(lam_prev_fields.u[a]);
+    for (int a = 0; a < 8; ++a) lam_s[a] = lam_prev[a];
+  }
+  if (C.err) return C.err;
+  for (size_t m = 0; m < C.ND; ++m) {
+    double den = (1.0 - gamma[m]) + P->q;
+    double dkdg = P->kappa_max * P->q * (1.0 + P->q) / (den * den);
+    if (dJdgamma) dJdgamma[m] = dk[m] * dkdg;
+    if (dJdkref) dJdkref[m] = dk[m];
+  }
+  if (lam_p0)
+    for (size_t n = 0; n < C.N; ++n) lam_p0[n] = lam.p[n];
+  if (lam_u0)
+    for (int a = 0; a < d; ++a)
+      for (size_t n = 0; n < C.N; ++n) lam_u0[(size_t)a * C.N + n] = lam.u[a][n];
+  if (lam_dof0)
+    for (int a = 0; a < 8; ++a) lam_dof0[a] = lam_s[a];
+  return ORC_OK;
+}
+
+// Complex-step directional derivative of J along (dgamma, dp0, du0, ddof0): dJ = Im J(x + i h v) / h.
+int oracle_forward_cs(const OracleProblem* P, const double* gamma, const double* dgamma, const double* p0,
+                      const double* dp0, const double* u0, const double* du0, const double* dof0,
+                      const double* ddof0, double h, double* J, double* dJ) {
+  Ctx C;
+  if (!make_ctx(P, &C)) return ORC_ERR_ARG;
+  const size_t N = C.N, ND = C.ND;
+  const int d = C.d;
+  std::vector<cplx> g(ND);
+  for (size_t m = 0; m < ND; ++m) g[m] = cplx(gamma[m], dgamma ? h * dgamma[m] : 0.0);
+  std::vector<cplx> kref = brinkman(C, g.data());
+  std::vector<cplx> pc(N), uc((size_t)d * N);
+  for (size_t n = 0; n < N; ++n) pc[n] = cplx(p0[n], dp0 ? h * dp0[n] : 0.0);
+  for (size_t n = 0; n < (size_t)d * N; ++n) uc[n] = cplx(u0[n], du0 ? h * du0[n] : 0.0);
+  Fields<cplx> cur;
+  load_fields(C, pc.data(), uc.data(), &cur);
+  cplx s[8];
+  for (int a = 0; a < 8; ++a) s[a] = cplx(dof0[a], ddof0 ? h * ddof0[a] : 0.0);
+  for (int t = 1; t <= P->n_steps; ++t) {
+    Fields<cplx> nxt;
+    cplx sn[8];
+    forward_step<cplx>(C, kref, cur, s, &nxt, sn, nullptr);
+    cur.p.swap(nxt.p);
+    for (int a = 0; a < 3; ++a) cur.u[a].swap(nxt.u[a]);
+    for (int a = 0; a < 8; ++a) s[a] = sn[a];
+  }
+  cplx Jc = objective(C, s);
+  if (J) *J = Jc.real();
+  if (dJ) *dJ = Jc.imag() / h;
+  return C.err;
+}
+
+// ---- sub-steps, for unit tests -------------------------------------------------------------
+
+// S1 + S2 only: p*, u* from (p, u).
+int oracle_stencil(const OracleProblem* P, const double* p, const double* u, double* ps, double* us) {
+  Ctx C;
+  if (!make_ctx(P, &C)) return ORC_ERR_ARG;
+  Fields<double> s, o;
+  load_fields(C, p, u, &s);
+  stencil_fwd(C, s, &o);
+  for (size_t n = 0; n < C.N; ++n) ps[n] = o.p[n];
+  for (int a = 0; a < C.d; ++a)
+    for (size_t n = 0; n < C.N; ++n) us[(size_t)a * C.N + n] = o.u[a][n];
+  return ORC_OK;
+}
+
+// Complex-step Jacobian-vector product of S1 + S2 along (dp, du).
+int oracle_stencil_jvp(const OracleProblem* P, const double* p, const double* dp, const double* u,
+                       const double* du, double h, double* dps, double* dus) {
+  Ctx C;
+  if (!make_ctx(P, &C)) return ORC_ERR_ARG;
+  const size_t N = C.N;
+  std::vector<cplx> pc(N), uc((size_t)C.d * N);
+  for (size_t n = 0; n < N; ++n) pc[n] = cplx(p[n], h * dp[n]);
+  for (size_t n = 0; n < (size_t)C.d * N; ++n) uc[n] = cplx(u[n], h * du[n]);
+  Fields<cplx> s, o;
+  load_fields(C, pc.data(), uc.data(), &s);
+  stencil_fwd(C, s, &o);
+  for (size_t n = 0; n < N; ++n) dps[n] = o.p[n].imag() / h;
+  for (int a = 0; a < C.d; ++a)
+    for (size_t n = 0; n < N; ++n) dus[(size_t)a * N + n] = o.u[a][n].imag() / h;
+  return ORC_OK;
+}
+
+// Vector-Jacobian product of S1 + S2 at (p, u).
+int oracle_stencil_vjp(const OracleProblem* P, const double* p, const double* u, const double* lps,
+                       const double* lus, double* lp, double* lu) {
+  Ctx C;
+  if (!make_ctx(P, &C)) return ORC_ERR_ARG;
+  Fields<double> s, ls, l;
+  load_fields(C, p, u, &s);
+  load_fields(C, lps, lus, &ls);
+  stencil_vjp(C, s, ls, &l);
+  for (size_t n = 0; n < C.N; ++n) lp[n] = l.p[n];
+  for (int a = 0; a < C.d; ++a)
+    for (size_t n = 0; n < C.N; ++n) lu[(size_t)a * C.N + n] = l.u[a][n];
+  return ORC_OK;
+}
+
+// One full forward step from (p, u, s); outputs the next state, the DOF iterates [(n_itr+1)*8].
+int oracle_step(const OracleProblem* P, const double* gamma, const double* p, const double* u, const double* s,
+                double* p_out, double* u_out, double* s_out, double* iters) {
+  Ctx C;
+  if (!make_ctx(P, &C)) return ORC_ERR_ARG;
+  std::vector<double> kref = brinkman(C, gamma);
+  Fields<double> cur, nxt;
+  load_fields(C, p, u, &cur);
+  std::vector<double> it;
+  forward_step(C, kref, cur, s, &nxt, s_out, &it);
+  for (size_t n = 0; n < C.N; ++n) p_out[n] = nxt.p[n];
+  for (int a = 0; a < C.d; ++a)
+    for (size_t n = 0; n < C.N; ++n) u_out[(size_t)a * C.N + n] = nxt.u[a][n];
+  if (iters) std::memcpy(iters, it.data(), it.size() * sizeof(double));
+  return C.err;
+}
+
+// Spread of kappa^ref and u^S,ref at the DOF vector s (Eqs. kappa_mapping, us_mapping), and the
+// number of design points with a non-zero weight at each analysis node.
+int oracle_spread(const OracleProblem* P, const double* gamma, const double* s, double* kappa, double* us,
+                  int* count) {
+  Ctx C;
+  if (!make_ctx(P, &C)) return ORC_ERR_ARG;
+  std::vector<double> kref = brinkman(C, gamma);
+  Geometry<double> geo;
+  transform(C, s, &geo);
+  std::vector<WindowNode> wn;
+  std::vector<double> wv, dwv;
+  for (size_t n = 0; n < C.N; ++n) {
+    if (kappa) kappa[n] = 0;
+    if (count) count[n] = 0;
+    if (us)
+      for (int a = 0; a < C.d; ++a) us[(size_t)a * C.N + n] = 0;
+  }
+  for (size_t m = 0; m < C.ND; ++m) {
+    window(C, &geo.xref[3 * m], &wn, &wv, &dwv);
+    for (size_t q = 0; q < wn.size(); ++q) {
+      if (wv[q] == 0.0) continue;
+      if (kappa) kappa[wn[q].n] += wv[q] * kref[m];
+      if (count) count[wn[q].n] += 1;
+      if (us)
+        for (int a = 0; a < C.d; ++a) us[(size_t)a * C.N + wn[q].n] += wv[q] * geo.usref[3 * m + a];
+    }
+  }
+  return C.err;
+}
+
+// Interpolation of an analysis-grid velocity to the design points (Eq. u_mapping): uref [ND][3].
+int oracle_interp(const OracleProblem* P, const double* s, const double* u, double* uref) {
+  Ctx C;
+  if (!make_ctx(P, &C)) return ORC_ERR_ARG;
+  Geometry<double> geo;
+  transform(C, s, &geo);
+  std::vector<WindowNode> wn;
+  std::vector<double> wv, dwv;
+  for (size_t m = 0; m < C.ND; ++m) {
+    window(C, &geo.xref[3 * m], &wn, &wv, &dwv);
+    for (int a = 0; a < 3; ++a) uref[3 * m + a] = 0;
+    for (size_t q = 0; q < wn.size(); ++q)
+      for (int a = 0; a < C.d; ++a) uref[3 * m + a] += wv[q] * u[(size_t)a * C.N + wn[q].n];
+  }
+  return C.err;
+}
+
+// One weight-kernel value w(r) and derivative, for the kernel tests.
+double oracle_weight(int kind, double r, double* dw) {
+  if (dw) *dw = dwk<double>(kind, r);
+  return wk<double>(kind, r);
+}
+
+}  // extern "C"
+
+extern "C" {
+// The velocity set and weights used for dimension dim: c [Q][3], w [Q]; returns Q.
+int oracle_lattice(int dim, int* c, double* w) {
+  Lattice L = make_lattice(dim);
+  for (int i = 0; i < L.Q; ++i) {
+    for (int a = 0; a < 3; ++a) c[3 * i + a] = L.c[i][a];
+    w[i] = L.w[i];
+  }
+  return L.Q;
+}
+}  // extern "C"

@@ -1,0 +1,220 @@
+"""ctypes wrapper around the oracle library (oracle/lks_oracle.cpp).
+
+Test infrastructure only: the tests, ``__graft_entry__.smoke()`` and the benchmark's
+CPU-baseline leg call it. It takes a ``workloads.Problem`` and numpy float64 arrays.
+"""
+from __future__ import annotations
+
+import ctypes
+from typing import Optional
+
+import numpy as np
+
+from . import build as _build
+
+
+class OracleProblem(ctypes.Structure):
+    _fields_ = [
+        ("dim", ctypes.c_int),
+        ("nx", ctypes.c_int), ("ny", ctypes.c_int), ("nz", ctypes.c_int),
+        ("ndx", ctypes.c_int), ("ndy", ctypes.c_int), ("ndz", ctypes.c_int),
+        ("rot_axis", ctypes.c_int),
+        ("dof_mask", ctypes.c_int),
+        ("bc", ctypes.c_int * 3),
+        ("weight_kind", ctypes.c_int),
+        ("n_steps", ctypes.c_int),
+        ("n_itr", ctypes.c_int),
+        ("mass", ctypes.c_double),
+        ("inertia", ctypes.c_double),
+        ("nu", ctypes.c_double),
+        ("u_in", ctypes.c_double),
+        ("dp", ctypes.c_double),
+        ("kappa_max", ctypes.c_double),
+        ("q", ctypes.c_double),
+        ("obj_w", ctypes.c_double * 8),
+    ]
+
+
+ERRORS = {0: "ok", 1: "bad argument", 2: "body outside the domain", 3: "non-finite state", 4: "unstable (nu <= 0)"}
+
+_lib = None
+
+
+def lib():
+    global _lib
+    if _lib is None:
+        path = _build.build()
+        L = ctypes.CDLL(path)
+        dp = ctypes.POINTER(ctypes.c_double)
+        ip = ctypes.POINTER(ctypes.c_int)
+        pp = ctypes.POINTER(OracleProblem)
+        L.oracle_forward.argtypes = [pp, dp, dp, dp, dp, dp, dp, dp, dp]
+        L.oracle_gradient.argtypes = [pp, dp, dp, dp, dp, dp, dp, dp, dp, dp, dp]
+        L.oracle_forward_cs.argtypes = [pp, dp, dp, dp, dp, dp, dp, dp, dp, ctypes.c_double, dp, dp]
+        L.oracle_stencil.argtypes = [pp, dp, dp, dp, dp]
+        L.oracle_stencil_jvp.argtypes = [pp, dp, dp, dp, dp, ctypes.c_double, dp, dp]
+        L.oracle_stencil_vjp.argtypes = [pp, dp, dp, dp, dp, dp, dp]
+        L.oracle_step.argtypes = [pp, dp, dp, dp, dp, dp, dp, dp, dp]
+        L.oracle_spread.argtypes = [pp, dp, dp, dp, dp, ip]
+        L.oracle_interp.argtypes = [pp, dp, dp, dp]
+        L.oracle_weight.argtypes = [ctypes.c_int, ctypes.c_double, dp]
+        L.oracle_weight.restype = ctypes.c_double
+        L.oracle_lattice.argtypes = [ctypes.c_int, ip, dp]
+        if L.oracle_sizeof_problem() != ctypes.sizeof(OracleProblem):
+            raise RuntimeError("oracle problem record layout mismatch")
+        _lib = L
+    return _lib
+
+
+class OracleError(RuntimeError):
+    pass
+
+
+def _check(rc: int):
+    if rc != 0:
+        raise OracleError(f"oracle error {rc}: {ERRORS.get(rc, '?')}")
+
+
+def _ptr(a: Optional[np.ndarray]):
+    if a is None:
+        return None
+    assert a.dtype == np.float64 and a.flags.c_contiguous
+    return a.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+
+
+def _f64(a) -> np.ndarray:
+    return np.ascontiguousarray(np.asarray(a, dtype=np.float64))
+
+
+def problem_record(P, n_steps: Optional[int] = None) -> OracleProblem:
+    r = OracleProblem()
+    r.dim = P.dim
+    r.nx, r.ny, r.nz = P.nx, P.ny, P.nz
+    r.ndx, r.ndy, r.ndz = P.ndx, P.ndy, P.ndz
+    r.rot_axis = P.rot_axis
+    r.dof_mask = P.dof_mask
+    for a in range(3):
+        r.bc[a] = P.bc[a]
+    r.weight_kind = P.weight_kind
+    r.n_steps = P.n_steps if n_steps is None else n_steps
+    r.n_itr = P.n_itr
+    r.mass, r.inertia, r.nu, r.u_in, r.dp = P.mass, P.inertia, P.nu, P.u_in, P.dp
+    r.kappa_max, r.q = P.kappa_max, P.q
+    for a in range(8):
+        r.obj_w[a] = P.obj_weights[a]
+    return r
+
+
+def forward(P, gamma, p0, u0, dof0, n_steps: Optional[int] = None, check: bool = True):
+    """Forward march. Returns (p, u [dim, N], dof history [(n_steps+1), 8], J)."""
+    rec = problem_record(P, n_steps)
+    N = P.n_cells
+    p = np.zeros(N)
+    u = np.zeros((P.dim, N))
+    hist = np.zeros((rec.n_steps + 1, 8))
+    J = ctypes.c_double(0.0)
+    rc = lib().oracle_forward(ctypes.byref(rec), _ptr(_f64(gamma)), _ptr(_f64(p0)), _ptr(_f64(u0)), _ptr(_f64(dof0)),
+                              _ptr(p), _ptr(u), _ptr(hist), ctypes.byref(J))
+    if check:
+        _check(rc)
+    return p, u, hist, J.value
+
+
+def gradient(P, gamma, p0, u0, dof0, n_steps: Optional[int] = None):
+    """Forward + exact discrete adjoint. Returns dict with J, dJdgamma, dJdkref, lam_p0, lam_u0, lam_dof0."""
+    rec = problem_record(P, n_steps)
+    N, ND = P.n_cells, P.n_design
+    out = {"dJdgamma": np.zeros(ND), "dJdkref": np.zeros(ND), "lam_p0": np.zeros(N),
+           "lam_u0": np.zeros((P.dim, N)), "lam_dof0": np.zeros(8)}
+    J = ctypes.c_double(0.0)
+    rc = lib().oracle_gradient(ctypes.byref(rec), _ptr(_f64(gamma)), _ptr(_f64(p0)), _ptr(_f64(u0)), _ptr(_f64(dof0)),
+                               ctypes.byref(J), _ptr(out["dJdgamma"]), _ptr(out["lam_p0"]), _ptr(out["lam_u0"]),
+                               _ptr(out["lam_dof0"]), _ptr(out["dJdkref"]))
+    _check(rc)
+    out["J"] = J.value
+    return out
+
+
+def forward_cs(P, gamma, p0, u0, dof0, dgamma=None, dp0=None, du0=None, ddof0=None, h: float = 1e-30,
+               n_steps: Optional[int] = None):
+    """Complex-step directional derivative of J. Returns (J, dJ)."""
+    rec = problem_record(P, n_steps)
+    J = ctypes.c_double(0.0)
+    dJ = ctypes.c_double(0.0)
+    rc = lib().oracle_forward_cs(ctypes.byref(rec), _ptr(_f64(gamma)), _ptr(None if dgamma is None else _f64(dgamma)),
+                                 _ptr(_f64(p0)), _ptr(None if dp0 is None else _f64(dp0)), _ptr(_f64(u0)),
+                                 _ptr(None if du0 is None else _f64(du0)), _ptr(_f64(dof0)),
+                                 _ptr(None if ddof0 is None else _f64(ddof0)), h, ctypes.byref(J), ctypes.byref(dJ))
+    _check(rc)
+    return J.value, dJ.value
+
+
+def stencil(P, p, u):
+    rec = problem_record(P)
+    ps = np.zeros(P.n_cells)
+    us = np.zeros((P.dim, P.n_cells))
+    _check(lib().oracle_stencil(ctypes.byref(rec), _ptr(_f64(p)), _ptr(_f64(u)), _ptr(ps), _ptr(us)))
+    return ps, us
+
+
+def stencil_jvp(P, p, u, dp, du, h: float = 1e-30):
+    rec = problem_record(P)
+    dps = np.zeros(P.n_cells)
+    dus = np.zeros((P.dim, P.n_cells))
+    _check(lib().oracle_stencil_jvp(ctypes.byref(rec), _ptr(_f64(p)), _ptr(_f64(dp)), _ptr(_f64(u)), _ptr(_f64(du)), h,
+                                    _ptr(dps), _ptr(dus)))
+    return dps, dus
+
+
+def stencil_vjp(P, p, u, lps, lus):
+    rec = problem_record(P)
+    lp = np.zeros(P.n_cells)
+    lu = np.zeros((P.dim, P.n_cells))
+    _check(lib().oracle_stencil_vjp(ctypes.byref(rec), _ptr(_f64(p)), _ptr(_f64(u)), _ptr(_f64(lps)), _ptr(_f64(lus)),
+                                    _ptr(lp), _ptr(lu)))
+    return lp, lu
+
+
+def step(P, gamma, p, u, s):
+    """One forward step. Returns (p, u, s_next, iterates [(n_itr+1), 8])."""
+    rec = problem_record(P)
+    po = np.zeros(P.n_cells)
+    uo = np.zeros((P.dim, P.n_cells))
+    so = np.zeros(8)
+    it = np.zeros((P.n_itr + 1, 8))
+    _check(lib().oracle_step(ctypes.byref(rec), _ptr(_f64(gamma)), _ptr(_f64(p)), _ptr(_f64(u)), _ptr(_f64(s)),
+                             _ptr(po), _ptr(uo), _ptr(so), _ptr(it)))
+    return po, uo, so, it
+
+
+def spread(P, gamma, s):
+    """Returns (kappa [N], u^S [dim, N], count [N] of design points with non-zero weight)."""
+    rec = problem_record(P)
+    k = np.zeros(P.n_cells)
+    us = np.zeros((P.dim, P.n_cells))
+    cnt = np.zeros(P.n_cells, dtype=np.int32)
+    rc = lib().oracle_spread(ctypes.byref(rec), _ptr(_f64(gamma)), _ptr(_f64(s)), _ptr(k), _ptr(us),
+                             cnt.ctypes.data_as(ctypes.POINTER(ctypes.c_int)))
+    _check(rc)
+    return k, us, cnt
+
+
+def interp(P, s, u):
+    rec = problem_record(P)
+    uref = np.zeros((P.n_design, 3))
+    _check(lib().oracle_interp(ctypes.byref(rec), _ptr(_f64(s)), _ptr(_f64(u)), _ptr(uref)))
+    return uref
+
+
+def weight(kind: int, r: float):
+    dw = ctypes.c_double(0.0)
+    w = lib().oracle_weight(kind, r, ctypes.byref(dw))
+    return w, dw.value
+
+
+def lattice(dim: int):
+    """(c [Q,3] int, w [Q]) of the oracle's velocity set."""
+    c = np.zeros((15, 3), dtype=np.int32)
+    w = np.zeros(15)
+    Q = lib().oracle_lattice(dim, c.ctypes.data_as(ctypes.POINTER(ctypes.c_int)), _ptr(w))
+    return c[:Q].copy(), w[:Q].copy()
