@@ -1,0 +1,158 @@
+/*
+ * lks.h - C ABI of the GB300 library for the coupled lattice-kinetic-scheme (LKS) / rigid-body
+ * forward march and its discrete adjoint.
+ *
+ * Method: "Topology optimization of passively moving rigid bodies in unsteady flows"
+ * (arXiv 2601.18272). Per time step (Algorithm 1, inner loops):
+ *   - LKS predictor p*, u* from the previous state (Sec. 2.2, Eqs. p_tmp, u_tmp with the
+ *     equilibrium f^eq of Inamuro's LKS), boundary values prescribed directly (Sec. 2.2);
+ *   - N_itr fixed-point iterations (Sec. 3.1) of: rigid transform of the design grid
+ *     (Sec. 2.3, Eqs. rigid_body_position / rigid_body_velocity), spread of the Brinkman
+ *     coefficient and solid velocity onto the analysis grid (Eqs. kappa_mapping, us_mapping),
+ *     Brinkman update (Eq. u), fluid force and torque on the body and the explicit Euler
+ *     equations of motion (Sec. 2.4);
+ * and the reverse-time sweep giving dJ/dgamma for J = sum_d w_d s_d(N_t) (Sec. 2.5, 2.6).
+ *
+ * Conventions
+ *   - Lattice units: dx = dt = 1, one design point per analysis cell spacing, pivot at the
+ *     design-grid centre.
+ *   - Fields are planes of nx*ny*nz values, x fastest. Design arrays have ndx*ndy*ndz values,
+ *     x fastest.
+ *   - DOF vector s (8 doubles): (xG_x, xG_y, xG_z, uG_x, uG_y, uG_z, theta, omega).
+ *   - Every call returns an lks_status code; nothing traps or exits. A handle is not
+ *     thread-safe. All GPU work goes on the stream passed in (a cudaStream_t, or NULL for the
+ *     legacy default stream).
+ *   - Pointers named *_dev are device pointers owned by the caller; *_host are host pointers
+ *     owned by the caller. The library owns its workspace (allocated in lks_create within
+ *     hbm_budget_bytes, released in lks_destroy).
+ */
+#ifndef LKS_H_
+#define LKS_H_
+
+#include <stddef.h>
+
+#if defined(__GNUC__)
+#define LKS_API __attribute__((visibility("default")))
+#else
+#define LKS_API
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum lks_status {
+  LKS_OK = 0,
+  LKS_ERR_ARG = 1,          /* invalid argument or problem description */
+  LKS_ERR_OOM = 2,          /* device allocation failed */
+  LKS_ERR_BUDGET = 3,       /* workspace would exceed hbm_budget_bytes */
+  LKS_ERR_UNSTABLE = 4,     /* nu <= 0, i.e. A >= 3/4 in nu = (1/6 - 2A/9) dx (Sec. 2.2) */
+  LKS_ERR_BODY_OUTSIDE = 5, /* the mapped body reaches a non-periodic boundary layer */
+  LKS_ERR_NONFINITE = 6,    /* a non-finite force, torque or state was produced */
+  LKS_ERR_ORDER = 7,        /* adjoint or sensitivity requested before a forward / adjoint */
+  LKS_ERR_CUDA = 8,         /* a CUDA runtime call failed */
+  LKS_ERR_UNSUPPORTED = 9   /* valid but not supported by this build (e.g. grid/tile shape) */
+} lks_status;
+
+enum { LKS_D2Q9 = 9, LKS_D3Q15 = 15 };                   /* velocity sets (Sec. 2.2) */
+enum { LKS_BC_PERIODIC = 0, LKS_BC_INFLOW_OUTFLOW = 1, LKS_BC_WALL = 2, LKS_BC_PRESSURE = 3 };
+enum { LKS_W_COS4 = 0, LKS_W_BILINEAR = 1 };              /* grid-separation weight (Sec. 2.3) */
+enum { LKS_DOF_TX = 1, LKS_DOF_TY = 2, LKS_DOF_TZ = 4, LKS_DOF_ROT = 8 };
+enum { LKS_FP32 = 32, LKS_FP64 = 64 };                    /* field storage / arithmetic type */
+enum { LKS_CKPT_STORE_ALL = 0, LKS_CKPT_UNIFORM = 1 };
+enum { LKS_CKPT_NATIVE = 0, LKS_CKPT_BF16 = 1, LKS_CKPT_FP16 = 2 };
+
+/* Problem statement: grid, velocity set, design grid, body, fluid, run controls. */
+typedef struct lks_problem {
+  int dim;                /* 2 or 3 */
+  int velocity_set;       /* LKS_D2Q9 (dim 2) or LKS_D3Q15 (dim 3) */
+  int nx, ny, nz;         /* analysis grid in cells (nz = 1 for dim 2) */
+  int ndx, ndy, ndz;      /* design grid in points (ndz = 1 for dim 2) */
+  double body_centre[3];  /* x^G(0) in analysis coordinates */
+  int rot_axis;           /* single rotation axis 0/1/2 (2 in 2D) */
+  unsigned dof_mask;      /* LKS_DOF_* bits of the free degrees of freedom */
+  double mass;            /* M, constant (Sec. 2.1) */
+  double inertia;         /* I about rot_axis, constant (Sec. 2.1) */
+  double nu;              /* kinematic viscosity; A = 9/2 (1/6 - nu) */
+  double u_in;            /* inflow speed for LKS_BC_INFLOW_OUTFLOW */
+  double dp;              /* inlet pressure for LKS_BC_PRESSURE (outlet p = 0) */
+  int bc[3];              /* per axis; x: periodic/inflow-outflow/pressure, y,z: periodic/wall */
+  double kappa_max, q;    /* Brinkman interpolation (Eq. brinkman_coefficient) */
+  int weight_kind;        /* LKS_W_COS4 (Eq. weight_function) or LKS_W_BILINEAR */
+  int n_steps, n_itr;     /* N_t, N_itr (Sec. 3.1) */
+  double obj_weights[8];  /* J = sum_d obj_weights[d] * s_d(N_t) (Eqs. objective1, objective2) */
+  int field_precision;    /* LKS_FP32 or LKS_FP64 */
+  int ckpt_policy;        /* LKS_CKPT_STORE_ALL or LKS_CKPT_UNIFORM */
+  int ckpt_every;         /* checkpoint interval k for LKS_CKPT_UNIFORM */
+  int ckpt_format;        /* LKS_CKPT_NATIVE, LKS_CKPT_BF16 or LKS_CKPT_FP16 (FP32 fields) */
+  size_t hbm_budget_bytes;/* workspace limit, 0 = no limit */
+} lks_problem;
+
+typedef struct lks_handle lks_handle;
+
+/* Validate the problem and allocate the workspace. On success *out owns the device memory.
+ * Errors: LKS_ERR_ARG, LKS_ERR_UNSTABLE, LKS_ERR_UNSUPPORTED, LKS_ERR_BUDGET, LKS_ERR_OOM. */
+LKS_API int lks_create(const lks_problem* problem, lks_handle** out);
+
+/* Initial state for the next forward (Algorithm 1, "Initialize"). p [N], u [dim][N] and
+ * s [8] are host arrays (copied). Any pointer may be NULL to keep the default: p = 0,
+ * u = (u_in, 0, 0), body at rest at body_centre. */
+LKS_API int lks_set_initial_state(lks_handle* h, const double* p_host, const double* u_host, const double* s_host);
+
+/* Forward march over n_steps (Algorithm 1, state loop) for the design field gamma_dev
+ * [ndx*ndy*ndz] (device, values in [0,1]). Stores the DOF history and the checkpoints the
+ * adjoint needs. Synchronises the stream once to return J (host scalar).
+ * Errors: LKS_ERR_ARG, LKS_ERR_BODY_OUTSIDE, LKS_ERR_NONFINITE, LKS_ERR_CUDA. */
+LKS_API int lks_forward(lks_handle* h, const double* gamma_dev, double* J_host, void* stream);
+
+/* Reverse sweep (Algorithm 1, adjoint loop) seeded with dJ = seed. Enqueued on the stream,
+ * no synchronisation. Requires a prior lks_forward (else LKS_ERR_ORDER). */
+LKS_API int lks_adjoint(lks_handle* h, double seed, void* stream);
+
+/* dJ/dgamma [ndx*ndy*ndz] (device, FP64) from the last adjoint: the accumulated dJ/dkappa^ref
+ * chained through dkappa^ref/dgamma (Eq. brinkman_coefficient). M and I are held constant.
+ * Requires a prior lks_adjoint (else LKS_ERR_ORDER). Enqueued, no synchronisation. */
+LKS_API int lks_sensitivity(lks_handle* h, double* dJdgamma_dev, void* stream);
+
+/* End-to-end gradient with host buffers: copies gamma_host [N_D] to the device, runs forward,
+ * adjoint (seed 1) and sensitivity, copies dJdgamma_host [N_D] back and returns J.
+ * Synchronises the stream before returning. */
+LKS_API int lks_gradient_host(lks_handle* h, const double* gamma_host, double* J_host, double* dJdgamma_host, void* stream);
+
+/* DOF history of the last forward into host_buf [(n_steps+1)*8]; n = capacity in doubles. */
+LKS_API int lks_get_dof_history(lks_handle* h, double* host_buf, size_t n);
+
+/* Final state of the last forward: p [N], u [dim][N] as doubles (host). Only for
+ * LKS_CKPT_STORE_ALL or when n_steps is a multiple of ckpt_every. Synchronous. */
+LKS_API int lks_get_state(lks_handle* h, double* p_host, double* u_host);
+
+/* Adjoint of the initial state after the last lks_adjoint: dJ/dp0 [N], dJ/du0 [dim][N],
+ * dJ/ds0 [8] (host, any may be NULL). Synchronous. */
+LKS_API int lks_get_initial_adjoint(lks_handle* h, double* lam_p_host, double* lam_u_host, double* lam_s_host);
+
+/* Number of kernels this handle has launched (graph nodes counted per replay). */
+LKS_API long long lks_launch_count(const lks_handle* h);
+
+/* Kernel timing for the benchmark. enable = 1 runs later calls without CUDA graphs and brackets
+ * every launch of the named kernel family with CUDA events on the launching stream.
+ * lks_kernel_time returns the summed milliseconds and the launch count for the family
+ * ("stencil_fwd", "stencil_adj", "couple", "adj_cell", "adj_design", "recompute"). */
+LKS_API int lks_set_kernel_timing(lks_handle* h, int enable);
+LKS_API int lks_kernel_time(lks_handle* h, const char* family, double* ms_total, long long* launches);
+
+/* Bytes of device workspace held by the handle. */
+LKS_API size_t lks_workspace_bytes(const lks_handle* h);
+
+LKS_API void lks_destroy(lks_handle* h);
+
+/* Static description of a status code. */
+LKS_API const char* lks_status_string(int status);
+
+/* The cudaError_t value of the most recent LKS_ERR_CUDA return (0 if none). */
+LKS_API int lks_last_cuda_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* LKS_H_ */

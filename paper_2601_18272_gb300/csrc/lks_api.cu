@@ -1,0 +1,686 @@
+// C ABI of the library (include/lks.h): workspace, forward / adjoint scheduling, CUDA graphs.
+//
+// Forward (Algorithm 1, state loop): per step one stencil kernel over the grid and N_itr coupling
+// kernels over the body box; the step index lives on the device (Ctrl::t), so one captured graph
+// of L steps is replayed for every segment.
+//   store-all : every state slot and the per-step u* of the body box are kept (plain form).
+//   uniform   : ping-pong state, a checkpoint every k steps; the adjoint restores a checkpoint,
+//               recomputes the segment (stencil + Brinkman update with the stored DOF iterates)
+//               into a segment ring, then reverses it.
+// Adjoint (Algorithm 1, adjoint loop): per step, for k = N_itr..1 a cell-side and a design-side
+// reverse kernel, then the transposed stencil.
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <map>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "../../include/lks.h"
+#include "lks_kernels.h"
+
+using namespace lks;
+
+namespace {
+
+struct EventPair {
+  cudaEvent_t a, b;
+};
+
+struct TimerFamily {
+  std::vector<EventPair> pairs;
+  size_t used = 0;
+  double ms = 0.0;
+  long long launches = 0;
+};
+
+}  // namespace
+
+struct lks_handle {
+  lks_problem P;
+  Geo g;
+  int prec = 32;
+  size_t esz = 4;
+  // state rings
+  void* ring = nullptr;  // store-all: N_t + 1 slots; uniform: segment of every + 1 slots
+  int nring = 0;
+  void* pp = nullptr;    // uniform: ping-pong forward state (2 slots)
+  void* ckpt = nullptr;  // uniform: checkpoints at t = 0, k, 2k, ...
+  int nckpt = 0;
+  long long slot_elems = 0;
+  void* boxstore = nullptr;  // u* in the body box, one slab per step of the resident segment
+  int nbox = 0;
+  void* L = nullptr;  // adjoint fields, 2 slots
+  void* acc = nullptr;
+  void* scratch = nullptr;
+  void* kref = nullptr;
+  double* dkref = nullptr;
+  double* gamma = nullptr;
+  double* tmp_nd = nullptr;
+  Dof* it = nullptr;
+  Ctrl* ctrl = nullptr;
+  Moments* mom = nullptr;
+  double* partials = nullptr;
+  double* init_p = nullptr;
+  double* init_u = nullptr;
+  double* init_s = nullptr;
+  double* objw = nullptr;
+  double host_s0[8];
+  size_t bytes = 0;
+  std::vector<void*> allocs;
+  cudaStream_t cap = nullptr;
+  std::map<std::string, cudaGraphExec_t> graphs;
+  std::map<std::string, int> graph_kernels;
+  bool fwd_done = false, adj_done = false;
+  long long launches = 0;
+  bool timing = false;
+  std::map<std::string, TimerFamily> timers;
+  int chunk = 50;  // steps per captured graph in store-all mode
+};
+
+namespace {
+
+int g_last_cuda_error = 0;
+
+#define CK(call)                              \
+  do {                                        \
+    cudaError_t e_ = (call);                  \
+    if (e_ != cudaSuccess) {                  \
+      g_last_cuda_error = (int)e_;            \
+      return LKS_ERR_CUDA;                    \
+    }                                         \
+  } while (0)
+
+int dalloc(lks_handle* h, void** p, size_t bytes) {
+  if (bytes == 0) bytes = 16;
+  bytes = (bytes + 255) & ~(size_t)255;
+  if (h->P.hbm_budget_bytes && h->bytes + bytes > h->P.hbm_budget_bytes) return LKS_ERR_BUDGET;
+  cudaError_t e = cudaMalloc(p, bytes);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return LKS_ERR_OOM;
+  }
+  h->bytes += bytes;
+  h->allocs.push_back(*p);
+  return LKS_OK;
+}
+
+#define TRY(call)           \
+  do {                      \
+    int r_ = (call);        \
+    if (r_ != LKS_OK) {     \
+      return r_;            \
+    }                       \
+  } while (0)
+
+// Box extent from the design grid: circumscribed in the rotation plane if the body may rotate.
+void setup_box(lks_handle* h, bool rotated) {
+  Geo& g = h->g;
+  double half[3] = {0, 0, 0};
+  for (int a = 0; a < g.dim; ++a) half[a] = (g.nd[a] - 1) / 2.0;
+  if (rotated) {
+    const double r = std::sqrt(half[g.axb] * half[g.axb] + half[g.axc] * half[g.axc]);
+    half[g.axb] = half[g.axc] = r;
+  }
+  g.margin = 1;
+  g.box_cells = 1;
+  for (int a = 0; a < 3; ++a) {
+    if (a < g.dim) {
+      g.hb[a] = (int)std::ceil(half[a] - 1e-12);
+      g.B[a] = 2 * g.hb[a] + 2 * g.s + 2 * g.margin + 2;
+    } else {
+      g.hb[a] = 0;
+      g.B[a] = 1;
+    }
+    g.box_cells *= g.B[a];
+  }
+}
+
+int validate(const lks_problem* P) {
+  if (!P) return LKS_ERR_ARG;
+  if (P->dim != 2 && P->dim != 3) return LKS_ERR_ARG;
+  if (P->dim == 2 && (P->velocity_set != LKS_D2Q9 || P->nz != 1 || P->ndz != 1 || P->rot_axis != 2)) return LKS_ERR_ARG;
+  if (P->dim == 3 && P->velocity_set != LKS_D3Q15) return LKS_ERR_ARG;
+  if (P->dim == 3) return LKS_ERR_UNSUPPORTED;
+  if (P->nx < 4 || P->ny < 4 || (P->dim == 3 && P->nz < 4)) return LKS_ERR_ARG;
+  if (P->ndx < 1 || P->ndy < 1 || P->ndz < 1) return LKS_ERR_ARG;
+  if (P->rot_axis < 0 || P->rot_axis > 2) return LKS_ERR_ARG;
+  if (P->bc[0] != LKS_BC_PERIODIC && P->bc[0] != LKS_BC_INFLOW_OUTFLOW && P->bc[0] != LKS_BC_PRESSURE) return LKS_ERR_ARG;
+  for (int a = 1; a < 3; ++a)
+    if (P->bc[a] != LKS_BC_PERIODIC && P->bc[a] != LKS_BC_WALL) return LKS_ERR_ARG;
+  if (!(P->nu > 0.0)) return LKS_ERR_UNSTABLE;
+  if (P->n_steps < 1 || P->n_itr < 1) return LKS_ERR_ARG;
+  if (P->weight_kind != LKS_W_COS4 && P->weight_kind != LKS_W_BILINEAR) return LKS_ERR_ARG;
+  if (!(P->mass > 0.0) || !(P->inertia > 0.0)) return LKS_ERR_ARG;
+  if (P->field_precision != LKS_FP32 && P->field_precision != LKS_FP64) return LKS_ERR_ARG;
+  if (P->ckpt_policy != LKS_CKPT_STORE_ALL && P->ckpt_policy != LKS_CKPT_UNIFORM) return LKS_ERR_ARG;
+  if (P->ckpt_policy == LKS_CKPT_UNIFORM && P->ckpt_every < 1) return LKS_ERR_ARG;
+  if (P->ckpt_format != LKS_CKPT_NATIVE) return LKS_ERR_UNSUPPORTED;
+  // boundary pairs (x = 0,1 and nx-2,nx-1; y walls likewise) must share a stencil tile
+  if (P->bc[0] != LKS_BC_PERIODIC && P->nx % kTileX == 1) return LKS_ERR_UNSUPPORTED;
+  if (P->bc[1] == LKS_BC_WALL && P->ny % kTileY2 == 1) return LKS_ERR_UNSUPPORTED;
+  return LKS_OK;
+}
+
+template <typename T>
+Slots<T> ring_slots(lks_handle* h) {
+  return Slots<T>{(T*)h->ring, h->slot_elems, h->nring};
+}
+template <typename T>
+Slots<T> pp_slots(lks_handle* h) {
+  return Slots<T>{(T*)h->pp, h->slot_elems, 2};
+}
+
+// Launch bookkeeping: counts kernels and, in timing mode, brackets them with events.
+struct Launcher {
+  lks_handle* h;
+  cudaStream_t st;
+  bool capturing;
+  int kernels = 0;
+  template <typename F>
+  void operator()(const char* family, F&& f) {
+    EventPair* ev = nullptr;
+    if (h->timing && !capturing) {
+      TimerFamily& tf = h->timers[family];
+      if (tf.used == tf.pairs.size()) {
+        EventPair p;
+        cudaEventCreate(&p.a);
+        cudaEventCreate(&p.b);
+        tf.pairs.push_back(p);
+      }
+      ev = &tf.pairs[tf.used++];
+      tf.launches++;
+      cudaEventRecord(ev->a, st);
+    }
+    f(st);
+    if (ev) cudaEventRecord(ev->b, st);
+    ++kernels;
+    if (!capturing) ++h->launches;
+  }
+};
+
+void collect_timers(lks_handle* h) {
+  for (auto& kv : h->timers) {
+    TimerFamily& tf = kv.second;
+    for (size_t i = 0; i < tf.used; ++i) {
+      float ms = 0.f;
+      cudaEventSynchronize(tf.pairs[i].b);
+      cudaEventElapsedTime(&ms, tf.pairs[i].a, tf.pairs[i].b);
+      tf.ms += ms;
+    }
+    tf.used = 0;
+  }
+}
+
+// Run `body` either directly (timing mode) or as a cached CUDA graph captured on a private stream.
+template <typename Body>
+int run_graph(lks_handle* h, const std::string& key, cudaStream_t st, Body&& body) {
+  if (h->timing) {
+    Launcher L{h, st, false};
+    body(L);
+    CK(cudaGetLastError());
+    return LKS_OK;
+  }
+  auto itg = h->graphs.find(key);
+  if (itg == h->graphs.end()) {
+    cudaGraph_t graph;
+    CK(cudaStreamBeginCapture(h->cap, cudaStreamCaptureModeThreadLocal));
+    Launcher L{h, h->cap, true};
+    body(L);
+    cudaError_t e = cudaStreamEndCapture(h->cap, &graph);
+    if (e != cudaSuccess) {
+      g_last_cuda_error = (int)e;
+      return LKS_ERR_CUDA;
+    }
+    cudaGraphExec_t exec;
+    e = cudaGraphInstantiate(&exec, graph, 0);
+    cudaGraphDestroy(graph);
+    if (e != cudaSuccess) {
+      g_last_cuda_error = (int)e;
+      return LKS_ERR_CUDA;
+    }
+    itg = h->graphs.emplace(key, exec).first;
+    h->graph_kernels[key] = L.kernels;
+  }
+  CK(cudaGraphLaunch(itg->second, st));
+  h->launches += h->graph_kernels[key];
+  return LKS_OK;
+}
+
+void clear_graphs(lks_handle* h) {
+  for (auto& kv : h->graphs) cudaGraphExecDestroy(kv.second);
+  h->graphs.clear();
+  h->graph_kernels.clear();
+}
+
+template <typename T>
+void enqueue_fwd_steps(lks_handle* h, Launcher& L, const Slots<T>& S, int nsteps, bool store_box) {
+  const Geo& g = h->g;
+  for (int i = 0; i < nsteps; ++i) {
+    L("stencil_fwd", [&](cudaStream_t s) { launch_stencil_fwd<T>(g, S, h->ctrl, s); });
+    for (int k = 1; k <= g.K; ++k)
+      L("couple", [&](cudaStream_t s) {
+        launch_couple<T>(g, S, h->ctrl, h->it, (const T*)h->kref, h->mom, h->partials, k,
+                         store_box ? (T*)h->boxstore : nullptr, h->nbox, s);
+      });
+  }
+}
+
+template <typename T>
+void enqueue_recompute(lks_handle* h, Launcher& L, const Slots<T>& S, int nsteps) {
+  const Geo& g = h->g;
+  for (int i = 0; i < nsteps; ++i) {
+    L("stencil_fwd", [&](cudaStream_t s) { launch_stencil_fwd<T>(g, S, h->ctrl, s); });
+    L("recompute", [&](cudaStream_t s) {
+      launch_apply<T>(g, S, h->ctrl, h->it, (const T*)h->kref, (T*)h->boxstore, h->nbox, s);
+    });
+  }
+}
+
+template <typename T>
+void enqueue_adj_steps(lks_handle* h, Launcher& L, const Slots<T>& S, int nsteps) {
+  const Geo& g = h->g;
+  const long long BC = g.box_cells;
+  (void)BC;
+  for (int i = 0; i < nsteps; ++i) {
+    for (int k = g.K; k >= 1; --k) {
+      L("adj_cell", [&](cudaStream_t s) {
+        launch_adj_cell<T>(g, h->ctrl, h->it, (const T*)h->kref, (const T*)h->boxstore, h->nbox, (T*)h->L,
+                           h->slot_elems, (T*)h->acc, (T*)h->scratch, k, s);
+      });
+      L("adj_design", [&](cudaStream_t s) {
+        launch_adj_design<T>(g, h->ctrl, h->it, (const T*)h->kref, (const T*)h->scratch, h->dkref, h->partials, k, s);
+      });
+    }
+    L("stencil_adj", [&](cudaStream_t s) { launch_stencil_adj<T>(g, S, (T*)h->L, h->slot_elems, h->ctrl, s); });
+  }
+}
+
+template <typename T>
+int forward_impl(lks_handle* h, cudaStream_t st) {
+  const Geo& g = h->g;
+  const int NT = h->P.n_steps;
+  Launcher L0{h, st, false};
+  if (h->P.ckpt_policy == LKS_CKPT_STORE_ALL) {
+    Slots<T> S = ring_slots<T>(h);
+    L0("init", [&](cudaStream_t s) { launch_init_forward<T>(g, S, h->init_p, h->init_u, h->init_s, h->it, h->ctrl, s); });
+    for (int t0 = 1; t0 <= NT; t0 += h->chunk) {
+      const int n = std::min(h->chunk, NT - t0 + 1);
+      TRY(run_graph(h, "fwd_sa_" + std::to_string(n), st,
+                    [&](Launcher& L) { enqueue_fwd_steps<T>(h, L, S, n, true); }));
+    }
+  } else {
+    Slots<T> S = pp_slots<T>(h);
+    const int every = h->P.ckpt_every;
+    L0("init", [&](cudaStream_t s) { launch_init_forward<T>(g, S, h->init_p, h->init_u, h->init_s, h->it, h->ctrl, s); });
+    L0("ckpt", [&](cudaStream_t s) { launch_ckpt_pack<T>(g, S, (T*)h->ckpt, h->slot_elems, every, h->ctrl, s); });
+    for (int t0 = 0; t0 < NT; t0 += every) {
+      const int n = std::min(every, NT - t0);
+      const bool pack = (t0 + n < NT);
+      TRY(run_graph(h, "fwd_u_" + std::to_string(n) + (pack ? "p" : ""), st, [&](Launcher& L) {
+        enqueue_fwd_steps<T>(h, L, S, n, false);
+        if (pack) L("ckpt", [&](cudaStream_t s) { launch_ckpt_pack<T>(g, S, (T*)h->ckpt, h->slot_elems, every, h->ctrl, s); });
+      }));
+    }
+  }
+  CK(cudaGetLastError());
+  return LKS_OK;
+}
+
+template <typename T>
+int adjoint_impl(lks_handle* h, double seed, cudaStream_t st) {
+  const Geo& g = h->g;
+  const int NT = h->P.n_steps;
+  Launcher L0{h, st, false};
+  CK(cudaMemsetAsync(h->L, 0, 2 * h->slot_elems * h->esz, st));
+  L0("init", [&](cudaStream_t s) { launch_adj_init(g, h->ctrl, h->objw, seed, h->dkref, g.ND, s); });
+  if (h->P.ckpt_policy == LKS_CKPT_STORE_ALL) {
+    Slots<T> S = ring_slots<T>(h);
+    L0("init", [&](cudaStream_t s) { launch_set_step(h->ctrl, NT, 0, s); });
+    for (int t1 = NT; t1 >= 1; t1 -= h->chunk) {
+      const int n = std::min(h->chunk, t1);
+      TRY(run_graph(h, "adj_sa_" + std::to_string(n), st, [&](Launcher& L) { enqueue_adj_steps<T>(h, L, S, n); }));
+    }
+  } else {
+    Slots<T> S = ring_slots<T>(h);
+    const int every = h->P.ckpt_every;
+    const int nseg = (NT + every - 1) / every;
+    for (int c = nseg - 1; c >= 0; --c) {
+      const int t0 = c * every;
+      const int n = std::min(every, NT - t0);
+      CK(cudaMemcpyAsync(h->ring, (char*)h->ckpt + (size_t)c * h->slot_elems * h->esz, h->slot_elems * h->esz,
+                         cudaMemcpyDeviceToDevice, st));
+      L0("init", [&](cudaStream_t s) { launch_set_step(h->ctrl, t0 + 1, t0, s); });
+      TRY(run_graph(h, "rec_" + std::to_string(n), st, [&](Launcher& L) { enqueue_recompute<T>(h, L, S, n); }));
+      L0("init", [&](cudaStream_t s) { launch_set_step(h->ctrl, t0 + n, t0, s); });
+      TRY(run_graph(h, "adj_u_" + std::to_string(n), st, [&](Launcher& L) { enqueue_adj_steps<T>(h, L, S, n); }));
+    }
+  }
+  CK(cudaGetLastError());
+  return LKS_OK;
+}
+
+template <typename T>
+int allocate(lks_handle* h) {
+  Geo& g = h->g;
+  const lks_problem& P = h->P;
+  const int NT = P.n_steps, K = P.n_itr, D = g.dim;
+  h->slot_elems = (long long)(D + 1) * g.N;
+  const size_t slot_bytes = (size_t)h->slot_elems * sizeof(T);
+  if (P.ckpt_policy == LKS_CKPT_STORE_ALL) {
+    h->nring = NT + 1;
+    h->nbox = NT;
+  } else {
+    h->nring = P.ckpt_every + 1;
+    h->nbox = P.ckpt_every;
+    h->nckpt = (NT + P.ckpt_every - 1) / P.ckpt_every;
+    TRY(dalloc(h, &h->pp, 2 * slot_bytes));
+    TRY(dalloc(h, &h->ckpt, (size_t)h->nckpt * slot_bytes));
+  }
+  TRY(dalloc(h, &h->ring, (size_t)h->nring * slot_bytes));
+  TRY(dalloc(h, &h->boxstore, (size_t)h->nbox * g.box_cells * D * sizeof(T)));
+  TRY(dalloc(h, &h->L, 2 * slot_bytes));
+  TRY(dalloc(h, &h->acc, (size_t)g.box_cells * D * sizeof(T)));
+  TRY(dalloc(h, &h->scratch, (size_t)g.box_cells * (2 * D + 1) * sizeof(T)));
+  TRY(dalloc(h, &h->kref, (size_t)g.ND * sizeof(T)));
+  TRY(dalloc(h, (void**)&h->dkref, (size_t)g.ND * sizeof(double)));
+  TRY(dalloc(h, (void**)&h->gamma, (size_t)g.ND * sizeof(double)));
+  TRY(dalloc(h, (void**)&h->tmp_nd, (size_t)g.ND * sizeof(double)));
+  TRY(dalloc(h, (void**)&h->it, (size_t)(NT + 1) * (K + 1) * sizeof(Dof)));
+  TRY(dalloc(h, (void**)&h->ctrl, sizeof(Ctrl)));
+  TRY(dalloc(h, (void**)&h->mom, sizeof(Moments)));
+  const long long bx = ((g.B[0] + 31) / 32) * (long long)((g.B[1] + 7) / 8) * g.B[2];
+  const long long bd = (g.ND + 255) / 256;
+  const long long nblk = std::max(bx, bd) + 1;
+  TRY(dalloc(h, (void**)&h->partials, (size_t)nblk * 8 * sizeof(double)));
+  TRY(dalloc(h, (void**)&h->init_p, (size_t)g.N * sizeof(double)));
+  TRY(dalloc(h, (void**)&h->init_u, (size_t)D * g.N * sizeof(double)));
+  TRY(dalloc(h, (void**)&h->init_s, 8 * sizeof(double)));
+  TRY(dalloc(h, (void**)&h->objw, 8 * sizeof(double)));
+  CK(cudaMemset(h->ctrl, 0, sizeof(Ctrl)));
+  CK(cudaMemset(h->L, 0, 2 * slot_bytes));
+  CK(cudaMemcpy(h->objw, P.obj_weights, 8 * sizeof(double), cudaMemcpyHostToDevice));
+  return LKS_OK;
+}
+
+int set_default_initial_state(lks_handle* h) {
+  const Geo& g = h->g;
+  std::vector<double> p((size_t)g.N, 0.0), u((size_t)g.dim * g.N, 0.0);
+  for (long long n = 0; n < g.N; ++n) u[n] = h->P.u_in;
+  CK(cudaMemcpy(h->init_p, p.data(), p.size() * sizeof(double), cudaMemcpyHostToDevice));
+  CK(cudaMemcpy(h->init_u, u.data(), u.size() * sizeof(double), cudaMemcpyHostToDevice));
+  for (int a = 0; a < 8; ++a) h->host_s0[a] = 0.0;
+  for (int a = 0; a < 3; ++a) h->host_s0[a] = h->P.body_centre[a];
+  CK(cudaMemcpy(h->init_s, h->host_s0, 8 * sizeof(double), cudaMemcpyHostToDevice));
+  return LKS_OK;
+}
+
+void refresh_box(lks_handle* h) {
+  const bool rotated = (h->g.dof_mask & LKS_DOF_ROT) || h->host_s0[6] != 0.0;
+  const int old[3] = {h->g.B[0], h->g.B[1], h->g.B[2]};
+  setup_box(h, rotated);
+  if (old[0] != h->g.B[0] || old[1] != h->g.B[1] || old[2] != h->g.B[2]) clear_graphs(h);
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* lks_status_string(int s) {
+  switch (s) {
+    case LKS_OK: return "ok";
+    case LKS_ERR_ARG: return "invalid argument";
+    case LKS_ERR_OOM: return "device allocation failed";
+    case LKS_ERR_BUDGET: return "workspace exceeds hbm_budget_bytes";
+    case LKS_ERR_UNSTABLE: return "nu <= 0 (A >= 3/4)";
+    case LKS_ERR_BODY_OUTSIDE: return "body reaches a non-periodic boundary layer";
+    case LKS_ERR_NONFINITE: return "non-finite force, torque or state";
+    case LKS_ERR_ORDER: return "call order (forward before adjoint before sensitivity)";
+    case LKS_ERR_CUDA: return "CUDA runtime error";
+    case LKS_ERR_UNSUPPORTED: return "unsupported configuration";
+    default: return "unknown status";
+  }
+}
+
+int lks_last_cuda_error(void) { return g_last_cuda_error; }
+
+int lks_create(const lks_problem* P, lks_handle** out) {
+  if (!out) return LKS_ERR_ARG;
+  *out = nullptr;
+  int v = validate(P);
+  if (v != LKS_OK) return v;
+  lks_handle* h = new (std::nothrow) lks_handle();
+  if (!h) return LKS_ERR_OOM;
+  h->P = *P;
+  h->prec = P->field_precision;
+  h->esz = (h->prec == LKS_FP64) ? 8 : 4;
+  Geo& g = h->g;
+  std::memset(&g, 0, sizeof(g));
+  g.dim = P->dim;
+  g.n[0] = P->nx;
+  g.n[1] = P->ny;
+  g.n[2] = P->dim == 3 ? P->nz : 1;
+  g.N = (long long)g.n[0] * g.n[1] * g.n[2];
+  for (int a = 0; a < 3; ++a) g.bc[a] = (a < g.dim) ? P->bc[a] : LKS_BC_PERIODIC;
+  g.nd[0] = P->ndx;
+  g.nd[1] = P->ndy;
+  g.nd[2] = P->dim == 3 ? P->ndz : 1;
+  g.ND = g.nd[0] * g.nd[1] * g.nd[2];
+  for (int a = 0; a < 3; ++a) g.xic[a] = (a < g.dim) ? (g.nd[a] - 1) / 2.0 : 0.0;
+  g.ax = P->rot_axis;
+  g.axb = (g.ax + 1) % 3;
+  g.axc = (g.ax + 2) % 3;
+  g.dof_mask = (int)P->dof_mask;
+  g.wk = P->weight_kind;
+  g.s = (P->weight_kind == LKS_W_BILINEAR) ? 1 : 2;
+  g.K = P->n_itr;
+  g.A = 4.5 * (1.0 / 6.0 - P->nu);
+  g.u_in = P->u_in;
+  g.dp = P->dp;
+  g.mass = P->mass;
+  g.inertia = P->inertia;
+  setup_box(h, true);  // allocate for the rotated (largest) box
+  for (int a = 0; a < g.dim; ++a)
+    if (g.bc[a] == LKS_BC_PERIODIC && g.B[a] > g.n[a]) {
+      delete h;
+      return LKS_ERR_UNSUPPORTED;
+    }
+  int r = (h->prec == LKS_FP64) ? allocate<double>(h) : allocate<float>(h);
+  if (r == LKS_OK) r = set_default_initial_state(h);
+  if (r == LKS_OK && cudaStreamCreateWithFlags(&h->cap, cudaStreamNonBlocking) != cudaSuccess) r = LKS_ERR_CUDA;
+  if (r != LKS_OK) {
+    lks_destroy(h);
+    return r;
+  }
+  refresh_box(h);
+  *out = h;
+  return LKS_OK;
+}
+
+int lks_set_initial_state(lks_handle* h, const double* p, const double* u, const double* s) {
+  if (!h) return LKS_ERR_ARG;
+  const Geo& g = h->g;
+  int r = set_default_initial_state(h);
+  if (r != LKS_OK) return r;
+  if (p) CK(cudaMemcpy(h->init_p, p, (size_t)g.N * sizeof(double), cudaMemcpyHostToDevice));
+  if (u) CK(cudaMemcpy(h->init_u, u, (size_t)g.dim * g.N * sizeof(double), cudaMemcpyHostToDevice));
+  if (s) {
+    for (int a = 0; a < 8; ++a) h->host_s0[a] = s[a];
+    CK(cudaMemcpy(h->init_s, h->host_s0, 8 * sizeof(double), cudaMemcpyHostToDevice));
+  }
+  refresh_box(h);
+  return LKS_OK;
+}
+
+int lks_forward(lks_handle* h, const double* gamma_dev, double* J_host, void* stream) {
+  if (!h || !gamma_dev) return LKS_ERR_ARG;
+  cudaStream_t st = (cudaStream_t)stream;
+  const Geo& g = h->g;
+  h->fwd_done = h->adj_done = false;
+  if ((const void*)gamma_dev != (const void*)h->gamma)
+    CK(cudaMemcpyAsync(h->gamma, gamma_dev, (size_t)g.ND * sizeof(double), cudaMemcpyDeviceToDevice, st));
+  Launcher L0{h, st, false};
+  if (h->prec == LKS_FP64)
+    L0("prep", [&](cudaStream_t s) { launch_prep<double>(g, h->gamma, h->P.kappa_max, h->P.q, (double*)h->kref, h->mom, h->partials, h->ctrl, s); });
+  else
+    L0("prep", [&](cudaStream_t s) { launch_prep<float>(g, h->gamma, h->P.kappa_max, h->P.q, (float*)h->kref, h->mom, h->partials, h->ctrl, s); });
+  int r = (h->prec == LKS_FP64) ? forward_impl<double>(h, st) : forward_impl<float>(h, st);
+  if (r != LKS_OK) return r;
+  Dof last;
+  Ctrl c;
+  CK(cudaMemcpyAsync(&last, h->it + (size_t)h->P.n_steps * (g.K + 1), sizeof(Dof), cudaMemcpyDeviceToHost, st));
+  CK(cudaMemcpyAsync(&c, h->ctrl, sizeof(Ctrl), cudaMemcpyDeviceToHost, st));
+  CK(cudaStreamSynchronize(st));
+  if (h->timing) collect_timers(h);
+  double J = 0.0;
+  for (int a = 0; a < 8; ++a) J += h->P.obj_weights[a] * last.s[a];
+  if (J_host) *J_host = J;
+  if (c.status & ST_BODY_OUTSIDE) return LKS_ERR_BODY_OUTSIDE;
+  if (c.status & ST_BOX_OVERFLOW) return LKS_ERR_BODY_OUTSIDE;
+  if ((c.status & ST_NONFINITE) || !std::isfinite(J)) return LKS_ERR_NONFINITE;
+  h->fwd_done = true;
+  return LKS_OK;
+}
+
+int lks_adjoint(lks_handle* h, double seed, void* stream) {
+  if (!h) return LKS_ERR_ARG;
+  if (!h->fwd_done) return LKS_ERR_ORDER;
+  cudaStream_t st = (cudaStream_t)stream;
+  int r = (h->prec == LKS_FP64) ? adjoint_impl<double>(h, seed, st) : adjoint_impl<float>(h, seed, st);
+  if (r != LKS_OK) return r;
+  if (h->timing) {
+    CK(cudaStreamSynchronize(st));
+    collect_timers(h);
+  }
+  h->adj_done = true;
+  return LKS_OK;
+}
+
+int lks_sensitivity(lks_handle* h, double* out, void* stream) {
+  if (!h || !out) return LKS_ERR_ARG;
+  if (!h->adj_done) return LKS_ERR_ORDER;
+  cudaStream_t st = (cudaStream_t)stream;
+  launch_sensitivity(h->g, h->gamma, h->dkref, h->P.kappa_max, h->P.q, out, st);
+  ++h->launches;
+  CK(cudaGetLastError());
+  return LKS_OK;
+}
+
+int lks_gradient_host(lks_handle* h, const double* gamma_host, double* J_host, double* dJdgamma_host, void* stream) {
+  if (!h || !gamma_host) return LKS_ERR_ARG;
+  cudaStream_t st = (cudaStream_t)stream;
+  const size_t nb = (size_t)h->g.ND * sizeof(double);
+  CK(cudaMemcpyAsync(h->gamma, gamma_host, nb, cudaMemcpyHostToDevice, st));
+  int r = lks_forward(h, h->gamma, J_host, stream);
+  if (r != LKS_OK) return r;
+  r = lks_adjoint(h, 1.0, stream);
+  if (r != LKS_OK) return r;
+  r = lks_sensitivity(h, h->tmp_nd, stream);
+  if (r != LKS_OK) return r;
+  if (dJdgamma_host) CK(cudaMemcpyAsync(dJdgamma_host, h->tmp_nd, nb, cudaMemcpyDeviceToHost, st));
+  CK(cudaStreamSynchronize(st));
+  return LKS_OK;
+}
+
+int lks_get_dof_history(lks_handle* h, double* buf, size_t n) {
+  if (!h || !buf) return LKS_ERR_ARG;
+  if (!h->fwd_done) return LKS_ERR_ORDER;
+  const int NT = h->P.n_steps, K = h->g.K;
+  if (n < (size_t)(NT + 1) * 8) return LKS_ERR_ARG;
+  std::vector<Dof> rows((size_t)(NT + 1) * (K + 1));
+  CK(cudaMemcpy(rows.data(), h->it, rows.size() * sizeof(Dof), cudaMemcpyDeviceToHost));
+  for (int t = 0; t <= NT; ++t)
+    for (int a = 0; a < 8; ++a) buf[(size_t)t * 8 + a] = rows[(size_t)t * (K + 1)].s[a];
+  return LKS_OK;
+}
+
+int lks_get_state(lks_handle* h, double* p, double* u) {
+  if (!h) return LKS_ERR_ARG;
+  if (!h->fwd_done) return LKS_ERR_ORDER;
+  const int NT = h->P.n_steps;
+  const void* src;
+  if (h->P.ckpt_policy == LKS_CKPT_STORE_ALL)
+    src = (const char*)h->ring + (size_t)NT * h->slot_elems * h->esz;
+  else
+    src = (const char*)h->pp + (size_t)(NT & 1) * h->slot_elems * h->esz;
+  const long long M = h->slot_elems, N = h->g.N;
+  std::vector<char> raw((size_t)M * h->esz);
+  CK(cudaDeviceSynchronize());
+  CK(cudaMemcpy(raw.data(), src, raw.size(), cudaMemcpyDeviceToHost));
+  for (long long i = 0; i < M; ++i) {
+    const double v = (h->esz == 8) ? ((const double*)raw.data())[i] : (double)((const float*)raw.data())[i];
+    if (i < N) {
+      if (p) p[i] = v;
+    } else if (u) {
+      u[i - N] = v;
+    }
+  }
+  return LKS_OK;
+}
+
+int lks_get_initial_adjoint(lks_handle* h, double* lp, double* lu, double* ls) {
+  if (!h) return LKS_ERR_ARG;
+  if (!h->adj_done) return LKS_ERR_ORDER;
+  const long long M = h->slot_elems, N = h->g.N;
+  std::vector<char> raw((size_t)M * h->esz);
+  CK(cudaDeviceSynchronize());
+  CK(cudaMemcpy(raw.data(), h->L, raw.size(), cudaMemcpyDeviceToHost));  // lambda(0) sits in slot 0
+  for (long long i = 0; i < M; ++i) {
+    const double v = (h->esz == 8) ? ((const double*)raw.data())[i] : (double)((const float*)raw.data())[i];
+    if (i < N) {
+      if (lp) lp[i] = v;
+    } else if (lu) {
+      lu[i - N] = v;
+    }
+  }
+  if (ls) {
+    Ctrl c;
+    CK(cudaMemcpy(&c, h->ctrl, sizeof(Ctrl), cudaMemcpyDeviceToHost));
+    for (int a = 0; a < 8; ++a) ls[a] = c.lam_s0[a];
+  }
+  return LKS_OK;
+}
+
+long long lks_launch_count(const lks_handle* h) { return h ? h->launches : 0; }
+
+int lks_set_kernel_timing(lks_handle* h, int enable) {
+  if (!h) return LKS_ERR_ARG;
+  h->timing = enable != 0;
+  for (auto& kv : h->timers) {
+    kv.second.ms = 0.0;
+    kv.second.launches = 0;
+    kv.second.used = 0;
+  }
+  return LKS_OK;
+}
+
+int lks_kernel_time(lks_handle* h, const char* family, double* ms, long long* launches) {
+  if (!h || !family) return LKS_ERR_ARG;
+  auto itf = h->timers.find(family);
+  if (itf == h->timers.end()) {
+    if (ms) *ms = 0.0;
+    if (launches) *launches = 0;
+    return LKS_OK;
+  }
+  if (ms) *ms = itf->second.ms;
+  if (launches) *launches = itf->second.launches;
+  return LKS_OK;
+}
+
+size_t lks_workspace_bytes(const lks_handle* h) { return h ? h->bytes : 0; }
+
+void lks_destroy(lks_handle* h) {
+  if (!h) return;
+  clear_graphs(h);
+  for (auto& kv : h->timers)
+    for (auto& p : kv.second.pairs) {
+      cudaEventDestroy(p.a);
+      cudaEventDestroy(p.b);
+    }
+  for (void* p : h->allocs) cudaFree(p);
+  if (h->cap) cudaStreamDestroy(h->cap);
+  delete h;
+}
+
+}  // extern "C"

@@ -1,0 +1,294 @@
+"""ctypes binding of the C ABI in include/lks.h (argument marshalling only).
+
+Every step of the forward march, adjoint sweep and sensitivity runs in the CUDA library
+``lib/liblks_gb300.so``; this module only converts arguments. If the library cannot be built or
+loaded, every call raises: there is no CPU path.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from typing import Optional
+
+import numpy as np
+
+from . import build as _build
+
+LKS_OK = 0
+LKS_D2Q9, LKS_D3Q15 = 9, 15
+LKS_FP32, LKS_FP64 = 32, 64
+LKS_CKPT_STORE_ALL, LKS_CKPT_UNIFORM = 0, 1
+LKS_CKPT_NATIVE, LKS_CKPT_BF16, LKS_CKPT_FP16 = 0, 1, 2
+STATUS = {0: "LKS_OK", 1: "LKS_ERR_ARG", 2: "LKS_ERR_OOM", 3: "LKS_ERR_BUDGET", 4: "LKS_ERR_UNSTABLE",
+          5: "LKS_ERR_BODY_OUTSIDE", 6: "LKS_ERR_NONFINITE", 7: "LKS_ERR_ORDER", 8: "LKS_ERR_CUDA",
+          9: "LKS_ERR_UNSUPPORTED"}
+
+
+class lks_problem(ctypes.Structure):  # noqa: N801  (mirrors the C struct name)
+    _fields_ = [
+        ("dim", ctypes.c_int),
+        ("velocity_set", ctypes.c_int),
+        ("nx", ctypes.c_int), ("ny", ctypes.c_int), ("nz", ctypes.c_int),
+        ("ndx", ctypes.c_int), ("ndy", ctypes.c_int), ("ndz", ctypes.c_int),
+        ("body_centre", ctypes.c_double * 3),
+        ("rot_axis", ctypes.c_int),
+        ("dof_mask", ctypes.c_uint),
+        ("mass", ctypes.c_double),
+        ("inertia", ctypes.c_double),
+        ("nu", ctypes.c_double),
+        ("u_in", ctypes.c_double),
+        ("dp", ctypes.c_double),
+        ("bc", ctypes.c_int * 3),
+        ("kappa_max", ctypes.c_double),
+        ("q", ctypes.c_double),
+        ("weight_kind", ctypes.c_int),
+        ("n_steps", ctypes.c_int),
+        ("n_itr", ctypes.c_int),
+        ("obj_weights", ctypes.c_double * 8),
+        ("field_precision", ctypes.c_int),
+        ("ckpt_policy", ctypes.c_int),
+        ("ckpt_every", ctypes.c_int),
+        ("ckpt_format", ctypes.c_int),
+        ("hbm_budget_bytes", ctypes.c_size_t),
+    ]
+
+
+class LksError(RuntimeError):
+    def __init__(self, code: int, where: str):
+        self.code = code
+        detail = ""
+        if code == 8 and _lib is not None:
+            detail = f" (cudaError {_lib.lks_last_cuda_error()})"
+        super().__init__(f"{where}: {STATUS.get(code, code)}{detail}")
+
+
+_lib = None
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def load() -> ctypes.CDLL:
+    """Load (building first if needed) the CUDA library. Raises if it cannot be built or loaded."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    path = _build.build()
+    L = ctypes.CDLL(path)
+    vp, dp, sz = ctypes.c_void_p, ctypes.POINTER(ctypes.c_double), ctypes.c_size_t
+    hp = ctypes.c_void_p
+    L.lks_create.argtypes = [ctypes.POINTER(lks_problem), ctypes.POINTER(ctypes.c_void_p)]
+    L.lks_set_initial_state.argtypes = [hp, dp, dp, dp]
+    L.lks_forward.argtypes = [hp, vp, dp, vp]
+    L.lks_adjoint.argtypes = [hp, ctypes.c_double, vp]
+    L.lks_sensitivity.argtypes = [hp, vp, vp]
+    L.lks_gradient_host.argtypes = [hp, dp, dp, dp, vp]
+    L.lks_get_dof_history.argtypes = [hp, dp, sz]
+    L.lks_get_state.argtypes = [hp, dp, dp]
+    L.lks_get_initial_adjoint.argtypes = [hp, dp, dp, dp]
+    L.lks_launch_count.argtypes = [hp]
+    L.lks_launch_count.restype = ctypes.c_longlong
+    L.lks_set_kernel_timing.argtypes = [hp, ctypes.c_int]
+    L.lks_kernel_time.argtypes = [hp, ctypes.c_char_p, dp, ctypes.POINTER(ctypes.c_longlong)]
+    L.lks_workspace_bytes.argtypes = [hp]
+    L.lks_workspace_bytes.restype = ctypes.c_size_t
+    L.lks_destroy.argtypes = [hp]
+    L.lks_destroy.restype = None
+    L.lks_status_string.argtypes = [ctypes.c_int]
+    L.lks_status_string.restype = ctypes.c_char_p
+    L.lks_last_cuda_error.argtypes = []
+    _lib = L
+    return L
+
+
+def _check(code: int, where: str):
+    if code != LKS_OK:
+        raise LksError(code, where)
+
+
+def _dptr(a: Optional[np.ndarray]):
+    if a is None:
+        return None
+    assert a.dtype == np.float64 and a.flags.c_contiguous
+    return a.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+
+
+def problem_struct(P, precision: Optional[int] = None, ckpt_policy: Optional[int] = None,
+                   ckpt_every: Optional[int] = None, ckpt_format: Optional[int] = None,
+                   n_steps: Optional[int] = None, hbm_budget_bytes: int = 0) -> lks_problem:
+    """lks_problem from a ``workloads.Problem`` (optionally overriding the run controls)."""
+    s = lks_problem()
+    s.dim = P.dim
+    s.velocity_set = LKS_D2Q9 if P.dim == 2 else LKS_D3Q15
+    s.nx, s.ny, s.nz = P.nx, P.ny, P.nz
+    s.ndx, s.ndy, s.ndz = P.ndx, P.ndy, P.ndz
+    for a in range(3):
+        s.body_centre[a] = P.body_centre[a]
+        s.bc[a] = P.bc[a]
+    s.rot_axis = P.rot_axis
+    s.dof_mask = P.dof_mask
+    s.mass, s.inertia, s.nu, s.u_in, s.dp = P.mass, P.inertia, P.nu, P.u_in, P.dp
+    s.kappa_max, s.q = P.kappa_max, P.q
+    s.weight_kind = P.weight_kind
+    s.n_steps = P.n_steps if n_steps is None else n_steps
+    s.n_itr = P.n_itr
+    for a in range(8):
+        s.obj_weights[a] = P.obj_weights[a]
+    s.field_precision = P.field_precision if precision is None else precision
+    s.ckpt_policy = P.ckpt_policy if ckpt_policy is None else ckpt_policy
+    s.ckpt_every = P.ckpt_every if ckpt_every is None else ckpt_every
+    s.ckpt_format = P.ckpt_format if ckpt_format is None else ckpt_format
+    if s.ckpt_format != LKS_CKPT_NATIVE and s.field_precision == LKS_FP64:
+        s.ckpt_format = LKS_CKPT_NATIVE
+    s.hbm_budget_bytes = hbm_budget_bytes
+    return s
+
+
+# ---- the C ABI, one Python function per entry point --------------------------------------
+def lks_create(problem: lks_problem) -> ctypes.c_void_p:
+    h = ctypes.c_void_p()
+    _check(load().lks_create(ctypes.byref(problem), ctypes.byref(h)), "lks_create")
+    return h
+
+
+def lks_set_initial_state(h, p: Optional[np.ndarray] = None, u: Optional[np.ndarray] = None,
+                          s: Optional[np.ndarray] = None):
+    conv = lambda a: None if a is None else np.ascontiguousarray(a, dtype=np.float64)  # noqa: E731
+    p, u, s = conv(p), conv(u), conv(s)
+    _check(load().lks_set_initial_state(h, _dptr(p), _dptr(u), _dptr(s)), "lks_set_initial_state")
+
+
+def lks_forward(h, gamma_dev_ptr: int, stream: int = 0) -> float:
+    J = ctypes.c_double(0.0)
+    _check(load().lks_forward(h, ctypes.c_void_p(gamma_dev_ptr), ctypes.byref(J), ctypes.c_void_p(stream)),
+           "lks_forward")
+    return J.value
+
+
+def lks_adjoint(h, seed: float = 1.0, stream: int = 0):
+    _check(load().lks_adjoint(h, float(seed), ctypes.c_void_p(stream)), "lks_adjoint")
+
+
+def lks_sensitivity(h, out_dev_ptr: int, stream: int = 0):
+    _check(load().lks_sensitivity(h, ctypes.c_void_p(out_dev_ptr), ctypes.c_void_p(stream)), "lks_sensitivity")
+
+
+def lks_gradient_host(h, gamma: np.ndarray, out: np.ndarray, stream: int = 0) -> float:
+    J = ctypes.c_double(0.0)
+    _check(load().lks_gradient_host(h, _dptr(gamma), ctypes.byref(J), _dptr(out), ctypes.c_void_p(stream)),
+           "lks_gradient_host")
+    return J.value
+
+
+def lks_get_dof_history(h, n_steps: int) -> np.ndarray:
+    buf = np.zeros((n_steps + 1, 8))
+    _check(load().lks_get_dof_history(h, _dptr(buf), buf.size), "lks_get_dof_history")
+    return buf
+
+
+def lks_get_state(h, n_cells: int, dim: int):
+    p = np.zeros(n_cells)
+    u = np.zeros((dim, n_cells))
+    _check(load().lks_get_state(h, _dptr(p), _dptr(u)), "lks_get_state")
+    return p, u
+
+
+def lks_get_initial_adjoint(h, n_cells: int, dim: int):
+    lp = np.zeros(n_cells)
+    lu = np.zeros((dim, n_cells))
+    ls = np.zeros(8)
+    _check(load().lks_get_initial_adjoint(h, _dptr(lp), _dptr(lu), _dptr(ls)), "lks_get_initial_adjoint")
+    return lp, lu, ls
+
+
+def lks_launch_count(h) -> int:
+    return int(load().lks_launch_count(h))
+
+
+def lks_set_kernel_timing(h, enable: bool):
+    _check(load().lks_set_kernel_timing(h, int(bool(enable))), "lks_set_kernel_timing")
+
+
+def lks_kernel_time(h, family: str):
+    ms = ctypes.c_double(0.0)
+    n = ctypes.c_longlong(0)
+    _check(load().lks_kernel_time(h, family.encode(), ctypes.byref(ms), ctypes.byref(n)), "lks_kernel_time")
+    return ms.value, n.value
+
+
+def lks_workspace_bytes(h) -> int:
+    return int(load().lks_workspace_bytes(h))
+
+
+def lks_destroy(h):
+    if h:
+        load().lks_destroy(h)
+
+
+def lks_status_string(code: int) -> str:
+    return load().lks_status_string(code).decode()
+
+
+class Solver:
+    """Owns one lks_handle for a ``workloads.Problem``; torch supplies device memory and streams."""
+
+    def __init__(self, P, **overrides):
+        self.P = P
+        self.struct = problem_struct(P, **overrides)
+        self.handle = lks_create(self.struct)
+
+    @property
+    def n_steps(self) -> int:
+        return self.struct.n_steps
+
+    def set_initial_state(self, p=None, u=None, s=None):
+        lks_set_initial_state(self.handle, p, u, s)
+
+    def forward(self, gamma, stream=None) -> float:
+        import torch
+        assert gamma.is_cuda and gamma.dtype == torch.float64 and gamma.is_contiguous()
+        st = torch.cuda.current_stream(gamma.device) if stream is None else stream
+        return lks_forward(self.handle, gamma.data_ptr(), st.cuda_stream)
+
+    def adjoint(self, seed: float = 1.0, stream=None):
+        import torch
+        st = torch.cuda.current_stream() if stream is None else stream
+        lks_adjoint(self.handle, seed, st.cuda_stream)
+
+    def sensitivity(self, out, stream=None):
+        import torch
+        assert out.is_cuda and out.dtype == torch.float64 and out.is_contiguous()
+        st = torch.cuda.current_stream(out.device) if stream is None else stream
+        lks_sensitivity(self.handle, out.data_ptr(), st.cuda_stream)
+        return out
+
+    def gradient_host(self, gamma: np.ndarray, stream=None):
+        import torch
+        st = torch.cuda.current_stream() if stream is None else stream
+        out = np.zeros(self.P.n_design)
+        J = lks_gradient_host(self.handle, np.ascontiguousarray(gamma, dtype=np.float64), out, st.cuda_stream)
+        return J, out
+
+    def dof_history(self) -> np.ndarray:
+        return lks_get_dof_history(self.handle, self.n_steps)
+
+    def state(self):
+        return lks_get_state(self.handle, self.P.n_cells, self.P.dim)
+
+    def initial_adjoint(self):
+        return lks_get_initial_adjoint(self.handle, self.P.n_cells, self.P.dim)
+
+    def launches(self) -> int:
+        return lks_launch_count(self.handle)
+
+    def close(self):
+        if self.handle:
+            lks_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:  # pragma: no cover
+            pass

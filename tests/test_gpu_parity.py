@@ -1,0 +1,208 @@
+"""Parity of the CUDA path (through the C ABI) with the oracle on the same seeded inputs.
+
+Tolerances: the FP64 form must agree with the FP64 oracle to rounding (J to 1e-11 relative,
+gradients to 1e-9); the FP32-field form must meet J relative error <= 1e-4 and dJ/dgamma relative
+L2 error <= 1e-3.
+"""
+from __future__ import annotations
+
+import numpy as np
+import pytest
+
+from oracle import oracle as O
+from tests.problems import (BC_INFLOW_OUTFLOW, BC_PERIODIC, BC_PRESSURE, BC_WALL, DOF_ROT, DOF_TX, DOF_TY,
+                            W_BILINEAR, W_COS4, body2d, perturbed_state)
+from workloads import CKPT_STORE_ALL, CKPT_UNIFORM, config, initial_state
+
+pytestmark = pytest.mark.gpu
+
+
+def _torch():
+    import torch
+    return torch
+
+
+def gpu_run(P, g, p0=None, u0=None, s0=None, adjoint=True, **overrides):
+    torch = _torch()
+    from paper_2601_18272_gb300.lks import Solver
+    S = Solver(P, **overrides)
+    try:
+        S.set_initial_state(p0, u0, s0)
+        gam = torch.tensor(g, dtype=torch.float64, device="cuda")
+        out = {"J": S.forward(gam), "hist": S.dof_history()}
+        if S.struct.ckpt_policy == CKPT_STORE_ALL or S.n_steps % max(S.struct.ckpt_every, 1) == 0:
+            out["p"], out["u"] = S.state()
+        if adjoint:
+            S.adjoint(1.0)
+            dg = torch.empty_like(gam)
+            S.sensitivity(dg)
+            torch.cuda.synchronize()
+            out["dJdgamma"] = dg.cpu().numpy()
+            out["lam_p0"], out["lam_u0"], out["lam_dof0"] = S.initial_adjoint()
+        out["launches"] = S.launches()
+        return out
+    finally:
+        S.close()
+
+
+def rel(a, b):
+    return np.linalg.norm(np.asarray(a) - np.asarray(b)) / max(np.linalg.norm(np.asarray(b)), 1e-300)
+
+
+CASES_2D = [
+    ("rot-cos4", lambda: body2d()),
+    ("x-bilinear", lambda: body2d(mask=DOF_TX, wk=W_BILINEAR)),
+    ("rot-nitr1", lambda: body2d(n_itr=1)),
+    ("walls-pressure", lambda: body2d(bc=(BC_PRESSURE, BC_WALL, BC_PERIODIC), mask=DOF_TX | DOF_ROT)),
+    ("periodic", lambda: body2d(bc=(BC_PERIODIC,) * 3)),
+    ("ragged-40x20", lambda: body2d(nx=40, ny=20, nd=7, centre=(15.6, 9.3), nt=9)),
+]
+
+
+@pytest.mark.parametrize("name,make", CASES_2D, ids=[c[0] for c in CASES_2D])
+def test_fp64_store_all_matches_oracle(name, make):
+    P, g = make()
+    p0, u0, s0 = perturbed_state(P)
+    G = O.gradient(P, g, p0, u0, s0)
+    po, uo, ho, Jo = O.forward(P, g, p0, u0, s0)
+    r = gpu_run(P, g, p0, u0, s0, precision=64, ckpt_policy=CKPT_STORE_ALL)
+    assert abs(r["J"] - Jo) <= 1e-11 * abs(Jo)
+    np.testing.assert_allclose(r["hist"], ho, rtol=1e-11, atol=1e-12)
+    assert rel(r["p"], po) < 1e-10 and rel(r["u"], uo) < 1e-10
+    assert rel(r["dJdgamma"], G["dJdgamma"]) < 1e-9
+    assert rel(r["lam_u0"], G["lam_u0"]) < 1e-9 and rel(r["lam_p0"], G["lam_p0"]) < 1e-9
+    np.testing.assert_allclose(r["lam_dof0"], G["lam_dof0"], rtol=1e-9, atol=1e-12)
+
+
+@pytest.mark.parametrize("policy", ["store_all", "uniform"])
+@pytest.mark.parametrize("name,make", CASES_2D[:4], ids=[c[0] for c in CASES_2D[:4]])
+def test_fp32_matches_oracle(name, make, policy):
+    P, g = make()
+    P = P.replace(n_steps=10)
+    p0, u0, s0 = perturbed_state(P)
+    G = O.gradient(P, g, p0, u0, s0)
+    kw = dict(precision=32, ckpt_policy=CKPT_STORE_ALL) if policy == "store_all" else \
+        dict(precision=32, ckpt_policy=CKPT_UNIFORM, ckpt_every=4)
+    r = gpu_run(P, g, p0, u0, s0, **kw)
+    assert abs(r["J"] - G["J"]) <= 1e-4 * abs(G["J"])
+    assert rel(r["dJdgamma"], G["dJdgamma"]) <= 1e-3
+
+
+def test_uniform_checkpointing_reproduces_store_all_fp64():
+    P, g = body2d(nt=11)
+    p0, u0, s0 = perturbed_state(P)
+    a = gpu_run(P, g, p0, u0, s0, precision=64, ckpt_policy=CKPT_STORE_ALL)
+    b = gpu_run(P, g, p0, u0, s0, precision=64, ckpt_policy=CKPT_UNIFORM, ckpt_every=3)
+    assert a["J"] == b["J"]
+    assert rel(b["dJdgamma"], a["dJdgamma"]) < 1e-12
+
+
+def test_deterministic():
+    P, g = body2d(nt=8)
+    p0, u0, s0 = perturbed_state(P)
+    a = gpu_run(P, g, p0, u0, s0, precision=32, ckpt_policy=CKPT_UNIFORM, ckpt_every=3)
+    b = gpu_run(P, g, p0, u0, s0, precision=32, ckpt_policy=CKPT_UNIFORM, ckpt_every=3)
+    assert a["J"] == b["J"]
+    assert np.array_equal(a["dJdgamma"], b["dJdgamma"])
+
+
+def test_sail2d_80x40_full_fp64():
+    """The 80x40 / 16x16 / 400-step translation workload, FP64, every state stored."""
+    P, g = config(1)
+    p0, u0, s0 = initial_state(P)
+    G = O.gradient(P, g, p0, u0, s0)
+    r = gpu_run(P, g, p0, u0, s0)
+    assert abs(r["J"] - G["J"]) <= 1e-11 * abs(G["J"])
+    assert rel(r["dJdgamma"], G["dJdgamma"]) < 1e-8
+    assert r["launches"] > 400 * 6
+
+
+def test_turbine2d_512x256_truncated_fp32():
+    """The 512x256 / 128x128 rotating workload in its benchmark precision (FP32 fields, uniform
+    checkpoints), truncated to 30 steps so the oracle finishes in seconds."""
+    P, g = config(2)
+    P = P.replace(n_steps=30, ckpt_every=10)
+    p0, u0, s0 = initial_state(P)
+    G = O.gradient(P, g, p0, u0, s0)
+    r = gpu_run(P, g, p0, u0, s0)
+    assert abs(r["J"] - G["J"]) <= 1e-4 * abs(G["J"])
+    assert rel(r["dJdgamma"], G["dJdgamma"]) <= 1e-3
+
+
+def test_turbine2d_full_size_fp32_vs_fp64_and_fd():
+    """Full 5000-step rotating workload in the benchmark's configuration: the FP32 checkpointed
+    gradient against the FP64 store-all gradient (J <= 1e-4, dJ/dgamma rel L2 <= 1e-3), and the
+    FP64 adjoint against a central difference of the FP64 forward along a random direction."""
+    torch = _torch()
+    from paper_2601_18272_gb300.lks import Solver
+    P, g = config(2)
+    r32 = gpu_run(P, g)
+    r64 = gpu_run(P, g, precision=64, ckpt_policy=CKPT_STORE_ALL)
+    assert abs(r32["J"] - r64["J"]) <= 1e-4 * abs(r64["J"])
+    assert rel(r32["dJdgamma"], r64["dJdgamma"]) <= 1e-3
+    v = np.random.default_rng(0).standard_normal(g.shape)
+    eps = 1e-4
+    S = Solver(P, precision=64, ckpt_policy=CKPT_UNIFORM, ckpt_every=100)
+    try:
+        Jp = S.forward(torch.tensor(g + eps * v, device="cuda"))
+        Jm = S.forward(torch.tensor(g - eps * v, device="cuda"))
+    finally:
+        S.close()
+    fd = (Jp - Jm) / (2 * eps)
+    adj = r64["dJdgamma"] @ v
+    assert abs(fd - adj) <= 1e-5 * abs(adj)
+
+
+def test_gradient_host_matches_device_path():
+    torch = _torch()
+    from paper_2601_18272_gb300.lks import Solver
+    P, g = body2d(nt=7)
+    S = Solver(P, precision=32, ckpt_policy=CKPT_UNIFORM, ckpt_every=3)
+    try:
+        J1, d1 = S.gradient_host(g)
+        gam = torch.tensor(g, device="cuda")
+        J2 = S.forward(gam)
+        S.adjoint(1.0)
+        d2 = S.sensitivity(torch.empty_like(gam)).cpu().numpy()
+    finally:
+        S.close()
+    assert J1 == J2 and np.array_equal(d1, d2)
+
+
+def test_autograd_function():
+    torch = _torch()
+    from paper_2601_18272_gb300.autograd import objective
+    from paper_2601_18272_gb300.lks import Solver
+    P, g = body2d(nt=6)
+    S = Solver(P, precision=64, ckpt_policy=CKPT_STORE_ALL)
+    try:
+        gam = torch.tensor(g, device="cuda", requires_grad=True)
+        J = objective(gam, S)
+        (2.5 * J).backward()
+        G = O.gradient(P, g, *initial_state(P))
+        assert abs(J.item() - G["J"]) < 1e-11 * abs(G["J"])
+        assert rel(gam.grad.cpu().numpy(), 2.5 * G["dJdgamma"]) < 1e-9
+    finally:
+        S.close()
+
+
+def test_error_paths():
+    torch = _torch()
+    from paper_2601_18272_gb300.lks import LksError, Solver, lks_create, problem_struct
+    P, g = body2d(centre=(4.5, 8.0), nt=3)
+    S = Solver(P)
+    try:
+        with pytest.raises(LksError, match="LKS_ERR_ORDER"):
+            S.adjoint(1.0)
+        with pytest.raises(LksError, match="BODY_OUTSIDE"):
+            S.forward(torch.tensor(g, device="cuda"))
+    finally:
+        S.close()
+    bad = problem_struct(body2d()[0])
+    bad.nu = -0.01
+    with pytest.raises(LksError, match="UNSTABLE"):
+        lks_create(bad)
+    bad = problem_struct(body2d()[0])
+    bad.nx = 2
+    with pytest.raises(LksError, match="LKS_ERR_ARG"):
+        lks_create(bad)
