@@ -1,0 +1,340 @@
+#!/usr/bin/env python
+"""Benchmark: forward + adjoint gradient of the coupled LKS / rigid-body march on GB300.
+
+One step = one full gradient (lks_forward over all N_t time steps, lks_adjoint, lks_sensitivity)
+of the 512x256 D2Q9 rotating-body workload (128x128 design grid, 5000 steps, N_itr = 5, FP32
+fields with FP64 force/torque/EOM, checkpoints every 100 steps) on synthetic seeded inputs.
+value = analysis-cell updates per second of the forward + adjoint pass, summed over all ranks
+(each rank runs an independent replica: the method has no data-parallel exchange).
+
+Prints one JSON line (rank 0). --impl reference times the FP64 CPU oracle on a bounded sample of
+the same workload instead.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "forward+adjoint LKS cell-updates/s vs HBM roofline; gradient rel. err vs FP64"
+UNIT = "cell-updates/s"
+CONFIG_INDEX = 2
+
+
+def _dist():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+class ClockSampler:
+    """nvidia-smi clock / throttle samples while the timed region runs."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.lines = []
+        self.thread = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits", "-lms", "200",
+                 "-i", str(self.gpu)], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.proc = None
+            return
+        self.thread = threading.Thread(target=self._read, daemon=True)
+        self.thread.start()
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self) -> dict:
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        if self.thread:
+            self.thread.join(timeout=2)
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, val in zip(names, parts[5:9]):
+                if val.lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": float(np.median(sm)) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def _peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+# Algorithmic bytes per launch of each kernel family (FP32 fields, 2D): see the data-layout
+# notes in the design doc. N = analysis cells, Bc = body-box cells, ND = design points.
+def _alg_bytes(family: str, P, box_cells: int, esz: int) -> float:
+    N, ND = P.n_cells, P.n_design
+    if family == "stencil_fwd":
+        return 6 * esz * N            # read p, u_x, u_y; write p*, u*_x, u*_y
+    if family == "stencil_adj":
+        return 8 * esz * N            # read 3 adjoint planes + u(t-1) (2 planes); write 3 planes
+    if family == "couple":
+        return 2 * esz * box_cells + 4 * ND  # read u* in the box (+ kappa^ref)
+    if family == "recompute":
+        return 6 * esz * box_cells + 4 * ND  # read u*, write u and the stored u*
+    if family == "adj_cell":
+        return 11 * esz * box_cells   # read stored u*, acc r/w, scratch write (5 planes)
+    if family == "adj_design":
+        return 5 * esz * box_cells + 20 * ND  # read scratch once, dJ/dkappa^ref r/w + kappa^ref
+    return 0.0
+
+
+def _box_cells(P) -> int:
+    import math
+    s = 1 if P.weight_kind == 1 else 2
+    half = [(P.ndx - 1) / 2.0, (P.ndy - 1) / 2.0]
+    r = math.sqrt(half[0] ** 2 + half[1] ** 2)
+    hb = math.ceil(r - 1e-12)
+    B = 2 * hb + 2 * s + 2 + 2
+    return B * B
+
+
+def run_reference(args, ws, rank):
+    """The FP64 oracle on the host cores, each step a bounded sample of the same workload."""
+    if rank != 0:
+        return 0
+    from oracle import oracle as O
+    from workloads import config, initial_state
+    P, g = config(CONFIG_INDEX)
+    sample = args.ref_sample_steps
+    p0, u0, s0 = initial_state(P)
+    times = []
+    for i in range(args.warmup + args.steps):
+        t0 = time.perf_counter()
+        O.gradient(P, g, p0, u0, s0, n_steps=sample)
+        dt = time.perf_counter() - t0
+        if i >= args.warmup:
+            times.append(dt)
+    total = sum(times)
+    value = P.n_cells * sample * len(times) / total
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000 * total / len(times),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": P.name, "grid": [P.nx, P.ny], "design": [P.ndx, P.ndy], "n_steps": P.n_steps,
+                       "n_itr": P.n_itr, "sample_steps_per_bench_step": sample},
+            "cpu_baseline": {"kind": "oracle", "value": value, "unit": UNIT, "cores": 1,
+                             "sample": f"{sample} forward+adjoint time steps of the {P.name} workload per step"},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def cpu_baseline(sample_steps: int):
+    from oracle import oracle as O
+    from workloads import config, initial_state
+    P, g = config(CONFIG_INDEX)
+    p0, u0, s0 = initial_state(P)
+    t0 = time.perf_counter()
+    O.gradient(P, g, p0, u0, s0, n_steps=sample_steps)
+    dt = time.perf_counter() - t0
+    return {"value": P.n_cells * sample_steps / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"forward+adjoint of the first {sample_steps} of {P.n_steps} time steps of {P.name}, "
+                      f"single-threaded FP64 ({dt:.1f} s)"}
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    ap.add_argument("--ref-sample-steps", type=int, default=8)
+    ap.add_argument("--cpu-sample-steps", type=int, default=24)
+    ap.add_argument("--skip-extras", action="store_true", help="only the timed region and e2e")
+    ap.add_argument("--time-steps", type=int, default=0,
+                    help="truncate N_t (profiling runs only: keeps the per-step kernel mix, shrinks the launch list)")
+    args = ap.parse_args()
+    ws, rank, local = _dist()
+    if args.impl == "reference":
+        return run_reference(args, ws, rank)
+
+    import torch
+    from paper_2601_18272_gb300 import lks
+    from paper_2601_18272_gb300.lks import Solver
+    from workloads import CKPT_STORE_ALL, config
+
+    torch.cuda.set_device(local)
+    dist = None
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    dev = torch.device("cuda", local)
+    P, g = config(CONFIG_INDEX)
+    if args.time_steps:
+        P = P.replace(n_steps=args.time_steps, ckpt_every=min(P.ckpt_every, max(1, args.time_steps // 2)))
+    solver = Solver(P)
+    gamma = torch.tensor(g, dtype=torch.float64, device=dev)
+    grad = torch.empty_like(gamma)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)  # > 129 MB L2
+    stream = torch.cuda.current_stream(dev)
+
+    def step():
+        solver.forward(gamma)
+        solver.adjoint(1.0)
+        solver.sensitivity(grad)
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    sampler = ClockSampler(torch.cuda.current_device() if "CUDA_VISIBLE_DEVICES" not in os.environ else local)
+    sampler.start()
+    l0 = solver.launches()
+    ms = []
+    for _ in range(args.steps):
+        flush.zero_()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        step()
+        e1.record(stream)
+        e1.synchronize()
+        ms.append(e0.elapsed_time(e1))
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    clocks = sampler.stop()
+    launches = solver.launches() - l0
+    total_ms = sum(ms)
+    t = torch.tensor([total_ms], dtype=torch.float64, device=dev)
+    nl = torch.tensor([float(launches)], dtype=torch.float64, device=dev)
+    if dist:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        dist.all_reduce(nl, op=dist.ReduceOp.SUM)
+    total_ms = float(t.item())
+    cell_steps = P.n_cells * P.n_steps
+    value = ws * args.steps * cell_steps / (total_ms / 1000.0)
+
+    # end to end: host gamma (pinned) -> device, forward, adjoint, sensitivity, gradient -> host
+    g_host = torch.tensor(g, dtype=torch.float64).pin_memory()
+    d_host = torch.empty(P.n_design, dtype=torch.float64).pin_memory()
+    gptr, dptr = g_host.numpy(), d_host.numpy()
+    solver.gradient_host(gptr)  # warm
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        J = lks.lks_gradient_host(solver.handle, gptr, dptr, stream.cuda_stream)
+    torch.cuda.synchronize()
+    e2e_s = time.perf_counter() - t0
+    te = torch.tensor([e2e_s], dtype=torch.float64, device=dev)
+    if dist:
+        dist.all_reduce(te, op=dist.ReduceOp.MAX)
+    e2e_value = ws * args.steps * cell_steps / float(te.item())
+
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": P.name, "grid": [P.nx, P.ny], "design": [P.ndx, P.ndy], "velocity_set": "D2Q9",
+                       "n_steps": P.n_steps, "n_itr": P.n_itr, "motion": "rotation about the body centre",
+                       "fields": "fp32 (force/torque/EOM fp64)", "checkpoints": f"uniform every {P.ckpt_every}, fp32",
+                       "l2": "flushed (256 MB write) between timed steps", "replicas": ws},
+            "clocks": clocks,
+            "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": 8 * P.n_design,
+                    "d2h_bytes_per_step": 8 * P.n_design + 8, "J": J},
+            "gpu_launches": int(nl.item())}
+
+    if rank == 0 and not args.skip_extras:
+        # dominant kernel: one more gradient with every launch bracketed by CUDA events
+        lks.lks_set_kernel_timing(solver.handle, True)
+        step()
+        torch.cuda.synchronize()
+        fams = {}
+        for fam in ("stencil_fwd", "couple", "recompute", "adj_cell", "adj_design", "stencil_adj"):
+            fams[fam] = lks.lks_kernel_time(solver.handle, fam)
+        lks.lks_set_kernel_timing(solver.handle, False)
+        dom = max(fams, key=lambda k: fams[k][0])
+        dom_ms, dom_n = fams[dom]
+        peak, peak_kind = _peaks()
+        per_launch_s = dom_ms / 1000.0 / dom_n
+        alg = _alg_bytes(dom, P, _box_cells(P), 4)
+        achieved = alg / per_launch_s / 1e9
+        line["roofline"] = {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peak, "unit": "GB/s",
+                            "frac": achieved / peak, "traffic": None, "peak_source": peak_kind,
+                            "alg_bytes_per_launch": alg, "avg_launch_us": per_launch_s * 1e6,
+                            "kernel_ms_per_gradient": {k: round(v[0], 3) for k, v in fams.items()},
+                            "launches_per_gradient": {k: v[1] for k, v in fams.items()}}
+        # accuracy of this FP32 checkpointed gradient against the FP64 store-all GPU form, and the
+        # throughput of that plain FP64 form
+        plain = Solver(P, precision=64, ckpt_policy=CKPT_STORE_ALL)
+        g64 = torch.empty_like(gamma)
+        plain.forward(gamma)
+        plain.adjoint(1.0)
+        plain.sensitivity(g64)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        flush.zero_()
+        e0.record(stream)
+        J64 = plain.forward(gamma)
+        plain.adjoint(1.0)
+        plain.sensitivity(g64)
+        e1.record(stream)
+        e1.synchronize()
+        plain_ms = e0.elapsed_time(e1)
+        step()
+        torch.cuda.synchronize()
+        rel = float(torch.linalg.norm(grad - g64) / torch.linalg.norm(g64))
+        line["gradient_rel_err_vs_fp64"] = {"dJdgamma_rel_l2": rel, "J_rel": abs(J - J64) / abs(J64),
+                                            "reference": "FP64 store-all GPU form"}
+        line["plain_fp64_store_all"] = {"value": cell_steps / (plain_ms / 1000.0), "unit": UNIT,
+                                        "ms_per_step": plain_ms, "workspace_gb": lks.lks_workspace_bytes(plain.handle) / 1e9}
+        line["workspace_gb"] = lks.lks_workspace_bytes(solver.handle) / 1e9
+        plain.close()
+        line["cpu_baseline"] = cpu_baseline(args.cpu_sample_steps)
+    solver.close()
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if dist:
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())
