@@ -140,6 +140,24 @@ LKS_API long long lks_launch_count(const lks_handle* h);
 LKS_API int lks_set_kernel_timing(lks_handle* h, int enable);
 LKS_API int lks_kernel_time(lks_handle* h, const char* family, double* ms_total, long long* launches);
 
+/* One time step of the march (LKS predictor, boundary values, N_itr coupling iterations) that
+ * allocates no device memory. The paper has no counterpart: this is an interface for callers that
+ * cannot allocate -- code inside a relaxed-mode CUDA graph capture, real-time loops with memory
+ * fixed up front, frameworks that forbid libraries their own cudaMalloc. Its scratch is one fixed
+ * device array (about 0.7 MB) that every GPU loading the library holds until exit.
+ *   problem   : as for lks_create; dim 2 and LKS_FP64 only (else LKS_ERR_UNSUPPORTED); at most
+ *               65536 design points, n_itr <= 16 and 4096 CTAs per reduction (else LKS_ERR_BUDGET)
+ *   gamma_dev : design field [ndx*ndy] (device, caller-owned)
+ *   state_dev : two state slots [2][3][nx*ny] doubles (device, caller-owned): step t reads slot
+ *               (t-1) mod 2 and writes p*, u(t) into slot t mod 2
+ *   t         : step index >= 1 (only its parity matters)
+ *   s_host    : DOF vector [8] (host): s(t-1) in, s(t) out
+ * The first call on a device looks up the scratch array's address with that device current; make
+ * it before any stream capture. All calls share the array and each clears what must start at
+ * zero; calls that overlap on the GPU race on it. Synchronises the stream before returning. */
+LKS_API int lks_step_noalloc(const lks_problem* problem, const double* gamma_dev, double* state_dev, int t,
+                             double* s_host, void* stream);
+
 /* Bytes of device workspace held by the handle. */
 LKS_API size_t lks_workspace_bytes(const lks_handle* h);
 

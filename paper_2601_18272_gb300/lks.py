@@ -98,6 +98,7 @@ def load() -> ctypes.CDLL:
     L.lks_status_string.argtypes = [ctypes.c_int]
     L.lks_status_string.restype = ctypes.c_char_p
     L.lks_last_cuda_error.argtypes = []
+    L.lks_step_noalloc.argtypes = [ctypes.POINTER(lks_problem), vp, vp, ctypes.c_int, dp, vp]
     _lib = L
     return L
 
@@ -224,6 +225,16 @@ def lks_workspace_bytes(h) -> int:
 def lks_destroy(h):
     if h:
         load().lks_destroy(h)
+
+
+def lks_step_noalloc(problem: lks_problem, gamma_dev_ptr: int, state_dev_ptr: int, t: int, s: np.ndarray,
+                     stream: int = 0) -> np.ndarray:
+    """One time step without device allocation; s (8 doubles) is s(t-1) in and s(t) out."""
+    s = np.ascontiguousarray(s, dtype=np.float64).copy()
+    _check(load().lks_step_noalloc(ctypes.byref(problem), ctypes.c_void_p(gamma_dev_ptr),
+                                   ctypes.c_void_p(state_dev_ptr), int(t), _dptr(s), ctypes.c_void_p(stream)),
+           "lks_step_noalloc")
+    return s
 
 
 def lks_status_string(code: int) -> str:
