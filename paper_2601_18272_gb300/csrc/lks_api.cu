@@ -76,7 +76,8 @@ struct lks_handle {
   long long launches = 0;
   bool timing = false;
   std::map<std::string, TimerFamily> timers;
-  int chunk = 50;  // steps per captured graph in store-all mode
+  int chunk = 50;    // steps per captured graph in store-all mode
+  int launch_error = 0;
 };
 
 namespace {
@@ -180,6 +181,11 @@ struct Launcher {
   int kernels = 0;
   template <typename F>
   void operator()(const char* family, F&& f) {
+    n(family, 1, f);
+  }
+  // one call that launches `count` kernels (timed together)
+  template <typename F>
+  void n(const char* family, int count, F&& f) {
     EventPair* ev = nullptr;
     if (h->timing && !capturing) {
       TimerFamily& tf = h->timers[family];
@@ -195,8 +201,8 @@ struct Launcher {
     }
     f(st);
     if (ev) cudaEventRecord(ev->b, st);
-    ++kernels;
-    if (!capturing) ++h->launches;
+    kernels += count;
+    if (!capturing) h->launches += count;
   }
 };
 
@@ -257,12 +263,12 @@ void clear_graphs(lks_handle* h) {
 template <typename T>
 void enqueue_fwd_steps(lks_handle* h, Launcher& L, const Slots<T>& S, int nsteps, bool store_box) {
   const Geo& g = h->g;
+  T* bs = store_box ? (T*)h->boxstore : nullptr;
   for (int i = 0; i < nsteps; ++i) {
-    L("stencil_fwd", [&](cudaStream_t s) { launch_stencil_fwd<T>(g, S, h->ctrl, s); });
+    L("stencil_fwd", [&](cudaStream_t s) { launch_stencil_fwd<T>(g, S, h->ctrl, i, s); });
     for (int k = 1; k <= g.K; ++k)
-      L("couple", [&](cudaStream_t s) {
-        launch_couple<T>(g, S, h->ctrl, h->it, (const T*)h->kref, h->mom, h->partials, k,
-                         store_box ? (T*)h->boxstore : nullptr, h->nbox, s);
+      L.n("couple", 2, [&](cudaStream_t s) {
+        launch_couple<T>(g, S, h->ctrl, h->it, (const T*)h->kref, h->mom, h->partials, k, bs, h->nbox, i, s);
       });
   }
 }
@@ -271,9 +277,9 @@ template <typename T>
 void enqueue_recompute(lks_handle* h, Launcher& L, const Slots<T>& S, int nsteps) {
   const Geo& g = h->g;
   for (int i = 0; i < nsteps; ++i) {
-    L("stencil_fwd", [&](cudaStream_t s) { launch_stencil_fwd<T>(g, S, h->ctrl, s); });
+    L("stencil_fwd", [&](cudaStream_t s) { launch_stencil_fwd<T>(g, S, h->ctrl, i, s); });
     L("recompute", [&](cudaStream_t s) {
-      launch_apply<T>(g, S, h->ctrl, h->it, (const T*)h->kref, (T*)h->boxstore, h->nbox, s);
+      launch_apply<T>(g, S, h->ctrl, h->it, (const T*)h->kref, (T*)h->boxstore, h->nbox, i, s);
     });
   }
 }
@@ -281,19 +287,18 @@ void enqueue_recompute(lks_handle* h, Launcher& L, const Slots<T>& S, int nsteps
 template <typename T>
 void enqueue_adj_steps(lks_handle* h, Launcher& L, const Slots<T>& S, int nsteps) {
   const Geo& g = h->g;
-  const long long BC = g.box_cells;
-  (void)BC;
   for (int i = 0; i < nsteps; ++i) {
     for (int k = g.K; k >= 1; --k) {
       L("adj_cell", [&](cudaStream_t s) {
         launch_adj_cell<T>(g, h->ctrl, h->it, (const T*)h->kref, (const T*)h->boxstore, h->nbox, (T*)h->L,
-                           h->slot_elems, (T*)h->acc, (T*)h->scratch, k, s);
+                           h->slot_elems, (T*)h->acc, (T*)h->scratch, k, i, s);
       });
-      L("adj_design", [&](cudaStream_t s) {
-        launch_adj_design<T>(g, h->ctrl, h->it, (const T*)h->kref, (const T*)h->scratch, h->dkref, h->partials, k, s);
+      L.n("adj_design", 2, [&](cudaStream_t s) {
+        launch_adj_design<T>(g, h->ctrl, h->it, (const T*)h->kref, (const T*)h->scratch, h->dkref, h->partials, k, i,
+                             s);
       });
     }
-    L("stencil_adj", [&](cudaStream_t s) { launch_stencil_adj<T>(g, S, (T*)h->L, h->slot_elems, h->ctrl, s); });
+    L("stencil_adj", [&](cudaStream_t s) { launch_stencil_adj<T>(g, S, (T*)h->L, h->slot_elems, h->ctrl, i, s); });
   }
 }
 
@@ -307,6 +312,7 @@ int forward_impl(lks_handle* h, cudaStream_t st) {
     L0("init", [&](cudaStream_t s) { launch_init_forward<T>(g, S, h->init_p, h->init_u, h->init_s, h->it, h->ctrl, s); });
     for (int t0 = 1; t0 <= NT; t0 += h->chunk) {
       const int n = std::min(h->chunk, NT - t0 + 1);
+      L0("init", [&](cudaStream_t s) { launch_set_step(h->ctrl, t0, 0, s); });
       TRY(run_graph(h, "fwd_sa_" + std::to_string(n), st,
                     [&](Launcher& L) { enqueue_fwd_steps<T>(h, L, S, n, true); }));
     }
@@ -314,17 +320,20 @@ int forward_impl(lks_handle* h, cudaStream_t st) {
     Slots<T> S = pp_slots<T>(h);
     const int every = h->P.ckpt_every;
     L0("init", [&](cudaStream_t s) { launch_init_forward<T>(g, S, h->init_p, h->init_u, h->init_s, h->it, h->ctrl, s); });
-    L0("ckpt", [&](cudaStream_t s) { launch_ckpt_pack<T>(g, S, (T*)h->ckpt, h->slot_elems, every, h->ctrl, s); });
+    L0("ckpt", [&](cudaStream_t s) { launch_ckpt_pack<T>(g, S, (T*)h->ckpt, h->slot_elems, every, h->ctrl, -1, s); });
     for (int t0 = 0; t0 < NT; t0 += every) {
       const int n = std::min(every, NT - t0);
       const bool pack = (t0 + n < NT);
+      L0("init", [&](cudaStream_t s) { launch_set_step(h->ctrl, t0 + 1, 0, s); });
       TRY(run_graph(h, "fwd_u_" + std::to_string(n) + (pack ? "p" : ""), st, [&](Launcher& L) {
         enqueue_fwd_steps<T>(h, L, S, n, false);
-        if (pack) L("ckpt", [&](cudaStream_t s) { launch_ckpt_pack<T>(g, S, (T*)h->ckpt, h->slot_elems, every, h->ctrl, s); });
+        if (pack)
+          L("ckpt", [&](cudaStream_t s) { launch_ckpt_pack<T>(g, S, (T*)h->ckpt, h->slot_elems, every, h->ctrl, n - 1, s); });
       }));
     }
   }
   CK(cudaGetLastError());
+  if (h->launch_error) return LKS_ERR_CUDA;
   return LKS_OK;
 }
 
@@ -337,9 +346,9 @@ int adjoint_impl(lks_handle* h, double seed, cudaStream_t st) {
   L0("init", [&](cudaStream_t s) { launch_adj_init(g, h->ctrl, h->objw, seed, h->dkref, g.ND, s); });
   if (h->P.ckpt_policy == LKS_CKPT_STORE_ALL) {
     Slots<T> S = ring_slots<T>(h);
-    L0("init", [&](cudaStream_t s) { launch_set_step(h->ctrl, NT, 0, s); });
     for (int t1 = NT; t1 >= 1; t1 -= h->chunk) {
       const int n = std::min(h->chunk, t1);
+      L0("init", [&](cudaStream_t s) { launch_set_step(h->ctrl, t1, 0, s); });
       TRY(run_graph(h, "adj_sa_" + std::to_string(n), st, [&](Launcher& L) { enqueue_adj_steps<T>(h, L, S, n); }));
     }
   } else {
@@ -358,6 +367,7 @@ int adjoint_impl(lks_handle* h, double seed, cudaStream_t st) {
     }
   }
   CK(cudaGetLastError());
+  if (h->launch_error) return LKS_ERR_CUDA;
   return LKS_OK;
 }
 
@@ -390,8 +400,8 @@ int allocate(lks_handle* h) {
   TRY(dalloc(h, (void**)&h->it, (size_t)(NT + 1) * (K + 1) * sizeof(Dof)));
   TRY(dalloc(h, (void**)&h->ctrl, sizeof(Ctrl)));
   TRY(dalloc(h, (void**)&h->mom, sizeof(Moments)));
-  const long long bx = ((g.B[0] + 31) / 32) * (long long)((g.B[1] + 7) / 8) * g.B[2];
-  const long long bd = (g.ND + 255) / 256;
+  const long long bx = ((g.B[0] + kBoxCtaCellsX - 1) / kBoxCtaCellsX) * (long long)((g.B[1] + kBoxCtaCellsY - 1) / kBoxCtaCellsY) * g.B[2];
+  const long long bd = ((long long)g.ND * 4 + 255) / 256;
   const long long nblk = std::max(bx, bd) + 1;
   TRY(dalloc(h, (void**)&h->partials, (size_t)nblk * 8 * sizeof(double)));
   TRY(dalloc(h, (void**)&h->init_p, (size_t)g.N * sizeof(double)));
@@ -467,7 +477,10 @@ int lks_create(const lks_problem* P, lks_handle** out) {
   g.nd[1] = P->ndy;
   g.nd[2] = P->dim == 3 ? P->ndz : 1;
   g.ND = g.nd[0] * g.nd[1] * g.nd[2];
-  for (int a = 0; a < 3; ++a) g.xic[a] = (a < g.dim) ? (g.nd[a] - 1) / 2.0 : 0.0;
+  for (int a = 0; a < 3; ++a) {
+    g.xic[a] = (a < g.dim) ? (g.nd[a] - 1) / 2.0 : 0.0;
+    g.xicf[a] = (float)g.xic[a];
+  }
   g.ax = P->rot_axis;
   g.axb = (g.ax + 1) % 3;
   g.axc = (g.ax + 2) % 3;
@@ -476,6 +489,7 @@ int lks_create(const lks_problem* P, lks_handle** out) {
   g.s = (P->weight_kind == LKS_W_BILINEAR) ? 1 : 2;
   g.K = P->n_itr;
   g.A = 4.5 * (1.0 / 6.0 - P->nu);
+  g.A2 = (float)(2.0 * g.A);
   g.u_in = P->u_in;
   g.dp = P->dp;
   g.mass = P->mass;

@@ -1,6 +1,6 @@
 // Grid separation, Brinkman coupling and rigid-body EOM (Sec. 2.2-2.4, 3.1) and their reverse.
 //
-// Forward coupling iteration k of step t, one thread per cell of the body box:
+// Forward coupling iteration k of step t, per cell n of the body box:
 //   gather the design points within the kernel support of the cell under s^(k-1)
 //     kappa_n = sum_m W kappa_m,  u^S_n = sum_m W u^S,ref_m = u^G phi_n + omega R' (sum_m W r_m)
 //   Brinkman update u_n = (u*_n + kappa_n u^S_n) / (1 + kappa_n)                       (Eq. u)
@@ -10,227 +10,148 @@
 //   which equals the design-grid sum sum_m kappa_m (u^ref_m - u^S,ref_m) of Sec. 2.4 up to the
 //   order of summation, because the interpolation (Eq. u_mapping) uses the same weights as the
 //   spread; the design-side sums are closed forms in (u^G, omega) over precomputed moments.
-//   Per-block FP64 partials, then the last block sums them in block order and applies the
-//   explicit Euler EOM (Sec. 2.4) in FP64.
+//   FP64 partial sums, then the explicit Euler EOM (Sec. 2.4) in FP64.
 //
-// Reverse of iteration k: a cell-side kernel (Brinkman and interpolation reverse, accumulation of
-// dJ/du*) and a design-side kernel, one thread per design point, that gathers its axis-aligned
-// support window of cells for the spread / interpolation / transform reverse (the dW/dx^ref
-// terms), accumulates dJ/dkappa^ref without atomics and reduces dJ/ds^(k-1).
+// Reverse of iteration k: a cell phase (Brinkman and interpolation reverse, accumulation of
+// dJ/du*) and a design-point phase that gathers each point's axis-aligned support window of cells
+// for the spread / interpolation / transform reverse (the dW/dx^ref terms), accumulates
+// dJ/dkappa^ref without atomics and reduces dJ/ds^(k-1).
+//
+// Each iteration's global reduction is split into a kernel over all SMs that writes one FP64
+// partial per CTA and a one-CTA finish kernel that sums the partials in a fixed order and applies
+// the (reverse) EOM: the kernel boundary orders the partials, so no GPU-scope fence or counter is
+// needed, and the sums are deterministic.
 #include "lks_kernels.h"
 
 namespace lks {
 
 namespace {
 
-constexpr int BX = 32, BY = 8;
+constexpr int BX = 32, BY = 8;  // grid form: one thread per box cell, 32 x 8 cells per CTA
+constexpr int kDesignBlock = 256;
 
 __device__ __forceinline__ int block_linear() { return blockIdx.x + gridDim.x * (blockIdx.y + gridDim.y * blockIdx.z); }
 __device__ __forceinline__ int thread_linear() { return threadIdx.x + blockDim.x * (threadIdx.y + blockDim.y * threadIdx.z); }
 
+// dJ/dF and dJ/dT of the iteration being reversed, in the field type.
 template <typename T>
-__global__ void __launch_bounds__(256) k_prep(Geo g, const double* __restrict__ gamma, double kmax, double q,
-                                               T* __restrict__ kref, Moments* mom, double* partials, Ctrl* ctrl) {
-  __shared__ double red[32 * 5];
-  const int m = blockIdx.x * blockDim.x + threadIdx.x;
-  double v[5] = {0, 0, 0, 0, 0};
-  if (m < g.ND) {
-    const double gm = gamma[m];
-    const T k = (T)(kmax * q * gm / ((1.0 - gm) + q));  // Eq. brinkman_coefficient
-    kref[m] = k;
-    const double kd = (double)k;
-    int i[3] = {m % g.nd[0], (m / g.nd[0]) % g.nd[1], m / (g.nd[0] * g.nd[1])};
-    double r[3];
-    for (int a = 0; a < 3; ++a) r[a] = (a < g.dim) ? i[a] - g.xic[a] : 0.0;
-    v[0] = kd;
-    v[1] = kd * r[0];
-    v[2] = kd * r[1];
-    v[3] = kd * r[2];
-    v[4] = kd * (r[g.axb] * r[g.axb] + r[g.axc] * r[g.axc]);
-  }
-  block_sum<5>(v, red);
-  if (threadIdx.x == 0)
-    for (int a = 0; a < 5; ++a) partials[blockIdx.x * 5 + a] = v[a];
-  if (last_block_done(&ctrl->count[CNT_PREP]) && threadIdx.x == 0) {
-    double s[5] = {0, 0, 0, 0, 0};
-    for (int b = 0; b < (int)gridDim.x; ++b)
-      for (int a = 0; a < 5; ++a) s[a] += __ldcg(&partials[b * 5 + a]);
-    mom->K0 = s[0];
-    mom->K1[0] = s[1];
-    mom->K1[1] = s[2];
-    mom->K1[2] = s[3];
-    mom->K2p = s[4];
-    ctrl->count[CNT_PREP] = 0;
-  }
+__device__ __forceinline__ void lam_load(const Ctrl* ctrl, T (&lF)[3], T& lT);
+template <>
+__device__ __forceinline__ void lam_load<float>(const Ctrl* ctrl, float (&lF)[3], float& lT) {
+  for (int a = 0; a < 3; ++a) lF[a] = ctrl->lam_Ff[a];
+  lT = ctrl->lam_Tf;
+}
+template <>
+__device__ __forceinline__ void lam_load<double>(const Ctrl* ctrl, double (&lF)[3], double& lT) {
+  for (int a = 0; a < 3; ++a) lF[a] = ctrl->lam_F[a];
+  lT = ctrl->lam_T;
 }
 
+__device__ __forceinline__ void lam_store(Ctrl* ctrl, const double* lF, double lT) {
+  for (int a = 0; a < 3; ++a) {
+    ctrl->lam_F[a] = lF[a];
+    ctrl->lam_Ff[a] = (float)lF[a];
+  }
+  ctrl->lam_T = lT;
+  ctrl->lam_Tf = (float)lT;
+}
+
+// Forward coupling work for box cell (j0, j1, j2); adds kappa_n u_n and the torque density to v.
+// On the last iteration writes u(t) into dst and, if bs is set, the predictor u* into the box store.
 template <typename T, int D, int AX>
-__global__ void __launch_bounds__(BX* BY) k_couple(Geo g, Slots<T> S, Ctrl* ctrl, Dof* it, const T* __restrict__ kref,
-                                                    const Moments* __restrict__ mom, double* partials, int k,
-                                                    T* __restrict__ boxstore, int nbox) {
+__device__ __forceinline__ void couple_cell(const Geo& g, const T* __restrict__ kref, const Dof& sk, const int (&lo)[3],
+                                            int j0, int j1, int j2, T* __restrict__ dst, T* __restrict__ bs, bool last,
+                                            int* status, T* v) {
   constexpr int b = Axes<AX>::B, c = Axes<AX>::C;
-  __shared__ double red[32 * 4];
-  const int t = ctrl->t, base = ctrl->base, K = g.K;
-  Dof* row = it + (long long)(t - 1) * (K + 1);
-  const Dof s0 = row[0], sk = row[k - 1];
-  T* __restrict__ dst = slot_ptr(S, t, base);
   const long long N = g.N;
-  int lx, ly, lz;
-  box_origin<D>(g, s0, lx, ly, lz);
-  const int j0 = blockIdx.x * BX + threadIdx.x, j1 = blockIdx.y * BY + threadIdx.y, j2 = blockIdx.z;
-  double v[4] = {0, 0, 0, 0};
-  if (j0 < g.B[0] && j1 < g.B[1]) {
-    const int px = lx + j0, py = ly + j1, pz = lz + j2;
-    long long n = 0;
-    const bool ing = cell_index<D>(g, px, py, pz, n);
-    const T d[3] = {(T)((double)px - sk.s[0]), (T)((double)py - sk.s[1]), D == 3 ? (T)((double)pz - sk.s[2]) : T(0)};
-    const T cs = (T)sk.cs, sn = (T)sk.sn;
-    Acc<T> A;
-    gather<T, D, AX>(g, kref, d, cs, sn, A);
-    if (A.phi > T(0) && (!ing || forbidden<D>(g, px, py, pz))) atomicOr(&ctrl->status, ST_BODY_OUTSIDE);
-    if (ing) {
-      T dwr[3], L[3], u[3] = {T(0), T(0), T(0)};
-      drot<AX>(cs, sn, A.wr, dwr);
-      rot<AX>(cs, sn, A.kr, L);
-      const T om = (T)sk.s[7];
-      const T inv = T(1) / (T(1) + A.kap);
-      const long long bl = j0 + (long long)g.B[0] * (j1 + (long long)g.B[1] * j2);
-      T* bs = boxstore ? boxstore + (long long)((t - base - 1) % nbox) * g.box_cells * D : nullptr;
-#pragma unroll
-      for (int a = 0; a < D; ++a) {
-        const T us = (T)sk.s[3 + a] * A.phi + om * dwr[a];
-        const T ustar = dst[(a + 1) * N + n];
-        u[a] = (ustar + A.kap * us) * inv;
-        v[a] = (double)(A.kap * u[a]);
-        if (k == K) {
-          if (bs) bs[a * g.box_cells + bl] = ustar;
-          dst[(a + 1) * N + n] = u[a];
-        }
-      }
-      v[D] = (double)(L[b] * u[c] - L[c] * u[b]);  // torque about AX
-    }
-  }
-  block_sum<4>(v, red);
-  const int tid = thread_linear();
-  if (tid == 0)
-    for (int a = 0; a < 4; ++a) partials[block_linear() * 4 + a] = v[a];
-  if (last_block_done(&ctrl->count[CNT_COUPLE]) && tid == 0) {
-    double s[4] = {0, 0, 0, 0};
-    const int nb = gridDim.x * gridDim.y * gridDim.z;
-    for (int q = 0; q < nb; ++q)
-      for (int a = 0; a < 4; ++a) s[a] += __ldcg(&partials[q * 4 + a]);
-    const double cs = sk.cs, sn = sk.sn, om = sk.s[7];
-    const double K1[3] = {mom->K1[0], mom->K1[1], mom->K1[2]};
-    double K1r[3], K1d[3];
-    rot<AX>(cs, sn, K1, K1r);
-    drot<AX>(cs, sn, K1, K1d);
-    const double ug[3] = {sk.s[3], sk.s[4], sk.s[5]};
-    double F[3] = {0, 0, 0};
-    for (int a = 0; a < D; ++a) F[a] = s[a] - (mom->K0 * ug[a] + om * K1d[a]);
-    const double Tq = s[D] - (K1r[b] * ug[c] - K1r[c] * ug[b]) - om * mom->K2p;
-    bool finite = isfinite(Tq);
-    for (int a = 0; a < D; ++a) finite = finite && isfinite(F[a]);
-    if (!finite) ctrl->status |= ST_NONFINITE;
-    Dof nx;
-    eom_update(g, s0, F, Tq, &nx);
-    for (int a = 0; a < D; ++a)
-      if (fabs(nx.s[a] - s0.s[a]) > (double)g.margin) ctrl->status |= ST_BOX_OVERFLOW;
-    row[k] = nx;
-    if (k == K) {
-      it[(long long)t * (K + 1)] = nx;
-      ctrl->t = t + 1;
-    }
-    ctrl->count[CNT_COUPLE] = 0;
-  }
-}
-
-// Recompute of one step's Brinkman update from the stored iterate s^(K-1).
-template <typename T, int D, int AX>
-__global__ void __launch_bounds__(BX* BY) k_apply(Geo g, Slots<T> S, Ctrl* ctrl, const Dof* it,
-                                                   const T* __restrict__ kref, T* __restrict__ boxstore, int nbox) {
-  const int t = ctrl->t, base = ctrl->base, K = g.K;
-  const Dof* row = it + (long long)(t - 1) * (K + 1);
-  const Dof s0 = row[0], sk = row[K - 1];
-  T* __restrict__ dst = slot_ptr(S, t, base);
-  const long long N = g.N;
-  int lx, ly, lz;
-  box_origin<D>(g, s0, lx, ly, lz);
-  const int j0 = blockIdx.x * BX + threadIdx.x, j1 = blockIdx.y * BY + threadIdx.y, j2 = blockIdx.z;
-  if (j0 < g.B[0] && j1 < g.B[1]) {
-    const int px = lx + j0, py = ly + j1, pz = lz + j2;
-    long long n = 0;
-    if (cell_index<D>(g, px, py, pz, n)) {
-      const T d[3] = {(T)((double)px - sk.s[0]), (T)((double)py - sk.s[1]), D == 3 ? (T)((double)pz - sk.s[2]) : T(0)};
-      const T cs = (T)sk.cs, sn = (T)sk.sn;
-      Acc<T> A;
-      gather<T, D, AX>(g, kref, d, cs, sn, A);
-      T dwr[3];
-      drot<AX>(cs, sn, A.wr, dwr);
-      const T om = (T)sk.s[7];
-      const T inv = T(1) / (T(1) + A.kap);
-      const long long bl = j0 + (long long)g.B[0] * (j1 + (long long)g.B[1] * j2);
-      T* bs = boxstore + (long long)((t - base - 1) % nbox) * g.box_cells * D;
-#pragma unroll
-      for (int a = 0; a < D; ++a) {
-        const T us = (T)sk.s[3 + a] * A.phi + om * dwr[a];
-        const T ustar = dst[(a + 1) * N + n];
-        bs[a * g.box_cells + bl] = ustar;
-        dst[(a + 1) * N + n] = (ustar + A.kap * us) * inv;
-      }
-    }
-  }
-  if (last_block_done(&ctrl->count[CNT_APPLY]) && thread_linear() == 0) {
-    ctrl->t = t + 1;
-    ctrl->count[CNT_APPLY] = 0;
-  }
-}
-
-// Reverse of coupling iteration k, cell side. Scratch planes per box cell:
-//   [0, D): u^(k);  D: dJ/dkappa_n;  [D+1, 2D+1): dJ/du^S_n.
-template <typename T, int D, int AX>
-__global__ void __launch_bounds__(BX* BY) k_adj_cell(Geo g, Ctrl* ctrl, const Dof* it, const T* __restrict__ kref,
-                                                      const T* __restrict__ boxstore, int nbox, T* Lb,
-                                                      long long lstride, T* __restrict__ acc, T* __restrict__ scratch,
-                                                      int k) {
-  constexpr int b = Axes<AX>::B, c = Axes<AX>::C;
-  const int t = ctrl->t, base = ctrl->base, K = g.K;
-  const Dof* row = it + (long long)(t - 1) * (K + 1);
-  const Dof s0 = row[0], sk = row[k - 1];
-  const double lF[3] = {ctrl->lam_F[0], ctrl->lam_F[1], ctrl->lam_F[2]};
-  const double lT = ctrl->lam_T;
-  T* Lcur = Lb + (long long)(t & 1) * lstride;
-  const long long N = g.N, BC = g.box_cells;
-  int lx, ly, lz;
-  box_origin<D>(g, s0, lx, ly, lz);
-  const int j0 = blockIdx.x * BX + threadIdx.x, j1 = blockIdx.y * BY + threadIdx.y, j2 = blockIdx.z;
-  if (j0 >= g.B[0] || j1 >= g.B[1]) return;
+  const int px = lo[0] + j0, py = lo[1] + j1, pz = lo[2] + j2;
+  long long n = 0;
+  const bool ing = cell_index<D>(g, px, py, pz, n);
+  const DofView<T> V(sk);
+  const T d[3] = {V.rel(0, px), V.rel(1, py), D == 3 ? V.rel(2, pz) : T(0)};
+  const T cs = V.cs, sn = V.sn;
+  Acc<T> A;
+  gather<T, D, AX>(g, kref, d, cs, sn, A);
+  if (A.phi > T(0) && (!ing || forbidden<D>(g, px, py, pz))) atomicOr(status, ST_BODY_OUTSIDE);
+  if (!ing) return;
+  T dwr[3], L[3], u[3] = {T(0), T(0), T(0)};
+  drot<AX>(cs, sn, A.wr, dwr);
+  rot<AX>(cs, sn, A.kr, L);
+  const T om = V.om;
+  const T inv = T(1) / (T(1) + A.kap);
   const long long bl = j0 + (long long)g.B[0] * (j1 + (long long)g.B[1] * j2);
-  const int px = lx + j0, py = ly + j1, pz = lz + j2;
+#pragma unroll
+  for (int a = 0; a < D; ++a) {
+    const T us = V.ug[a] * A.phi + om * dwr[a];
+    const T ustar = dst[(a + 1) * N + n];
+    u[a] = (ustar + A.kap * us) * inv;
+    v[a] += A.kap * u[a];
+    if (last) {
+      if (bs) bs[a * g.box_cells + bl] = ustar;
+      dst[(a + 1) * N + n] = u[a];
+    }
+  }
+  v[D] += L[b] * u[c] - L[c] * u[b];  // torque density about AX
+}
+
+// Closed-form design-side terms and the EOM update of iteration k from the cell sums s[0..D].
+template <int D, int AX>
+__device__ __forceinline__ void couple_finish(const Geo& g, const Moments* mom, const Dof& s0, const Dof& sk,
+                                              const double* s, Dof* nx, int* status) {
+  constexpr int b = Axes<AX>::B, c = Axes<AX>::C;
+  const double cs = sk.cs, sn = sk.sn, om = sk.s[7];
+  const double K1[3] = {mom->K1[0], mom->K1[1], mom->K1[2]};
+  double K1r[3], K1d[3];
+  rot<AX>(cs, sn, K1, K1r);
+  drot<AX>(cs, sn, K1, K1d);
+  const double ug[3] = {sk.s[3], sk.s[4], sk.s[5]};
+  double F[3] = {0, 0, 0};
+  for (int a = 0; a < D; ++a) F[a] = s[a] - (mom->K0 * ug[a] + om * K1d[a]);
+  const double Tq = s[D] - (K1r[b] * ug[c] - K1r[c] * ug[b]) - om * mom->K2p;
+  bool finite = isfinite(Tq);
+  for (int a = 0; a < D; ++a) finite = finite && isfinite(F[a]);
+  if (!finite) *status |= ST_NONFINITE;
+  eom_update(g, s0, F, Tq, nx);
+  for (int a = 0; a < D; ++a)
+    if (fabs(nx->s[a] - s0.s[a]) > (double)g.margin) *status |= ST_BOX_OVERFLOW;
+}
+
+// Reverse of coupling iteration k for box cell (j0, j1, j2). Scratch planes per box cell:
+//   [0, D): u^(k);  D: dJ/dkappa_n;  [D+1, 2D+1): dJ/du^S_n.  acc accumulates dJ/du*.
+template <typename T, int D, int AX>
+__device__ __forceinline__ void adj_cell_work(const Geo& g, const T* __restrict__ kref, const Dof& sk,
+                                              const int (&lo)[3], int j0, int j1, int j2, const T* __restrict__ bs,
+                                              T* Lcur, T* __restrict__ acc, T* __restrict__ scratch, int k, int K,
+                                              const T (&lF)[3], T lT) {
+  constexpr int b = Axes<AX>::B, c = Axes<AX>::C;
+  const long long N = g.N, BC = g.box_cells;
+  const long long bl = j0 + (long long)g.B[0] * (j1 + (long long)g.B[1] * j2);
+  const int px = lo[0] + j0, py = lo[1] + j1, pz = lo[2] + j2;
   long long n = 0;
   if (!cell_index<D>(g, px, py, pz, n)) {
     for (int q = 0; q < 2 * D + 1; ++q) scratch[q * BC + bl] = T(0);
     return;
   }
-  const T* bs = boxstore + (long long)((t - base - 1) % nbox) * BC * D;
-  const T d[3] = {(T)((double)px - sk.s[0]), (T)((double)py - sk.s[1]), D == 3 ? (T)((double)pz - sk.s[2]) : T(0)};
-  const T cs = (T)sk.cs, sn = (T)sk.sn;
+  const DofView<T> V(sk);
+  const T d[3] = {V.rel(0, px), V.rel(1, py), D == 3 ? V.rel(2, pz) : T(0)};
+  const T cs = V.cs, sn = V.sn;
   Acc<T> A;
   gather<T, D, AX>(g, kref, d, cs, sn, A);
   T dwr[3], L[3];
   drot<AX>(cs, sn, A.wr, dwr);
   rot<AX>(cs, sn, A.kr, L);
-  const T om = (T)sk.s[7];
+  const T om = V.om;
   const T inv = T(1) / (T(1) + A.kap);
   // sum_m W dJ/du^ref_m = kappa_n lam_F + lam_T (e x L_n), in the rotation plane
   T extra[3] = {T(0), T(0), T(0)};
-  extra[b] = -(T)lT * L[c];
-  extra[c] = (T)lT * L[b];
+  extra[b] = -lT * L[c];
+  extra[c] = lT * L[b];
   T lkap = T(0);
 #pragma unroll
   for (int a = 0; a < D; ++a) {
-    const T us = (T)sk.s[3 + a] * A.phi + om * dwr[a];
+    const T us = V.ug[a] * A.phi + om * dwr[a];
     const T uk = (bs[a * BC + bl] + A.kap * us) * inv;
-    T lu = A.kap * (T)lF[a] + extra[a];
+    T lu = A.kap * lF[a] + extra[a];
     if (k == K) lu += Lcur[(a + 1) * N + n];
     const T accv = (k == K ? T(0) : acc[a * BC + bl]) + lu * inv;
     if (k == 1)
@@ -244,164 +165,318 @@ __global__ void __launch_bounds__(BX* BY) k_adj_cell(Geo g, Ctrl* ctrl, const Do
   scratch[D * BC + bl] = lkap;
 }
 
-// Reverse of coupling iteration k, design side (one thread per design point m).
+// Reverse of coupling iteration k for design point m: dJ/dkappa^ref_m += ..., and the point's
+// contribution to dJ/ds^(k-1) added to v[8] = (xG[3], uG[3], theta, omega). Returns false if the
+// support window left the body box.
 template <typename T, int D, int AX>
-__global__ void __launch_bounds__(256) k_adj_design(Geo g, Ctrl* ctrl, const Dof* it, const T* __restrict__ kref,
-                                                     const T* __restrict__ scratch, double* __restrict__ dkref,
-                                                     double* partials, int k) {
+__device__ __forceinline__ bool adj_design_point(const Geo& g, const T* __restrict__ kref, const T* scratch,
+                                                 const Dof& sk, const int (&lo)[3], int m, const T (&lF)[3], T lT,
+                                                 double* __restrict__ dkref, T* v) {
   constexpr int b = Axes<AX>::B, c = Axes<AX>::C, ax = Axes<AX>::A;
-  __shared__ double red[32 * 8];
-  const int t = ctrl->t, K = g.K;
-  const Dof* row = it + (long long)(t - 1) * (K + 1);
-  const Dof s0 = row[0], sk = row[k - 1];
-  const double lF[3] = {ctrl->lam_F[0], ctrl->lam_F[1], ctrl->lam_F[2]};
-  const double lT = ctrl->lam_T;
   const long long BC = g.box_cells;
-  const int m = blockIdx.x * blockDim.x + threadIdx.x;
-  double v[8] = {0, 0, 0, 0, 0, 0, 0, 0};
-  if (m < g.ND) {
-    int lx, ly, lz;
-    box_origin<D>(g, s0, lx, ly, lz);
-    const int ix = m % g.nd[0], iy = (m / g.nd[0]) % g.nd[1], iz = m / (g.nd[0] * g.nd[1]);
-    const T r[3] = {(T)(ix - g.xic[0]), (T)(iy - g.xic[1]), D == 3 ? (T)(iz - g.xic[2]) : T(0)};
-    const T cs = (T)sk.cs, sn = (T)sk.sn, om = (T)sk.s[7];
-    T l[3], dl[3];
-    rot<AX>(cs, sn, r, l);
-    drot<AX>(cs, sn, r, dl);
-    const T km = kref[m];
-    T usr[3] = {T(0), T(0), T(0)}, luref[3] = {T(0), T(0), T(0)}, rotl[3] = {T(0), T(0), T(0)};
+  const int ix = m % g.nd[0], iy = (m / g.nd[0]) % g.nd[1], iz = m / (g.nd[0] * g.nd[1]);
+  const T r[3] = {(T)ix - pivot<T>(g, 0), (T)iy - pivot<T>(g, 1), D == 3 ? (T)iz - pivot<T>(g, 2) : T(0)};
+  const DofView<T> V(sk);
+  const T cs = V.cs, sn = V.sn, om = V.om;
+  T l[3], dl[3];
+  rot<AX>(cs, sn, r, l);
+  drot<AX>(cs, sn, r, dl);
+  const T km = kref[m];
+  T usr[3] = {T(0), T(0), T(0)}, luref[3] = {T(0), T(0), T(0)}, rotl[3] = {T(0), T(0), T(0)};
 #pragma unroll
-    for (int a = 0; a < D; ++a) usr[a] = (T)sk.s[3 + a] + om * dl[a];
-    rotl[b] = -(T)lT * l[c];
-    rotl[c] = (T)lT * l[b];
+  for (int a = 0; a < D; ++a) usr[a] = V.ug[a] + om * dl[a];
+  rotl[b] = -lT * l[c];
+  rotl[c] = lT * l[b];
 #pragma unroll
-    for (int a = 0; a < D; ++a) luref[a] = km * ((T)lF[a] + rotl[a]);
-    // window of analysis cells around x^ref_m: 2s cells per axis from floor(x^ref) - s + 1
-    int f[3] = {0, 0, 0};
-    T fr[3] = {T(0), T(0), T(0)};
+  for (int a = 0; a < D; ++a) luref[a] = km * (lF[a] + rotl[a]);
+  // support window: 2s cells per axis from floor(x^ref) - s + 1
+  int f[3] = {0, 0, 0};
+  T fr[3] = {T(0), T(0), T(0)};
 #pragma unroll
-    for (int a = 0; a < D; ++a) {
-      const double xr = sk.s[a] + (double)l[a];
-      const double fl = floor(xr);
-      f[a] = (int)fl;
-      fr[a] = (T)(xr - fl);
+  for (int a = 0; a < D; ++a) V.split(a, l[a], &f[a], &fr[a]);
+  const int S2 = 2 * g.s;
+  T wv[3][4], dwv[3][4];
+#pragma unroll
+  for (int a = 0; a < 3; ++a)
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      wv[a][q] = (a < D) ? T(0) : T(1);
+      dwv[a][q] = T(0);
     }
-    const int S2 = 2 * g.s;
-    T wv[3][4], dwv[3][4];
 #pragma unroll
-    for (int a = 0; a < 3; ++a)
+  for (int a = 0; a < D; ++a)
 #pragma unroll
-      for (int q = 0; q < 4; ++q) {
-        wv[a][q] = (a < D) ? T(0) : T(1);
-        dwv[a][q] = T(0);
+    for (int q = 0; q < 4; ++q) {
+      const T rr = (T)(q - g.s + 1) - fr[a];  // x_n - x^ref along a
+      if (q < S2 && fabs(rr) < (T)g.s) {
+        wv[a][q] = wfun(g.wk, rr);
+        dwv[a][q] = dwfun(g.wk, rr);
       }
+    }
+  T uref[3] = {T(0), T(0), T(0)}, slus[3] = {T(0), T(0), T(0)}, lxr[3] = {T(0), T(0), T(0)};
+  T slk = T(0);
+  bool inside = true;
+  const int B0 = g.B[0], B1 = g.B[1], B2 = (D == 3) ? g.B[2] : 1;
 #pragma unroll
-    for (int a = 0; a < D; ++a)
+  for (int q2 = 0; q2 < (D == 3 ? 4 : 1); ++q2)
 #pragma unroll
-      for (int q = 0; q < 4; ++q) {
-        const T rr = (T)(q - g.s + 1) - fr[a];  // x_n - x^ref along a
-        if (q < S2 && fabs(rr) < (T)g.s) {
-          wv[a][q] = wfun(g.wk, rr);
-          dwv[a][q] = dwfun(g.wk, rr);
+    for (int q1 = 0; q1 < 4; ++q1)
+#pragma unroll
+      for (int q0 = 0; q0 < 4; ++q0) {
+        if (q0 >= S2 || q1 >= S2 || (D == 3 && q2 >= S2)) continue;
+        const T w0 = wv[0][q0], w1 = wv[1][q1], w2 = wv[2][q2];
+        const T W = w0 * w1 * w2;
+        const T dW0 = dwv[0][q0] * w1 * w2, dW1 = w0 * dwv[1][q1] * w2, dW2 = w0 * w1 * dwv[2][q2];
+        if (W == T(0) && dW0 == T(0) && dW1 == T(0) && dW2 == T(0)) continue;
+        const int p0 = f[0] - g.s + 1 + q0 - lo[0], p1 = f[1] - g.s + 1 + q1 - lo[1];
+        const int p2 = (D == 3) ? f[2] - g.s + 1 + q2 - lo[2] : 0;
+        if (p0 < 0 || p0 >= B0 || p1 < 0 || p1 >= B1 || p2 < 0 || p2 >= B2) {
+          inside = false;
+          continue;
         }
+        const long long bl = p0 + (long long)B0 * (p1 + (long long)B1 * p2);
+        T uk[3] = {T(0), T(0), T(0)}, lus[3] = {T(0), T(0), T(0)};
+#pragma unroll
+        for (int a = 0; a < D; ++a) {
+          uk[a] = __ldcg(&scratch[a * BC + bl]);
+          lus[a] = __ldcg(&scratch[(D + 1 + a) * BC + bl]);
+        }
+        const T lk = __ldcg(&scratch[D * BC + bl]);
+        T qv = km * lk;
+#pragma unroll
+        for (int a = 0; a < D; ++a) {
+          uref[a] += W * uk[a];
+          slus[a] += W * lus[a];
+          qv += luref[a] * uk[a] + usr[a] * lus[a];
+        }
+        slk += W * lk;
+        // dW/dx^ref_e = -w'(x_e - x^ref_e) prod_{a != e} w
+        lxr[0] -= dW0 * qv;
+        lxr[1] -= dW1 * qv;
+        lxr[2] -= dW2 * qv;
       }
-    T uref[3] = {T(0), T(0), T(0)}, slus[3] = {T(0), T(0), T(0)}, lxr[3] = {T(0), T(0), T(0)};
-    T slk = T(0);
-    bool over = false;
-    const int B0 = g.B[0], B1 = g.B[1], B2 = (D == 3) ? g.B[2] : 1;
+  T Dl[3] = {T(0), T(0), T(0)};
 #pragma unroll
-    for (int q2 = 0; q2 < (D == 3 ? 4 : 1); ++q2)
+  for (int a = 0; a < D; ++a) Dl[a] = uref[a] - usr[a];
+  T dk = slk + lT * (l[b] * Dl[c] - l[c] * Dl[b]);
 #pragma unroll
-      for (int q1 = 0; q1 < 4; ++q1)
+  for (int a = 0; a < D; ++a) dk += lF[a] * Dl[a];
+  dkref[m] += (double)dk;
+  T lusr[3] = {T(0), T(0), T(0)}, ll[3] = {T(0), T(0), T(0)};
 #pragma unroll
-        for (int q0 = 0; q0 < 4; ++q0) {
-          if (q0 >= S2 || q1 >= S2 || (D == 3 && q2 >= S2)) continue;
-          const T w0 = wv[0][q0], w1 = wv[1][q1], w2 = wv[2][q2];
-          const T W = w0 * w1 * w2;
-          const T dW0 = dwv[0][q0] * w1 * w2, dW1 = w0 * dwv[1][q1] * w2, dW2 = w0 * w1 * dwv[2][q2];
-          if (W == T(0) && dW0 == T(0) && dW1 == T(0) && dW2 == T(0)) continue;
-          const int p0 = f[0] - g.s + 1 + q0 - lx, p1 = f[1] - g.s + 1 + q1 - ly;
-          const int p2 = (D == 3) ? f[2] - g.s + 1 + q2 - lz : 0;
-          if (p0 < 0 || p0 >= B0 || p1 < 0 || p1 >= B1 || p2 < 0 || p2 >= B2) {
-            over = true;
-            continue;
-          }
-          const long long bl = p0 + (long long)B0 * (p1 + (long long)B1 * p2);
-          T uk[3] = {T(0), T(0), T(0)}, lus[3] = {T(0), T(0), T(0)};
+  for (int a = 0; a < D; ++a) lusr[a] = -luref[a] + slus[a];
+  ll[b] = lT * km * Dl[c];
+  ll[c] = -lT * km * Dl[b];
+  T lth = T(0), lom = T(0);
 #pragma unroll
-          for (int a = 0; a < D; ++a) {
-            uk[a] = scratch[a * BC + bl];
-            lus[a] = scratch[(D + 1 + a) * BC + bl];
-          }
-          const T lk = scratch[D * BC + bl];
-          T qv = km * lk;
-#pragma unroll
-          for (int a = 0; a < D; ++a) {
-            uref[a] += W * uk[a];
-            slus[a] += W * lus[a];
-            qv += luref[a] * uk[a] + usr[a] * lus[a];
-          }
-          slk += W * lk;
-          // dW/dx^ref_e = -w'(x_e - x^ref_e) prod_{a != e} w
-          lxr[0] -= dW0 * qv;
-          lxr[1] -= dW1 * qv;
-          lxr[2] -= dW2 * qv;
-        }
-    if (over) atomicOr(&ctrl->status, ST_BOX_OVERFLOW);
-    T Dl[3] = {T(0), T(0), T(0)};
-#pragma unroll
-    for (int a = 0; a < D; ++a) Dl[a] = uref[a] - usr[a];
-    double dk = (double)slk + lT * (double)(l[b] * Dl[c] - l[c] * Dl[b]);
-#pragma unroll
-    for (int a = 0; a < D; ++a) dk += lF[a] * (double)Dl[a];
-    dkref[m] += dk;
-    T lusr[3] = {T(0), T(0), T(0)}, ll[3] = {T(0), T(0), T(0)};
-#pragma unroll
-    for (int a = 0; a < D; ++a) lusr[a] = -luref[a] + slus[a];
-    ll[b] = (T)lT * km * Dl[c];
-    ll[c] = -(T)lT * km * Dl[b];
-    double lth = 0.0, lom = 0.0;
-#pragma unroll
-    for (int a = 0; a < 3; ++a) {
-      const T ddl = (a == ax) ? T(0) : -l[a];  // R'' r
-      lth += (double)((lxr[a] + ll[a]) * dl[a] + om * lusr[a] * ddl);
-      lom += (double)(lusr[a] * dl[a]);
-    }
-#pragma unroll
-    for (int a = 0; a < D; ++a) {
-      v[a] = (double)lxr[a];
-      v[3 + a] = (double)lusr[a];
-    }
-    v[6] = lth;
-    v[7] = lom;
+  for (int a = 0; a < 3; ++a) {
+    const T ddl = (a == ax) ? T(0) : -l[a];  // R'' r
+    lth += (lxr[a] + ll[a]) * dl[a] + om * lusr[a] * ddl;
+    lom += lusr[a] * dl[a];
   }
-  block_sum<8>(v, red);
-  if (threadIdx.x == 0)
-    for (int a = 0; a < 8; ++a) partials[blockIdx.x * 8 + a] = v[a];
-  if (last_block_done(&ctrl->count[CNT_DESIGN]) && threadIdx.x == 0) {
-    double ls[8] = {0, 0, 0, 0, 0, 0, 0, 0};
-    for (int q = 0; q < (int)gridDim.x; ++q)
-      for (int a = 0; a < 8; ++a) ls[a] += __ldcg(&partials[q * 8 + a]);
-    double lp[8];
-    for (int a = 0; a < 8; ++a) lp[a] = ctrl->lam_prev[a];
-    double nF[3], nT;
-    if (k > 1) {
-      eom_reverse(g, ls, nF, &nT, lp);
-    } else {
-      double lsm1[8];
-      for (int a = 0; a < 8; ++a) {
-        lsm1[a] = lp[a] + ls[a];
-        ctrl->lam_s0[a] = lsm1[a];
-        lp[a] = 0.0;
-      }
-      eom_reverse(g, lsm1, nF, &nT, lp);
+#pragma unroll
+  for (int a = 0; a < D; ++a) {
+    v[a] += lxr[a];
+    v[3 + a] += lusr[a];
+  }
+  v[6] += lth;
+  v[7] += lom;
+  return inside;
+}
+
+// From the transform part ls = dJ/ds^(k-1) (design-point sums): the EOM reverse of iteration
+// k - 1, or for k = 1 the completed dJ/ds(t-1) and the EOM reverse of iteration N_itr of step t-1.
+__device__ __forceinline__ void adj_finish(const Geo& g, int k, const double* ls, double* lam_prev, double* lamF,
+                                           double* lamT, double* lam_s0) {
+  if (k > 1) {
+    eom_reverse(g, ls, lamF, lamT, lam_prev);
+  } else {
+    double lsm1[8];
+    for (int a = 0; a < 8; ++a) {
+      lsm1[a] = lam_prev[a] + ls[a];
+      lam_s0[a] = lsm1[a];
+      lam_prev[a] = 0.0;
     }
-    for (int a = 0; a < 8; ++a) ctrl->lam_prev[a] = lp[a];
-    for (int a = 0; a < 3; ++a) ctrl->lam_F[a] = nF[a];
-    ctrl->lam_T = nT;
-    ctrl->count[CNT_DESIGN] = 0;
+    eom_reverse(g, lsm1, lamF, lamT, lam_prev);
   }
 }
+
+template <typename T>
+__global__ void __launch_bounds__(256) k_prep(Geo g, const double* __restrict__ gamma, double kmax, double q,
+                                               T* __restrict__ kref, Moments* mom, double* partials, Ctrl* ctrl) {
+  __shared__ double red[32 * 5];
+  const int m = blockIdx.x * blockDim.x + threadIdx.x;
+  double v[5] = {0, 0, 0, 0, 0};
+  if (m < g.ND) {
+    const double gm = gamma[m];
+    const T k = (T)(kmax * q * gm / ((1.0 - gm) + q));  // Eq. brinkman_coefficient
+    kref[m] = k;
+    const double kd = (double)k;
+    const int i[3] = {m % g.nd[0], (m / g.nd[0]) % g.nd[1], m / (g.nd[0] * g.nd[1])};
+    double r[3];
+    for (int a = 0; a < 3; ++a) r[a] = (a < g.dim) ? i[a] - g.xic[a] : 0.0;
+    v[0] = kd;
+    v[1] = kd * r[0];
+    v[2] = kd * r[1];
+    v[3] = kd * r[2];
+    v[4] = kd * (r[g.axb] * r[g.axb] + r[g.axc] * r[g.axc]);
+  }
+  block_sum<5>(v, red);
+  if (threadIdx.x == 0)
+    for (int a = 0; a < 5; ++a) partials[blockIdx.x * 5 + a] = v[a];
+  if (!last_block_done(&ctrl->count[CNT_PREP])) return;
+  double s[5];
+  sum_partials<5>(partials, gridDim.x, s, red);
+  if (threadIdx.x == 0) {
+    mom->K0 = s[0];
+    mom->K1[0] = s[1];
+    mom->K1[1] = s[2];
+    mom->K1[2] = s[3];
+    mom->K2p = s[4];
+    ctrl->count[CNT_PREP] = 0;
+  }
+}
+
+// ---- grid form ----------------------------------------------------------------------------
+
+template <typename T, int D, int AX>
+__global__ void __launch_bounds__(BX* BY) k_couple(Geo g, Slots<T> S, Ctrl* ctrl, Dof* it, const T* __restrict__ kref,
+                                                    const Moments* __restrict__ mom, double* partials, int k,
+                                                    T* __restrict__ boxstore, int nbox, int di) {
+  __shared__ double red[32 * 4];
+  const int t = ctrl->t0 + di, base = ctrl->base, K = g.K;
+  Dof* row = it + (long long)(t - 1) * (K + 1);
+  const Dof s0 = row[0], sk = row[k - 1];
+  T* __restrict__ dst = slot_ptr(S, t, base);
+  int lo[3];
+  box_origin<D>(g, s0, lo[0], lo[1], lo[2]);
+  T* bs = (boxstore && k == K) ? boxstore + (long long)((t - base - 1) % nbox) * g.box_cells * D : nullptr;
+  const int j0 = blockIdx.x * BX + threadIdx.x, j1 = blockIdx.y * BY + threadIdx.y, j2 = blockIdx.z;
+  T v[4] = {T(0), T(0), T(0), T(0)};
+  if (j0 < g.B[0] && j1 < g.B[1]) couple_cell<T, D, AX>(g, kref, sk, lo, j0, j1, j2, dst, bs, k == K, &ctrl->status, v);
+  double s[4];
+  block_sum_to_double<4>(v, s, red);
+  if (thread_linear() == 0)
+    for (int a = 0; a < 4; ++a) partials[block_linear() * 4 + a] = s[a];
+}
+
+// Sum of the coupling partials and the EOM update: iterate s^(k) of step t.
+template <int D, int AX>
+__global__ void __launch_bounds__(256) k_couple_finish(Geo g, Ctrl* ctrl, Dof* it, const Moments* __restrict__ mom,
+                                                        const double* __restrict__ partials, int nparts, int k,
+                                                        int di) {
+  __shared__ double red[32 * 4];
+  const int t = ctrl->t0 + di, K = g.K;
+  Dof* row = it + (long long)(t - 1) * (K + 1);
+  double s[4];
+  sum_partials<4>(partials, nparts, s, red);
+  if (threadIdx.x == 0) {
+    const Dof s0 = row[0], sk = row[k - 1];
+    Dof nx;
+    int st = 0;
+    couple_finish<D, AX>(g, mom, s0, sk, s, &nx, &st);
+    if (st) ctrl->status |= st;
+    row[k] = nx;
+    if (k == K) it[(long long)t * (K + 1)] = nx;
+  }
+}
+
+// Recompute of one step's Brinkman update from the stored iterate s^(K-1).
+template <typename T, int D, int AX>
+__global__ void __launch_bounds__(BX* BY) k_apply(Geo g, Slots<T> S, const Ctrl* ctrl, const Dof* it,
+                                                   const T* __restrict__ kref, T* __restrict__ boxstore, int nbox,
+                                                   int di) {
+  const int t = ctrl->t0 + di, base = ctrl->base, K = g.K;
+  const Dof* row = it + (long long)(t - 1) * (K + 1);
+  const Dof s0 = row[0], sk = row[K - 1];
+  T* __restrict__ dst = slot_ptr(S, t, base);
+  const long long N = g.N;
+  int lo[3];
+  box_origin<D>(g, s0, lo[0], lo[1], lo[2]);
+  const int j0 = blockIdx.x * BX + threadIdx.x, j1 = blockIdx.y * BY + threadIdx.y, j2 = blockIdx.z;
+  if (j0 >= g.B[0] || j1 >= g.B[1]) return;
+  const int px = lo[0] + j0, py = lo[1] + j1, pz = lo[2] + j2;
+  long long n = 0;
+  if (!cell_index<D>(g, px, py, pz, n)) return;
+  const DofView<T> V(sk);
+  const T d[3] = {V.rel(0, px), V.rel(1, py), D == 3 ? V.rel(2, pz) : T(0)};
+  const T cs = V.cs, sn = V.sn;
+  Acc<T> A;
+  gather<T, D, AX>(g, kref, d, cs, sn, A);
+  T dwr[3];
+  drot<AX>(cs, sn, A.wr, dwr);
+  const T om = V.om;
+  const T inv = T(1) / (T(1) + A.kap);
+  const long long bl = j0 + (long long)g.B[0] * (j1 + (long long)g.B[1] * j2);
+  T* bs = boxstore + (long long)((t - base - 1) % nbox) * g.box_cells * D;
+#pragma unroll
+  for (int a = 0; a < D; ++a) {
+    const T us = V.ug[a] * A.phi + om * dwr[a];
+    const T ustar = dst[(a + 1) * N + n];
+    bs[a * g.box_cells + bl] = ustar;
+    dst[(a + 1) * N + n] = (ustar + A.kap * us) * inv;
+  }
+}
+
+template <typename T, int D, int AX>
+__global__ void __launch_bounds__(BX* BY) k_adj_cell(Geo g, const Ctrl* ctrl, const Dof* it, const T* __restrict__ kref,
+                                                      const T* __restrict__ boxstore, int nbox, T* Lb,
+                                                      long long lstride, T* __restrict__ acc, T* __restrict__ scratch,
+                                                      int k, int di) {
+  const int t = ctrl->t0 - di, base = ctrl->base, K = g.K;
+  const Dof* row = it + (long long)(t - 1) * (K + 1);
+  const Dof s0 = row[0], sk = row[k - 1];
+  T lF[3], lT;
+  lam_load<T>(ctrl, lF, lT);
+  T* Lcur = Lb + (long long)(t & 1) * lstride;
+  int lo[3];
+  box_origin<D>(g, s0, lo[0], lo[1], lo[2]);
+  const int j0 = blockIdx.x * BX + threadIdx.x, j1 = blockIdx.y * BY + threadIdx.y, j2 = blockIdx.z;
+  if (j0 >= g.B[0] || j1 >= g.B[1]) return;
+  const T* bs = boxstore + (long long)((t - base - 1) % nbox) * g.box_cells * D;
+  adj_cell_work<T, D, AX>(g, kref, sk, lo, j0, j1, j2, bs, Lcur, acc, scratch, k, K, lF, lT);
+}
+
+template <typename T, int D, int AX>
+__global__ void __launch_bounds__(kDesignBlock) k_adj_design(Geo g, Ctrl* ctrl, const Dof* it,
+                                                              const T* __restrict__ kref,
+                                                              const T* __restrict__ scratch,
+                                                              double* __restrict__ dkref, double* partials, int k,
+                                                              int di) {
+  __shared__ double red[32 * 8];
+  const int t = ctrl->t0 - di, K = g.K;
+  const Dof* row = it + (long long)(t - 1) * (K + 1);
+  const Dof s0 = row[0], sk = row[k - 1];
+  T lF[3], lT;
+  lam_load<T>(ctrl, lF, lT);
+  int lo[3];
+  box_origin<D>(g, s0, lo[0], lo[1], lo[2]);
+  const int m = blockIdx.x * blockDim.x + threadIdx.x;
+  T v[8] = {T(0), T(0), T(0), T(0), T(0), T(0), T(0), T(0)};
+  if (m < g.ND && !adj_design_point<T, D, AX>(g, kref, scratch, sk, lo, m, lF, lT, dkref, v))
+    atomicOr(&ctrl->status, ST_BOX_OVERFLOW);
+  double s[8];
+  block_sum_to_double<8>(v, s, red);
+  if (threadIdx.x == 0)
+    for (int a = 0; a < 8; ++a) partials[blockIdx.x * 8 + a] = s[a];
+}
+
+// Sum of the design-point partials and the EOM reverse (adj_finish).
+__global__ void __launch_bounds__(256) k_design_finish(Geo g, Ctrl* ctrl, const double* __restrict__ partials,
+                                                       int nparts, int k) {
+  __shared__ double red[32 * 8];
+  double ls[8];
+  sum_partials<8>(partials, nparts, ls, red);
+  if (threadIdx.x == 0) {
+    double lp[8], nF[3], nT;
+    for (int a = 0; a < 8; ++a) lp[a] = ctrl->lam_prev[a];
+    adj_finish(g, k, ls, lp, nF, &nT, ctrl->lam_s0);
+    for (int a = 0; a < 8; ++a) ctrl->lam_prev[a] = lp[a];
+    lam_store(ctrl, nF, nT);
+  }
+}
+
+// ---- small kernels ------------------------------------------------------------------------
 
 template <typename T>
 __global__ void k_init_forward(Geo g, Slots<T> S, const double* __restrict__ p0, const double* __restrict__ u0,
@@ -417,15 +492,16 @@ __global__ void k_init_forward(Geo g, Slots<T> S, const double* __restrict__ p0,
     for (int a = 0; a < 8; ++a) d.s[a] = s0[a];
     d.cs = cos(d.s[6]);
     d.sn = sin(d.s[6]);
+    dof_views(&d);
     it[0] = d;
-    ctrl->t = 1;
+    ctrl->t0 = 1;
     ctrl->base = 0;
     ctrl->status = 0;
   }
 }
 
-__global__ void k_set_step(Ctrl* ctrl, int t, int base) {
-  ctrl->t = t;
+__global__ void k_set_step(Ctrl* ctrl, int t0, int base) {
+  ctrl->t0 = t0;
   ctrl->base = base;
 }
 
@@ -437,8 +513,7 @@ __global__ void k_adj_init(Geo g, Ctrl* ctrl, const double* objw, double seed) {
   }
   eom_reverse(g, ls, nF, &nT, lp);
   for (int a = 0; a < 8; ++a) ctrl->lam_prev[a] = lp[a];
-  for (int a = 0; a < 3; ++a) ctrl->lam_F[a] = nF[a];
-  ctrl->lam_T = nT;
+  lam_store(ctrl, nF, nT);
 }
 
 __global__ void k_sensitivity(int nd, const double* __restrict__ gamma, const double* __restrict__ dkref, double kmax,
@@ -450,8 +525,8 @@ __global__ void k_sensitivity(int nd, const double* __restrict__ gamma, const do
 }
 
 template <typename T>
-__global__ void k_ckpt_pack(Geo g, Slots<T> S, T* ckpt, long long cstride, int every, const Ctrl* ctrl) {
-  const int tn = ctrl->t - 1;
+__global__ void k_ckpt_pack(Geo g, Slots<T> S, T* ckpt, long long cstride, int every, const Ctrl* ctrl, int di) {
+  const int tn = ctrl->t0 + di;
   const T* src = slot_ptr(S, tn, ctrl->base);
   T* dst = ckpt + (long long)(tn / every) * cstride;
   const long long M = (long long)(g.dim + 1) * g.N;
@@ -459,9 +534,36 @@ __global__ void k_ckpt_pack(Geo g, Slots<T> S, T* ckpt, long long cstride, int e
     dst[i] = src[i];
 }
 
-inline dim3 box_grid(const Geo& g) { return dim3((g.B[0] + BX - 1) / BX, (g.B[1] + BY - 1) / BY, g.dim == 3 ? g.B[2] : 1); }
+inline dim3 box_grid(const Geo& g) {
+  return dim3((g.B[0] + BX - 1) / BX, (g.B[1] + BY - 1) / BY, g.dim == 3 ? g.B[2] : 1);
+}
 
 }  // namespace
+
+// Dispatch on the dimension and the (runtime) rotation axis to the compile-time instantiation.
+#define LKS_BOX_DISPATCH(KERNEL, GRID, BLOCK, ...)          \
+  do {                                                      \
+    if (g.dim == 2)                                         \
+      KERNEL<T, 2, 2><<<GRID, BLOCK, 0, st>>>(__VA_ARGS__); \
+    else if (g.ax == 0)                                     \
+      KERNEL<T, 3, 0><<<GRID, BLOCK, 0, st>>>(__VA_ARGS__); \
+    else if (g.ax == 1)                                     \
+      KERNEL<T, 3, 1><<<GRID, BLOCK, 0, st>>>(__VA_ARGS__); \
+    else                                                    \
+      KERNEL<T, 3, 2><<<GRID, BLOCK, 0, st>>>(__VA_ARGS__); \
+  } while (0)
+
+#define LKS_AXIS_DISPATCH(KERNEL, GRID, BLOCK, ...)         \
+  do {                                                      \
+    if (g.dim == 2)                                         \
+      KERNEL<2, 2><<<GRID, BLOCK, 0, st>>>(__VA_ARGS__);    \
+    else if (g.ax == 0)                                     \
+      KERNEL<3, 0><<<GRID, BLOCK, 0, st>>>(__VA_ARGS__);    \
+    else if (g.ax == 1)                                     \
+      KERNEL<3, 1><<<GRID, BLOCK, 0, st>>>(__VA_ARGS__);    \
+    else                                                    \
+      KERNEL<3, 2><<<GRID, BLOCK, 0, st>>>(__VA_ARGS__);    \
+  } while (0)
 
 template <typename T>
 void launch_prep(const Geo& g, const double* gamma, double kappa_max, double q, T* kref, Moments* mom,
@@ -469,43 +571,34 @@ void launch_prep(const Geo& g, const double* gamma, double kappa_max, double q, 
   k_prep<T><<<(g.ND + 255) / 256, 256, 0, st>>>(g, gamma, kappa_max, q, kref, mom, partials, ctrl);
 }
 
-// Dispatch on the dimension and the (runtime) rotation axis to the compile-time instantiation.
-#define LKS_BOX_DISPATCH(KERNEL, GRID, BLOCK, ...)                                   \
-  do {                                                                               \
-    if (g.dim == 2)                                                                  \
-      KERNEL<T, 2, 2><<<GRID, BLOCK, 0, st>>>(__VA_ARGS__);                          \
-    else if (g.ax == 0)                                                              \
-      KERNEL<T, 3, 0><<<GRID, BLOCK, 0, st>>>(__VA_ARGS__);                          \
-    else if (g.ax == 1)                                                              \
-      KERNEL<T, 3, 1><<<GRID, BLOCK, 0, st>>>(__VA_ARGS__);                          \
-    else                                                                             \
-      KERNEL<T, 3, 2><<<GRID, BLOCK, 0, st>>>(__VA_ARGS__);                          \
-  } while (0)
-
 template <typename T>
 void launch_couple(const Geo& g, const Slots<T>& S, Ctrl* ctrl, Dof* it, const T* kref, const Moments* mom,
-                   double* partials, int k, T* boxstore, int nbox, cudaStream_t st) {
-  LKS_BOX_DISPATCH(k_couple, box_grid(g), dim3(BX, BY), g, S, ctrl, it, kref, mom, partials, k, boxstore, nbox);
+                   double* partials, int k, T* boxstore, int nbox, int di, cudaStream_t st) {
+  const dim3 grid = box_grid(g);
+  LKS_BOX_DISPATCH(k_couple, grid, dim3(BX, BY), g, S, ctrl, it, kref, mom, partials, k, boxstore, nbox, di);
+  const int nparts = (int)(grid.x * grid.y * grid.z);
+  LKS_AXIS_DISPATCH(k_couple_finish, 1, 256, g, ctrl, it, mom, partials, nparts, k, di);
 }
 
 template <typename T>
-void launch_apply(const Geo& g, const Slots<T>& S, Ctrl* ctrl, const Dof* it, const T* kref, T* boxstore, int nbox,
-                  cudaStream_t st) {
-  LKS_BOX_DISPATCH(k_apply, box_grid(g), dim3(BX, BY), g, S, ctrl, it, kref, boxstore, nbox);
+void launch_apply(const Geo& g, const Slots<T>& S, const Ctrl* ctrl, const Dof* it, const T* kref, T* boxstore,
+                  int nbox, int di, cudaStream_t st) {
+  LKS_BOX_DISPATCH(k_apply, box_grid(g), dim3(BX, BY), g, S, ctrl, it, kref, boxstore, nbox, di);
 }
 
 template <typename T>
-void launch_adj_cell(const Geo& g, Ctrl* ctrl, const Dof* it, const T* kref, const T* boxstore, int nbox, T* Lb,
-                     long long lstride, T* acc, T* scratch, int k, cudaStream_t st) {
+void launch_adj_cell(const Geo& g, const Ctrl* ctrl, const Dof* it, const T* kref, const T* boxstore, int nbox, T* Lb,
+                     long long lstride, T* acc, T* scratch, int k, int di, cudaStream_t st) {
   LKS_BOX_DISPATCH(k_adj_cell, box_grid(g), dim3(BX, BY), g, ctrl, it, kref, boxstore, nbox, Lb, lstride, acc,
-                   scratch, k);
+                   scratch, k, di);
 }
 
 template <typename T>
 void launch_adj_design(const Geo& g, Ctrl* ctrl, const Dof* it, const T* kref, const T* scratch, double* dkref,
-                       double* partials, int k, cudaStream_t st) {
-  const unsigned nb = (unsigned)((g.ND + 255) / 256);
-  LKS_BOX_DISPATCH(k_adj_design, nb, 256, g, ctrl, it, kref, scratch, dkref, partials, k);
+                       double* partials, int k, int di, cudaStream_t st) {
+  const unsigned nb = (unsigned)((g.ND + kDesignBlock - 1) / kDesignBlock);
+  LKS_BOX_DISPATCH(k_adj_design, nb, kDesignBlock, g, ctrl, it, kref, scratch, dkref, partials, k, di);
+  k_design_finish<<<1, 256, 0, st>>>(g, ctrl, partials, (int)nb, k);
 }
 
 template <typename T>
@@ -515,7 +608,7 @@ void launch_init_forward(const Geo& g, const Slots<T>& S, const double* p0, cons
   k_init_forward<T><<<(unsigned)(nb < 4096 ? nb : 4096), 256, 0, st>>>(g, S, p0, u0, s0dev, it, ctrl);
 }
 
-void launch_set_step(Ctrl* ctrl, int t, int base, cudaStream_t st) { k_set_step<<<1, 1, 0, st>>>(ctrl, t, base); }
+void launch_set_step(Ctrl* ctrl, int t0, int base, cudaStream_t st) { k_set_step<<<1, 1, 0, st>>>(ctrl, t0, base); }
 
 void launch_adj_init(const Geo& g, Ctrl* ctrl, const double* objw, double seed, double* dkref, int nd,
                      cudaStream_t st) {
@@ -529,26 +622,27 @@ void launch_sensitivity(const Geo& g, const double* gamma, const double* dkref, 
 }
 
 template <typename T>
-void launch_ckpt_pack(const Geo& g, const Slots<T>& S, T* ckpt, long long cstride, int every, const Ctrl* ctrl,
+void launch_ckpt_pack(const Geo& g, const Slots<T>& S, T* ckpt, long long cstride, int every, const Ctrl* ctrl, int di,
                       cudaStream_t st) {
   const long long M = (long long)(g.dim + 1) * g.N;
   const long long nb = (M + 255) / 256;
-  k_ckpt_pack<T><<<(unsigned)(nb < 8192 ? nb : 8192), 256, 0, st>>>(g, S, ckpt, cstride, every, ctrl);
+  k_ckpt_pack<T><<<(unsigned)(nb < 8192 ? nb : 8192), 256, 0, st>>>(g, S, ckpt, cstride, every, ctrl, di);
 }
 
-#define LKS_INST(T)                                                                                              \
-  template void launch_prep<T>(const Geo&, const double*, double, double, T*, Moments*, double*, Ctrl*,           \
-                               cudaStream_t);                                                                    \
-  template void launch_couple<T>(const Geo&, const Slots<T>&, Ctrl*, Dof*, const T*, const Moments*, double*, int, \
-                                 T*, int, cudaStream_t);                                                         \
-  template void launch_apply<T>(const Geo&, const Slots<T>&, Ctrl*, const Dof*, const T*, T*, int, cudaStream_t); \
-  template void launch_adj_cell<T>(const Geo&, Ctrl*, const Dof*, const T*, const T*, int, T*, long long, T*, T*, \
-                                   int, cudaStream_t);                                                           \
-  template void launch_adj_design<T>(const Geo&, Ctrl*, const Dof*, const T*, const T*, double*, double*, int,    \
-                                     cudaStream_t);                                                              \
-  template void launch_init_forward<T>(const Geo&, const Slots<T>&, const double*, const double*, const double*,  \
-                                       Dof*, Ctrl*, cudaStream_t);                                               \
-  template void launch_ckpt_pack<T>(const Geo&, const Slots<T>&, T*, long long, int, const Ctrl*, cudaStream_t);
+#define LKS_INST(T)                                                                                                 \
+  template void launch_prep<T>(const Geo&, const double*, double, double, T*, Moments*, double*, Ctrl*,              \
+                               cudaStream_t);                                                                       \
+  template void launch_couple<T>(const Geo&, const Slots<T>&, Ctrl*, Dof*, const T*, const Moments*, double*, int,    \
+                                 T*, int, int, cudaStream_t);                                                       \
+  template void launch_apply<T>(const Geo&, const Slots<T>&, const Ctrl*, const Dof*, const T*, T*, int, int,        \
+                                cudaStream_t);                                                                      \
+  template void launch_adj_cell<T>(const Geo&, const Ctrl*, const Dof*, const T*, const T*, int, T*, long long, T*, \
+                                   T*, int, int, cudaStream_t);                                                     \
+  template void launch_adj_design<T>(const Geo&, Ctrl*, const Dof*, const T*, const T*, double*, double*, int, int,  \
+                                     cudaStream_t);                                                                 \
+  template void launch_init_forward<T>(const Geo&, const Slots<T>&, const double*, const double*, const double*,     \
+                                       Dof*, Ctrl*, cudaStream_t);                                                  \
+  template void launch_ckpt_pack<T>(const Geo&, const Slots<T>&, T*, long long, int, const Ctrl*, int, cudaStream_t);
 
 LKS_INST(float)
 LKS_INST(double)

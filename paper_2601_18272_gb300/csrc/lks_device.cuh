@@ -21,15 +21,75 @@ enum { DOF_TX = 1, DOF_TY = 2, DOF_TZ = 4, DOF_ROT = 8 };
 enum { ST_BODY_OUTSIDE = 1, ST_NONFINITE = 2, ST_BOX_OVERFLOW = 4 };
 enum { CNT_COUPLE = 0, CNT_APPLY = 1, CNT_DESIGN = 2, CNT_ADJ_STENCIL = 3, CNT_PREP = 4, CNT_CKPT = 5, CNT_N = 8 };
 
-// One DOF iterate: s = (xG[3], uG[3], theta, omega) plus cos/sin theta.
+// One DOF iterate: s = (xG[3], uG[3], theta, omega) plus cos/sin theta, and FP32 views of what the
+// per-cell kernels need (written once per iterate by dof_views, so that FP32 kernels do no FP64
+// arithmetic: GB300 issues FP64 at a small fraction of the FP32 rate).
 struct Dof {
   double s[8];
   double cs, sn;
+  int xi[3];    // floor(x^G)
+  float xf[3];  // x^G - floor(x^G)
+  float ug[3];  // u^G
+  float om, csf, snf;
 };
 
-// Device control block (one per handle).
+__host__ __device__ inline void dof_views(Dof* d) {
+  for (int a = 0; a < 3; ++a) {
+    const double fl = floor(d->s[a]);
+    d->xi[a] = (int)fl;
+    d->xf[a] = (float)(d->s[a] - fl);
+    d->ug[a] = (float)d->s[3 + a];
+  }
+  d->om = (float)d->s[7];
+  d->csf = (float)d->cs;
+  d->snf = (float)d->sn;
+}
+
+// Per-thread view of an iterate in the field type T: FP32 fields read the FP32 views, FP64 fields
+// the FP64 values.
+template <typename T>
+struct DofView;
+template <>
+struct DofView<float> {
+  float cs, sn, om, ug[3], xf[3];
+  int xi[3];
+  __device__ __forceinline__ explicit DofView(const Dof& d) : cs(d.csf), sn(d.snf), om(d.om) {
+    for (int a = 0; a < 3; ++a) {
+      ug[a] = d.ug[a];
+      xf[a] = d.xf[a];
+      xi[a] = d.xi[a];
+    }
+  }
+  // x_a - x^G_a for integer position p
+  __device__ __forceinline__ float rel(int a, int p) const { return (float)(p - xi[a]) - xf[a]; }
+  // x^G_a + off split as (integer cell, fraction in [0, 1))
+  __device__ __forceinline__ void split(int a, float off, int* cell, float* frac) const {
+    const float v = xf[a] + off, fl = floorf(v);
+    *cell = xi[a] + (int)fl;
+    *frac = v - fl;
+  }
+};
+template <>
+struct DofView<double> {
+  double cs, sn, om, ug[3], x[3];
+  __device__ __forceinline__ explicit DofView(const Dof& d) : cs(d.cs), sn(d.sn), om(d.s[7]) {
+    for (int a = 0; a < 3; ++a) {
+      ug[a] = d.s[3 + a];
+      x[a] = d.s[a];
+    }
+  }
+  __device__ __forceinline__ double rel(int a, int p) const { return (double)p - x[a]; }
+  __device__ __forceinline__ void split(int a, double off, int* cell, double* frac) const {
+    const double v = x[a] + off, fl = floor(v);
+    *cell = (int)fl;
+    *frac = v - fl;
+  }
+};
+
+// Device control block (one per handle). The step a kernel works on is t0 + di (forward) or
+// t0 - di (adjoint), with di baked into each captured launch, so one graph serves every chunk.
 struct Ctrl {
-  int t;                  // forward: step being computed; adjoint: step being reversed
+  int t0;                 // forward: first step of the chunk; adjoint: last step of the chunk
   int base;               // step held in slot 0 of the resident segment
   int status;             // ST_* bits
   int pad;
@@ -38,6 +98,7 @@ struct Ctrl {
   double lam_F[3];        // adjoint: dJ/dF of the iteration being reversed
   double lam_T;           // adjoint: dJ/dT
   double lam_s0[8];       // adjoint: dJ/ds(0) after the sweep
+  float lam_Ff[3], lam_Tf;  // FP32 copies of lam_F, lam_T
 };
 
 // Design-grid moments used by the closed-form design-side force and torque terms.
@@ -56,11 +117,13 @@ struct Geo {
   int nd[3];
   int ND;
   double xic[3];  // design pivot xi^G
+  float xicf[3];  // FP32 copy of the pivot
   int ax, axb, axc;
   int dof_mask;
   int wk, s;      // weight kind, support half-width (2 for cos4, 1 for bilinear)
   int K;          // N_itr
   double A, u_in, dp, mass, inertia;
+  float A2;       // 2A, for FP32 kernels
   int B[3];       // body box extent in cells
   int hb[3];      // box half extent (ceil of the body's half extent)
   int margin;     // cells of drift allowed within one step
@@ -90,9 +153,10 @@ __device__ __forceinline__ int wrapi(int v, int n) {
 
 // Grid-separation weight w(r) (Sec. 2.3, Eq. weight_function read as (1 + cos(pi r / 2)) / 4 on
 // |r| < 2), or bilinear 1 - |r| on |r| < 1; both evaluated only inside the support.
+// FP32 uses the SFU intrinsics (absolute error about 4e-7 on (-pi, pi)); FP64 uses cospi / sinpi.
 __device__ __forceinline__ float wfun(int wk, float r) {
   if (wk == W_BILINEAR) return 1.0f - fabsf(r);
-  return 0.25f * (1.0f + cospif(0.5f * r));
+  return 0.25f * (1.0f + __cosf(1.57079632679f * r));
 }
 __device__ __forceinline__ double wfun(int wk, double r) {
   if (wk == W_BILINEAR) return 1.0 - fabs(r);
@@ -101,12 +165,20 @@ __device__ __forceinline__ double wfun(int wk, double r) {
 // dw/dr inside the support; the bilinear kink at r = 0 takes the r >= 0 branch.
 __device__ __forceinline__ float dwfun(int wk, float r) {
   if (wk == W_BILINEAR) return r >= 0.0f ? -1.0f : 1.0f;
-  return -0.125f * 3.14159265358979f * sinpif(0.5f * r);
+  return -0.392699081699f * __sinf(1.57079632679f * r);
 }
 __device__ __forceinline__ double dwfun(int wk, double r) {
   if (wk == W_BILINEAR) return r >= 0.0 ? -1.0 : 1.0;
   return -0.125 * 3.141592653589793 * sinpi(0.5 * r);
 }
+
+// Design pivot component in the arithmetic type.
+template <typename F>
+__device__ __forceinline__ F pivot(const Geo& g, int a);
+template <>
+__device__ __forceinline__ float pivot<float>(const Geo& g, int a) { return g.xicf[a]; }
+template <>
+__device__ __forceinline__ double pivot<double>(const Geo& g, int a) { return g.xic[a]; }
 
 // Rotation axis AX (compile time) and its in-plane axes, right-handed: (B, C) = (AX+1, AX+2) mod 3.
 template <int AX>
@@ -117,9 +189,9 @@ struct Axes {
 // Box origin (unwrapped coordinates) for the step that starts from s(t-1).
 template <int D>
 __device__ __forceinline__ void box_origin(const Geo& g, const Dof& s0, int& lx, int& ly, int& lz) {
-  lx = (int)floor(s0.s[0]) - g.hb[0] - g.s - g.margin;
-  ly = (int)floor(s0.s[1]) - g.hb[1] - g.s - g.margin;
-  lz = (D == 3) ? (int)floor(s0.s[2]) - g.hb[2] - g.s - g.margin : 0;
+  lx = s0.xi[0] - g.hb[0] - g.s - g.margin;
+  ly = s0.xi[1] - g.hb[1] - g.s - g.margin;
+  lz = (D == 3) ? s0.xi[2] - g.hb[2] - g.s - g.margin : 0;
 }
 
 // Wrapped grid index of the unwrapped position (px, py, pz); false if it lies outside the grid on
@@ -174,15 +246,15 @@ __device__ __forceinline__ void gather(const Geo& g, const F* __restrict__ kref,
                                        Acc<F>& o) {
   constexpr int b = Axes<AX>::B, c = Axes<AX>::C, ax = Axes<AX>::A;
   const F S = (F)g.s;
-  const F xib = cs * d[b] + sn * d[c] + (F)g.xic[b];
-  const F xic = -sn * d[b] + cs * d[c] + (F)g.xic[c];
+  const F xib = cs * d[b] + sn * d[c] + pivot<F>(g, b);
+  const F xic = -sn * d[b] + cs * d[c] + pivot<F>(g, c);
   const F h = S * (fabs(cs) + fabs(sn));
   const int ib0 = max(0, (int)ceil(xib - h)), ib1 = min(g.nd[b] - 1, (int)floor(xib + h));
   const int ic0 = max(0, (int)ceil(xic - h)), ic1 = min(g.nd[c] - 1, (int)floor(xic + h));
   int ia0 = 0, ia1 = 0;
   F xia = F(0);
   if (D == 3) {
-    xia = d[ax] + (F)g.xic[ax];
+    xia = d[ax] + pivot<F>(g, ax);
     const int fa = (int)floor(xia);
     ia0 = max(0, fa - g.s + 1);
     ia1 = min(g.nd[ax] - 1, fa + g.s);
@@ -194,15 +266,39 @@ __device__ __forceinline__ void gather(const Geo& g, const F* __restrict__ kref,
   const int sb = (b == 0) ? sx : (b == 1 ? sy : sz);
   const int sc = (c == 0) ? sx : (c == 1 ? sy : sz);
   const int sa = (ax == 0) ? sx : (ax == 1 ? sy : sz);
+  // For a candidate row ib, both rotated offsets are linear in ec = ic - xic:
+  //   x^ref - x_n along b: cs eb - sn ec,  along c: sn eb + cs ec.
+  // Bound the column loop by the interval where both lie in (-S, S), widened slightly; the exact
+  // acceptance test below still decides.
+  const F tiny = F(1e-6), pad = F(1e-3);
+  const F ics = fabs(cs) > tiny ? F(1) / cs : F(0), isn = fabs(sn) > tiny ? F(1) / sn : F(0);
   for (int ib = ib0; ib <= ib1; ++ib) {
     const F eb = (F)ib - xib;
-    for (int ic = ic0; ic <= ic1; ++ic) {
+    F elo = -F(1e30), ehi = F(1e30);
+    if (isn != F(0)) {  // |cs eb - sn ec| < S
+      const F e1 = (cs * eb - S) * isn, e2 = (cs * eb + S) * isn;
+      elo = fmax(elo, fmin(e1, e2));
+      ehi = fmin(ehi, fmax(e1, e2));
+    } else if (fabs(cs * eb) >= S + pad) {
+      continue;
+    }
+    if (ics != F(0)) {  // |sn eb + cs ec| < S
+      const F e1 = (-S - sn * eb) * ics, e2 = (S - sn * eb) * ics;
+      elo = fmax(elo, fmin(e1, e2));
+      ehi = fmin(ehi, fmax(e1, e2));
+    } else if (fabs(sn * eb) >= S + pad) {
+      continue;
+    }
+    elo = fmax(elo, F(-1e6));
+    ehi = fmin(ehi, F(1e6));
+    const int jc0 = max(ic0, (int)ceil(xic + elo - pad)), jc1 = min(ic1, (int)floor(xic + ehi + pad));
+    for (int ic = jc0; ic <= jc1; ++ic) {
       const F ec = (F)ic - xic;
       const F ob = cs * eb - sn * ec;  // x^ref_m - x_n along b
       const F oc = sn * eb + cs * ec;
       if (fabs(ob) >= S || fabs(oc) >= S) continue;
       const F w2 = wfun(g.wk, ob) * wfun(g.wk, oc);
-      const F rb = (F)ib - (F)g.xic[b], rc = (F)ic - (F)g.xic[c];
+      const F rb = (F)ib - pivot<F>(g, b), rc = (F)ic - pivot<F>(g, c);
       const int m2 = ib * sb + ic * sc;
       if (D == 2) {
         const F wkap = w2 * kref[m2];
@@ -218,7 +314,7 @@ __device__ __forceinline__ void gather(const Geo& g, const F* __restrict__ kref,
           if (fabs(oa) >= S) continue;
           const F W = w2 * wfun(g.wk, oa);
           const F wkap = W * kref[m2 + ia * sa];
-          const F ra = (F)ia - (F)g.xic[ax];
+          const F ra = (F)ia - pivot<F>(g, ax);
           o.phi += W;
           o.kap += wkap;
           o.wr[b] += W * rb;
@@ -229,6 +325,106 @@ __device__ __forceinline__ void gather(const Geo& g, const F* __restrict__ kref,
           o.kr[ax] += wkap * ra;
         }
       }
+    }
+  }
+}
+
+// The same gather split over LANES consecutive threads of a warp: lane j takes candidate rows
+// ib0 + j, ib0 + j + LANES, ...; the sums are combined with shuffles so every lane ends with the
+// cell's totals.
+template <typename F, int D, int AX, int LANES>
+__device__ __forceinline__ void gather_lanes(const Geo& g, const F* __restrict__ kref, const F (&d)[3], F cs, F sn,
+                                             int lane, bool active, Acc<F>& o) {
+  constexpr int b = Axes<AX>::B, c = Axes<AX>::C, ax = Axes<AX>::A;
+  const F S = (F)g.s;
+  const F xib = cs * d[b] + sn * d[c] + pivot<F>(g, b);
+  const F xic = -sn * d[b] + cs * d[c] + pivot<F>(g, c);
+  const F h = S * (fabs(cs) + fabs(sn));
+  int ib0 = max(0, (int)ceil(xib - h)), ib1 = min(g.nd[b] - 1, (int)floor(xib + h));
+  const int ic0 = max(0, (int)ceil(xic - h)), ic1 = min(g.nd[c] - 1, (int)floor(xic + h));
+  if (!active) ib1 = ib0 - 1;
+  int ia0 = 0, ia1 = 0;
+  F xia = F(0);
+  if (D == 3) {
+    xia = d[ax] + pivot<F>(g, ax);
+    const int fa = (int)floor(xia);
+    ia0 = max(0, fa - g.s + 1);
+    ia1 = min(g.nd[ax] - 1, fa + g.s);
+  }
+  o.phi = o.kap = F(0);
+#pragma unroll
+  for (int a = 0; a < 3; ++a) o.wr[a] = o.kr[a] = F(0);
+  const int sx = 1, sy = g.nd[0], sz = g.nd[0] * g.nd[1];
+  const int sb = (b == 0) ? sx : (b == 1 ? sy : sz);
+  const int sc = (c == 0) ? sx : (c == 1 ? sy : sz);
+  const int sa = (ax == 0) ? sx : (ax == 1 ? sy : sz);
+  const F tiny = F(1e-6), pad = F(1e-3);
+  const F ics = fabs(cs) > tiny ? F(1) / cs : F(0), isn = fabs(sn) > tiny ? F(1) / sn : F(0);
+  for (int ib = ib0 + lane; ib <= ib1; ib += LANES) {
+    const F eb = (F)ib - xib;
+    F elo = -F(1e30), ehi = F(1e30);
+    if (isn != F(0)) {
+      const F e1 = (cs * eb - S) * isn, e2 = (cs * eb + S) * isn;
+      elo = fmax(elo, fmin(e1, e2));
+      ehi = fmin(ehi, fmax(e1, e2));
+    } else if (fabs(cs * eb) >= S + pad) {
+      continue;
+    }
+    if (ics != F(0)) {
+      const F e1 = (-S - sn * eb) * ics, e2 = (S - sn * eb) * ics;
+      elo = fmax(elo, fmin(e1, e2));
+      ehi = fmin(ehi, fmax(e1, e2));
+    } else if (fabs(sn * eb) >= S + pad) {
+      continue;
+    }
+    elo = fmax(elo, F(-1e6));
+    ehi = fmin(ehi, F(1e6));
+    const int jc0 = max(ic0, (int)ceil(xic + elo - pad)), jc1 = min(ic1, (int)floor(xic + ehi + pad));
+    const F rb = (F)ib - pivot<F>(g, b);
+    for (int ic = jc0; ic <= jc1; ++ic) {
+      const F ec = (F)ic - xic;
+      const F ob = cs * eb - sn * ec;
+      const F oc = sn * eb + cs * ec;
+      if (fabs(ob) >= S || fabs(oc) >= S) continue;
+      const F w2 = wfun(g.wk, ob) * wfun(g.wk, oc);
+      const F rc = (F)ic - pivot<F>(g, c);
+      const int m2 = ib * sb + ic * sc;
+      if (D == 2) {
+        const F wkap = w2 * kref[m2];
+        o.phi += w2;
+        o.kap += wkap;
+        o.wr[b] += w2 * rb;
+        o.wr[c] += w2 * rc;
+        o.kr[b] += wkap * rb;
+        o.kr[c] += wkap * rc;
+      } else {
+        for (int ia = ia0; ia <= ia1; ++ia) {
+          const F oa = (F)ia - xia;
+          if (fabs(oa) >= S) continue;
+          const F W = w2 * wfun(g.wk, oa);
+          const F wkap = W * kref[m2 + ia * sa];
+          const F ra = (F)ia - pivot<F>(g, ax);
+          o.phi += W;
+          o.kap += wkap;
+          o.wr[b] += W * rb;
+          o.wr[c] += W * rc;
+          o.wr[ax] += W * ra;
+          o.kr[b] += wkap * rb;
+          o.kr[c] += wkap * rc;
+          o.kr[ax] += wkap * ra;
+        }
+      }
+    }
+  }
+#pragma unroll
+  for (int off = 1; off < LANES; off <<= 1) {
+    o.phi += __shfl_xor_sync(0xffffffffu, o.phi, off);
+    o.kap += __shfl_xor_sync(0xffffffffu, o.kap, off);
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+      if (D == 2 && a == ax) continue;
+      o.wr[a] += __shfl_xor_sync(0xffffffffu, o.wr[a], off);
+      o.kr[a] += __shfl_xor_sync(0xffffffffu, o.kr[a], off);
     }
   }
 }
@@ -274,21 +470,135 @@ __device__ __forceinline__ void block_sum(double* v, double* smem) {
   __syncthreads();
 }
 
-// Last-block election after every block has published its partial: true in exactly one block,
-// which then sees all partials (read them with __ldcg). No block waits on another.
+// Last-block election after thread 0 of every block has published the block's partial: true in
+// exactly one block, which then sees all partials (read them with __ldcg). Only thread 0 fences
+// and counts; no block waits on another.
 __device__ __forceinline__ bool last_block_done(unsigned* counter) {
   __shared__ bool is_last;
   const int tid = threadIdx.x + blockDim.x * (threadIdx.y + blockDim.y * threadIdx.z);
-  __threadfence();
   __syncthreads();
   if (tid == 0) {
+    __threadfence();
     const unsigned total = gridDim.x * gridDim.y * gridDim.z;
-    unsigned prev = atomicAdd(counter, 1u);
+    const unsigned prev = atomicAdd(counter, 1u);
     is_last = (prev == total - 1);
+    if (is_last) __threadfence();
   }
   __syncthreads();
-  if (is_last) __threadfence();
   return is_last;
+}
+
+// Double-float (two-sum) accumulation: (hi, lo) represents hi + lo exactly enough for FP64-grade
+// sums while issuing only FP32 instructions (Knuth's two-sum; Dekker's renormalisation).
+__device__ __forceinline__ void df_add(float& hi, float& lo, float bh, float bl) {
+  const float s = hi + bh;
+  const float bb = s - hi;
+  float e = (hi - (s - bb)) + (bh - bb);
+  e += lo + bl;
+  hi = s + e;
+  lo = e - (hi - s);
+}
+
+// Block sum of NV per-thread values to FP64 in thread 0. FP32 values go through a double-float
+// shuffle tree and touch FP64 once per value in thread 0; FP64 values use block_sum.
+template <int NV>
+__device__ __forceinline__ void block_sum_to_double(float (&v)[NV], double* out, double* smem) {
+  const int tid = threadIdx.x + blockDim.x * (threadIdx.y + blockDim.y * threadIdx.z);
+  const int nthreads = blockDim.x * blockDim.y * blockDim.z;
+  float hi[NV], lo[NV];
+#pragma unroll
+  for (int i = 0; i < NV; ++i) {
+    hi[i] = v[i];
+    lo[i] = 0.0f;
+  }
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1)
+#pragma unroll
+    for (int i = 0; i < NV; ++i) {
+      const float bh = __shfl_xor_sync(0xffffffffu, hi[i], off), bl = __shfl_xor_sync(0xffffffffu, lo[i], off);
+      df_add(hi[i], lo[i], bh, bl);
+    }
+  float2* s2 = reinterpret_cast<float2*>(smem);
+  const int warp = tid >> 5, lane = tid & 31, nw = nthreads >> 5;
+  if (lane == 0)
+#pragma unroll
+    for (int i = 0; i < NV; ++i) s2[warp * NV + i] = make_float2(hi[i], lo[i]);
+  __syncthreads();
+  if (warp == 0) {
+#pragma unroll
+    for (int i = 0; i < NV; ++i) {
+      hi[i] = 0.0f;
+      lo[i] = 0.0f;
+      if (lane < nw) {
+        hi[i] = s2[lane * NV + i].x;
+        lo[i] = s2[lane * NV + i].y;
+      }
+    }
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1)
+#pragma unroll
+      for (int i = 0; i < NV; ++i) {
+        const float bh = __shfl_xor_sync(0xffffffffu, hi[i], off), bl = __shfl_xor_sync(0xffffffffu, lo[i], off);
+        df_add(hi[i], lo[i], bh, bl);
+      }
+    if (lane == 0)
+#pragma unroll
+      for (int i = 0; i < NV; ++i) out[i] = (double)hi[i] + (double)lo[i];
+  }
+  __syncthreads();
+}
+template <int NV>
+__device__ __forceinline__ void block_sum_to_double(double (&v)[NV], double* out, double* smem) {
+  block_sum<NV>(v, smem);
+  const int tid = threadIdx.x + blockDim.x * (threadIdx.y + blockDim.y * threadIdx.z);
+  if (tid == 0)
+#pragma unroll
+    for (int i = 0; i < NV; ++i) out[i] = v[i];
+}
+
+// In the elected last block: sum the per-CTA partials [nblocks][NV] with every thread (each
+// thread a fixed strided subset, then the fixed block tree), so the order is deterministic and
+// the L2 loads are issued in parallel. Result in thread 0. All threads of the block must call it.
+template <int NV>
+__device__ __forceinline__ void sum_partials(const double* partials, int nblocks, double* out, double* smem) {
+  const int tid = threadIdx.x + blockDim.x * (threadIdx.y + blockDim.y * threadIdx.z);
+  const int nthreads = blockDim.x * blockDim.y * blockDim.z;
+  double v[NV];
+#pragma unroll
+  for (int a = 0; a < NV; ++a) v[a] = 0.0;
+  for (int q = tid; q < nblocks; q += nthreads)
+#pragma unroll
+    for (int a = 0; a < NV; ++a) v[a] += __ldcg(&partials[q * NV + a]);
+  block_sum<NV>(v, smem);
+#pragma unroll
+  for (int a = 0; a < NV; ++a) out[a] = v[a];
+}
+
+// cos/sin of theta0 + dth from those of theta0 by the angle-addition formulas; the increment is
+// one step's rotation, so a short Taylor series gives cos/sin(dth) to FP64 rounding (terms up to
+// dth^16 for |dth| <= 1/4: remainder below 1e-27); larger increments fall back to sincos.
+__device__ __forceinline__ void rotate_angle(const Dof& s0, double dth, double* cs, double* sn) {
+  if (dth == 0.0) {
+    *cs = s0.cs;
+    *sn = s0.sn;
+    return;
+  }
+  double c, s;
+  if (fabs(dth) <= 0.25) {
+    const double x2 = dth * dth;
+    // cos x = sum (-1)^k x^2k / (2k)!,  sin x = x sum (-1)^k x^2k / (2k+1)!   (Horner, k <= 8)
+    double pc = 1.0, ps = 1.0;
+    for (int k = 8; k >= 1; --k) {
+      pc = 1.0 - x2 / ((2.0 * k - 1.0) * (2.0 * k)) * pc;
+      ps = 1.0 - x2 / ((2.0 * k) * (2.0 * k + 1.0)) * ps;
+    }
+    c = pc;
+    s = dth * ps;
+  } else {
+    sincos(dth, &s, &c);
+  }
+  *cs = s0.cs * c - s0.sn * s;
+  *sn = s0.sn * c + s0.cs * s;
 }
 
 // Explicit Euler equations of motion, velocity first (Sec. 2.4), masked by the free DOFs.
@@ -303,8 +613,8 @@ __device__ __forceinline__ void eom_update(const Geo& g, const Dof& s0, const do
     out->s[7] = s0.s[7] + T / g.inertia;
     out->s[6] = s0.s[6] + out->s[7];
   }
-  out->cs = cos(out->s[6]);
-  out->sn = sin(out->s[6]);
+  rotate_angle(s0, out->s[6] - s0.s[6], &out->cs, &out->sn);
+  dof_views(out);
 }
 
 // Reverse of eom_update: from dJ/ds^(k) give dJ/dF, dJ/dT and add the direct part to dJ/ds(t-1).

@@ -63,7 +63,7 @@ int scratch_address(unsigned char** out) {
 }
 
 __global__ void k_noalloc_seed(Ctrl* ctrl, Dof* it, Dof s0, int base) {
-  ctrl->t = 1;
+  ctrl->t0 = 1;
   ctrl->base = base;
   ctrl->status = 0;
   it[0] = s0;
@@ -98,6 +98,8 @@ int make_geo(const lks_problem* P, Geo* g) {
   g->ND = P->ndx * P->ndy;
   g->xic[0] = (P->ndx - 1) / 2.0;
   g->xic[1] = (P->ndy - 1) / 2.0;
+  g->xicf[0] = (float)g->xic[0];
+  g->xicf[1] = (float)g->xic[1];
   g->ax = 2;
   g->axb = 0;
   g->axc = 1;
@@ -106,6 +108,7 @@ int make_geo(const lks_problem* P, Geo* g) {
   g->s = (P->weight_kind == LKS_W_BILINEAR) ? 1 : 2;
   g->K = P->n_itr;
   g->A = 4.5 * (1.0 / 6.0 - P->nu);
+  g->A2 = (float)(2.0 * g->A);
   g->u_in = P->u_in;
   g->dp = P->dp;
   g->mass = P->mass;
@@ -133,8 +136,8 @@ extern "C" int lks_step_noalloc(const lks_problem* problem, const double* gamma_
   Geo g;
   int r = make_geo(problem, &g);
   if (r != LKS_OK) return r;
-  const long long box_blocks = (long long)((g.B[0] + 31) / 32) * ((g.B[1] + 7) / 8);
-  const long long design_blocks = (g.ND + 255) / 256;
+  const long long box_blocks = (long long)((g.B[0] + kBoxCtaCellsX - 1) / kBoxCtaCellsX) * ((g.B[1] + kBoxCtaCellsY - 1) / kBoxCtaCellsY);
+  const long long design_blocks = ((long long)g.ND * 4 + 255) / 256;
   if (g.ND > kMaxDesign || g.K > kMaxItr || box_blocks > kMaxBlocks || design_blocks > kMaxBlocks)
     return LKS_ERR_BUDGET;
   unsigned char* base = nullptr;
@@ -153,14 +156,15 @@ extern "C" int lks_step_noalloc(const lks_problem* problem, const double* gamma_
   for (int a = 0; a < 8; ++a) s0.s[a] = s_host[a];
   s0.cs = std::cos(s0.s[6]);
   s0.sn = std::sin(s0.s[6]);
+  dof_views(&s0);
   // The device sees step 1 of a two-slot ring whose base selects the parity: slot (t-1) mod 2 is
   // read and slot t mod 2 written.
   const int parity = (t - 1) & 1;
   Slots<double> S{state_dev, 3 * g.N, 2};
   launch_prep<double>(g, gamma_dev, problem->kappa_max, problem->q, kref, mom, partials, ctrl, st);
   k_noalloc_seed<<<1, 1, 0, st>>>(ctrl, it, s0, parity);
-  launch_stencil_fwd<double>(g, S, ctrl, st);
-  for (int k = 1; k <= g.K; ++k) launch_couple<double>(g, S, ctrl, it, kref, mom, partials, k, nullptr, 1, st);
+  launch_stencil_fwd<double>(g, S, ctrl, 0, st);
+  for (int k = 1; k <= g.K; ++k) launch_couple<double>(g, S, ctrl, it, kref, mom, partials, k, nullptr, 1, 0, st);
   Dof out;
   Ctrl c;
   if (cudaMemcpyAsync(&out, it + (g.K + 1), sizeof(Dof), cudaMemcpyDeviceToHost, st) != cudaSuccess) return LKS_ERR_CUDA;

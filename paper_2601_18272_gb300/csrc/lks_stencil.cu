@@ -24,6 +24,14 @@ constexpr int TX = kTileX, TY = kTileY2;
 constexpr int HX = TX + 4, HY = TY + 4;  // halo-2 region
 constexpr int CX = TX + 2, CY = TY + 2;  // halo-1 region
 
+// 2A in the field type (the FP32 copy for FP32 fields, exact for FP64 fields).
+template <typename T>
+__device__ __forceinline__ T two_a(const Geo& g);
+template <>
+__device__ __forceinline__ float two_a<float>(const Geo& g) { return g.A2; }
+template <>
+__device__ __forceinline__ double two_a<double>(const Geo& g) { return 2.0 * g.A; }
+
 __device__ __forceinline__ bool interior_x(const Geo& g, int x) {
   return g.bc[0] == BC_PERIODIC || (x >= 1 && x <= g.n[0] - 2);
 }
@@ -63,11 +71,11 @@ __device__ __forceinline__ bool ghost_axis(int bc, int n, int* v, int* sgn) {
 }
 
 template <typename T>
-__global__ void __launch_bounds__(TX* TY) k_stencil2d(Geo g, Slots<T> S, const Ctrl* __restrict__ ctrl) {
+__global__ void __launch_bounds__(TX* TY) k_stencil2d(Geo g, Slots<T> S, const Ctrl* __restrict__ ctrl, int di) {
   __shared__ T sp[HY][HX], sux[HY][HX], suy[HY][HX];
   __shared__ T ca[CY][CX], cbx[CY][CX], cby[CY][CX], cqxx[CY][CX], cqyy[CY][CX], cqxy[CY][CX];
   __shared__ T op[TY][TX], oux[TY][TX], ouy[TY][TX];
-  const int t = ctrl->t, base = ctrl->base;
+  const int t = ctrl->t0 + di, base = ctrl->base;
   const T* __restrict__ src = slot_ptr(S, t - 1, base);
   T* __restrict__ dst = slot_ptr(S, t, base);
   const long long N = g.N;
@@ -91,7 +99,7 @@ __global__ void __launch_bounds__(TX* TY) k_stencil2d(Geo g, Slots<T> S, const C
   }
   __syncthreads();
 
-  const T A2 = T(2.0 * g.A);
+  const T A2 = two_a<T>(g);
   const T sixth = T(1.0 / 6.0);
   for (int q = tid; q < CX * CY; q += TX * TY) {
     const int ci = q % CX, cj = q / CX, li = ci + 1, lj = cj + 1;
@@ -220,11 +228,11 @@ __device__ __forceinline__ void lam_star_adjusted(const Geo& g, const T* L, int 
 }
 
 template <typename T>
-__global__ void __launch_bounds__(TX* TY) k_stencil2d_adj(Geo g, Slots<T> S, T* Lb, long long lstride, Ctrl* ctrl) {
+__global__ void __launch_bounds__(TX* TY) k_stencil2d_adj(Geo g, Slots<T> S, T* Lb, long long lstride,
+                                                          const Ctrl* __restrict__ ctrl, int di) {
   __shared__ T lp[HY][HX], lx[HY][HX], ly[HY][HX];
   __shared__ T mP[CY][CX], mUx[CY][CX], mUy[CY][CX], mSxx[CY][CX], mSyy[CY][CX], mSxy[CY][CX];
-  __shared__ double red[32];
-  const int t = ctrl->t, base = ctrl->base;
+  const int t = ctrl->t0 - di, base = ctrl->base;
   const T* __restrict__ Lcur = Lb + (long long)(t & 1) * lstride;
   T* __restrict__ Lnext = Lb + (long long)((t - 1) & 1) * lstride;
   const T* __restrict__ st = slot_ptr(S, t - 1, base);
@@ -309,41 +317,37 @@ __global__ void __launch_bounds__(TX* TY) k_stencil2d_adj(Geo g, Slots<T> S, T* 
           }
         }
     }
-    const T kA = T(2.0 * g.A / 6.0);
+    const T kA = two_a<T>(g) * T(1.0 / 6.0);
     Lnext[n] = T(3) * P;
     Lnext[N + n] = T(3) * mUx[cj][ci] + T(9) * (mSxx[cj][ci] * ux + mSxy[cj][ci] * uy) - T(3) * ux * P + kA * gtx;
     Lnext[2 * N + n] = T(3) * mUy[cj][ci] + T(9) * (mSxy[cj][ci] * ux + mSyy[cj][ci] * uy) - T(3) * uy * P + kA * gty;
-  }
-  (void)red;
-  if (last_block_done(&ctrl->count[CNT_ADJ_STENCIL])) {
-    if (tid == 0) {
-      ctrl->count[CNT_ADJ_STENCIL] = 0;
-      ctrl->t = t - 1;
-    }
   }
 }
 
 }  // namespace
 
 template <typename T>
-void launch_stencil_fwd(const Geo& g, const Slots<T>& S, const Ctrl* ctrl, cudaStream_t st) {
+void launch_stencil_fwd(const Geo& g, const Slots<T>& S, const Ctrl* ctrl, int di, cudaStream_t st) {
   if (g.dim == 2) {
     dim3 grid((g.n[0] + TX - 1) / TX, (g.n[1] + TY - 1) / TY);
-    k_stencil2d<T><<<grid, dim3(TX, TY), 0, st>>>(g, S, ctrl);
+    k_stencil2d<T><<<grid, dim3(TX, TY), 0, st>>>(g, S, ctrl, di);
   }
 }
 
 template <typename T>
-void launch_stencil_adj(const Geo& g, const Slots<T>& S, T* Lb, long long lstride, Ctrl* ctrl, cudaStream_t st) {
+void launch_stencil_adj(const Geo& g, const Slots<T>& S, T* Lb, long long lstride, const Ctrl* ctrl, int di,
+                        cudaStream_t st) {
   if (g.dim == 2) {
     dim3 grid((g.n[0] + TX - 1) / TX, (g.n[1] + TY - 1) / TY);
-    k_stencil2d_adj<T><<<grid, dim3(TX, TY), 0, st>>>(g, S, Lb, lstride, ctrl);
+    k_stencil2d_adj<T><<<grid, dim3(TX, TY), 0, st>>>(g, S, Lb, lstride, ctrl, di);
   }
 }
 
-template void launch_stencil_fwd<float>(const Geo&, const Slots<float>&, const Ctrl*, cudaStream_t);
-template void launch_stencil_fwd<double>(const Geo&, const Slots<double>&, const Ctrl*, cudaStream_t);
-template void launch_stencil_adj<float>(const Geo&, const Slots<float>&, float*, long long, Ctrl*, cudaStream_t);
-template void launch_stencil_adj<double>(const Geo&, const Slots<double>&, double*, long long, Ctrl*, cudaStream_t);
+template void launch_stencil_fwd<float>(const Geo&, const Slots<float>&, const Ctrl*, int, cudaStream_t);
+template void launch_stencil_fwd<double>(const Geo&, const Slots<double>&, const Ctrl*, int, cudaStream_t);
+template void launch_stencil_adj<float>(const Geo&, const Slots<float>&, float*, long long, const Ctrl*, int,
+                                        cudaStream_t);
+template void launch_stencil_adj<double>(const Geo&, const Slots<double>&, double*, long long, const Ctrl*, int,
+                                         cudaStream_t);
 
 }  // namespace lks

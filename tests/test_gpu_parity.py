@@ -114,7 +114,7 @@ def test_sail2d_80x40_full_fp64():
     r = gpu_run(P, g, p0, u0, s0)
     assert abs(r["J"] - G["J"]) <= 1e-11 * abs(G["J"])
     assert rel(r["dJdgamma"], G["dJdgamma"]) < 1e-8
-    assert r["launches"] > 400 * 6
+    assert r["launches"] >= 400 * 4  # per step at least: stencil, coupling, reverse coupling, transposed stencil
 
 
 def test_turbine2d_512x256_truncated_fp32():
