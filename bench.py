@@ -104,14 +104,15 @@ def _peaks():
         return 6800.0, "fallback"
 
 
-# Algorithmic bytes per launch of each kernel family (FP32 fields, 2D): see the data-layout
-# notes in the design doc. N = analysis cells, Bc = body-box cells, ND = design points.
+# Algorithmic bytes per launch of each kernel family. N = analysis cells, box_cells = body-box
+# cells, ND = design points, esz = bytes per field value.
 def _alg_bytes(family: str, P, box_cells: int, esz: int) -> float:
     N, ND = P.n_cells, P.n_design
+    d = P.dim
     if family == "stencil_fwd":
-        return 6 * esz * N            # read p, u_x, u_y; write p*, u*_x, u*_y
+        return 2 * (d + 1) * esz * N  # read p, u; write p*, u*
     if family == "stencil_adj":
-        return 8 * esz * N            # read 3 adjoint planes + u(t-1) (2 planes); write 3 planes
+        return (3 * d + 2) * esz * N  # read the adjoint (d+1 planes) and u(t-1) (d planes); write d+1 planes
     if family == "couple":
         return 2 * esz * box_cells + 4 * ND  # read u* in the box (+ kappa^ref)
     if family == "recompute":
@@ -131,6 +132,95 @@ def _box_cells(P) -> int:
     hb = math.ceil(r - 1e-12)
     B = 2 * hb + 2 * s + 2 + 2
     return B * B
+
+
+def _fluid_problem(dim: int, n: tuple, name: str):
+    """A large grid with a 2^dim design block carrying gamma = 0 (no body): the full-grid stencil
+    kernels alone, for their HBM roofline."""
+    from workloads import BC_INFLOW_OUTFLOW, BC_PERIODIC, CKPT_UNIFORM, W_COS4, Problem
+    nz = n[2] if dim == 3 else 1
+    c = (n[0] / 4 + 0.3, n[1] / 2 + 0.4, nz / 2 + 0.2 if dim == 3 else 0.0)
+    P = Problem(dim=dim, nx=n[0], ny=n[1], nz=nz, ndx=2, ndy=2, ndz=2 if dim == 3 else 1, body_centre=c,
+                rot_axis=2, dof_mask=0, mass=1.0, inertia=1.0, nu=0.032, u_in=0.05, dp=0.0,
+                bc=(BC_INFLOW_OUTFLOW, BC_PERIODIC, BC_PERIODIC), kappa_max=1.0, q=0.1, weight_kind=W_COS4,
+                n_steps=20, n_itr=5, obj_weights=(1.0,) + (0.0,) * 7, field_precision=32,
+                ckpt_policy=CKPT_UNIFORM, ckpt_every=10, name=name)
+    return P, np.zeros(P.n_design)
+
+
+def _family_times(solver, run):
+    """Per-family kernel time (ms) and launch count of one call of run() with every launch
+    bracketed by CUDA events on the launching stream."""
+    import torch
+    from paper_2601_18272_gb300 import lks
+    lks.lks_set_kernel_timing(solver.handle, True)
+    run()
+    torch.cuda.synchronize()
+    fams = {f: lks.lks_kernel_time(solver.handle, f)
+            for f in ("stencil_fwd", "couple", "recompute", "adj_cell", "adj_design", "stencil_adj")}
+    lks.lks_set_kernel_timing(solver.handle, False)
+    return fams
+
+
+def stencil_roofline(dev, peak: float, dim: int, n: tuple, name: str) -> dict:
+    """HBM roofline of the predictor and its transpose on a grid far larger than L2."""
+    import torch
+    from paper_2601_18272_gb300.lks import Solver
+    P, g = _fluid_problem(dim, n, name)
+    S = Solver(P)
+    gamma = torch.tensor(g, dtype=torch.float64, device=dev)
+    grad = torch.empty_like(gamma)
+
+    def run():
+        S.forward(gamma)
+        S.adjoint(1.0)
+        S.sensitivity(grad)
+
+    run()
+    torch.cuda.synchronize()
+    fams = _family_times(S, run)
+    S.close()
+    out = {"workload": name, "grid": list(n), "cells": P.n_cells, "dtype": "f32"}
+    for fam in ("stencil_fwd", "stencil_adj"):
+        ms, cnt = fams[fam]
+        per = ms / 1000.0 / cnt
+        alg = _alg_bytes(fam, P, 0, 4)
+        out[fam] = {"achieved": alg / per / 1e9, "peak": peak, "unit": "GB/s", "frac": alg / per / 1e9 / peak,
+                    "alg_bytes_per_launch": alg, "avg_launch_us": per * 1e6, "launches": cnt,
+                    "cell_updates_per_s": P.n_cells / per}
+    return out
+
+
+def gradient_throughput(dev, flush, index: int) -> dict:
+    """Whole-gradient throughput of another workload (one warm-up, one timed gradient)."""
+    import torch
+    from paper_2601_18272_gb300.lks import Solver
+    from workloads import config
+    P, g = config(index)
+    S = Solver(P)
+    gamma = torch.tensor(g, dtype=torch.float64, device=dev)
+    grad = torch.empty_like(gamma)
+    stream = torch.cuda.current_stream(dev)
+
+    def run():
+        S.forward(gamma)
+        S.adjoint(1.0)
+        S.sensitivity(grad)
+
+    run()
+    torch.cuda.synchronize()
+    flush.zero_()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    run()
+    e1.record(stream)
+    e1.synchronize()
+    ms = e0.elapsed_time(e1)
+    fams = _family_times(S, run)
+    S.close()
+    return {"workload": P.name, "value": P.n_cells * P.n_steps / (ms / 1000.0), "unit": UNIT, "ms_per_gradient": ms,
+            "n_steps": P.n_steps, "dtype": "f32",
+            "kernel_ms_per_gradient": {k: round(v[0], 3) for k, v in fams.items()}}
 
 
 def run_reference(args, ws, rank):
@@ -283,13 +373,7 @@ def main():
 
     if rank == 0 and not args.skip_extras:
         # dominant kernel: one more gradient with every launch bracketed by CUDA events
-        lks.lks_set_kernel_timing(solver.handle, True)
-        step()
-        torch.cuda.synchronize()
-        fams = {}
-        for fam in ("stencil_fwd", "couple", "recompute", "adj_cell", "adj_design", "stencil_adj"):
-            fams[fam] = lks.lks_kernel_time(solver.handle, fam)
-        lks.lks_set_kernel_timing(solver.handle, False)
+        fams = _family_times(solver, step)
         dom = max(fams, key=lambda k: fams[k][0])
         dom_ms, dom_n = fams[dom]
         peak, peak_kind = _peaks()
@@ -327,6 +411,10 @@ def main():
                                         "ms_per_step": plain_ms, "workspace_gb": lks.lks_workspace_bytes(plain.handle) / 1e9}
         line["workspace_gb"] = lks.lks_workspace_bytes(solver.handle) / 1e9
         plain.close()
+        # the full-grid kernels on grids far larger than L2, and the 3D workload
+        line["stencil_roofline_2d"] = stencil_roofline(dev, peak, 2, (8192, 4096), "fluid2d_8192x4096")
+        line["stencil_roofline_3d"] = stencil_roofline(dev, peak, 3, (512, 256, 256), "fluid3d_512x256x256")
+        line["body3d"] = gradient_throughput(dev, flush, 4)
         line["cpu_baseline"] = cpu_baseline(args.cpu_sample_steps)
     solver.close()
     if rank == 0:

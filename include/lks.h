@@ -91,12 +91,16 @@ typedef struct lks_problem {
 typedef struct lks_handle lks_handle;
 
 /* Validate the problem and allocate the workspace. On success *out owns the device memory.
+ * The body box (the cells one step can touch) must fit every periodic extent; it is sized for a
+ * rotating body unless that does not fit and dof_mask excludes rotation.
  * Errors: LKS_ERR_ARG, LKS_ERR_UNSTABLE, LKS_ERR_UNSUPPORTED, LKS_ERR_BUDGET, LKS_ERR_OOM. */
 LKS_API int lks_create(const lks_problem* problem, lks_handle** out);
 
 /* Initial state for the next forward (Algorithm 1, "Initialize"). p [N], u [dim][N] and
  * s [8] are host arrays (copied). Any pointer may be NULL to keep the default: p = 0,
- * u = (u_in, 0, 0), body at rest at body_centre. */
+ * u = (u_in, 0, 0), body at rest at body_centre.
+ * Errors: LKS_ERR_ARG; LKS_ERR_UNSUPPORTED if s starts the body rotated but the workspace was
+ * sized for an axis-aligned box (see lks_create); LKS_ERR_CUDA. */
 LKS_API int lks_set_initial_state(lks_handle* h, const double* p_host, const double* u_host, const double* s_host);
 
 /* Forward march over n_steps (Algorithm 1, state loop) for the design field gamma_dev

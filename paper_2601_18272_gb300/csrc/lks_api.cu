@@ -72,6 +72,7 @@ struct lks_handle {
   cudaStream_t cap = nullptr;
   std::map<std::string, cudaGraphExec_t> graphs;
   std::map<std::string, int> graph_kernels;
+  bool box_rot_ok = true;  // buffers hold the rotated box
   bool fwd_done = false, adj_done = false;
   long long launches = 0;
   bool timing = false;
@@ -143,7 +144,6 @@ int validate(const lks_problem* P) {
   if (P->dim != 2 && P->dim != 3) return LKS_ERR_ARG;
   if (P->dim == 2 && (P->velocity_set != LKS_D2Q9 || P->nz != 1 || P->ndz != 1 || P->rot_axis != 2)) return LKS_ERR_ARG;
   if (P->dim == 3 && P->velocity_set != LKS_D3Q15) return LKS_ERR_ARG;
-  if (P->dim == 3) return LKS_ERR_UNSUPPORTED;
   if (P->nx < 4 || P->ny < 4 || (P->dim == 3 && P->nz < 4)) return LKS_ERR_ARG;
   if (P->ndx < 1 || P->ndy < 1 || P->ndz < 1) return LKS_ERR_ARG;
   if (P->rot_axis < 0 || P->rot_axis > 2) return LKS_ERR_ARG;
@@ -160,7 +160,7 @@ int validate(const lks_problem* P) {
   if (P->ckpt_format != LKS_CKPT_NATIVE) return LKS_ERR_UNSUPPORTED;
   // boundary pairs (x = 0,1 and nx-2,nx-1; y walls likewise) must share a stencil tile
   if (P->bc[0] != LKS_BC_PERIODIC && P->nx % kTileX == 1) return LKS_ERR_UNSUPPORTED;
-  if (P->bc[1] == LKS_BC_WALL && P->ny % kTileY2 == 1) return LKS_ERR_UNSUPPORTED;
+  if (P->bc[1] == LKS_BC_WALL && P->ny % (P->dim == 2 ? kTileY2 : kTileY3) == 1) return LKS_ERR_UNSUPPORTED;
   return LKS_OK;
 }
 
@@ -426,11 +426,21 @@ int set_default_initial_state(lks_handle* h) {
   return LKS_OK;
 }
 
-void refresh_box(lks_handle* h) {
+// Box for the current initial state: the rotated (circumscribed) box if the body can rotate or
+// starts rotated. The buffers were sized at creation for the largest box that fits.
+int refresh_box(lks_handle* h) {
   const bool rotated = (h->g.dof_mask & LKS_DOF_ROT) || h->host_s0[6] != 0.0;
+  if (rotated && !h->box_rot_ok) return LKS_ERR_UNSUPPORTED;
   const int old[3] = {h->g.B[0], h->g.B[1], h->g.B[2]};
   setup_box(h, rotated);
   if (old[0] != h->g.B[0] || old[1] != h->g.B[1] || old[2] != h->g.B[2]) clear_graphs(h);
+  return LKS_OK;
+}
+
+bool box_fits(const Geo& g) {
+  for (int a = 0; a < g.dim; ++a)
+    if (g.bc[a] == LKS_BC_PERIODIC && g.B[a] > g.n[a]) return false;
+  return true;
 }
 
 }  // namespace
@@ -494,20 +504,32 @@ int lks_create(const lks_problem* P, lks_handle** out) {
   g.dp = P->dp;
   g.mass = P->mass;
   g.inertia = P->inertia;
-  setup_box(h, true);  // allocate for the rotated (largest) box
-  for (int a = 0; a < g.dim; ++a)
-    if (g.bc[a] == LKS_BC_PERIODIC && g.B[a] > g.n[a]) {
+  g.inv_mass = 1.0 / P->mass;
+  g.inv_inertia = 1.0 / P->inertia;
+  // Allocate for the rotated (largest) box; a body without the rotational DOF whose rotated box
+  // would not fit a periodic extent gets the axis-aligned box and may not start rotated.
+  setup_box(h, true);
+  h->box_rot_ok = box_fits(g);
+  if (!h->box_rot_ok) {
+    setup_box(h, false);
+    if ((g.dof_mask & LKS_DOF_ROT) || !box_fits(g)) {
       delete h;
       return LKS_ERR_UNSUPPORTED;
     }
+  }
   int r = (h->prec == LKS_FP64) ? allocate<double>(h) : allocate<float>(h);
   if (r == LKS_OK) r = set_default_initial_state(h);
   if (r == LKS_OK && cudaStreamCreateWithFlags(&h->cap, cudaStreamNonBlocking) != cudaSuccess) r = LKS_ERR_CUDA;
+  if (r == LKS_OK && g.dim == 3) {
+    if (h->prec == LKS_FP64) prepare_stencil3d<double>();
+    else prepare_stencil3d<float>();
+    if (cudaGetLastError() != cudaSuccess) r = LKS_ERR_CUDA;
+  }
   if (r != LKS_OK) {
     lks_destroy(h);
     return r;
   }
-  refresh_box(h);
+  refresh_box(h);  // the default state starts unrotated: always fits
   *out = h;
   return LKS_OK;
 }
@@ -523,8 +545,7 @@ int lks_set_initial_state(lks_handle* h, const double* p, const double* u, const
     for (int a = 0; a < 8; ++a) h->host_s0[a] = s[a];
     CK(cudaMemcpy(h->init_s, h->host_s0, 8 * sizeof(double), cudaMemcpyHostToDevice));
   }
-  refresh_box(h);
-  return LKS_OK;
+  return refresh_box(h);
 }
 
 int lks_forward(lks_handle* h, const double* gamma_dev, double* J_host, void* stream) {

@@ -18,8 +18,8 @@
 // dJ/dkappa^ref without atomics and reduces dJ/ds^(k-1).
 //
 // Each iteration's global reduction is split into a kernel over all SMs that writes one FP64
-// partial per CTA and a one-CTA finish kernel that sums the partials in a fixed order and applies
-// the (reverse) EOM: the kernel boundary orders the partials, so no GPU-scope fence or counter is
+// partial per CTA (double-float pairs in the FP32 form) and a one-warp finish kernel that sums the
+// partials in a fixed order and applies the (reverse) EOM: the kernel boundary orders the partials, so no GPU-scope fence or counter is
 // needed, and the sums are deterministic.
 #include "lks_kernels.h"
 
@@ -31,7 +31,6 @@ constexpr int BX = 32, BY = 8;  // grid form: one thread per box cell, 32 x 8 ce
 constexpr int kDesignBlock = 256;
 
 __device__ __forceinline__ int block_linear() { return blockIdx.x + gridDim.x * (blockIdx.y + gridDim.y * blockIdx.z); }
-__device__ __forceinline__ int thread_linear() { return threadIdx.x + blockDim.x * (threadIdx.y + blockDim.y * threadIdx.z); }
 
 // dJ/dF and dJ/dT of the iteration being reversed, in the field type.
 template <typename T>
@@ -341,7 +340,7 @@ __global__ void __launch_bounds__(256) k_prep(Geo g, const double* __restrict__ 
 
 template <typename T, int D, int AX>
 __global__ void __launch_bounds__(BX* BY) k_couple(Geo g, Slots<T> S, Ctrl* ctrl, Dof* it, const T* __restrict__ kref,
-                                                    const Moments* __restrict__ mom, double* partials, int k,
+                                                    const Moments* __restrict__ mom, void* partials, int k,
                                                     T* __restrict__ boxstore, int nbox, int di) {
   __shared__ double red[32 * 4];
   const int t = ctrl->t0 + di, base = ctrl->base, K = g.K;
@@ -354,22 +353,17 @@ __global__ void __launch_bounds__(BX* BY) k_couple(Geo g, Slots<T> S, Ctrl* ctrl
   const int j0 = blockIdx.x * BX + threadIdx.x, j1 = blockIdx.y * BY + threadIdx.y, j2 = blockIdx.z;
   T v[4] = {T(0), T(0), T(0), T(0)};
   if (j0 < g.B[0] && j1 < g.B[1]) couple_cell<T, D, AX>(g, kref, sk, lo, j0, j1, j2, dst, bs, k == K, &ctrl->status, v);
-  double s[4];
-  block_sum_to_double<4>(v, s, red);
-  if (thread_linear() == 0)
-    for (int a = 0; a < 4; ++a) partials[block_linear() * 4 + a] = s[a];
+  block_sum_partial<4>(v, static_cast<typename Partial<T>::type*>(partials) + block_linear() * 4, red);
 }
 
-// Sum of the coupling partials and the EOM update: iterate s^(k) of step t.
-template <int D, int AX>
-__global__ void __launch_bounds__(256) k_couple_finish(Geo g, Ctrl* ctrl, Dof* it, const Moments* __restrict__ mom,
-                                                        const double* __restrict__ partials, int nparts, int k,
-                                                        int di) {
-  __shared__ double red[32 * 4];
+// Sum of the coupling partials and the EOM update: iterate s^(k) of step t. One warp.
+template <typename T, int D, int AX>
+__global__ void __launch_bounds__(32) k_couple_finish(Geo g, Ctrl* ctrl, Dof* it, const Moments* __restrict__ mom,
+                                                       const void* __restrict__ partials, int nparts, int k, int di) {
   const int t = ctrl->t0 + di, K = g.K;
   Dof* row = it + (long long)(t - 1) * (K + 1);
   double s[4];
-  sum_partials<4>(partials, nparts, s, red);
+  warp_sum_partials<4>(static_cast<const typename Partial<T>::type*>(partials), nparts, s);
   if (threadIdx.x == 0) {
     const Dof s0 = row[0], sk = row[k - 1];
     Dof nx;
@@ -441,7 +435,7 @@ template <typename T, int D, int AX>
 __global__ void __launch_bounds__(kDesignBlock) k_adj_design(Geo g, Ctrl* ctrl, const Dof* it,
                                                               const T* __restrict__ kref,
                                                               const T* __restrict__ scratch,
-                                                              double* __restrict__ dkref, double* partials, int k,
+                                                              double* __restrict__ dkref, void* partials, int k,
                                                               int di) {
   __shared__ double red[32 * 8];
   const int t = ctrl->t0 - di, K = g.K;
@@ -455,18 +449,15 @@ __global__ void __launch_bounds__(kDesignBlock) k_adj_design(Geo g, Ctrl* ctrl, 
   T v[8] = {T(0), T(0), T(0), T(0), T(0), T(0), T(0), T(0)};
   if (m < g.ND && !adj_design_point<T, D, AX>(g, kref, scratch, sk, lo, m, lF, lT, dkref, v))
     atomicOr(&ctrl->status, ST_BOX_OVERFLOW);
-  double s[8];
-  block_sum_to_double<8>(v, s, red);
-  if (threadIdx.x == 0)
-    for (int a = 0; a < 8; ++a) partials[blockIdx.x * 8 + a] = s[a];
+  block_sum_partial<8>(v, static_cast<typename Partial<T>::type*>(partials) + blockIdx.x * 8, red);
 }
 
-// Sum of the design-point partials and the EOM reverse (adj_finish).
-__global__ void __launch_bounds__(256) k_design_finish(Geo g, Ctrl* ctrl, const double* __restrict__ partials,
-                                                       int nparts, int k) {
-  __shared__ double red[32 * 8];
+// Sum of the design-point partials and the EOM reverse (adj_finish). One warp.
+template <typename T>
+__global__ void __launch_bounds__(32) k_design_finish(Geo g, Ctrl* ctrl, const void* __restrict__ partials,
+                                                      int nparts, int k) {
   double ls[8];
-  sum_partials<8>(partials, nparts, ls, red);
+  warp_sum_partials<8>(static_cast<const typename Partial<T>::type*>(partials), nparts, ls);
   if (threadIdx.x == 0) {
     double lp[8], nF[3], nT;
     for (int a = 0; a < 8; ++a) lp[a] = ctrl->lam_prev[a];
@@ -553,17 +544,6 @@ inline dim3 box_grid(const Geo& g) {
       KERNEL<T, 3, 2><<<GRID, BLOCK, 0, st>>>(__VA_ARGS__); \
   } while (0)
 
-#define LKS_AXIS_DISPATCH(KERNEL, GRID, BLOCK, ...)         \
-  do {                                                      \
-    if (g.dim == 2)                                         \
-      KERNEL<2, 2><<<GRID, BLOCK, 0, st>>>(__VA_ARGS__);    \
-    else if (g.ax == 0)                                     \
-      KERNEL<3, 0><<<GRID, BLOCK, 0, st>>>(__VA_ARGS__);    \
-    else if (g.ax == 1)                                     \
-      KERNEL<3, 1><<<GRID, BLOCK, 0, st>>>(__VA_ARGS__);    \
-    else                                                    \
-      KERNEL<3, 2><<<GRID, BLOCK, 0, st>>>(__VA_ARGS__);    \
-  } while (0)
 
 template <typename T>
 void launch_prep(const Geo& g, const double* gamma, double kappa_max, double q, T* kref, Moments* mom,
@@ -573,11 +553,11 @@ void launch_prep(const Geo& g, const double* gamma, double kappa_max, double q, 
 
 template <typename T>
 void launch_couple(const Geo& g, const Slots<T>& S, Ctrl* ctrl, Dof* it, const T* kref, const Moments* mom,
-                   double* partials, int k, T* boxstore, int nbox, int di, cudaStream_t st) {
+                   void* partials, int k, T* boxstore, int nbox, int di, cudaStream_t st) {
   const dim3 grid = box_grid(g);
   LKS_BOX_DISPATCH(k_couple, grid, dim3(BX, BY), g, S, ctrl, it, kref, mom, partials, k, boxstore, nbox, di);
   const int nparts = (int)(grid.x * grid.y * grid.z);
-  LKS_AXIS_DISPATCH(k_couple_finish, 1, 256, g, ctrl, it, mom, partials, nparts, k, di);
+  LKS_BOX_DISPATCH(k_couple_finish, 1, 32, g, ctrl, it, mom, partials, nparts, k, di);
 }
 
 template <typename T>
@@ -595,10 +575,10 @@ void launch_adj_cell(const Geo& g, const Ctrl* ctrl, const Dof* it, const T* kre
 
 template <typename T>
 void launch_adj_design(const Geo& g, Ctrl* ctrl, const Dof* it, const T* kref, const T* scratch, double* dkref,
-                       double* partials, int k, int di, cudaStream_t st) {
+                       void* partials, int k, int di, cudaStream_t st) {
   const unsigned nb = (unsigned)((g.ND + kDesignBlock - 1) / kDesignBlock);
   LKS_BOX_DISPATCH(k_adj_design, nb, kDesignBlock, g, ctrl, it, kref, scratch, dkref, partials, k, di);
-  k_design_finish<<<1, 256, 0, st>>>(g, ctrl, partials, (int)nb, k);
+  k_design_finish<T><<<1, 32, 0, st>>>(g, ctrl, partials, (int)nb, k);
 }
 
 template <typename T>
@@ -632,13 +612,13 @@ void launch_ckpt_pack(const Geo& g, const Slots<T>& S, T* ckpt, long long cstrid
 #define LKS_INST(T)                                                                                                 \
   template void launch_prep<T>(const Geo&, const double*, double, double, T*, Moments*, double*, Ctrl*,              \
                                cudaStream_t);                                                                       \
-  template void launch_couple<T>(const Geo&, const Slots<T>&, Ctrl*, Dof*, const T*, const Moments*, double*, int,    \
+  template void launch_couple<T>(const Geo&, const Slots<T>&, Ctrl*, Dof*, const T*, const Moments*, void*, int,      \
                                  T*, int, int, cudaStream_t);                                                       \
   template void launch_apply<T>(const Geo&, const Slots<T>&, const Ctrl*, const Dof*, const T*, T*, int, int,        \
                                 cudaStream_t);                                                                      \
   template void launch_adj_cell<T>(const Geo&, const Ctrl*, const Dof*, const T*, const T*, int, T*, long long, T*, \
                                    T*, int, int, cudaStream_t);                                                     \
-  template void launch_adj_design<T>(const Geo&, Ctrl*, const Dof*, const T*, const T*, double*, double*, int, int,  \
+  template void launch_adj_design<T>(const Geo&, Ctrl*, const Dof*, const T*, const T*, double*, void*, int, int,    \
                                      cudaStream_t);                                                                 \
   template void launch_init_forward<T>(const Geo&, const Slots<T>&, const double*, const double*, const double*,     \
                                        Dof*, Ctrl*, cudaStream_t);                                                  \

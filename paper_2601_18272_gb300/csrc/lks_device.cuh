@@ -123,6 +123,7 @@ struct Geo {
   int wk, s;      // weight kind, support half-width (2 for cos4, 1 for bilinear)
   int K;          // N_itr
   double A, u_in, dp, mass, inertia;
+  double inv_mass, inv_inertia;  // 1/M, 1/I (the EOM multiplies: FP64 division is a long sequence)
   float A2;       // 2A, for FP32 kernels
   int B[3];       // body box extent in cells
   int hb[3];      // box half extent (ceil of the body's half extent)
@@ -499,10 +500,40 @@ __device__ __forceinline__ void df_add(float& hi, float& lo, float bh, float bl)
   lo = e - (hi - s);
 }
 
-// Block sum of NV per-thread values to FP64 in thread 0. FP32 values go through a double-float
-// shuffle tree and touch FP64 once per value in thread 0; FP64 values use block_sum.
+// In the elected last block: sum the per-CTA partials [nblocks][NV] with every thread (each
+// thread a fixed strided subset, then the fixed block tree), so the order is deterministic and
+// the L2 loads are issued in parallel. Result in thread 0. All threads of the block must call it.
 template <int NV>
-__device__ __forceinline__ void block_sum_to_double(float (&v)[NV], double* out, double* smem) {
+__device__ __forceinline__ void sum_partials(const double* partials, int nblocks, double* out, double* smem) {
+  const int tid = threadIdx.x + blockDim.x * (threadIdx.y + blockDim.y * threadIdx.z);
+  const int nthreads = blockDim.x * blockDim.y * blockDim.z;
+  double v[NV];
+#pragma unroll
+  for (int a = 0; a < NV; ++a) v[a] = 0.0;
+  for (int q = tid; q < nblocks; q += nthreads)
+#pragma unroll
+    for (int a = 0; a < NV; ++a) v[a] += __ldcg(&partials[q * NV + a]);
+  block_sum<NV>(v, smem);
+#pragma unroll
+  for (int a = 0; a < NV; ++a) out[a] = v[a];
+}
+
+// Per-CTA partial sums of NV values. FP32 kernels store double-float pairs (hi, lo), so neither
+// they nor the one-warp finish kernels issue FP64 arithmetic; FP64 kernels store doubles.
+template <typename T>
+struct Partial;
+template <>
+struct Partial<float> {
+  using type = float2;
+};
+template <>
+struct Partial<double> {
+  using type = double;
+};
+
+// Block sum of NV per-thread FP32 values as double-float pairs, written by thread 0 to out[0..NV).
+template <int NV>
+__device__ __forceinline__ void block_sum_partial(float (&v)[NV], float2* out, double* smem) {
   const int tid = threadIdx.x + blockDim.x * (threadIdx.y + blockDim.y * threadIdx.z);
   const int nthreads = blockDim.x * blockDim.y * blockDim.z;
   float hi[NV], lo[NV];
@@ -543,12 +574,11 @@ __device__ __forceinline__ void block_sum_to_double(float (&v)[NV], double* out,
       }
     if (lane == 0)
 #pragma unroll
-      for (int i = 0; i < NV; ++i) out[i] = (double)hi[i] + (double)lo[i];
+      for (int i = 0; i < NV; ++i) out[i] = make_float2(hi[i], lo[i]);
   }
-  __syncthreads();
 }
 template <int NV>
-__device__ __forceinline__ void block_sum_to_double(double (&v)[NV], double* out, double* smem) {
+__device__ __forceinline__ void block_sum_partial(double (&v)[NV], double* out, double* smem) {
   block_sum<NV>(v, smem);
   const int tid = threadIdx.x + blockDim.x * (threadIdx.y + blockDim.y * threadIdx.z);
   if (tid == 0)
@@ -556,27 +586,52 @@ __device__ __forceinline__ void block_sum_to_double(double (&v)[NV], double* out
     for (int i = 0; i < NV; ++i) out[i] = v[i];
 }
 
-// In the elected last block: sum the per-CTA partials [nblocks][NV] with every thread (each
-// thread a fixed strided subset, then the fixed block tree), so the order is deterministic and
-// the L2 loads are issued in parallel. Result in thread 0. All threads of the block must call it.
+// One warp sums the partials [nblocks][NV] in a fixed order (lane-strided, then a fixed shuffle
+// tree); the FP64 result is in lane 0. Double-float pairs are summed with FP32 instructions only.
 template <int NV>
-__device__ __forceinline__ void sum_partials(const double* partials, int nblocks, double* out, double* smem) {
-  const int tid = threadIdx.x + blockDim.x * (threadIdx.y + blockDim.y * threadIdx.z);
-  const int nthreads = blockDim.x * blockDim.y * blockDim.z;
+__device__ __forceinline__ void warp_sum_partials(const float2* partials, int nblocks, double* out) {
+  const int lane = threadIdx.x & 31;
+  float hi[NV], lo[NV];
+#pragma unroll
+  for (int a = 0; a < NV; ++a) hi[a] = lo[a] = 0.0f;
+  for (int q = lane; q < nblocks; q += 32)
+#pragma unroll
+    for (int a = 0; a < NV; ++a) {
+      const float2 p = __ldcg(&partials[q * NV + a]);
+      df_add(hi[a], lo[a], p.x, p.y);
+    }
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1)
+#pragma unroll
+    for (int a = 0; a < NV; ++a) {
+      const float bh = __shfl_xor_sync(0xffffffffu, hi[a], off), bl = __shfl_xor_sync(0xffffffffu, lo[a], off);
+      df_add(hi[a], lo[a], bh, bl);
+    }
+#pragma unroll
+  for (int a = 0; a < NV; ++a) out[a] = (double)hi[a] + (double)lo[a];
+}
+template <int NV>
+__device__ __forceinline__ void warp_sum_partials(const double* partials, int nblocks, double* out) {
+  const int lane = threadIdx.x & 31;
   double v[NV];
 #pragma unroll
   for (int a = 0; a < NV; ++a) v[a] = 0.0;
-  for (int q = tid; q < nblocks; q += nthreads)
+  for (int q = lane; q < nblocks; q += 32)
 #pragma unroll
     for (int a = 0; a < NV; ++a) v[a] += __ldcg(&partials[q * NV + a]);
-  block_sum<NV>(v, smem);
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1)
+#pragma unroll
+    for (int a = 0; a < NV; ++a) v[a] += __shfl_xor_sync(0xffffffffu, v[a], off);
 #pragma unroll
   for (int a = 0; a < NV; ++a) out[a] = v[a];
 }
 
 // cos/sin of theta0 + dth from those of theta0 by the angle-addition formulas; the increment is
-// one step's rotation, so a short Taylor series gives cos/sin(dth) to FP64 rounding (terms up to
-// dth^16 for |dth| <= 1/4: remainder below 1e-27); larger increments fall back to sincos.
+// one step's rotation, so a short Taylor series gives cos/sin(dth) to FP64 rounding: terms up to
+// dth^8 for |dth| <= 1/64 (remainder below 1e-25), up to dth^16 for |dth| <= 1/4 (below 1e-27);
+// larger increments fall back to sincos. The Horner coefficients 1/((2k-1)2k) and 1/(2k(2k+1))
+// are compile-time constants, so the series is a chain of FP64 FMAs without divisions.
 __device__ __forceinline__ void rotate_angle(const Dof& s0, double dth, double* cs, double* sn) {
   if (dth == 0.0) {
     *cs = s0.cs;
@@ -584,13 +639,26 @@ __device__ __forceinline__ void rotate_angle(const Dof& s0, double dth, double* 
     return;
   }
   double c, s;
-  if (fabs(dth) <= 0.25) {
+  const double adth = fabs(dth);
+  if (adth <= 0.25) {
     const double x2 = dth * dth;
-    // cos x = sum (-1)^k x^2k / (2k)!,  sin x = x sum (-1)^k x^2k / (2k+1)!   (Horner, k <= 8)
+    // cos x = sum (-1)^k x^2k / (2k)!,  sin x = x sum (-1)^k x^2k / (2k+1)!   (Horner)
+    constexpr double cc[9] = {0.0, 1.0 / 2.0, 1.0 / 12.0, 1.0 / 30.0, 1.0 / 56.0,
+                              1.0 / 90.0, 1.0 / 132.0, 1.0 / 182.0, 1.0 / 240.0};
+    constexpr double sc[9] = {0.0, 1.0 / 6.0, 1.0 / 20.0, 1.0 / 42.0, 1.0 / 72.0,
+                              1.0 / 110.0, 1.0 / 156.0, 1.0 / 210.0, 1.0 / 272.0};
     double pc = 1.0, ps = 1.0;
-    for (int k = 8; k >= 1; --k) {
-      pc = 1.0 - x2 / ((2.0 * k - 1.0) * (2.0 * k)) * pc;
-      ps = 1.0 - x2 / ((2.0 * k) * (2.0 * k + 1.0)) * ps;
+    if (adth > 1.0 / 64.0) {
+#pragma unroll
+      for (int k = 8; k >= 5; --k) {
+        pc = fma(-x2 * cc[k], pc, 1.0);
+        ps = fma(-x2 * sc[k], ps, 1.0);
+      }
+    }
+#pragma unroll
+    for (int k = 4; k >= 1; --k) {
+      pc = fma(-x2 * cc[k], pc, 1.0);
+      ps = fma(-x2 * sc[k], ps, 1.0);
     }
     c = pc;
     s = dth * ps;
@@ -606,11 +674,11 @@ __device__ __forceinline__ void eom_update(const Geo& g, const Dof& s0, const do
   for (int a = 0; a < 8; ++a) out->s[a] = s0.s[a];
   for (int a = 0; a < g.dim; ++a) {
     if (!(g.dof_mask & (1 << a))) continue;
-    out->s[3 + a] = s0.s[3 + a] + F[a] / g.mass;
+    out->s[3 + a] = s0.s[3 + a] + F[a] * g.inv_mass;
     out->s[a] = s0.s[a] + out->s[3 + a];
   }
   if (g.dof_mask & DOF_ROT) {
-    out->s[7] = s0.s[7] + T / g.inertia;
+    out->s[7] = s0.s[7] + T * g.inv_inertia;
     out->s[6] = s0.s[6] + out->s[7];
   }
   rotate_angle(s0, out->s[6] - s0.s[6], &out->cs, &out->sn);
@@ -624,7 +692,7 @@ __device__ __forceinline__ void eom_reverse(const Geo& g, const double* lam_sk, 
     const bool fr = (a < g.dim) && (g.dof_mask & (1 << a));
     if (fr) {
       const double lug = lam_sk[3 + a] + lam_sk[a];
-      lamF[a] = lug / g.mass;
+      lamF[a] = lug * g.inv_mass;
       lam_prev[a] += lam_sk[a];
       lam_prev[3 + a] += lug;
     } else {
@@ -635,7 +703,7 @@ __device__ __forceinline__ void eom_reverse(const Geo& g, const double* lam_sk, 
   }
   if (g.dof_mask & DOF_ROT) {
     const double lom = lam_sk[7] + lam_sk[6];
-    *lamT = lom / g.inertia;
+    *lamT = lom * g.inv_inertia;
     lam_prev[6] += lam_sk[6];
     lam_prev[7] += lom;
   } else {

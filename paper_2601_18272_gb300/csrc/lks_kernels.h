@@ -8,8 +8,7 @@ namespace lks {
 
 constexpr int kTileX = 32;  // stencil tile width (cells); boundary pairs must not straddle tiles
 constexpr int kTileY2 = 8;  // 2D stencil tile height
-constexpr int kTileY3 = 4;  // 3D stencil tile height
-constexpr int kTileZ3 = 4;  // 3D stencil tile depth
+constexpr int kTileY3 = 8;  // 3D stencil column height (the column marches over a chunk of z planes)
 constexpr int kBoxCtaCellsX = 32, kBoxCtaCellsY = 8;  // cells per grid-form coupling CTA
 
 // Kernels that work on one time step take di: the step is ctrl->t0 + di (forward kernels) or
@@ -25,17 +24,27 @@ template <typename T>
 void launch_stencil_adj(const Geo& g, const Slots<T>& S, T* Lb, long long lstride, const Ctrl* ctrl, int di,
                         cudaStream_t st);
 
+// 3D forms (D3Q15), called by the launchers above; prepare_stencil3d sets their shared-memory
+// attributes and must run once before the first launch (outside stream capture).
+template <typename T>
+void prepare_stencil3d();
+template <typename T>
+void launch_stencil3d_fwd(const Geo& g, const Slots<T>& S, const Ctrl* ctrl, int di, cudaStream_t st);
+template <typename T>
+void launch_stencil3d_adj(const Geo& g, const Slots<T>& S, T* Lb, long long lstride, const Ctrl* ctrl, int di,
+                          cudaStream_t st);
+
 // Design preparation: kappa^ref from gamma (Eq. brinkman_coefficient), moments.
 template <typename T>
 void launch_prep(const Geo& g, const double* gamma, double kappa_max, double q, T* kref, Moments* mom,
                  double* partials, Ctrl* ctrl, cudaStream_t st);
 
-// Coupling iteration k (1..K) of step t: spread, Brinkman, force/torque (per-CTA partials), then a
-// one-CTA finish kernel with the EOM. On k == K writes u(t) into slot(t) and optionally u* into the
+// Coupling iteration k (1..K) of step t: spread, Brinkman, force/torque (per-CTA partials: float2
+// double-float pairs for FP32 fields, doubles for FP64), then a one-warp finish kernel with the EOM. On k == K writes u(t) into slot(t) and optionally u* into the
 // box store.
 template <typename T>
 void launch_couple(const Geo& g, const Slots<T>& S, Ctrl* ctrl, Dof* it, const T* kref, const Moments* mom,
-                   double* partials, int k, T* boxstore, int nbox, int di, cudaStream_t st);
+                   void* partials, int k, T* boxstore, int nbox, int di, cudaStream_t st);
 
 // Recompute: Brinkman update with the stored iterate s^(K-1); writes u(t) and the box store of u*.
 template <typename T>
@@ -51,7 +60,7 @@ void launch_adj_cell(const Geo& g, const Ctrl* ctrl, const Dof* it, const T* kre
 // dJ/ds^(k-1)), then a one-CTA finish kernel with the EOM reverse of the previous iteration.
 template <typename T>
 void launch_adj_design(const Geo& g, Ctrl* ctrl, const Dof* it, const T* kref, const T* scratch, double* dkref,
-                       double* partials, int k, int di, cudaStream_t st);
+                       void* partials, int k, int di, cudaStream_t st);
 
 // Initial state (double) -> slot(0); s0 -> it row 0; ctrl reset for a forward (t0 = 1, base 0).
 template <typename T>

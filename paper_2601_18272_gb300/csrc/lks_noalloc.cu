@@ -113,6 +113,8 @@ int make_geo(const lks_problem* P, Geo* g) {
   g->dp = P->dp;
   g->mass = P->mass;
   g->inertia = P->inertia;
+  g->inv_mass = 1.0 / P->mass;
+  g->inv_inertia = 1.0 / P->inertia;
   // body box placed from x^G(t-1): circumscribed in the plane (the body may rotate)
   const double hx = (P->ndx - 1) / 2.0, hy = (P->ndy - 1) / 2.0;
   const int hb = (int)std::ceil(std::sqrt(hx * hx + hy * hy) - 1e-12);

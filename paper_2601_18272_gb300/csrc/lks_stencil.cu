@@ -15,6 +15,7 @@
 //
 // Algorithmic traffic per cell: read p, u (3 values), write p*, u* (3 values): 24 B in FP32.
 #include "lks_kernels.h"
+#include "lks_stencil_common.cuh"
 
 namespace lks {
 
@@ -24,51 +25,8 @@ constexpr int TX = kTileX, TY = kTileY2;
 constexpr int HX = TX + 4, HY = TY + 4;  // halo-2 region
 constexpr int CX = TX + 2, CY = TY + 2;  // halo-1 region
 
-// 2A in the field type (the FP32 copy for FP32 fields, exact for FP64 fields).
-template <typename T>
-__device__ __forceinline__ T two_a(const Geo& g);
-template <>
-__device__ __forceinline__ float two_a<float>(const Geo& g) { return g.A2; }
-template <>
-__device__ __forceinline__ double two_a<double>(const Geo& g) { return 2.0 * g.A; }
-
-__device__ __forceinline__ bool interior_x(const Geo& g, int x) {
-  return g.bc[0] == BC_PERIODIC || (x >= 1 && x <= g.n[0] - 2);
-}
-__device__ __forceinline__ bool interior_y(const Geo& g, int y) {
-  return g.bc[1] == BC_PERIODIC || (y >= 1 && y <= g.n[1] - 2);
-}
-
-// Gradient ghost rule along one axis: returns false if the position is beyond the ghost layer.
-__device__ __forceinline__ bool ghost_axis(int bc, int n, int* v, int* sgn) {
-  if (bc == BC_PERIODIC) {
-    *v = wrapi(*v, n);
-    return true;
-  }
-  if (*v >= 0 && *v < n) return true;
-  if (bc == BC_WALL) {
-    if (*v == -1) {
-      *v = 1;
-      *sgn = -*sgn;
-      return true;
-    }
-    if (*v == n) {
-      *v = n - 2;
-      *sgn = -*sgn;
-      return true;
-    }
-    return false;
-  }
-  if (*v == -1) {
-    *v = 0;
-    return true;
-  }
-  if (*v == n) {
-    *v = n - 1;
-    return true;
-  }
-  return false;
-}
+__device__ __forceinline__ bool interior_x(const Geo& g, int x) { return interior_axis(g.bc[0], g.n[0], x); }
+__device__ __forceinline__ bool interior_y(const Geo& g, int y) { return interior_axis(g.bc[1], g.n[1], y); }
 
 template <typename T>
 __global__ void __launch_bounds__(TX* TY) k_stencil2d(Geo g, Slots<T> S, const Ctrl* __restrict__ ctrl, int di) {
@@ -331,6 +289,8 @@ void launch_stencil_fwd(const Geo& g, const Slots<T>& S, const Ctrl* ctrl, int d
   if (g.dim == 2) {
     dim3 grid((g.n[0] + TX - 1) / TX, (g.n[1] + TY - 1) / TY);
     k_stencil2d<T><<<grid, dim3(TX, TY), 0, st>>>(g, S, ctrl, di);
+  } else {
+    launch_stencil3d_fwd<T>(g, S, ctrl, di, st);
   }
 }
 
@@ -340,6 +300,8 @@ void launch_stencil_adj(const Geo& g, const Slots<T>& S, T* Lb, long long lstrid
   if (g.dim == 2) {
     dim3 grid((g.n[0] + TX - 1) / TX, (g.n[1] + TY - 1) / TY);
     k_stencil2d_adj<T><<<grid, dim3(TX, TY), 0, st>>>(g, S, Lb, lstride, ctrl, di);
+  } else {
+    launch_stencil3d_adj<T>(g, S, Lb, lstride, ctrl, di, st);
   }
 }
 

@@ -1,0 +1,565 @@
+// LKS predictor (Sec. 2.2) and its exact transpose on D3Q15.
+//
+// Velocities: rest (w = 2/9), the six axis vectors (w = 1/9) and the eight (+-1, +-1, +-1)
+// (w = 1/72). With tau = 1, per cell x:
+//   f_i^eq(y) = w_i (a + c.b + sum_ab c_a c_b Q_ab),  a = 3p - 3/2 |u|^2,  b = 3u,
+//   Q_aa = 9/2 u_a^2 + 2A G_aa,  Q_ab = 9 u_a u_b + 2A (G_ab + G_ba)  (a < b),
+//   G_ab = d_b u_a = sum_j c_jb u_a(y + c_j) / 10,
+//   p*(x) = 1/3 sum_i f_i^eq(x - c_i),  u*(x) = sum_i c_i f_i^eq(x - c_i).
+// Boundary values (Sec. 2.2), in this order: y walls for nodes with x and z interior (u = 0, p from
+// the inner row), z walls for nodes with x interior (u = 0, p from the inner plane), then the open
+// x planes (all rows). Gradient ghosts: open planes copy the boundary node, walls reflect u with a
+// sign flip.
+//
+// GB300 form: one CTA per 32 x 8 column of cells marches over a chunk of z planes. Shared memory
+// holds a ring of three input planes (halo 2 in x and y) and one plane of the 15 f_i^eq values
+// (halo 1); each plane's f values are scattered into three register accumulators (outputs at
+// z - 1, z, z + 1), so every input is read from L2/HBM about (1 + 4/chunk) times per step.
+// A z-wall plane is completed from its neighbour plane inside the same chunk (chunks hold at
+// least two planes).
+//
+// Algorithmic traffic per cell: read p, u (4 values), write p*, u* (4 values): 32 B in FP32.
+// Transpose: read the adjoint (4 values) and u(t-1) (3 values), write 4 values: 44 B in FP32.
+#include "lks_kernels.h"
+#include "lks_stencil_common.cuh"
+
+namespace lks {
+
+namespace {
+
+constexpr int TX = kTileX, TY = kTileY3;
+constexpr int NT = TX * TY;
+constexpr int RX = TX + 4, RY = TY + 4;  // halo-2 input plane
+constexpr int FX = TX + 2, FY = TY + 2;  // halo-1 plane of per-node values
+constexpr int RPL = RX * RY, FPL = FX * FY;
+
+template <typename T>
+struct Fwd3Smem {
+  T raw[3][4][RY][RX];  // ring of input planes: p, ux, uy, uz
+  T f[15][FY][FX];      // f_i^eq of one plane
+  T out[4][TY][TX];     // the plane being completed
+  T out0[4][TY][TX];    // plane 0 of a z-wall, built from plane 1
+  T prevp[TY][TX];      // p of the previous plane after the y-wall phase
+};
+
+template <typename T>
+struct Adj3Smem {
+  T raw[3][4][RY][RX];  // ring of adjoint planes with the boundary rules reversed
+  T m[10][FY][FX];      // P, Ux, Uy, Uz, Sxx, Syy, Szz, Sxy, Sxz, Syz of one plane
+};
+
+__device__ __forceinline__ int ring(int z, int z0) { return (z - z0 + 3) % 3; }
+
+// z range of this CTA's chunk: chunks split nz evenly (the host keeps each at >= 2 planes).
+__device__ __forceinline__ void chunk_range(int nz, int* z0, int* z1) {
+  *z0 = (int)(((long long)blockIdx.z * nz) / gridDim.z);
+  *z1 = (int)(((long long)(blockIdx.z + 1) * nz) / gridDim.z);
+}
+
+// corner k = 0..7: (sx, sy, sz) = (+-1, +-1, +-1) with bit 0, 1, 2 selecting the minus sign
+__device__ __forceinline__ constexpr int csx(int k) { return (k & 1) ? -1 : 1; }
+__device__ __forceinline__ constexpr int csy(int k) { return (k & 2) ? -1 : 1; }
+__device__ __forceinline__ constexpr int csz(int k) { return (k & 4) ? -1 : 1; }
+// the 14 moving velocities: j < 6 the axis vectors +x, -x, +y, -y, +z, -z; then the corners
+__device__ __forceinline__ constexpr int dir_x(int j) { return j < 6 ? (j == 0 ? 1 : (j == 1 ? -1 : 0)) : csx(j - 6); }
+__device__ __forceinline__ constexpr int dir_y(int j) { return j < 6 ? (j == 2 ? 1 : (j == 3 ? -1 : 0)) : csy(j - 6); }
+__device__ __forceinline__ constexpr int dir_z(int j) { return j < 6 ? (j == 4 ? 1 : (j == 5 ? -1 : 0)) : csz(j - 6); }
+
+template <typename T>
+__device__ __forceinline__ void load_state_plane(const Geo& g, const T* __restrict__ src, T (*dst)[RY][RX], int x0,
+                                                 int y0, int zr) {
+  const long long N = g.N;
+  const int nx = g.n[0], ny = g.n[1], nz = g.n[2];
+  for (int q = threadIdx.x; q < RPL; q += NT) {
+    const int li = q % RX, lj = q / RX;
+    int gx = x0 - 2 + li, gy = y0 - 2 + lj, gz = zr, sgn = 1;
+    T v[4] = {T(0), T(0), T(0), T(0)};
+    if (ghost_axis(g.bc[0], nx, &gx, &sgn) && ghost_axis(g.bc[1], ny, &gy, &sgn) &&
+        ghost_axis(g.bc[2], nz, &gz, &sgn)) {
+      const long long n = gx + (long long)nx * (gy + (long long)ny * gz);
+      v[0] = src[n];
+      v[1] = T(sgn) * src[N + n];
+      v[2] = T(sgn) * src[2 * N + n];
+      v[3] = T(sgn) * src[3 * N + n];
+    }
+#pragma unroll
+    for (int c = 0; c < 4; ++c) dst[c][lj][li] = v[c];
+  }
+}
+
+// f_i^eq on the halo-1 nodes of plane zr from the input planes zr - 1, zr, zr + 1.
+template <typename T>
+__device__ __forceinline__ void feq_plane(const Geo& g, Fwd3Smem<T>& s, int zr, int z0) {
+  const int sm = ring(zr - 1, z0), s0 = ring(zr, z0), sp = ring(zr + 1, z0);
+  const T A2 = two_a<T>(g), tenth = T(0.1);
+  const T w0 = T(2.0 / 9.0), w1 = T(1.0 / 9.0), w3 = T(1.0 / 72.0);
+  for (int q = threadIdx.x; q < FPL; q += NT) {
+    const int ci = q % FX, cj = q / FX, li = ci + 1, lj = cj + 1;
+    const T p = s.raw[s0][0][lj][li];
+    T u[3], G[3][3];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+      const T(*U0)[RX] = s.raw[s0][1 + a];
+      const T(*Um)[RX] = s.raw[sm][1 + a];
+      const T(*Up)[RX] = s.raw[sp][1 + a];
+      u[a] = U0[lj][li];
+      T gx = U0[lj][li + 1] - U0[lj][li - 1];
+      T gy = U0[lj + 1][li] - U0[lj - 1][li];
+      T gz = Up[lj][li] - Um[lj][li];
+#pragma unroll
+      for (int k = 0; k < 8; ++k) {
+        const T v = (csz(k) > 0 ? Up : Um)[lj + csy(k)][li + csx(k)];
+        gx += T(csx(k)) * v;
+        gy += T(csy(k)) * v;
+        gz += T(csz(k)) * v;
+      }
+      G[a][0] = gx * tenth;
+      G[a][1] = gy * tenth;
+      G[a][2] = gz * tenth;
+    }
+    const T a0 = T(3) * p - T(1.5) * (u[0] * u[0] + u[1] * u[1] + u[2] * u[2]);
+    const T bx = T(3) * u[0], by = T(3) * u[1], bz = T(3) * u[2];
+    const T qxx = T(4.5) * u[0] * u[0] + A2 * G[0][0];
+    const T qyy = T(4.5) * u[1] * u[1] + A2 * G[1][1];
+    const T qzz = T(4.5) * u[2] * u[2] + A2 * G[2][2];
+    const T qxy = T(9) * u[0] * u[1] + A2 * (G[0][1] + G[1][0]);
+    const T qxz = T(9) * u[0] * u[2] + A2 * (G[0][2] + G[2][0]);
+    const T qyz = T(9) * u[1] * u[2] + A2 * (G[1][2] + G[2][1]);
+    s.f[0][cj][ci] = w0 * a0;
+    s.f[1][cj][ci] = w1 * (a0 + bx + qxx);
+    s.f[2][cj][ci] = w1 * (a0 - bx + qxx);
+    s.f[3][cj][ci] = w1 * (a0 + by + qyy);
+    s.f[4][cj][ci] = w1 * (a0 - by + qyy);
+    s.f[5][cj][ci] = w1 * (a0 + bz + qzz);
+    s.f[6][cj][ci] = w1 * (a0 - bz + qzz);
+    const T diag = a0 + qxx + qyy + qzz;
+#pragma unroll
+    for (int k = 0; k < 8; ++k) {
+      const T sx = T(csx(k)), sy = T(csy(k)), sz = T(csz(k));
+      s.f[7 + k][cj][ci] = w3 * (diag + sx * bx + sy * by + sz * bz + sx * sy * qxy + sx * sz * qxz + sy * sz * qyz);
+    }
+  }
+}
+
+// Open x planes on one completed plane (rows of this tile).
+template <typename T>
+__device__ __forceinline__ void x_planes(const Geo& g, T (*O)[TY][TX], int gx, int tx, int ty) {
+  const int nx = g.n[0];
+  if (g.bc[0] == BC_PERIODIC || !(gx == 0 || gx == nx - 1)) return;
+  const bool inlet = gx == 0;
+  const int tin = inlet ? tx + 1 : tx - 1;
+  if (g.bc[0] == BC_INFLOW_OUTFLOW) {
+    if (inlet) {
+      O[0][ty][tx] = O[0][ty][tin];
+      O[1][ty][tx] = T(g.u_in);
+      O[2][ty][tx] = T(0);
+      O[3][ty][tx] = T(0);
+    } else {
+      O[0][ty][tx] = T(0);
+      for (int c = 1; c < 4; ++c) O[c][ty][tx] = O[c][ty][tin];
+    }
+  } else {
+    O[0][ty][tx] = inlet ? T(g.dp) : T(0);
+    for (int c = 1; c < 4; ++c) O[c][ty][tx] = O[c][ty][tin];
+  }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(NT) k_stencil3d(Geo g, Slots<T> S, const Ctrl* __restrict__ ctrl, int di) {
+  extern __shared__ __align__(16) unsigned char smem_bytes[];
+  Fwd3Smem<T>& s = *reinterpret_cast<Fwd3Smem<T>*>(smem_bytes);
+  const int t = ctrl->t0 + di, base = ctrl->base;
+  const T* __restrict__ src = slot_ptr(S, t - 1, base);
+  T* __restrict__ dst = slot_ptr(S, t, base);
+  const long long N = g.N;
+  const int nx = g.n[0], ny = g.n[1], nz = g.n[2];
+  const int x0 = blockIdx.x * TX, y0 = blockIdx.y * TY;
+  const int tx = threadIdx.x % TX, ty = threadIdx.x / TX;
+  const int gx = x0 + tx, gy = y0 + ty;
+  const bool ingrid = gx < nx && gy < ny;
+  const bool zwall = g.bc[2] == BC_WALL;
+  int z0, z1;
+  chunk_range(nz, &z0, &z1);
+  const int ci = tx + 1, cj = ty + 1;
+  // acc[d]: output plane zr - 1 + d, (sum f, sum c_x f, sum c_y f, sum c_z f)
+  T acc[3][4];
+#pragma unroll
+  for (int d = 0; d < 3; ++d)
+#pragma unroll
+    for (int c = 0; c < 4; ++c) acc[d][c] = T(0);
+
+  load_state_plane(g, src, s.raw[ring(z0 - 2, z0)], x0, y0, z0 - 2);
+  load_state_plane(g, src, s.raw[ring(z0 - 1, z0)], x0, y0, z0 - 1);
+  for (int zr = z0 - 1; zr <= z1; ++zr) {
+    load_state_plane(g, src, s.raw[ring(zr + 1, z0)], x0, y0, zr + 1);
+    __syncthreads();
+    feq_plane(g, s, zr, z0);
+    __syncthreads();
+    {
+      // c_z = 0: rest and the four in-plane axis vectors -> output zr
+      const T f0 = s.f[0][cj][ci], f1 = s.f[1][cj][ci - 1], f2 = s.f[2][cj][ci + 1];
+      const T f3 = s.f[3][cj - 1][ci], f4 = s.f[4][cj + 1][ci];
+      acc[1][0] += f0 + f1 + f2 + f3 + f4;
+      acc[1][1] += f1 - f2;
+      acc[1][2] += f3 - f4;
+      // +z axis -> output zr + 1, -z axis -> output zr - 1
+      const T f5 = s.f[5][cj][ci], f6 = s.f[6][cj][ci];
+      acc[2][0] += f5;
+      acc[2][3] += f5;
+      acc[0][0] += f6;
+      acc[0][3] -= f6;
+#pragma unroll
+      for (int k = 0; k < 8; ++k) {
+        const int sx = csx(k), sy = csy(k), sz = csz(k);
+        const T v = s.f[7 + k][cj - sy][ci - sx];
+        const int d = sz > 0 ? 2 : 0;
+        acc[d][0] += v;
+        acc[d][1] += T(sx) * v;
+        acc[d][2] += T(sy) * v;
+        acc[d][3] += T(sz) * v;
+      }
+    }
+    const int zo = zr - 1;
+    if (zo >= z0) {  // output plane zo is complete
+      s.out[0][ty][tx] = acc[0][0] * T(1.0 / 3.0);
+      s.out[1][ty][tx] = acc[0][1];
+      s.out[2][ty][tx] = acc[0][2];
+      s.out[3][ty][tx] = acc[0][3];
+      __syncthreads();
+      // y walls, for nodes with x and z interior
+      if (ingrid && g.bc[1] == BC_WALL && (gy == 0 || gy == ny - 1) && interior_axis(g.bc[0], nx, gx) &&
+          interior_axis(g.bc[2], nz, zo)) {
+        const int tin = (gy == 0) ? ty + 1 : ty - 1;
+        s.out[0][ty][tx] = s.out[0][tin][tx];
+        s.out[1][ty][tx] = s.out[2][ty][tx] = s.out[3][ty][tx] = T(0);
+      }
+      __syncthreads();
+      // z walls, for nodes with x interior (own column only)
+      const T pp = s.out[0][ty][tx];
+      if (zwall && interior_axis(g.bc[0], nx, gx)) {
+        if (zo == nz - 1) {
+          s.out[0][ty][tx] = s.prevp[ty][tx];
+          s.out[1][ty][tx] = s.out[2][ty][tx] = s.out[3][ty][tx] = T(0);
+        }
+        if (zo == 1) {
+          s.out0[0][ty][tx] = pp;
+          s.out0[1][ty][tx] = s.out0[2][ty][tx] = s.out0[3][ty][tx] = T(0);
+        }
+      }
+      s.prevp[ty][tx] = pp;
+      __syncthreads();
+      if (ingrid) {
+        x_planes(g, s.out, gx, tx, ty);
+        if (zwall && zo == 1) x_planes(g, s.out0, gx, tx, ty);
+        const long long n = gx + (long long)nx * gy;
+        if (!(zwall && zo == 0)) {
+          const long long nz_off = (long long)zo * nx * ny;
+#pragma unroll
+          for (int c = 0; c < 4; ++c) dst[c * N + nz_off + n] = s.out[c][ty][tx];
+        }
+        if (zwall && zo == 1) {
+#pragma unroll
+          for (int c = 0; c < 4; ++c) dst[c * N + n] = s.out0[c][ty][tx];
+        }
+      }
+    }
+#pragma unroll
+    for (int c = 0; c < 4; ++c) {
+      acc[0][c] = acc[1][c];
+      acc[1][c] = acc[2][c];
+      acc[2][c] = T(0);
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------------------------
+// Transpose. The adjoint of (p*, u*) is first routed back through the boundary rules
+// (lam_star3), giving zero on every non-interior node. Then with
+// fbar_i(y) = 1/3 lam_p*(y + c_i) + c_i . lam_u*(y + c_i) and the moments
+//   P = sum_i w_i fbar_i, U = sum_i w_i c_i fbar_i, S = sum_i w_i c_i c_i fbar_i,
+//   lam_p(z) = 3P,  lam_u(z) = 3U + 9 S u - 3 u P + (2A/10) sum_{(y,j): nbr(y,c_j) = z} sgn S(y) c_j
+// where the last sum is the transpose of the velocity-gradient stencil with its ghost rule.
+// ---------------------------------------------------------------------------------------------
+template <typename T>
+__device__ __forceinline__ T ldl(const T* L, long long N, int c, int nx, int ny, int x, int y, int z) {
+  return L[c * N + x + (long long)nx * (y + (long long)ny * z)];
+}
+
+// Adjoint of (p*, u*) seen by interior node (x, y, z) once the boundary rules are reversed: p is
+// copied (through the y-wall, z-wall and inflow phases) into every node of the product of
+// {x, inlet if x == 1} x {y, wall row if y is next to it} x {z, wall plane likewise}; u is copied
+// only by the outflow / pressure planes from x = nx - 2 and (pressure) x = 1.
+template <typename T>
+__device__ __forceinline__ void lam_star3(const Geo& g, const T* L, int x, int y, int z, T* v) {
+  const long long N = g.N;
+  const int nx = g.n[0], ny = g.n[1], nz = g.n[2];
+  if (!interior_axis(g.bc[0], nx, x) || !interior_axis(g.bc[1], ny, y) || !interior_axis(g.bc[2], nz, z)) {
+    v[0] = v[1] = v[2] = v[3] = T(0);
+    return;
+  }
+  const int bx = g.bc[0];
+  int xs[2] = {x, 0}, ys[2] = {y, 0}, zs[2] = {z, 0};
+  const int nxs = (bx == BC_INFLOW_OUTFLOW && x == 1) ? 2 : 1;
+  int nys = 1, nzs = 1;
+  if (g.bc[1] == BC_WALL && (y == 1 || y == ny - 2)) {
+    ys[1] = (y == 1) ? 0 : ny - 1;
+    nys = 2;
+  }
+  if (g.bc[2] == BC_WALL && (z == 1 || z == nz - 2)) {
+    zs[1] = (z == 1) ? 0 : nz - 1;
+    nzs = 2;
+  }
+  T p = T(0);
+  for (int c = 0; c < nzs; ++c)
+    for (int b = 0; b < nys; ++b)
+      for (int a = 0; a < nxs; ++a) p += ldl(L, N, 0, nx, ny, xs[a], ys[b], zs[c]);
+  v[0] = p;
+  for (int c = 1; c < 4; ++c) {
+    T u = ldl(L, N, c, nx, ny, x, y, z);
+    if ((bx == BC_INFLOW_OUTFLOW || bx == BC_PRESSURE) && x == nx - 2) u += ldl(L, N, c, nx, ny, nx - 1, y, z);
+    if (bx == BC_PRESSURE && x == 1) u += ldl(L, N, c, nx, ny, 0, y, z);
+    v[c] = u;
+  }
+}
+
+template <typename T>
+__device__ __forceinline__ void load_adj_plane(const Geo& g, const T* __restrict__ L, T (*dst)[RY][RX], int x0, int y0,
+                                               int zr) {
+  const int nx = g.n[0], ny = g.n[1], nz = g.n[2];
+  for (int q = threadIdx.x; q < RPL; q += NT) {
+    const int li = q % RX, lj = q / RX;
+    int gx = x0 - 2 + li, gy = y0 - 2 + lj, gz = zr;
+    T v[4] = {T(0), T(0), T(0), T(0)};
+    bool ok = true;
+    if (g.bc[0] == BC_PERIODIC) gx = wrapi(gx, nx);
+    else if (gx < 0 || gx >= nx) ok = false;
+    if (g.bc[1] == BC_PERIODIC) gy = wrapi(gy, ny);
+    else if (gy < 0 || gy >= ny) ok = false;
+    if (g.bc[2] == BC_PERIODIC) gz = wrapi(gz, nz);
+    else if (gz < 0 || gz >= nz) ok = false;
+    if (ok) lam_star3(g, L, gx, gy, gz, v);
+#pragma unroll
+    for (int c = 0; c < 4; ++c) dst[c][lj][li] = v[c];
+  }
+}
+
+template <typename T>
+__device__ __forceinline__ void moment_plane(Adj3Smem<T>& s, int zr, int z0) {
+  const int sm = ring(zr - 1, z0), s0 = ring(zr, z0), sp = ring(zr + 1, z0);
+  const T third = T(1.0 / 3.0), w0 = T(2.0 / 9.0), w1 = T(1.0 / 9.0), w3 = T(1.0 / 72.0);
+  for (int q = threadIdx.x; q < FPL; q += NT) {
+    const int ci = q % FX, cj = q / FX, li = ci + 1, lj = cj + 1;
+    const T(*P0)[RX] = s.raw[s0][0];
+    const T fb0 = third * P0[lj][li];
+    const T fpx = third * P0[lj][li + 1] + s.raw[s0][1][lj][li + 1];
+    const T fmx = third * P0[lj][li - 1] - s.raw[s0][1][lj][li - 1];
+    const T fpy = third * P0[lj + 1][li] + s.raw[s0][2][lj + 1][li];
+    const T fmy = third * P0[lj - 1][li] - s.raw[s0][2][lj - 1][li];
+    const T fpz = third * s.raw[sp][0][lj][li] + s.raw[sp][3][lj][li];
+    const T fmz = third * s.raw[sm][0][lj][li] - s.raw[sm][3][lj][li];
+    T cP = T(0), cX = T(0), cY = T(0), cZ = T(0), cXY = T(0), cXZ = T(0), cYZ = T(0);
+#pragma unroll
+    for (int k = 0; k < 8; ++k) {
+      const int sx = csx(k), sy = csy(k), sz = csz(k);
+      const int pl = sz > 0 ? sp : sm;
+      const int yy = lj + sy, xx = li + sx;
+      const T fb = third * s.raw[pl][0][yy][xx] + T(sx) * s.raw[pl][1][yy][xx] + T(sy) * s.raw[pl][2][yy][xx] +
+                   T(sz) * s.raw[pl][3][yy][xx];
+      cP += fb;
+      cX += T(sx) * fb;
+      cY += T(sy) * fb;
+      cZ += T(sz) * fb;
+      cXY += T(sx * sy) * fb;
+      cXZ += T(sx * sz) * fb;
+      cYZ += T(sy * sz) * fb;
+    }
+    s.m[0][cj][ci] = w0 * fb0 + w1 * (fpx + fmx + fpy + fmy + fpz + fmz) + w3 * cP;
+    s.m[1][cj][ci] = w1 * (fpx - fmx) + w3 * cX;
+    s.m[2][cj][ci] = w1 * (fpy - fmy) + w3 * cY;
+    s.m[3][cj][ci] = w1 * (fpz - fmz) + w3 * cZ;
+    s.m[4][cj][ci] = w1 * (fpx + fmx) + w3 * cP;
+    s.m[5][cj][ci] = w1 * (fpy + fmy) + w3 * cP;
+    s.m[6][cj][ci] = w1 * (fpz + fmz) + w3 * cP;
+    s.m[7][cj][ci] = w3 * cXY;
+    s.m[8][cj][ci] = w3 * cXZ;
+    s.m[9][cj][ci] = w3 * cYZ;
+  }
+}
+
+// S_ab of the moment plane at (cj, ci), b-th column (symmetric).
+template <typename T>
+__device__ __forceinline__ T Sab(const Adj3Smem<T>& s, int a, int b, int cj, int ci) {
+  const int idx = (a == b) ? 4 + a : (a + b == 1 ? 7 : (a + b == 2 ? 8 : 9));
+  return s.m[idx][cj][ci];
+}
+
+template <typename T>
+__global__ void __launch_bounds__(NT) k_stencil3d_adj(Geo g, Slots<T> S, T* Lb, long long lstride,
+                                                      const Ctrl* __restrict__ ctrl, int di) {
+  extern __shared__ __align__(16) unsigned char smem_bytes[];
+  Adj3Smem<T>& s = *reinterpret_cast<Adj3Smem<T>*>(smem_bytes);
+  const int t = ctrl->t0 - di, base = ctrl->base;
+  const T* __restrict__ Lcur = Lb + (long long)(t & 1) * lstride;
+  T* __restrict__ Lnext = Lb + (long long)((t - 1) & 1) * lstride;
+  const T* __restrict__ st = slot_ptr(S, t - 1, base);
+  const long long N = g.N;
+  const int nx = g.n[0], ny = g.n[1], nz = g.n[2];
+  const int x0 = blockIdx.x * TX, y0 = blockIdx.y * TY;
+  const int tx = threadIdx.x % TX, ty = threadIdx.x / TX;
+  const int gx = x0 + tx, gy = y0 + ty;
+  const bool ingrid = gx < nx && gy < ny;
+  int z0, z1;
+  chunk_range(nz, &z0, &z1);
+  const int ci = tx + 1, cj = ty + 1;
+  const T kA = two_a<T>(g) * T(0.1);
+  const bool near_xy = (g.bc[0] != BC_PERIODIC && (gx <= 1 || gx >= nx - 2)) ||
+                       (g.bc[1] != BC_PERIODIC && (gy <= 1 || gy >= ny - 2));
+  T acc[3][4];
+#pragma unroll
+  for (int d = 0; d < 3; ++d)
+#pragma unroll
+    for (int c = 0; c < 4; ++c) acc[d][c] = T(0);
+
+  load_adj_plane(g, Lcur, s.raw[ring(z0 - 2, z0)], x0, y0, z0 - 2);
+  load_adj_plane(g, Lcur, s.raw[ring(z0 - 1, z0)], x0, y0, z0 - 1);
+  for (int zr = z0 - 1; zr <= z1; ++zr) {
+    load_adj_plane(g, Lcur, s.raw[ring(zr + 1, z0)], x0, y0, zr + 1);
+    __syncthreads();
+    moment_plane(s, zr, z0);
+    __syncthreads();
+    // local part of output zr
+    if (ingrid && zr >= z0 && zr < z1) {
+      const long long n = gx + (long long)nx * (gy + (long long)ny * zr);
+      const T u[3] = {st[N + n], st[2 * N + n], st[3 * N + n]};
+      const T P = s.m[0][cj][ci];
+      acc[1][0] += T(3) * P;
+#pragma unroll
+      for (int a = 0; a < 3; ++a) {
+        T su = T(0);
+#pragma unroll
+        for (int b = 0; b < 3; ++b) su += Sab(s, a, b, cj, ci) * u[b];
+        acc[1][1 + a] += T(3) * s.m[1 + a][cj][ci] + T(9) * su - T(3) * u[a] * P;
+      }
+    }
+    // velocity-gradient transpose: plane zr feeds outputs zr - 1, zr, zr + 1
+    const bool zplane_ok = g.bc[2] == BC_PERIODIC || (zr >= 0 && zr < nz);
+    const bool slow = near_xy || (g.bc[2] != BC_PERIODIC && (zr <= 0 || zr >= nz - 1));
+    if (ingrid && zplane_ok) {
+      if (!slow) {
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+          T v1 = Sab(s, a, 0, cj, ci - 1) - Sab(s, a, 0, cj, ci + 1) + Sab(s, a, 1, cj - 1, ci) - Sab(s, a, 1, cj + 1, ci);
+          T v2 = Sab(s, a, 2, cj, ci), v0 = -Sab(s, a, 2, cj, ci);
+#pragma unroll
+          for (int k = 0; k < 8; ++k) {
+            const int sx = csx(k), sy = csy(k), sz = csz(k);
+            const int yy = cj - sy, xx = ci - sx;
+            const T h = T(sx) * Sab(s, a, 0, yy, xx) + T(sy) * Sab(s, a, 1, yy, xx) + T(sz) * Sab(s, a, 2, yy, xx);
+            if (sz > 0) v2 += h;
+            else v0 += h;
+          }
+          acc[0][1 + a] += kA * v0;
+          acc[1][1 + a] += kA * v1;
+          acc[2][1 + a] += kA * v2;
+        }
+      } else {
+        for (int dy = -1; dy <= 1; ++dy)
+          for (int dx = -1; dx <= 1; ++dx) {
+            int yx = gx + dx, yy = gy + dy;
+            if (g.bc[0] == BC_PERIODIC) yx = wrapi(yx, nx);
+            else if (yx < 0 || yx >= nx) continue;
+            if (g.bc[1] == BC_PERIODIC) yy = wrapi(yy, ny);
+            else if (yy < 0 || yy >= ny) continue;
+            const int mj = cj + dy, mi = ci + dx;
+            T Sm[3][3];
+#pragma unroll
+            for (int a = 0; a < 3; ++a)
+#pragma unroll
+              for (int b = 0; b < 3; ++b) Sm[a][b] = Sab(s, a, b, mj, mi);
+#pragma unroll
+            for (int j = 0; j < 14; ++j) {
+              const int cx = dir_x(j), cy = dir_y(j), cz = dir_z(j);
+              int mx = yx + cx, my = yy + cy, sgn = 1;
+              if (!ghost_axis(g.bc[0], nx, &mx, &sgn) || !ghost_axis(g.bc[1], ny, &my, &sgn)) continue;
+              if (mx != gx || my != gy) continue;
+              int dz = cz;
+              if (g.bc[2] != BC_PERIODIC) {
+                const int vz = zr + cz;
+                if (vz < 0 || vz >= nz) {
+                  if (g.bc[2] != BC_WALL) continue;
+                  dz = -dz;  // reflected onto the plane on the other side of zr
+                  sgn = -sgn;
+                }
+              }
+              T h[3];
+#pragma unroll
+              for (int a = 0; a < 3; ++a) h[a] = kA * T(sgn) * (T(cx) * Sm[a][0] + T(cy) * Sm[a][1] + T(cz) * Sm[a][2]);
+              if (dz < 0) {
+#pragma unroll
+                for (int a = 0; a < 3; ++a) acc[0][1 + a] += h[a];
+              } else if (dz == 0) {
+#pragma unroll
+                for (int a = 0; a < 3; ++a) acc[1][1 + a] += h[a];
+              } else {
+#pragma unroll
+                for (int a = 0; a < 3; ++a) acc[2][1 + a] += h[a];
+              }
+            }
+          }
+      }
+    }
+    const int zo = zr - 1;
+    if (ingrid && zo >= z0) {
+      const long long n = gx + (long long)nx * (gy + (long long)ny * zo);
+#pragma unroll
+      for (int c = 0; c < 4; ++c) Lnext[c * N + n] = acc[0][c];
+    }
+#pragma unroll
+    for (int c = 0; c < 4; ++c) {
+      acc[0][c] = acc[1][c];
+      acc[1][c] = acc[2][c];
+      acc[2][c] = T(0);
+    }
+  }
+}
+
+// Number of z chunks: enough CTAs to fill the GPU, every chunk at least four planes.
+int z_chunks(const Geo& g) {
+  const int tiles = ((g.n[0] + TX - 1) / TX) * ((g.n[1] + TY - 1) / TY);
+  const int want = (4 * 152 + tiles - 1) / tiles;
+  int c = g.n[2] / 4;
+  if (c > want) c = want;
+  return c < 1 ? 1 : c;
+}
+
+}  // namespace
+
+template <typename T>
+void prepare_stencil3d() {
+  cudaFuncSetAttribute(k_stencil3d<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(Fwd3Smem<T>));
+  cudaFuncSetAttribute(k_stencil3d_adj<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(Adj3Smem<T>));
+}
+
+template <typename T>
+void launch_stencil3d_fwd(const Geo& g, const Slots<T>& S, const Ctrl* ctrl, int di, cudaStream_t st) {
+  const dim3 grid((g.n[0] + TX - 1) / TX, (g.n[1] + TY - 1) / TY, z_chunks(g));
+  k_stencil3d<T><<<grid, NT, sizeof(Fwd3Smem<T>), st>>>(g, S, ctrl, di);
+}
+
+template <typename T>
+void launch_stencil3d_adj(const Geo& g, const Slots<T>& S, T* Lb, long long lstride, const Ctrl* ctrl, int di,
+                          cudaStream_t st) {
+  const dim3 grid((g.n[0] + TX - 1) / TX, (g.n[1] + TY - 1) / TY, z_chunks(g));
+  k_stencil3d_adj<T><<<grid, NT, sizeof(Adj3Smem<T>), st>>>(g, S, Lb, lstride, ctrl, di);
+}
+
+template void prepare_stencil3d<float>();
+template void prepare_stencil3d<double>();
+template void launch_stencil3d_fwd<float>(const Geo&, const Slots<float>&, const Ctrl*, int, cudaStream_t);
+template void launch_stencil3d_fwd<double>(const Geo&, const Slots<double>&, const Ctrl*, int, cudaStream_t);
+template void launch_stencil3d_adj<float>(const Geo&, const Slots<float>&, float*, long long, const Ctrl*, int,
+                                          cudaStream_t);
+template void launch_stencil3d_adj<double>(const Geo&, const Slots<double>&, double*, long long, const Ctrl*, int,
+                                           cudaStream_t);
+
+}  // namespace lks

@@ -10,8 +10,8 @@ import numpy as np
 import pytest
 
 from oracle import oracle as O
-from tests.problems import (BC_INFLOW_OUTFLOW, BC_PERIODIC, BC_PRESSURE, BC_WALL, DOF_ROT, DOF_TX, DOF_TY,
-                            W_BILINEAR, W_COS4, body2d, perturbed_state)
+from tests.problems import (BC_INFLOW_OUTFLOW, BC_PERIODIC, BC_PRESSURE, BC_WALL, DOF_ROT, DOF_TX, DOF_TY, DOF_TZ,
+                            W_BILINEAR, W_COS4, body2d, body3d, perturbed_state)
 from workloads import CKPT_STORE_ALL, CKPT_UNIFORM, config, initial_state
 
 pytestmark = pytest.mark.gpu
@@ -206,3 +206,55 @@ def test_error_paths():
     bad.nx = 2
     with pytest.raises(LksError, match="LKS_ERR_ARG"):
         lks_create(bad)
+
+
+# ---- 3D (D3Q15) ------------------------------------------------------------------------------
+
+CASES_3D = [
+    ("3d-rot-y", lambda: body3d(nx=24, ny=16, nz=16, centre=(9.3, 7.6, 8.2))),
+    ("3d-walls-pressure-rotx", lambda: body3d(nx=40, ny=18, nz=14, centre=(12.4, 8.7, 6.6),
+                                              bc=(BC_PRESSURE, BC_WALL, BC_WALL), rot_axis=0)),
+    ("3d-periodic-rotz", lambda: body3d(nx=20, ny=16, nz=18, centre=(9.1, 8.4, 8.8), bc=(BC_PERIODIC,) * 3,
+                                        rot_axis=2)),
+    ("3d-trans-bilinear-walls", lambda: body3d(nx=34, ny=18, nz=13, centre=(10.2, 9.1, 6.4),
+                                               mask=DOF_TX | DOF_TY | DOF_TZ, wk=W_BILINEAR,
+                                               bc=(BC_INFLOW_OUTFLOW, BC_WALL, BC_WALL))),
+]
+
+
+@pytest.mark.parametrize("name,make", CASES_3D, ids=[c[0] for c in CASES_3D])
+def test_3d_fp64_store_all_matches_oracle(name, make):
+    P, g = make()
+    p0, u0, s0 = perturbed_state(P)
+    G = O.gradient(P, g, p0, u0, s0)
+    po, uo, ho, Jo = O.forward(P, g, p0, u0, s0)
+    r = gpu_run(P, g, p0, u0, s0, precision=64, ckpt_policy=CKPT_STORE_ALL)
+    assert abs(r["J"] - Jo) <= 1e-11 * abs(Jo)
+    np.testing.assert_allclose(r["hist"], ho, rtol=1e-11, atol=1e-12)
+    assert rel(r["p"], po) < 1e-10 and rel(r["u"], uo) < 1e-10
+    assert rel(r["dJdgamma"], G["dJdgamma"]) < 1e-9
+    assert rel(r["lam_u0"], G["lam_u0"]) < 1e-9 and rel(r["lam_p0"], G["lam_p0"]) < 1e-9
+    np.testing.assert_allclose(r["lam_dof0"], G["lam_dof0"], rtol=1e-9, atol=1e-12)
+
+
+@pytest.mark.parametrize("name,make", CASES_3D[:2], ids=[c[0] for c in CASES_3D[:2]])
+def test_3d_fp32_uniform_matches_oracle(name, make):
+    P, g = make()
+    P = P.replace(n_steps=9)
+    p0, u0, s0 = perturbed_state(P)
+    G = O.gradient(P, g, p0, u0, s0)
+    r = gpu_run(P, g, p0, u0, s0, precision=32, ckpt_policy=CKPT_UNIFORM, ckpt_every=4)
+    assert abs(r["J"] - G["J"]) <= 1e-4 * abs(G["J"])
+    assert rel(r["dJdgamma"], G["dJdgamma"]) <= 1e-3
+
+
+def test_body3d_128x64x64_truncated_fp32():
+    """The 128x64x64 D3Q15 / 48^3 translating workload in its benchmark precision (FP32 fields,
+    uniform checkpoints), truncated to 2 steps so the oracle finishes in about half a minute."""
+    P, g = config(4)
+    P = P.replace(n_steps=2, ckpt_every=1)
+    p0, u0, s0 = initial_state(P)
+    G = O.gradient(P, g, p0, u0, s0)
+    r = gpu_run(P, g, p0, u0, s0)
+    assert abs(r["J"] - G["J"]) <= 1e-4 * abs(G["J"])
+    assert rel(r["dJdgamma"], G["dJdgamma"]) <= 1e-3
