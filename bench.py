@@ -134,7 +134,7 @@ def _box_cells(P) -> int:
     return B * B
 
 
-def _fluid_problem(dim: int, n: tuple, name: str):
+def _fluid_problem(dim: int, n: tuple, name: str, n_steps: int = 20, every: int = 10):
     """A large grid with a 2^dim design block carrying gamma = 0 (no body): the full-grid stencil
     kernels alone, for their HBM roofline."""
     from workloads import BC_INFLOW_OUTFLOW, BC_PERIODIC, CKPT_UNIFORM, W_COS4, Problem
@@ -143,8 +143,8 @@ def _fluid_problem(dim: int, n: tuple, name: str):
     P = Problem(dim=dim, nx=n[0], ny=n[1], nz=nz, ndx=2, ndy=2, ndz=2 if dim == 3 else 1, body_centre=c,
                 rot_axis=2, dof_mask=0, mass=1.0, inertia=1.0, nu=0.032, u_in=0.05, dp=0.0,
                 bc=(BC_INFLOW_OUTFLOW, BC_PERIODIC, BC_PERIODIC), kappa_max=1.0, q=0.1, weight_kind=W_COS4,
-                n_steps=20, n_itr=5, obj_weights=(1.0,) + (0.0,) * 7, field_precision=32,
-                ckpt_policy=CKPT_UNIFORM, ckpt_every=10, name=name)
+                n_steps=n_steps, n_itr=5, obj_weights=(1.0,) + (0.0,) * 7, field_precision=32,
+                ckpt_policy=CKPT_UNIFORM, ckpt_every=every, name=name)
     return P, np.zeros(P.n_design)
 
 
@@ -162,11 +162,11 @@ def _family_times(solver, run):
     return fams
 
 
-def stencil_roofline(dev, peak: float, dim: int, n: tuple, name: str) -> dict:
+def stencil_roofline(dev, peak: float, dim: int, n: tuple, name: str, n_steps: int = 20, every: int = 10) -> dict:
     """HBM roofline of the predictor and its transpose on a grid far larger than L2."""
     import torch
     from paper_2601_18272_gb300.lks import Solver
-    P, g = _fluid_problem(dim, n, name)
+    P, g = _fluid_problem(dim, n, name, n_steps, every)
     S = Solver(P)
     gamma = torch.tensor(g, dtype=torch.float64, device=dev)
     grad = torch.empty_like(gamma)
@@ -223,6 +223,45 @@ def gradient_throughput(dev, flush, index: int) -> dict:
             "kernel_ms_per_gradient": {k: round(v[0], 3) for k, v in fams.items()}}
 
 
+def ckpt_precision_study(dev, n_steps: int = 400) -> dict:
+    """Gradient error of FP32 / BF16 / FP16 checkpoints against the FP64 store-all GPU form on the
+    1024x512 / 256x256 x-y-theta workload truncated to n_steps (checkpoints every 100)."""
+    import torch
+    from paper_2601_18272_gb300.lks import Solver
+    from workloads import CKPT_BF16, CKPT_FP16, CKPT_FP32, CKPT_STORE_ALL, CKPT_UNIFORM, config
+    P, g = config(3)
+    P = P.replace(n_steps=n_steps)
+    gamma = torch.tensor(g, dtype=torch.float64, device=dev)
+    stream = torch.cuda.current_stream(dev)
+
+    def grad(S):
+        out = torch.empty_like(gamma)
+        J = S.forward(gamma)
+        S.adjoint(1.0)
+        S.sensitivity(out)
+        torch.cuda.synchronize()
+        return J, out
+
+    ref = Solver(P, precision=64, ckpt_policy=CKPT_STORE_ALL)
+    J64, g64 = grad(ref)
+    ref.close()
+    out = {"workload": P.name + f"_first{n_steps}", "reference": "FP64 store-all GPU form"}
+    for name, fmt in (("fp32", CKPT_FP32), ("bf16", CKPT_BF16), ("fp16", CKPT_FP16)):
+        S = Solver(P, precision=32, ckpt_policy=CKPT_UNIFORM, ckpt_every=100, ckpt_format=fmt)
+        J, d = grad(S)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        grad(S)
+        e1.record(stream)
+        e1.synchronize()
+        from paper_2601_18272_gb300 import lks
+        out[name] = {"dJdgamma_rel_l2": float(torch.linalg.norm(d - g64) / torch.linalg.norm(g64)),
+                     "J_rel": abs(J - J64) / abs(J64), "ms_per_gradient": e0.elapsed_time(e1),
+                     "workspace_gb": lks.lks_workspace_bytes(S.handle) / 1e9}
+        S.close()
+    return out
+
+
 def run_reference(args, ws, rank):
     """The FP64 oracle on the host cores, each step a bounded sample of the same workload."""
     if rank != 0:
@@ -277,10 +316,24 @@ def main():
     ap.add_argument("--skip-extras", action="store_true", help="only the timed region and e2e")
     ap.add_argument("--time-steps", type=int, default=0,
                     help="truncate N_t (profiling runs only: keeps the per-step kernel mix, shrinks the launch list)")
+    ap.add_argument("--case", choices=["fluid2d", "fluid3d"], default=None,
+                    help="profiling runs only: the stencil roofline of a fluid grid (--grid NXxNY[xNZ]) alone")
+    ap.add_argument("--grid", default=None)
+    ap.add_argument("--case-steps", type=int, default=4)
     args = ap.parse_args()
     ws, rank, local = _dist()
     if args.impl == "reference":
         return run_reference(args, ws, rank)
+    if args.case:
+        import torch
+        torch.cuda.set_device(local)
+        dim = 2 if args.case == "fluid2d" else 3
+        n = tuple(int(v) for v in (args.grid or ("4096x4096" if dim == 2 else "256x256x256")).split("x"))
+        name = f"{args.case}_{'x'.join(map(str, n))}"
+        out = stencil_roofline(torch.device("cuda", local), _peaks()[0], dim, n, name, args.case_steps,
+                               max(1, args.case_steps // 2))
+        print(json.dumps(out), flush=True)
+        return 0
 
     import torch
     from paper_2601_18272_gb300 import lks
@@ -415,6 +468,7 @@ def main():
         line["stencil_roofline_2d"] = stencil_roofline(dev, peak, 2, (8192, 4096), "fluid2d_8192x4096")
         line["stencil_roofline_3d"] = stencil_roofline(dev, peak, 3, (512, 256, 256), "fluid3d_512x256x256")
         line["body3d"] = gradient_throughput(dev, flush, 4)
+        line["ckpt_precision"] = ckpt_precision_study(dev)
         line["cpu_baseline"] = cpu_baseline(args.cpu_sample_steps)
     solver.close()
     if rank == 0:

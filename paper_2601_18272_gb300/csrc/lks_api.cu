@@ -46,7 +46,9 @@ struct lks_handle {
   void* ring = nullptr;  // store-all: N_t + 1 slots; uniform: segment of every + 1 slots
   int nring = 0;
   void* pp = nullptr;    // uniform: ping-pong forward state (2 slots)
-  void* ckpt = nullptr;  // uniform: checkpoints at t = 0, k, 2k, ...
+  void* ckpt = nullptr;  // uniform: checkpoints at t = 0, k, 2k, ... (native format)
+  unsigned short* ckq = nullptr;  // uniform, BF16/FP16: checkpoints at t = k, 2k, ... (t = 0 from init)
+  unsigned* ckkeys = nullptr;     // their per-plane ranges
   int nckpt = 0;
   long long slot_elems = 0;
   void* boxstore = nullptr;  // u* in the body box, one slab per step of the resident segment
@@ -157,10 +159,15 @@ int validate(const lks_problem* P) {
   if (P->field_precision != LKS_FP32 && P->field_precision != LKS_FP64) return LKS_ERR_ARG;
   if (P->ckpt_policy != LKS_CKPT_STORE_ALL && P->ckpt_policy != LKS_CKPT_UNIFORM) return LKS_ERR_ARG;
   if (P->ckpt_policy == LKS_CKPT_UNIFORM && P->ckpt_every < 1) return LKS_ERR_ARG;
-  if (P->ckpt_format != LKS_CKPT_NATIVE) return LKS_ERR_UNSUPPORTED;
-  // boundary pairs (x = 0,1 and nx-2,nx-1; y walls likewise) must share a stencil tile
-  if (P->bc[0] != LKS_BC_PERIODIC && P->nx % kTileX == 1) return LKS_ERR_UNSUPPORTED;
-  if (P->bc[1] == LKS_BC_WALL && P->ny % (P->dim == 2 ? kTileY2 : kTileY3) == 1) return LKS_ERR_UNSUPPORTED;
+  if (P->ckpt_format != LKS_CKPT_NATIVE && P->ckpt_format != LKS_CKPT_BF16 && P->ckpt_format != LKS_CKPT_FP16)
+    return LKS_ERR_ARG;
+  // reduced-precision checkpoints: FP32 fields with uniform checkpoints
+  if (P->ckpt_format != LKS_CKPT_NATIVE && (P->ckpt_policy != LKS_CKPT_UNIFORM || P->field_precision != LKS_FP32))
+    return LKS_ERR_UNSUPPORTED;
+  // 3D: boundary pairs (x = 0,1 and nx-2,nx-1; y walls likewise) must share a stencil column
+  // (2D strips choose their width so that they always do)
+  if (P->dim == 3 && P->bc[0] != LKS_BC_PERIODIC && P->nx % kTileX == 1) return LKS_ERR_UNSUPPORTED;
+  if (P->dim == 3 && P->bc[1] == LKS_BC_WALL && P->ny % kTileY3 == 1) return LKS_ERR_UNSUPPORTED;
   return LKS_OK;
 }
 
@@ -320,15 +327,23 @@ int forward_impl(lks_handle* h, cudaStream_t st) {
     Slots<T> S = pp_slots<T>(h);
     const int every = h->P.ckpt_every;
     L0("init", [&](cudaStream_t s) { launch_init_forward<T>(g, S, h->init_p, h->init_u, h->init_s, h->it, h->ctrl, s); });
-    L0("ckpt", [&](cudaStream_t s) { launch_ckpt_pack<T>(g, S, (T*)h->ckpt, h->slot_elems, every, h->ctrl, -1, s); });
+    const int fmt = h->P.ckpt_format;
+    auto pack = [&](Launcher& L, int di) {
+      if (fmt == LKS_CKPT_NATIVE)
+        L("ckpt", [&](cudaStream_t s) { launch_ckpt_pack<T>(g, S, (T*)h->ckpt, h->slot_elems, every, h->ctrl, di, s); });
+      else
+        L("ckpt", [&](cudaStream_t s) {
+          launch_ckpt_pack_q(g, reinterpret_cast<const Slots<float>&>(S), h->ckq, h->ckkeys, fmt, every, h->ctrl, di, s);
+        });
+    };
+    if (fmt == LKS_CKPT_NATIVE) pack(L0, -1);  // reduced formats restart segment 0 from the initial state
     for (int t0 = 0; t0 < NT; t0 += every) {
       const int n = std::min(every, NT - t0);
-      const bool pack = (t0 + n < NT);
+      const bool do_pack = (t0 + n < NT);
       L0("init", [&](cudaStream_t s) { launch_set_step(h->ctrl, t0 + 1, 0, s); });
-      TRY(run_graph(h, "fwd_u_" + std::to_string(n) + (pack ? "p" : ""), st, [&](Launcher& L) {
+      TRY(run_graph(h, "fwd_u_" + std::to_string(n) + (do_pack ? "p" : ""), st, [&](Launcher& L) {
         enqueue_fwd_steps<T>(h, L, S, n, false);
-        if (pack)
-          L("ckpt", [&](cudaStream_t s) { launch_ckpt_pack<T>(g, S, (T*)h->ckpt, h->slot_elems, every, h->ctrl, n - 1, s); });
+        if (do_pack) pack(L, n - 1);
       }));
     }
   }
@@ -358,8 +373,16 @@ int adjoint_impl(lks_handle* h, double seed, cudaStream_t st) {
     for (int c = nseg - 1; c >= 0; --c) {
       const int t0 = c * every;
       const int n = std::min(every, NT - t0);
-      CK(cudaMemcpyAsync(h->ring, (char*)h->ckpt + (size_t)c * h->slot_elems * h->esz, h->slot_elems * h->esz,
-                         cudaMemcpyDeviceToDevice, st));
+      if (h->P.ckpt_format == LKS_CKPT_NATIVE) {
+        CK(cudaMemcpyAsync(h->ring, (char*)h->ckpt + (size_t)c * h->slot_elems * h->esz, h->slot_elems * h->esz,
+                           cudaMemcpyDeviceToDevice, st));
+      } else if (c == 0) {
+        L0("ckpt", [&](cudaStream_t s) { launch_state_from_double<T>(g, (T*)h->ring, h->init_p, h->init_u, s); });
+      } else {
+        L0("ckpt", [&](cudaStream_t s) {
+          launch_ckpt_restore_q(g, (float*)h->ring, h->ckq, h->ckkeys, h->P.ckpt_format, c, s);
+        });
+      }
       L0("init", [&](cudaStream_t s) { launch_set_step(h->ctrl, t0 + 1, t0, s); });
       TRY(run_graph(h, "rec_" + std::to_string(n), st, [&](Launcher& L) { enqueue_recompute<T>(h, L, S, n); }));
       L0("init", [&](cudaStream_t s) { launch_set_step(h->ctrl, t0 + n, t0, s); });
@@ -386,7 +409,12 @@ int allocate(lks_handle* h) {
     h->nbox = P.ckpt_every;
     h->nckpt = (NT + P.ckpt_every - 1) / P.ckpt_every;
     TRY(dalloc(h, &h->pp, 2 * slot_bytes));
-    TRY(dalloc(h, &h->ckpt, (size_t)h->nckpt * slot_bytes));
+    if (P.ckpt_format == LKS_CKPT_NATIVE) {
+      TRY(dalloc(h, &h->ckpt, (size_t)h->nckpt * slot_bytes));
+    } else {
+      TRY(dalloc(h, (void**)&h->ckq, (size_t)h->nckpt * h->slot_elems * sizeof(unsigned short)));
+      TRY(dalloc(h, (void**)&h->ckkeys, (size_t)h->nckpt * (D + 1) * 2 * sizeof(unsigned)));
+    }
   }
   TRY(dalloc(h, &h->ring, (size_t)h->nring * slot_bytes));
   TRY(dalloc(h, &h->boxstore, (size_t)h->nbox * g.box_cells * D * sizeof(T)));
@@ -401,7 +429,7 @@ int allocate(lks_handle* h) {
   TRY(dalloc(h, (void**)&h->ctrl, sizeof(Ctrl)));
   TRY(dalloc(h, (void**)&h->mom, sizeof(Moments)));
   const long long bx = ((g.B[0] + kBoxCtaCellsX - 1) / kBoxCtaCellsX) * (long long)((g.B[1] + kBoxCtaCellsY - 1) / kBoxCtaCellsY) * g.B[2];
-  const long long bd = ((long long)g.ND * 4 + 255) / 256;
+  const long long bd = ((long long)g.ND + kDesignPointsPerCta - 1) / kDesignPointsPerCta;
   const long long nblk = std::max(bx, bd) + 1;
   TRY(dalloc(h, (void**)&h->partials, (size_t)nblk * 8 * sizeof(double)));
   TRY(dalloc(h, (void**)&h->init_p, (size_t)g.N * sizeof(double)));

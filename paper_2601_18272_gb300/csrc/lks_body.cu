@@ -27,8 +27,30 @@ namespace lks {
 
 namespace {
 
-constexpr int BX = 32, BY = 8;  // grid form: one thread per box cell, 32 x 8 cells per CTA
-constexpr int kDesignBlock = 256;
+// Box-cell kernels: LN consecutive threads share one cell's gather (candidate rows split among
+// them), CX x CY cells per CTA. Design-point kernel: LN threads per point (rows, or planes in 3D,
+// of its support window), kDesignPointsPerCta points per CTA. The split multiplies the resident
+// warps of these latency-bound kernels by LN.
+constexpr int LN = kLanesPerCell;
+constexpr int CX = kBoxCtaCellsX, CY = kBoxCtaCellsY;
+constexpr int kCellThreads = CX * CY * LN;
+constexpr int kDesignBlock = kDesignPointsPerCta * LN;
+constexpr int kFinishThreads = 256;
+
+struct CellSlot {
+  int j0, j1, j2, lane;
+  bool active;  // inside the box
+};
+__device__ __forceinline__ CellSlot cell_slot(const Geo& g) {
+  CellSlot c;
+  const int q = threadIdx.x / LN;
+  c.lane = threadIdx.x % LN;
+  c.j0 = blockIdx.x * CX + q % CX;
+  c.j1 = blockIdx.y * CY + q / CX;
+  c.j2 = blockIdx.z;
+  c.active = c.j0 < g.B[0] && c.j1 < g.B[1];
+  return c;
+}
 
 __device__ __forceinline__ int block_linear() { return blockIdx.x + gridDim.x * (blockIdx.y + gridDim.y * blockIdx.z); }
 
@@ -55,14 +77,17 @@ __device__ __forceinline__ void lam_store(Ctrl* ctrl, const double* lF, double l
   ctrl->lam_Tf = (float)lT;
 }
 
-// Forward coupling work for box cell (j0, j1, j2); adds kappa_n u_n and the torque density to v.
-// On the last iteration writes u(t) into dst and, if bs is set, the predictor u* into the box store.
+// Forward coupling work for box cell (j0, j1, j2), called by all LN lanes of the cell (every
+// thread of the warp must call it: the gather combines lanes with shuffles); lane 0 adds
+// kappa_n u_n and the torque density to v. On the last iteration lane 0 writes u(t) into dst and,
+// if bs is set, the predictor u* into the box store.
 template <typename T, int D, int AX>
 __device__ __forceinline__ void couple_cell(const Geo& g, const T* __restrict__ kref, const Dof& sk, const int (&lo)[3],
-                                            int j0, int j1, int j2, T* __restrict__ dst, T* __restrict__ bs, bool last,
+                                            const CellSlot& cc, T* __restrict__ dst, T* __restrict__ bs, bool last,
                                             int* status, T* v) {
   constexpr int b = Axes<AX>::B, c = Axes<AX>::C;
   const long long N = g.N;
+  const int j0 = cc.j0, j1 = cc.j1, j2 = cc.j2;
   const int px = lo[0] + j0, py = lo[1] + j1, pz = lo[2] + j2;
   long long n = 0;
   const bool ing = cell_index<D>(g, px, py, pz, n);
@@ -70,7 +95,8 @@ __device__ __forceinline__ void couple_cell(const Geo& g, const T* __restrict__ 
   const T d[3] = {V.rel(0, px), V.rel(1, py), D == 3 ? V.rel(2, pz) : T(0)};
   const T cs = V.cs, sn = V.sn;
   Acc<T> A;
-  gather<T, D, AX>(g, kref, d, cs, sn, A);
+  gather_lanes<T, D, AX, LN>(g, kref, d, cs, sn, cc.lane, cc.active, A);
+  if (!cc.active || cc.lane != 0) return;
   if (A.phi > T(0) && (!ing || forbidden<D>(g, px, py, pz))) atomicOr(status, ST_BODY_OUTSIDE);
   if (!ing) return;
   T dwr[3], L[3], u[3] = {T(0), T(0), T(0)};
@@ -110,32 +136,36 @@ __device__ __forceinline__ void couple_finish(const Geo& g, const Moments* mom, 
   bool finite = isfinite(Tq);
   for (int a = 0; a < D; ++a) finite = finite && isfinite(F[a]);
   if (!finite) *status |= ST_NONFINITE;
-  eom_update(g, s0, F, Tq, nx);
+  eom_update<D>(g, s0, F, Tq, nx);
   for (int a = 0; a < D; ++a)
     if (fabs(nx->s[a] - s0.s[a]) > (double)g.margin) *status |= ST_BOX_OVERFLOW;
 }
 
 // Reverse of coupling iteration k for box cell (j0, j1, j2). Scratch planes per box cell:
 //   [0, D): u^(k);  D: dJ/dkappa_n;  [D+1, 2D+1): dJ/du^S_n.  acc accumulates dJ/du*.
+// Called by all LN lanes of the cell (see couple_cell); lane 0 does the per-cell work.
 template <typename T, int D, int AX>
 __device__ __forceinline__ void adj_cell_work(const Geo& g, const T* __restrict__ kref, const Dof& sk,
-                                              const int (&lo)[3], int j0, int j1, int j2, const T* __restrict__ bs,
+                                              const int (&lo)[3], const CellSlot& cc, const T* __restrict__ bs,
                                               T* Lcur, T* __restrict__ acc, T* __restrict__ scratch, int k, int K,
                                               const T (&lF)[3], T lT) {
   constexpr int b = Axes<AX>::B, c = Axes<AX>::C;
   const long long N = g.N, BC = g.box_cells;
+  const int j0 = cc.j0, j1 = cc.j1, j2 = cc.j2;
   const long long bl = j0 + (long long)g.B[0] * (j1 + (long long)g.B[1] * j2);
   const int px = lo[0] + j0, py = lo[1] + j1, pz = lo[2] + j2;
   long long n = 0;
-  if (!cell_index<D>(g, px, py, pz, n)) {
-    for (int q = 0; q < 2 * D + 1; ++q) scratch[q * BC + bl] = T(0);
-    return;
-  }
+  const bool ing = cell_index<D>(g, px, py, pz, n);
   const DofView<T> V(sk);
   const T d[3] = {V.rel(0, px), V.rel(1, py), D == 3 ? V.rel(2, pz) : T(0)};
   const T cs = V.cs, sn = V.sn;
   Acc<T> A;
-  gather<T, D, AX>(g, kref, d, cs, sn, A);
+  gather_lanes<T, D, AX, LN>(g, kref, d, cs, sn, cc.lane, cc.active && ing, A);
+  if (!cc.active || cc.lane != 0) return;
+  if (!ing) {
+    for (int q = 0; q < 2 * D + 1; ++q) scratch[q * BC + bl] = T(0);
+    return;
+  }
   T dwr[3], L[3];
   drot<AX>(cs, sn, A.wr, dwr);
   rot<AX>(cs, sn, A.kr, L);
@@ -165,22 +195,25 @@ __device__ __forceinline__ void adj_cell_work(const Geo& g, const T* __restrict_
 }
 
 // Reverse of coupling iteration k for design point m: dJ/dkappa^ref_m += ..., and the point's
-// contribution to dJ/ds^(k-1) added to v[8] = (xG[3], uG[3], theta, omega). Returns false if the
-// support window left the body box.
+// contribution to dJ/ds^(k-1) added to v[8] = (xG[3], uG[3], theta, omega). Called by all LN lanes
+// of the point (each takes one row, or in 3D one plane, of the support window; every thread of the
+// warp must call it); lane 0 finishes the point. Returns false if the support window left the
+// body box.
 template <typename T, int D, int AX>
 __device__ __forceinline__ bool adj_design_point(const Geo& g, const T* __restrict__ kref, const T* scratch,
-                                                 const Dof& sk, const int (&lo)[3], int m, const T (&lF)[3], T lT,
-                                                 double* __restrict__ dkref, T* v) {
+                                                 const Dof& sk, const int (&lo)[3], int m, bool valid, int lane,
+                                                 const T (&lF)[3], T lT, double* __restrict__ dkref, T* v) {
   constexpr int b = Axes<AX>::B, c = Axes<AX>::C, ax = Axes<AX>::A;
   const long long BC = g.box_cells;
-  const int ix = m % g.nd[0], iy = (m / g.nd[0]) % g.nd[1], iz = m / (g.nd[0] * g.nd[1]);
+  const int mm = valid ? m : 0;
+  const int ix = mm % g.nd[0], iy = (mm / g.nd[0]) % g.nd[1], iz = mm / (g.nd[0] * g.nd[1]);
   const T r[3] = {(T)ix - pivot<T>(g, 0), (T)iy - pivot<T>(g, 1), D == 3 ? (T)iz - pivot<T>(g, 2) : T(0)};
   const DofView<T> V(sk);
   const T cs = V.cs, sn = V.sn, om = V.om;
   T l[3], dl[3];
   rot<AX>(cs, sn, r, l);
   drot<AX>(cs, sn, r, dl);
-  const T km = kref[m];
+  const T km = kref[mm];
   T usr[3] = {T(0), T(0), T(0)}, luref[3] = {T(0), T(0), T(0)}, rotl[3] = {T(0), T(0), T(0)};
 #pragma unroll
   for (int a = 0; a < D; ++a) usr[a] = V.ug[a] + om * dl[a];
@@ -194,6 +227,9 @@ __device__ __forceinline__ bool adj_design_point(const Geo& g, const T* __restri
 #pragma unroll
   for (int a = 0; a < D; ++a) V.split(a, l[a], &f[a], &fr[a]);
   const int S2 = 2 * g.s;
+  // kernel weights along each axis of the window; the axis E split across the lanes only needs
+  // this lane's entry (q = lane)
+  constexpr int E = (D == 3) ? 2 : 1;
   T wv[3][4], dwv[3][4];
 #pragma unroll
   for (int a = 0; a < 3; ++a)
@@ -203,7 +239,8 @@ __device__ __forceinline__ bool adj_design_point(const Geo& g, const T* __restri
       dwv[a][q] = T(0);
     }
 #pragma unroll
-  for (int a = 0; a < D; ++a)
+  for (int a = 0; a < D; ++a) {
+    if (a == E) continue;
 #pragma unroll
     for (int q = 0; q < 4; ++q) {
       const T rr = (T)(q - g.s + 1) - fr[a];  // x_n - x^ref along a
@@ -212,48 +249,72 @@ __device__ __forceinline__ bool adj_design_point(const Geo& g, const T* __restri
         dwv[a][q] = dwfun(g.wk, rr);
       }
     }
+  }
+  T we = T(0), dwe = T(0);
+  {
+    const T rr = (T)(lane - g.s + 1) - fr[E];
+    if (lane < S2 && fabs(rr) < (T)g.s) {
+      we = wfun(g.wk, rr);
+      dwe = dwfun(g.wk, rr);
+    }
+  }
   T uref[3] = {T(0), T(0), T(0)}, slus[3] = {T(0), T(0), T(0)}, lxr[3] = {T(0), T(0), T(0)};
   T slk = T(0);
   bool inside = true;
   const int B0 = g.B[0], B1 = g.B[1], B2 = (D == 3) ? g.B[2] : 1;
+  // this lane's part of the window: row q1 = lane (2D) or plane q2 = lane (3D)
 #pragma unroll
-  for (int q2 = 0; q2 < (D == 3 ? 4 : 1); ++q2)
+  for (int u = 0; u < (D == 3 ? 4 : 1); ++u)
 #pragma unroll
-    for (int q1 = 0; q1 < 4; ++q1)
-#pragma unroll
-      for (int q0 = 0; q0 < 4; ++q0) {
-        if (q0 >= S2 || q1 >= S2 || (D == 3 && q2 >= S2)) continue;
-        const T w0 = wv[0][q0], w1 = wv[1][q1], w2 = wv[2][q2];
-        const T W = w0 * w1 * w2;
-        const T dW0 = dwv[0][q0] * w1 * w2, dW1 = w0 * dwv[1][q1] * w2, dW2 = w0 * w1 * dwv[2][q2];
-        if (W == T(0) && dW0 == T(0) && dW1 == T(0) && dW2 == T(0)) continue;
-        const int p0 = f[0] - g.s + 1 + q0 - lo[0], p1 = f[1] - g.s + 1 + q1 - lo[1];
-        const int p2 = (D == 3) ? f[2] - g.s + 1 + q2 - lo[2] : 0;
-        if (p0 < 0 || p0 >= B0 || p1 < 0 || p1 >= B1 || p2 < 0 || p2 >= B2) {
-          inside = false;
-          continue;
-        }
-        const long long bl = p0 + (long long)B0 * (p1 + (long long)B1 * p2);
-        T uk[3] = {T(0), T(0), T(0)}, lus[3] = {T(0), T(0), T(0)};
-#pragma unroll
-        for (int a = 0; a < D; ++a) {
-          uk[a] = __ldcg(&scratch[a * BC + bl]);
-          lus[a] = __ldcg(&scratch[(D + 1 + a) * BC + bl]);
-        }
-        const T lk = __ldcg(&scratch[D * BC + bl]);
-        T qv = km * lk;
-#pragma unroll
-        for (int a = 0; a < D; ++a) {
-          uref[a] += W * uk[a];
-          slus[a] += W * lus[a];
-          qv += luref[a] * uk[a] + usr[a] * lus[a];
-        }
-        slk += W * lk;
-        // dW/dx^ref_e = -w'(x_e - x^ref_e) prod_{a != e} w
-        lxr[0] -= dW0 * qv;
-        lxr[1] -= dW1 * qv;
-        lxr[2] -= dW2 * qv;
+    for (int q0 = 0; q0 < 4; ++q0) {
+      const int q1 = (D == 3) ? u : lane, q2 = (D == 3) ? lane : 0;
+      if (!valid || q0 >= S2 || q1 >= S2 || (D == 3 && q2 >= S2)) continue;
+      const T w0 = wv[0][q0];
+      const T w1 = (E == 1) ? we : wv[1][u], dw1 = (E == 1) ? dwe : dwv[1][u];
+      const T w2 = (E == 2) ? we : T(1), dw2 = (E == 2) ? dwe : T(0);
+      const T W = w0 * w1 * w2;
+      const T dW0 = dwv[0][q0] * w1 * w2, dW1 = w0 * dw1 * w2, dW2 = w0 * w1 * dw2;
+      if (W == T(0) && dW0 == T(0) && dW1 == T(0) && dW2 == T(0)) continue;
+      const int p0 = f[0] - g.s + 1 + q0 - lo[0], p1 = f[1] - g.s + 1 + q1 - lo[1];
+      const int p2 = (D == 3) ? f[2] - g.s + 1 + q2 - lo[2] : 0;
+      if (p0 < 0 || p0 >= B0 || p1 < 0 || p1 >= B1 || p2 < 0 || p2 >= B2) {
+        inside = false;
+        continue;
       }
+      const long long bl = p0 + (long long)B0 * (p1 + (long long)B1 * p2);
+      T uk[3] = {T(0), T(0), T(0)}, lus[3] = {T(0), T(0), T(0)};
+#pragma unroll
+      for (int a = 0; a < D; ++a) {
+        uk[a] = __ldcg(&scratch[a * BC + bl]);
+        lus[a] = __ldcg(&scratch[(D + 1 + a) * BC + bl]);
+      }
+      const T lk = __ldcg(&scratch[D * BC + bl]);
+      T qv = km * lk;
+#pragma unroll
+      for (int a = 0; a < D; ++a) {
+        uref[a] += W * uk[a];
+        slus[a] += W * lus[a];
+        qv += luref[a] * uk[a] + usr[a] * lus[a];
+      }
+      slk += W * lk;
+      // dW/dx^ref_e = -w'(x_e - x^ref_e) prod_{a != e} w
+      lxr[0] -= dW0 * qv;
+      lxr[1] -= dW1 * qv;
+      lxr[2] -= dW2 * qv;
+    }
+  // combine the LN lanes of this point (consecutive lanes of one warp)
+#pragma unroll
+  for (int off = 1; off < LN; off <<= 1) {
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+      uref[a] += __shfl_xor_sync(0xffffffffu, uref[a], off);
+      slus[a] += __shfl_xor_sync(0xffffffffu, slus[a], off);
+      lxr[a] += __shfl_xor_sync(0xffffffffu, lxr[a], off);
+    }
+    slk += __shfl_xor_sync(0xffffffffu, slk, off);
+    inside = __shfl_xor_sync(0xffffffffu, (int)inside, off) && inside;
+  }
+  if (!valid || lane != 0) return true;
   T Dl[3] = {T(0), T(0), T(0)};
 #pragma unroll
   for (int a = 0; a < D; ++a) Dl[a] = uref[a] - usr[a];
@@ -339,7 +400,7 @@ __global__ void __launch_bounds__(256) k_prep(Geo g, const double* __restrict__ 
 // ---- grid form ----------------------------------------------------------------------------
 
 template <typename T, int D, int AX>
-__global__ void __launch_bounds__(BX* BY) k_couple(Geo g, Slots<T> S, Ctrl* ctrl, Dof* it, const T* __restrict__ kref,
+__global__ void __launch_bounds__(kCellThreads) k_couple(Geo g, Slots<T> S, Ctrl* ctrl, Dof* it, const T* __restrict__ kref,
                                                     const Moments* __restrict__ mom, void* partials, int k,
                                                     T* __restrict__ boxstore, int nbox, int di) {
   __shared__ double red[32 * 4];
@@ -350,25 +411,35 @@ __global__ void __launch_bounds__(BX* BY) k_couple(Geo g, Slots<T> S, Ctrl* ctrl
   int lo[3];
   box_origin<D>(g, s0, lo[0], lo[1], lo[2]);
   T* bs = (boxstore && k == K) ? boxstore + (long long)((t - base - 1) % nbox) * g.box_cells * D : nullptr;
-  const int j0 = blockIdx.x * BX + threadIdx.x, j1 = blockIdx.y * BY + threadIdx.y, j2 = blockIdx.z;
+  const CellSlot cc = cell_slot(g);
   T v[4] = {T(0), T(0), T(0), T(0)};
-  if (j0 < g.B[0] && j1 < g.B[1]) couple_cell<T, D, AX>(g, kref, sk, lo, j0, j1, j2, dst, bs, k == K, &ctrl->status, v);
+  couple_cell<T, D, AX>(g, kref, sk, lo, cc, dst, bs, k == K, &ctrl->status, v);
   block_sum_partial<4>(v, static_cast<typename Partial<T>::type*>(partials) + block_linear() * 4, red);
 }
 
-// Sum of the coupling partials and the EOM update: iterate s^(k) of step t. One warp.
+// Sum of the coupling partials and the EOM update: iterate s^(k) of step t.
 template <typename T, int D, int AX>
-__global__ void __launch_bounds__(32) k_couple_finish(Geo g, Ctrl* ctrl, Dof* it, const Moments* __restrict__ mom,
-                                                       const void* __restrict__ partials, int nparts, int k, int di) {
+__global__ void __launch_bounds__(kFinishThreads) k_couple_finish(Geo g, Ctrl* ctrl, Dof* it,
+                                                                   const Moments* __restrict__ mom,
+                                                                   const void* __restrict__ partials, int nparts, int k,
+                                                                   int di) {
+  __shared__ double red[32 * 4];
   const int t = ctrl->t0 + di, K = g.K;
   Dof* row = it + (long long)(t - 1) * (K + 1);
-  double s[4];
-  warp_sum_partials<4>(static_cast<const typename Partial<T>::type*>(partials), nparts, s);
+  // thread 0 fetches what the EOM needs before the reduction, so the loads overlap it
+  Dof s0, sk;
+  Moments m;
   if (threadIdx.x == 0) {
-    const Dof s0 = row[0], sk = row[k - 1];
+    s0 = row[0];
+    sk = row[k - 1];
+    m = *mom;
+  }
+  double s[4];
+  block_sum_partials<4>(static_cast<const typename Partial<T>::type*>(partials), nparts, s, red);
+  if (threadIdx.x == 0) {
     Dof nx;
     int st = 0;
-    couple_finish<D, AX>(g, mom, s0, sk, s, &nx, &st);
+    couple_finish<D, AX>(g, &m, s0, sk, s, &nx, &st);
     if (st) ctrl->status |= st;
     row[k] = nx;
     if (k == K) it[(long long)t * (K + 1)] = nx;
@@ -377,7 +448,7 @@ __global__ void __launch_bounds__(32) k_couple_finish(Geo g, Ctrl* ctrl, Dof* it
 
 // Recompute of one step's Brinkman update from the stored iterate s^(K-1).
 template <typename T, int D, int AX>
-__global__ void __launch_bounds__(BX* BY) k_apply(Geo g, Slots<T> S, const Ctrl* ctrl, const Dof* it,
+__global__ void __launch_bounds__(kCellThreads) k_apply(Geo g, Slots<T> S, const Ctrl* ctrl, const Dof* it,
                                                    const T* __restrict__ kref, T* __restrict__ boxstore, int nbox,
                                                    int di) {
   const int t = ctrl->t0 + di, base = ctrl->base, K = g.K;
@@ -387,16 +458,17 @@ __global__ void __launch_bounds__(BX* BY) k_apply(Geo g, Slots<T> S, const Ctrl*
   const long long N = g.N;
   int lo[3];
   box_origin<D>(g, s0, lo[0], lo[1], lo[2]);
-  const int j0 = blockIdx.x * BX + threadIdx.x, j1 = blockIdx.y * BY + threadIdx.y, j2 = blockIdx.z;
-  if (j0 >= g.B[0] || j1 >= g.B[1]) return;
+  const CellSlot cc = cell_slot(g);
+  const int j0 = cc.j0, j1 = cc.j1, j2 = cc.j2;
   const int px = lo[0] + j0, py = lo[1] + j1, pz = lo[2] + j2;
   long long n = 0;
-  if (!cell_index<D>(g, px, py, pz, n)) return;
+  const bool ing = cell_index<D>(g, px, py, pz, n);
   const DofView<T> V(sk);
   const T d[3] = {V.rel(0, px), V.rel(1, py), D == 3 ? V.rel(2, pz) : T(0)};
   const T cs = V.cs, sn = V.sn;
   Acc<T> A;
-  gather<T, D, AX>(g, kref, d, cs, sn, A);
+  gather_lanes<T, D, AX, LN>(g, kref, d, cs, sn, cc.lane, cc.active && ing, A);
+  if (!cc.active || !ing || cc.lane != 0) return;
   T dwr[3];
   drot<AX>(cs, sn, A.wr, dwr);
   const T om = V.om;
@@ -413,7 +485,7 @@ __global__ void __launch_bounds__(BX* BY) k_apply(Geo g, Slots<T> S, const Ctrl*
 }
 
 template <typename T, int D, int AX>
-__global__ void __launch_bounds__(BX* BY) k_adj_cell(Geo g, const Ctrl* ctrl, const Dof* it, const T* __restrict__ kref,
+__global__ void __launch_bounds__(kCellThreads) k_adj_cell(Geo g, const Ctrl* ctrl, const Dof* it, const T* __restrict__ kref,
                                                       const T* __restrict__ boxstore, int nbox, T* Lb,
                                                       long long lstride, T* __restrict__ acc, T* __restrict__ scratch,
                                                       int k, int di) {
@@ -425,10 +497,9 @@ __global__ void __launch_bounds__(BX* BY) k_adj_cell(Geo g, const Ctrl* ctrl, co
   T* Lcur = Lb + (long long)(t & 1) * lstride;
   int lo[3];
   box_origin<D>(g, s0, lo[0], lo[1], lo[2]);
-  const int j0 = blockIdx.x * BX + threadIdx.x, j1 = blockIdx.y * BY + threadIdx.y, j2 = blockIdx.z;
-  if (j0 >= g.B[0] || j1 >= g.B[1]) return;
+  const CellSlot cc = cell_slot(g);
   const T* bs = boxstore + (long long)((t - base - 1) % nbox) * g.box_cells * D;
-  adj_cell_work<T, D, AX>(g, kref, sk, lo, j0, j1, j2, bs, Lcur, acc, scratch, k, K, lF, lT);
+  adj_cell_work<T, D, AX>(g, kref, sk, lo, cc, bs, Lcur, acc, scratch, k, K, lF, lT);
 }
 
 template <typename T, int D, int AX>
@@ -445,22 +516,25 @@ __global__ void __launch_bounds__(kDesignBlock) k_adj_design(Geo g, Ctrl* ctrl, 
   lam_load<T>(ctrl, lF, lT);
   int lo[3];
   box_origin<D>(g, s0, lo[0], lo[1], lo[2]);
-  const int m = blockIdx.x * blockDim.x + threadIdx.x;
+  const int m = blockIdx.x * kDesignPointsPerCta + threadIdx.x / LN, lane = threadIdx.x % LN;
   T v[8] = {T(0), T(0), T(0), T(0), T(0), T(0), T(0), T(0)};
-  if (m < g.ND && !adj_design_point<T, D, AX>(g, kref, scratch, sk, lo, m, lF, lT, dkref, v))
+  if (!adj_design_point<T, D, AX>(g, kref, scratch, sk, lo, m, m < g.ND, lane, lF, lT, dkref, v))
     atomicOr(&ctrl->status, ST_BOX_OVERFLOW);
   block_sum_partial<8>(v, static_cast<typename Partial<T>::type*>(partials) + blockIdx.x * 8, red);
 }
 
-// Sum of the design-point partials and the EOM reverse (adj_finish). One warp.
+// Sum of the design-point partials and the EOM reverse (adj_finish).
 template <typename T>
-__global__ void __launch_bounds__(32) k_design_finish(Geo g, Ctrl* ctrl, const void* __restrict__ partials,
-                                                      int nparts, int k) {
-  double ls[8];
-  warp_sum_partials<8>(static_cast<const typename Partial<T>::type*>(partials), nparts, ls);
-  if (threadIdx.x == 0) {
-    double lp[8], nF[3], nT;
+__global__ void __launch_bounds__(kFinishThreads) k_design_finish(Geo g, Ctrl* ctrl, const void* __restrict__ partials,
+                                                                  int nparts, int k) {
+  __shared__ double red[32 * 8];
+  double lp[8];  // thread 0 fetches the carried adjoint before the reduction
+  if (threadIdx.x == 0)
     for (int a = 0; a < 8; ++a) lp[a] = ctrl->lam_prev[a];
+  double ls[8];
+  block_sum_partials<8>(static_cast<const typename Partial<T>::type*>(partials), nparts, ls, red);
+  if (threadIdx.x == 0) {
+    double nF[3], nT;
     adj_finish(g, k, ls, lp, nF, &nT, ctrl->lam_s0);
     for (int a = 0; a < 8; ++a) ctrl->lam_prev[a] = lp[a];
     lam_store(ctrl, nF, nT);
@@ -526,7 +600,7 @@ __global__ void k_ckpt_pack(Geo g, Slots<T> S, T* ckpt, long long cstride, int e
 }
 
 inline dim3 box_grid(const Geo& g) {
-  return dim3((g.B[0] + BX - 1) / BX, (g.B[1] + BY - 1) / BY, g.dim == 3 ? g.B[2] : 1);
+  return dim3((g.B[0] + CX - 1) / CX, (g.B[1] + CY - 1) / CY, g.dim == 3 ? g.B[2] : 1);
 }
 
 }  // namespace
@@ -535,70 +609,70 @@ inline dim3 box_grid(const Geo& g) {
 #define LKS_BOX_DISPATCH(KERNEL, GRID, BLOCK, ...)          \
   do {                                                      \
     if (g.dim == 2)                                         \
-      KERNEL<T, 2, 2><<<GRID, BLOCK, 0, st>>>(__VA_ARGS__); \
+      launch(KERNEL<T, 2, 2>, GRID, BLOCK, 0, st, __VA_ARGS__); \
     else if (g.ax == 0)                                     \
-      KERNEL<T, 3, 0><<<GRID, BLOCK, 0, st>>>(__VA_ARGS__); \
+      launch(KERNEL<T, 3, 0>, GRID, BLOCK, 0, st, __VA_ARGS__); \
     else if (g.ax == 1)                                     \
-      KERNEL<T, 3, 1><<<GRID, BLOCK, 0, st>>>(__VA_ARGS__); \
+      launch(KERNEL<T, 3, 1>, GRID, BLOCK, 0, st, __VA_ARGS__); \
     else                                                    \
-      KERNEL<T, 3, 2><<<GRID, BLOCK, 0, st>>>(__VA_ARGS__); \
+      launch(KERNEL<T, 3, 2>, GRID, BLOCK, 0, st, __VA_ARGS__); \
   } while (0)
 
 
 template <typename T>
 void launch_prep(const Geo& g, const double* gamma, double kappa_max, double q, T* kref, Moments* mom,
                  double* partials, Ctrl* ctrl, cudaStream_t st) {
-  k_prep<T><<<(g.ND + 255) / 256, 256, 0, st>>>(g, gamma, kappa_max, q, kref, mom, partials, ctrl);
+  launch(k_prep<T>, (g.ND + 255) / 256, 256, 0, st, g, gamma, kappa_max, q, kref, mom, partials, ctrl);
 }
 
 template <typename T>
 void launch_couple(const Geo& g, const Slots<T>& S, Ctrl* ctrl, Dof* it, const T* kref, const Moments* mom,
                    void* partials, int k, T* boxstore, int nbox, int di, cudaStream_t st) {
   const dim3 grid = box_grid(g);
-  LKS_BOX_DISPATCH(k_couple, grid, dim3(BX, BY), g, S, ctrl, it, kref, mom, partials, k, boxstore, nbox, di);
+  LKS_BOX_DISPATCH(k_couple, grid, kCellThreads, g, S, ctrl, it, kref, mom, partials, k, boxstore, nbox, di);
   const int nparts = (int)(grid.x * grid.y * grid.z);
-  LKS_BOX_DISPATCH(k_couple_finish, 1, 32, g, ctrl, it, mom, partials, nparts, k, di);
+  LKS_BOX_DISPATCH(k_couple_finish, 1, kFinishThreads, g, ctrl, it, mom, partials, nparts, k, di);
 }
 
 template <typename T>
 void launch_apply(const Geo& g, const Slots<T>& S, const Ctrl* ctrl, const Dof* it, const T* kref, T* boxstore,
                   int nbox, int di, cudaStream_t st) {
-  LKS_BOX_DISPATCH(k_apply, box_grid(g), dim3(BX, BY), g, S, ctrl, it, kref, boxstore, nbox, di);
+  LKS_BOX_DISPATCH(k_apply, box_grid(g), kCellThreads, g, S, ctrl, it, kref, boxstore, nbox, di);
 }
 
 template <typename T>
 void launch_adj_cell(const Geo& g, const Ctrl* ctrl, const Dof* it, const T* kref, const T* boxstore, int nbox, T* Lb,
                      long long lstride, T* acc, T* scratch, int k, int di, cudaStream_t st) {
-  LKS_BOX_DISPATCH(k_adj_cell, box_grid(g), dim3(BX, BY), g, ctrl, it, kref, boxstore, nbox, Lb, lstride, acc,
+  LKS_BOX_DISPATCH(k_adj_cell, box_grid(g), kCellThreads, g, ctrl, it, kref, boxstore, nbox, Lb, lstride, acc,
                    scratch, k, di);
 }
 
 template <typename T>
 void launch_adj_design(const Geo& g, Ctrl* ctrl, const Dof* it, const T* kref, const T* scratch, double* dkref,
                        void* partials, int k, int di, cudaStream_t st) {
-  const unsigned nb = (unsigned)((g.ND + kDesignBlock - 1) / kDesignBlock);
+  const unsigned nb = (unsigned)((g.ND + kDesignPointsPerCta - 1) / kDesignPointsPerCta);
   LKS_BOX_DISPATCH(k_adj_design, nb, kDesignBlock, g, ctrl, it, kref, scratch, dkref, partials, k, di);
-  k_design_finish<T><<<1, 32, 0, st>>>(g, ctrl, partials, (int)nb, k);
+  launch(k_design_finish<T>, 1, kFinishThreads, 0, st, g, ctrl, (const void*)partials, (int)nb, k);
 }
 
 template <typename T>
 void launch_init_forward(const Geo& g, const Slots<T>& S, const double* p0, const double* u0, const double* s0dev,
                          Dof* it, Ctrl* ctrl, cudaStream_t st) {
   const long long nb = (g.N + 255) / 256;
-  k_init_forward<T><<<(unsigned)(nb < 4096 ? nb : 4096), 256, 0, st>>>(g, S, p0, u0, s0dev, it, ctrl);
+  launch(k_init_forward<T>, (unsigned)(nb < 4096 ? nb : 4096), 256, 0, st, g, S, p0, u0, s0dev, it, ctrl);
 }
 
-void launch_set_step(Ctrl* ctrl, int t0, int base, cudaStream_t st) { k_set_step<<<1, 1, 0, st>>>(ctrl, t0, base); }
+void launch_set_step(Ctrl* ctrl, int t0, int base, cudaStream_t st) { launch(k_set_step, 1, 1, 0, st, ctrl, t0, base); }
 
 void launch_adj_init(const Geo& g, Ctrl* ctrl, const double* objw, double seed, double* dkref, int nd,
                      cudaStream_t st) {
   cudaMemsetAsync(dkref, 0, sizeof(double) * (size_t)nd, st);
-  k_adj_init<<<1, 1, 0, st>>>(g, ctrl, objw, seed);
+  launch(k_adj_init, 1, 1, 0, st, g, ctrl, objw, seed);
 }
 
 void launch_sensitivity(const Geo& g, const double* gamma, const double* dkref, double kappa_max, double q,
                         double* out, cudaStream_t st) {
-  k_sensitivity<<<(g.ND + 255) / 256, 256, 0, st>>>(g.ND, gamma, dkref, kappa_max, q, out);
+  launch(k_sensitivity, (g.ND + 255) / 256, 256, 0, st, g.ND, gamma, dkref, kappa_max, q, out);
 }
 
 template <typename T>
@@ -606,7 +680,7 @@ void launch_ckpt_pack(const Geo& g, const Slots<T>& S, T* ckpt, long long cstrid
                       cudaStream_t st) {
   const long long M = (long long)(g.dim + 1) * g.N;
   const long long nb = (M + 255) / 256;
-  k_ckpt_pack<T><<<(unsigned)(nb < 8192 ? nb : 8192), 256, 0, st>>>(g, S, ckpt, cstride, every, ctrl, di);
+  launch(k_ckpt_pack<T>, (unsigned)(nb < 8192 ? nb : 8192), 256, 0, st, g, S, ckpt, cstride, every, ctrl, di);
 }
 
 #define LKS_INST(T)                                                                                                 \

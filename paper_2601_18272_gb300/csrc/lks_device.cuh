@@ -18,6 +18,7 @@ namespace lks {
 enum { BC_PERIODIC = 0, BC_INFLOW_OUTFLOW = 1, BC_WALL = 2, BC_PRESSURE = 3 };
 enum { W_COS4 = 0, W_BILINEAR = 1 };
 enum { DOF_TX = 1, DOF_TY = 2, DOF_TZ = 4, DOF_ROT = 8 };
+enum { CKQ_BF16 = 1, CKQ_FP16 = 2 };  // reduced-precision checkpoint formats
 enum { ST_BODY_OUTSIDE = 1, ST_NONFINITE = 2, ST_BOX_OVERFLOW = 4 };
 enum { CNT_COUPLE = 0, CNT_APPLY = 1, CNT_DESIGN = 2, CNT_ADJ_STENCIL = 3, CNT_PREP = 4, CNT_CKPT = 5, CNT_N = 8 };
 
@@ -34,6 +35,7 @@ struct Dof {
 };
 
 __host__ __device__ inline void dof_views(Dof* d) {
+#pragma unroll
   for (int a = 0; a < 3; ++a) {
     const double fl = floor(d->s[a]);
     d->xi[a] = (int)fl;
@@ -531,17 +533,13 @@ struct Partial<double> {
   using type = double;
 };
 
-// Block sum of NV per-thread FP32 values as double-float pairs, written by thread 0 to out[0..NV).
+// Fixed-order block tree of NV double-float pairs (shuffles within warps, then warp 0 over the
+// warps' results); the total is in thread 0's (hi, lo). Requires blockDim a multiple of 32 and
+// smem >= 32 * NV doubles. All threads of the block must call it.
 template <int NV>
-__device__ __forceinline__ void block_sum_partial(float (&v)[NV], float2* out, double* smem) {
+__device__ __forceinline__ void block_df_tree(float (&hi)[NV], float (&lo)[NV], double* smem) {
   const int tid = threadIdx.x + blockDim.x * (threadIdx.y + blockDim.y * threadIdx.z);
   const int nthreads = blockDim.x * blockDim.y * blockDim.z;
-  float hi[NV], lo[NV];
-#pragma unroll
-  for (int i = 0; i < NV; ++i) {
-    hi[i] = v[i];
-    lo[i] = 0.0f;
-  }
 #pragma unroll
   for (int off = 16; off > 0; off >>= 1)
 #pragma unroll
@@ -572,10 +570,23 @@ __device__ __forceinline__ void block_sum_partial(float (&v)[NV], float2* out, d
         const float bh = __shfl_xor_sync(0xffffffffu, hi[i], off), bl = __shfl_xor_sync(0xffffffffu, lo[i], off);
         df_add(hi[i], lo[i], bh, bl);
       }
-    if (lane == 0)
-#pragma unroll
-      for (int i = 0; i < NV; ++i) out[i] = make_float2(hi[i], lo[i]);
   }
+}
+
+// Block sum of NV per-thread FP32 values as double-float pairs, written by thread 0 to out[0..NV).
+template <int NV>
+__device__ __forceinline__ void block_sum_partial(float (&v)[NV], float2* out, double* smem) {
+  const int tid = threadIdx.x + blockDim.x * (threadIdx.y + blockDim.y * threadIdx.z);
+  float hi[NV], lo[NV];
+#pragma unroll
+  for (int i = 0; i < NV; ++i) {
+    hi[i] = v[i];
+    lo[i] = 0.0f;
+  }
+  block_df_tree<NV>(hi, lo, smem);
+  if (tid == 0)
+#pragma unroll
+    for (int i = 0; i < NV; ++i) out[i] = make_float2(hi[i], lo[i]);
 }
 template <int NV>
 __device__ __forceinline__ void block_sum_partial(double (&v)[NV], double* out, double* smem) {
@@ -586,43 +597,39 @@ __device__ __forceinline__ void block_sum_partial(double (&v)[NV], double* out, 
     for (int i = 0; i < NV; ++i) out[i] = v[i];
 }
 
-// One warp sums the partials [nblocks][NV] in a fixed order (lane-strided, then a fixed shuffle
-// tree); the FP64 result is in lane 0. Double-float pairs are summed with FP32 instructions only.
+// The block sums the partials [nblocks][NV] in a fixed order (thread-strided, then the fixed
+// block tree); the FP64 result is in thread 0. Double-float pairs are summed with FP32
+// instructions only.
 template <int NV>
-__device__ __forceinline__ void warp_sum_partials(const float2* partials, int nblocks, double* out) {
-  const int lane = threadIdx.x & 31;
+__device__ __forceinline__ void block_sum_partials(const float2* partials, int nblocks, double* out, double* smem) {
+  const int tid = threadIdx.x + blockDim.x * (threadIdx.y + blockDim.y * threadIdx.z);
+  const int nthreads = blockDim.x * blockDim.y * blockDim.z;
   float hi[NV], lo[NV];
 #pragma unroll
   for (int a = 0; a < NV; ++a) hi[a] = lo[a] = 0.0f;
-  for (int q = lane; q < nblocks; q += 32)
+#pragma unroll 4
+  for (int q = tid; q < nblocks; q += nthreads)
 #pragma unroll
     for (int a = 0; a < NV; ++a) {
       const float2 p = __ldcg(&partials[q * NV + a]);
       df_add(hi[a], lo[a], p.x, p.y);
     }
+  block_df_tree<NV>(hi, lo, smem);
+  if (tid == 0)
 #pragma unroll
-  for (int off = 16; off > 0; off >>= 1)
-#pragma unroll
-    for (int a = 0; a < NV; ++a) {
-      const float bh = __shfl_xor_sync(0xffffffffu, hi[a], off), bl = __shfl_xor_sync(0xffffffffu, lo[a], off);
-      df_add(hi[a], lo[a], bh, bl);
-    }
-#pragma unroll
-  for (int a = 0; a < NV; ++a) out[a] = (double)hi[a] + (double)lo[a];
+    for (int a = 0; a < NV; ++a) out[a] = (double)hi[a] + (double)lo[a];
 }
 template <int NV>
-__device__ __forceinline__ void warp_sum_partials(const double* partials, int nblocks, double* out) {
-  const int lane = threadIdx.x & 31;
+__device__ __forceinline__ void block_sum_partials(const double* partials, int nblocks, double* out, double* smem) {
+  const int tid = threadIdx.x + blockDim.x * (threadIdx.y + blockDim.y * threadIdx.z);
+  const int nthreads = blockDim.x * blockDim.y * blockDim.z;
   double v[NV];
 #pragma unroll
   for (int a = 0; a < NV; ++a) v[a] = 0.0;
-  for (int q = lane; q < nblocks; q += 32)
+  for (int q = tid; q < nblocks; q += nthreads)
 #pragma unroll
     for (int a = 0; a < NV; ++a) v[a] += __ldcg(&partials[q * NV + a]);
-#pragma unroll
-  for (int off = 16; off > 0; off >>= 1)
-#pragma unroll
-    for (int a = 0; a < NV; ++a) v[a] += __shfl_xor_sync(0xffffffffu, v[a], off);
+  block_sum<NV>(v, smem);
 #pragma unroll
   for (int a = 0; a < NV; ++a) out[a] = v[a];
 }
@@ -669,10 +676,15 @@ __device__ __forceinline__ void rotate_angle(const Dof& s0, double dth, double* 
   *sn = s0.sn * c + s0.cs * s;
 }
 
-// Explicit Euler equations of motion, velocity first (Sec. 2.4), masked by the free DOFs.
+// Explicit Euler equations of motion, velocity first (Sec. 2.4), masked by the free DOFs. All
+// loops have compile-time bounds so the iterates stay in registers (a local-memory round trip
+// would sit inside this single-thread FP64 chain).
+template <int D>
 __device__ __forceinline__ void eom_update(const Geo& g, const Dof& s0, const double* F, double T, Dof* out) {
+#pragma unroll
   for (int a = 0; a < 8; ++a) out->s[a] = s0.s[a];
-  for (int a = 0; a < g.dim; ++a) {
+#pragma unroll
+  for (int a = 0; a < D; ++a) {
     if (!(g.dof_mask & (1 << a))) continue;
     out->s[3 + a] = s0.s[3 + a] + F[a] * g.inv_mass;
     out->s[a] = s0.s[a] + out->s[3 + a];
@@ -688,6 +700,7 @@ __device__ __forceinline__ void eom_update(const Geo& g, const Dof& s0, const do
 // Reverse of eom_update: from dJ/ds^(k) give dJ/dF, dJ/dT and add the direct part to dJ/ds(t-1).
 __device__ __forceinline__ void eom_reverse(const Geo& g, const double* lam_sk, double* lamF, double* lamT,
                                             double* lam_prev) {
+#pragma unroll
   for (int a = 0; a < 3; ++a) {
     const bool fr = (a < g.dim) && (g.dof_mask & (1 << a));
     if (fr) {

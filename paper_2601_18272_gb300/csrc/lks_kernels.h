@@ -6,10 +6,30 @@
 
 namespace lks {
 
-constexpr int kTileX = 32;  // stencil tile width (cells); boundary pairs must not straddle tiles
-constexpr int kTileY2 = 8;  // 2D stencil tile height
+// One launch path for every kernel of the library (grid, block, dynamic shared memory, stream).
+template <typename... KArgs, typename... Args>
+inline void launch(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t st, Args... args) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = grid;
+  cfg.blockDim = block;
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = st;
+  cfg.attrs = nullptr;
+  cfg.numAttrs = 0;
+  cudaLaunchKernelEx(&cfg, kernel, args...);
+}
+
+constexpr int kTileX = 32;  // 3D stencil column width (cells); boundary pairs must not straddle columns
 constexpr int kTileY3 = 8;  // 3D stencil column height (the column marches over a chunk of z planes)
-constexpr int kBoxCtaCellsX = 32, kBoxCtaCellsY = 8;  // cells per grid-form coupling CTA
+constexpr int kStripWarps = 4;  // 2D stencil: warps per CTA, each streaming its own strip of rows
+
+// 2D stencil strips: W output columns per warp (<= 28), ntx column tiles, nstrip row strips.
+struct StripPlan {
+  int W, ntx, nstrip;
+};
+constexpr int kLanesPerCell = 4;                      // threads per box cell / design point in the body kernels
+constexpr int kBoxCtaCellsX = 16, kBoxCtaCellsY = 4;  // box cells per body-kernel CTA
+constexpr int kDesignPointsPerCta = 64;               // design points per reverse design-side CTA
 
 // Kernels that work on one time step take di: the step is ctrl->t0 + di (forward kernels) or
 // ctrl->t0 - di (adjoint kernels), so one captured graph of L steps serves every chunk.
@@ -77,6 +97,17 @@ void launch_adj_init(const Geo& g, Ctrl* ctrl, const double* objw, double seed, 
 // dJ/dgamma = dJ/dkappa^ref * dkappa^ref/dgamma.
 void launch_sensitivity(const Geo& g, const double* gamma, const double* dkref, double kappa_max, double q,
                         double* out, cudaStream_t st);
+
+// Reduced-precision checkpoint (FP32 fields) of the state at step ctrl->t0 + di into checkpoint
+// c = step / every: per-plane range keys[c][plane][2] and q[c][plane][N] in BF16 or FP16.
+void launch_ckpt_pack_q(const Geo& g, const Slots<float>& S, unsigned short* q, unsigned* keys, int fmt, int every,
+                        const Ctrl* ctrl, int di, cudaStream_t st);
+// Restore of checkpoint c into dst ((dim+1) planes of N floats).
+void launch_ckpt_restore_q(const Geo& g, float* dst, const unsigned short* q, const unsigned* keys, int fmt, int c,
+                           cudaStream_t st);
+// State (p0 [N], u0 [dim][N] in FP64) into dst in the field type.
+template <typename T>
+void launch_state_from_double(const Geo& g, T* dst, const double* p0, const double* u0, cudaStream_t st);
 
 // Checkpoint of the state at step ctrl->t0 + di into ckpt[step / every] (native precision).
 template <typename T>

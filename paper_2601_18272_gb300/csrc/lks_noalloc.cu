@@ -81,8 +81,6 @@ int make_geo(const lks_problem* P, Geo* g) {
   if (!(P->nu > 0.0)) return LKS_ERR_UNSTABLE;
   if (P->n_itr < 1 || !(P->mass > 0.0) || !(P->inertia > 0.0)) return LKS_ERR_ARG;
   if (P->weight_kind != LKS_W_COS4 && P->weight_kind != LKS_W_BILINEAR) return LKS_ERR_ARG;
-  if (P->bc[0] != LKS_BC_PERIODIC && P->nx % kTileX == 1) return LKS_ERR_UNSUPPORTED;
-  if (P->bc[1] == LKS_BC_WALL && P->ny % kTileY2 == 1) return LKS_ERR_UNSUPPORTED;
   std::memset(g, 0, sizeof(Geo));
   g->dim = 2;
   g->n[0] = P->nx;

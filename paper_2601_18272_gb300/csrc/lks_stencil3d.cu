@@ -60,10 +60,6 @@ __device__ __forceinline__ void chunk_range(int nz, int* z0, int* z1) {
 __device__ __forceinline__ constexpr int csx(int k) { return (k & 1) ? -1 : 1; }
 __device__ __forceinline__ constexpr int csy(int k) { return (k & 2) ? -1 : 1; }
 __device__ __forceinline__ constexpr int csz(int k) { return (k & 4) ? -1 : 1; }
-// the 14 moving velocities: j < 6 the axis vectors +x, -x, +y, -y, +z, -z; then the corners
-__device__ __forceinline__ constexpr int dir_x(int j) { return j < 6 ? (j == 0 ? 1 : (j == 1 ? -1 : 0)) : csx(j - 6); }
-__device__ __forceinline__ constexpr int dir_y(int j) { return j < 6 ? (j == 2 ? 1 : (j == 3 ? -1 : 0)) : csy(j - 6); }
-__device__ __forceinline__ constexpr int dir_z(int j) { return j < 6 ? (j == 4 ? 1 : (j == 5 ? -1 : 0)) : csz(j - 6); }
 
 template <typename T>
 __device__ __forceinline__ void load_state_plane(const Geo& g, const T* __restrict__ src, T (*dst)[RY][RX], int x0,
@@ -343,12 +339,22 @@ __device__ __forceinline__ void load_adj_plane(const Geo& g, const T* __restrict
   }
 }
 
+// Moments of plane zr on the halo-1 nodes; zero on nodes off the grid (non-periodic axes), where
+// the gradient-stencil transpose reads them as absent.
 template <typename T>
-__device__ __forceinline__ void moment_plane(Adj3Smem<T>& s, int zr, int z0) {
+__device__ __forceinline__ void moment_plane(const Geo& g, Adj3Smem<T>& s, int zr, int z0, int x0, int y0) {
   const int sm = ring(zr - 1, z0), s0 = ring(zr, z0), sp = ring(zr + 1, z0);
   const T third = T(1.0 / 3.0), w0 = T(2.0 / 9.0), w1 = T(1.0 / 9.0), w3 = T(1.0 / 72.0);
+  const bool zoff = g.bc[2] != BC_PERIODIC && (zr < 0 || zr >= g.n[2]);
   for (int q = threadIdx.x; q < FPL; q += NT) {
     const int ci = q % FX, cj = q / FX, li = ci + 1, lj = cj + 1;
+    const int x = x0 - 1 + ci, y = y0 - 1 + cj;
+    if (zoff || (g.bc[0] != BC_PERIODIC && (x < 0 || x >= g.n[0])) ||
+        (g.bc[1] != BC_PERIODIC && (y < 0 || y >= g.n[1]))) {
+#pragma unroll
+      for (int c = 0; c < 10; ++c) s.m[c][cj][ci] = T(0);
+      continue;
+    }
     const T(*P0)[RX] = s.raw[s0][0];
     const T fb0 = third * P0[lj][li];
     const T fpx = third * P0[lj][li + 1] + s.raw[s0][1][lj][li + 1];
@@ -393,6 +399,47 @@ __device__ __forceinline__ T Sab(const Adj3Smem<T>& s, int a, int b, int cj, int
   return s.m[idx][cj][ci];
 }
 
+// Moment S_ab at (cj, ci) of the moment plane, zero outside the plane's halo (those positions are
+// off the grid whenever they are read).
+template <typename T>
+__device__ __forceinline__ T Sab_or0(const Adj3Smem<T>& s, int a, int b, int cj, int ci) {
+  return (cj >= 0 && cj < FY && ci >= 0 && ci < FX) ? Sab(s, a, b, cj, ci) : T(0);
+}
+
+// h_a = sum_j c_j . S_a(z - c_j) at position (cj, ci) split by the plane offset of c_j:
+// hv[0] (c_z = -1, output plane zr - 1), hv[1] (c_z = 0, plane zr), hv[2] (c_z = +1, plane zr + 1).
+template <typename T, bool CHECK>
+__device__ __forceinline__ void h_plane(const Adj3Smem<T>& s, int cj, int ci, T (&hv)[3][3]) {
+  auto S = [&](int a, int b, int j, int i) { return CHECK ? Sab_or0(s, a, b, j, i) : Sab(s, a, b, j, i); };
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    T v1 = S(a, 0, cj, ci - 1) - S(a, 0, cj, ci + 1) + S(a, 1, cj - 1, ci) - S(a, 1, cj + 1, ci);
+    T v2 = S(a, 2, cj, ci), v0 = -S(a, 2, cj, ci);
+#pragma unroll
+    for (int k = 0; k < 8; ++k) {
+      const int sx = csx(k), sy = csy(k), sz = csz(k);
+      const int yy = cj - sy, xx = ci - sx;
+      const T h = T(sx) * S(a, 0, yy, xx) + T(sy) * S(a, 1, yy, xx) + T(sz) * S(a, 2, yy, xx);
+      if (sz > 0) v2 += h;
+      else v0 += h;
+    }
+    hv[0][a] = v0;
+    hv[1][a] = v1;
+    hv[2][a] = v2;
+  }
+}
+
+// hv += sgn * h at a ghost position (cj, ci)
+template <typename T>
+__device__ __forceinline__ void h_add(const Adj3Smem<T>& s, int cj, int ci, T sgn, T (&hv)[3][3]) {
+  T g[3][3];
+  h_plane<T, true>(s, cj, ci, g);
+#pragma unroll
+  for (int d = 0; d < 3; ++d)
+#pragma unroll
+    for (int a = 0; a < 3; ++a) hv[d][a] += sgn * g[d][a];
+}
+
 template <typename T>
 __global__ void __launch_bounds__(NT) k_stencil3d_adj(Geo g, Slots<T> S, T* Lb, long long lstride,
                                                       const Ctrl* __restrict__ ctrl, int di) {
@@ -412,8 +459,6 @@ __global__ void __launch_bounds__(NT) k_stencil3d_adj(Geo g, Slots<T> S, T* Lb, 
   chunk_range(nz, &z0, &z1);
   const int ci = tx + 1, cj = ty + 1;
   const T kA = two_a<T>(g) * T(0.1);
-  const bool near_xy = (g.bc[0] != BC_PERIODIC && (gx <= 1 || gx >= nx - 2)) ||
-                       (g.bc[1] != BC_PERIODIC && (gy <= 1 || gy >= ny - 2));
   T acc[3][4];
 #pragma unroll
   for (int d = 0; d < 3; ++d)
@@ -425,7 +470,7 @@ __global__ void __launch_bounds__(NT) k_stencil3d_adj(Geo g, Slots<T> S, T* Lb, 
   for (int zr = z0 - 1; zr <= z1; ++zr) {
     load_adj_plane(g, Lcur, s.raw[ring(zr + 1, z0)], x0, y0, zr + 1);
     __syncthreads();
-    moment_plane(s, zr, z0);
+    moment_plane(g, s, zr, z0, x0, y0);
     __syncthreads();
     // local part of output zr
     if (ingrid && zr >= z0 && zr < z1) {
@@ -441,72 +486,36 @@ __global__ void __launch_bounds__(NT) k_stencil3d_adj(Geo g, Slots<T> S, T* Lb, 
         acc[1][1 + a] += T(3) * s.m[1 + a][cj][ci] + T(9) * su - T(3) * u[a] * P;
       }
     }
-    // velocity-gradient transpose: plane zr feeds outputs zr - 1, zr, zr + 1
-    const bool zplane_ok = g.bc[2] == BC_PERIODIC || (zr >= 0 && zr < nz);
-    const bool slow = near_xy || (g.bc[2] != BC_PERIODIC && (zr <= 0 || zr >= nz - 1));
-    if (ingrid && zplane_ok) {
-      if (!slow) {
-#pragma unroll
-        for (int a = 0; a < 3; ++a) {
-          T v1 = Sab(s, a, 0, cj, ci - 1) - Sab(s, a, 0, cj, ci + 1) + Sab(s, a, 1, cj - 1, ci) - Sab(s, a, 1, cj + 1, ci);
-          T v2 = Sab(s, a, 2, cj, ci), v0 = -Sab(s, a, 2, cj, ci);
-#pragma unroll
-          for (int k = 0; k < 8; ++k) {
-            const int sx = csx(k), sy = csy(k), sz = csz(k);
-            const int yy = cj - sy, xx = ci - sx;
-            const T h = T(sx) * Sab(s, a, 0, yy, xx) + T(sy) * Sab(s, a, 1, yy, xx) + T(sz) * Sab(s, a, 2, yy, xx);
-            if (sz > 0) v2 += h;
-            else v0 += h;
-          }
-          acc[0][1 + a] += kA * v0;
-          acc[1][1 + a] += kA * v1;
-          acc[2][1 + a] += kA * v2;
-        }
-      } else {
-        for (int dy = -1; dy <= 1; ++dy)
-          for (int dx = -1; dx <= 1; ++dx) {
-            int yx = gx + dx, yy = gy + dy;
-            if (g.bc[0] == BC_PERIODIC) yx = wrapi(yx, nx);
-            else if (yx < 0 || yx >= nx) continue;
-            if (g.bc[1] == BC_PERIODIC) yy = wrapi(yy, ny);
-            else if (yy < 0 || yy >= ny) continue;
-            const int mj = cj + dy, mi = ci + dx;
-            T Sm[3][3];
-#pragma unroll
-            for (int a = 0; a < 3; ++a)
-#pragma unroll
-              for (int b = 0; b < 3; ++b) Sm[a][b] = Sab(s, a, b, mj, mi);
-#pragma unroll
-            for (int j = 0; j < 14; ++j) {
-              const int cx = dir_x(j), cy = dir_y(j), cz = dir_z(j);
-              int mx = yx + cx, my = yy + cy, sgn = 1;
-              if (!ghost_axis(g.bc[0], nx, &mx, &sgn) || !ghost_axis(g.bc[1], ny, &my, &sgn)) continue;
-              if (mx != gx || my != gy) continue;
-              int dz = cz;
-              if (g.bc[2] != BC_PERIODIC) {
-                const int vz = zr + cz;
-                if (vz < 0 || vz >= nz) {
-                  if (g.bc[2] != BC_WALL) continue;
-                  dz = -dz;  // reflected onto the plane on the other side of zr
-                  sgn = -sgn;
-                }
-              }
-              T h[3];
-#pragma unroll
-              for (int a = 0; a < 3; ++a) h[a] = kA * T(sgn) * (T(cx) * Sm[a][0] + T(cy) * Sm[a][1] + T(cz) * Sm[a][2]);
-              if (dz < 0) {
-#pragma unroll
-                for (int a = 0; a < 3; ++a) acc[0][1 + a] += h[a];
-              } else if (dz == 0) {
-#pragma unroll
-                for (int a = 0; a < 3; ++a) acc[1][1 + a] += h[a];
-              } else {
-#pragma unroll
-                for (int a = 0; a < 3; ++a) acc[2][1 + a] += h[a];
-              }
-            }
-          }
+    // velocity-gradient transpose: moment plane zr feeds outputs zr - 1, zr, zr + 1 at this
+    // node, plus the ghost positions that the gradient stencil mapped onto it (open x planes copy:
+    // sign +1; walls reflect: sign -1). S is zero off the grid, so one formula serves all.
+    if (ingrid) {
+      T hv[3][3];
+      h_plane<T, false>(s, cj, ci, hv);
+      const bool gx_lo = g.bc[0] != BC_PERIODIC && gx == 0, gx_hi = g.bc[0] != BC_PERIODIC && gx == nx - 1;
+      const bool gy_lo = g.bc[1] == BC_WALL && gy == 1, gy_hi = g.bc[1] == BC_WALL && gy == ny - 2;
+      if (gx_lo || gx_hi || gy_lo || gy_hi) {
+        // ghost offsets (in the moment plane) and signs along x and y
+        const int ox = gx_lo ? -1 : (gx_hi ? 1 : 0);
+        const int oy = gy_lo ? -2 : (gy_hi ? 2 : 0);
+        if (ox != 0) h_add<T>(s, cj, ci + ox, T(1), hv);
+        if (oy != 0) h_add<T>(s, cj + oy, ci, T(-1), hv);
+        if (ox != 0 && oy != 0) h_add<T>(s, cj + oy, ci + ox, T(-1), hv);
       }
+#pragma unroll
+      for (int d = 0; d < 3; ++d)
+#pragma unroll
+        for (int a = 0; a < 3; ++a) acc[d][1 + a] += kA * hv[d][a];
+    }
+    // wall planes: ghost plane -1 (complete once moment plane 0 is in) reflects onto plane 1,
+    // ghost plane nz (complete once moment plane nz - 1 is in) onto plane nz - 2
+    if (g.bc[2] == BC_WALL && zr == 0) {
+#pragma unroll
+      for (int a = 1; a < 4; ++a) acc[2][a] -= acc[0][a];
+    }
+    if (g.bc[2] == BC_WALL && zr == nz - 1) {
+#pragma unroll
+      for (int a = 1; a < 4; ++a) acc[0][a] -= acc[2][a];
     }
     const int zo = zr - 1;
     if (ingrid && zo >= z0) {
@@ -543,14 +552,14 @@ void prepare_stencil3d() {
 template <typename T>
 void launch_stencil3d_fwd(const Geo& g, const Slots<T>& S, const Ctrl* ctrl, int di, cudaStream_t st) {
   const dim3 grid((g.n[0] + TX - 1) / TX, (g.n[1] + TY - 1) / TY, z_chunks(g));
-  k_stencil3d<T><<<grid, NT, sizeof(Fwd3Smem<T>), st>>>(g, S, ctrl, di);
+  launch(k_stencil3d<T>, grid, NT, sizeof(Fwd3Smem<T>), st, g, S, ctrl, di);
 }
 
 template <typename T>
 void launch_stencil3d_adj(const Geo& g, const Slots<T>& S, T* Lb, long long lstride, const Ctrl* ctrl, int di,
                           cudaStream_t st) {
   const dim3 grid((g.n[0] + TX - 1) / TX, (g.n[1] + TY - 1) / TY, z_chunks(g));
-  k_stencil3d_adj<T><<<grid, NT, sizeof(Adj3Smem<T>), st>>>(g, S, Lb, lstride, ctrl, di);
+  launch(k_stencil3d_adj<T>, grid, NT, sizeof(Adj3Smem<T>), st, g, S, Lb, lstride, ctrl, di);
 }
 
 template void prepare_stencil3d<float>();

@@ -12,7 +12,7 @@ import pytest
 from oracle import oracle as O
 from tests.problems import (BC_INFLOW_OUTFLOW, BC_PERIODIC, BC_PRESSURE, BC_WALL, DOF_ROT, DOF_TX, DOF_TY, DOF_TZ,
                             W_BILINEAR, W_COS4, body2d, body3d, perturbed_state)
-from workloads import CKPT_STORE_ALL, CKPT_UNIFORM, config, initial_state
+from workloads import CKPT_BF16, CKPT_FP16, CKPT_STORE_ALL, CKPT_UNIFORM, config, initial_state
 
 pytestmark = pytest.mark.gpu
 
@@ -56,6 +56,12 @@ CASES_2D = [
     ("walls-pressure", lambda: body2d(bc=(BC_PRESSURE, BC_WALL, BC_PERIODIC), mask=DOF_TX | DOF_ROT)),
     ("periodic", lambda: body2d(bc=(BC_PERIODIC,) * 3)),
     ("ragged-40x20", lambda: body2d(nx=40, ny=20, nd=7, centre=(15.6, 9.3), nt=9)),
+    # odd widths (scalar column path), several column tiles, a tile width reduced so that the last
+    # two columns share a tile (nx - 1 = 56)
+    ("odd-37x21-walls", lambda: body2d(nx=37, ny=21, centre=(14.3, 10.4), bc=(BC_INFLOW_OUTFLOW, BC_WALL, BC_PERIODIC))),
+    ("odd-33x18-periodic", lambda: body2d(nx=33, ny=18, centre=(16.1, 8.7), bc=(BC_PERIODIC,) * 3)),
+    ("wide-130x20-pressure", lambda: body2d(nx=130, ny=20, centre=(60.2, 9.6), bc=(BC_PRESSURE, BC_WALL, BC_PERIODIC))),
+    ("57x16-tile54", lambda: body2d(nx=57, ny=16, centre=(40.4, 7.7))),
 ]
 
 
@@ -258,3 +264,33 @@ def test_body3d_128x64x64_truncated_fp32():
     r = gpu_run(P, g, p0, u0, s0)
     assert abs(r["J"] - G["J"]) <= 1e-4 * abs(G["J"])
     assert rel(r["dJdgamma"], G["dJdgamma"]) <= 1e-3
+
+
+# ---- reduced-precision checkpoints -----------------------------------------------------------
+
+@pytest.mark.parametrize("fmt,tol", [(CKPT_BF16, 5e-2), (CKPT_FP16, 5e-3)], ids=["bf16", "fp16"])
+@pytest.mark.parametrize("name,make", CASES_2D[:2] + CASES_3D[:1], ids=[c[0] for c in CASES_2D[:2] + CASES_3D[:1]])
+def test_reduced_precision_checkpoints(name, make, fmt, tol):
+    """BF16 / FP16 checkpoints with a per-plane affine range: the forward (and J) is that of the
+    FP32 run bit for bit; the gradient carries the quantisation of the restored segment starts."""
+    P, g = make()
+    P = P.replace(n_steps=12)
+    p0, u0, s0 = perturbed_state(P)
+    G = O.gradient(P, g, p0, u0, s0)
+    r32 = gpu_run(P, g, p0, u0, s0, precision=32, ckpt_policy=CKPT_UNIFORM, ckpt_every=4)
+    rq = gpu_run(P, g, p0, u0, s0, precision=32, ckpt_policy=CKPT_UNIFORM, ckpt_every=4, ckpt_format=fmt)
+    assert rq["J"] == r32["J"]
+    np.testing.assert_array_equal(rq["hist"], r32["hist"])
+    e32 = rel(r32["dJdgamma"], G["dJdgamma"])
+    eq = rel(rq["dJdgamma"], G["dJdgamma"])
+    assert eq <= tol, f"dJ/dgamma rel err {eq:.3e} (FP32 checkpoints: {e32:.3e})"
+
+
+def test_reduced_precision_first_segment_exact():
+    """With a single segment the restore is the exact initial state: the gradient equals the FP32
+    checkpointed one bit for bit."""
+    P, g = body2d(nt=4)
+    p0, u0, s0 = perturbed_state(P)
+    a = gpu_run(P, g, p0, u0, s0, precision=32, ckpt_policy=CKPT_UNIFORM, ckpt_every=4)
+    b = gpu_run(P, g, p0, u0, s0, precision=32, ckpt_policy=CKPT_UNIFORM, ckpt_every=4, ckpt_format=CKPT_BF16)
+    assert np.array_equal(a["dJdgamma"], b["dJdgamma"])
