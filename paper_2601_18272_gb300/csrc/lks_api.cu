@@ -64,6 +64,7 @@ struct lks_handle {
   Ctrl* ctrl = nullptr;
   Moments* mom = nullptr;
   double* partials = nullptr;
+  long long pstride = 0;  // elements per half of the double-buffered coupling partials
   double* init_p = nullptr;
   double* init_u = nullptr;
   double* init_s = nullptr;
@@ -274,8 +275,9 @@ void enqueue_fwd_steps(lks_handle* h, Launcher& L, const Slots<T>& S, int nsteps
   for (int i = 0; i < nsteps; ++i) {
     L("stencil_fwd", [&](cudaStream_t s) { launch_stencil_fwd<T>(g, S, h->ctrl, i, s); });
     for (int k = 1; k <= g.K; ++k)
-      L.n("couple", 2, [&](cudaStream_t s) {
-        launch_couple<T>(g, S, h->ctrl, h->it, (const T*)h->kref, h->mom, h->partials, k, bs, h->nbox, i, s);
+      L("couple", [&](cudaStream_t s) {
+        launch_couple<T>(g, S, h->ctrl, h->it, (const T*)h->kref, h->mom, h->partials, h->pstride, k, bs, h->nbox, i,
+                         s);
       });
   }
 }
@@ -347,6 +349,7 @@ int forward_impl(lks_handle* h, cudaStream_t st) {
       }));
     }
   }
+  L0("couple", [&](cudaStream_t s) { launch_couple_last<T>(g, h->ctrl, h->it, h->mom, h->partials, h->pstride, NT, s); });
   CK(cudaGetLastError());
   if (h->launch_error) return LKS_ERR_CUDA;
   return LKS_OK;
@@ -432,6 +435,7 @@ int allocate(lks_handle* h) {
   const long long bd = ((long long)g.ND + kDesignPointsPerCta - 1) / kDesignPointsPerCta;
   const long long nblk = std::max(bx, bd) + 1;
   TRY(dalloc(h, (void**)&h->partials, (size_t)nblk * 8 * sizeof(double)));
+  h->pstride = 4 * nblk;
   TRY(dalloc(h, (void**)&h->init_p, (size_t)g.N * sizeof(double)));
   TRY(dalloc(h, (void**)&h->init_u, (size_t)D * g.N * sizeof(double)));
   TRY(dalloc(h, (void**)&h->init_s, 8 * sizeof(double)));

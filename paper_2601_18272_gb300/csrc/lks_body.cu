@@ -399,14 +399,55 @@ __global__ void __launch_bounds__(256) k_prep(Geo g, const double* __restrict__ 
 
 // ---- grid form ----------------------------------------------------------------------------
 
+// Coupling iteration k of step t. The EOM of the previous iteration (k-1 of step t, or N_itr of
+// step t-1) is folded into this kernel: every CTA sums that iteration's partials (double-buffered
+// by the parity of the iteration index) and runs the same deterministic FP64 EOM, and CTA 0 records
+// the iterate. This removes a launch and a dependent round trip per iteration; the EOM of the run's
+// last iteration is k_couple_last.
 template <typename T, int D, int AX>
-__global__ void __launch_bounds__(kCellThreads) k_couple(Geo g, Slots<T> S, Ctrl* ctrl, Dof* it, const T* __restrict__ kref,
-                                                    const Moments* __restrict__ mom, void* partials, int k,
-                                                    T* __restrict__ boxstore, int nbox, int di) {
+__global__ void __launch_bounds__(kCellThreads, 2) k_couple(Geo g, Slots<T> S, Ctrl* ctrl, Dof* it,
+                                                          const T* __restrict__ kref, const Moments* __restrict__ mom,
+                                                          void* partials, long long pstride, int nparts, int k,
+                                                          T* __restrict__ boxstore, int nbox, int di) {
+  using PT = typename Partial<T>::type;
   __shared__ double red[32 * 4];
+  __shared__ Dof sd[2];  // s(t-1), s^(k-1)
   const int t = ctrl->t0 + di, base = ctrl->base, K = g.K;
   Dof* row = it + (long long)(t - 1) * (K + 1);
-  const Dof s0 = row[0], sk = row[k - 1];
+  const long long idx = (long long)(t - 1) * K + (k - 1);  // iteration index in the run
+  PT* pin = static_cast<PT*>(partials) + ((idx - 1) & 1) * pstride;
+  PT* pout = static_cast<PT*>(partials) + (idx & 1) * pstride;
+  if (idx > 0) {
+    // previous iteration kp of step tp
+    Dof* prow = (k > 1) ? row : row - (K + 1);
+    const int kp = (k > 1) ? k - 1 : K;
+    Dof p0, pk;
+    Moments m;
+    if (threadIdx.x == 0) {
+      p0 = prow[0];
+      pk = prow[kp - 1];
+      m = *mom;
+    }
+    double sm[4];
+    block_sum_partials<4>(pin, nparts, sm, red);
+    if (threadIdx.x == 0) {
+      Dof nx;
+      int st = 0;
+      couple_finish<D, AX>(g, &m, p0, pk, sm, &nx, &st);
+      if (blockIdx.x == 0 && blockIdx.y == 0 && blockIdx.z == 0) {
+        if (st) ctrl->status |= st;
+        prow[kp] = nx;
+        if (kp == K) row[0] = nx;
+      }
+      sd[0] = (k > 1) ? row[0] : nx;
+      sd[1] = nx;
+    }
+  } else if (threadIdx.x == 0) {
+    sd[0] = row[0];
+    sd[1] = row[0];
+  }
+  __syncthreads();
+  const Dof s0 = sd[0], sk = sd[1];
   T* __restrict__ dst = slot_ptr(S, t, base);
   int lo[3];
   box_origin<D>(g, s0, lo[0], lo[1], lo[2]);
@@ -414,41 +455,43 @@ __global__ void __launch_bounds__(kCellThreads) k_couple(Geo g, Slots<T> S, Ctrl
   const CellSlot cc = cell_slot(g);
   T v[4] = {T(0), T(0), T(0), T(0)};
   couple_cell<T, D, AX>(g, kref, sk, lo, cc, dst, bs, k == K, &ctrl->status, v);
-  block_sum_partial<4>(v, static_cast<typename Partial<T>::type*>(partials) + block_linear() * 4, red);
+  block_sum_partial<4>(v, pout + block_linear() * 4, red);
 }
 
-// Sum of the coupling partials and the EOM update: iterate s^(k) of step t.
+// EOM of the last coupling iteration of the run (step t_last, iteration N_itr).
 template <typename T, int D, int AX>
-__global__ void __launch_bounds__(kFinishThreads) k_couple_finish(Geo g, Ctrl* ctrl, Dof* it,
-                                                                   const Moments* __restrict__ mom,
-                                                                   const void* __restrict__ partials, int nparts, int k,
-                                                                   int di) {
+__global__ void __launch_bounds__(kFinishThreads, 1) k_couple_last(Geo g, Ctrl* ctrl, Dof* it,
+                                                                 const Moments* __restrict__ mom,
+                                                                 const void* __restrict__ partials,
+                                                                 long long pstride, int nparts, int t_last) {
+  using PT = typename Partial<T>::type;
   __shared__ double red[32 * 4];
-  const int t = ctrl->t0 + di, K = g.K;
-  Dof* row = it + (long long)(t - 1) * (K + 1);
-  // thread 0 fetches what the EOM needs before the reduction, so the loads overlap it
+  const int K = g.K;
+  Dof* row = it + (long long)(t_last - 1) * (K + 1);
+  const long long idx = (long long)(t_last - 1) * K + (K - 1);
+  const PT* pin = static_cast<const PT*>(partials) + (idx & 1) * pstride;
   Dof s0, sk;
   Moments m;
   if (threadIdx.x == 0) {
     s0 = row[0];
-    sk = row[k - 1];
+    sk = row[K - 1];
     m = *mom;
   }
-  double s[4];
-  block_sum_partials<4>(static_cast<const typename Partial<T>::type*>(partials), nparts, s, red);
+  double sm[4];
+  block_sum_partials<4>(pin, nparts, sm, red);
   if (threadIdx.x == 0) {
     Dof nx;
     int st = 0;
-    couple_finish<D, AX>(g, &m, s0, sk, s, &nx, &st);
+    couple_finish<D, AX>(g, &m, s0, sk, sm, &nx, &st);
     if (st) ctrl->status |= st;
-    row[k] = nx;
-    if (k == K) it[(long long)t * (K + 1)] = nx;
+    row[K] = nx;
+    it[(long long)t_last * (K + 1)] = nx;
   }
 }
 
 // Recompute of one step's Brinkman update from the stored iterate s^(K-1).
 template <typename T, int D, int AX>
-__global__ void __launch_bounds__(kCellThreads) k_apply(Geo g, Slots<T> S, const Ctrl* ctrl, const Dof* it,
+__global__ void __launch_bounds__(kCellThreads, 2) k_apply(Geo g, Slots<T> S, const Ctrl* ctrl, const Dof* it,
                                                    const T* __restrict__ kref, T* __restrict__ boxstore, int nbox,
                                                    int di) {
   const int t = ctrl->t0 + di, base = ctrl->base, K = g.K;
@@ -485,7 +528,7 @@ __global__ void __launch_bounds__(kCellThreads) k_apply(Geo g, Slots<T> S, const
 }
 
 template <typename T, int D, int AX>
-__global__ void __launch_bounds__(kCellThreads) k_adj_cell(Geo g, const Ctrl* ctrl, const Dof* it, const T* __restrict__ kref,
+__global__ void __launch_bounds__(kCellThreads, 2) k_adj_cell(Geo g, const Ctrl* ctrl, const Dof* it, const T* __restrict__ kref,
                                                       const T* __restrict__ boxstore, int nbox, T* Lb,
                                                       long long lstride, T* __restrict__ acc, T* __restrict__ scratch,
                                                       int k, int di) {
@@ -627,11 +670,19 @@ void launch_prep(const Geo& g, const double* gamma, double kappa_max, double q, 
 
 template <typename T>
 void launch_couple(const Geo& g, const Slots<T>& S, Ctrl* ctrl, Dof* it, const T* kref, const Moments* mom,
-                   void* partials, int k, T* boxstore, int nbox, int di, cudaStream_t st) {
+                   void* partials, long long pstride, int k, T* boxstore, int nbox, int di, cudaStream_t st) {
   const dim3 grid = box_grid(g);
-  LKS_BOX_DISPATCH(k_couple, grid, kCellThreads, g, S, ctrl, it, kref, mom, partials, k, boxstore, nbox, di);
   const int nparts = (int)(grid.x * grid.y * grid.z);
-  LKS_BOX_DISPATCH(k_couple_finish, 1, kFinishThreads, g, ctrl, it, mom, partials, nparts, k, di);
+  LKS_BOX_DISPATCH(k_couple, grid, kCellThreads, g, S, ctrl, it, kref, mom, partials, pstride, nparts, k, boxstore,
+                   nbox, di);
+}
+
+template <typename T>
+void launch_couple_last(const Geo& g, Ctrl* ctrl, Dof* it, const Moments* mom, const void* partials,
+                        long long pstride, int t_last, cudaStream_t st) {
+  const dim3 grid = box_grid(g);
+  const int nparts = (int)(grid.x * grid.y * grid.z);
+  LKS_BOX_DISPATCH(k_couple_last, 1, kFinishThreads, g, ctrl, it, mom, partials, pstride, nparts, t_last);
 }
 
 template <typename T>
@@ -686,8 +737,10 @@ void launch_ckpt_pack(const Geo& g, const Slots<T>& S, T* ckpt, long long cstrid
 #define LKS_INST(T)                                                                                                 \
   template void launch_prep<T>(const Geo&, const double*, double, double, T*, Moments*, double*, Ctrl*,              \
                                cudaStream_t);                                                                       \
-  template void launch_couple<T>(const Geo&, const Slots<T>&, Ctrl*, Dof*, const T*, const Moments*, void*, int,      \
-                                 T*, int, int, cudaStream_t);                                                       \
+  template void launch_couple<T>(const Geo&, const Slots<T>&, Ctrl*, Dof*, const T*, const Moments*, void*,          \
+                                 long long, int, T*, int, int, cudaStream_t);                                       \
+  template void launch_couple_last<T>(const Geo&, Ctrl*, Dof*, const Moments*, const void*, long long, int,          \
+                                      cudaStream_t);                                                                \
   template void launch_apply<T>(const Geo&, const Slots<T>&, const Ctrl*, const Dof*, const T*, T*, int, int,        \
                                 cudaStream_t);                                                                      \
   template void launch_adj_cell<T>(const Geo&, const Ctrl*, const Dof*, const T*, const T*, int, T*, long long, T*, \

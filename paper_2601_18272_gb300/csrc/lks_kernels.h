@@ -28,7 +28,7 @@ struct StripPlan {
   int W, ntx, nstrip;
 };
 constexpr int kLanesPerCell = 4;                      // threads per box cell / design point in the body kernels
-constexpr int kBoxCtaCellsX = 16, kBoxCtaCellsY = 4;  // box cells per body-kernel CTA
+constexpr int kBoxCtaCellsX = 16, kBoxCtaCellsY = 8;  // box cells per body-kernel CTA
 constexpr int kDesignPointsPerCta = 64;               // design points per reverse design-side CTA
 
 // Kernels that work on one time step take di: the step is ctrl->t0 + di (forward kernels) or
@@ -59,12 +59,17 @@ template <typename T>
 void launch_prep(const Geo& g, const double* gamma, double kappa_max, double q, T* kref, Moments* mom,
                  double* partials, Ctrl* ctrl, cudaStream_t st);
 
-// Coupling iteration k (1..K) of step t: spread, Brinkman, force/torque (per-CTA partials: float2
-// double-float pairs for FP32 fields, doubles for FP64), then a one-warp finish kernel with the EOM. On k == K writes u(t) into slot(t) and optionally u* into the
-// box store.
+// Coupling iteration k (1..K) of step t: the EOM of the previous iteration (from the other half
+// of the double-buffered partials, pstride elements apart), then spread, Brinkman, force/torque
+// partials (float2 double-float pairs for FP32 fields, doubles for FP64). On k == K writes u(t) into
+// slot(t) and optionally u* into the box store.
 template <typename T>
 void launch_couple(const Geo& g, const Slots<T>& S, Ctrl* ctrl, Dof* it, const T* kref, const Moments* mom,
-                   void* partials, int k, T* boxstore, int nbox, int di, cudaStream_t st);
+                   void* partials, long long pstride, int k, T* boxstore, int nbox, int di, cudaStream_t st);
+// EOM of the last iteration of a forward run ending at step t_last.
+template <typename T>
+void launch_couple_last(const Geo& g, Ctrl* ctrl, Dof* it, const Moments* mom, const void* partials,
+                        long long pstride, int t_last, cudaStream_t st);
 
 // Recompute: Brinkman update with the stored iterate s^(K-1); writes u(t) and the box store of u*.
 template <typename T>

@@ -164,7 +164,9 @@ extern "C" int lks_step_noalloc(const lks_problem* problem, const double* gamma_
   launch_prep<double>(g, gamma_dev, problem->kappa_max, problem->q, kref, mom, partials, ctrl, st);
   k_noalloc_seed<<<1, 1, 0, st>>>(ctrl, it, s0, parity);
   launch_stencil_fwd<double>(g, S, ctrl, 0, st);
-  for (int k = 1; k <= g.K; ++k) launch_couple<double>(g, S, ctrl, it, kref, mom, partials, k, nullptr, 1, 0, st);
+  const long long pstride = 4LL * kMaxBlocks;  // halves of the double-buffered coupling partials
+  for (int k = 1; k <= g.K; ++k) launch_couple<double>(g, S, ctrl, it, kref, mom, partials, pstride, k, nullptr, 1, 0, st);
+  launch_couple_last<double>(g, ctrl, it, mom, partials, pstride, 1, st);
   Dof out;
   Ctrl c;
   if (cudaMemcpyAsync(&out, it + (g.K + 1), sizeof(Dof), cudaMemcpyDeviceToHost, st) != cudaSuccess) return LKS_ERR_CUDA;

@@ -10,8 +10,8 @@
 // copy the boundary node, walls reflect u with a sign flip.
 //
 // GB300 form: each warp streams a strip of rows through 64 consecutive columns, two per lane
-// (lane L holds columns x0 - 4 + 2L and x0 - 3 + 2L, loaded as one vector where the pair is on the
-// grid), and writes the W <= 56 columns of lanes 2 .. 1 + W/2. Neighbour columns come from warp
+// (lane L holds columns x0 - 2 + 2L and x0 - 1 + 2L, loaded as one vector where the pair is on the
+// grid), and writes the W <= 60 columns of lanes 1 .. W/2. Neighbour columns come from warp
 // shuffles (one per neighbouring lane and value, shared by the pair), so there is no shared
 // memory and no block barrier. Per row the warp loads the state once, forms the velocity-gradient
 // row sums, the nine f_i^eq of the row above the newest, and scatters them into three rolling row
@@ -84,9 +84,9 @@ __device__ __forceinline__ bool strip_of(const Geo& g, const StripPlan& sp, Stri
   st->x0 = tx * sp.W;
   st->y0 = (int)(((long long)sy * g.n[1]) / sp.nstrip);
   st->y1 = (int)(((long long)(sy + 1) * g.n[1]) / sp.nstrip);
-  st->ca = st->x0 - 4 + 2 * st->lane;
+  st->ca = st->x0 - 2 + 2 * st->lane;
   st->cb = st->ca + 1;
-  st->out = st->lane >= 2 && st->lane < 2 + sp.W / 2;
+  st->out = st->lane >= 1 && st->lane <= sp.W / 2;
   return true;
 }
 
@@ -136,27 +136,32 @@ struct F9 {
 };
 template <typename T>
 __device__ __forceinline__ F9<T> feq9(T p, T ux, T uy, T dxux, T dxuy, T sxux_up, T sxux_dn, T sxuy_up, T sxuy_dn,
-                                      T A2) {
-  const T sixth = T(1.0 / 6.0);
-  const T w0 = T(4.0 / 9.0), w1 = T(1.0 / 9.0), w5 = T(1.0 / 36.0);
-  const T gxx = dxux * sixth, gyx = dxuy * sixth;
-  const T gxy = (sxux_up - sxux_dn) * sixth, gyy = (sxuy_up - sxuy_dn) * sixth;
-  const T a = T(3) * p - T(1.5) * (ux * ux + uy * uy);
-  const T bx = T(3) * ux, by = T(3) * uy;
-  const T qxx = T(4.5) * ux * ux + A2 * gxx;
-  const T qyy = T(4.5) * uy * uy + A2 * gyy;
-  const T qxy = T(9) * ux * uy + A2 * (gxy + gyx);
-  const T d = a + qxx + qyy;
+                                      T K) {
+  // K = 2A/6 multiplies the raw row sums (the gradient's 1/6 folded in); with ux2 = ux^2 etc.:
+  //   a = 3p - 3/2 (ux2 + uy2),  f0 = 4/9 a,
+  //   f1,3 = 1/9 (a + 9/2 ux2 + K Gxx) +- ux/3,  f2,4 = 1/9 (a + 9/2 uy2 + K Gyy) +- uy/3,
+  //   f5..8 = 1/36 (d +- qxy) + (+-ux +-uy)/12 with d = 3p + 3 (ux2 + uy2) + K (Gxx + Gyy),
+  //   qxy = 9 ux uy + K (Gxy + Gyx)
+  const T ux2 = ux * ux, uy2 = uy * uy, s2 = ux2 + uy2, p3 = T(3) * p;
+  const T kxx = K * dxux, kyy = K * (sxuy_up - sxuy_dn);
+  const T kxy = K * ((sxux_up - sxux_dn) + dxuy);
+  const T a = fma(T(-1.5), s2, p3);
+  const T h1 = T(1.0 / 9.0) * (fma(T(4.5), ux2, a) + kxx), v1 = T(1.0 / 3.0) * ux;
+  const T h2 = T(1.0 / 9.0) * (fma(T(4.5), uy2, a) + kyy), v2 = T(1.0 / 3.0) * uy;
+  const T d36 = T(1.0 / 36.0) * (fma(T(3), s2, p3) + kxx + kyy);
+  const T q36 = T(1.0 / 36.0) * fma(T(9) * ux, uy, kxy);
+  const T bx = T(1.0 / 12.0) * ux, by = T(1.0 / 12.0) * uy;
+  const T e1 = d36 + q36, e2 = d36 - q36, s1 = bx + by, sm = bx - by;
   F9<T> f;
-  f.f0 = w0 * a;
-  f.f1 = w1 * (a + bx + qxx);
-  f.f3 = w1 * (a - bx + qxx);
-  f.f2 = w1 * (a + by + qyy);
-  f.f4 = w1 * (a - by + qyy);
-  f.f5 = w5 * (d + bx + by + qxy);
-  f.f6 = w5 * (d - bx + by - qxy);
-  f.f7 = w5 * (d - bx - by + qxy);
-  f.f8 = w5 * (d + bx - by - qxy);
+  f.f0 = T(4.0 / 9.0) * a;
+  f.f1 = h1 + v1;
+  f.f3 = h1 - v1;
+  f.f2 = h2 + v2;
+  f.f4 = h2 - v2;
+  f.f5 = e1 + s1;
+  f.f7 = e1 - s1;
+  f.f6 = e2 - sm;
+  f.f8 = e2 + sm;
   return f;
 }
 
@@ -170,7 +175,7 @@ struct Acc2 {
 // A strip whose 64 columns and rows y0-2 .. y1+1 all lie on the grid, clear of every boundary node
 // and of any wrap: it needs neither the ghost rule nor a boundary phase (most strips of a large grid).
 __device__ __forceinline__ bool interior_strip(const Geo& g, const StripPlan& sp, const Strip& st) {
-  return st.x0 - 4 >= 0 && st.x0 + 60 <= g.n[0] && st.y0 - 2 >= 0 && st.y1 + 1 <= g.n[1] - 1;
+  return st.x0 - 2 >= 0 && st.x0 + 62 <= g.n[0] && st.y0 - 2 >= 0 && st.y1 + 1 <= g.n[1] - 1;
 }
 
 // One warp's strip of the predictor. LEAN: the strip is interior (interior_strip), so every load
@@ -188,7 +193,7 @@ __device__ __forceinline__ void fwd_strip(const Geo& g, const Slots<T>& S, const
   const bool xia = xint_of(g, st.ca), xib = xint_of(g, st.cb);
   const bool has_xb = !LEAN && g.bc[0] != BC_PERIODIC && (st.x0 == 0 || st.x0 + sp.W >= nx - 1);
   const bool wall_y = !LEAN && g.bc[1] == BC_WALL;
-  const T A2 = two_a<T>(g);
+  const T K = two_a<T>(g) * T(1.0 / 6.0);
 
   // Row r of the state at this lane's two columns, staged through the warp's shared ring.
   constexpr int D = Ring<T>::rows;
@@ -261,9 +266,9 @@ __device__ __forceinline__ void fwd_strip(const Geo& g, const Slots<T>& S, const
     if (r + 1 <= st.y1 + 1) load(r + 1, X);
     {
       const F9<T> A = feq9(cB.pa, cB.xa, cB.ya, gA.dxa + gB.dxa + gC.dxa, gA.dya + gB.dya + gC.dya, gC.sxa, gA.sxa,
-                           gC.sya, gA.sya, A2);
+                           gC.sya, gA.sya, K);
       const F9<T> B = feq9(cB.pb, cB.xb, cB.yb, gA.dxb + gB.dxb + gC.dxb, gA.dyb + gB.dyb + gC.dyb, gC.sxb, gA.sxb,
-                           gC.syb, gA.syb, A2);
+                           gC.syb, gA.syb, K);
       // c_x = +1 directions reach the next column, c_x = -1 the previous one
       const T l1 = shup(B.f1), l5 = shup(B.f5), l8 = shup(B.f8);  // from column ca - 1
       const T r3 = shdn(A.f3), r6 = shdn(A.f6), r7 = shdn(A.f7);  // from column cb + 1
@@ -578,7 +583,7 @@ __device__ __forceinline__ void lam_route(const Geo& g, const T* L, int x, int y
 // boundary routing, ghost fold or off-grid node) and no wrap.
 __device__ __forceinline__ bool interior_strip_adj(const Geo& g, const Strip& st) {
   const int mx = g.bc[0] == BC_PERIODIC ? 0 : 2, my = g.bc[1] == BC_PERIODIC ? 0 : 2;
-  return st.x0 - 4 >= mx && st.x0 + 60 <= g.n[0] - mx && st.y0 - 2 >= my && st.y1 + 1 <= g.n[1] - 1 - my;
+  return st.x0 - 2 >= mx && st.x0 + 62 <= g.n[0] - mx && st.y0 - 2 >= my && st.y1 + 1 <= g.n[1] - 1 - my;
 }
 
 // One warp's strip of the transpose (LEAN as in fwd_strip, with interior_strip_adj).
@@ -815,12 +820,12 @@ __global__ void __launch_bounds__(SW * 32) k_stencil2d_adj(Geo g, Slots<T> S, T*
     adj_strip<T, VEC, false>(g, S, Lb, lstride, ctrl, di, sp, st);
 }
 
-// Column tiles and row strips: W output columns per warp (56, or a little less so that the
+// Column tiles and row strips: W output columns per warp (60, or a little less so that the
 // columns nx-2 and nx-1 of a non-periodic x axis share a warp; always even so column pairs start
 // on an even column), strips of rows sized so the grid has a few warps per SM scheduler.
 StripPlan plan_strips(const Geo& g) {
   StripPlan sp;
-  sp.W = 56;
+  sp.W = 60;
   if (g.bc[0] != BC_PERIODIC)
     while ((g.n[0] - 1) % sp.W == 0) sp.W -= 2;
   sp.ntx = (g.n[0] + sp.W - 1) / sp.W;
