@@ -124,6 +124,15 @@ def _alg_bytes(family: str, P, box_cells: int, esz: int) -> float:
     return 0.0
 
 
+def _traffic(workload: str, family: str):
+    """DRAM bytes per launch of a kernel family measured by ncu (profiles/dram_traffic.json), or None."""
+    try:
+        with open(os.path.join(ROOT, "profiles", "dram_traffic.json")) as f:
+            return json.load(f)[workload][family]["bytes_per_launch"]
+    except Exception:
+        return None
+
+
 def _box_cells(P) -> int:
     import math
     s = 1 if P.weight_kind == 1 else 2
@@ -434,7 +443,7 @@ def main():
         alg = _alg_bytes(dom, P, _box_cells(P), 4)
         achieved = alg / per_launch_s / 1e9
         line["roofline"] = {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peak, "unit": "GB/s",
-                            "frac": achieved / peak, "traffic": None, "peak_source": peak_kind,
+                            "frac": achieved / peak, "traffic": _traffic(P.name, dom), "peak_source": peak_kind,
                             "alg_bytes_per_launch": alg, "avg_launch_us": per_launch_s * 1e6,
                             "kernel_ms_per_gradient": {k: round(v[0], 3) for k, v in fams.items()},
                             "launches_per_gradient": {k: v[1] for k, v in fams.items()}}

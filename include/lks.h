@@ -59,7 +59,7 @@ enum { LKS_BC_PERIODIC = 0, LKS_BC_INFLOW_OUTFLOW = 1, LKS_BC_WALL = 2, LKS_BC_P
 enum { LKS_W_COS4 = 0, LKS_W_BILINEAR = 1 };              /* grid-separation weight (Sec. 2.3) */
 enum { LKS_DOF_TX = 1, LKS_DOF_TY = 2, LKS_DOF_TZ = 4, LKS_DOF_ROT = 8 };
 enum { LKS_FP32 = 32, LKS_FP64 = 64 };                    /* field storage / arithmetic type */
-enum { LKS_CKPT_STORE_ALL = 0, LKS_CKPT_UNIFORM = 1 };
+enum { LKS_CKPT_STORE_ALL = 0, LKS_CKPT_UNIFORM = 1, LKS_CKPT_BINOMIAL = 2 };
 enum { LKS_CKPT_NATIVE = 0, LKS_CKPT_BF16 = 1, LKS_CKPT_FP16 = 2 };
 
 /* Problem statement: grid, velocity set, design grid, body, fluid, run controls. */
@@ -82,8 +82,9 @@ typedef struct lks_problem {
   int n_steps, n_itr;     /* N_t, N_itr (Sec. 3.1) */
   double obj_weights[8];  /* J = sum_d obj_weights[d] * s_d(N_t) (Eqs. objective1, objective2) */
   int field_precision;    /* LKS_FP32 or LKS_FP64 */
-  int ckpt_policy;        /* LKS_CKPT_STORE_ALL or LKS_CKPT_UNIFORM */
-  int ckpt_every;         /* checkpoint interval k for LKS_CKPT_UNIFORM */
+  int ckpt_policy;        /* LKS_CKPT_STORE_ALL, LKS_CKPT_UNIFORM or LKS_CKPT_BINOMIAL */
+  int ckpt_every;         /* UNIFORM: checkpoint interval k; BINOMIAL: number of state snapshots
+                           * (the reverse sweep recomputes along a binomial schedule) */
   int ckpt_format;        /* LKS_CKPT_NATIVE, LKS_CKPT_BF16 or LKS_CKPT_FP16 (FP32 fields) */
   size_t hbm_budget_bytes;/* workspace limit, 0 = no limit */
 } lks_problem;

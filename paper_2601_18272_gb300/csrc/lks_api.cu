@@ -7,6 +7,9 @@
 //   uniform   : ping-pong state, a checkpoint every k steps; the adjoint restores a checkpoint,
 //               recomputes the segment (stencil + Brinkman update with the stored DOF iterates)
 //               into a segment ring, then reverses it.
+//   binomial  : s state snapshots placed along a binomial schedule (the classic optimal
+//               checkpointing recursion for a fixed number of snapshots); the reverse sweep
+//               re-advances from the nearest snapshot and reverses one step at a time.
 // Adjoint (Algorithm 1, adjoint loop): per step, for k = N_itr..1 a cell-side and a design-side
 // reverse kernel, then the transposed stencil.
 #include <cmath>
@@ -50,6 +53,7 @@ struct lks_handle {
   unsigned short* ckq = nullptr;  // uniform, BF16/FP16: checkpoints at t = k, 2k, ... (t = 0 from init)
   unsigned* ckkeys = nullptr;     // their per-plane ranges
   int nckpt = 0;
+  std::vector<int> bin_pts;  // binomial: steps whose state the forward snapshots (slot j for entry j)
   long long slot_elems = 0;
   void* boxstore = nullptr;  // u* in the body box, one slab per step of the resident segment
   int nbox = 0;
@@ -158,8 +162,11 @@ int validate(const lks_problem* P) {
   if (P->weight_kind != LKS_W_COS4 && P->weight_kind != LKS_W_BILINEAR) return LKS_ERR_ARG;
   if (!(P->mass > 0.0) || !(P->inertia > 0.0)) return LKS_ERR_ARG;
   if (P->field_precision != LKS_FP32 && P->field_precision != LKS_FP64) return LKS_ERR_ARG;
-  if (P->ckpt_policy != LKS_CKPT_STORE_ALL && P->ckpt_policy != LKS_CKPT_UNIFORM) return LKS_ERR_ARG;
-  if (P->ckpt_policy == LKS_CKPT_UNIFORM && P->ckpt_every < 1) return LKS_ERR_ARG;
+  if (P->ckpt_policy != LKS_CKPT_STORE_ALL && P->ckpt_policy != LKS_CKPT_UNIFORM &&
+      P->ckpt_policy != LKS_CKPT_BINOMIAL)
+    return LKS_ERR_ARG;
+  if (P->ckpt_policy != LKS_CKPT_STORE_ALL && P->ckpt_every < 1) return LKS_ERR_ARG;
+  if (P->ckpt_policy == LKS_CKPT_BINOMIAL && P->ckpt_format != LKS_CKPT_NATIVE) return LKS_ERR_UNSUPPORTED;
   if (P->ckpt_format != LKS_CKPT_NATIVE && P->ckpt_format != LKS_CKPT_BF16 && P->ckpt_format != LKS_CKPT_FP16)
     return LKS_ERR_ARG;
   // reduced-precision checkpoints: FP32 fields with uniform checkpoints
@@ -268,6 +275,40 @@ void clear_graphs(lks_handle* h) {
   h->graph_kernels.clear();
 }
 
+// Binomial checkpointing. beta(s, r) = C(s + r, s) is the longest march that s snapshots reverse
+// with each step advanced at most r + 1 times; a march of n steps with s snapshots is split after
+// m steps, the remaining n - m being reversed with s - 1 snapshots and r repetitions and the first
+// m with s snapshots and r - 1 (beta(s, r) = beta(s, r - 1) + beta(s - 1, r)).
+long long binomial_beta(int s, int r) {
+  long long b = 1;
+  for (int i = 1; i <= s; ++i) {
+    b = b * (r + i) / i;  // C(r + i, i), exact at every step
+    if (b > (1LL << 50)) return 1LL << 50;
+  }
+  return b;
+}
+int binomial_split(int n, int s) {  // n >= 2, s >= 1
+  int r = 0;
+  while (binomial_beta(s, r) < n) ++r;
+  long long m = n - binomial_beta(s - 1, r);
+  if (m < 1) m = 1;
+  if (m > n - 1) m = n - 1;
+  return (int)m;
+}
+// The snapshots of the first descent of the recursion, which the forward pass takes on its way.
+std::vector<int> binomial_first_descent(int n, int s) {
+  std::vector<int> pts;
+  int t = 0;
+  while (s > 0 && n > 1) {
+    const int m = binomial_split(n, s);
+    t += m;
+    pts.push_back(t);
+    n -= m;
+    --s;
+  }
+  return pts;
+}
+
 template <typename T>
 void enqueue_fwd_steps(lks_handle* h, Launcher& L, const Slots<T>& S, int nsteps, bool store_box) {
   const Geo& g = h->g;
@@ -316,7 +357,24 @@ int forward_impl(lks_handle* h, cudaStream_t st) {
   const Geo& g = h->g;
   const int NT = h->P.n_steps;
   Launcher L0{h, st, false};
-  if (h->P.ckpt_policy == LKS_CKPT_STORE_ALL) {
+  if (h->P.ckpt_policy == LKS_CKPT_BINOMIAL) {
+    // march in pieces between the snapshot steps of the first descent, snapshotting each
+    Slots<T> S = pp_slots<T>(h);
+    L0("init", [&](cudaStream_t s) { launch_init_forward<T>(g, S, h->init_p, h->init_u, h->init_s, h->it, h->ctrl, s); });
+    int t = 0;
+    for (size_t j = 0; j <= h->bin_pts.size(); ++j) {
+      const int t1 = (j < h->bin_pts.size()) ? h->bin_pts[j] : NT;
+      const int n = t1 - t;
+      if (n > 0) {
+        L0("init", [&](cudaStream_t s) { launch_set_step(h->ctrl, t + 1, 0, s); });
+        TRY(run_graph(h, "fwd_b_" + std::to_string(n), st, [&](Launcher& L) { enqueue_fwd_steps<T>(h, L, S, n, false); }));
+      }
+      if (j < h->bin_pts.size())
+        CK(cudaMemcpyAsync((char*)h->ckpt + j * h->slot_elems * h->esz, (char*)h->pp + (t1 & 1) * h->slot_elems * h->esz,
+                           h->slot_elems * h->esz, cudaMemcpyDeviceToDevice, st));
+      t = t1;
+    }
+  } else if (h->P.ckpt_policy == LKS_CKPT_STORE_ALL) {
     Slots<T> S = ring_slots<T>(h);
     L0("init", [&](cudaStream_t s) { launch_init_forward<T>(g, S, h->init_p, h->init_u, h->init_s, h->it, h->ctrl, s); });
     for (int t0 = 1; t0 <= NT; t0 += h->chunk) {
@@ -355,6 +413,60 @@ int forward_impl(lks_handle* h, cudaStream_t st) {
   return LKS_OK;
 }
 
+// Reverse of steps t0+1 .. t0+n with s free snapshot slots; state(t0) is the initial state
+// (src < 0) or snapshot src. The working pair (ring) holds state(t0) in slot 0 after a restore, so
+// its slot base is t0. first: the snapshots of this branch's first descent exist (the forward took
+// them). Snapshot slot d belongs to recursion depth d.
+template <typename T>
+int binomial_reverse(lks_handle* h, cudaStream_t st, int t0, int n, int s, bool first, int src, int depth) {
+  const Geo& g = h->g;
+  Slots<T> W = ring_slots<T>(h);
+  Launcher L0{h, st, false};
+  const size_t sb = h->slot_elems * h->esz;
+  auto restore = [&]() -> int {
+    if (src < 0)
+      L0("ckpt", [&](cudaStream_t x) { launch_state_from_double<T>(g, (T*)h->ring, h->init_p, h->init_u, x); });
+    else
+      CK(cudaMemcpyAsync(h->ring, (char*)h->ckpt + (size_t)src * sb, sb, cudaMemcpyDeviceToDevice, st));
+    return LKS_OK;
+  };
+  auto advance = [&](int nadv) -> int {  // state(t0) -> state(t0 + nadv) in the working pair
+    if (nadv <= 0) return LKS_OK;
+    L0("init", [&](cudaStream_t x) { launch_set_step(h->ctrl, t0 + 1, t0, x); });
+    return run_graph(h, "bin_adv_" + std::to_string(nadv), st,
+                     [&](Launcher& L) { enqueue_recompute<T>(h, L, W, nadv); });
+  };
+  auto reverse_step = [&](int t) -> int {  // needs state(t-1) in the working pair (base t0)
+    L0("init", [&](cudaStream_t x) { launch_set_step(h->ctrl, t, t0, x); });
+    return run_graph(h, "bin_rev1", st, [&](Launcher& L) {
+      enqueue_recompute<T>(h, L, W, 1);
+      enqueue_adj_steps<T>(h, L, W, 1);
+    });
+  };
+  if (n <= 0) return LKS_OK;
+  if (n == 1) {
+    TRY(restore());
+    return reverse_step(t0 + 1);
+  }
+  if (s == 0) {  // no snapshot left: re-advance for every step
+    for (int j = n; j >= 1; --j) {
+      TRY(restore());
+      TRY(advance(j - 1));
+      TRY(reverse_step(t0 + j));
+    }
+    return LKS_OK;
+  }
+  const int m = binomial_split(n, s);
+  if (!first) {
+    TRY(restore());
+    TRY(advance(m));
+    CK(cudaMemcpyAsync((char*)h->ckpt + (size_t)depth * sb, (char*)h->ring + (size_t)(m & 1) * sb, sb,
+                       cudaMemcpyDeviceToDevice, st));
+  }
+  TRY(binomial_reverse<T>(h, st, t0 + m, n - m, s - 1, first, depth, depth + 1));
+  return binomial_reverse<T>(h, st, t0, m, s, false, src, depth);
+}
+
 template <typename T>
 int adjoint_impl(lks_handle* h, double seed, cudaStream_t st) {
   const Geo& g = h->g;
@@ -362,7 +474,9 @@ int adjoint_impl(lks_handle* h, double seed, cudaStream_t st) {
   Launcher L0{h, st, false};
   CK(cudaMemsetAsync(h->L, 0, 2 * h->slot_elems * h->esz, st));
   L0("init", [&](cudaStream_t s) { launch_adj_init(g, h->ctrl, h->objw, seed, h->dkref, g.ND, s); });
-  if (h->P.ckpt_policy == LKS_CKPT_STORE_ALL) {
+  if (h->P.ckpt_policy == LKS_CKPT_BINOMIAL) {
+    TRY(binomial_reverse<T>(h, st, 0, NT, h->P.ckpt_every, true, -1, 0));
+  } else if (h->P.ckpt_policy == LKS_CKPT_STORE_ALL) {
     Slots<T> S = ring_slots<T>(h);
     for (int t1 = NT; t1 >= 1; t1 -= h->chunk) {
       const int n = std::min(h->chunk, t1);
@@ -407,6 +521,13 @@ int allocate(lks_handle* h) {
   if (P.ckpt_policy == LKS_CKPT_STORE_ALL) {
     h->nring = NT + 1;
     h->nbox = NT;
+  } else if (P.ckpt_policy == LKS_CKPT_BINOMIAL) {
+    h->nring = 2;  // working pair of the reverse sweep
+    h->nbox = 1;
+    h->bin_pts = binomial_first_descent(NT, P.ckpt_every);
+    h->nckpt = (int)h->bin_pts.size();
+    TRY(dalloc(h, &h->pp, 2 * slot_bytes));
+    if (h->nckpt > 0) TRY(dalloc(h, &h->ckpt, (size_t)h->nckpt * slot_bytes));
   } else {
     h->nring = P.ckpt_every + 1;
     h->nbox = P.ckpt_every;

@@ -439,7 +439,7 @@ __global__ void __launch_bounds__(kCellThreads, 2) k_couple(Geo g, Slots<T> S, C
         prow[kp] = nx;
         if (kp == K) row[0] = nx;
       }
-      sd[0] = (k > 1) ? row[0] : nx;
+      sd[0] = (k > 1) ? p0 : nx;  // s(t-1): already fetched for k > 1
       sd[1] = nx;
     }
   } else if (threadIdx.x == 0) {

@@ -17,7 +17,7 @@ from . import build as _build
 LKS_OK = 0
 LKS_D2Q9, LKS_D3Q15 = 9, 15
 LKS_FP32, LKS_FP64 = 32, 64
-LKS_CKPT_STORE_ALL, LKS_CKPT_UNIFORM = 0, 1
+LKS_CKPT_STORE_ALL, LKS_CKPT_UNIFORM, LKS_CKPT_BINOMIAL = 0, 1, 2
 LKS_CKPT_NATIVE, LKS_CKPT_BF16, LKS_CKPT_FP16 = 0, 1, 2
 STATUS = {0: "LKS_OK", 1: "LKS_ERR_ARG", 2: "LKS_ERR_OOM", 3: "LKS_ERR_BUDGET", 4: "LKS_ERR_UNSTABLE",
           5: "LKS_ERR_BODY_OUTSIDE", 6: "LKS_ERR_NONFINITE", 7: "LKS_ERR_ORDER", 8: "LKS_ERR_CUDA",

@@ -12,7 +12,7 @@ import pytest
 from oracle import oracle as O
 from tests.problems import (BC_INFLOW_OUTFLOW, BC_PERIODIC, BC_PRESSURE, BC_WALL, DOF_ROT, DOF_TX, DOF_TY, DOF_TZ,
                             W_BILINEAR, W_COS4, body2d, body3d, perturbed_state)
-from workloads import CKPT_BF16, CKPT_FP16, CKPT_STORE_ALL, CKPT_UNIFORM, config, initial_state
+from workloads import CKPT_BF16, CKPT_BINOMIAL, CKPT_FP16, CKPT_STORE_ALL, CKPT_UNIFORM, config, initial_state
 
 pytestmark = pytest.mark.gpu
 
@@ -294,3 +294,31 @@ def test_reduced_precision_first_segment_exact():
     a = gpu_run(P, g, p0, u0, s0, precision=32, ckpt_policy=CKPT_UNIFORM, ckpt_every=4)
     b = gpu_run(P, g, p0, u0, s0, precision=32, ckpt_policy=CKPT_UNIFORM, ckpt_every=4, ckpt_format=CKPT_BF16)
     assert np.array_equal(a["dJdgamma"], b["dJdgamma"])
+
+
+# ---- binomial checkpointing ------------------------------------------------------------------
+
+@pytest.mark.parametrize("nt,snaps", [(11, 1), (11, 2), (23, 3), (40, 5), (7, 9)])
+def test_binomial_checkpointing_reproduces_store_all(nt, snaps):
+    """Binomial snapshots (the reverse sweep re-advances from the nearest snapshot along the
+    optimal recursion): the recomputed states are those of the forward, so the gradient equals the
+    store-all gradient (FP64) to rounding."""
+    P, g = body2d(nt=nt)
+    p0, u0, s0 = perturbed_state(P)
+    a = gpu_run(P, g, p0, u0, s0, precision=64, ckpt_policy=CKPT_STORE_ALL)
+    b = gpu_run(P, g, p0, u0, s0, precision=64, ckpt_policy=CKPT_BINOMIAL, ckpt_every=snaps)
+    assert a["J"] == b["J"]
+    np.testing.assert_array_equal(a["hist"], b["hist"])
+    assert rel(b["dJdgamma"], a["dJdgamma"]) < 1e-12
+    assert rel(b["lam_u0"], a["lam_u0"]) < 1e-12
+    np.testing.assert_allclose(b["lam_dof0"], a["lam_dof0"], rtol=1e-12, atol=1e-15)
+
+
+def test_binomial_fp32_3d_matches_oracle():
+    P, g = CASES_3D[0][1]()
+    P = P.replace(n_steps=10)
+    p0, u0, s0 = perturbed_state(P)
+    G = O.gradient(P, g, p0, u0, s0)
+    r = gpu_run(P, g, p0, u0, s0, precision=32, ckpt_policy=CKPT_BINOMIAL, ckpt_every=2)
+    assert abs(r["J"] - G["J"]) <= 1e-4 * abs(G["J"])
+    assert rel(r["dJdgamma"], G["dJdgamma"]) <= 1e-3

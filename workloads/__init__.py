@@ -10,6 +10,7 @@ from .synth import (  # noqa: F401
     BC_PRESSURE,
     BC_WALL,
     CKPT_BF16,
+    CKPT_BINOMIAL,
     CKPT_FP16,
     CKPT_FP32,
     CKPT_STORE_ALL,

@@ -38,6 +38,7 @@ DOF_ROT = 8
 # Checkpoint policies and storage formats.
 CKPT_STORE_ALL = 0
 CKPT_UNIFORM = 1
+CKPT_BINOMIAL = 2
 CKPT_FP32 = 0
 CKPT_BF16 = 1
 CKPT_FP16 = 2
