@@ -28,6 +28,20 @@
 //   centre; DOF^(0) = DOF(t-1), u(t) from the last iteration, DOF(t) = DOF^(N_itr); lever arm
 //   R(theta^(k-1)) r_m; M and I held constant.
 //
+// Free rotation in 3D (six DOFs; the paper treats one rotation axis and names Euler angles or
+// quaternions as the extension). The DOF vector is s = (x^G[3], u^G[3], h[3], omega[3], R[9]),
+// R row-major, h the angular momentum and omega the angular velocity (world frame). Explicit
+// Euler with the body's inertia frozen over the step, velocity first as in the paper's scheme:
+//   h^(k) = h(t-1) + T^(k),  omega^(k) = R(t-1) I_b^-1 R(t-1)^T h^(k),
+//   R^(k) = exp([omega^(k)]x) R(t-1)   (Rodrigues' formula for the rotation by |omega| about omega),
+// with I_b the body-frame inertia tensor about the pivot; the transform of iteration k uses
+// R^(k-1) and omega^(k-1) (lever arm R r_m, solid velocity u^G + omega x R r_m). For a body whose
+// rotation stays about one principal axis this is the single-axis scheme.
+//
+// Design domain: with design_radius > 0 only the design points with |r_m| <= design_radius
+// belong to the body (a ball-shaped design domain); the others take no part in any sum and
+// their sensitivity is zero.
+//
 // Templated on the scalar type: double, and std::complex<double> for complex-step derivatives.
 // Every branch (kernel support, floor, bilinear sign) is taken on the real part.
 
@@ -58,7 +72,7 @@ extern "C" struct OracleProblem {
   int dim;             // 2 or 3
   int nx, ny, nz;      // analysis grid (nz = 1 in 2D)
   int ndx, ndy, ndz;   // design grid (ndz = 1 in 2D)
-  int rot_axis;        // single rotation axis (2 = z in 2D)
+  int rot_axis;        // single rotation axis (2 = z in 2D), or -1: free rotation (3D)
   int dof_mask;        // DOF_TX | DOF_TY | DOF_TZ | DOF_ROT
   int bc[3];           // boundary kind per axis
   int weight_kind;     // W_COS4 or W_BILINEAR
@@ -71,7 +85,9 @@ extern "C" struct OracleProblem {
   double dp;           // pressure at the inlet for the pressure-driven boundary
   double kappa_max;    // kappa_max in the Brinkman interpolation
   double q;            // convexity parameter
-  double obj_w[8];     // J = sum_d obj_w[d] * s_d(N_t) over (xG, uG, theta, omega)
+  double obj_w[21];    // J = sum_d obj_w[d] * s_d(N_t) over the DOF vector
+  double inertia_tensor[9];  // free rotation: body-frame inertia tensor about the pivot
+  double design_radius;      // > 0: ball-shaped design domain |r_m| <= design_radius
 };
 
 namespace {
@@ -128,7 +144,26 @@ struct Ctx {
   int support;    // kernel half-width in cells
   int err = ORC_OK;
   std::vector<double> r;  // r_m = xi_m - xi^G, [ND][3]
+  std::vector<char> dom;  // design point m belongs to the design domain
+  bool free_rot = false;  // six DOFs
+  int ns = 8;             // DOF vector length: 8, or 21 with free rotation
+  double Jinv[9];         // free rotation: I_b^-1
 };
+
+// Inverse of a symmetric positive definite 3x3 matrix (row-major) by cofactors; false unless
+// the leading minors are positive.
+bool invert3(const double* a, double* inv) {
+  const double m1 = a[0], m2 = a[0] * a[4] - a[1] * a[3];
+  const double c00 = a[4] * a[8] - a[5] * a[7], c01 = a[5] * a[6] - a[3] * a[8], c02 = a[3] * a[7] - a[4] * a[6];
+  const double det = a[0] * c00 + a[1] * c01 + a[2] * c02;
+  if (!(m1 > 0.0) || !(m2 > 0.0) || !(det > 0.0)) return false;
+  const double c10 = a[2] * a[7] - a[1] * a[8], c11 = a[0] * a[8] - a[2] * a[6], c12 = a[1] * a[6] - a[0] * a[7];
+  const double c20 = a[1] * a[5] - a[2] * a[4], c21 = a[2] * a[3] - a[0] * a[5], c22 = a[0] * a[4] - a[1] * a[3];
+  // inverse = adjugate / det, the adjugate being the transposed cofactor matrix
+  const double adj[9] = {c00, c10, c20, c01, c11, c21, c02, c12, c22};
+  for (int i = 0; i < 9; ++i) inv[i] = adj[i] / det;
+  return true;
+}
 
 bool make_ctx(const OracleProblem* P, Ctx* C) {
   C->P = *P;
@@ -149,7 +184,10 @@ bool make_ctx(const OracleProblem* P, Ctx* C) {
   for (int a = 1; a < 3; ++a)
     if (P->bc[a] != BC_PERIODIC && P->bc[a] != BC_WALL) return false;
   if (C->d == 2 && P->rot_axis != 2) return false;
-  if (P->rot_axis < 0 || P->rot_axis > 2) return false;
+  C->free_rot = (C->d == 3 && P->rot_axis == -1);
+  if (!C->free_rot && (P->rot_axis < 0 || P->rot_axis > 2)) return false;
+  C->ns = C->free_rot ? 21 : 8;
+  if (C->free_rot && !invert3(P->inertia_tensor, C->Jinv)) return false;
   if (P->n_itr < 1 || P->n_steps < 0) return false;
   C->A = 4.5 * (1.0 / 6.0 - P->nu);
   C->support = (P->weight_kind == W_BILINEAR) ? 1 : 2;
@@ -162,6 +200,12 @@ bool make_ctx(const OracleProblem* P, Ctx* C) {
         C->r[3 * m + 1] = j - (C->nd[1] - 1) / 2.0;
         C->r[3 * m + 2] = (C->d == 3) ? k - (C->nd[2] - 1) / 2.0 : 0.0;
       }
+  C->dom.assign(C->ND, 1);
+  if (P->design_radius > 0.0)
+    for (size_t m = 0; m < C->ND; ++m) {
+      const double* r = &C->r[3 * m];
+      C->dom[m] = (r[0] * r[0] + r[1] * r[1] + r[2] * r[2] <= P->design_radius * P->design_radius) ? 1 : 0;
+    }
   return true;
 }
 
@@ -473,6 +517,23 @@ void transform(const Ctx& C, const T* s, Geometry<T>* g) {
   g->usref.assign(ND * 3, T(0));
   g->lev.assign(ND * 3, T(0));
   g->dlev.assign(ND * 3, T(0));
+  if (C.free_rot) {
+    // x^ref = x^G + R r, u^S,ref = u^G + omega x (R r); dlev unused
+    const T* om = s + 9;
+    const T* R = s + 12;
+    for (size_t m = 0; m < ND; ++m) {
+      const double* r = &C.r[3 * m];
+      T l[3];
+      for (int i = 0; i < 3; ++i) l[i] = R[3 * i + 0] * r[0] + R[3 * i + 1] * r[1] + R[3 * i + 2] * r[2];
+      const T w[3] = {om[1] * l[2] - om[2] * l[1], om[2] * l[0] - om[0] * l[2], om[0] * l[1] - om[1] * l[0]};
+      for (int a = 0; a < 3; ++a) {
+        g->lev[3 * m + a] = l[a];
+        g->xref[3 * m + a] = s[a] + l[a];
+        g->usref[3 * m + a] = s[3 + a] + w[a];
+      }
+    }
+    return;
+  }
   int ax = C.P.rot_axis, b, c;
   plane_axes(ax, &b, &c);
   T ct = std::cos(s[6]), st = std::sin(s[6]);
@@ -566,8 +627,75 @@ struct IterRecord {
   std::vector<T> kap, us[3], u[3];  // analysis-grid fields
   std::vector<T> uref;              // [ND][3]
   Geometry<T> geo;
-  T F[3], Tq;
+  T F[3], Tq;  // force; torque about the rotation axis
+  T Tv[3];     // free rotation: torque vector
 };
+
+// Rodrigues' formula: the rotation by |v| about v, Q = I + a [v]x + b [v]x^2 with
+// a = sin|v| / |v| and b = (1 - cos|v|) / |v|^2, from their power series in x = v.v when |v| is
+// small (terms to x^10, remainder below 1e-40 for |v| < 0.1).
+template <class T>
+void rodrigues(const T* v, T* Q) {
+  const T x = v[0] * v[0] + v[1] * v[1] + v[2] * v[2];
+  T a, b;
+  if (std::fabs(re(x)) < 1e-2) {
+    T ta = T(1), tb = T(0.5);  // k = 0 terms: 1/1!, 1/2!
+    a = ta;
+    b = tb;
+    for (int k = 1; k <= 10; ++k) {
+      ta *= -x / double((2 * k) * (2 * k + 1));
+      tb *= -x / double((2 * k + 1) * (2 * k + 2));
+      a += ta;
+      b += tb;
+    }
+  } else {
+    const T th = std::sqrt(x);
+    a = std::sin(th) / th;
+    b = (1.0 - std::cos(th)) / x;
+  }
+  const T K[9] = {T(0), -v[2], v[1], v[2], T(0), -v[0], -v[1], v[0], T(0)};
+  for (int i = 0; i < 3; ++i)
+    for (int j = 0; j < 3; ++j) {
+      T k2 = T(0);
+      for (int l = 0; l < 3; ++l) k2 += K[3 * i + l] * K[3 * l + j];
+      Q[3 * i + j] = (i == j ? T(1) : T(0)) + a * K[3 * i + j] + b * k2;
+    }
+}
+
+// Explicit Euler EOM of one coupling iteration (Sec. 2.4), velocity first, masked by the DOFs:
+// from s(t-1) = s0 and the iteration's force F and torque (Tq about the axis, or the vector Tv
+// with free rotation) to s^(k).
+template <class T>
+void eom_apply(const Ctx& C, const T* s0, const T* F, T Tq, const T* Tv, T* out) {
+  for (int a = 0; a < C.ns; ++a) out[a] = s0[a];
+  const int mask = C.P.dof_mask;
+  for (int a = 0; a < C.d; ++a) {
+    if (!(mask & (1 << a))) continue;
+    out[3 + a] = s0[3 + a] + F[a] / C.P.mass;
+    out[a] = s0[a] + out[3 + a];
+  }
+  if (!(mask & DOF_ROT)) return;
+  if (!C.free_rot) {
+    out[7] = s0[7] + Tq / C.P.inertia;
+    out[6] = s0[6] + out[7];
+    return;
+  }
+  const T* R0 = s0 + 12;
+  T h[3], v1[3], v2[3], w[3];
+  for (int a = 0; a < 3; ++a) h[a] = s0[6 + a] + Tv[a];
+  for (int j = 0; j < 3; ++j) v1[j] = R0[0 + j] * h[0] + R0[3 + j] * h[1] + R0[6 + j] * h[2];  // R0^T h
+  for (int i = 0; i < 3; ++i) v2[i] = C.Jinv[3 * i + 0] * v1[0] + C.Jinv[3 * i + 1] * v1[1] + C.Jinv[3 * i + 2] * v1[2];
+  for (int i = 0; i < 3; ++i) w[i] = R0[3 * i + 0] * v2[0] + R0[3 * i + 1] * v2[1] + R0[3 * i + 2] * v2[2];
+  T Q[9];
+  rodrigues(w, Q);
+  for (int a = 0; a < 3; ++a) {
+    out[6 + a] = h[a];
+    out[9 + a] = w[a];
+  }
+  for (int i = 0; i < 3; ++i)
+    for (int j = 0; j < 3; ++j)
+      out[12 + 3 * i + j] = Q[3 * i + 0] * R0[0 + j] + Q[3 * i + 1] * R0[3 + j] + Q[3 * i + 2] * R0[6 + j];
+}
 
 template <class T>
 void coupling_iteration(Ctx& C, const std::vector<T>& kref, const T* s_prev_iter, const T* s_step_start,
@@ -584,6 +712,7 @@ void coupling_iteration(Ctx& C, const std::vector<T>& kref, const T* s_prev_iter
   std::vector<T> wv, dwv;
   // spread (Eqs. kappa_mapping, us_mapping): scatter each design point over its window
   for (size_t m = 0; m < ND; ++m) {
+    if (!C.dom[m]) continue;
     window(C, &rec->geo.xref[3 * m], &wn, &wv, &dwv);
     for (size_t q = 0; q < wn.size(); ++q) {
       rec->kap[wn[q].n] += wv[q] * kref[m];
@@ -596,35 +725,33 @@ void coupling_iteration(Ctx& C, const std::vector<T>& kref, const T* s_prev_iter
   // interpolation to the design points (Eq. u_mapping)
   rec->uref.assign(ND * 3, T(0));
   for (size_t m = 0; m < ND; ++m) {
+    if (!C.dom[m]) continue;
     window(C, &rec->geo.xref[3 * m], &wn, &wv, &dwv);
     for (size_t q = 0; q < wn.size(); ++q)
       for (int a = 0; a < d; ++a) rec->uref[3 * m + a] += wv[q] * rec->u[a][wn[q].n];
   }
   // force and torque from the design-grid sums (Sec. 2.4); lever arm x^ref - x^G = R r
-  int ax = C.P.rot_axis, b, c;
+  int ax = C.free_rot ? 2 : C.P.rot_axis, b, c;
   plane_axes(ax, &b, &c);
-  T F[3] = {T(0), T(0), T(0)}, Tq = T(0);
+  T F[3] = {T(0), T(0), T(0)}, Tq = T(0), Tv[3] = {T(0), T(0), T(0)};
   for (size_t m = 0; m < ND; ++m) {
+    if (!C.dom[m]) continue;
     T D[3];
     for (int a = 0; a < 3; ++a) D[a] = (a < d) ? rec->uref[3 * m + a] - rec->geo.usref[3 * m + a] : T(0);
     for (int a = 0; a < d; ++a) F[a] += kref[m] * D[a];
     const T* l = &rec->geo.lev[3 * m];
     Tq += kref[m] * (l[b] * D[c] - l[c] * D[b]);
+    Tv[0] += kref[m] * (l[1] * D[2] - l[2] * D[1]);
+    Tv[1] += kref[m] * (l[2] * D[0] - l[0] * D[2]);
+    Tv[2] += kref[m] * (l[0] * D[1] - l[1] * D[0]);
   }
-  for (int a = 0; a < 3; ++a) rec->F[a] = F[a];
+  for (int a = 0; a < 3; ++a) {
+    rec->F[a] = F[a];
+    rec->Tv[a] = Tv[a];
+  }
   rec->Tq = Tq;
   // explicit Euler EOM, velocity first (Eqs. equation_of_motion_*_discretized), masked by the DOFs
-  for (int a = 0; a < 8; ++a) s_new[a] = s_step_start[a];
-  const int mask = C.P.dof_mask;
-  for (int a = 0; a < d; ++a) {
-    if (!(mask & (1 << a))) continue;
-    s_new[3 + a] = s_step_start[3 + a] + F[a] / C.P.mass;
-    s_new[a] = s_step_start[a] + s_new[3 + a];
-  }
-  if (mask & DOF_ROT) {
-    s_new[7] = s_step_start[7] + Tq / C.P.inertia;
-    s_new[6] = s_step_start[6] + s_new[7];
-  }
+  eom_apply(C, s_step_start, F, Tq, Tv, s_new);
 }
 
 template <class T>
@@ -632,14 +759,15 @@ void forward_step(Ctx& C, const std::vector<T>& kref, const Fields<T>& prev, con
                   T* s_next, std::vector<T>* iters_out) {
   Fields<T> star;
   stencil_fwd(C, prev, &star);
-  const int K = C.P.n_itr;
-  std::vector<T> it((size_t)(K + 1) * 8);
-  for (int a = 0; a < 8; ++a) it[a] = s_prev[a];
+  const int K = C.P.n_itr, ns = C.ns;
+  std::vector<T> it((size_t)(K + 1) * ns);
+  for (int a = 0; a < ns; ++a) it[a] = s_prev[a];
   IterRecord<T> rec;
-  for (int k = 1; k <= K; ++k) coupling_iteration(C, kref, &it[(size_t)(k - 1) * 8], s_prev, star, &rec, &it[(size_t)k * 8]);
+  for (int k = 1; k <= K; ++k)
+    coupling_iteration(C, kref, &it[(size_t)(k - 1) * ns], s_prev, star, &rec, &it[(size_t)k * ns]);
   next->p = star.p;
   for (int a = 0; a < 3; ++a) next->u[a] = rec.u[a];
-  for (int a = 0; a < 8; ++a) s_next[a] = it[(size_t)K * 8 + a];
+  for (int a = 0; a < ns; ++a) s_next[a] = it[(size_t)K * ns + a];
   if (iters_out) *iters_out = it;
 }
 
@@ -647,7 +775,8 @@ void forward_step(Ctx& C, const std::vector<T>& kref, const Fields<T>& prev, con
 template <class T>
 std::vector<T> brinkman(const Ctx& C, const T* gamma) {
   std::vector<T> k(C.ND);
-  for (size_t m = 0; m < C.ND; ++m) k[m] = C.P.kappa_max * C.P.q * gamma[m] / ((1.0 - gamma[m]) + C.P.q);
+  for (size_t m = 0; m < C.ND; ++m)
+    k[m] = C.dom[m] ? C.P.kappa_max * C.P.q * gamma[m] / ((1.0 - gamma[m]) + C.P.q) : T(0);
   return k;
 }
 
@@ -662,7 +791,7 @@ void load_fields(const Ctx& C, const T* p, const T* u, Fields<T>* f) {
 template <class T>
 T objective(const Ctx& C, const T* s) {
   T J = T(0);
-  for (int a = 0; a < 8; ++a) J += C.P.obj_w[a] * s[a];
+  for (int a = 0; a < C.ns; ++a) J += C.P.obj_w[a] * s[a];
   return J;
 }
 
@@ -681,12 +810,158 @@ bool finite_fields(const Ctx& C, const Fields<double>& f) {
 //   out: lam_ustar += dJ/du* ; lam_prev += direct EOM part of dJ/ds(t-1) ;
 //        lam_skm1 = dJ/ds^(k-1) through the transform ; dkref += dJ/dkappa^ref
 // ------------------------------------------------------------------------------------------
-void coupling_iteration_vjp(Ctx& C, const std::vector<double>& kref, const IterRecord<double>& rec,
-                            const double* s_km1, const double* lam_sk, const Fields<double>* lam_uk_ext,
-                            Fields<double>* lam_ustar, double* lam_prev, double* lam_skm1, std::vector<double>* dkref) {
+// Reverse of the interpolation, Brinkman update and spread of one coupling iteration, given
+// dJ/du^ref (l_uref): accumulates dJ/du* into lam_ustar, dJ/du^S,ref into l_usref, dJ/dx^ref into
+// l_xref and the kernel-weight part of dJ/dkappa^ref into dkref.
+void mapping_vjp(Ctx& C, const std::vector<double>& kref, const IterRecord<double>& rec,
+                 const std::vector<double>& l_uref, const Fields<double>* lam_uk_ext, Fields<double>* lam_ustar,
+                 std::vector<double>* l_usref_p, std::vector<double>* l_xref_p, std::vector<double>* dkref) {
   const int d = C.d;
   const size_t N = C.N, ND = C.ND;
+  std::vector<double>& l_usref = *l_usref_p;
+  std::vector<double>& l_xref = *l_xref_p;
+  // interpolation reverse
+  Fields<double> lam_uk;
+  lam_uk.alloc(C);
+  if (lam_uk_ext)
+    for (int a = 0; a < d; ++a) lam_uk.u[a] = lam_uk_ext->u[a];
+  std::vector<WindowNode> wn;
+  std::vector<double> wv, dwv;
+  for (size_t m = 0; m < ND; ++m) {
+    if (!C.dom[m]) continue;
+    window(C, &rec.geo.xref[3 * m], &wn, &wv, &dwv);
+    for (size_t q = 0; q < wn.size(); ++q) {
+      double ul = 0;
+      for (int a = 0; a < d; ++a) {
+        lam_uk.u[a][wn[q].n] += wv[q] * l_uref[3 * m + a];
+        ul += rec.u[a][wn[q].n] * l_uref[3 * m + a];
+      }
+      for (int e = 0; e < d; ++e) l_xref[3 * m + e] += dwv[3 * q + e] * ul;
+    }
+  }
+  // Brinkman reverse
+  std::vector<double> l_kap(N, 0.0);
+  std::vector<double> l_us[3];
+  for (int a = 0; a < d; ++a) l_us[a].assign(N, 0.0);
+  for (size_t n = 0; n < N; ++n) {
+    double inv = 1.0 / (1.0 + rec.kap[n]);
+    double lk = 0;
+    for (int a = 0; a < d; ++a) {
+      double lu = lam_uk.u[a][n];
+      lam_ustar->u[a][n] += lu * inv;
+      lk += lu * (rec.us[a][n] - rec.u[a][n]) * inv;
+      l_us[a][n] = lu * rec.kap[n] * inv;
+    }
+    l_kap[n] = lk;
+  }
+  // spread reverse
+  for (size_t m = 0; m < ND; ++m) {
+    if (!C.dom[m]) continue;
+    window(C, &rec.geo.xref[3 * m], &wn, &wv, &dwv);
+    double dk = 0;
+    for (size_t q = 0; q < wn.size(); ++q) {
+      size_t n = wn[q].n;
+      dk += wv[q] * l_kap[n];
+      double su = kref[m] * l_kap[n];
+      for (int a = 0; a < d; ++a) {
+        l_usref[3 * m + a] += wv[q] * l_us[a][n];
+        su += rec.geo.usref[3 * m + a] * l_us[a][n];
+      }
+      for (int e = 0; e < d; ++e) l_xref[3 * m + e] += dwv[3 * q + e] * su;
+    }
+    (*dkref)[m] += dk;
+  }
+}
+
+// Reverse of eom_apply with free rotation, by complex-step derivatives: column j of the Jacobian
+// of s^(k) with respect to the inputs (s0[21], F[3], Tv[3]) is Im eom_apply(input + i h e_j) / h,
+// exact to rounding (no difference is taken). lam_in[j] = sum_i lam_out[i] d out_i / d in_j.
+void eom_vjp_free(const Ctx& C, const double* s0, const double* F, const double* Tv, const double* lam_out,
+                  double* lam_in) {
+  const int ns = C.ns, nin = ns + 6;
+  const double h = 1e-30;
+  for (int j = 0; j < nin; ++j) {
+    cplx in[27], out[21];
+    for (int a = 0; a < ns; ++a) in[a] = cplx(s0[a], 0.0);
+    for (int a = 0; a < 3; ++a) {
+      in[ns + a] = cplx(F[a], 0.0);
+      in[ns + 3 + a] = cplx(Tv[a], 0.0);
+    }
+    in[j] += cplx(0.0, h);
+    eom_apply<cplx>(C, in, in + ns, cplx(0.0), in + ns + 3, out);
+    double acc = 0.0;
+    for (int i = 0; i < ns; ++i) acc += lam_out[i] * (out[i].imag() / h);
+    lam_in[j] = acc;
+  }
+}
+
+// Exact reverse of coupling_iteration with free rotation (see coupling_iteration_vjp).
+void coupling_iteration_vjp_free(Ctx& C, const std::vector<double>& kref, const IterRecord<double>& rec,
+                                 const double* s_km1, const double* s_step_start, const double* lam_sk,
+                                 const Fields<double>* lam_uk_ext, Fields<double>* lam_ustar, double* lam_prev,
+                                 double* lam_skm1, std::vector<double>* dkref) {
+  const size_t ND = C.ND;
+  const int ns = C.ns;
+  // EOM reverse
+  double lin[27];
+  eom_vjp_free(C, s_step_start, rec.F, rec.Tv, lam_sk, lin);
+  for (int a = 0; a < ns; ++a) lam_prev[a] += lin[a];
+  const double* lF = lin + ns;
+  const double* lT = lin + ns + 3;
+  // force / torque reverse: F = sum_m kappa_m D_m, T = sum_m kappa_m l_m x D_m, D = u^ref - u^S,ref
+  std::vector<double> l_uref(ND * 3, 0.0), l_usref(ND * 3, 0.0), l_lev(ND * 3, 0.0), l_xref(ND * 3, 0.0);
+  for (size_t m = 0; m < ND; ++m) {
+    if (!C.dom[m]) continue;
+    const double* l = &rec.geo.lev[3 * m];
+    double D[3];
+    for (int a = 0; a < 3; ++a) D[a] = rec.uref[3 * m + a] - rec.geo.usref[3 * m + a];
+    const double txl[3] = {lT[1] * l[2] - lT[2] * l[1], lT[2] * l[0] - lT[0] * l[2], lT[0] * l[1] - lT[1] * l[0]};
+    const double dxt[3] = {D[1] * lT[2] - D[2] * lT[1], D[2] * lT[0] - D[0] * lT[2], D[0] * lT[1] - D[1] * lT[0]};
+    double dk = 0;
+    for (int a = 0; a < 3; ++a) {
+      const double lD = kref[m] * (lF[a] + txl[a]);  // d/dD of lF.D + lT.(l x D) = D.(lT x l)
+      l_uref[3 * m + a] = lD;
+      l_usref[3 * m + a] = -lD;
+      l_lev[3 * m + a] += kref[m] * dxt[a];           // lT.(l x D) = l.(D x lT)
+      dk += lF[a] * D[a] + txl[a] * D[a];
+    }
+    (*dkref)[m] += dk;
+  }
+  mapping_vjp(C, kref, rec, l_uref, lam_uk_ext, lam_ustar, &l_usref, &l_xref, dkref);
+  // transform reverse: xref = xG + R r, usref = uG + omega x (R r), lev = R r
+  for (int a = 0; a < ns; ++a) lam_skm1[a] = 0.0;
+  const double* om = s_km1 + 9;
+  for (size_t m = 0; m < ND; ++m) {
+    if (!C.dom[m]) continue;
+    const double* l = &rec.geo.lev[3 * m];
+    const double* r = &C.r[3 * m];
+    const double* lu = &l_usref[3 * m];
+    const double lxu[3] = {l[1] * lu[2] - l[2] * lu[1], l[2] * lu[0] - l[0] * lu[2], l[0] * lu[1] - l[1] * lu[0]};
+    const double uxo[3] = {lu[1] * om[2] - lu[2] * om[1], lu[2] * om[0] - lu[0] * om[2], lu[0] * om[1] - lu[1] * om[0]};
+    for (int a = 0; a < 3; ++a) {
+      lam_skm1[a] += l_xref[3 * m + a];
+      lam_skm1[3 + a] += lu[a];
+      lam_skm1[9 + a] += lxu[a];  // lu.(omega x l) = omega.(l x lu)
+    }
+    for (int i = 0; i < 3; ++i) {
+      const double gl = l_lev[3 * m + i] + l_xref[3 * m + i] + uxo[i];  // lu.(omega x l) = l.(lu x omega)
+      for (int j = 0; j < 3; ++j) lam_skm1[12 + 3 * i + j] += gl * r[j];
+    }
+  }
+}
+
+void coupling_iteration_vjp(Ctx& C, const std::vector<double>& kref, const IterRecord<double>& rec,
+                            const double* s_km1, const double* s_step_start, const double* lam_sk,
+                            const Fields<double>* lam_uk_ext, Fields<double>* lam_ustar, double* lam_prev,
+                            double* lam_skm1, std::vector<double>* dkref) {
+  const int d = C.d;
+  const size_t ND = C.ND;
   const int mask = C.P.dof_mask;
+  if (C.free_rot) {
+    coupling_iteration_vjp_free(C, kref, rec, s_km1, s_step_start, lam_sk, lam_uk_ext, lam_ustar, lam_prev, lam_skm1,
+                                dkref);
+    return;
+  }
   // EOM reverse
   double lF[3] = {0, 0, 0}, lT = 0;
   for (int a = 0; a < 3; ++a) {
@@ -715,6 +990,7 @@ void coupling_iteration_vjp(Ctx& C, const std::vector<double>& kref, const IterR
   plane_axes(ax, &b, &c);
   std::vector<double> l_uref(ND * 3, 0.0), l_usref(ND * 3, 0.0), l_lev(ND * 3, 0.0), l_xref(ND * 3, 0.0);
   for (size_t m = 0; m < ND; ++m) {
+    if (!C.dom[m]) continue;
     double D[3];
     for (int a = 0; a < 3; ++a) D[a] = (a < d) ? rec.uref[3 * m + a] - rec.geo.usref[3 * m + a] : 0.0;
     const double* l = &rec.geo.lev[3 * m];
@@ -733,59 +1009,12 @@ void coupling_iteration_vjp(Ctx& C, const std::vector<double>& kref, const IterR
     dk += lT * (l[b] * D[c] - l[c] * D[b]);
     (*dkref)[m] += dk;
   }
-  // interpolation reverse
-  Fields<double> lam_uk;
-  lam_uk.alloc(C);
-  if (lam_uk_ext)
-    for (int a = 0; a < d; ++a) lam_uk.u[a] = lam_uk_ext->u[a];
-  std::vector<WindowNode> wn;
-  std::vector<double> wv, dwv;
-  for (size_t m = 0; m < ND; ++m) {
-    window(C, &rec.geo.xref[3 * m], &wn, &wv, &dwv);
-    for (size_t q = 0; q < wn.size(); ++q) {
-      double ul = 0;
-      for (int a = 0; a < d; ++a) {
-        lam_uk.u[a][wn[q].n] += wv[q] * l_uref[3 * m + a];
-        ul += rec.u[a][wn[q].n] * l_uref[3 * m + a];
-      }
-      for (int e = 0; e < d; ++e) l_xref[3 * m + e] += dwv[3 * q + e] * ul;
-    }
-  }
-  // Brinkman reverse
-  std::vector<double> l_kap(N, 0.0);
-  std::vector<double> l_us[3];
-  for (int a = 0; a < d; ++a) l_us[a].assign(N, 0.0);
-  for (size_t n = 0; n < N; ++n) {
-    double inv = 1.0 / (1.0 + rec.kap[n]);
-    double lk = 0;
-    for (int a = 0; a < d; ++a) {
-      double lu = lam_uk.u[a][n];
-      lam_ustar->u[a][n] += lu * inv;
-      lk += lu * (rec.us[a][n] - rec.u[a][n]) * inv;
-      l_us[a][n] = lu * rec.kap[n] * inv;
-    }
-    l_kap[n] = lk;
-  }
-  // spread reverse
-  for (size_t m = 0; m < ND; ++m) {
-    window(C, &rec.geo.xref[3 * m], &wn, &wv, &dwv);
-    double dk = 0;
-    for (size_t q = 0; q < wn.size(); ++q) {
-      size_t n = wn[q].n;
-      dk += wv[q] * l_kap[n];
-      double su = kref[m] * l_kap[n];
-      for (int a = 0; a < d; ++a) {
-        l_usref[3 * m + a] += wv[q] * l_us[a][n];
-        su += rec.geo.usref[3 * m + a] * l_us[a][n];
-      }
-      for (int e = 0; e < d; ++e) l_xref[3 * m + e] += dwv[3 * q + e] * su;
-    }
-    (*dkref)[m] += dk;
-  }
+  mapping_vjp(C, kref, rec, l_uref, lam_uk_ext, lam_ustar, &l_usref, &l_xref, dkref);
   // transform reverse: xref = xG + R r, usref = uG + omega R' r, lev = R r
   for (int a = 0; a < 8; ++a) lam_skm1[a] = 0.0;
   const double om = s_km1[7];
   for (size_t m = 0; m < ND; ++m) {
+    if (!C.dom[m]) continue;
     const double* l = &rec.geo.lev[3 * m];
     const double* dl = &rec.geo.dlev[3 * m];
     double ddl[3];  // R'' r = -(R r) in the rotation plane, 0 along the axis
@@ -806,8 +1035,8 @@ void coupling_iteration_vjp(Ctx& C, const std::vector<double>& kref, const IterR
 // Full forward with every state and DOF iterate stored, then the exact reverse sweep.
 struct Trajectory {
   std::vector<Fields<double>> states;  // t = 0..N_t
-  std::vector<std::vector<double>> iters;  // per step t = 1..N_t: (K+1)*8
-  std::vector<double> s;               // (N_t+1)*8
+  std::vector<std::vector<double>> iters;  // per step t = 1..N_t: (K+1)*ns
+  std::vector<double> s;               // (N_t+1)*ns
 };
 
 int run_forward(Ctx& C, const std::vector<double>& kref, const double* p0, const double* u0, const double* dof0,
@@ -815,8 +1044,9 @@ int run_forward(Ctx& C, const std::vector<double>& kref, const double* p0, const
   const int NT = C.P.n_steps;
   Fields<double> cur;
   load_fields(C, p0, u0, &cur);
-  tr->s.assign((size_t)(NT + 1) * 8, 0.0);
-  for (int a = 0; a < 8; ++a) tr->s[a] = dof0[a];
+  const int ns = C.ns;
+  tr->s.assign((size_t)(NT + 1) * ns, 0.0);
+  for (int a = 0; a < ns; ++a) tr->s[a] = dof0[a];
   if (keep) {
     tr->states.clear();
     tr->states.push_back(cur);
@@ -825,7 +1055,7 @@ int run_forward(Ctx& C, const std::vector<double>& kref, const double* p0, const
   for (int t = 1; t <= NT; ++t) {
     Fields<double> nxt;
     std::vector<double> it;
-    forward_step(C, kref, cur, &tr->s[(size_t)(t - 1) * 8], &nxt, &tr->s[(size_t)t * 8], keep ? &it : nullptr);
+    forward_step(C, kref, cur, &tr->s[(size_t)(t - 1) * ns], &nxt, &tr->s[(size_t)t * ns], keep ? &it : nullptr);
     cur.p.swap(nxt.p);
     for (int a = 0; a < 3; ++a) cur.u[a].swap(nxt.u[a]);
     if (keep) {
@@ -843,8 +1073,10 @@ int run_forward(Ctx& C, const std::vector<double>& kref, const double* p0, const
 }  // namespace
 
 // ============================================================================================
-// C API (ctypes). Field arrays: p [N], u [dim][N] planes, x fastest. DOF vectors: 8 doubles
-// (xG_x, xG_y, xG_z, uG_x, uG_y, uG_z, theta, omega). Return: 0 ok, else an ORC_ERR_* code.
+// C API (ctypes). Field arrays: p [N], u [dim][N] planes, x fastest. DOF vectors: ns doubles,
+// ns = 8 (xG_x, xG_y, xG_z, uG_x, uG_y, uG_z, theta, omega) for a single rotation axis, or 21
+// (xG[3], uG[3], h[3], omega[3], R[9] row-major) for free rotation. Return: 0 ok, else an
+// ORC_ERR_* code.
 // ============================================================================================
 extern "C" {
 
@@ -852,7 +1084,14 @@ int oracle_abi_version(void) { return 1; }
 
 int oracle_sizeof_problem(void) { return (int)sizeof(OracleProblem); }
 
-// Forward march: final fields, DOF history [(n_steps+1)*8] (optional), J (optional).
+// Length of the DOF vector of the problem (0 if the problem is invalid).
+int oracle_dof_count(const OracleProblem* P) {
+  Ctx C;
+  if (!make_ctx(P, &C)) return 0;
+  return C.ns;
+}
+
+// Forward march: final fields, DOF history [(n_steps+1)*ns] (optional), J (optional).
 int oracle_forward(const OracleProblem* P, const double* gamma, const double* p0, const double* u0,
                    const double* dof0, double* p_out, double* u_out, double* dof_hist, double* J) {
   Ctx C;
@@ -868,7 +1107,7 @@ int oracle_forward(const OracleProblem* P, const double* gamma, const double* p0
     for (int a = 0; a < C.d; ++a)
       for (size_t n = 0; n < C.N; ++n) u_out[(size_t)a * C.N + n] = f.u[a][n];
   if (dof_hist) std::memcpy(dof_hist, tr.s.data(), tr.s.size() * sizeof(double));
-  if (J) *J = objective(C, &tr.s[(size_t)P->n_steps * 8]);
+  if (J) *J = objective(C, &tr.s[(size_t)P->n_steps * C.ns]);
   if (C.err) return C.err;
   if (!finite_fields(C, f)) return ORC_ERR_NONFINITE;
   return ORC_OK;
@@ -876,7 +1115,7 @@ int oracle_forward(const OracleProblem* P, const double* gamma, const double* p0
 
 // Forward + exact discrete adjoint with seed dJ = 1. Outputs J, dJ/dgamma [ND] and, when the
 // pointers are non-null, the adjoint of the initial state: dJ/dp0 [N], dJ/du0 [dim][N],
-// dJ/ds0 [8], and dJ/dkappa^ref [ND].
+// dJ/ds0 [ns], and dJ/dkappa^ref [ND].
 int oracle_gradient(const OracleProblem* P, const double* gamma, const double* p0, const double* u0,
                     const double* dof0, double* J, double* dJdgamma, double* lam_p0, double* lam_u0,
                     double* lam_dof0, double* dJdkref) {
@@ -887,13 +1126,13 @@ int oracle_gradient(const OracleProblem* P, const double* gamma, const double* p
   Trajectory tr;
   run_forward(C, kref, p0, u0, dof0, &tr, true);
   if (C.err) return C.err;
-  const int NT = P->n_steps, K = P->n_itr, d = C.d;
-  if (J) *J = objective(C, &tr.s[(size_t)NT * 8]);
+  const int NT = P->n_steps, K = P->n_itr, d = C.d, ns = C.ns;
+  if (J) *J = objective(C, &tr.s[(size_t)NT * ns]);
   // terminal adjoint: the objective depends on the DOFs only
   Fields<double> lam;
   lam.alloc(C);
-  double lam_s[8];
-  for (int a = 0; a < 8; ++a) lam_s[a] = P->obj_w[a];
+  double lam_s[21];
+  for (int a = 0; a < ns; ++a) lam_s[a] = P->obj_w[a];
   std::vector<double> dk(C.ND, 0.0);
   for (int t = NT; t >= 1; --t) {
     const Fields<double>& prev = tr.states[t - 1];
@@ -902,30 +1141,30 @@ int oracle_gradient(const OracleProblem* P, const double* gamma, const double* p
     stencil_fwd(C, prev, &star);
     std::vector<IterRecord<double>> recs(K + 1);
     for (int k = 1; k <= K; ++k) {
-      double tmp[8];
-      coupling_iteration(C, kref, &it[(size_t)(k - 1) * 8], &it[0], star, &recs[k], tmp);
+      double tmp[21];
+      coupling_iteration(C, kref, &it[(size_t)(k - 1) * ns], &it[0], star, &recs[k], tmp);
     }
     Fields<double> lam_star;
     lam_star.alloc(C);
     lam_star.p = lam.p;  // p(t) = p*(t)
-    double lam_prev[8] = {0, 0, 0, 0, 0, 0, 0, 0};
-    double lam_sk[8];
-    for (int a = 0; a < 8; ++a) lam_sk[a] = lam_s[a];
+    double lam_prev[21] = {0};
+    double lam_sk[21];
+    for (int a = 0; a < ns; ++a) lam_sk[a] = lam_s[a];
     for (int k = K; k >= 1; --k) {
-      double lam_skm1[8];
-      coupling_iteration_vjp(C, kref, recs[k], &it[(size_t)(k - 1) * 8], lam_sk, (k == K) ? &lam : nullptr,
-                             &lam_star, lam_prev, lam_skm1, &dk);
+      double lam_skm1[21];
+      coupling_iteration_vjp(C, kref, recs[k], &it[(size_t)(k - 1) * ns], &it[0], lam_sk,
+                             (k == K) ? &lam : nullptr, &lam_star, lam_prev, lam_skm1, &dk);
       if (k > 1) {
-        for (int a = 0; a < 8; ++a) lam_sk[a] = lam_skm1[a];
+        for (int a = 0; a < ns; ++a) lam_sk[a] = lam_skm1[a];
       } else {
-        for (int a = 0; a < 8; ++a) lam_prev[a] += lam_skm1[a];
+        for (int a = 0; a < ns; ++a) lam_prev[a] += lam_skm1[a];
       }
     }
     Fields<double> lam_prev_fields;
     stencil_vjp(C, prev, lam_star, &lam_prev_fields);
     lam.p.swap(lam_prev_fields.p);
     for (int a = 0; a < 3; ++a) lam.u[a].swap(lam_prev_fields.u[a]);
-    for (int a = 0; a < 8; ++a) lam_s[a] = lam_prev[a];
+    for (int a = 0; a < ns; ++a) lam_s[a] = lam_prev[a];
   }
   if (C.err) return C.err;
   for (size_t m = 0; m < C.ND; ++m) {
@@ -940,7 +1179,7 @@ int oracle_gradient(const OracleProblem* P, const double* gamma, const double* p
     for (int a = 0; a < d; ++a)
       for (size_t n = 0; n < C.N; ++n) lam_u0[(size_t)a * C.N + n] = lam.u[a][n];
   if (lam_dof0)
-    for (int a = 0; a < 8; ++a) lam_dof0[a] = lam_s[a];
+    for (int a = 0; a < ns; ++a) lam_dof0[a] = lam_s[a];
   return ORC_OK;
 }
 
@@ -960,15 +1199,15 @@ int oracle_forward_cs(const OracleProblem* P, const double* gamma, const double*
   for (size_t n = 0; n < (size_t)d * N; ++n) uc[n] = cplx(u0[n], du0 ? h * du0[n] : 0.0);
   Fields<cplx> cur;
   load_fields(C, pc.data(), uc.data(), &cur);
-  cplx s[8];
-  for (int a = 0; a < 8; ++a) s[a] = cplx(dof0[a], ddof0 ? h * ddof0[a] : 0.0);
+  cplx s[21];
+  for (int a = 0; a < C.ns; ++a) s[a] = cplx(dof0[a], ddof0 ? h * ddof0[a] : 0.0);
   for (int t = 1; t <= P->n_steps; ++t) {
     Fields<cplx> nxt;
-    cplx sn[8];
+    cplx sn[21];
     forward_step<cplx>(C, kref, cur, s, &nxt, sn, nullptr);
     cur.p.swap(nxt.p);
     for (int a = 0; a < 3; ++a) cur.u[a].swap(nxt.u[a]);
-    for (int a = 0; a < 8; ++a) s[a] = sn[a];
+    for (int a = 0; a < C.ns; ++a) s[a] = sn[a];
   }
   cplx Jc = objective(C, s);
   if (J) *J = Jc.real();
@@ -1024,7 +1263,7 @@ int oracle_stencil_vjp(const OracleProblem* P, const double* p, const double* u,
   return ORC_OK;
 }
 
-// One full forward step from (p, u, s); outputs the next state, the DOF iterates [(n_itr+1)*8].
+// One full forward step from (p, u, s); outputs the next state, the DOF iterates [(n_itr+1)*ns].
 int oracle_step(const OracleProblem* P, const double* gamma, const double* p, const double* u, const double* s,
                 double* p_out, double* u_out, double* s_out, double* iters) {
   Ctx C;
@@ -1059,6 +1298,7 @@ int oracle_spread(const OracleProblem* P, const double* gamma, const double* s, 
       for (int a = 0; a < C.d; ++a) us[(size_t)a * C.N + n] = 0;
   }
   for (size_t m = 0; m < C.ND; ++m) {
+    if (!C.dom[m]) continue;
     window(C, &geo.xref[3 * m], &wn, &wv, &dwv);
     for (size_t q = 0; q < wn.size(); ++q) {
       if (wv[q] == 0.0) continue;
@@ -1080,8 +1320,9 @@ int oracle_interp(const OracleProblem* P, const double* s, const double* u, doub
   std::vector<WindowNode> wn;
   std::vector<double> wv, dwv;
   for (size_t m = 0; m < C.ND; ++m) {
-    window(C, &geo.xref[3 * m], &wn, &wv, &dwv);
     for (int a = 0; a < 3; ++a) uref[3 * m + a] = 0;
+    if (!C.dom[m]) continue;
+    window(C, &geo.xref[3 * m], &wn, &wv, &dwv);
     for (size_t q = 0; q < wn.size(); ++q)
       for (int a = 0; a < C.d; ++a) uref[3 * m + a] += wv[q] * u[(size_t)a * C.N + wn[q].n];
   }

@@ -31,7 +31,9 @@ class OracleProblem(ctypes.Structure):
         ("dp", ctypes.c_double),
         ("kappa_max", ctypes.c_double),
         ("q", ctypes.c_double),
-        ("obj_w", ctypes.c_double * 8),
+        ("obj_w", ctypes.c_double * 21),
+        ("inertia_tensor", ctypes.c_double * 9),
+        ("design_radius", ctypes.c_double),
     ]
 
 
@@ -60,6 +62,7 @@ def lib():
         L.oracle_weight.argtypes = [ctypes.c_int, ctypes.c_double, dp]
         L.oracle_weight.restype = ctypes.c_double
         L.oracle_lattice.argtypes = [ctypes.c_int, ip, dp]
+        L.oracle_dof_count.argtypes = [pp]
         if L.oracle_sizeof_problem() != ctypes.sizeof(OracleProblem):
             raise RuntimeError("oracle problem record layout mismatch")
         _lib = L
@@ -100,18 +103,29 @@ def problem_record(P, n_steps: Optional[int] = None) -> OracleProblem:
     r.n_itr = P.n_itr
     r.mass, r.inertia, r.nu, r.u_in, r.dp = P.mass, P.inertia, P.nu, P.u_in, P.dp
     r.kappa_max, r.q = P.kappa_max, P.q
-    for a in range(8):
+    for a in range(len(P.obj_weights)):
         r.obj_w[a] = P.obj_weights[a]
+    for a in range(9):
+        r.inertia_tensor[a] = P.inertia_tensor[a]
+    r.design_radius = P.design_radius
     return r
 
 
+def dof_count(P) -> int:
+    """Length of the DOF vector: 8 for a single rotation axis, 21 for free rotation."""
+    n = lib().oracle_dof_count(ctypes.byref(problem_record(P)))
+    if n <= 0:
+        raise OracleError("invalid problem")
+    return n
+
+
 def forward(P, gamma, p0, u0, dof0, n_steps: Optional[int] = None, check: bool = True):
-    """Forward march. Returns (p, u [dim, N], dof history [(n_steps+1), 8], J)."""
+    """Forward march. Returns (p, u [dim, N], dof history [(n_steps+1), ns], J)."""
     rec = problem_record(P, n_steps)
     N = P.n_cells
     p = np.zeros(N)
     u = np.zeros((P.dim, N))
-    hist = np.zeros((rec.n_steps + 1, 8))
+    hist = np.zeros((rec.n_steps + 1, dof_count(P)))
     J = ctypes.c_double(0.0)
     rc = lib().oracle_forward(ctypes.byref(rec), _ptr(_f64(gamma)), _ptr(_f64(p0)), _ptr(_f64(u0)), _ptr(_f64(dof0)),
                               _ptr(p), _ptr(u), _ptr(hist), ctypes.byref(J))
@@ -125,7 +139,7 @@ def gradient(P, gamma, p0, u0, dof0, n_steps: Optional[int] = None):
     rec = problem_record(P, n_steps)
     N, ND = P.n_cells, P.n_design
     out = {"dJdgamma": np.zeros(ND), "dJdkref": np.zeros(ND), "lam_p0": np.zeros(N),
-           "lam_u0": np.zeros((P.dim, N)), "lam_dof0": np.zeros(8)}
+           "lam_u0": np.zeros((P.dim, N)), "lam_dof0": np.zeros(dof_count(P))}
     J = ctypes.c_double(0.0)
     rc = lib().oracle_gradient(ctypes.byref(rec), _ptr(_f64(gamma)), _ptr(_f64(p0)), _ptr(_f64(u0)), _ptr(_f64(dof0)),
                                ctypes.byref(J), _ptr(out["dJdgamma"]), _ptr(out["lam_p0"]), _ptr(out["lam_u0"]),
@@ -176,12 +190,13 @@ def stencil_vjp(P, p, u, lps, lus):
 
 
 def step(P, gamma, p, u, s):
-    """One forward step. Returns (p, u, s_next, iterates [(n_itr+1), 8])."""
+    """One forward step. Returns (p, u, s_next, iterates [(n_itr+1), ns])."""
     rec = problem_record(P)
+    ns = dof_count(P)
     po = np.zeros(P.n_cells)
     uo = np.zeros((P.dim, P.n_cells))
-    so = np.zeros(8)
-    it = np.zeros((P.n_itr + 1, 8))
+    so = np.zeros(ns)
+    it = np.zeros((P.n_itr + 1, ns))
     _check(lib().oracle_step(ctypes.byref(rec), _ptr(_f64(gamma)), _ptr(_f64(p)), _ptr(_f64(u)), _ptr(_f64(s)),
                              _ptr(po), _ptr(uo), _ptr(so), _ptr(it)))
     return po, uo, so, it

@@ -19,6 +19,7 @@ from .synth import (  # noqa: F401
     DOF_TX,
     DOF_TY,
     DOF_TZ,
+    ROT_FREE,
     W_BILINEAR,
     W_COS4,
     Problem,
@@ -26,6 +27,7 @@ from .synth import (  # noqa: F401
     config_names,
     gamma_2d,
     gamma_3d,
+    inertia_tensor,
     initial_state,
     mass_properties,
     splitmix64_uniform,

@@ -35,6 +35,8 @@ DOF_TX = 1
 DOF_TY = 2
 DOF_TZ = 4
 DOF_ROT = 8
+# rot_axis value of a freely rotating 3D body (six DOFs)
+ROT_FREE = -1
 # Checkpoint policies and storage formats.
 CKPT_STORE_ALL = 0
 CKPT_UNIFORM = 1
@@ -108,6 +110,18 @@ def design_offsets(nd: tuple, dim: int) -> np.ndarray:
     return r.astype(np.float64)
 
 
+def inertia_tensor(gamma: np.ndarray, nd: tuple) -> tuple:
+    """Body-frame inertia tensor about the pivot, 2 sum(gamma (|r|^2 1 - r r^T)), row-major (9)."""
+    r = design_offsets(nd, 3)
+    w = 2.0 * gamma
+    r2 = (r ** 2).sum(axis=1)
+    I = np.zeros((3, 3))
+    for i in range(3):
+        for j in range(3):
+            I[i, j] = float((w * ((r2 if i == j else 0.0) - r[:, i] * r[:, j])).sum())
+    return tuple(I.reshape(-1))
+
+
 def mass_properties(gamma: np.ndarray, nd: tuple, dim: int, rot_axis: int) -> tuple:
     """M = 2 sum(gamma), I = 2 sum(gamma |r_perp|^2) about ``rot_axis`` (held constant)."""
     r = design_offsets(nd, dim)
@@ -140,13 +154,16 @@ class Problem:
     weight_kind: int
     n_steps: int
     n_itr: int
-    obj_weights: tuple        # 8 weights over (xG_x, xG_y, xG_z, uG_x, uG_y, uG_z, theta, omega)
+    obj_weights: tuple        # one weight per DOF: 8 over (xG[3], uG[3], theta, omega), or 21 with free
+                              # rotation over (xG[3], uG[3], h[3], omega[3], R[9] row-major)
     field_precision: int = 64  # 32 or 64
     ckpt_policy: int = CKPT_STORE_ALL
     ckpt_every: int = 0
     ckpt_format: int = CKPT_FP32
     name: str = ""
     seed: int = 0
+    inertia_tensor: tuple = (0.0,) * 9  # free rotation: body-frame inertia about the pivot
+    design_radius: float = 0.0          # > 0: ball-shaped design domain |r_m| <= design_radius
 
     @property
     def n_cells(self) -> int:
@@ -155,6 +172,10 @@ class Problem:
     @property
     def n_design(self) -> int:
         return self.ndx * self.ndy * self.ndz
+
+    @property
+    def n_dof(self) -> int:
+        return 21 if self.rot_axis == ROT_FREE else 8
 
     def replace(self, **kw) -> "Problem":
         return dataclasses.replace(self, **kw)
@@ -169,8 +190,10 @@ def initial_state(P: Problem, p0: float = 0.0, u0: Optional[tuple] = None) -> tu
     u = np.zeros((P.dim, N), dtype=np.float64)
     for a in range(P.dim):
         u[a, :] = u0[a]
-    dof = np.zeros(8, dtype=np.float64)
+    dof = np.zeros(P.n_dof, dtype=np.float64)
     dof[0:3] = P.body_centre
+    if P.n_dof == 21:
+        dof[12:21] = np.eye(3).reshape(-1)  # R = identity
     return p, u, dof
 
 
@@ -178,8 +201,8 @@ def _nu_from_re(u_in: float, length: float, re: float) -> float:
     return u_in * length / re
 
 
-def _obj(index: int) -> tuple:
-    w = [0.0] * 8
+def _obj(index: int, n: int = 8) -> tuple:
+    w = [0.0] * n
     w[index] = 1.0
     return tuple(w)
 
@@ -241,14 +264,18 @@ def _cfg4(**kw) -> tuple:
 def _cfg5(**kw) -> tuple:
     nd, seed = 96, 20260118 + 5
     g = gamma_3d(nd, seed, sphere_mask=True)
-    M, I = mass_properties(g, (nd, nd, nd), 3, 0)
+    M, _ = mass_properties(g, (nd, nd, nd), 3, 0)
+    It = inertia_tensor(g, (nd, nd, nd))
+    # six DOFs (free rotation); the design domain is the ball of the sphere mask, radius nd/2 - 2;
+    # J = h_x(N_t), the angular momentum about the flow axis
     P = Problem(dim=3, nx=256, ny=128, nz=128, ndx=nd, ndy=nd, ndz=nd, body_centre=(96.0, 64.0, 64.0),
-                rot_axis=0, dof_mask=DOF_TX | DOF_TY | DOF_TZ | DOF_ROT, mass=M, inertia=I,
+                rot_axis=ROT_FREE, dof_mask=DOF_TX | DOF_TY | DOF_TZ | DOF_ROT, mass=M, inertia=It[0],
                 nu=_nu_from_re(0.05, nd, 300), u_in=0.05, dp=0.0,
                 bc=(BC_INFLOW_OUTFLOW, BC_PERIODIC, BC_PERIODIC), kappa_max=1.0, q=0.1,
-                weight_kind=W_COS4, n_steps=10000, n_itr=5, obj_weights=_obj(6), field_precision=32,
+                weight_kind=W_COS4, n_steps=10000, n_itr=5, obj_weights=_obj(6, 21), field_precision=32,
                 ckpt_policy=CKPT_UNIFORM, ckpt_every=200, ckpt_format=CKPT_BF16,
-                name="turbine3d_256x128x128_d96", seed=seed)
+                name="turbine3d_256x128x128_d96_6dof", seed=seed, inertia_tensor=It,
+                design_radius=nd / 2.0 - 2.0)
     return P, g
 
 
