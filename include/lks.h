@@ -18,7 +18,15 @@
  *     design-grid centre.
  *   - Fields are planes of nx*ny*nz values, x fastest. Design arrays have ndx*ndy*ndz values,
  *     x fastest.
- *   - DOF vector s (8 doubles): (xG_x, xG_y, xG_z, uG_x, uG_y, uG_z, theta, omega).
+ *   - DOF vector s: 8 doubles (xG_x, xG_y, xG_z, uG_x, uG_y, uG_z, theta, omega) for a body
+ *     rotating about one axis; 21 doubles (xG[3], uG[3], h[3], omega[3], R[9] row-major) for a
+ *     freely rotating 3D body (rot_axis = LKS_ROT_FREE), h the angular momentum and omega the
+ *     angular velocity, both in the world frame. lks_dof_count gives the length.
+ *   - Free rotation (six DOFs; the paper rotates about one axis and names Euler angles or
+ *     quaternions as the extension, Sec. 2.1): explicit Euler, velocity first, with the inertia
+ *     frozen over the step: h^(k) = h(t-1) + T^(k), omega^(k) = R(t-1) I_b^-1 R(t-1)^T h^(k),
+ *     R^(k) = exp([omega^(k)]x) R(t-1) (Rodrigues' formula); iteration k's transform uses
+ *     R^(k-1) and omega^(k-1).
  *   - Every call returns an lks_status code; nothing traps or exits. A handle is not
  *     thread-safe. All GPU work goes on the stream passed in (a cudaStream_t, or NULL for the
  *     legacy default stream).
@@ -58,6 +66,8 @@ enum { LKS_D2Q9 = 9, LKS_D3Q15 = 15 };                   /* velocity sets (Sec. 
 enum { LKS_BC_PERIODIC = 0, LKS_BC_INFLOW_OUTFLOW = 1, LKS_BC_WALL = 2, LKS_BC_PRESSURE = 3 };
 enum { LKS_W_COS4 = 0, LKS_W_BILINEAR = 1 };              /* grid-separation weight (Sec. 2.3) */
 enum { LKS_DOF_TX = 1, LKS_DOF_TY = 2, LKS_DOF_TZ = 4, LKS_DOF_ROT = 8 };
+enum { LKS_ROT_FREE = -1 };                               /* rot_axis of a freely rotating 3D body */
+enum { LKS_NDOF_AXIS = 8, LKS_NDOF_FREE = 21, LKS_MAX_DOF = 21 };  /* DOF vector lengths */
 enum { LKS_FP32 = 32, LKS_FP64 = 64 };                    /* field storage / arithmetic type */
 enum { LKS_CKPT_STORE_ALL = 0, LKS_CKPT_UNIFORM = 1, LKS_CKPT_BINOMIAL = 2 };
 enum { LKS_CKPT_NATIVE = 0, LKS_CKPT_BF16 = 1, LKS_CKPT_FP16 = 2 };
@@ -69,10 +79,15 @@ typedef struct lks_problem {
   int nx, ny, nz;         /* analysis grid in cells (nz = 1 for dim 2) */
   int ndx, ndy, ndz;      /* design grid in points (ndz = 1 for dim 2) */
   double body_centre[3];  /* x^G(0) in analysis coordinates */
-  int rot_axis;           /* single rotation axis 0/1/2 (2 in 2D) */
-  unsigned dof_mask;      /* LKS_DOF_* bits of the free degrees of freedom */
+  int rot_axis;           /* single rotation axis 0/1/2 (2 in 2D), or LKS_ROT_FREE (3D only) */
+  unsigned dof_mask;      /* LKS_DOF_* bits of the free degrees of freedom (LKS_DOF_ROT: all rotation) */
   double mass;            /* M, constant (Sec. 2.1) */
-  double inertia;         /* I about rot_axis, constant (Sec. 2.1) */
+  double inertia;         /* I about rot_axis, constant (Sec. 2.1); positive, unused with LKS_ROT_FREE */
+  double inertia_tensor[9]; /* LKS_ROT_FREE: body-frame inertia tensor I_b about the pivot, row-major,
+                           * symmetric positive definite, constant */
+  double design_radius;   /* > 0: the design domain is the ball |r_m| <= design_radius (r_m = xi_m - xi^G);
+                           * design points outside it take no part in any sum and get dJ/dgamma = 0.
+                           * 0: the whole design grid */
   double nu;              /* kinematic viscosity; A = 9/2 (1/6 - nu) */
   double u_in;            /* inflow speed for LKS_BC_INFLOW_OUTFLOW */
   double dp;              /* inlet pressure for LKS_BC_PRESSURE (outlet p = 0) */
@@ -80,7 +95,8 @@ typedef struct lks_problem {
   double kappa_max, q;    /* Brinkman interpolation (Eq. brinkman_coefficient) */
   int weight_kind;        /* LKS_W_COS4 (Eq. weight_function) or LKS_W_BILINEAR */
   int n_steps, n_itr;     /* N_t, N_itr (Sec. 3.1) */
-  double obj_weights[8];  /* J = sum_d obj_weights[d] * s_d(N_t) (Eqs. objective1, objective2) */
+  double obj_weights[LKS_MAX_DOF]; /* J = sum_d obj_weights[d] * s_d(N_t) over the DOF vector
+                           * (Eqs. objective1, objective2); entries beyond lks_dof_count are ignored */
   int field_precision;    /* LKS_FP32 or LKS_FP64 */
   int ckpt_policy;        /* LKS_CKPT_STORE_ALL, LKS_CKPT_UNIFORM or LKS_CKPT_BINOMIAL */
   int ckpt_every;         /* UNIFORM: checkpoint interval k; BINOMIAL: number of state snapshots
@@ -97,9 +113,16 @@ typedef struct lks_handle lks_handle;
  * Errors: LKS_ERR_ARG, LKS_ERR_UNSTABLE, LKS_ERR_UNSUPPORTED, LKS_ERR_BUDGET, LKS_ERR_OOM. */
 LKS_API int lks_create(const lks_problem* problem, lks_handle** out);
 
+/* Length of the DOF vector of a problem: LKS_NDOF_AXIS, or LKS_NDOF_FREE with rot_axis =
+ * LKS_ROT_FREE; 0 if problem is NULL. */
+LKS_API int lks_dof_count(const lks_problem* problem);
+
+/* sizeof(lks_problem) as compiled into the library, for bindings that mirror the struct. */
+LKS_API size_t lks_problem_size(void);
+
 /* Initial state for the next forward (Algorithm 1, "Initialize"). p [N], u [dim][N] and
- * s [8] are host arrays (copied). Any pointer may be NULL to keep the default: p = 0,
- * u = (u_in, 0, 0), body at rest at body_centre.
+ * s [lks_dof_count] are host arrays (copied). Any pointer may be NULL to keep the default: p = 0,
+ * u = (u_in, 0, 0), body at rest at body_centre (R = identity with free rotation).
  * Errors: LKS_ERR_ARG; LKS_ERR_UNSUPPORTED if s starts the body rotated but the workspace was
  * sized for an axis-aligned box (see lks_create); LKS_ERR_CUDA. */
 LKS_API int lks_set_initial_state(lks_handle* h, const double* p_host, const double* u_host, const double* s_host);
@@ -124,7 +147,8 @@ LKS_API int lks_sensitivity(lks_handle* h, double* dJdgamma_dev, void* stream);
  * Synchronises the stream before returning. */
 LKS_API int lks_gradient_host(lks_handle* h, const double* gamma_host, double* J_host, double* dJdgamma_host, void* stream);
 
-/* DOF history of the last forward into host_buf [(n_steps+1)*8]; n = capacity in doubles. */
+/* DOF history of the last forward into host_buf [(n_steps+1)*lks_dof_count]; n = capacity in
+ * doubles. */
 LKS_API int lks_get_dof_history(lks_handle* h, double* host_buf, size_t n);
 
 /* Final state of the last forward: p [N], u [dim][N] as doubles (host). Only for
@@ -132,7 +156,7 @@ LKS_API int lks_get_dof_history(lks_handle* h, double* host_buf, size_t n);
 LKS_API int lks_get_state(lks_handle* h, double* p_host, double* u_host);
 
 /* Adjoint of the initial state after the last lks_adjoint: dJ/dp0 [N], dJ/du0 [dim][N],
- * dJ/ds0 [8] (host, any may be NULL). Synchronous. */
+ * dJ/ds0 [lks_dof_count] (host, any may be NULL). Synchronous. */
 LKS_API int lks_get_initial_adjoint(lks_handle* h, double* lam_p_host, double* lam_u_host, double* lam_s_host);
 
 /* Number of kernels this handle has launched (graph nodes counted per replay). */

@@ -12,6 +12,8 @@
 //               re-advances from the nearest snapshot and reverses one step at a time.
 // Adjoint (Algorithm 1, adjoint loop): per step, for k = N_itr..1 a cell-side and a design-side
 // reverse kernel, then the transposed stencil.
+#include <algorithm>
+#include <climits>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -73,7 +75,7 @@ struct lks_handle {
   double* init_u = nullptr;
   double* init_s = nullptr;
   double* objw = nullptr;
-  double host_s0[8];
+  double host_s0[kNdofFree];
   size_t bytes = 0;
   std::vector<void*> allocs;
   cudaStream_t cap = nullptr;
@@ -123,15 +125,22 @@ int dalloc(lks_handle* h, void** p, size_t bytes) {
     }                       \
   } while (0)
 
-// Box extent from the design grid: circumscribed in the rotation plane if the body may rotate.
+// Box extent from the design grid: circumscribed in the rotation plane if the body may rotate
+// (in every axis with free rotation), and within the design domain's radius when one is set.
 void setup_box(lks_handle* h, bool rotated) {
   Geo& g = h->g;
   double half[3] = {0, 0, 0};
   for (int a = 0; a < g.dim; ++a) half[a] = (g.nd[a] - 1) / 2.0;
-  if (rotated) {
+  if (rotated && g.ax == AX_FREE) {
+    const double r = std::sqrt(half[0] * half[0] + half[1] * half[1] + half[2] * half[2]);
+    half[0] = half[1] = half[2] = r;
+  } else if (rotated) {
     const double r = std::sqrt(half[g.axb] * half[g.axb] + half[g.axc] * half[g.axc]);
     half[g.axb] = half[g.axc] = r;
   }
+  const double rad = h->P.design_radius;
+  if (rad > 0.0)
+    for (int a = 0; a < g.dim; ++a) half[a] = std::min(half[a], rad);
   g.margin = 1;
   g.box_cells = 1;
   for (int a = 0; a < 3; ++a) {
@@ -146,6 +155,38 @@ void setup_box(lks_handle* h, bool rotated) {
   }
 }
 
+// Symmetric (to rounding) positive definite 3x3 matrix, by its leading minors.
+bool spd3(const double* A) {
+  double mx = 0.0;
+  for (int i = 0; i < 9; ++i) {
+    if (!std::isfinite(A[i])) return false;
+    mx = std::max(mx, std::fabs(A[i]));
+  }
+  for (int i = 0; i < 3; ++i)
+    for (int j = 0; j < i; ++j)
+      if (std::fabs(A[3 * i + j] - A[3 * j + i]) > 1e-12 * mx) return false;
+  const double m2 = A[0] * A[4] - A[1] * A[3];
+  const double det = A[0] * (A[4] * A[8] - A[5] * A[7]) - A[1] * (A[3] * A[8] - A[5] * A[6]) +
+                     A[2] * (A[3] * A[7] - A[4] * A[6]);
+  return A[0] > 0.0 && m2 > 0.0 && det > 0.0;
+}
+
+// Inverse of a symmetric 3x3 matrix: row i is c_(i+1) x c_(i+2) / det for the columns c.
+void inverse_sym3(const double* A, double* inv) {
+  const double c[3][3] = {{A[0], A[3], A[6]}, {A[1], A[4], A[7]}, {A[2], A[5], A[8]}};
+  double rows[3][3];
+  for (int i = 0; i < 3; ++i) {
+    const double* u = c[(i + 1) % 3];
+    const double* v = c[(i + 2) % 3];
+    rows[i][0] = u[1] * v[2] - u[2] * v[1];
+    rows[i][1] = u[2] * v[0] - u[0] * v[2];
+    rows[i][2] = u[0] * v[1] - u[1] * v[0];
+  }
+  const double det = c[0][0] * rows[0][0] + c[0][1] * rows[0][1] + c[0][2] * rows[0][2];
+  for (int i = 0; i < 3; ++i)
+    for (int j = 0; j < 3; ++j) inv[3 * i + j] = rows[i][j] / det;
+}
+
 int validate(const lks_problem* P) {
   if (!P) return LKS_ERR_ARG;
   if (P->dim != 2 && P->dim != 3) return LKS_ERR_ARG;
@@ -153,7 +194,12 @@ int validate(const lks_problem* P) {
   if (P->dim == 3 && P->velocity_set != LKS_D3Q15) return LKS_ERR_ARG;
   if (P->nx < 4 || P->ny < 4 || (P->dim == 3 && P->nz < 4)) return LKS_ERR_ARG;
   if (P->ndx < 1 || P->ndy < 1 || P->ndz < 1) return LKS_ERR_ARG;
-  if (P->rot_axis < 0 || P->rot_axis > 2) return LKS_ERR_ARG;
+  if (P->rot_axis == LKS_ROT_FREE) {
+    if (P->dim != 3 || !spd3(P->inertia_tensor)) return LKS_ERR_ARG;
+  } else if (P->rot_axis < 0 || P->rot_axis > 2) {
+    return LKS_ERR_ARG;
+  }
+  if (!(P->design_radius >= 0.0) || !std::isfinite(P->design_radius)) return LKS_ERR_ARG;
   if (P->bc[0] != LKS_BC_PERIODIC && P->bc[0] != LKS_BC_INFLOW_OUTFLOW && P->bc[0] != LKS_BC_PRESSURE) return LKS_ERR_ARG;
   for (int a = 1; a < 3; ++a)
     if (P->bc[a] != LKS_BC_PERIODIC && P->bc[a] != LKS_BC_WALL) return LKS_ERR_ARG;
@@ -473,7 +519,7 @@ int adjoint_impl(lks_handle* h, double seed, cudaStream_t st) {
   const int NT = h->P.n_steps;
   Launcher L0{h, st, false};
   CK(cudaMemsetAsync(h->L, 0, 2 * h->slot_elems * h->esz, st));
-  L0("init", [&](cudaStream_t s) { launch_adj_init(g, h->ctrl, h->objw, seed, h->dkref, g.ND, s); });
+  L0("init", [&](cudaStream_t s) { launch_adj_init(g, h->ctrl, h->it, h->P.n_steps, h->objw, seed, h->dkref, g.ND, s); });
   if (h->P.ckpt_policy == LKS_CKPT_BINOMIAL) {
     TRY(binomial_reverse<T>(h, st, 0, NT, h->P.ckpt_every, true, -1, 0));
   } else if (h->P.ckpt_policy == LKS_CKPT_STORE_ALL) {
@@ -555,15 +601,17 @@ int allocate(lks_handle* h) {
   const long long bx = ((g.B[0] + kBoxCtaCellsX - 1) / kBoxCtaCellsX) * (long long)((g.B[1] + kBoxCtaCellsY - 1) / kBoxCtaCellsY) * g.B[2];
   const long long bd = ((long long)g.ND + kDesignPointsPerCta - 1) / kDesignPointsPerCta;
   const long long nblk = std::max(bx, bd) + 1;
-  TRY(dalloc(h, (void**)&h->partials, (size_t)nblk * 8 * sizeof(double)));
-  h->pstride = 4 * nblk;
+  // per-CTA partials: up to 18 values (design-point reverse with free rotation); the coupling's
+  // double-buffered halves hold up to 6 values each
+  TRY(dalloc(h, (void**)&h->partials, (size_t)nblk * 18 * sizeof(double)));
+  h->pstride = 6 * nblk;
   TRY(dalloc(h, (void**)&h->init_p, (size_t)g.N * sizeof(double)));
   TRY(dalloc(h, (void**)&h->init_u, (size_t)D * g.N * sizeof(double)));
-  TRY(dalloc(h, (void**)&h->init_s, 8 * sizeof(double)));
-  TRY(dalloc(h, (void**)&h->objw, 8 * sizeof(double)));
+  TRY(dalloc(h, (void**)&h->init_s, kNdofFree * sizeof(double)));
+  TRY(dalloc(h, (void**)&h->objw, kNdofFree * sizeof(double)));
   CK(cudaMemset(h->ctrl, 0, sizeof(Ctrl)));
   CK(cudaMemset(h->L, 0, 2 * slot_bytes));
-  CK(cudaMemcpy(h->objw, P.obj_weights, 8 * sizeof(double), cudaMemcpyHostToDevice));
+  CK(cudaMemcpy(h->objw, P.obj_weights, g.ns * sizeof(double), cudaMemcpyHostToDevice));
   return LKS_OK;
 }
 
@@ -573,16 +621,22 @@ int set_default_initial_state(lks_handle* h) {
   for (long long n = 0; n < g.N; ++n) u[n] = h->P.u_in;
   CK(cudaMemcpy(h->init_p, p.data(), p.size() * sizeof(double), cudaMemcpyHostToDevice));
   CK(cudaMemcpy(h->init_u, u.data(), u.size() * sizeof(double), cudaMemcpyHostToDevice));
-  for (int a = 0; a < 8; ++a) h->host_s0[a] = 0.0;
+  for (int a = 0; a < kNdofFree; ++a) h->host_s0[a] = 0.0;
   for (int a = 0; a < 3; ++a) h->host_s0[a] = h->P.body_centre[a];
-  CK(cudaMemcpy(h->init_s, h->host_s0, 8 * sizeof(double), cudaMemcpyHostToDevice));
+  if (g.ax == AX_FREE) h->host_s0[S_R] = h->host_s0[S_R + 4] = h->host_s0[S_R + 8] = 1.0;  // R = I
+  CK(cudaMemcpy(h->init_s, h->host_s0, g.ns * sizeof(double), cudaMemcpyHostToDevice));
   return LKS_OK;
 }
 
 // Box for the current initial state: the rotated (circumscribed) box if the body can rotate or
 // starts rotated. The buffers were sized at creation for the largest box that fits.
 int refresh_box(lks_handle* h) {
-  const bool rotated = (h->g.dof_mask & LKS_DOF_ROT) || h->host_s0[6] != 0.0;
+  bool start_rotated = h->host_s0[6] != 0.0;
+  if (h->g.ax == AX_FREE) {
+    start_rotated = false;
+    for (int i = 0; i < 9; ++i) start_rotated = start_rotated || h->host_s0[S_R + i] != ((i % 4 == 0) ? 1.0 : 0.0);
+  }
+  const bool rotated = (h->g.dof_mask & LKS_DOF_ROT) || start_rotated;
   if (rotated && !h->box_rot_ok) return LKS_ERR_UNSUPPORTED;
   const int old[3] = {h->g.B[0], h->g.B[1], h->g.B[2]};
   setup_box(h, rotated);
@@ -618,6 +672,13 @@ const char* lks_status_string(int s) {
 
 int lks_last_cuda_error(void) { return g_last_cuda_error; }
 
+size_t lks_problem_size(void) { return sizeof(lks_problem); }
+
+int lks_dof_count(const lks_problem* P) {
+  if (!P) return 0;
+  return P->rot_axis == LKS_ROT_FREE ? LKS_NDOF_FREE : LKS_NDOF_AXIS;
+}
+
 int lks_create(const lks_problem* P, lks_handle** out) {
   if (!out) return LKS_ERR_ARG;
   *out = nullptr;
@@ -644,9 +705,24 @@ int lks_create(const lks_problem* P, lks_handle** out) {
     g.xic[a] = (a < g.dim) ? (g.nd[a] - 1) / 2.0 : 0.0;
     g.xicf[a] = (float)g.xic[a];
   }
-  g.ax = P->rot_axis;
-  g.axb = (g.ax + 1) % 3;
-  g.axc = (g.ax + 2) % 3;
+  if (P->rot_axis == LKS_ROT_FREE) {
+    g.ax = AX_FREE;
+    g.axb = 0;  // (unused with free rotation)
+    g.axc = 1;
+    g.ns = kNdofFree;
+    inverse_sym3(P->inertia_tensor, g.Jinv);
+  } else {
+    g.ax = P->rot_axis;
+    g.axb = (g.ax + 1) % 3;
+    g.axc = (g.ax + 2) % 3;
+    g.ns = kNdofAxis;
+  }
+  // design domain 4 |r_m|^2 <= rad4, compared in integers (4 |r_m|^2 is an integer)
+  g.rad4 = INT_MAX;
+  if (P->design_radius > 0.0) {
+    const double q = std::floor(4.0 * P->design_radius * P->design_radius);
+    g.rad4 = q < (double)INT_MAX ? (int)q : INT_MAX;
+  }
   g.dof_mask = (int)P->dof_mask;
   g.wk = P->weight_kind;
   g.s = (P->weight_kind == LKS_W_BILINEAR) ? 1 : 2;
@@ -695,8 +771,8 @@ int lks_set_initial_state(lks_handle* h, const double* p, const double* u, const
   if (p) CK(cudaMemcpy(h->init_p, p, (size_t)g.N * sizeof(double), cudaMemcpyHostToDevice));
   if (u) CK(cudaMemcpy(h->init_u, u, (size_t)g.dim * g.N * sizeof(double), cudaMemcpyHostToDevice));
   if (s) {
-    for (int a = 0; a < 8; ++a) h->host_s0[a] = s[a];
-    CK(cudaMemcpy(h->init_s, h->host_s0, 8 * sizeof(double), cudaMemcpyHostToDevice));
+    for (int a = 0; a < g.ns; ++a) h->host_s0[a] = s[a];
+    CK(cudaMemcpy(h->init_s, h->host_s0, g.ns * sizeof(double), cudaMemcpyHostToDevice));
   }
   return refresh_box(h);
 }
@@ -722,7 +798,7 @@ int lks_forward(lks_handle* h, const double* gamma_dev, double* J_host, void* st
   CK(cudaStreamSynchronize(st));
   if (h->timing) collect_timers(h);
   double J = 0.0;
-  for (int a = 0; a < 8; ++a) J += h->P.obj_weights[a] * last.s[a];
+  for (int a = 0; a < g.ns; ++a) J += h->P.obj_weights[a] * last.s[a];
   if (J_host) *J_host = J;
   if (c.status & ST_BODY_OUTSIDE) return LKS_ERR_BODY_OUTSIDE;
   if (c.status & ST_BOX_OVERFLOW) return LKS_ERR_BODY_OUTSIDE;
@@ -774,12 +850,12 @@ int lks_gradient_host(lks_handle* h, const double* gamma_host, double* J_host, d
 int lks_get_dof_history(lks_handle* h, double* buf, size_t n) {
   if (!h || !buf) return LKS_ERR_ARG;
   if (!h->fwd_done) return LKS_ERR_ORDER;
-  const int NT = h->P.n_steps, K = h->g.K;
-  if (n < (size_t)(NT + 1) * 8) return LKS_ERR_ARG;
+  const int NT = h->P.n_steps, K = h->g.K, ns = h->g.ns;
+  if (n < (size_t)(NT + 1) * ns) return LKS_ERR_ARG;
   std::vector<Dof> rows((size_t)(NT + 1) * (K + 1));
   CK(cudaMemcpy(rows.data(), h->it, rows.size() * sizeof(Dof), cudaMemcpyDeviceToHost));
   for (int t = 0; t <= NT; ++t)
-    for (int a = 0; a < 8; ++a) buf[(size_t)t * 8 + a] = rows[(size_t)t * (K + 1)].s[a];
+    for (int a = 0; a < ns; ++a) buf[(size_t)t * ns + a] = rows[(size_t)t * (K + 1)].s[a];
   return LKS_OK;
 }
 
@@ -825,7 +901,7 @@ int lks_get_initial_adjoint(lks_handle* h, double* lp, double* lu, double* ls) {
   if (ls) {
     Ctrl c;
     CK(cudaMemcpy(&c, h->ctrl, sizeof(Ctrl), cudaMemcpyDeviceToHost));
-    for (int a = 0; a < 8; ++a) ls[a] = c.lam_s0[a];
+    for (int a = 0; a < h->g.ns; ++a) ls[a] = c.lam_s0[a];
   }
   return LKS_OK;
 }

@@ -17,6 +17,11 @@
 // for the spread / interpolation / transform reverse (the dW/dx^ref terms), accumulates
 // dJ/dkappa^ref without atomics and reduces dJ/ds^(k-1).
 //
+// Free rotation (AX = AX_FREE): R is a full rotation matrix and omega a vector; the solid velocity
+// is u^G phi_n + omega x (R sum_m W r_m), the torque a vector sum_n L_n x u_n - sum_m kappa_m
+// (R r_m) x u^S,ref_m whose design-side part is (R K1) x u^G + K2s omega - R K2 R^T omega with
+// K2s = sum kappa_m |r_m|^2, K2 = sum kappa_m r_m r_m^T.
+//
 // Each iteration's global reduction is split into a kernel over all SMs that writes one FP64
 // partial per CTA (double-float pairs in the FP32 form) and a one-warp finish kernel that sums the
 // partials in a fixed order and applies the (reverse) EOM: the kernel boundary orders the partials, so no GPU-scope fence or counter is
@@ -54,27 +59,87 @@ __device__ __forceinline__ CellSlot cell_slot(const Geo& g) {
 
 __device__ __forceinline__ int block_linear() { return blockIdx.x + gridDim.x * (blockIdx.y + gridDim.y * blockIdx.z); }
 
-// dJ/dF and dJ/dT of the iteration being reversed, in the field type.
+// Partial sums per CTA: the coupling reduces force and torque (one torque component about the
+// axis, or the torque vector with free rotation); the design-point reverse reduces dJ/ds^(k-1)
+// through the transform: (xG, uG, theta, omega), or (xG, uG, omega[3], R[9]) with free rotation.
+template <int AX>
+__host__ __device__ constexpr int nv_couple() { return AX == AX_FREE ? 6 : 4; }
+template <int AX>
+__host__ __device__ constexpr int nv_design() { return AX == AX_FREE ? 18 : 8; }
+
+// R and omega of a free-rotation iterate in the field type.
 template <typename T>
-__device__ __forceinline__ void lam_load(const Ctrl* ctrl, T (&lF)[3], T& lT);
+struct FreeView;
 template <>
-__device__ __forceinline__ void lam_load<float>(const Ctrl* ctrl, float (&lF)[3], float& lT) {
-  for (int a = 0; a < 3; ++a) lF[a] = ctrl->lam_Ff[a];
-  lT = ctrl->lam_Tf;
+struct FreeView<float> {
+  float R[9], om[3];
+  __device__ __forceinline__ explicit FreeView(const Dof& d) {
+#pragma unroll
+    for (int i = 0; i < 9; ++i) R[i] = d.Rf[i];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) om[a] = d.omf[a];
+  }
+};
+template <>
+struct FreeView<double> {
+  double R[9], om[3];
+  __device__ __forceinline__ explicit FreeView(const Dof& d) {
+#pragma unroll
+    for (int i = 0; i < 9; ++i) R[i] = d.s[S_R + i];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) om[a] = d.s[S_OM + a];
+  }
+};
+
+// dJ/dF and dJ/dT of the iteration being reversed, in the field type (dJ/dT about the axis in [0]).
+template <typename T>
+__device__ __forceinline__ void lam_load(const Ctrl* ctrl, T (&lF)[3], T (&lT)[3]);
+template <>
+__device__ __forceinline__ void lam_load<float>(const Ctrl* ctrl, float (&lF)[3], float (&lT)[3]) {
+  for (int a = 0; a < 3; ++a) {
+    lF[a] = ctrl->lam_Ff[a];
+    lT[a] = ctrl->lam_Tf[a];
+  }
 }
 template <>
-__device__ __forceinline__ void lam_load<double>(const Ctrl* ctrl, double (&lF)[3], double& lT) {
-  for (int a = 0; a < 3; ++a) lF[a] = ctrl->lam_F[a];
-  lT = ctrl->lam_T;
+__device__ __forceinline__ void lam_load<double>(const Ctrl* ctrl, double (&lF)[3], double (&lT)[3]) {
+  for (int a = 0; a < 3; ++a) {
+    lF[a] = ctrl->lam_F[a];
+    lT[a] = ctrl->lam_T[a];
+  }
 }
 
-__device__ __forceinline__ void lam_store(Ctrl* ctrl, const double* lF, double lT) {
+__device__ __forceinline__ void lam_store(Ctrl* ctrl, const double* lF, const double* lT) {
   for (int a = 0; a < 3; ++a) {
     ctrl->lam_F[a] = lF[a];
     ctrl->lam_Ff[a] = (float)lF[a];
+    ctrl->lam_T[a] = lT[a];
+    ctrl->lam_Tf[a] = (float)lT[a];
   }
-  ctrl->lam_T = lT;
-  ctrl->lam_Tf = (float)lT;
+}
+
+// Gather of the cell's design-point sums under the iterate's rotation, and from them the
+// rotational part of the solid velocity (omega R' sum W r, or omega x R sum W r) and the lever
+// sum L_n = R sum W kappa r.
+template <typename T, int D, int AX>
+__device__ __forceinline__ void gather_cell(const Geo& g, const T* __restrict__ kref, const Dof& sk,
+                                            const DofView<T>& V, const T (&d)[3], int lane, bool active, Acc<T>& A,
+                                            T (&rotv)[3], T (&L)[3]) {
+  if constexpr (AX == AX_FREE) {
+    const FreeView<T> FV(sk);
+    gather_free_lanes<T, LN>(g, kref, d, FV.R, lane, active, A);
+    T Rwr[3];
+    matvec3(FV.R, A.wr, Rwr);
+    cross3(FV.om, Rwr, rotv);
+    matvec3(FV.R, A.kr, L);
+  } else {
+    gather_lanes<T, D, AX, LN>(g, kref, d, V.cs, V.sn, lane, active, A);
+    T dwr[3];
+    drot<AX>(V.cs, V.sn, A.wr, dwr);
+#pragma unroll
+    for (int a = 0; a < 3; ++a) rotv[a] = V.om * dwr[a];
+    rot<AX>(V.cs, V.sn, A.kr, L);
+  }
 }
 
 // Forward coupling work for box cell (j0, j1, j2), called by all LN lanes of the cell (every
@@ -85,7 +150,6 @@ template <typename T, int D, int AX>
 __device__ __forceinline__ void couple_cell(const Geo& g, const T* __restrict__ kref, const Dof& sk, const int (&lo)[3],
                                             const CellSlot& cc, T* __restrict__ dst, T* __restrict__ bs, bool last,
                                             int* status, T* v) {
-  constexpr int b = Axes<AX>::B, c = Axes<AX>::C;
   const long long N = g.N;
   const int j0 = cc.j0, j1 = cc.j1, j2 = cc.j2;
   const int px = lo[0] + j0, py = lo[1] + j1, pz = lo[2] + j2;
@@ -93,21 +157,17 @@ __device__ __forceinline__ void couple_cell(const Geo& g, const T* __restrict__ 
   const bool ing = cell_index<D>(g, px, py, pz, n);
   const DofView<T> V(sk);
   const T d[3] = {V.rel(0, px), V.rel(1, py), D == 3 ? V.rel(2, pz) : T(0)};
-  const T cs = V.cs, sn = V.sn;
   Acc<T> A;
-  gather_lanes<T, D, AX, LN>(g, kref, d, cs, sn, cc.lane, cc.active, A);
+  T rotv[3], L[3], u[3] = {T(0), T(0), T(0)};
+  gather_cell<T, D, AX>(g, kref, sk, V, d, cc.lane, cc.active, A, rotv, L);
   if (!cc.active || cc.lane != 0) return;
   if (A.phi > T(0) && (!ing || forbidden<D>(g, px, py, pz))) atomicOr(status, ST_BODY_OUTSIDE);
   if (!ing) return;
-  T dwr[3], L[3], u[3] = {T(0), T(0), T(0)};
-  drot<AX>(cs, sn, A.wr, dwr);
-  rot<AX>(cs, sn, A.kr, L);
-  const T om = V.om;
   const T inv = T(1) / (T(1) + A.kap);
   const long long bl = j0 + (long long)g.B[0] * (j1 + (long long)g.B[1] * j2);
 #pragma unroll
   for (int a = 0; a < D; ++a) {
-    const T us = V.ug[a] * A.phi + om * dwr[a];
+    const T us = V.ug[a] * A.phi + rotv[a];
     const T ustar = dst[(a + 1) * N + n];
     u[a] = (ustar + A.kap * us) * inv;
     v[a] += A.kap * u[a];
@@ -116,7 +176,16 @@ __device__ __forceinline__ void couple_cell(const Geo& g, const T* __restrict__ 
       dst[(a + 1) * N + n] = u[a];
     }
   }
-  v[D] += L[b] * u[c] - L[c] * u[b];  // torque density about AX
+  if constexpr (AX == AX_FREE) {  // torque density vector L_n x u_n
+    T tq[3];
+    cross3(L, u, tq);
+    v[3] += tq[0];
+    v[4] += tq[1];
+    v[5] += tq[2];
+  } else {  // about AX
+    constexpr int b = Axes<AX>::B, c = Axes<AX>::C;
+    v[D] += L[b] * u[c] - L[c] * u[b];
+  }
 }
 
 // Closed-form design-side terms and the EOM update of iteration k from the cell sums s[0..D].
@@ -141,6 +210,46 @@ __device__ __forceinline__ void couple_finish(const Geo& g, const Moments* mom, 
     if (fabs(nx->s[a] - s0.s[a]) > (double)g.margin) *status |= ST_BOX_OVERFLOW;
 }
 
+// The same with free rotation from the cell sums s[0..5] = (F_cell, T_cell).
+__device__ __forceinline__ void couple_finish_free(const Geo& g, const Moments* mom, const Dof& s0, const Dof& sk,
+                                                   const double* s, Dof* nx, int* status) {
+  const double* R = sk.s + S_R;
+  const double* om = sk.s + S_OM;
+  const double ug[3] = {sk.s[3], sk.s[4], sk.s[5]};
+  double K1r[3], oxk[3], kxu[3], K2o[3], v1[3];
+  matvec3(R, mom->K1, K1r);
+  cross3(om, K1r, oxk);
+  cross3(K1r, ug, kxu);
+  // R K2 R^T omega
+  const double K2[9] = {mom->K2[0], mom->K2[3], mom->K2[4], mom->K2[3], mom->K2[1],
+                        mom->K2[5], mom->K2[4], mom->K2[5], mom->K2[2]};
+  matTvec3(R, om, v1);
+  double v2[3];
+  matvec3(K2, v1, v2);
+  matvec3(R, v2, K2o);
+  double F[3], Tv[3];
+  bool finite = true;
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    F[a] = s[a] - (mom->K0 * ug[a] + oxk[a]);
+    Tv[a] = s[3 + a] - (kxu[a] + mom->K2s * om[a] - K2o[a]);
+    finite = finite && isfinite(F[a]) && isfinite(Tv[a]);
+  }
+  if (!finite) *status |= ST_NONFINITE;
+  eom_update_free(g, s0, F, Tv, nx);
+  for (int a = 0; a < 3; ++a)
+    if (fabs(nx->s[a] - s0.s[a]) > (double)g.margin) *status |= ST_BOX_OVERFLOW;
+}
+
+template <int D, int AX>
+__device__ __forceinline__ void couple_finish_any(const Geo& g, const Moments* mom, const Dof& s0, const Dof& sk,
+                                                  const double* s, Dof* nx, int* status) {
+  if constexpr (AX == AX_FREE)
+    couple_finish_free(g, mom, s0, sk, s, nx, status);
+  else
+    couple_finish<D, AX>(g, mom, s0, sk, s, nx, status);
+}
+
 // Reverse of coupling iteration k for box cell (j0, j1, j2). Scratch planes per box cell:
 //   [0, D): u^(k);  D: dJ/dkappa_n;  [D+1, 2D+1): dJ/du^S_n.  acc accumulates dJ/du*.
 // Called by all LN lanes of the cell (see couple_cell); lane 0 does the per-cell work.
@@ -148,8 +257,7 @@ template <typename T, int D, int AX>
 __device__ __forceinline__ void adj_cell_work(const Geo& g, const T* __restrict__ kref, const Dof& sk,
                                               const int (&lo)[3], const CellSlot& cc, const T* __restrict__ bs,
                                               T* Lcur, T* __restrict__ acc, T* __restrict__ scratch, int k, int K,
-                                              const T (&lF)[3], T lT) {
-  constexpr int b = Axes<AX>::B, c = Axes<AX>::C;
+                                              const T (&lF)[3], const T (&lT)[3]) {
   const long long N = g.N, BC = g.box_cells;
   const int j0 = cc.j0, j1 = cc.j1, j2 = cc.j2;
   const long long bl = j0 + (long long)g.B[0] * (j1 + (long long)g.B[1] * j2);
@@ -158,27 +266,28 @@ __device__ __forceinline__ void adj_cell_work(const Geo& g, const T* __restrict_
   const bool ing = cell_index<D>(g, px, py, pz, n);
   const DofView<T> V(sk);
   const T d[3] = {V.rel(0, px), V.rel(1, py), D == 3 ? V.rel(2, pz) : T(0)};
-  const T cs = V.cs, sn = V.sn;
   Acc<T> A;
-  gather_lanes<T, D, AX, LN>(g, kref, d, cs, sn, cc.lane, cc.active && ing, A);
+  T rotv[3], L[3];
+  gather_cell<T, D, AX>(g, kref, sk, V, d, cc.lane, cc.active && ing, A, rotv, L);
   if (!cc.active || cc.lane != 0) return;
   if (!ing) {
     for (int q = 0; q < 2 * D + 1; ++q) scratch[q * BC + bl] = T(0);
     return;
   }
-  T dwr[3], L[3];
-  drot<AX>(cs, sn, A.wr, dwr);
-  rot<AX>(cs, sn, A.kr, L);
-  const T om = V.om;
   const T inv = T(1) / (T(1) + A.kap);
-  // sum_m W dJ/du^ref_m = kappa_n lam_F + lam_T (e x L_n), in the rotation plane
+  // sum_m W dJ/du^ref_m = kappa_n lam_F + lam_T x L_n (lam_T along the axis for one axis)
   T extra[3] = {T(0), T(0), T(0)};
-  extra[b] = -lT * L[c];
-  extra[c] = lT * L[b];
+  if constexpr (AX == AX_FREE) {
+    cross3(lT, L, extra);
+  } else {
+    constexpr int b = Axes<AX>::B, c = Axes<AX>::C;
+    extra[b] = -lT[0] * L[c];
+    extra[c] = lT[0] * L[b];
+  }
   T lkap = T(0);
 #pragma unroll
   for (int a = 0; a < D; ++a) {
-    const T us = V.ug[a] * A.phi + om * dwr[a];
+    const T us = V.ug[a] * A.phi + rotv[a];
     const T uk = (bs[a * BC + bl] + A.kap * us) * inv;
     T lu = A.kap * lF[a] + extra[a];
     if (k == K) lu += Lcur[(a + 1) * N + n];
@@ -195,30 +304,45 @@ __device__ __forceinline__ void adj_cell_work(const Geo& g, const T* __restrict_
 }
 
 // Reverse of coupling iteration k for design point m: dJ/dkappa^ref_m += ..., and the point's
-// contribution to dJ/ds^(k-1) added to v[8] = (xG[3], uG[3], theta, omega). Called by all LN lanes
-// of the point (each takes one row, or in 3D one plane, of the support window; every thread of the
-// warp must call it); lane 0 finishes the point. Returns false if the support window left the
-// body box.
+// contribution to dJ/ds^(k-1) added to v: (xG[3], uG[3], theta, omega) about one axis, or
+// (xG[3], uG[3], omega[3], R[9]) with free rotation. Called by all LN lanes of the point (each
+// takes one row, or in 3D one plane, of the support window; every thread of the warp must call it);
+// lane 0 finishes the point. Design points outside the design domain do nothing. Returns false if
+// the support window left the body box.
 template <typename T, int D, int AX>
 __device__ __forceinline__ bool adj_design_point(const Geo& g, const T* __restrict__ kref, const T* scratch,
-                                                 const Dof& sk, const int (&lo)[3], int m, bool valid, int lane,
-                                                 const T (&lF)[3], T lT, double* __restrict__ dkref, T* v) {
-  constexpr int b = Axes<AX>::B, c = Axes<AX>::C, ax = Axes<AX>::A;
+                                                 const Dof& sk, const int (&lo)[3], int m, bool valid_m, int lane,
+                                                 const T (&lF)[3], const T (&lT)[3], double* __restrict__ dkref,
+                                                 T* v) {
   const long long BC = g.box_cells;
-  const int mm = valid ? m : 0;
+  const int mm = valid_m ? m : 0;
   const int ix = mm % g.nd[0], iy = (mm / g.nd[0]) % g.nd[1], iz = mm / (g.nd[0] * g.nd[1]);
+  const bool valid = valid_m && dsq(ix, g.nd[0]) + dsq(iy, g.nd[1]) + dsq(iz, g.nd[2]) <= g.rad4;
   const T r[3] = {(T)ix - pivot<T>(g, 0), (T)iy - pivot<T>(g, 1), D == 3 ? (T)iz - pivot<T>(g, 2) : T(0)};
   const DofView<T> V(sk);
-  const T cs = V.cs, sn = V.sn, om = V.om;
-  T l[3], dl[3];
-  rot<AX>(cs, sn, r, l);
-  drot<AX>(cs, sn, r, dl);
+  T l[3], dl[3] = {T(0), T(0), T(0)}, om3[3] = {T(0), T(0), T(0)};
   const T km = kref[mm];
   T usr[3] = {T(0), T(0), T(0)}, luref[3] = {T(0), T(0), T(0)}, rotl[3] = {T(0), T(0), T(0)};
+  if constexpr (AX == AX_FREE) {
+    const FreeView<T> FV(sk);
+    matvec3(FV.R, r, l);
+    T oxl[3];
+    cross3(FV.om, l, oxl);
 #pragma unroll
-  for (int a = 0; a < D; ++a) usr[a] = V.ug[a] + om * dl[a];
-  rotl[b] = -lT * l[c];
-  rotl[c] = lT * l[b];
+    for (int a = 0; a < 3; ++a) {
+      om3[a] = FV.om[a];
+      usr[a] = V.ug[a] + oxl[a];
+    }
+    cross3(lT, l, rotl);
+  } else {
+    constexpr int b = Axes<AX>::B, c = Axes<AX>::C;
+    rot<AX>(V.cs, V.sn, r, l);
+    drot<AX>(V.cs, V.sn, r, dl);
+#pragma unroll
+    for (int a = 0; a < D; ++a) usr[a] = V.ug[a] + V.om * dl[a];
+    rotl[b] = -lT[0] * l[c];
+    rotl[c] = lT[0] * l[b];
+  }
 #pragma unroll
   for (int a = 0; a < D; ++a) luref[a] = km * (lF[a] + rotl[a]);
   // support window: 2s cells per axis from floor(x^ref) - s + 1
@@ -318,20 +442,45 @@ __device__ __forceinline__ bool adj_design_point(const Geo& g, const T* __restri
   T Dl[3] = {T(0), T(0), T(0)};
 #pragma unroll
   for (int a = 0; a < D; ++a) Dl[a] = uref[a] - usr[a];
-  T dk = slk + lT * (l[b] * Dl[c] - l[c] * Dl[b]);
+  if constexpr (AX == AX_FREE) {
+    T lxD[3], DxT[3], lusr[3], lxu[3], uxo[3];
+    cross3(l, Dl, lxD);
+    cross3(Dl, lT, DxT);
+    T dk = slk;
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+      dk += lF[a] * Dl[a] + lT[a] * lxD[a];
+      lusr[a] = -luref[a] + slus[a];
+    }
+    dkref[m] += (double)dk;
+    cross3(l, lusr, lxu);   // lusr . (omega x l) = omega . (l x lusr)
+    cross3(lusr, om3, uxo);  //                   = l . (lusr x omega)
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+      v[i] += lxr[i];
+      v[3 + i] += lusr[i];
+      v[6 + i] += lxu[i];
+      const T gl = lxr[i] + km * DxT[i] + uxo[i];  // dJ/d(R r_m): transform, torque lever, solid velocity
+#pragma unroll
+      for (int j = 0; j < 3; ++j) v[9 + 3 * i + j] += gl * r[j];
+    }
+    return inside;
+  } else {
+  constexpr int b = Axes<AX>::B, c = Axes<AX>::C, ax = Axes<AX>::A;
+  T dk = slk + lT[0] * (l[b] * Dl[c] - l[c] * Dl[b]);
 #pragma unroll
   for (int a = 0; a < D; ++a) dk += lF[a] * Dl[a];
   dkref[m] += (double)dk;
   T lusr[3] = {T(0), T(0), T(0)}, ll[3] = {T(0), T(0), T(0)};
 #pragma unroll
   for (int a = 0; a < D; ++a) lusr[a] = -luref[a] + slus[a];
-  ll[b] = lT * km * Dl[c];
-  ll[c] = -lT * km * Dl[b];
+  ll[b] = lT[0] * km * Dl[c];
+  ll[c] = -lT[0] * km * Dl[b];
   T lth = T(0), lom = T(0);
 #pragma unroll
   for (int a = 0; a < 3; ++a) {
     const T ddl = (a == ax) ? T(0) : -l[a];  // R'' r
-    lth += (lxr[a] + ll[a]) * dl[a] + om * lusr[a] * ddl;
+    lth += (lxr[a] + ll[a]) * dl[a] + V.om * lusr[a] * ddl;
     lom += lusr[a] * dl[a];
   }
 #pragma unroll
@@ -342,6 +491,7 @@ __device__ __forceinline__ bool adj_design_point(const Geo& g, const T* __restri
   v[6] += lth;
   v[7] += lom;
   return inside;
+  }
 }
 
 // From the transform part ls = dJ/ds^(k-1) (design-point sums): the EOM reverse of iteration
@@ -351,8 +501,8 @@ __device__ __forceinline__ void adj_finish(const Geo& g, int k, const double* ls
   if (k > 1) {
     eom_reverse(g, ls, lamF, lamT, lam_prev);
   } else {
-    double lsm1[8];
-    for (int a = 0; a < 8; ++a) {
+    double lsm1[kNdofAxis];
+    for (int a = 0; a < kNdofAxis; ++a) {
       lsm1[a] = lam_prev[a] + ls[a];
       lam_s0[a] = lsm1[a];
       lam_prev[a] = 0.0;
@@ -361,18 +511,55 @@ __device__ __forceinline__ void adj_finish(const Geo& g, int k, const double* ls
   }
 }
 
+// adj_finish with free rotation. ls = (xG[3], uG[3], omega[3], R[9]) from the design points; the
+// EOM being reversed maps e0 = s(t'-1) to ek = s^(k') (iteration k - 1 of step t, or N_itr of step
+// t - 1); has_eom is false before step 1.
+__device__ __forceinline__ void adj_finish_free(const Geo& g, int k, const double* ls, double* lam_prev,
+                                                double* lamF, double* lamT, double* lam_s0, const Dof& e0,
+                                                const Dof& ek, bool has_eom) {
+  double lsf[kNdofFree];
+#pragma unroll
+  for (int a = 0; a < 6; ++a) lsf[a] = ls[a];
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    lsf[S_H + a] = 0.0;
+    lsf[S_OM + a] = ls[6 + a];
+  }
+#pragma unroll
+  for (int i = 0; i < 9; ++i) lsf[S_R + i] = ls[9 + i];
+  if (k == 1) {
+#pragma unroll
+    for (int a = 0; a < kNdofFree; ++a) {
+      lsf[a] += lam_prev[a];
+      lam_s0[a] = lsf[a];
+      lam_prev[a] = 0.0;
+    }
+  }
+  if (has_eom) {
+    eom_reverse_free(g, e0, ek, lsf, lamF, lamT, lam_prev);
+  } else {
+    for (int a = 0; a < 3; ++a) lamF[a] = lamT[a] = 0.0;
+  }
+}
+
+// kappa^ref (Eq. brinkman_coefficient; zero outside the design domain) and the design-grid
+// moments of kappa^ref.
 template <typename T>
 __global__ void __launch_bounds__(256) k_prep(Geo g, const double* __restrict__ gamma, double kmax, double q,
                                                T* __restrict__ kref, Moments* mom, double* partials, Ctrl* ctrl) {
-  __shared__ double red[32 * 5];
+  constexpr int NM = 12;  // K0, K1[3], K2p, K2s, K2[6]
+  __shared__ double red[32 * NM];
   const int m = blockIdx.x * blockDim.x + threadIdx.x;
-  double v[5] = {0, 0, 0, 0, 0};
+  double v[NM];
+#pragma unroll
+  for (int a = 0; a < NM; ++a) v[a] = 0.0;
   if (m < g.ND) {
+    const int i[3] = {m % g.nd[0], (m / g.nd[0]) % g.nd[1], m / (g.nd[0] * g.nd[1])};
+    const bool dom = dsq(i[0], g.nd[0]) + dsq(i[1], g.nd[1]) + dsq(i[2], g.nd[2]) <= g.rad4;
     const double gm = gamma[m];
-    const T k = (T)(kmax * q * gm / ((1.0 - gm) + q));  // Eq. brinkman_coefficient
+    const T k = dom ? (T)(kmax * q * gm / ((1.0 - gm) + q)) : T(0);
     kref[m] = k;
     const double kd = (double)k;
-    const int i[3] = {m % g.nd[0], (m / g.nd[0]) % g.nd[1], m / (g.nd[0] * g.nd[1])};
     double r[3];
     for (int a = 0; a < 3; ++a) r[a] = (a < g.dim) ? i[a] - g.xic[a] : 0.0;
     v[0] = kd;
@@ -380,19 +567,28 @@ __global__ void __launch_bounds__(256) k_prep(Geo g, const double* __restrict__ 
     v[2] = kd * r[1];
     v[3] = kd * r[2];
     v[4] = kd * (r[g.axb] * r[g.axb] + r[g.axc] * r[g.axc]);
+    v[5] = kd * (r[0] * r[0] + r[1] * r[1] + r[2] * r[2]);
+    v[6] = kd * r[0] * r[0];
+    v[7] = kd * r[1] * r[1];
+    v[8] = kd * r[2] * r[2];
+    v[9] = kd * r[0] * r[1];
+    v[10] = kd * r[0] * r[2];
+    v[11] = kd * r[1] * r[2];
   }
-  block_sum<5>(v, red);
+  block_sum<NM>(v, red);
   if (threadIdx.x == 0)
-    for (int a = 0; a < 5; ++a) partials[blockIdx.x * 5 + a] = v[a];
+    for (int a = 0; a < NM; ++a) partials[blockIdx.x * NM + a] = v[a];
   if (!last_block_done(&ctrl->count[CNT_PREP])) return;
-  double s[5];
-  sum_partials<5>(partials, gridDim.x, s, red);
+  double s[NM];
+  sum_partials<NM>(partials, gridDim.x, s, red);
   if (threadIdx.x == 0) {
     mom->K0 = s[0];
     mom->K1[0] = s[1];
     mom->K1[1] = s[2];
     mom->K1[2] = s[3];
     mom->K2p = s[4];
+    mom->K2s = s[5];
+    for (int a = 0; a < 6; ++a) mom->K2[a] = s[6 + a];
     ctrl->count[CNT_PREP] = 0;
   }
 }
@@ -410,41 +606,51 @@ __global__ void __launch_bounds__(kCellThreads, 2) k_couple(Geo g, Slots<T> S, C
                                                           void* partials, long long pstride, int nparts, int k,
                                                           T* __restrict__ boxstore, int nbox, int di) {
   using PT = typename Partial<T>::type;
-  __shared__ double red[32 * 4];
-  __shared__ Dof sd[2];  // s(t-1), s^(k-1)
+  constexpr int NV = nv_couple<AX>();
+  constexpr int DW = (int)(sizeof(Dof) / sizeof(double));  // the iterate in 8-byte words
+  static_assert(sizeof(Dof) % sizeof(double) == 0, "iterate copies by 8-byte words");
+  __shared__ double red[32 * NV];
+  __shared__ Dof sd[3];  // s(t-1), s^(k-1), and the previous iteration's transform iterate
   const int t = ctrl->t0 + di, base = ctrl->base, K = g.K;
   Dof* row = it + (long long)(t - 1) * (K + 1);
   const long long idx = (long long)(t - 1) * K + (k - 1);  // iteration index in the run
   PT* pin = static_cast<PT*>(partials) + ((idx - 1) & 1) * pstride;
   PT* pout = static_cast<PT*>(partials) + (idx & 1) * pstride;
+  double* sdw = reinterpret_cast<double*>(sd);
+  const int tid = threadIdx.x;
   if (idx > 0) {
-    // previous iteration kp of step tp
+    // previous iteration kp of step tp: its EOM starts from prow[0] with the transform of
+    // prow[kp - 1]; both are staged in shared memory by the block (thread 0 then reads only the
+    // fields it needs, keeping its FP64 chain in registers)
     Dof* prow = (k > 1) ? row : row - (K + 1);
     const int kp = (k > 1) ? k - 1 : K;
-    Dof p0, pk;
+    const double* g0 = reinterpret_cast<const double*>(prow);
+    const double* gk = reinterpret_cast<const double*>(prow + (kp - 1));
+    if (tid < DW) {
+      sdw[tid] = g0[tid];
+      sdw[2 * DW + tid] = gk[tid];
+    }
     Moments m;
-    if (threadIdx.x == 0) {
-      p0 = prow[0];
-      pk = prow[kp - 1];
-      m = *mom;
-    }
-    double sm[4];
-    block_sum_partials<4>(pin, nparts, sm, red);
-    if (threadIdx.x == 0) {
-      Dof nx;
-      int st = 0;
-      couple_finish<D, AX>(g, &m, p0, pk, sm, &nx, &st);
-      if (blockIdx.x == 0 && blockIdx.y == 0 && blockIdx.z == 0) {
-        if (st) ctrl->status |= st;
-        prow[kp] = nx;
-        if (kp == K) row[0] = nx;
+    if (tid == 0) m = *mom;
+    double sm[NV];
+    block_sum_partials<NV>(pin, nparts, sm, red);  // its barriers order the staging copies
+    int st = 0;
+    if (tid == 0) couple_finish_any<D, AX>(g, &m, sd[0], sd[2], sm, &sd[1], &st);
+    __syncthreads();
+    if (k == 1 && tid < DW) sdw[tid] = sdw[DW + tid];  // s(t-1) is the new iterate
+    if (blockIdx.x == 0 && blockIdx.y == 0 && blockIdx.z == 0) {
+      if (tid == 0 && st) ctrl->status |= st;
+      double* o1 = reinterpret_cast<double*>(prow + kp);
+      double* o2 = reinterpret_cast<double*>(row);
+      if (tid < DW) {
+        o1[tid] = sdw[DW + tid];
+        if (kp == K) o2[tid] = sdw[DW + tid];
       }
-      sd[0] = (k > 1) ? p0 : nx;  // s(t-1): already fetched for k > 1
-      sd[1] = nx;
     }
-  } else if (threadIdx.x == 0) {
-    sd[0] = row[0];
-    sd[1] = row[0];
+  } else if (tid < DW) {
+    const double* g0 = reinterpret_cast<const double*>(row);
+    sdw[tid] = g0[tid];
+    sdw[DW + tid] = g0[tid];
   }
   __syncthreads();
   const Dof s0 = sd[0], sk = sd[1];
@@ -453,9 +659,11 @@ __global__ void __launch_bounds__(kCellThreads, 2) k_couple(Geo g, Slots<T> S, C
   box_origin<D>(g, s0, lo[0], lo[1], lo[2]);
   T* bs = (boxstore && k == K) ? boxstore + (long long)((t - base - 1) % nbox) * g.box_cells * D : nullptr;
   const CellSlot cc = cell_slot(g);
-  T v[4] = {T(0), T(0), T(0), T(0)};
+  T v[NV];
+#pragma unroll
+  for (int a = 0; a < NV; ++a) v[a] = T(0);
   couple_cell<T, D, AX>(g, kref, sk, lo, cc, dst, bs, k == K, &ctrl->status, v);
-  block_sum_partial<4>(v, pout + block_linear() * 4, red);
+  block_sum_partial<NV>(v, pout + block_linear() * NV, red);
 }
 
 // EOM of the last coupling iteration of the run (step t_last, iteration N_itr).
@@ -465,7 +673,8 @@ __global__ void __launch_bounds__(kFinishThreads, 1) k_couple_last(Geo g, Ctrl* 
                                                                  const void* __restrict__ partials,
                                                                  long long pstride, int nparts, int t_last) {
   using PT = typename Partial<T>::type;
-  __shared__ double red[32 * 4];
+  constexpr int NV = nv_couple<AX>();
+  __shared__ double red[32 * NV];
   const int K = g.K;
   Dof* row = it + (long long)(t_last - 1) * (K + 1);
   const long long idx = (long long)(t_last - 1) * K + (K - 1);
@@ -477,12 +686,12 @@ __global__ void __launch_bounds__(kFinishThreads, 1) k_couple_last(Geo g, Ctrl* 
     sk = row[K - 1];
     m = *mom;
   }
-  double sm[4];
-  block_sum_partials<4>(pin, nparts, sm, red);
+  double sm[NV];
+  block_sum_partials<NV>(pin, nparts, sm, red);
   if (threadIdx.x == 0) {
     Dof nx;
     int st = 0;
-    couple_finish<D, AX>(g, &m, s0, sk, sm, &nx, &st);
+    couple_finish_any<D, AX>(g, &m, s0, sk, sm, &nx, &st);
     if (st) ctrl->status |= st;
     row[K] = nx;
     it[(long long)t_last * (K + 1)] = nx;
@@ -508,19 +717,16 @@ __global__ void __launch_bounds__(kCellThreads, 2) k_apply(Geo g, Slots<T> S, co
   const bool ing = cell_index<D>(g, px, py, pz, n);
   const DofView<T> V(sk);
   const T d[3] = {V.rel(0, px), V.rel(1, py), D == 3 ? V.rel(2, pz) : T(0)};
-  const T cs = V.cs, sn = V.sn;
   Acc<T> A;
-  gather_lanes<T, D, AX, LN>(g, kref, d, cs, sn, cc.lane, cc.active && ing, A);
+  T rotv[3], L[3];
+  gather_cell<T, D, AX>(g, kref, sk, V, d, cc.lane, cc.active && ing, A, rotv, L);
   if (!cc.active || !ing || cc.lane != 0) return;
-  T dwr[3];
-  drot<AX>(cs, sn, A.wr, dwr);
-  const T om = V.om;
   const T inv = T(1) / (T(1) + A.kap);
   const long long bl = j0 + (long long)g.B[0] * (j1 + (long long)g.B[1] * j2);
   T* bs = boxstore + (long long)((t - base - 1) % nbox) * g.box_cells * D;
 #pragma unroll
   for (int a = 0; a < D; ++a) {
-    const T us = V.ug[a] * A.phi + om * dwr[a];
+    const T us = V.ug[a] * A.phi + rotv[a];
     const T ustar = dst[(a + 1) * N + n];
     bs[a * g.box_cells + bl] = ustar;
     dst[(a + 1) * N + n] = (ustar + A.kap * us) * inv;
@@ -535,7 +741,7 @@ __global__ void __launch_bounds__(kCellThreads, 2) k_adj_cell(Geo g, const Ctrl*
   const int t = ctrl->t0 - di, base = ctrl->base, K = g.K;
   const Dof* row = it + (long long)(t - 1) * (K + 1);
   const Dof s0 = row[0], sk = row[k - 1];
-  T lF[3], lT;
+  T lF[3], lT[3];
   lam_load<T>(ctrl, lF, lT);
   T* Lcur = Lb + (long long)(t & 1) * lstride;
   int lo[3];
@@ -551,35 +757,58 @@ __global__ void __launch_bounds__(kDesignBlock) k_adj_design(Geo g, Ctrl* ctrl, 
                                                               const T* __restrict__ scratch,
                                                               double* __restrict__ dkref, void* partials, int k,
                                                               int di) {
-  __shared__ double red[32 * 8];
+  constexpr int NV = nv_design<AX>();
+  __shared__ double red[32 * NV];
   const int t = ctrl->t0 - di, K = g.K;
   const Dof* row = it + (long long)(t - 1) * (K + 1);
   const Dof s0 = row[0], sk = row[k - 1];
-  T lF[3], lT;
+  T lF[3], lT[3];
   lam_load<T>(ctrl, lF, lT);
   int lo[3];
   box_origin<D>(g, s0, lo[0], lo[1], lo[2]);
   const int m = blockIdx.x * kDesignPointsPerCta + threadIdx.x / LN, lane = threadIdx.x % LN;
-  T v[8] = {T(0), T(0), T(0), T(0), T(0), T(0), T(0), T(0)};
+  T v[NV];
+#pragma unroll
+  for (int a = 0; a < NV; ++a) v[a] = T(0);
   if (!adj_design_point<T, D, AX>(g, kref, scratch, sk, lo, m, m < g.ND, lane, lF, lT, dkref, v))
     atomicOr(&ctrl->status, ST_BOX_OVERFLOW);
-  block_sum_partial<8>(v, static_cast<typename Partial<T>::type*>(partials) + blockIdx.x * 8, red);
+  block_sum_partial<NV>(v, static_cast<typename Partial<T>::type*>(partials) + blockIdx.x * NV, red);
 }
 
-// Sum of the design-point partials and the EOM reverse (adj_finish).
-template <typename T>
-__global__ void __launch_bounds__(kFinishThreads) k_design_finish(Geo g, Ctrl* ctrl, const void* __restrict__ partials,
-                                                                  int nparts, int k) {
-  __shared__ double red[32 * 8];
-  double lp[8];  // thread 0 fetches the carried adjoint before the reduction
-  if (threadIdx.x == 0)
-    for (int a = 0; a < 8; ++a) lp[a] = ctrl->lam_prev[a];
-  double ls[8];
-  block_sum_partials<8>(static_cast<const typename Partial<T>::type*>(partials), nparts, ls, red);
+// Sum of the design-point partials and the EOM reverse (adj_finish, or adj_finish_free with the
+// iterates of the EOM being reversed).
+template <typename T, bool FREE>
+__global__ void __launch_bounds__(kFinishThreads) k_design_finish(Geo g, Ctrl* ctrl, const Dof* it,
+                                                                  const void* __restrict__ partials, int nparts,
+                                                                  int k, int di) {
+  constexpr int NV = FREE ? nv_design<AX_FREE>() : nv_design<0>();
+  constexpr int NS = FREE ? kNdofFree : kNdofAxis;
+  __shared__ double red[32 * NV];
+  double lp[NS];  // thread 0 fetches the carried adjoint (and the EOM's iterates) before the reduction
+  Dof e0, ek;
+  bool has_eom = true;
   if (threadIdx.x == 0) {
-    double nF[3], nT;
-    adj_finish(g, k, ls, lp, nF, &nT, ctrl->lam_s0);
-    for (int a = 0; a < 8; ++a) ctrl->lam_prev[a] = lp[a];
+    for (int a = 0; a < NS; ++a) lp[a] = ctrl->lam_prev[a];
+    if (FREE) {
+      const int t = ctrl->t0 - di, K = g.K;
+      const int te = (k > 1) ? t : t - 1, ke = (k > 1) ? k - 1 : K;
+      has_eom = te >= 1;
+      if (has_eom) {
+        const Dof* row = it + (long long)(te - 1) * (K + 1);
+        e0 = row[0];
+        ek = row[ke];
+      }
+    }
+  }
+  double ls[NV];
+  block_sum_partials<NV>(static_cast<const typename Partial<T>::type*>(partials), nparts, ls, red);
+  if (threadIdx.x == 0) {
+    double nF[3], nT[3];
+    if constexpr (FREE)
+      adj_finish_free(g, k, ls, lp, nF, nT, ctrl->lam_s0, e0, ek, has_eom);
+    else
+      adj_finish(g, k, ls, lp, nF, nT, ctrl->lam_s0);
+    for (int a = 0; a < NS; ++a) ctrl->lam_prev[a] = lp[a];
     lam_store(ctrl, nF, nT);
   }
 }
@@ -597,10 +826,11 @@ __global__ void k_init_forward(Geo g, Slots<T> S, const double* __restrict__ p0,
   }
   if (blockIdx.x == 0 && threadIdx.x == 0) {
     Dof d;
-    for (int a = 0; a < 8; ++a) d.s[a] = s0[a];
-    d.cs = cos(d.s[6]);
-    d.sn = sin(d.s[6]);
-    dof_views(&d);
+    const bool free_rot = g.ax == AX_FREE;
+    for (int a = 0; a < kNdofFree; ++a) d.s[a] = (a < g.ns) ? s0[a] : 0.0;
+    d.cs = free_rot ? 1.0 : cos(d.s[6]);
+    d.sn = free_rot ? 0.0 : sin(d.s[6]);
+    dof_views(&d, free_rot);
     it[0] = d;
     ctrl->t0 = 1;
     ctrl->base = 0;
@@ -613,14 +843,21 @@ __global__ void k_set_step(Ctrl* ctrl, int t0, int base) {
   ctrl->base = base;
 }
 
-__global__ void k_adj_init(Geo g, Ctrl* ctrl, const double* objw, double seed) {
-  double ls[8], lp[8], nF[3], nT;
-  for (int a = 0; a < 8; ++a) {
-    ls[a] = seed * objw[a];
+// Seed of the reverse sweep: dJ/ds(N_t) = seed * w, then the EOM reverse of iteration N_itr of
+// step N_t (free rotation: from the iterates it[N_t - 1][0] and it[N_t - 1][N_itr]).
+__global__ void k_adj_init(Geo g, Ctrl* ctrl, const Dof* it, int nt, const double* objw, double seed) {
+  double ls[kNdofFree], lp[kNdofFree], nF[3], nT[3];
+  for (int a = 0; a < kNdofFree; ++a) {
+    ls[a] = (a < g.ns) ? seed * objw[a] : 0.0;
     lp[a] = 0.0;
   }
-  eom_reverse(g, ls, nF, &nT, lp);
-  for (int a = 0; a < 8; ++a) ctrl->lam_prev[a] = lp[a];
+  if (g.ax == AX_FREE) {
+    const Dof* row = it + (long long)(nt - 1) * (g.K + 1);
+    eom_reverse_free(g, row[0], row[g.K], ls, nF, nT, lp);
+  } else {
+    eom_reverse(g, ls, nF, nT, lp);
+  }
+  for (int a = 0; a < kNdofFree; ++a) ctrl->lam_prev[a] = lp[a];
   lam_store(ctrl, nF, nT);
 }
 
@@ -657,8 +894,10 @@ inline dim3 box_grid(const Geo& g) {
       launch(KERNEL<T, 3, 0>, GRID, BLOCK, 0, st, __VA_ARGS__); \
     else if (g.ax == 1)                                     \
       launch(KERNEL<T, 3, 1>, GRID, BLOCK, 0, st, __VA_ARGS__); \
-    else                                                    \
+    else if (g.ax == 2)                                     \
       launch(KERNEL<T, 3, 2>, GRID, BLOCK, 0, st, __VA_ARGS__); \
+    else                                                    \
+      launch(KERNEL<T, 3, AX_FREE>, GRID, BLOCK, 0, st, __VA_ARGS__); \
   } while (0)
 
 
@@ -703,7 +942,10 @@ void launch_adj_design(const Geo& g, Ctrl* ctrl, const Dof* it, const T* kref, c
                        void* partials, int k, int di, cudaStream_t st) {
   const unsigned nb = (unsigned)((g.ND + kDesignPointsPerCta - 1) / kDesignPointsPerCta);
   LKS_BOX_DISPATCH(k_adj_design, nb, kDesignBlock, g, ctrl, it, kref, scratch, dkref, partials, k, di);
-  launch(k_design_finish<T>, 1, kFinishThreads, 0, st, g, ctrl, (const void*)partials, (int)nb, k);
+  if (g.ax == AX_FREE)
+    launch(k_design_finish<T, true>, 1, kFinishThreads, 0, st, g, ctrl, it, (const void*)partials, (int)nb, k, di);
+  else
+    launch(k_design_finish<T, false>, 1, kFinishThreads, 0, st, g, ctrl, it, (const void*)partials, (int)nb, k, di);
 }
 
 template <typename T>
@@ -715,10 +957,10 @@ void launch_init_forward(const Geo& g, const Slots<T>& S, const double* p0, cons
 
 void launch_set_step(Ctrl* ctrl, int t0, int base, cudaStream_t st) { launch(k_set_step, 1, 1, 0, st, ctrl, t0, base); }
 
-void launch_adj_init(const Geo& g, Ctrl* ctrl, const double* objw, double seed, double* dkref, int nd,
-                     cudaStream_t st) {
+void launch_adj_init(const Geo& g, Ctrl* ctrl, const Dof* it, int nt, const double* objw, double seed, double* dkref,
+                     int nd, cudaStream_t st) {
   cudaMemsetAsync(dkref, 0, sizeof(double) * (size_t)nd, st);
-  launch(k_adj_init, 1, 1, 0, st, g, ctrl, objw, seed);
+  launch(k_adj_init, 1, 1, 0, st, g, ctrl, it, nt, objw, seed);
 }
 
 void launch_sensitivity(const Geo& g, const double* gamma, const double* dkref, double kappa_max, double q,

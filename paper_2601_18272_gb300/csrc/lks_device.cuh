@@ -8,6 +8,8 @@
 //   body box     : the cells a body can touch during one step, a box of B[0]*B[1]*B[2] cells
 //                  placed from x^G(t-1) (unwrapped coordinates, wrapped on periodic axes)
 //   DOF iterates : Dof it[(t-1)*(K+1) + k], k = 0..K, s^(0) = s(t-1), s^(K) = s(t)  (FP64)
+//   DOF vector   : (xG[3], uG[3], theta, omega) about one axis, or with free rotation
+//                  (xG[3], uG[3], h[3], omega[3], R[9] row-major)
 #pragma once
 
 #include <cuda_runtime.h>
@@ -21,20 +23,26 @@ enum { DOF_TX = 1, DOF_TY = 2, DOF_TZ = 4, DOF_ROT = 8 };
 enum { CKQ_BF16 = 1, CKQ_FP16 = 2 };  // reduced-precision checkpoint formats
 enum { ST_BODY_OUTSIDE = 1, ST_NONFINITE = 2, ST_BOX_OVERFLOW = 4 };
 enum { CNT_COUPLE = 0, CNT_APPLY = 1, CNT_DESIGN = 2, CNT_ADJ_STENCIL = 3, CNT_PREP = 4, CNT_CKPT = 5, CNT_N = 8 };
+// Rotation modes (the AX template argument of the body kernels): 0, 1, 2 = one axis; free rotation.
+constexpr int AX_FREE = 3;
+constexpr int kNdofAxis = 8, kNdofFree = 21;
+// DOF-vector offsets with free rotation
+constexpr int S_H = 6, S_OM = 9, S_R = 12;
 
-// One DOF iterate: s = (xG[3], uG[3], theta, omega) plus cos/sin theta, and FP32 views of what the
-// per-cell kernels need (written once per iterate by dof_views, so that FP32 kernels do no FP64
-// arithmetic: GB300 issues FP64 at a small fraction of the FP32 rate).
+// One DOF iterate: s plus cos/sin theta, and FP32 views of what the per-cell kernels need
+// (written once per iterate by dof_views, so that FP32 kernels do no FP64 arithmetic: GB300 issues
+// FP64 at a small fraction of the FP32 rate). With free rotation Rf and omf view R and omega.
 struct Dof {
-  double s[8];
+  double s[kNdofFree];
   double cs, sn;
   int xi[3];    // floor(x^G)
   float xf[3];  // x^G - floor(x^G)
   float ug[3];  // u^G
   float om, csf, snf;
+  float Rf[9], omf[3];
 };
 
-__host__ __device__ inline void dof_views(Dof* d) {
+__host__ __device__ inline void dof_views(Dof* d, bool free_rot) {
 #pragma unroll
   for (int a = 0; a < 3; ++a) {
     const double fl = floor(d->s[a]);
@@ -45,6 +53,12 @@ __host__ __device__ inline void dof_views(Dof* d) {
   d->om = (float)d->s[7];
   d->csf = (float)d->cs;
   d->snf = (float)d->sn;
+  if (free_rot) {
+#pragma unroll
+    for (int i = 0; i < 9; ++i) d->Rf[i] = (float)d->s[S_R + i];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) d->omf[a] = (float)d->s[S_OM + a];
+  }
 }
 
 // Per-thread view of an iterate in the field type T: FP32 fields read the FP32 views, FP64 fields
@@ -96,11 +110,11 @@ struct Ctrl {
   int status;             // ST_* bits
   int pad;
   unsigned count[CNT_N];  // last-block counters, one per kernel family
-  double lam_prev[8];     // adjoint: direct EOM part of dJ/ds(t-1)
+  double lam_prev[kNdofFree];  // adjoint: direct EOM part of dJ/ds(t-1)
   double lam_F[3];        // adjoint: dJ/dF of the iteration being reversed
-  double lam_T;           // adjoint: dJ/dT
-  double lam_s0[8];       // adjoint: dJ/ds(0) after the sweep
-  float lam_Ff[3], lam_Tf;  // FP32 copies of lam_F, lam_T
+  double lam_T[3];        // adjoint: dJ/dT (about the axis in [0], or the vector with free rotation)
+  double lam_s0[kNdofFree];  // adjoint: dJ/ds(0) after the sweep
+  float lam_Ff[3], lam_Tf[3];  // FP32 copies of lam_F, lam_T
 };
 
 // Design-grid moments used by the closed-form design-side force and torque terms.
@@ -108,6 +122,8 @@ struct Moments {
   double K0;        // sum kappa_m
   double K1[3];     // sum kappa_m r_m
   double K2p;       // sum kappa_m |r_m perp|^2 (perpendicular to the rotation axis)
+  double K2s;       // sum kappa_m |r_m|^2
+  double K2[6];     // sum kappa_m r_m r_m^T: xx, yy, zz, xy, xz, yz
 };
 
 // Problem constants passed by value to every kernel.
@@ -120,7 +136,10 @@ struct Geo {
   int ND;
   double xic[3];  // design pivot xi^G
   float xicf[3];  // FP32 copy of the pivot
-  int ax, axb, axc;
+  int ax, axb, axc;  // rotation axis and its plane; ax = AX_FREE with free rotation
+  int ns;            // DOF vector length
+  int rad4;          // design domain: 4|r_m|^2 <= rad4 (an integer test; INT_MAX for the whole grid)
+  double Jinv[9];    // free rotation: I_b^-1
   int dof_mask;
   int wk, s;      // weight kind, support half-width (2 for cos4, 1 for bilinear)
   int K;          // N_itr
@@ -241,98 +260,17 @@ struct Acc {
   F wr[3], kr[3];
 };
 
-// Gather (Eqs. kappa_mapping, us_mapping) for the cell at d = x_n - x^G under rotation (cs, sn)
-// about AX. Candidates: the design points whose rotated position lies in the axis-aligned support
-// square of the cell; in the design frame they lie within s (|cos| + |sin|) of the cell's image.
-template <typename F, int D, int AX>
-__device__ __forceinline__ void gather(const Geo& g, const F* __restrict__ kref, const F (&d)[3], F cs, F sn,
-                                       Acc<F>& o) {
-  constexpr int b = Axes<AX>::B, c = Axes<AX>::C, ax = Axes<AX>::A;
-  const F S = (F)g.s;
-  const F xib = cs * d[b] + sn * d[c] + pivot<F>(g, b);
-  const F xic = -sn * d[b] + cs * d[c] + pivot<F>(g, c);
-  const F h = S * (fabs(cs) + fabs(sn));
-  const int ib0 = max(0, (int)ceil(xib - h)), ib1 = min(g.nd[b] - 1, (int)floor(xib + h));
-  const int ic0 = max(0, (int)ceil(xic - h)), ic1 = min(g.nd[c] - 1, (int)floor(xic + h));
-  int ia0 = 0, ia1 = 0;
-  F xia = F(0);
-  if (D == 3) {
-    xia = d[ax] + pivot<F>(g, ax);
-    const int fa = (int)floor(xia);
-    ia0 = max(0, fa - g.s + 1);
-    ia1 = min(g.nd[ax] - 1, fa + g.s);
-  }
-  o.phi = o.kap = F(0);
-#pragma unroll
-  for (int a = 0; a < 3; ++a) o.wr[a] = o.kr[a] = F(0);
-  const int sx = 1, sy = g.nd[0], sz = g.nd[0] * g.nd[1];
-  const int sb = (b == 0) ? sx : (b == 1 ? sy : sz);
-  const int sc = (c == 0) ? sx : (c == 1 ? sy : sz);
-  const int sa = (ax == 0) ? sx : (ax == 1 ? sy : sz);
-  // For a candidate row ib, both rotated offsets are linear in ec = ic - xic:
-  //   x^ref - x_n along b: cs eb - sn ec,  along c: sn eb + cs ec.
-  // Bound the column loop by the interval where both lie in (-S, S), widened slightly; the exact
-  // acceptance test below still decides.
-  const F tiny = F(1e-6), pad = F(1e-3);
-  const F ics = fabs(cs) > tiny ? F(1) / cs : F(0), isn = fabs(sn) > tiny ? F(1) / sn : F(0);
-  for (int ib = ib0; ib <= ib1; ++ib) {
-    const F eb = (F)ib - xib;
-    F elo = -F(1e30), ehi = F(1e30);
-    if (isn != F(0)) {  // |cs eb - sn ec| < S
-      const F e1 = (cs * eb - S) * isn, e2 = (cs * eb + S) * isn;
-      elo = fmax(elo, fmin(e1, e2));
-      ehi = fmin(ehi, fmax(e1, e2));
-    } else if (fabs(cs * eb) >= S + pad) {
-      continue;
-    }
-    if (ics != F(0)) {  // |sn eb + cs ec| < S
-      const F e1 = (-S - sn * eb) * ics, e2 = (S - sn * eb) * ics;
-      elo = fmax(elo, fmin(e1, e2));
-      ehi = fmin(ehi, fmax(e1, e2));
-    } else if (fabs(sn * eb) >= S + pad) {
-      continue;
-    }
-    elo = fmax(elo, F(-1e6));
-    ehi = fmin(ehi, F(1e6));
-    const int jc0 = max(ic0, (int)ceil(xic + elo - pad)), jc1 = min(ic1, (int)floor(xic + ehi + pad));
-    for (int ic = jc0; ic <= jc1; ++ic) {
-      const F ec = (F)ic - xic;
-      const F ob = cs * eb - sn * ec;  // x^ref_m - x_n along b
-      const F oc = sn * eb + cs * ec;
-      if (fabs(ob) >= S || fabs(oc) >= S) continue;
-      const F w2 = wfun(g.wk, ob) * wfun(g.wk, oc);
-      const F rb = (F)ib - pivot<F>(g, b), rc = (F)ic - pivot<F>(g, c);
-      const int m2 = ib * sb + ic * sc;
-      if (D == 2) {
-        const F wkap = w2 * kref[m2];
-        o.phi += w2;
-        o.kap += wkap;
-        o.wr[b] += w2 * rb;
-        o.wr[c] += w2 * rc;
-        o.kr[b] += wkap * rb;
-        o.kr[c] += wkap * rc;
-      } else {
-        for (int ia = ia0; ia <= ia1; ++ia) {
-          const F oa = (F)ia - xia;
-          if (fabs(oa) >= S) continue;
-          const F W = w2 * wfun(g.wk, oa);
-          const F wkap = W * kref[m2 + ia * sa];
-          const F ra = (F)ia - pivot<F>(g, ax);
-          o.phi += W;
-          o.kap += wkap;
-          o.wr[b] += W * rb;
-          o.wr[c] += W * rc;
-          o.wr[ax] += W * ra;
-          o.kr[b] += wkap * rb;
-          o.kr[c] += wkap * rc;
-          o.kr[ax] += wkap * ra;
-        }
-      }
-    }
-  }
+// Design-domain test on the doubled offset 2 r_m = 2 i - (nd - 1), exact in integers:
+// 4 |r_m|^2 <= rad4.
+__device__ __forceinline__ int dsq(int i, int nd) {
+  const int e = 2 * i - (nd - 1);
+  return e * e;
 }
 
-// The same gather split over LANES consecutive threads of a warp: lane j takes candidate rows
+// Gather (Eqs. kappa_mapping, us_mapping) for the cell at d = x_n - x^G under rotation (cs, sn)
+// about AX, split over LANES consecutive threads of a warp. Candidates: the design points of the
+// design domain whose rotated position lies in the axis-aligned support square of the cell; in the
+// design frame they lie within s (|cos| + |sin|) of the cell's image. Lane j takes candidate rows
 // ib0 + j, ib0 + j + LANES, ...; the sums are combined with shuffles so every lane ends with the
 // cell's totals.
 template <typename F, int D, int AX, int LANES>
@@ -384,11 +322,14 @@ __device__ __forceinline__ void gather_lanes(const Geo& g, const F* __restrict__
     ehi = fmin(ehi, F(1e6));
     const int jc0 = max(ic0, (int)ceil(xic + elo - pad)), jc1 = min(ic1, (int)floor(xic + ehi + pad));
     const F rb = (F)ib - pivot<F>(g, b);
+    const int qb = dsq(ib, g.nd[b]);
     for (int ic = jc0; ic <= jc1; ++ic) {
       const F ec = (F)ic - xic;
       const F ob = cs * eb - sn * ec;
       const F oc = sn * eb + cs * ec;
       if (fabs(ob) >= S || fabs(oc) >= S) continue;
+      const int qbc = qb + dsq(ic, g.nd[c]);
+      if (D == 2 && qbc > g.rad4) continue;
       const F w2 = wfun(g.wk, ob) * wfun(g.wk, oc);
       const F rc = (F)ic - pivot<F>(g, c);
       const int m2 = ib * sb + ic * sc;
@@ -403,7 +344,7 @@ __device__ __forceinline__ void gather_lanes(const Geo& g, const F* __restrict__
       } else {
         for (int ia = ia0; ia <= ia1; ++ia) {
           const F oa = (F)ia - xia;
-          if (fabs(oa) >= S) continue;
+          if (fabs(oa) >= S || qbc + dsq(ia, g.nd[ax]) > g.rad4) continue;
           const F W = w2 * wfun(g.wk, oa);
           const F wkap = W * kref[m2 + ia * sa];
           const F ra = (F)ia - pivot<F>(g, ax);
@@ -430,6 +371,107 @@ __device__ __forceinline__ void gather_lanes(const Geo& g, const F* __restrict__
       o.kr[a] += __shfl_xor_sync(0xffffffffu, o.kr[a], off);
     }
   }
+}
+
+// Gather with free rotation: R (row-major, FP32 or FP64 like the cell) maps design offsets to the
+// world. The support cube |x^ref_m - x_n|_a < s of the cell, pulled back to the design frame, is the
+// cube R^T [-s, s]^3 around the cell's image xi = R^T d + xi^G; its bounding box has half extents
+// s sum_a |R_ab|. Rows (iy, iz) of that box are split over the lanes; within a row the three world
+// offsets are linear in ix, which bounds ix to the interval where all three lie in (-s, s)
+// (widened slightly; the exact test decides).
+template <typename F, int LANES>
+__device__ __forceinline__ void gather_free_lanes(const Geo& g, const F* __restrict__ kref, const F (&d)[3],
+                                                  const F (&R)[9], int lane, bool active, Acc<F>& o) {
+  const F S = (F)g.s;
+  F xi[3];
+  int lo[3], hi[3];
+#pragma unroll
+  for (int b = 0; b < 3; ++b) {
+    xi[b] = R[b] * d[0] + R[3 + b] * d[1] + R[6 + b] * d[2] + pivot<F>(g, b);
+    const F h = S * (fabs(R[b]) + fabs(R[3 + b]) + fabs(R[6 + b]));
+    lo[b] = max(0, (int)ceil(xi[b] - h));
+    hi[b] = min(g.nd[b] - 1, (int)floor(xi[b] + h));
+  }
+  o.phi = o.kap = F(0);
+#pragma unroll
+  for (int a = 0; a < 3; ++a) o.wr[a] = o.kr[a] = F(0);
+  const int nyr = hi[1] - lo[1] + 1, nzr = hi[2] - lo[2] + 1;
+  const int nrows = (active && nyr > 0 && nzr > 0) ? nyr * nzr : 0;
+  const F tiny = F(1e-6), pad = F(1e-3);
+  F inv[3];
+#pragma unroll
+  for (int a = 0; a < 3; ++a) inv[a] = fabs(R[3 * a]) > tiny ? F(1) / R[3 * a] : F(0);
+  const int sy = g.nd[0], sz = g.nd[0] * g.nd[1];
+  for (int q = lane; q < nrows; q += LANES) {
+    const int iy = lo[1] + q % nyr, iz = lo[2] + q / nyr;
+    const int qyz = dsq(iy, g.nd[1]) + dsq(iz, g.nd[2]);
+    if (qyz > g.rad4) continue;
+    const F ey = (F)iy - xi[1], ez = (F)iz - xi[2];
+    F cw[3];  // world offset of the row at ix = xi_x
+    F elo = -F(1e30), ehi = F(1e30);
+    bool empty = false;
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+      cw[a] = R[3 * a + 1] * ey + R[3 * a + 2] * ez;
+      if (inv[a] != F(0)) {
+        const F e1 = (-S - cw[a]) * inv[a], e2 = (S - cw[a]) * inv[a];
+        elo = fmax(elo, fmin(e1, e2));
+        ehi = fmin(ehi, fmax(e1, e2));
+      } else if (fabs(cw[a]) >= S + pad) {
+        empty = true;
+      }
+    }
+    if (empty) continue;
+    elo = fmax(elo, F(-1e6));
+    ehi = fmin(ehi, F(1e6));
+    const int jx0 = max(lo[0], (int)ceil(xi[0] + elo - pad)), jx1 = min(hi[0], (int)floor(xi[0] + ehi + pad));
+    const F ry = (F)iy - pivot<F>(g, 1), rz = (F)iz - pivot<F>(g, 2);
+    const int mrow = iy * sy + iz * sz;
+    for (int ix = jx0; ix <= jx1; ++ix) {
+      const F ex = (F)ix - xi[0];
+      const F o0 = R[0] * ex + cw[0], o1 = R[3] * ex + cw[1], o2 = R[6] * ex + cw[2];
+      if (fabs(o0) >= S || fabs(o1) >= S || fabs(o2) >= S || qyz + dsq(ix, g.nd[0]) > g.rad4) continue;
+      const F W = wfun(g.wk, o0) * wfun(g.wk, o1) * wfun(g.wk, o2);
+      const F wkap = W * kref[mrow + ix];
+      const F rx = (F)ix - pivot<F>(g, 0);
+      o.phi += W;
+      o.kap += wkap;
+      o.wr[0] += W * rx;
+      o.wr[1] += W * ry;
+      o.wr[2] += W * rz;
+      o.kr[0] += wkap * rx;
+      o.kr[1] += wkap * ry;
+      o.kr[2] += wkap * rz;
+    }
+  }
+#pragma unroll
+  for (int off = 1; off < LANES; off <<= 1) {
+    o.phi += __shfl_xor_sync(0xffffffffu, o.phi, off);
+    o.kap += __shfl_xor_sync(0xffffffffu, o.kap, off);
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+      o.wr[a] += __shfl_xor_sync(0xffffffffu, o.wr[a], off);
+      o.kr[a] += __shfl_xor_sync(0xffffffffu, o.kr[a], off);
+    }
+  }
+}
+
+// Small 3-vector / 3x3 helpers (row-major matrices).
+template <typename F>
+__device__ __forceinline__ void cross3(const F* a, const F* b, F* out) {
+  out[0] = a[1] * b[2] - a[2] * b[1];
+  out[1] = a[2] * b[0] - a[0] * b[2];
+  out[2] = a[0] * b[1] - a[1] * b[0];
+}
+template <typename F>
+__device__ __forceinline__ void matvec3(const F* M, const F* v, F* out) {
+#pragma unroll
+  for (int i = 0; i < 3; ++i) out[i] = M[3 * i] * v[0] + M[3 * i + 1] * v[1] + M[3 * i + 2] * v[2];
+}
+template <typename F>
+__device__ __forceinline__ void matTvec3(const F* M, const F* v, F* out) {
+#pragma unroll
+  for (int j = 0; j < 3; ++j) out[j] = M[j] * v[0] + M[3 + j] * v[1] + M[6 + j] * v[2];
 }
 
 // R r and R' r = d(R r)/d theta for the rotation about AX.
@@ -682,7 +724,9 @@ __device__ __forceinline__ void rotate_angle(const Dof& s0, double dth, double* 
 template <int D>
 __device__ __forceinline__ void eom_update(const Geo& g, const Dof& s0, const double* F, double T, Dof* out) {
 #pragma unroll
-  for (int a = 0; a < 8; ++a) out->s[a] = s0.s[a];
+  for (int a = 0; a < kNdofAxis; ++a) out->s[a] = s0.s[a];
+#pragma unroll
+  for (int a = kNdofAxis; a < kNdofFree; ++a) out->s[a] = 0.0;
 #pragma unroll
   for (int a = 0; a < D; ++a) {
     if (!(g.dof_mask & (1 << a))) continue;
@@ -694,12 +738,12 @@ __device__ __forceinline__ void eom_update(const Geo& g, const Dof& s0, const do
     out->s[6] = s0.s[6] + out->s[7];
   }
   rotate_angle(s0, out->s[6] - s0.s[6], &out->cs, &out->sn);
-  dof_views(out);
+  dof_views(out, false);
 }
 
-// Reverse of eom_update: from dJ/ds^(k) give dJ/dF, dJ/dT and add the direct part to dJ/ds(t-1).
-__device__ __forceinline__ void eom_reverse(const Geo& g, const double* lam_sk, double* lamF, double* lamT,
-                                            double* lam_prev) {
+// Reverse of the translational EOM: from dJ/ds^(k) give dJ/dF and add the direct part to dJ/ds(t-1).
+__device__ __forceinline__ void eom_reverse_translation(const Geo& g, const double* lam_sk, double* lamF,
+                                                        double* lam_prev) {
 #pragma unroll
   for (int a = 0; a < 3; ++a) {
     const bool fr = (a < g.dim) && (g.dof_mask & (1 << a));
@@ -714,15 +758,173 @@ __device__ __forceinline__ void eom_reverse(const Geo& g, const double* lam_sk, 
       lam_prev[3 + a] += lam_sk[3 + a];
     }
   }
+}
+
+// Reverse of eom_update: from dJ/ds^(k) give dJ/dF, dJ/dT (about the axis, in lamT[0]) and add the
+// direct part to dJ/ds(t-1).
+__device__ __forceinline__ void eom_reverse(const Geo& g, const double* lam_sk, double* lamF, double* lamT,
+                                            double* lam_prev) {
+  eom_reverse_translation(g, lam_sk, lamF, lam_prev);
+  lamT[1] = lamT[2] = 0.0;
   if (g.dof_mask & DOF_ROT) {
     const double lom = lam_sk[7] + lam_sk[6];
-    *lamT = lom * g.inv_inertia;
+    lamT[0] = lom * g.inv_inertia;
     lam_prev[6] += lam_sk[6];
     lam_prev[7] += lom;
   } else {
-    *lamT = 0.0;
+    lamT[0] = 0.0;
     lam_prev[6] += lam_sk[6];
     lam_prev[7] += lam_sk[7];
+  }
+}
+
+// Rodrigues' formula exp([w]x) = I + a [w]x + b [w]x^2 with a = sin t / t, b = (1 - cos t) / t^2,
+// t = |w|, and the derivatives da/dx, db/dx with respect to x = t^2. For t <= 1/4 from the power
+// series in x (a = sum (-x)^k / (2k+1)!, b = sum (-x)^k / (2k+2)!, terms to x^8, remainder below
+// 1e-26); otherwise from the closed forms.
+__device__ __forceinline__ void rod_coeffs(double x, double* a, double* b, double* da, double* db) {
+  if (x <= 1.0 / 16.0) {
+    // (-1)^k / (2k+1)! and (-1)^k / (2k+2)!, k = 0..8
+    constexpr double ca[9] = {1.0, -1.0 / 6.0, 1.0 / 120.0, -1.0 / 5040.0, 1.0 / 362880.0, -1.0 / 39916800.0,
+                              1.0 / 6227020800.0, -1.0 / 1307674368000.0, 1.0 / 355687428096000.0};
+    constexpr double cb[9] = {1.0 / 2.0, -1.0 / 24.0, 1.0 / 720.0, -1.0 / 40320.0, 1.0 / 3628800.0,
+                              -1.0 / 479001600.0, 1.0 / 87178291200.0, -1.0 / 20922789888000.0,
+                              1.0 / 6402373705728000.0};
+    double pa = ca[8], pb = cb[8], qa = 8.0 * ca[8], qb = 8.0 * cb[8];
+#pragma unroll
+    for (int k = 7; k >= 1; --k) {
+      pa = fma(pa, x, ca[k]);
+      pb = fma(pb, x, cb[k]);
+      qa = fma(qa, x, k * ca[k]);
+      qb = fma(qb, x, k * cb[k]);
+    }
+    *a = fma(pa, x, ca[0]);
+    *b = fma(pb, x, cb[0]);
+    *da = qa;
+    *db = qb;
+  } else {
+    const double t = sqrt(x);
+    double sn, cs;
+    sincos(t, &sn, &cs);
+    *a = sn / t;
+    *b = (1.0 - cs) / x;
+    *da = (t * cs - sn) / (2.0 * x * t);
+    *db = (t * sn - 2.0 * (1.0 - cs)) / (2.0 * x * x);
+  }
+}
+
+__device__ __forceinline__ void rod_matrix(const double* w, double a, double b, double* Q) {
+  const double K[9] = {0.0, -w[2], w[1], w[2], 0.0, -w[0], -w[1], w[0], 0.0};
+  const double x = w[0] * w[0] + w[1] * w[1] + w[2] * w[2];
+#pragma unroll
+  for (int i = 0; i < 3; ++i)
+#pragma unroll
+    for (int j = 0; j < 3; ++j)  // [w]x^2 = w w^T - x I
+      Q[3 * i + j] = (i == j ? 1.0 : 0.0) + a * K[3 * i + j] + b * (w[i] * w[j] - (i == j ? x : 0.0));
+}
+
+// Explicit Euler EOM with free rotation (velocity first): u^G, x^G as eom_update;
+// h = h(t-1) + T, omega = R0 I_b^-1 R0^T h, R = exp([omega]x) R0 with R0 = R(t-1).
+__device__ __forceinline__ void eom_update_free(const Geo& g, const Dof& s0, const double* F, const double* T,
+                                                Dof* out) {
+#pragma unroll
+  for (int a = 0; a < kNdofFree; ++a) out->s[a] = s0.s[a];
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    if (!(g.dof_mask & (1 << a))) continue;
+    out->s[3 + a] = s0.s[3 + a] + F[a] * g.inv_mass;
+    out->s[a] = s0.s[a] + out->s[3 + a];
+  }
+  if (g.dof_mask & DOF_ROT) {
+    const double* R0 = s0.s + S_R;
+    double h[3], v1[3], v2[3], w[3], Q[9], a, b, da, db;
+#pragma unroll
+    for (int i = 0; i < 3; ++i) h[i] = s0.s[S_H + i] + T[i];
+    matTvec3(R0, h, v1);
+    matvec3(g.Jinv, v1, v2);
+    matvec3(R0, v2, w);
+    rod_coeffs(w[0] * w[0] + w[1] * w[1] + w[2] * w[2], &a, &b, &da, &db);
+    rod_matrix(w, a, b, Q);
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+      out->s[S_H + i] = h[i];
+      out->s[S_OM + i] = w[i];
+#pragma unroll
+      for (int j = 0; j < 3; ++j)
+        out->s[S_R + 3 * i + j] = Q[3 * i] * R0[j] + Q[3 * i + 1] * R0[3 + j] + Q[3 * i + 2] * R0[6 + j];
+    }
+  }
+  out->cs = 1.0;
+  out->sn = 0.0;
+  dof_views(out, true);
+}
+
+// Reverse of eom_update_free from s0 = s(t-1) and the iterate sk = s^(k) it produced: dJ/dF,
+// dJ/dT (vector) and the direct part of dJ/ds(t-1). With G = (dJ/dR) R0^T the rotation term
+// phi(w) = <G, exp([w]x)> has gradient
+//   2 a'(x) (w.v) w + a v + 2 b'(x) (w^T G w - x tr G) w + b ((G + G^T) w - 2 tr G w),
+// v = (G21 - G12, G02 - G20, G10 - G01), x = |w|^2 (a', b' with respect to x).
+__device__ __forceinline__ void eom_reverse_free(const Geo& g, const Dof& s0, const Dof& sk, const double* lam_sk,
+                                                 double* lamF, double* lamT, double* lam_prev) {
+  eom_reverse_translation(g, lam_sk, lamF, lam_prev);
+  if (!(g.dof_mask & DOF_ROT)) {
+#pragma unroll
+    for (int a = S_H; a < kNdofFree; ++a) lam_prev[a] += lam_sk[a];
+    lamT[0] = lamT[1] = lamT[2] = 0.0;
+    return;
+  }
+  const double* R0 = s0.s + S_R;
+  const double* h = sk.s + S_H;
+  const double* w = sk.s + S_OM;
+  const double* LR = lam_sk + S_R;
+  const double x = w[0] * w[0] + w[1] * w[1] + w[2] * w[2];
+  double a, b, da, db, Q[9], G[9];
+  rod_coeffs(x, &a, &b, &da, &db);
+  rod_matrix(w, a, b, Q);
+#pragma unroll
+  for (int i = 0; i < 3; ++i)
+#pragma unroll
+    for (int j = 0; j < 3; ++j) {
+      // R = Q R0:  dJ/dR0 += Q^T LR,  G = LR R0^T
+      lam_prev[S_R + 3 * i + j] += Q[i] * LR[j] + Q[3 + i] * LR[3 + j] + Q[6 + i] * LR[6 + j];
+      G[3 * i + j] = LR[3 * i] * R0[3 * j] + LR[3 * i + 1] * R0[3 * j + 1] + LR[3 * i + 2] * R0[3 * j + 2];
+    }
+  const double v[3] = {G[7] - G[5], G[2] - G[6], G[3] - G[1]};
+  const double trG = G[0] + G[4] + G[8];
+  double Gw[3], GTw[3];
+  matvec3(G, w, Gw);
+  matTvec3(G, w, GTw);
+  const double wv = w[0] * v[0] + w[1] * v[1] + w[2] * v[2];
+  const double wGw = w[0] * Gw[0] + w[1] * Gw[1] + w[2] * Gw[2];
+  const double c1 = 2.0 * da * wv + 2.0 * db * (wGw - x * trG) - 2.0 * b * trG;
+  double lw[3];
+#pragma unroll
+  for (int i = 0; i < 3; ++i) lw[i] = lam_sk[S_OM + i] + c1 * w[i] + a * v[i] + b * (Gw[i] + GTw[i]);
+  // w = R0 I_b^-1 R0^T h:  dJ/dh += R0 I_b^-1 R0^T lw,  dJ/dR0 += (lw h^T + h lw^T) R0 I_b^-1
+  double p1[3], p2[3], lh[3], RJ[9];
+  matTvec3(R0, lw, p1);
+  matvec3(g.Jinv, p1, p2);
+  matvec3(R0, p2, lh);
+#pragma unroll
+  for (int i = 0; i < 3; ++i)
+#pragma unroll
+    for (int j = 0; j < 3; ++j)
+      RJ[3 * i + j] = R0[3 * i] * g.Jinv[j] + R0[3 * i + 1] * g.Jinv[3 + j] + R0[3 * i + 2] * g.Jinv[6 + j];
+#pragma unroll
+  for (int i = 0; i < 3; ++i)
+#pragma unroll
+    for (int j = 0; j < 3; ++j) {
+      double acc = 0.0;
+#pragma unroll
+      for (int l = 0; l < 3; ++l) acc += (lw[i] * h[l] + h[i] * lw[l]) * RJ[3 * l + j];
+      lam_prev[S_R + 3 * i + j] += acc;
+    }
+  // h = h(t-1) + T
+#pragma unroll
+  for (int i = 0; i < 3; ++i) {
+    const double lhi = lam_sk[S_H + i] + lh[i];
+    lamT[i] = lhi;
+    lam_prev[S_H + i] += lhi;
   }
 }
 

@@ -96,8 +96,8 @@ void launch_init_forward(const Geo& g, const Slots<T>& S, const double* p0, cons
 void launch_set_step(Ctrl* ctrl, int t0, int base, cudaStream_t st);
 
 // Adjoint initialisation: dJ/ds(N_t) = seed * w, EOM reverse of iteration K, zero dJ/dkappa^ref.
-void launch_adj_init(const Geo& g, Ctrl* ctrl, const double* objw, double seed, double* dkref, int nd,
-                     cudaStream_t st);
+void launch_adj_init(const Geo& g, Ctrl* ctrl, const Dof* it, int nt, const double* objw, double seed, double* dkref,
+                     int nd, cudaStream_t st);
 
 // dJ/dgamma = dJ/dkappa^ref * dkappa^ref/dgamma.
 void launch_sensitivity(const Geo& g, const double* gamma, const double* dkref, double kappa_max, double q,

@@ -17,6 +17,7 @@
 //     part that must start at zero, and calls that overlap on the GPU (two streams, two host
 //     threads) race on it -- serialise them;
 //   - sizes beyond the array's limits are rejected with LKS_ERR_BUDGET.
+#include <climits>
 #include <cmath>
 #include <cstring>
 #include <mutex>
@@ -34,14 +35,14 @@ constexpr int kMaxBlocks = 4096;   // CTAs of one reduction (partials)
 constexpr int kMaxDevices = 64;
 
 // Byte layout of the scratch array (each part 256-byte aligned).
+constexpr size_t align256(size_t b) { return ((b + 255) / 256) * 256; }
 constexpr size_t kOffCtrl = 0;
-constexpr size_t kOffMom = 256;
-constexpr size_t kOffIt = 512;
-constexpr size_t kItBytes = ((sizeof(Dof) * (kMaxItr + 2) + 255) / 256) * 256;
+constexpr size_t kOffMom = kOffCtrl + align256(sizeof(Ctrl));
+constexpr size_t kOffIt = kOffMom + align256(sizeof(Moments));
+constexpr size_t kItBytes = align256(sizeof(Dof) * (kMaxItr + 2));
 constexpr size_t kOffKref = kOffIt + kItBytes;
 constexpr size_t kOffPartials = kOffKref + sizeof(double) * kMaxDesign;
 constexpr size_t kScratchBytes = kOffPartials + sizeof(double) * 8 * kMaxBlocks;
-static_assert(sizeof(Ctrl) <= 256 && sizeof(Moments) <= 256, "control block layout");
 
 static __device__ __align__(256) unsigned char g_noalloc_scratch[kScratchBytes];
 
@@ -81,6 +82,7 @@ int make_geo(const lks_problem* P, Geo* g) {
   if (!(P->nu > 0.0)) return LKS_ERR_UNSTABLE;
   if (P->n_itr < 1 || !(P->mass > 0.0) || !(P->inertia > 0.0)) return LKS_ERR_ARG;
   if (P->weight_kind != LKS_W_COS4 && P->weight_kind != LKS_W_BILINEAR) return LKS_ERR_ARG;
+  if (P->design_radius != 0.0) return LKS_ERR_UNSUPPORTED;
   std::memset(g, 0, sizeof(Geo));
   g->dim = 2;
   g->n[0] = P->nx;
@@ -101,6 +103,8 @@ int make_geo(const lks_problem* P, Geo* g) {
   g->ax = 2;
   g->axb = 0;
   g->axc = 1;
+  g->ns = kNdofAxis;
+  g->rad4 = INT_MAX;  // the whole design grid
   g->dof_mask = (int)P->dof_mask;
   g->wk = P->weight_kind;
   g->s = (P->weight_kind == LKS_W_BILINEAR) ? 1 : 2;
@@ -153,10 +157,10 @@ extern "C" int lks_step_noalloc(const lks_problem* problem, const double* gamma_
   // last-block counters and status must start at zero
   if (cudaMemsetAsync(ctrl, 0, sizeof(Ctrl), st) != cudaSuccess) return LKS_ERR_CUDA;
   Dof s0;
-  for (int a = 0; a < 8; ++a) s0.s[a] = s_host[a];
+  for (int a = 0; a < kNdofFree; ++a) s0.s[a] = (a < kNdofAxis) ? s_host[a] : 0.0;
   s0.cs = std::cos(s0.s[6]);
   s0.sn = std::sin(s0.s[6]);
-  dof_views(&s0);
+  dof_views(&s0, false);
   // The device sees step 1 of a two-slot ring whose base selects the parity: slot (t-1) mod 2 is
   // read and slot t mod 2 written.
   const int parity = (t - 1) & 1;

@@ -19,6 +19,8 @@ LKS_D2Q9, LKS_D3Q15 = 9, 15
 LKS_FP32, LKS_FP64 = 32, 64
 LKS_CKPT_STORE_ALL, LKS_CKPT_UNIFORM, LKS_CKPT_BINOMIAL = 0, 1, 2
 LKS_CKPT_NATIVE, LKS_CKPT_BF16, LKS_CKPT_FP16 = 0, 1, 2
+LKS_ROT_FREE = -1
+LKS_NDOF_AXIS, LKS_NDOF_FREE, LKS_MAX_DOF = 8, 21, 21
 STATUS = {0: "LKS_OK", 1: "LKS_ERR_ARG", 2: "LKS_ERR_OOM", 3: "LKS_ERR_BUDGET", 4: "LKS_ERR_UNSTABLE",
           5: "LKS_ERR_BODY_OUTSIDE", 6: "LKS_ERR_NONFINITE", 7: "LKS_ERR_ORDER", 8: "LKS_ERR_CUDA",
           9: "LKS_ERR_UNSUPPORTED"}
@@ -35,6 +37,8 @@ class lks_problem(ctypes.Structure):  # noqa: N801  (mirrors the C struct name)
         ("dof_mask", ctypes.c_uint),
         ("mass", ctypes.c_double),
         ("inertia", ctypes.c_double),
+        ("inertia_tensor", ctypes.c_double * 9),
+        ("design_radius", ctypes.c_double),
         ("nu", ctypes.c_double),
         ("u_in", ctypes.c_double),
         ("dp", ctypes.c_double),
@@ -44,7 +48,7 @@ class lks_problem(ctypes.Structure):  # noqa: N801  (mirrors the C struct name)
         ("weight_kind", ctypes.c_int),
         ("n_steps", ctypes.c_int),
         ("n_itr", ctypes.c_int),
-        ("obj_weights", ctypes.c_double * 8),
+        ("obj_weights", ctypes.c_double * LKS_MAX_DOF),
         ("field_precision", ctypes.c_int),
         ("ckpt_policy", ctypes.c_int),
         ("ckpt_every", ctypes.c_int),
@@ -99,6 +103,11 @@ def load() -> ctypes.CDLL:
     L.lks_status_string.restype = ctypes.c_char_p
     L.lks_last_cuda_error.argtypes = []
     L.lks_step_noalloc.argtypes = [ctypes.POINTER(lks_problem), vp, vp, ctypes.c_int, dp, vp]
+    L.lks_dof_count.argtypes = [ctypes.POINTER(lks_problem)]
+    L.lks_problem_size.argtypes = []
+    L.lks_problem_size.restype = ctypes.c_size_t
+    if L.lks_problem_size() != ctypes.sizeof(lks_problem):
+        raise RuntimeError("lks_problem layout of the binding does not match the library")
     _lib = L
     return L
 
@@ -130,11 +139,14 @@ def problem_struct(P, precision: Optional[int] = None, ckpt_policy: Optional[int
     s.rot_axis = P.rot_axis
     s.dof_mask = P.dof_mask
     s.mass, s.inertia, s.nu, s.u_in, s.dp = P.mass, P.inertia, P.nu, P.u_in, P.dp
+    for a in range(9):
+        s.inertia_tensor[a] = P.inertia_tensor[a]
+    s.design_radius = P.design_radius
     s.kappa_max, s.q = P.kappa_max, P.q
     s.weight_kind = P.weight_kind
     s.n_steps = P.n_steps if n_steps is None else n_steps
     s.n_itr = P.n_itr
-    for a in range(8):
+    for a in range(len(P.obj_weights)):
         s.obj_weights[a] = P.obj_weights[a]
     s.field_precision = P.field_precision if precision is None else precision
     s.ckpt_policy = P.ckpt_policy if ckpt_policy is None else ckpt_policy
@@ -182,8 +194,12 @@ def lks_gradient_host(h, gamma: np.ndarray, out: np.ndarray, stream: int = 0) ->
     return J.value
 
 
-def lks_get_dof_history(h, n_steps: int) -> np.ndarray:
-    buf = np.zeros((n_steps + 1, 8))
+def lks_dof_count(problem: lks_problem) -> int:
+    return int(load().lks_dof_count(ctypes.byref(problem)))
+
+
+def lks_get_dof_history(h, n_steps: int, n_dof: int = LKS_NDOF_AXIS) -> np.ndarray:
+    buf = np.zeros((n_steps + 1, n_dof))
     _check(load().lks_get_dof_history(h, _dptr(buf), buf.size), "lks_get_dof_history")
     return buf
 
@@ -195,10 +211,10 @@ def lks_get_state(h, n_cells: int, dim: int):
     return p, u
 
 
-def lks_get_initial_adjoint(h, n_cells: int, dim: int):
+def lks_get_initial_adjoint(h, n_cells: int, dim: int, n_dof: int = LKS_NDOF_AXIS):
     lp = np.zeros(n_cells)
     lu = np.zeros((dim, n_cells))
-    ls = np.zeros(8)
+    ls = np.zeros(n_dof)
     _check(load().lks_get_initial_adjoint(h, _dptr(lp), _dptr(lu), _dptr(ls)), "lks_get_initial_adjoint")
     return lp, lu, ls
 
@@ -281,14 +297,18 @@ class Solver:
         J = lks_gradient_host(self.handle, np.ascontiguousarray(gamma, dtype=np.float64), out, st.cuda_stream)
         return J, out
 
+    @property
+    def n_dof(self) -> int:
+        return lks_dof_count(self.struct)
+
     def dof_history(self) -> np.ndarray:
-        return lks_get_dof_history(self.handle, self.n_steps)
+        return lks_get_dof_history(self.handle, self.n_steps, self.n_dof)
 
     def state(self):
         return lks_get_state(self.handle, self.P.n_cells, self.P.dim)
 
     def initial_adjoint(self):
-        return lks_get_initial_adjoint(self.handle, self.P.n_cells, self.P.dim)
+        return lks_get_initial_adjoint(self.handle, self.P.n_cells, self.P.dim, self.n_dof)
 
     def launches(self) -> int:
         return lks_launch_count(self.handle)
