@@ -200,36 +200,52 @@ def stencil_roofline(dev, peak: float, dim: int, n: tuple, name: str, n_steps: i
     return out
 
 
-def gradient_throughput(dev, flush, index: int) -> dict:
-    """Whole-gradient throughput of another workload (one warm-up, one timed gradient)."""
+def gradient_throughput(dev, flush, index: int, n_steps: int = 0, plain_fp64: bool = False) -> dict:
+    """Whole-gradient throughput of another workload (one warm-up, one timed gradient), optionally
+    truncated to n_steps time steps and compared with the plain FP64 form (every state stored)."""
     import torch
+    from paper_2601_18272_gb300 import lks
     from paper_2601_18272_gb300.lks import Solver
-    from workloads import config
+    from workloads import CKPT_STORE_ALL, config
     P, g = config(index)
-    S = Solver(P)
+    if n_steps:
+        P = P.replace(n_steps=n_steps)
     gamma = torch.tensor(g, dtype=torch.float64, device=dev)
     grad = torch.empty_like(gamma)
     stream = torch.cuda.current_stream(dev)
 
-    def run():
-        S.forward(gamma)
-        S.adjoint(1.0)
-        S.sensitivity(grad)
+    def timed(S):
+        def run():
+            S.forward(gamma)
+            S.adjoint(1.0)
+            S.sensitivity(grad)
+        run()
+        torch.cuda.synchronize()
+        flush.zero_()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        run()
+        e1.record(stream)
+        e1.synchronize()
+        return e0.elapsed_time(e1), run
 
-    run()
-    torch.cuda.synchronize()
-    flush.zero_()
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    e0.record(stream)
-    run()
-    e1.record(stream)
-    e1.synchronize()
-    ms = e0.elapsed_time(e1)
+    S = Solver(P)
+    ms, run = timed(S)
     fams = _family_times(S, run)
+    g32 = grad.clone()
+    out = {"workload": P.name, "value": P.n_cells * P.n_steps / (ms / 1000.0), "unit": UNIT, "ms_per_gradient": ms,
+           "n_steps": P.n_steps, "dtype": "f32", "workspace_gb": lks.lks_workspace_bytes(S.handle) / 1e9,
+           "kernel_ms_per_gradient": {k: round(v[0], 3) for k, v in fams.items()}}
     S.close()
-    return {"workload": P.name, "value": P.n_cells * P.n_steps / (ms / 1000.0), "unit": UNIT, "ms_per_gradient": ms,
-            "n_steps": P.n_steps, "dtype": "f32",
-            "kernel_ms_per_gradient": {k: round(v[0], 3) for k, v in fams.items()}}
+    if plain_fp64:
+        S = Solver(P, precision=64, ckpt_policy=CKPT_STORE_ALL)
+        ms64, _ = timed(S)
+        out["plain_fp64_store_all"] = {"value": P.n_cells * P.n_steps / (ms64 / 1000.0), "unit": UNIT,
+                                       "ms_per_gradient": ms64,
+                                       "workspace_gb": lks.lks_workspace_bytes(S.handle) / 1e9}
+        out["dJdgamma_rel_l2_vs_fp64"] = float(torch.linalg.norm(g32 - grad) / torch.linalg.norm(grad))
+        S.close()
+    return out
 
 
 def ckpt_precision_study(dev, n_steps: int = 400) -> dict:
@@ -477,6 +493,7 @@ def main():
         line["stencil_roofline_2d"] = stencil_roofline(dev, peak, 2, (8192, 4096), "fluid2d_8192x4096")
         line["stencil_roofline_3d"] = stencil_roofline(dev, peak, 3, (512, 256, 256), "fluid3d_512x256x256")
         line["body3d"] = gradient_throughput(dev, flush, 4)
+        line["turbine3d_6dof"] = gradient_throughput(dev, flush, 5, n_steps=200, plain_fp64=True)
         line["ckpt_precision"] = ckpt_precision_study(dev)
         line["cpu_baseline"] = cpu_baseline(args.cpu_sample_steps)
     solver.close()
