@@ -20,7 +20,7 @@ inline void launch(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t smem,
 }
 
 constexpr int kTileX = 32;  // 3D stencil column width (cells); boundary pairs must not straddle columns
-constexpr int kTileY3 = 8;  // 3D stencil column height (the column marches over a chunk of z planes)
+constexpr int kTileY3 = 16;  // 3D stencil column height (the column marches over a chunk of z planes)
 constexpr int kStripWarps = 4;  // 2D stencil: warps per CTA, each streaming its own strip of rows
 
 // 2D stencil strips: W output columns per warp (<= 28), ntx column tiles, nstrip row strips.

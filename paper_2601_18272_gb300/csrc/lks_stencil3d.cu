@@ -11,12 +11,15 @@
 // x planes (all rows). Gradient ghosts: open planes copy the boundary node, walls reflect u with a
 // sign flip.
 //
-// GB300 form: one CTA per 32 x 8 column of cells marches over a chunk of z planes. Shared memory
-// holds a ring of three input planes (halo 2 in x and y) and one plane of the 15 f_i^eq values
-// (halo 1); each plane's f values are scattered into three register accumulators (outputs at
-// z - 1, z, z + 1), so every input is read from L2/HBM about (1 + 4/chunk) times per step.
-// A z-wall plane is completed from its neighbour plane inside the same chunk (chunks hold at
-// least two planes).
+// GB300 form: one CTA of 512 threads per 32 x 16 column of cells marches over a chunk of z planes.
+// Shared memory holds a ring of three input planes (halo 2 in x and y) and one plane of the 15
+// f_i^eq values (halo 1); each plane's f values are scattered into three register accumulators
+// (outputs at z - 1, z, z + 1). Each thread resolves its halo nodes' sources (the ghost rule along
+// x and y) once for the whole march, and the next plane's global loads are issued into registers
+// before the current plane is worked on, so their latency hides behind the f^eq arithmetic. Tiles
+// whose outputs need no boundary phase write them straight from the accumulators. The number of z
+// chunks is chosen to fill whole waves of resident CTAs. A z-wall plane is completed from its
+// neighbour plane inside the same chunk (chunks hold at least four planes).
 //
 // Algorithmic traffic per cell: read p, u (4 values), write p*, u* (4 values): 32 B in FP32.
 // Transpose: read the adjoint (4 values) and u(t-1) (3 values), write 4 values: 44 B in FP32.
@@ -61,79 +64,122 @@ __device__ __forceinline__ constexpr int csx(int k) { return (k & 1) ? -1 : 1; }
 __device__ __forceinline__ constexpr int csy(int k) { return (k & 2) ? -1 : 1; }
 __device__ __forceinline__ constexpr int csz(int k) { return (k & 4) ? -1 : 1; }
 
-template <typename T>
-__device__ __forceinline__ void load_state_plane(const Geo& g, const T* __restrict__ src, T (*dst)[RY][RX], int x0,
-                                                 int y0, int zr) {
-  const long long N = g.N;
-  const int nx = g.n[0], ny = g.n[1], nz = g.n[2];
-  for (int q = threadIdx.x; q < RPL; q += NT) {
-    const int li = q % RX, lj = q / RX;
-    int gx = x0 - 2 + li, gy = y0 - 2 + lj, gz = zr, sgn = 1;
-    T v[4] = {T(0), T(0), T(0), T(0)};
-    if (ghost_axis(g.bc[0], nx, &gx, &sgn) && ghost_axis(g.bc[1], ny, &gy, &sgn) &&
-        ghost_axis(g.bc[2], nz, &gz, &sgn)) {
-      const long long n = gx + (long long)nx * (gy + (long long)ny * gz);
-      v[0] = src[n];
-      v[1] = T(sgn) * src[N + n];
-      v[2] = T(sgn) * src[2 * N + n];
-      v[3] = T(sgn) * src[3 * N + n];
-    }
+constexpr int NLD = (RPL + NT - 1) / NT;  // halo-2 plane nodes per thread
+constexpr int NFQ = (FPL + NT - 1) / NT;  // halo-1 plane nodes per thread
+
+// This thread's nodes of the halo-2 input plane, resolved once for the whole z march: the source
+// column x + nx y after the ghost rule along x and y, its sign for u, and the shared-memory slot.
+struct PlaneSrc {
+  long long off[NLD];
+  int slot[NLD];  // lj * RX + li, or -1
+  int sgn[NLD];   // 0: no source (beyond the ghost layer), else +-1
+};
+
+__device__ __forceinline__ PlaneSrc plane_src(const Geo& g, int x0, int y0) {
+  PlaneSrc ps;
 #pragma unroll
-    for (int c = 0; c < 4; ++c) dst[c][lj][li] = v[c];
+  for (int j = 0; j < NLD; ++j) {
+    const int q = threadIdx.x + j * NT;
+    ps.slot[j] = -1;
+    ps.sgn[j] = 0;
+    ps.off[j] = 0;
+    if (q >= RPL) continue;
+    const int li = q % RX, lj = q / RX;
+    int gx = x0 - 2 + li, gy = y0 - 2 + lj, sgn = 1;
+    ps.slot[j] = q;
+    if (ghost_axis(g.bc[0], g.n[0], &gx, &sgn) && ghost_axis(g.bc[1], g.n[1], &gy, &sgn)) {
+      ps.sgn[j] = sgn;
+      ps.off[j] = gx + (long long)g.n[0] * gy;
+    }
+  }
+  return ps;
+}
+
+// Read plane zr of the state (after the ghost rule along z) into registers.
+template <typename T>
+__device__ __forceinline__ void fetch_plane(const Geo& g, const T* __restrict__ src, const PlaneSrc& ps, int zr,
+                                            T (&v)[NLD][4]) {
+  int gz = zr, sz = 1;
+  const bool okz = ghost_axis(g.bc[2], g.n[2], &gz, &sz);
+  const long long N = g.N, zoff = (long long)gz * g.n[0] * g.n[1];
+#pragma unroll
+  for (int j = 0; j < NLD; ++j) {
+    const bool ok = okz && ps.sgn[j] != 0;
+    const long long n = ps.off[j] + zoff;
+    const T sg = T(ps.sgn[j] * sz);
+    v[j][0] = ok ? src[n] : T(0);
+    v[j][1] = ok ? sg * src[N + n] : T(0);
+    v[j][2] = ok ? sg * src[2 * N + n] : T(0);
+    v[j][3] = ok ? sg * src[3 * N + n] : T(0);
   }
 }
 
-// f_i^eq on the halo-1 nodes of plane zr from the input planes zr - 1, zr, zr + 1.
 template <typename T>
-__device__ __forceinline__ void feq_plane(const Geo& g, Fwd3Smem<T>& s, int zr, int z0) {
-  const int sm = ring(zr - 1, z0), s0 = ring(zr, z0), sp = ring(zr + 1, z0);
+__device__ __forceinline__ void store_plane(T (*dst)[RY][RX], const PlaneSrc& ps, const T (&v)[NLD][4]) {
+#pragma unroll
+  for (int j = 0; j < NLD; ++j) {
+    if (ps.slot[j] < 0) continue;
+#pragma unroll
+    for (int c = 0; c < 4; ++c) (&dst[c][0][0])[ps.slot[j]] = v[j][c];
+  }
+}
+
+// f_i^eq of one halo-1 node (ci, cj) of plane zr from the input planes zr - 1, zr, zr + 1.
+// The velocity gradient sums the corner columns along z first. The eight corner values share
+// their terms: with alpha = w3 (a + Qxx + Qyy + Qzz) and the w3-scaled b, Q, the corners of one z
+// sign are (alpha +- Bz + Qxy) +- (X + Y) and (alpha +- Bz - Qxy) +- (X - Y), X = Bx +- Qxz,
+// Y = By +- Qyz.
+template <typename T>
+__device__ __forceinline__ void feq_node(const Geo& g, Fwd3Smem<T>& s, int sm, int s0, int sp, int ci, int cj) {
+  const int li = ci + 1, lj = cj + 1;
   const T A2 = two_a<T>(g), tenth = T(0.1);
+  const T p = s.raw[s0][0][lj][li];
+  T u[3], G[3][3];
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    const T(*U0)[RX] = s.raw[s0][1 + a];
+    const T(*Um)[RX] = s.raw[sm][1 + a];
+    const T(*Up)[RX] = s.raw[sp][1 + a];
+    u[a] = U0[lj][li];
+    const T pp = Up[lj + 1][li + 1], pm = Up[lj - 1][li + 1], mp = Up[lj + 1][li - 1], mm = Up[lj - 1][li - 1];
+    const T qp = Um[lj + 1][li + 1], qm = Um[lj - 1][li + 1], np_ = Um[lj + 1][li - 1], nm = Um[lj - 1][li - 1];
+    const T Spp = pp + qp, Spm = pm + qm, Smp = mp + np_, Smm = mm + nm;
+    const T gx = (U0[lj][li + 1] - U0[lj][li - 1]) + (Spp + Spm) - (Smp + Smm);
+    const T gy = (U0[lj + 1][li] - U0[lj - 1][li]) + (Spp + Smp) - (Spm + Smm);
+    const T gz = (Up[lj][li] - Um[lj][li]) + ((pp - qp) + (pm - qm)) + ((mp - np_) + (mm - nm));
+    G[a][0] = gx * tenth;
+    G[a][1] = gy * tenth;
+    G[a][2] = gz * tenth;
+  }
   const T w0 = T(2.0 / 9.0), w1 = T(1.0 / 9.0), w3 = T(1.0 / 72.0);
-  for (int q = threadIdx.x; q < FPL; q += NT) {
-    const int ci = q % FX, cj = q / FX, li = ci + 1, lj = cj + 1;
-    const T p = s.raw[s0][0][lj][li];
-    T u[3], G[3][3];
+  const T a0 = T(3) * p - T(1.5) * (u[0] * u[0] + u[1] * u[1] + u[2] * u[2]);
+  const T qxx = T(4.5) * u[0] * u[0] + A2 * G[0][0];
+  const T qyy = T(4.5) * u[1] * u[1] + A2 * G[1][1];
+  const T qzz = T(4.5) * u[2] * u[2] + A2 * G[2][2];
+  const T qxy = T(9) * u[0] * u[1] + A2 * (G[0][1] + G[1][0]);
+  const T qxz = T(9) * u[0] * u[2] + A2 * (G[0][2] + G[2][0]);
+  const T qyz = T(9) * u[1] * u[2] + A2 * (G[1][2] + G[2][1]);
+  s.f[0][cj][ci] = w0 * a0;
+  const T bx1 = T(3) * w1 * u[0], by1 = T(3) * w1 * u[1], bz1 = T(3) * w1 * u[2];
+  const T tx = w1 * (a0 + qxx), ty = w1 * (a0 + qyy), tz = w1 * (a0 + qzz);
+  s.f[1][cj][ci] = tx + bx1;
+  s.f[2][cj][ci] = tx - bx1;
+  s.f[3][cj][ci] = ty + by1;
+  s.f[4][cj][ci] = ty - by1;
+  s.f[5][cj][ci] = tz + bz1;
+  s.f[6][cj][ci] = tz - bz1;
+  const T al = w3 * (a0 + qxx + qyy + qzz);
+  const T Bx = T(3) * w3 * u[0], By = T(3) * w3 * u[1], Bz = T(3) * w3 * u[2];
+  const T Qxy = w3 * qxy, Qxz = w3 * qxz, Qyz = w3 * qyz;
 #pragma unroll
-    for (int a = 0; a < 3; ++a) {
-      const T(*U0)[RX] = s.raw[s0][1 + a];
-      const T(*Um)[RX] = s.raw[sm][1 + a];
-      const T(*Up)[RX] = s.raw[sp][1 + a];
-      u[a] = U0[lj][li];
-      T gx = U0[lj][li + 1] - U0[lj][li - 1];
-      T gy = U0[lj + 1][li] - U0[lj - 1][li];
-      T gz = Up[lj][li] - Um[lj][li];
-#pragma unroll
-      for (int k = 0; k < 8; ++k) {
-        const T v = (csz(k) > 0 ? Up : Um)[lj + csy(k)][li + csx(k)];
-        gx += T(csx(k)) * v;
-        gy += T(csy(k)) * v;
-        gz += T(csz(k)) * v;
-      }
-      G[a][0] = gx * tenth;
-      G[a][1] = gy * tenth;
-      G[a][2] = gz * tenth;
-    }
-    const T a0 = T(3) * p - T(1.5) * (u[0] * u[0] + u[1] * u[1] + u[2] * u[2]);
-    const T bx = T(3) * u[0], by = T(3) * u[1], bz = T(3) * u[2];
-    const T qxx = T(4.5) * u[0] * u[0] + A2 * G[0][0];
-    const T qyy = T(4.5) * u[1] * u[1] + A2 * G[1][1];
-    const T qzz = T(4.5) * u[2] * u[2] + A2 * G[2][2];
-    const T qxy = T(9) * u[0] * u[1] + A2 * (G[0][1] + G[1][0]);
-    const T qxz = T(9) * u[0] * u[2] + A2 * (G[0][2] + G[2][0]);
-    const T qyz = T(9) * u[1] * u[2] + A2 * (G[1][2] + G[2][1]);
-    s.f[0][cj][ci] = w0 * a0;
-    s.f[1][cj][ci] = w1 * (a0 + bx + qxx);
-    s.f[2][cj][ci] = w1 * (a0 - bx + qxx);
-    s.f[3][cj][ci] = w1 * (a0 + by + qyy);
-    s.f[4][cj][ci] = w1 * (a0 - by + qyy);
-    s.f[5][cj][ci] = w1 * (a0 + bz + qzz);
-    s.f[6][cj][ci] = w1 * (a0 - bz + qzz);
-    const T diag = a0 + qxx + qyy + qzz;
-#pragma unroll
-    for (int k = 0; k < 8; ++k) {
-      const T sx = T(csx(k)), sy = T(csy(k)), sz = T(csz(k));
-      s.f[7 + k][cj][ci] = w3 * (diag + sx * bx + sy * by + sz * bz + sx * sy * qxy + sx * sz * qxz + sy * sz * qyz);
-    }
+  for (int h = 0; h < 2; ++h) {  // h = 0: c_z = +1 (k = 0..3), h = 1: c_z = -1 (k = 4..7)
+    const T e = h ? al - Bz : al + Bz;
+    const T X = h ? Bx - Qxz : Bx + Qxz, Y = h ? By - Qyz : By + Qyz;
+    const T t1 = e + Qxy, t2 = e - Qxy, P = X + Y, M = X - Y;
+    s.f[7 + 4 * h + 0][cj][ci] = t1 + P;  // (+, +)
+    s.f[7 + 4 * h + 1][cj][ci] = t2 - M;  // (-, +)
+    s.f[7 + 4 * h + 2][cj][ci] = t2 + M;  // (+, -)
+    s.f[7 + 4 * h + 3][cj][ci] = t1 - P;  // (-, -)
   }
 }
 
@@ -161,7 +207,7 @@ __device__ __forceinline__ void x_planes(const Geo& g, T (*O)[TY][TX], int gx, i
 }
 
 template <typename T>
-__global__ void __launch_bounds__(NT) k_stencil3d(Geo g, Slots<T> S, const Ctrl* __restrict__ ctrl, int di) {
+__global__ void __launch_bounds__(NT, sizeof(T) == 4 ? 2 : 1) k_stencil3d(Geo g, Slots<T> S, const Ctrl* __restrict__ ctrl, int di) {
   extern __shared__ __align__(16) unsigned char smem_bytes[];
   Fwd3Smem<T>& s = *reinterpret_cast<Fwd3Smem<T>*>(smem_bytes);
   const int t = ctrl->t0 + di, base = ctrl->base;
@@ -176,7 +222,18 @@ __global__ void __launch_bounds__(NT) k_stencil3d(Geo g, Slots<T> S, const Ctrl*
   const bool zwall = g.bc[2] == BC_WALL;
   int z0, z1;
   chunk_range(nz, &z0, &z1);
+  // a tile whose outputs need no boundary phase writes them straight from registers
+  const bool plain = (g.bc[0] == BC_PERIODIC || (x0 >= 1 && x0 + TX <= nx - 1)) &&
+                     (g.bc[1] != BC_WALL || (y0 >= 1 && y0 + TY <= ny - 1)) && (!zwall || (z0 >= 2 && z1 <= nz - 2));
   const int ci = tx + 1, cj = ty + 1;
+  int fci[NFQ], fcj[NFQ];
+#pragma unroll
+  for (int j = 0; j < NFQ; ++j) {
+    const int q = threadIdx.x + j * NT;
+    fci[j] = q < FPL ? q % FX : -1;
+    fcj[j] = q < FPL ? q / FX : -1;
+  }
+  const PlaneSrc ps = plane_src(g, x0, y0);
   // acc[d]: output plane zr - 1 + d, (sum f, sum c_x f, sum c_y f, sum c_z f)
   T acc[3][4];
 #pragma unroll
@@ -184,13 +241,25 @@ __global__ void __launch_bounds__(NT) k_stencil3d(Geo g, Slots<T> S, const Ctrl*
 #pragma unroll
     for (int c = 0; c < 4; ++c) acc[d][c] = T(0);
 
-  load_state_plane(g, src, s.raw[ring(z0 - 2, z0)], x0, y0, z0 - 2);
-  load_state_plane(g, src, s.raw[ring(z0 - 1, z0)], x0, y0, z0 - 1);
+  T v[NLD][4];
+  for (int zl = z0 - 2; zl <= z0; ++zl) {
+    fetch_plane(g, src, ps, zl, v);
+    store_plane(s.raw[ring(zl, z0)], ps, v);
+  }
+  fetch_plane(g, src, ps, z0 + 1, v);  // in flight while plane z0 - 1 is worked on
   for (int zr = z0 - 1; zr <= z1; ++zr) {
-    load_state_plane(g, src, s.raw[ring(zr + 1, z0)], x0, y0, zr + 1);
+    __syncthreads();  // planes zr - 1 .. zr + 1 are in the ring; the previous f plane is consumed
+    {
+      const int sm = ring(zr - 1, z0), s0 = ring(zr, z0), sp = ring(zr + 1, z0);
+#pragma unroll
+      for (int j = 0; j < NFQ; ++j)
+        if (fci[j] >= 0) feq_node(g, s, sm, s0, sp, fci[j], fcj[j]);
+    }
     __syncthreads();
-    feq_plane(g, s, zr, z0);
-    __syncthreads();
+    if (zr + 2 <= z1 + 1) {
+      store_plane(s.raw[ring(zr + 2, z0)], ps, v);  // replaces plane zr - 1, no longer read
+      if (zr + 3 <= z1 + 1) fetch_plane(g, src, ps, zr + 3, v);
+    }
     {
       // c_z = 0: rest and the four in-plane axis vectors -> output zr
       const T f0 = s.f[0][cj][ci], f1 = s.f[1][cj][ci - 1], f2 = s.f[2][cj][ci + 1];
@@ -207,55 +276,65 @@ __global__ void __launch_bounds__(NT) k_stencil3d(Geo g, Slots<T> S, const Ctrl*
 #pragma unroll
       for (int k = 0; k < 8; ++k) {
         const int sx = csx(k), sy = csy(k), sz = csz(k);
-        const T v = s.f[7 + k][cj - sy][ci - sx];
+        const T vv = s.f[7 + k][cj - sy][ci - sx];
         const int d = sz > 0 ? 2 : 0;
-        acc[d][0] += v;
-        acc[d][1] += T(sx) * v;
-        acc[d][2] += T(sy) * v;
-        acc[d][3] += T(sz) * v;
+        acc[d][0] += vv;
+        acc[d][1] += T(sx) * vv;
+        acc[d][2] += T(sy) * vv;
+        acc[d][3] += T(sz) * vv;
       }
     }
     const int zo = zr - 1;
     if (zo >= z0) {  // output plane zo is complete
-      s.out[0][ty][tx] = acc[0][0] * T(1.0 / 3.0);
-      s.out[1][ty][tx] = acc[0][1];
-      s.out[2][ty][tx] = acc[0][2];
-      s.out[3][ty][tx] = acc[0][3];
-      __syncthreads();
-      // y walls, for nodes with x and z interior
-      if (ingrid && g.bc[1] == BC_WALL && (gy == 0 || gy == ny - 1) && interior_axis(g.bc[0], nx, gx) &&
-          interior_axis(g.bc[2], nz, zo)) {
-        const int tin = (gy == 0) ? ty + 1 : ty - 1;
-        s.out[0][ty][tx] = s.out[0][tin][tx];
-        s.out[1][ty][tx] = s.out[2][ty][tx] = s.out[3][ty][tx] = T(0);
-      }
-      __syncthreads();
-      // z walls, for nodes with x interior (own column only)
-      const T pp = s.out[0][ty][tx];
-      if (zwall && interior_axis(g.bc[0], nx, gx)) {
-        if (zo == nz - 1) {
-          s.out[0][ty][tx] = s.prevp[ty][tx];
+      if (plain) {
+        if (ingrid) {
+          const long long n = gx + (long long)nx * (gy + (long long)ny * zo);
+          dst[n] = acc[0][0] * T(1.0 / 3.0);
+          dst[N + n] = acc[0][1];
+          dst[2 * N + n] = acc[0][2];
+          dst[3 * N + n] = acc[0][3];
+        }
+      } else {
+        s.out[0][ty][tx] = acc[0][0] * T(1.0 / 3.0);
+        s.out[1][ty][tx] = acc[0][1];
+        s.out[2][ty][tx] = acc[0][2];
+        s.out[3][ty][tx] = acc[0][3];
+        __syncthreads();
+        // y walls, for nodes with x and z interior
+        if (ingrid && g.bc[1] == BC_WALL && (gy == 0 || gy == ny - 1) && interior_axis(g.bc[0], nx, gx) &&
+            interior_axis(g.bc[2], nz, zo)) {
+          const int tin = (gy == 0) ? ty + 1 : ty - 1;
+          s.out[0][ty][tx] = s.out[0][tin][tx];
           s.out[1][ty][tx] = s.out[2][ty][tx] = s.out[3][ty][tx] = T(0);
         }
-        if (zo == 1) {
-          s.out0[0][ty][tx] = pp;
-          s.out0[1][ty][tx] = s.out0[2][ty][tx] = s.out0[3][ty][tx] = T(0);
+        __syncthreads();
+        // z walls, for nodes with x interior (own column only)
+        const T pp = s.out[0][ty][tx];
+        if (zwall && interior_axis(g.bc[0], nx, gx)) {
+          if (zo == nz - 1) {
+            s.out[0][ty][tx] = s.prevp[ty][tx];
+            s.out[1][ty][tx] = s.out[2][ty][tx] = s.out[3][ty][tx] = T(0);
+          }
+          if (zo == 1) {
+            s.out0[0][ty][tx] = pp;
+            s.out0[1][ty][tx] = s.out0[2][ty][tx] = s.out0[3][ty][tx] = T(0);
+          }
         }
-      }
-      s.prevp[ty][tx] = pp;
-      __syncthreads();
-      if (ingrid) {
-        x_planes(g, s.out, gx, tx, ty);
-        if (zwall && zo == 1) x_planes(g, s.out0, gx, tx, ty);
-        const long long n = gx + (long long)nx * gy;
-        if (!(zwall && zo == 0)) {
-          const long long nz_off = (long long)zo * nx * ny;
+        s.prevp[ty][tx] = pp;
+        __syncthreads();
+        if (ingrid) {
+          x_planes(g, s.out, gx, tx, ty);
+          if (zwall && zo == 1) x_planes(g, s.out0, gx, tx, ty);
+          const long long n = gx + (long long)nx * gy;
+          if (!(zwall && zo == 0)) {
+            const long long nz_off = (long long)zo * nx * ny;
 #pragma unroll
-          for (int c = 0; c < 4; ++c) dst[c * N + nz_off + n] = s.out[c][ty][tx];
-        }
-        if (zwall && zo == 1) {
+            for (int c = 0; c < 4; ++c) dst[c * N + nz_off + n] = s.out[c][ty][tx];
+          }
+          if (zwall && zo == 1) {
 #pragma unroll
-          for (int c = 0; c < 4; ++c) dst[c * N + n] = s.out0[c][ty][tx];
+            for (int c = 0; c < 4; ++c) dst[c * N + n] = s.out0[c][ty][tx];
+          }
         }
       }
     }
@@ -318,78 +397,116 @@ __device__ __forceinline__ void lam_star3(const Geo& g, const T* L, int x, int y
   }
 }
 
-template <typename T>
-__device__ __forceinline__ void load_adj_plane(const Geo& g, const T* __restrict__ L, T (*dst)[RY][RX], int x0, int y0,
-                                               int zr) {
-  const int nx = g.n[0], ny = g.n[1], nz = g.n[2];
-  for (int q = threadIdx.x; q < RPL; q += NT) {
-    const int li = q % RX, lj = q / RX;
-    int gx = x0 - 2 + li, gy = y0 - 2 + lj, gz = zr;
-    T v[4] = {T(0), T(0), T(0), T(0)};
-    bool ok = true;
-    if (g.bc[0] == BC_PERIODIC) gx = wrapi(gx, nx);
-    else if (gx < 0 || gx >= nx) ok = false;
-    if (g.bc[1] == BC_PERIODIC) gy = wrapi(gy, ny);
-    else if (gy < 0 || gy >= ny) ok = false;
-    if (g.bc[2] == BC_PERIODIC) gz = wrapi(gz, nz);
-    else if (gz < 0 || gz >= nz) ok = false;
-    if (ok) lam_star3(g, L, gx, gy, gz, v);
+// This thread's nodes of the adjoint's halo-2 input plane: the (wrapped) column and whether it is
+// on the grid, resolved once for the whole z march.
+struct AdjSrc {
+  int gx[NLD], gy[NLD];
+  int slot[NLD];  // lj * RX + li, or -1
+  bool ok[NLD];
+};
+
+__device__ __forceinline__ AdjSrc adj_src(const Geo& g, int x0, int y0) {
+  AdjSrc as;
 #pragma unroll
-    for (int c = 0; c < 4; ++c) dst[c][lj][li] = v[c];
+  for (int j = 0; j < NLD; ++j) {
+    const int q = threadIdx.x + j * NT;
+    as.slot[j] = q < RPL ? q : -1;
+    int gx = x0 - 2 + q % RX, gy = y0 - 2 + q / RX;
+    bool ok = q < RPL;
+    if (g.bc[0] == BC_PERIODIC) gx = wrapi(gx, g.n[0]);
+    else if (gx < 0 || gx >= g.n[0]) ok = false;
+    if (g.bc[1] == BC_PERIODIC) gy = wrapi(gy, g.n[1]);
+    else if (gy < 0 || gy >= g.n[1]) ok = false;
+    as.gx[j] = gx;
+    as.gy[j] = gy;
+    as.ok[j] = ok;
+  }
+  return as;
+}
+
+template <typename T>
+__device__ __forceinline__ void store_raw(T (*dst)[RY][RX], const AdjSrc& as, const T (&v)[NLD][4]) {
+#pragma unroll
+  for (int j = 0; j < NLD; ++j) {
+    if (as.slot[j] < 0) continue;
+#pragma unroll
+    for (int c = 0; c < 4; ++c) (&dst[c][0][0])[as.slot[j]] = v[j][c];
   }
 }
 
-// Moments of plane zr on the halo-1 nodes; zero on nodes off the grid (non-periodic axes), where
-// the gradient-stencil transpose reads them as absent.
+// Plane zr of the adjoint with the boundary rules reversed (lam_star3), into registers. In a
+// column whose halo stays two nodes away from every non-periodic boundary (direct) and on a plane
+// likewise, the rules are the identity and the values are read directly.
 template <typename T>
-__device__ __forceinline__ void moment_plane(const Geo& g, Adj3Smem<T>& s, int zr, int z0, int x0, int y0) {
-  const int sm = ring(zr - 1, z0), s0 = ring(zr, z0), sp = ring(zr + 1, z0);
-  const T third = T(1.0 / 3.0), w0 = T(2.0 / 9.0), w1 = T(1.0 / 9.0), w3 = T(1.0 / 72.0);
-  const bool zoff = g.bc[2] != BC_PERIODIC && (zr < 0 || zr >= g.n[2]);
-  for (int q = threadIdx.x; q < FPL; q += NT) {
-    const int ci = q % FX, cj = q / FX, li = ci + 1, lj = cj + 1;
-    const int x = x0 - 1 + ci, y = y0 - 1 + cj;
-    if (zoff || (g.bc[0] != BC_PERIODIC && (x < 0 || x >= g.n[0])) ||
-        (g.bc[1] != BC_PERIODIC && (y < 0 || y >= g.n[1]))) {
+__device__ __forceinline__ void fetch_adj_plane(const Geo& g, const T* __restrict__ L, const AdjSrc& as, bool direct,
+                                                int zr, T (&v)[NLD][4]) {
+  const int nx = g.n[0], ny = g.n[1], nz = g.n[2];
+  int gz = zr;
+  bool okz = true;
+  if (g.bc[2] == BC_PERIODIC) gz = wrapi(gz, nz);
+  else if (gz < 0 || gz >= nz) okz = false;
+  const bool dz = g.bc[2] == BC_PERIODIC || (zr >= 2 && zr <= nz - 3);
+  const long long N = g.N;
 #pragma unroll
-      for (int c = 0; c < 10; ++c) s.m[c][cj][ci] = T(0);
-      continue;
-    }
-    const T(*P0)[RX] = s.raw[s0][0];
-    const T fb0 = third * P0[lj][li];
-    const T fpx = third * P0[lj][li + 1] + s.raw[s0][1][lj][li + 1];
-    const T fmx = third * P0[lj][li - 1] - s.raw[s0][1][lj][li - 1];
-    const T fpy = third * P0[lj + 1][li] + s.raw[s0][2][lj + 1][li];
-    const T fmy = third * P0[lj - 1][li] - s.raw[s0][2][lj - 1][li];
-    const T fpz = third * s.raw[sp][0][lj][li] + s.raw[sp][3][lj][li];
-    const T fmz = third * s.raw[sm][0][lj][li] - s.raw[sm][3][lj][li];
-    T cP = T(0), cX = T(0), cY = T(0), cZ = T(0), cXY = T(0), cXZ = T(0), cYZ = T(0);
+  for (int j = 0; j < NLD; ++j) {
 #pragma unroll
-    for (int k = 0; k < 8; ++k) {
-      const int sx = csx(k), sy = csy(k), sz = csz(k);
-      const int pl = sz > 0 ? sp : sm;
-      const int yy = lj + sy, xx = li + sx;
-      const T fb = third * s.raw[pl][0][yy][xx] + T(sx) * s.raw[pl][1][yy][xx] + T(sy) * s.raw[pl][2][yy][xx] +
-                   T(sz) * s.raw[pl][3][yy][xx];
-      cP += fb;
-      cX += T(sx) * fb;
-      cY += T(sy) * fb;
-      cZ += T(sz) * fb;
-      cXY += T(sx * sy) * fb;
-      cXZ += T(sx * sz) * fb;
-      cYZ += T(sy * sz) * fb;
+    for (int c = 0; c < 4; ++c) v[j][c] = T(0);
+    if (!as.ok[j] || !okz) continue;
+    if (direct && dz) {
+      const long long n = as.gx[j] + (long long)nx * (as.gy[j] + (long long)ny * gz);
+#pragma unroll
+      for (int c = 0; c < 4; ++c) v[j][c] = L[c * N + n];
+    } else {
+      lam_star3(g, L, as.gx[j], as.gy[j], gz, v[j]);
     }
-    s.m[0][cj][ci] = w0 * fb0 + w1 * (fpx + fmx + fpy + fmy + fpz + fmz) + w3 * cP;
-    s.m[1][cj][ci] = w1 * (fpx - fmx) + w3 * cX;
-    s.m[2][cj][ci] = w1 * (fpy - fmy) + w3 * cY;
-    s.m[3][cj][ci] = w1 * (fpz - fmz) + w3 * cZ;
-    s.m[4][cj][ci] = w1 * (fpx + fmx) + w3 * cP;
-    s.m[5][cj][ci] = w1 * (fpy + fmy) + w3 * cP;
-    s.m[6][cj][ci] = w1 * (fpz + fmz) + w3 * cP;
-    s.m[7][cj][ci] = w3 * cXY;
-    s.m[8][cj][ci] = w3 * cXZ;
-    s.m[9][cj][ci] = w3 * cYZ;
   }
+}
+
+// Moments of plane zr at the halo-1 node (ci, cj); zero on nodes off the grid (non-periodic axes),
+// where the gradient-stencil transpose reads them as absent (off: the node is off the grid).
+template <typename T>
+__device__ __forceinline__ void moment_node(Adj3Smem<T>& s, int sm, int s0, int sp, int ci, int cj, bool off) {
+  const T third = T(1.0 / 3.0), w0 = T(2.0 / 9.0), w1 = T(1.0 / 9.0), w3 = T(1.0 / 72.0);
+  if (off) {
+#pragma unroll
+    for (int c = 0; c < 10; ++c) s.m[c][cj][ci] = T(0);
+    return;
+  }
+  const int li = ci + 1, lj = cj + 1;
+  const T(*P0)[RX] = s.raw[s0][0];
+  const T fb0 = third * P0[lj][li];
+  const T fpx = third * P0[lj][li + 1] + s.raw[s0][1][lj][li + 1];
+  const T fmx = third * P0[lj][li - 1] - s.raw[s0][1][lj][li - 1];
+  const T fpy = third * P0[lj + 1][li] + s.raw[s0][2][lj + 1][li];
+  const T fmy = third * P0[lj - 1][li] - s.raw[s0][2][lj - 1][li];
+  const T fpz = third * s.raw[sp][0][lj][li] + s.raw[sp][3][lj][li];
+  const T fmz = third * s.raw[sm][0][lj][li] - s.raw[sm][3][lj][li];
+  T cP = T(0), cX = T(0), cY = T(0), cZ = T(0), cXY = T(0), cXZ = T(0), cYZ = T(0);
+#pragma unroll
+  for (int k = 0; k < 8; ++k) {
+    const int sx = csx(k), sy = csy(k), sz = csz(k);
+    const int pl = sz > 0 ? sp : sm;
+    const int yy = lj + sy, xx = li + sx;
+    const T fb = third * s.raw[pl][0][yy][xx] + T(sx) * s.raw[pl][1][yy][xx] + T(sy) * s.raw[pl][2][yy][xx] +
+                 T(sz) * s.raw[pl][3][yy][xx];
+    cP += fb;
+    cX += T(sx) * fb;
+    cY += T(sy) * fb;
+    cZ += T(sz) * fb;
+    cXY += T(sx * sy) * fb;
+    cXZ += T(sx * sz) * fb;
+    cYZ += T(sy * sz) * fb;
+  }
+  s.m[0][cj][ci] = w0 * fb0 + w1 * (fpx + fmx + fpy + fmy + fpz + fmz) + w3 * cP;
+  s.m[1][cj][ci] = w1 * (fpx - fmx) + w3 * cX;
+  s.m[2][cj][ci] = w1 * (fpy - fmy) + w3 * cY;
+  s.m[3][cj][ci] = w1 * (fpz - fmz) + w3 * cZ;
+  s.m[4][cj][ci] = w1 * (fpx + fmx) + w3 * cP;
+  s.m[5][cj][ci] = w1 * (fpy + fmy) + w3 * cP;
+  s.m[6][cj][ci] = w1 * (fpz + fmz) + w3 * cP;
+  s.m[7][cj][ci] = w3 * cXY;
+  s.m[8][cj][ci] = w3 * cXZ;
+  s.m[9][cj][ci] = w3 * cYZ;
 }
 
 // S_ab of the moment plane at (cj, ci), b-th column (symmetric).
@@ -441,7 +558,7 @@ __device__ __forceinline__ void h_add(const Adj3Smem<T>& s, int cj, int ci, T sg
 }
 
 template <typename T>
-__global__ void __launch_bounds__(NT) k_stencil3d_adj(Geo g, Slots<T> S, T* Lb, long long lstride,
+__global__ void __launch_bounds__(NT, sizeof(T) == 4 ? 2 : 1) k_stencil3d_adj(Geo g, Slots<T> S, T* Lb, long long lstride,
                                                       const Ctrl* __restrict__ ctrl, int di) {
   extern __shared__ __align__(16) unsigned char smem_bytes[];
   Adj3Smem<T>& s = *reinterpret_cast<Adj3Smem<T>*>(smem_bytes);
@@ -465,13 +582,40 @@ __global__ void __launch_bounds__(NT) k_stencil3d_adj(Geo g, Slots<T> S, T* Lb, 
 #pragma unroll
     for (int c = 0; c < 4; ++c) acc[d][c] = T(0);
 
-  load_adj_plane(g, Lcur, s.raw[ring(z0 - 2, z0)], x0, y0, z0 - 2);
-  load_adj_plane(g, Lcur, s.raw[ring(z0 - 1, z0)], x0, y0, z0 - 1);
+  int fci[NFQ], fcj[NFQ];
+  bool foffxy[NFQ];
+#pragma unroll
+  for (int j = 0; j < NFQ; ++j) {
+    const int q = threadIdx.x + j * NT;
+    fci[j] = q < FPL ? q % FX : -1;
+    fcj[j] = q < FPL ? q / FX : -1;
+    const int x = x0 - 1 + fci[j], y = y0 - 1 + fcj[j];
+    foffxy[j] = (g.bc[0] != BC_PERIODIC && (x < 0 || x >= nx)) || (g.bc[1] != BC_PERIODIC && (y < 0 || y >= ny));
+  }
+  const AdjSrc as = adj_src(g, x0, y0);
+  // every halo node of the column two nodes clear of the non-periodic boundaries
+  const bool direct = (g.bc[0] == BC_PERIODIC || (x0 >= 4 && x0 + TX + 4 <= nx)) &&
+                      (g.bc[1] == BC_PERIODIC || (y0 >= 4 && y0 + TY + 4 <= ny));
+  T v[NLD][4];
+  for (int zl = z0 - 2; zl <= z0; ++zl) {
+    fetch_adj_plane(g, Lcur, as, direct, zl, v);
+    store_raw(s.raw[ring(zl, z0)], as, v);
+  }
+  fetch_adj_plane(g, Lcur, as, direct, z0 + 1, v);
   for (int zr = z0 - 1; zr <= z1; ++zr) {
-    load_adj_plane(g, Lcur, s.raw[ring(zr + 1, z0)], x0, y0, zr + 1);
+    __syncthreads();  // planes zr - 1 .. zr + 1 are in the ring; the previous moment plane is consumed
+    {
+      const int sm = ring(zr - 1, z0), s0 = ring(zr, z0), sp = ring(zr + 1, z0);
+      const bool zoff = g.bc[2] != BC_PERIODIC && (zr < 0 || zr >= nz);
+#pragma unroll
+      for (int j = 0; j < NFQ; ++j)
+        if (fci[j] >= 0) moment_node(s, sm, s0, sp, fci[j], fcj[j], zoff || foffxy[j]);
+    }
     __syncthreads();
-    moment_plane(g, s, zr, z0, x0, y0);
-    __syncthreads();
+    if (zr + 2 <= z1 + 1) {
+      store_raw(s.raw[ring(zr + 2, z0)], as, v);  // replaces plane zr - 1, no longer read
+      if (zr + 3 <= z1 + 1) fetch_adj_plane(g, Lcur, as, direct, zr + 3, v);
+    }
     // local part of output zr
     if (ingrid && zr >= z0 && zr < z1) {
       const long long n = gx + (long long)nx * (gy + (long long)ny * zr);
@@ -532,13 +676,26 @@ __global__ void __launch_bounds__(NT) k_stencil3d_adj(Geo g, Slots<T> S, T* Lb, 
   }
 }
 
-// Number of z chunks: enough CTAs to fill the GPU, every chunk at least four planes.
-int z_chunks(const Geo& g) {
+// Number of z chunks: the count that best fills whole waves of resident CTAs (ctas_per_sm on each
+// of the 152 SMs) weighed against the two extra planes of f^eq each chunk computes; every chunk
+// holds at least four planes.
+int z_chunks(const Geo& g, int ctas_per_sm) {
   const int tiles = ((g.n[0] + TX - 1) / TX) * ((g.n[1] + TY - 1) / TY);
-  const int want = (4 * 152 + tiles - 1) / tiles;
-  int c = g.n[2] / 4;
-  if (c > want) c = want;
-  return c < 1 ? 1 : c;
+  const int slots = 152 * ctas_per_sm;
+  const int cmax = g.n[2] / 4 < 1 ? 1 : g.n[2] / 4;
+  int best = 1;
+  double best_eff = 0.0;
+  for (int c = 1; c <= cmax; ++c) {
+    const long long total = (long long)tiles * c;
+    const long long waves = (total + slots - 1) / slots;
+    const double planes = (double)g.n[2] / c;
+    const double eff = (double)total / (double)(waves * slots) * planes / (planes + 2.0);
+    if (eff > best_eff + 1e-9) {
+      best_eff = eff;
+      best = c;
+    }
+  }
+  return best;
 }
 
 }  // namespace
@@ -551,14 +708,14 @@ void prepare_stencil3d() {
 
 template <typename T>
 void launch_stencil3d_fwd(const Geo& g, const Slots<T>& S, const Ctrl* ctrl, int di, cudaStream_t st) {
-  const dim3 grid((g.n[0] + TX - 1) / TX, (g.n[1] + TY - 1) / TY, z_chunks(g));
+  const dim3 grid((g.n[0] + TX - 1) / TX, (g.n[1] + TY - 1) / TY, z_chunks(g, sizeof(T) == 4 ? 2 : 1));
   launch(k_stencil3d<T>, grid, NT, sizeof(Fwd3Smem<T>), st, g, S, ctrl, di);
 }
 
 template <typename T>
 void launch_stencil3d_adj(const Geo& g, const Slots<T>& S, T* Lb, long long lstride, const Ctrl* ctrl, int di,
                           cudaStream_t st) {
-  const dim3 grid((g.n[0] + TX - 1) / TX, (g.n[1] + TY - 1) / TY, z_chunks(g));
+  const dim3 grid((g.n[0] + TX - 1) / TX, (g.n[1] + TY - 1) / TY, z_chunks(g, sizeof(T) == 4 ? 2 : 1));
   launch(k_stencil3d_adj<T>, grid, NT, sizeof(Adj3Smem<T>), st, g, S, Lb, lstride, ctrl, di);
 }
 

@@ -225,6 +225,11 @@ CASES_3D = [
     ("3d-trans-bilinear-walls", lambda: body3d(nx=34, ny=18, nz=13, centre=(10.2, 9.1, 6.4),
                                                mask=DOF_TX | DOF_TY | DOF_TZ, wk=W_BILINEAR,
                                                bc=(BC_INFLOW_OUTFLOW, BC_WALL, BC_WALL))),
+    # several 32x16 column tiles (one of them two nodes clear of every boundary) and z chunks
+    ("3d-multitile-walls", lambda: body3d(nx=100, ny=40, nz=14, centre=(30.3, 19.6, 6.9),
+                                          bc=(BC_INFLOW_OUTFLOW, BC_WALL, BC_WALL), rot_axis=0, nt=4)),
+    ("3d-multitile-periodic", lambda: body3d(nx=70, ny=36, nz=22, centre=(40.3, 17.6, 10.9),
+                                             bc=(BC_PERIODIC,) * 3, rot_axis=2, nt=4)),
 ]
 
 
