@@ -387,11 +387,11 @@ void enqueue_adj_steps(lks_handle* h, Launcher& L, const Slots<T>& S, int nsteps
     for (int k = g.K; k >= 1; --k) {
       L("adj_cell", [&](cudaStream_t s) {
         launch_adj_cell<T>(g, h->ctrl, h->it, (const T*)h->kref, (const T*)h->boxstore, h->nbox, (T*)h->L,
-                           h->slot_elems, (T*)h->acc, (T*)h->scratch, k, i, h->partials, h->P.n_steps, s);
+                           h->slot_elems, (T*)h->acc, (T*)h->scratch, k, i, s);
       });
-      L.n("adj_design", g.ax == AX_FREE ? 2 : 1, [&](cudaStream_t s) {
+      L.n("adj_design", 2, [&](cudaStream_t s) {
         launch_adj_design<T>(g, h->ctrl, h->it, (const T*)h->kref, (const T*)h->scratch, h->dkref, h->partials, k, i,
-                             h->P.n_steps, s);
+                             s);
       });
     }
     L("stencil_adj", [&](cudaStream_t s) { launch_stencil_adj<T>(g, S, (T*)h->L, h->slot_elems, h->ctrl, i, s); });
@@ -552,10 +552,6 @@ int adjoint_impl(lks_handle* h, double seed, cudaStream_t st) {
       TRY(run_graph(h, "adj_u_" + std::to_string(n), st, [&](Launcher& L) { enqueue_adj_steps<T>(h, L, S, n); }));
     }
   }
-  // with one rotation axis each pass's EOM reverse runs inside the next pass's cell kernel; the
-  // sweep's last pass has no next one
-  if (g.ax != AX_FREE)
-    L0("adj_design", [&](cudaStream_t s) { launch_design_finish_last<T>(g, h->ctrl, h->it, h->partials, NT, s); });
   CK(cudaGetLastError());
   if (h->launch_error) return LKS_ERR_CUDA;
   return LKS_OK;

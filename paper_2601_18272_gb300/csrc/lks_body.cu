@@ -733,61 +733,16 @@ __global__ void __launch_bounds__(kCellThreads, 2) k_apply(Geo g, Slots<T> S, co
   }
 }
 
-// The EOM reverse of reverse pass rf (iteration kf) from its design-point partials, inside a
-// kernel of kCellThreads threads (one rotation axis): returns dJ/dF, dJ/dT in the field type to
-// every thread; CTA 0 stores the carried adjoint, dJ/dF, dJ/dT and (kf = 1) dJ/ds(t-1) in ctrl.
-template <typename T>
-__device__ __forceinline__ void fused_design_finish(const Geo& g, Ctrl* ctrl, const void* __restrict__ dparts,
-                                                    int nparts, int kf, long long rf, T (&lF)[3], T (&lT)[3]) {
-  __shared__ double red[32 * 8];
-  __shared__ double bc[6];
-  const int tid = threadIdx.x;
-  double lp[kNdofAxis];
-  if (tid == 0)
-    for (int a = 0; a < kNdofAxis; ++a) lp[a] = ctrl->lam_prev[(rf + 1) & 1][a];
-  double ls[8];
-  block_sum_partials<8>(static_cast<const typename Partial<T>::type*>(dparts), nparts, ls, red);
-  if (tid == 0) {
-    double nF[3], nT[3], s0v[kNdofAxis];
-    adj_finish(g, kf, ls, lp, nF, nT, s0v);
-    for (int a = 0; a < 3; ++a) {
-      bc[a] = nF[a];
-      bc[3 + a] = nT[a];
-    }
-    if (blockIdx.x == 0 && blockIdx.y == 0 && blockIdx.z == 0) {
-      for (int a = 0; a < kNdofAxis; ++a) ctrl->lam_prev[rf & 1][a] = lp[a];
-      if (kf == 1)
-        for (int a = 0; a < kNdofAxis; ++a) ctrl->lam_s0[a] = s0v[a];
-      lam_store(ctrl, nF, nT);
-    }
-  }
-  __syncthreads();
-#pragma unroll
-  for (int a = 0; a < 3; ++a) {
-    lF[a] = (T)bc[a];
-    lT[a] = (T)bc[3 + a];
-  }
-}
-
 template <typename T, int D, int AX>
-__global__ void __launch_bounds__(kCellThreads, 2) k_adj_cell(Geo g, Ctrl* ctrl, const Dof* it, const T* __restrict__ kref,
+__global__ void __launch_bounds__(kCellThreads, 2) k_adj_cell(Geo g, const Ctrl* ctrl, const Dof* it, const T* __restrict__ kref,
                                                       const T* __restrict__ boxstore, int nbox, T* Lb,
                                                       long long lstride, T* __restrict__ acc, T* __restrict__ scratch,
-                                                      int k, int di, const void* __restrict__ dparts, int ndparts,
-                                                      int nt) {
+                                                      int k, int di) {
   const int t = ctrl->t0 - di, base = ctrl->base, K = g.K;
   const Dof* row = it + (long long)(t - 1) * (K + 1);
   const Dof s0 = row[0], sk = row[k - 1];
   T lF[3], lT[3];
-  // Reverse pass r = (nt - t) N_itr + (N_itr - k). With one rotation axis the EOM reverse of pass
-  // r - 1 (the design pass before this one) is folded in here: every CTA sums that pass's
-  // design-point partials in the same fixed order and runs the same FP64 reverse, which yields this
-  // pass's dJ/dF and dJ/dT; CTA 0 records it. Free rotation keeps a separate finish kernel.
-  const long long r = (long long)(nt - t) * K + (K - k);
-  if (AX != AX_FREE && r > 0)
-    fused_design_finish<T>(g, ctrl, dparts, ndparts, k == K ? 1 : k + 1, r - 1, lF, lT);
-  else
-    lam_load<T>(ctrl, lF, lT);
+  lam_load<T>(ctrl, lF, lT);
   T* Lcur = Lb + (long long)(t & 1) * lstride;
   int lo[3];
   box_origin<D>(g, s0, lo[0], lo[1], lo[2]);
@@ -822,24 +777,20 @@ __global__ void __launch_bounds__(kDesignBlock) k_adj_design(Geo g, Ctrl* ctrl, 
 
 // Sum of the design-point partials and the EOM reverse (adj_finish, or adj_finish_free with the
 // iterates of the EOM being reversed).
-// k, t: the reverse pass being finished (t = ctrl->t0 - di unless tfix > 0); nt = N_t fixes the
-// pass index r = (nt - t) N_itr + (N_itr - k) and with it the carried-adjoint buffers.
 template <typename T, bool FREE>
 __global__ void __launch_bounds__(kFinishThreads) k_design_finish(Geo g, Ctrl* ctrl, const Dof* it,
                                                                   const void* __restrict__ partials, int nparts,
-                                                                  int k, int di, int tfix, int nt) {
+                                                                  int k, int di) {
   constexpr int NV = FREE ? nv_design<AX_FREE>() : nv_design<0>();
   constexpr int NS = FREE ? kNdofFree : kNdofAxis;
   __shared__ double red[32 * NV];
-  const int tp = tfix > 0 ? tfix : ctrl->t0 - di;
-  const long long r = (long long)(nt - tp) * g.K + (g.K - k);
   double lp[NS];  // thread 0 fetches the carried adjoint (and the EOM's iterates) before the reduction
   Dof e0, ek;
   bool has_eom = true;
   if (threadIdx.x == 0) {
-    for (int a = 0; a < NS; ++a) lp[a] = ctrl->lam_prev[(r + 1) & 1][a];
+    for (int a = 0; a < NS; ++a) lp[a] = ctrl->lam_prev[a];
     if (FREE) {
-      const int t = tp, K = g.K;
+      const int t = ctrl->t0 - di, K = g.K;
       const int te = (k > 1) ? t : t - 1, ke = (k > 1) ? k - 1 : K;
       has_eom = te >= 1;
       if (has_eom) {
@@ -857,7 +808,7 @@ __global__ void __launch_bounds__(kFinishThreads) k_design_finish(Geo g, Ctrl* c
       adj_finish_free(g, k, ls, lp, nF, nT, ctrl->lam_s0, e0, ek, has_eom);
     else
       adj_finish(g, k, ls, lp, nF, nT, ctrl->lam_s0);
-    for (int a = 0; a < NS; ++a) ctrl->lam_prev[r & 1][a] = lp[a];
+    for (int a = 0; a < NS; ++a) ctrl->lam_prev[a] = lp[a];
     lam_store(ctrl, nF, nT);
   }
 }
@@ -906,7 +857,7 @@ __global__ void k_adj_init(Geo g, Ctrl* ctrl, const Dof* it, int nt, const doubl
   } else {
     eom_reverse(g, ls, nF, nT, lp);
   }
-  for (int a = 0; a < kNdofFree; ++a) ctrl->lam_prev[1][a] = lp[a];  // buffer of pass r = -1
+  for (int a = 0; a < kNdofFree; ++a) ctrl->lam_prev[a] = lp[a];
   lam_store(ctrl, nF, nT);
 }
 
@@ -979,28 +930,22 @@ void launch_apply(const Geo& g, const Slots<T>& S, const Ctrl* ctrl, const Dof* 
   LKS_BOX_DISPATCH(k_apply, box_grid(g), kCellThreads, g, S, ctrl, it, kref, boxstore, nbox, di);
 }
 
-inline int design_blocks(const Geo& g) { return (g.ND + kDesignPointsPerCta - 1) / kDesignPointsPerCta; }
-
 template <typename T>
-void launch_adj_cell(const Geo& g, Ctrl* ctrl, const Dof* it, const T* kref, const T* boxstore, int nbox, T* Lb,
-                     long long lstride, T* acc, T* scratch, int k, int di, const void* dparts, int nt, cudaStream_t st) {
+void launch_adj_cell(const Geo& g, const Ctrl* ctrl, const Dof* it, const T* kref, const T* boxstore, int nbox, T* Lb,
+                     long long lstride, T* acc, T* scratch, int k, int di, cudaStream_t st) {
   LKS_BOX_DISPATCH(k_adj_cell, box_grid(g), kCellThreads, g, ctrl, it, kref, boxstore, nbox, Lb, lstride, acc,
-                   scratch, k, di, dparts, design_blocks(g), nt);
+                   scratch, k, di);
 }
 
 template <typename T>
 void launch_adj_design(const Geo& g, Ctrl* ctrl, const Dof* it, const T* kref, const T* scratch, double* dkref,
-                       void* partials, int k, int di, int nt, cudaStream_t st) {
-  const unsigned nb = (unsigned)design_blocks(g);
+                       void* partials, int k, int di, cudaStream_t st) {
+  const unsigned nb = (unsigned)((g.ND + kDesignPointsPerCta - 1) / kDesignPointsPerCta);
   LKS_BOX_DISPATCH(k_adj_design, nb, kDesignBlock, g, ctrl, it, kref, scratch, dkref, partials, k, di);
   if (g.ax == AX_FREE)
-    launch(k_design_finish<T, true>, 1, kFinishThreads, 0, st, g, ctrl, it, (const void*)partials, (int)nb, k, di, 0,
-           nt);
-}
-
-template <typename T>
-void launch_design_finish_last(const Geo& g, Ctrl* ctrl, const Dof* it, const void* partials, int nt, cudaStream_t st) {
-  launch(k_design_finish<T, false>, 1, kFinishThreads, 0, st, g, ctrl, it, partials, design_blocks(g), 1, 0, 1, nt);
+    launch(k_design_finish<T, true>, 1, kFinishThreads, 0, st, g, ctrl, it, (const void*)partials, (int)nb, k, di);
+  else
+    launch(k_design_finish<T, false>, 1, kFinishThreads, 0, st, g, ctrl, it, (const void*)partials, (int)nb, k, di);
 }
 
 template <typename T>
@@ -1040,11 +985,10 @@ void launch_ckpt_pack(const Geo& g, const Slots<T>& S, T* ckpt, long long cstrid
                                       cudaStream_t);                                                                \
   template void launch_apply<T>(const Geo&, const Slots<T>&, const Ctrl*, const Dof*, const T*, T*, int, int,        \
                                 cudaStream_t);                                                                      \
-  template void launch_adj_cell<T>(const Geo&, Ctrl*, const Dof*, const T*, const T*, int, T*, long long, T*, T*,  \
-                                   int, int, const void*, int, cudaStream_t);                                       \
+  template void launch_adj_cell<T>(const Geo&, const Ctrl*, const Dof*, const T*, const T*, int, T*, long long, T*, \
+                                   T*, int, int, cudaStream_t);                                                     \
   template void launch_adj_design<T>(const Geo&, Ctrl*, const Dof*, const T*, const T*, double*, void*, int, int,    \
-                                     int, cudaStream_t);                                                            \
-  template void launch_design_finish_last<T>(const Geo&, Ctrl*, const Dof*, const void*, int, cudaStream_t);       \
+                                     cudaStream_t);                                                                 \
   template void launch_init_forward<T>(const Geo&, const Slots<T>&, const double*, const double*, const double*,     \
                                        Dof*, Ctrl*, cudaStream_t);                                                  \
   template void launch_ckpt_pack<T>(const Geo&, const Slots<T>&, T*, long long, int, const Ctrl*, int, cudaStream_t);

@@ -110,8 +110,7 @@ struct Ctrl {
   int status;             // ST_* bits
   int pad;
   unsigned count[CNT_N];  // last-block counters, one per kernel family
-  double lam_prev[2][kNdofFree];  // adjoint: direct EOM part of dJ/ds(t-1), double-buffered: the EOM
-                                 // reverse of reverse pass r reads [(r+1)&1] and writes [r&1]
+  double lam_prev[kNdofFree];  // adjoint: direct EOM part of dJ/ds(t-1)
   double lam_F[3];        // adjoint: dJ/dF of the iteration being reversed
   double lam_T[3];        // adjoint: dJ/dT (about the axis in [0], or the vector with free rotation)
   double lam_s0[kNdofFree];  // adjoint: dJ/ds(0) after the sweep

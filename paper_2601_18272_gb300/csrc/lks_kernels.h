@@ -77,22 +77,15 @@ void launch_apply(const Geo& g, const Slots<T>& S, const Ctrl* ctrl, const Dof* 
                   int nbox, int di, cudaStream_t st);
 
 // Reverse of coupling iteration k: cell side (Brinkman and interpolation reverse)...
-// With one rotation axis it first finishes the previous reverse pass from the design-point partials
-// dparts (the EOM reverse; nt = N_t fixes the pass index).
 template <typename T>
-void launch_adj_cell(const Geo& g, Ctrl* ctrl, const Dof* it, const T* kref, const T* boxstore, int nbox, T* Lb,
-                     long long lstride, T* acc, T* scratch, int k, int di, const void* dparts, int nt, cudaStream_t st);
+void launch_adj_cell(const Geo& g, const Ctrl* ctrl, const Dof* it, const T* kref, const T* boxstore, int nbox, T* Lb,
+                     long long lstride, T* acc, T* scratch, int k, int di, cudaStream_t st);
 
 // ... and design-point side (spread/transform reverse, dJ/dkappa^ref, per-CTA partials of
-// dJ/ds^(k-1)); with free rotation a one-CTA finish kernel then runs the EOM reverse.
+// dJ/ds^(k-1)), then a one-CTA finish kernel with the EOM reverse of the previous iteration.
 template <typename T>
 void launch_adj_design(const Geo& g, Ctrl* ctrl, const Dof* it, const T* kref, const T* scratch, double* dkref,
-                       void* partials, int k, int di, int nt, cudaStream_t st);
-
-// The EOM reverse of the sweep's last reverse pass (step 1, iteration 1) with one rotation axis,
-// whose finish no later cell kernel folds in.
-template <typename T>
-void launch_design_finish_last(const Geo& g, Ctrl* ctrl, const Dof* it, const void* partials, int nt, cudaStream_t st);
+                       void* partials, int k, int di, cudaStream_t st);
 
 // Initial state (double) -> slot(0); s0 -> it row 0; ctrl reset for a forward (t0 = 1, base 0).
 template <typename T>
