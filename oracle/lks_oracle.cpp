@@ -42,6 +42,15 @@
 // belong to the body (a ball-shaped design domain); the others take no part in any sum and
 // their sensitivity is zero.
 //
+// Design chain (Sec. 3.2, Sec. 4.2): the design variables gamma are first expanded cyclically
+// (cyclic_order 2 or 4: the value at a point is that of its orbit's representative, the point of
+// smallest index among its images under rotations by 360/order degrees about the design-grid
+// centre in the plane normal to rot_axis), then filtered (Eq. filter: conic weights
+// (R - |x_i - x_j|) / R within the filter radius R over the design domain, normalised), then
+// projected (Eq. projection, parameters beta and eta); the result gamma-bar enters the Brinkman
+// coefficient and the volume constraint G = sum gamma-bar / (V_min N_dom) - 1 (Eq. constraint, N_dom
+// the number of design points in the domain). Radius 0, beta 0 or order 1 skip the step.
+//
 // Templated on the scalar type: double, and std::complex<double> for complex-step derivatives.
 // Every branch (kernel support, floor, bilinear sign) is taken on the real part.
 
@@ -88,6 +97,10 @@ extern "C" struct OracleProblem {
   double obj_w[21];    // J = sum_d obj_w[d] * s_d(N_t) over the DOF vector
   double inertia_tensor[9];  // free rotation: body-frame inertia tensor about the pivot
   double design_radius;      // > 0: ball-shaped design domain |r_m| <= design_radius
+  double filter_radius;      // density filter radius R (0: no filter)
+  double proj_beta, proj_eta;  // Heaviside projection (beta 0: no projection)
+  double v_min;              // minimum volume ratio of the constraint
+  int cyclic_order;          // 1 (none), 2 or 4
 };
 
 namespace {
@@ -145,6 +158,7 @@ struct Ctx {
   int err = ORC_OK;
   std::vector<double> r;  // r_m = xi_m - xi^G, [ND][3]
   std::vector<char> dom;  // design point m belongs to the design domain
+  std::vector<size_t> rep;  // representative of m's orbit under the cyclic rotations
   bool free_rot = false;  // six DOFs
   int ns = 8;             // DOF vector length: 8, or 21 with free rotation
   double Jinv[9];         // free rotation: I_b^-1
@@ -162,6 +176,39 @@ bool invert3(const double* a, double* inv) {
   // inverse = adjugate / det, the adjugate being the transposed cofactor matrix
   const double adj[9] = {c00, c10, c20, c01, c11, c21, c02, c12, c22};
   for (int i = 0; i < 9; ++i) inv[i] = adj[i] / det;
+  return true;
+}
+
+// Orbit representatives of the cyclic expansion: the rotation by 90 degrees (order 4) or 180
+// degrees (order 2) about the design-grid centre in the plane (b, c) normal to rot_axis maps
+// (i_b, i_c) to (n - 1 - i_c, i_b) or (n_b - 1 - i_b, n_c - 1 - i_c).
+bool make_cyclic(Ctx* C) {
+  const int order = C->P.cyclic_order;
+  C->rep.resize(C->ND);
+  for (size_t m = 0; m < C->ND; ++m) C->rep[m] = m;
+  if (order == 1) return true;
+  if (order != 2 && order != 4) return false;
+  if (C->P.rot_axis < 0) return false;
+  const int ax = C->P.rot_axis, b = (ax + 1) % 3, c = (ax + 2) % 3;
+  if (order == 4 && C->nd[b] != C->nd[c]) return false;
+  for (size_t m = 0; m < C->ND; ++m) {
+    int i[3] = {(int)(m % C->nd[0]), (int)((m / C->nd[0]) % C->nd[1]), (int)(m / ((size_t)C->nd[0] * C->nd[1]))};
+    size_t best = m;
+    for (int k = 1; k < order; ++k) {
+      int j[3] = {i[0], i[1], i[2]};
+      if (order == 4) {
+        j[b] = C->nd[c] - 1 - i[c];
+        j[c] = i[b];
+      } else {
+        j[b] = C->nd[b] - 1 - i[b];
+        j[c] = C->nd[c] - 1 - i[c];
+      }
+      for (int a = 0; a < 3; ++a) i[a] = j[a];
+      const size_t mj = (size_t)i[0] + C->nd[0] * ((size_t)i[1] + (size_t)C->nd[1] * i[2]);
+      if (mj < best) best = mj;
+    }
+    C->rep[m] = best;
+  }
   return true;
 }
 
@@ -200,6 +247,7 @@ bool make_ctx(const OracleProblem* P, Ctx* C) {
         C->r[3 * m + 1] = j - (C->nd[1] - 1) / 2.0;
         C->r[3 * m + 2] = (C->d == 3) ? k - (C->nd[2] - 1) / 2.0 : 0.0;
       }
+  if (!make_cyclic(C)) return false;
   C->dom.assign(C->ND, 1);
   if (P->design_radius > 0.0)
     for (size_t m = 0; m < C->ND; ++m) {
@@ -771,12 +819,109 @@ void forward_step(Ctx& C, const std::vector<T>& kref, const Fields<T>& prev, con
   if (iters_out) *iters_out = it;
 }
 
-// Brinkman interpolation (Eq. brinkman_coefficient).
+// The design chain (cyclic expansion, Eq. filter, Eq. projection) from gamma to gamma-bar.
 template <class T>
-std::vector<T> brinkman(const Ctx& C, const T* gamma) {
+struct Chain {
+  std::vector<T> g1, g2, g3;  // expanded, filtered, projected
+  std::vector<double> W;      // filter normaliser sum_j w_ij
+};
+
+// Filter neighbours of design point i: (j, w_ij) with |x_i - x_j| <= R, both in the domain.
+void filter_nbrs(const Ctx& C, size_t i, std::vector<std::pair<size_t, double>>* out) {
+  out->clear();
+  const double R = C.P.filter_radius;
+  const int rr = (int)std::floor(R);
+  const int ii[3] = {(int)(i % C.nd[0]), (int)((i / C.nd[0]) % C.nd[1]), (int)(i / ((size_t)C.nd[0] * C.nd[1]))};
+  const int ext[3] = {rr, rr, C.d == 3 ? rr : 0};
+  for (int dz = -ext[2]; dz <= ext[2]; ++dz)
+    for (int dy = -ext[1]; dy <= ext[1]; ++dy)
+      for (int dx = -ext[0]; dx <= ext[0]; ++dx) {
+        const int j[3] = {ii[0] + dx, ii[1] + dy, ii[2] + dz};
+        bool ok = true;
+        for (int a = 0; a < 3; ++a) ok = ok && j[a] >= 0 && j[a] < C.nd[a];
+        if (!ok) continue;
+        const double dist = std::sqrt((double)(dx * dx + dy * dy + dz * dz));
+        if (dist > R) continue;
+        const size_t mj = (size_t)j[0] + C.nd[0] * ((size_t)j[1] + (size_t)C.nd[1] * j[2]);
+        if (!C.dom[mj]) continue;
+        out->push_back({mj, (R - dist) / R});
+      }
+}
+
+template <class T>
+T project(const Ctx& C, T x) {
+  const double b = C.P.proj_beta, e = C.P.proj_eta;
+  return (std::tanh(b * e) + std::tanh(b * (x - e))) / (std::tanh(b * e) + std::tanh(b * (1.0 - e)));
+}
+
+template <class T>
+void design_chain(const Ctx& C, const T* gamma, Chain<T>* ch) {
+  const size_t ND = C.ND;
+  ch->g1.assign(ND, T(0));
+  ch->g2.assign(ND, T(0));
+  ch->g3.assign(ND, T(0));
+  ch->W.assign(ND, 1.0);
+  for (size_t m = 0; m < ND; ++m) ch->g1[m] = gamma[C.rep[m]];
+  std::vector<std::pair<size_t, double>> nb;
+  for (size_t i = 0; i < ND; ++i) {
+    if (!C.dom[i]) continue;
+    if (C.P.filter_radius > 0.0) {
+      filter_nbrs(C, i, &nb);
+      T acc = T(0);
+      double W = 0.0;
+      for (auto& q : nb) {
+        acc += q.second * ch->g1[q.first];
+        W += q.second;
+      }
+      ch->W[i] = W;
+      ch->g2[i] = acc / W;
+    } else {
+      ch->g2[i] = ch->g1[i];
+    }
+    ch->g3[i] = (C.P.proj_beta > 0.0) ? project(C, ch->g2[i]) : ch->g2[i];
+  }
+}
+
+// dJ/dgamma from dJ/dgamma-bar (gb3): the transposes of the projection, the filter (its weights are
+// symmetric in i and j) and the cyclic expansion (a sum over each orbit onto its representative).
+void design_chain_vjp(const Ctx& C, const Chain<double>& ch, const std::vector<double>& gb3, double* out) {
+  const size_t ND = C.ND;
+  std::vector<double> gb2(ND, 0.0), gb1(ND, 0.0);
+  const double b = C.P.proj_beta, e = C.P.proj_eta;
+  for (size_t i = 0; i < ND; ++i) {
+    if (!C.dom[i]) continue;
+    if (b > 0.0) {
+      const double th = std::tanh(b * (ch.g2[i] - e));
+      gb2[i] = gb3[i] * b * (1.0 - th * th) / (std::tanh(b * e) + std::tanh(b * (1.0 - e)));
+    } else {
+      gb2[i] = gb3[i];
+    }
+  }
+  if (C.P.filter_radius > 0.0) {
+    std::vector<std::pair<size_t, double>> nb;
+    for (size_t i = 0; i < ND; ++i) {
+      if (!C.dom[i]) continue;
+      filter_nbrs(C, i, &nb);
+      for (auto& q : nb) gb1[q.first] += q.second / ch.W[i] * gb2[i];
+    }
+  } else {
+    gb1 = gb2;
+  }
+  for (size_t m = 0; m < ND; ++m) out[m] = 0.0;
+  for (size_t m = 0; m < ND; ++m) out[C.rep[m]] += gb1[m];
+}
+
+// Brinkman interpolation (Eq. brinkman_coefficient) of gamma-bar, after the design chain.
+template <class T>
+std::vector<T> brinkman(const Ctx& C, const T* gamma, Chain<T>* keep = nullptr) {
+  Chain<T> local;
+  Chain<T>* ch = keep ? keep : &local;
+  design_chain(C, gamma, ch);
   std::vector<T> k(C.ND);
-  for (size_t m = 0; m < C.ND; ++m)
-    k[m] = C.dom[m] ? C.P.kappa_max * C.P.q * gamma[m] / ((1.0 - gamma[m]) + C.P.q) : T(0);
+  for (size_t m = 0; m < C.ND; ++m) {
+    const T gb = ch->g3[m];
+    k[m] = C.dom[m] ? C.P.kappa_max * C.P.q * gb / ((1.0 - gb) + C.P.q) : T(0);
+  }
   return k;
 }
 
@@ -1122,7 +1267,8 @@ int oracle_gradient(const OracleProblem* P, const double* gamma, const double* p
   Ctx C;
   if (!make_ctx(P, &C)) return ORC_ERR_ARG;
   if (P->nu <= 0.0) return ORC_ERR_UNSTABLE;
-  std::vector<double> kref = brinkman(C, gamma);
+  Chain<double> chain;
+  std::vector<double> kref = brinkman(C, gamma, &chain);
   Trajectory tr;
   run_forward(C, kref, p0, u0, dof0, &tr, true);
   if (C.err) return C.err;
@@ -1167,12 +1313,14 @@ int oracle_gradient(const OracleProblem* P, const double* gamma, const double* p
     for (int a = 0; a < ns; ++a) lam_s[a] = lam_prev[a];
   }
   if (C.err) return C.err;
+  std::vector<double> gb3(C.ND, 0.0);
   for (size_t m = 0; m < C.ND; ++m) {
-    double den = (1.0 - gamma[m]) + P->q;
-    double dkdg = P->kappa_max * P->q * (1.0 + P->q) / (den * den);
-    if (dJdgamma) dJdgamma[m] = dk[m] * dkdg;
+    // dkappa/dgamma-bar at gamma-bar (Eq. brinkman_coefficient), then the chain's transpose
+    const double den = (1.0 - chain.g3[m]) + P->q;
+    gb3[m] = C.dom[m] ? dk[m] * P->kappa_max * P->q * (1.0 + P->q) / (den * den) : 0.0;
     if (dJdkref) dJdkref[m] = dk[m];
   }
+  if (dJdgamma) design_chain_vjp(C, chain, gb3, dJdgamma);
   if (lam_p0)
     for (size_t n = 0; n < C.N; ++n) lam_p0[n] = lam.p[n];
   if (lam_u0)
@@ -1327,6 +1475,63 @@ int oracle_interp(const OracleProblem* P, const double* s, const double* u, doub
       for (int a = 0; a < C.d; ++a) uref[3 * m + a] += wv[q] * u[(size_t)a * C.N + wn[q].n];
   }
   return C.err;
+}
+
+// gamma-bar [ND] of the design chain (cyclic expansion, filter, projection) for gamma [ND].
+int oracle_design_chain(const OracleProblem* P, const double* gamma, double* gbar) {
+  Ctx C;
+  if (!make_ctx(P, &C)) return ORC_ERR_ARG;
+  Chain<double> ch;
+  design_chain(C, gamma, &ch);
+  for (size_t m = 0; m < C.ND; ++m) gbar[m] = ch.g3[m];
+  return ORC_OK;
+}
+
+// Transpose of the design chain at gamma: out = (d gamma-bar / d gamma)^T v, v [ND].
+int oracle_design_chain_vjp(const OracleProblem* P, const double* gamma, const double* v, double* out) {
+  Ctx C;
+  if (!make_ctx(P, &C)) return ORC_ERR_ARG;
+  Chain<double> ch;
+  design_chain(C, gamma, &ch);
+  std::vector<double> gb3(v, v + C.ND);
+  design_chain_vjp(C, ch, gb3, out);
+  return ORC_OK;
+}
+
+// Complex-step directional derivative of gamma-bar along dgamma: out = Im gbar(gamma + i h v) / h.
+int oracle_design_chain_jvp(const OracleProblem* P, const double* gamma, const double* v, double h, double* out) {
+  Ctx C;
+  if (!make_ctx(P, &C)) return ORC_ERR_ARG;
+  std::vector<cplx> g(C.ND);
+  for (size_t m = 0; m < C.ND; ++m) g[m] = cplx(gamma[m], h * v[m]);
+  Chain<cplx> ch;
+  design_chain(C, g.data(), &ch);
+  for (size_t m = 0; m < C.ND; ++m) out[m] = ch.g3[m].imag() / h;
+  return ORC_OK;
+}
+
+// Volume constraint (Eq. constraint) G = sum_dom gamma-bar / (V_min N_dom) - 1 and dG/dgamma.
+int oracle_constraint(const OracleProblem* P, const double* gamma, double* G, double* dGdgamma) {
+  Ctx C;
+  if (!make_ctx(P, &C)) return ORC_ERR_ARG;
+  if (!(P->v_min > 0.0)) return ORC_ERR_ARG;
+  Chain<double> ch;
+  design_chain(C, gamma, &ch);
+  size_t ndom = 0;
+  double sum = 0.0;
+  for (size_t m = 0; m < C.ND; ++m)
+    if (C.dom[m]) {
+      ++ndom;
+      sum += ch.g3[m];
+    }
+  const double scale = 1.0 / (P->v_min * (double)ndom);
+  if (G) *G = sum * scale - 1.0;
+  if (dGdgamma) {
+    std::vector<double> gb3(C.ND, 0.0);
+    for (size_t m = 0; m < C.ND; ++m) gb3[m] = C.dom[m] ? scale : 0.0;
+    design_chain_vjp(C, ch, gb3, dGdgamma);
+  }
+  return ORC_OK;
 }
 
 // One weight-kernel value w(r) and derivative, for the kernel tests.

@@ -34,6 +34,11 @@ class OracleProblem(ctypes.Structure):
         ("obj_w", ctypes.c_double * 21),
         ("inertia_tensor", ctypes.c_double * 9),
         ("design_radius", ctypes.c_double),
+        ("filter_radius", ctypes.c_double),
+        ("proj_beta", ctypes.c_double),
+        ("proj_eta", ctypes.c_double),
+        ("v_min", ctypes.c_double),
+        ("cyclic_order", ctypes.c_int),
     ]
 
 
@@ -63,6 +68,10 @@ def lib():
         L.oracle_weight.restype = ctypes.c_double
         L.oracle_lattice.argtypes = [ctypes.c_int, ip, dp]
         L.oracle_dof_count.argtypes = [pp]
+        L.oracle_design_chain.argtypes = [pp, dp, dp]
+        L.oracle_design_chain_vjp.argtypes = [pp, dp, dp, dp]
+        L.oracle_design_chain_jvp.argtypes = [pp, dp, dp, ctypes.c_double, dp]
+        L.oracle_constraint.argtypes = [pp, dp, dp, dp]
         if L.oracle_sizeof_problem() != ctypes.sizeof(OracleProblem):
             raise RuntimeError("oracle problem record layout mismatch")
         _lib = L
@@ -108,6 +117,10 @@ def problem_record(P, n_steps: Optional[int] = None) -> OracleProblem:
     for a in range(9):
         r.inertia_tensor[a] = P.inertia_tensor[a]
     r.design_radius = P.design_radius
+    r.filter_radius = P.filter_radius
+    r.proj_beta, r.proj_eta = P.proj_beta, P.proj_eta
+    r.v_min = P.v_min
+    r.cyclic_order = P.cyclic_order
     return r
 
 
@@ -233,3 +246,34 @@ def lattice(dim: int):
     w = np.zeros(15)
     Q = lib().oracle_lattice(dim, c.ctypes.data_as(ctypes.POINTER(ctypes.c_int)), _ptr(w))
     return c[:Q].copy(), w[:Q].copy()
+
+
+def design_chain(P, gamma):
+    """gamma-bar [N_D]: cyclic expansion, density filter and Heaviside projection of gamma."""
+    out = np.zeros(P.n_design)
+    _check(lib().oracle_design_chain(ctypes.byref(problem_record(P)), _ptr(_f64(gamma)), _ptr(out)))
+    return out
+
+
+def design_chain_vjp(P, gamma, v):
+    """(d gamma-bar / d gamma)^T v at gamma."""
+    out = np.zeros(P.n_design)
+    _check(lib().oracle_design_chain_vjp(ctypes.byref(problem_record(P)), _ptr(_f64(gamma)), _ptr(_f64(v)),
+                                         _ptr(out)))
+    return out
+
+
+def design_chain_jvp(P, gamma, v, h: float = 1e-30):
+    """Complex-step (d gamma-bar / d gamma) v at gamma."""
+    out = np.zeros(P.n_design)
+    _check(lib().oracle_design_chain_jvp(ctypes.byref(problem_record(P)), _ptr(_f64(gamma)), _ptr(_f64(v)), h,
+                                         _ptr(out)))
+    return out
+
+
+def constraint(P, gamma):
+    """(G, dG/dgamma) of the volume constraint on gamma-bar."""
+    G = ctypes.c_double(0.0)
+    d = np.zeros(P.n_design)
+    _check(lib().oracle_constraint(ctypes.byref(problem_record(P)), _ptr(_f64(gamma)), ctypes.byref(G), _ptr(d)))
+    return G.value, d

@@ -164,6 +164,11 @@ class Problem:
     seed: int = 0
     inertia_tensor: tuple = (0.0,) * 9  # free rotation: body-frame inertia about the pivot
     design_radius: float = 0.0          # > 0: ball-shaped design domain |r_m| <= design_radius
+    filter_radius: float = 0.0          # density filter radius (0: no filter)
+    proj_beta: float = 0.0              # Heaviside projection steepness (0: no projection)
+    proj_eta: float = 0.5               # Heaviside projection threshold
+    v_min: float = 0.25                 # minimum volume ratio of the constraint
+    cyclic_order: int = 1               # cyclic expansion of the design about the rotation axis: 1, 2, 4
 
     @property
     def n_cells(self) -> int:
