@@ -88,6 +88,15 @@ typedef struct lks_problem {
   double design_radius;   /* > 0: the design domain is the ball |r_m| <= design_radius (r_m = xi_m - xi^G);
                            * design points outside it take no part in any sum and get dJ/dgamma = 0.
                            * 0: the whole design grid */
+  double filter_radius;   /* density filter radius R in design cells (Sec. 3.2, Eq. filter); 0: no filter */
+  double proj_beta, proj_eta; /* Heaviside projection (Eq. projection); proj_beta 0: no projection,
+                           * else 0 < proj_eta < 1 */
+  double v_min;           /* minimum volume ratio of the constraint (Eq. constraint), used by lks_constraint */
+  int cyclic_order;       /* cyclic periodic design (Sec. 4.2): 1 (none), 2 or 4; the design is expanded
+                           * from each orbit's representative (smallest index) under rotations by
+                           * 360/order degrees about the design-grid centre in the plane normal to
+                           * rot_axis (order 4 needs equal extents in that plane; not with
+                           * LKS_ROT_FREE) */
   double nu;              /* kinematic viscosity; A = 9/2 (1/6 - nu) */
   double u_in;            /* inflow speed for LKS_BC_INFLOW_OUTFLOW */
   double dp;              /* inlet pressure for LKS_BC_PRESSURE (outlet p = 0) */
@@ -138,9 +147,17 @@ LKS_API int lks_forward(lks_handle* h, const double* gamma_dev, double* J_host, 
 LKS_API int lks_adjoint(lks_handle* h, double seed, void* stream);
 
 /* dJ/dgamma [ndx*ndy*ndz] (device, FP64) from the last adjoint: the accumulated dJ/dkappa^ref
- * chained through dkappa^ref/dgamma (Eq. brinkman_coefficient). M and I are held constant.
- * Requires a prior lks_adjoint (else LKS_ERR_ORDER). Enqueued, no synchronisation. */
+ * chained through dkappa^ref/dgamma-bar (Eq. brinkman_coefficient) and the transpose of the design
+ * chain (projection, filter, cyclic expansion: only orbit representatives receive sensitivity).
+ * M and I are held constant. Requires a prior lks_adjoint (else LKS_ERR_ORDER). Enqueued, no
+ * synchronisation. */
 LKS_API int lks_sensitivity(lks_handle* h, double* dJdgamma_dev, void* stream);
+
+/* Volume constraint (Eq. constraint) of the design gamma_dev [N_D] (device): G = sum of gamma-bar over
+ * the design domain / (v_min * its point count) - 1 into G_host, and dG/dgamma [N_D] (device, FP64,
+ * through the design chain) into dGdgamma_dev if not NULL. Synchronises the stream to return G.
+ * Errors: LKS_ERR_ARG (v_min <= 0, NULL pointers), LKS_ERR_CUDA. */
+LKS_API int lks_constraint(lks_handle* h, const double* gamma_dev, double* G_host, double* dGdgamma_dev, void* stream);
 
 /* End-to-end gradient with host buffers: copies gamma_host [N_D] to the device, runs forward,
  * adjoint (seed 1) and sensitivity, copies dJdgamma_host [N_D] back and returns J.

@@ -66,6 +66,11 @@ struct lks_handle {
   double* dkref = nullptr;
   double* gamma = nullptr;
   double* tmp_nd = nullptr;
+  // design chain of the last forward (gbar feeds kappa^ref; gtil and the filter normaliser W serve
+  // the transpose), of lks_constraint, and scratch for the transposes
+  double *cg1 = nullptr, *cgtil = nullptr, *cgbar = nullptr, *cW = nullptr;
+  double *kg1 = nullptr, *kgtil = nullptr, *kgbar = nullptr, *kW = nullptr;
+  double *dv = nullptr, *dtmp = nullptr, *vol = nullptr;
   Dof* it = nullptr;
   Ctrl* ctrl = nullptr;
   Moments* mom = nullptr;
@@ -200,6 +205,16 @@ int validate(const lks_problem* P) {
     return LKS_ERR_ARG;
   }
   if (!(P->design_radius >= 0.0) || !std::isfinite(P->design_radius)) return LKS_ERR_ARG;
+  if (!(P->filter_radius >= 0.0) || !std::isfinite(P->filter_radius)) return LKS_ERR_ARG;
+  if (!(P->proj_beta >= 0.0) || !std::isfinite(P->proj_beta)) return LKS_ERR_ARG;
+  if (P->proj_beta > 0.0 && !(P->proj_eta > 0.0 && P->proj_eta < 1.0)) return LKS_ERR_ARG;
+  if (P->cyclic_order != 1 && P->cyclic_order != 2 && P->cyclic_order != 4) return LKS_ERR_ARG;
+  if (P->cyclic_order > 1) {
+    if (P->rot_axis == LKS_ROT_FREE) return LKS_ERR_ARG;
+    const int nd[3] = {P->ndx, P->ndy, P->dim == 3 ? P->ndz : 1};
+    const int b = (P->rot_axis + 1) % 3, c = (P->rot_axis + 2) % 3;
+    if (P->cyclic_order == 4 && nd[b] != nd[c]) return LKS_ERR_ARG;
+  }
   if (P->bc[0] != LKS_BC_PERIODIC && P->bc[0] != LKS_BC_INFLOW_OUTFLOW && P->bc[0] != LKS_BC_PRESSURE) return LKS_ERR_ARG;
   for (int a = 1; a < 3; ++a)
     if (P->bc[a] != LKS_BC_PERIODIC && P->bc[a] != LKS_BC_WALL) return LKS_ERR_ARG;
@@ -595,6 +610,9 @@ int allocate(lks_handle* h) {
   TRY(dalloc(h, (void**)&h->dkref, (size_t)g.ND * sizeof(double)));
   TRY(dalloc(h, (void**)&h->gamma, (size_t)g.ND * sizeof(double)));
   TRY(dalloc(h, (void**)&h->tmp_nd, (size_t)g.ND * sizeof(double)));
+  double** chain_bufs[] = {&h->cg1, &h->cgtil, &h->cgbar, &h->cW, &h->kg1, &h->kgtil, &h->kgbar, &h->kW, &h->dv, &h->dtmp};
+  for (double** b : chain_bufs) TRY(dalloc(h, (void**)b, (size_t)g.ND * sizeof(double)));
+  TRY(dalloc(h, (void**)&h->vol, 2 * sizeof(double)));
   TRY(dalloc(h, (void**)&h->it, (size_t)(NT + 1) * (K + 1) * sizeof(Dof)));
   TRY(dalloc(h, (void**)&h->ctrl, sizeof(Ctrl)));
   TRY(dalloc(h, (void**)&h->mom, sizeof(Moments)));
@@ -717,6 +735,10 @@ int lks_create(const lks_problem* P, lks_handle** out) {
     g.axc = (g.ax + 2) % 3;
     g.ns = kNdofAxis;
   }
+  g.frad = P->filter_radius;
+  g.pbeta = P->proj_beta;
+  g.peta = P->proj_eta;
+  g.cyc = P->cyclic_order;
   // design domain 4 |r_m|^2 <= rad4, compared in integers (4 |r_m|^2 is an integer)
   g.rad4 = INT_MAX;
   if (P->design_radius > 0.0) {
@@ -785,10 +807,12 @@ int lks_forward(lks_handle* h, const double* gamma_dev, double* J_host, void* st
   if ((const void*)gamma_dev != (const void*)h->gamma)
     CK(cudaMemcpyAsync(h->gamma, gamma_dev, (size_t)g.ND * sizeof(double), cudaMemcpyDeviceToDevice, st));
   Launcher L0{h, st, false};
+  // design chain gamma -> gamma-bar (Sec. 3.2, 4.2), then kappa^ref of gamma-bar
+  L0.n("prep", 2, [&](cudaStream_t s) { launch_design_chain(g, h->gamma, h->cg1, h->cgtil, h->cgbar, h->cW, s); });
   if (h->prec == LKS_FP64)
-    L0("prep", [&](cudaStream_t s) { launch_prep<double>(g, h->gamma, h->P.kappa_max, h->P.q, (double*)h->kref, h->mom, h->partials, h->ctrl, s); });
+    L0("prep", [&](cudaStream_t s) { launch_prep<double>(g, h->cgbar, h->P.kappa_max, h->P.q, (double*)h->kref, h->mom, h->partials, h->ctrl, s); });
   else
-    L0("prep", [&](cudaStream_t s) { launch_prep<float>(g, h->gamma, h->P.kappa_max, h->P.q, (float*)h->kref, h->mom, h->partials, h->ctrl, s); });
+    L0("prep", [&](cudaStream_t s) { launch_prep<float>(g, h->cgbar, h->P.kappa_max, h->P.q, (float*)h->kref, h->mom, h->partials, h->ctrl, s); });
   int r = (h->prec == LKS_FP64) ? forward_impl<double>(h, st) : forward_impl<float>(h, st);
   if (r != LKS_OK) return r;
   Dof last;
@@ -825,8 +849,32 @@ int lks_sensitivity(lks_handle* h, double* out, void* stream) {
   if (!h || !out) return LKS_ERR_ARG;
   if (!h->adj_done) return LKS_ERR_ORDER;
   cudaStream_t st = (cudaStream_t)stream;
-  launch_sensitivity(h->g, h->gamma, h->dkref, h->P.kappa_max, h->P.q, out, st);
-  ++h->launches;
+  // dJ/dgamma-bar at gamma-bar, then the transpose of the design chain
+  launch_sensitivity(h->g, h->cgbar, h->dkref, h->P.kappa_max, h->P.q, h->dv, st);
+  launch_design_chain_T(h->g, h->cgtil, h->cW, h->dv, h->dtmp, out, st);
+  h->launches += 4;
+  CK(cudaGetLastError());
+  return LKS_OK;
+}
+
+int lks_constraint(lks_handle* h, const double* gamma_dev, double* G_host, double* dGdgamma_dev, void* stream) {
+  if (!h || !gamma_dev || !G_host) return LKS_ERR_ARG;
+  if (!(h->P.v_min > 0.0)) return LKS_ERR_ARG;
+  cudaStream_t st = (cudaStream_t)stream;
+  const Geo& g = h->g;
+  launch_design_chain(g, gamma_dev, h->kg1, h->kgtil, h->kgbar, h->kW, st);
+  launch_volume(g, h->kgbar, h->vol, st);
+  double vol[2];
+  CK(cudaMemcpyAsync(vol, h->vol, sizeof(vol), cudaMemcpyDeviceToHost, st));
+  CK(cudaStreamSynchronize(st));
+  const double scale = 1.0 / (h->P.v_min * vol[1]);
+  *G_host = vol[0] * scale - 1.0;
+  h->launches += 3;
+  if (dGdgamma_dev) {
+    launch_fill_domain(g, scale, h->dv, st);
+    launch_design_chain_T(g, h->kgtil, h->kW, h->dv, h->dtmp, dGdgamma_dev, st);
+    h->launches += 4;
+  }
   CK(cudaGetLastError());
   return LKS_OK;
 }

@@ -140,6 +140,8 @@ struct Geo {
   int ns;            // DOF vector length
   int rad4;          // design domain: 4|r_m|^2 <= rad4 (an integer test; INT_MAX for the whole grid)
   double Jinv[9];    // free rotation: I_b^-1
+  double frad, pbeta, peta;  // design chain: filter radius, projection steepness and threshold
+  int cyc;           // design chain: cyclic expansion order (1: none)
   int dof_mask;
   int wk, s;      // weight kind, support half-width (2 for cos4, 1 for bilinear)
   int K;          // N_itr

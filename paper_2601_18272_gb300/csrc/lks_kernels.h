@@ -87,6 +87,19 @@ template <typename T>
 void launch_adj_design(const Geo& g, Ctrl* ctrl, const Dof* it, const T* kref, const T* scratch, double* dkref,
                        void* partials, int k, int di, cudaStream_t st);
 
+// Design chain (cyclic expansion, density filter, Heaviside projection) gamma -> gbar, keeping the
+// filtered field gtil and the filter normaliser W for the transpose; active unless every step is off.
+bool design_chain_active(const Geo& g);
+void launch_design_chain(const Geo& g, const double* gamma, double* g1, double* gtil, double* gbar, double* W,
+                         cudaStream_t st);
+// Transpose: out = (dgbar/dgamma)^T v; v and tmp are overwritten.
+void launch_design_chain_T(const Geo& g, const double* gtil, const double* W, double* v, double* tmp, double* out,
+                           cudaStream_t st);
+// out2[0] = sum of gbar over the design domain, out2[1] = the domain's point count.
+void launch_volume(const Geo& g, const double* gbar, double* out2, cudaStream_t st);
+// out = value on the design domain, 0 elsewhere.
+void launch_fill_domain(const Geo& g, double value, double* out, cudaStream_t st);
+
 // Initial state (double) -> slot(0); s0 -> it row 0; ctrl reset for a forward (t0 = 1, base 0).
 template <typename T>
 void launch_init_forward(const Geo& g, const Slots<T>& S, const double* p0, const double* u0, const double* s0dev,
@@ -99,8 +112,8 @@ void launch_set_step(Ctrl* ctrl, int t0, int base, cudaStream_t st);
 void launch_adj_init(const Geo& g, Ctrl* ctrl, const Dof* it, int nt, const double* objw, double seed, double* dkref,
                      int nd, cudaStream_t st);
 
-// dJ/dgamma = dJ/dkappa^ref * dkappa^ref/dgamma.
-void launch_sensitivity(const Geo& g, const double* gamma, const double* dkref, double kappa_max, double q,
+// dJ/dgamma-bar = dJ/dkappa^ref * dkappa^ref/dgamma-bar at gamma-bar (Eq. brinkman_coefficient).
+void launch_sensitivity(const Geo& g, const double* gbar, const double* dkref, double kappa_max, double q,
                         double* out, cudaStream_t st);
 
 // Reduced-precision checkpoint (FP32 fields) of the state at step ctrl->t0 + di into checkpoint

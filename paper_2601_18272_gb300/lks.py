@@ -39,6 +39,11 @@ class lks_problem(ctypes.Structure):  # noqa: N801  (mirrors the C struct name)
         ("inertia", ctypes.c_double),
         ("inertia_tensor", ctypes.c_double * 9),
         ("design_radius", ctypes.c_double),
+        ("filter_radius", ctypes.c_double),
+        ("proj_beta", ctypes.c_double),
+        ("proj_eta", ctypes.c_double),
+        ("v_min", ctypes.c_double),
+        ("cyclic_order", ctypes.c_int),
         ("nu", ctypes.c_double),
         ("u_in", ctypes.c_double),
         ("dp", ctypes.c_double),
@@ -104,6 +109,7 @@ def load() -> ctypes.CDLL:
     L.lks_last_cuda_error.argtypes = []
     L.lks_step_noalloc.argtypes = [ctypes.POINTER(lks_problem), vp, vp, ctypes.c_int, dp, vp]
     L.lks_dof_count.argtypes = [ctypes.POINTER(lks_problem)]
+    L.lks_constraint.argtypes = [hp, vp, dp, vp, vp]
     L.lks_problem_size.argtypes = []
     L.lks_problem_size.restype = ctypes.c_size_t
     if L.lks_problem_size() != ctypes.sizeof(lks_problem):
@@ -142,6 +148,10 @@ def problem_struct(P, precision: Optional[int] = None, ckpt_policy: Optional[int
     for a in range(9):
         s.inertia_tensor[a] = P.inertia_tensor[a]
     s.design_radius = P.design_radius
+    s.filter_radius = P.filter_radius
+    s.proj_beta, s.proj_eta = P.proj_beta, P.proj_eta
+    s.v_min = P.v_min
+    s.cyclic_order = P.cyclic_order
     s.kappa_max, s.q = P.kappa_max, P.q
     s.weight_kind = P.weight_kind
     s.n_steps = P.n_steps if n_steps is None else n_steps
@@ -192,6 +202,14 @@ def lks_gradient_host(h, gamma: np.ndarray, out: np.ndarray, stream: int = 0) ->
     _check(load().lks_gradient_host(h, _dptr(gamma), ctypes.byref(J), _dptr(out), ctypes.c_void_p(stream)),
            "lks_gradient_host")
     return J.value
+
+
+def lks_constraint(h, gamma_dev_ptr: int, dG_dev_ptr: int = 0, stream: int = 0) -> float:
+    G = ctypes.c_double(0.0)
+    _check(load().lks_constraint(h, ctypes.c_void_p(gamma_dev_ptr), ctypes.byref(G),
+                                 ctypes.c_void_p(dG_dev_ptr) if dG_dev_ptr else None, ctypes.c_void_p(stream)),
+           "lks_constraint")
+    return G.value
 
 
 def lks_dof_count(problem: lks_problem) -> int:
@@ -300,6 +318,12 @@ class Solver:
     @property
     def n_dof(self) -> int:
         return lks_dof_count(self.struct)
+
+    def constraint(self, gamma, dG=None, stream=None) -> float:
+        import torch
+        assert gamma.is_cuda and gamma.dtype == torch.float64 and gamma.is_contiguous()
+        st = torch.cuda.current_stream(gamma.device) if stream is None else stream
+        return lks_constraint(self.handle, gamma.data_ptr(), 0 if dG is None else dG.data_ptr(), st.cuda_stream)
 
     def dof_history(self) -> np.ndarray:
         return lks_get_dof_history(self.handle, self.n_steps, self.n_dof)

@@ -327,3 +327,43 @@ def test_binomial_fp32_3d_matches_oracle():
     r = gpu_run(P, g, p0, u0, s0, precision=32, ckpt_policy=CKPT_BINOMIAL, ckpt_every=2)
     assert abs(r["J"] - G["J"]) <= 1e-4 * abs(G["J"])
     assert rel(r["dJdgamma"], G["dJdgamma"]) <= 1e-3
+
+
+# ------------------------------------------------------------------ design chain ----------
+CHAIN_CASES = [
+    ("filter", dict(filter_radius=1.9)),
+    ("projection", dict(proj_beta=4.0, proj_eta=0.45)),
+    ("cyclic4-filter-projection", dict(filter_radius=2.2, proj_beta=3.0, proj_eta=0.5, cyclic_order=4)),
+    ("cyclic2-odd-grid", dict(cyclic_order=2, filter_radius=1.5)),
+]
+
+
+@pytest.mark.parametrize("name,kw", CHAIN_CASES, ids=[c[0] for c in CHAIN_CASES])
+def test_design_chain_gradient_matches_oracle(name, kw):
+    """Forward through gamma-bar and dJ/dgamma through the chain's transpose (FP64 fields)."""
+    nd = 9 if "odd" in name else 8
+    P, g = body2d(nd=nd, nx=30, ny=24, centre=(12.3, 11.8), mask=DOF_TX | DOF_ROT, nt=5)
+    P = P.replace(**kw)
+    p0, u0, s0 = perturbed_state(P)
+    G = O.gradient(P, g, p0, u0, s0)
+    r = gpu_run(P, g, p0, u0, s0, precision=64, ckpt_policy=CKPT_STORE_ALL)
+    assert abs(r["J"] - G["J"]) <= 1e-11 * abs(G["J"])
+    assert rel(r["dJdgamma"], G["dJdgamma"]) < 1e-9
+
+
+def test_volume_constraint_matches_oracle():
+    torch = _torch()
+    from paper_2601_18272_gb300.lks import Solver
+    P, g = body2d(nd=12, nx=40, ny=32, centre=(16.3, 15.8), bc=(BC_PERIODIC,) * 3)
+    P = P.replace(v_min=0.3, filter_radius=2.2, proj_beta=3.0, cyclic_order=4, design_radius=5.0)
+    Go, dGo = O.constraint(P, g)
+    S = Solver(P, precision=64)
+    try:
+        gam = torch.tensor(g, dtype=torch.float64, device="cuda")
+        dG = torch.empty_like(gam)
+        Gg = S.constraint(gam, dG)
+        torch.cuda.synchronize()
+        assert abs(Gg - Go) <= 1e-13 * max(abs(Go), 1.0)
+        np.testing.assert_allclose(dG.cpu().numpy(), dGo, rtol=1e-12, atol=1e-15)
+    finally:
+        S.close()
