@@ -1261,9 +1261,25 @@ int oracle_forward(const OracleProblem* P, const double* gamma, const double* p0
 // Forward + exact discrete adjoint with seed dJ = 1. Outputs J, dJ/dgamma [ND] and, when the
 // pointers are non-null, the adjoint of the initial state: dJ/dp0 [N], dJ/du0 [dim][N],
 // dJ/ds0 [ns], and dJ/dkappa^ref [ND].
+// The same with a terminal adjoint (the warm start of periodic problems, Sec. 3.4): the reverse sweep
+// starts from dJ/dp(N_t) = lam_pT [N], dJ/du(N_t) = lam_uT [dim][N] and dJ/ds(N_t) = w + lam_sT [ns],
+// i.e. it differentiates J + lam_pT.p(N_t) + lam_uT.u(N_t) + lam_sT.s(N_t). Any of the three may be NULL.
+int oracle_gradient_terminal(const OracleProblem* P, const double* gamma, const double* p0, const double* u0,
+                             const double* dof0, const double* lam_pT, const double* lam_uT, const double* lam_sT,
+                             double* J, double* dJdgamma, double* lam_p0, double* lam_u0, double* lam_dof0,
+                             double* dJdkref);
+
 int oracle_gradient(const OracleProblem* P, const double* gamma, const double* p0, const double* u0,
                     const double* dof0, double* J, double* dJdgamma, double* lam_p0, double* lam_u0,
                     double* lam_dof0, double* dJdkref) {
+  return oracle_gradient_terminal(P, gamma, p0, u0, dof0, nullptr, nullptr, nullptr, J, dJdgamma, lam_p0, lam_u0,
+                                  lam_dof0, dJdkref);
+}
+
+int oracle_gradient_terminal(const OracleProblem* P, const double* gamma, const double* p0, const double* u0,
+                             const double* dof0, const double* lam_pT, const double* lam_uT, const double* lam_sT,
+                             double* J, double* dJdgamma, double* lam_p0, double* lam_u0, double* lam_dof0,
+                             double* dJdkref) {
   Ctx C;
   if (!make_ctx(P, &C)) return ORC_ERR_ARG;
   if (P->nu <= 0.0) return ORC_ERR_UNSTABLE;
@@ -1278,7 +1294,12 @@ int oracle_gradient(const OracleProblem* P, const double* gamma, const double* p
   Fields<double> lam;
   lam.alloc(C);
   double lam_s[21];
-  for (int a = 0; a < ns; ++a) lam_s[a] = P->obj_w[a];
+  for (int a = 0; a < ns; ++a) lam_s[a] = P->obj_w[a] + (lam_sT ? lam_sT[a] : 0.0);
+  if (lam_pT)
+    for (size_t n = 0; n < C.N; ++n) lam.p[n] = lam_pT[n];
+  if (lam_uT)
+    for (int a = 0; a < d; ++a)
+      for (size_t n = 0; n < C.N; ++n) lam.u[a][n] = lam_uT[(size_t)a * C.N + n];
   std::vector<double> dk(C.ND, 0.0);
   for (int t = NT; t >= 1; --t) {
     const Fields<double>& prev = tr.states[t - 1];
@@ -1359,6 +1380,41 @@ int oracle_forward_cs(const OracleProblem* P, const double* gamma, const double*
   }
   cplx Jc = objective(C, s);
   if (J) *J = Jc.real();
+  if (dJ) *dJ = Jc.imag() / h;
+  return C.err;
+}
+
+// Complex-step derivative along dgamma of J + lam_pT.p(N_t) + lam_uT.u(N_t) + lam_sT.s(N_t).
+int oracle_forward_cs_terminal(const OracleProblem* P, const double* gamma, const double* dgamma, const double* p0,
+                               const double* u0, const double* dof0, const double* lam_pT, const double* lam_uT,
+                               const double* lam_sT, double h, double* dJ) {
+  Ctx C;
+  if (!make_ctx(P, &C)) return ORC_ERR_ARG;
+  const size_t N = C.N, ND = C.ND;
+  const int d = C.d;
+  std::vector<cplx> g(ND);
+  for (size_t m = 0; m < ND; ++m) g[m] = cplx(gamma[m], h * dgamma[m]);
+  std::vector<cplx> kref = brinkman(C, g.data());
+  std::vector<cplx> pc(N), uc((size_t)d * N);
+  for (size_t n = 0; n < N; ++n) pc[n] = cplx(p0[n], 0.0);
+  for (size_t n = 0; n < (size_t)d * N; ++n) uc[n] = cplx(u0[n], 0.0);
+  Fields<cplx> cur;
+  load_fields(C, pc.data(), uc.data(), &cur);
+  cplx s[21];
+  for (int a = 0; a < C.ns; ++a) s[a] = cplx(dof0[a], 0.0);
+  for (int t = 1; t <= P->n_steps; ++t) {
+    Fields<cplx> nxt;
+    cplx sn[21];
+    forward_step<cplx>(C, kref, cur, s, &nxt, sn, nullptr);
+    cur.p.swap(nxt.p);
+    for (int a = 0; a < 3; ++a) cur.u[a].swap(nxt.u[a]);
+    for (int a = 0; a < C.ns; ++a) s[a] = sn[a];
+  }
+  cplx Jc = objective(C, s);
+  for (int a = 0; a < C.ns; ++a) Jc += lam_sT[a] * s[a];
+  for (size_t n = 0; n < N; ++n) Jc += lam_pT[n] * cur.p[n];
+  for (int a = 0; a < d; ++a)
+    for (size_t n = 0; n < N; ++n) Jc += lam_uT[(size_t)a * N + n] * cur.u[a][n];
   if (dJ) *dJ = Jc.imag() / h;
   return C.err;
 }

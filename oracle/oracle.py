@@ -72,6 +72,8 @@ def lib():
         L.oracle_design_chain_vjp.argtypes = [pp, dp, dp, dp]
         L.oracle_design_chain_jvp.argtypes = [pp, dp, dp, ctypes.c_double, dp]
         L.oracle_constraint.argtypes = [pp, dp, dp, dp]
+        L.oracle_gradient_terminal.argtypes = [pp, dp, dp, dp, dp, dp, dp, dp, dp, dp, dp, dp, dp, dp]
+        L.oracle_forward_cs_terminal.argtypes = [pp, dp, dp, dp, dp, dp, dp, dp, dp, ctypes.c_double, dp]
         if L.oracle_sizeof_problem() != ctypes.sizeof(OracleProblem):
             raise RuntimeError("oracle problem record layout mismatch")
         _lib = L
@@ -277,3 +279,29 @@ def constraint(P, gamma):
     d = np.zeros(P.n_design)
     _check(lib().oracle_constraint(ctypes.byref(problem_record(P)), _ptr(_f64(gamma)), ctypes.byref(G), _ptr(d)))
     return G.value, d
+
+
+def gradient_terminal(P, gamma, p0, u0, dof0, lam_pT, lam_uT, lam_sT, n_steps: Optional[int] = None):
+    """Forward + exact adjoint started from a terminal adjoint (the periodic warm start of Sec. 3.4):
+    the derivative of J + lam_pT.p(N_t) + lam_uT.u(N_t) + lam_sT.s(N_t)."""
+    rec = problem_record(P, n_steps)
+    N, ND = P.n_cells, P.n_design
+    out = {"dJdgamma": np.zeros(ND), "dJdkref": np.zeros(ND), "lam_p0": np.zeros(N),
+           "lam_u0": np.zeros((P.dim, N)), "lam_dof0": np.zeros(dof_count(P))}
+    J = ctypes.c_double(0.0)
+    rc = lib().oracle_gradient_terminal(ctypes.byref(rec), _ptr(_f64(gamma)), _ptr(_f64(p0)), _ptr(_f64(u0)),
+                                        _ptr(_f64(dof0)), _ptr(_f64(lam_pT)), _ptr(_f64(lam_uT)), _ptr(_f64(lam_sT)),
+                                        ctypes.byref(J), _ptr(out["dJdgamma"]), _ptr(out["lam_p0"]),
+                                        _ptr(out["lam_u0"]), _ptr(out["lam_dof0"]), _ptr(out["dJdkref"]))
+    _check(rc)
+    out["J"] = J.value
+    return out
+
+
+def forward_cs_terminal(P, gamma, p0, u0, dof0, lam_pT, lam_uT, lam_sT, dgamma, h: float = 1e-30):
+    """Complex-step derivative along dgamma of J + lam_pT.p(N_t) + lam_uT.u(N_t) + lam_sT.s(N_t)."""
+    dJ = ctypes.c_double(0.0)
+    _check(lib().oracle_forward_cs_terminal(ctypes.byref(problem_record(P)), _ptr(_f64(gamma)), _ptr(_f64(dgamma)),
+                                            _ptr(_f64(p0)), _ptr(_f64(u0)), _ptr(_f64(dof0)), _ptr(_f64(lam_pT)),
+                                            _ptr(_f64(lam_uT)), _ptr(_f64(lam_sT)), h, ctypes.byref(dJ)))
+    return dJ.value

@@ -345,3 +345,21 @@ def test_stencil_dot_product(dim, bc):
     lhs = jp @ wp + (ju * wu).sum()
     rhs = lp @ vp + (lu * vu).sum()
     assert abs(lhs - rhs) < 1e-12 * abs(lhs)
+
+
+# ------------------------------------------------------- periodic warm start (Sec. 3.4) ----
+def test_terminal_adjoint_is_the_derivative_of_the_terminal_functional():
+    """A reverse sweep started from a terminal adjoint (lam_p, lam_u, lam_s at N_t) differentiates
+    J + lam_p.p(N_t) + lam_u.u(N_t) + lam_s.s(N_t): checked against the complex-step derivative of
+    that functional, with the terminal adjoint taken from a previous sweep's initial adjoint as the
+    warm start of periodic problems does."""
+    P, g = body2d(nt=6)
+    p0, u0, s0 = perturbed_state(P)
+    first = O.gradient(P, g, p0, u0, s0)
+    pT, uT, sT = first["lam_p0"], first["lam_u0"], first["lam_dof0"]
+    G = O.gradient_terminal(P, g, p0, u0, s0, pT, uT, sT)
+    assert abs(G["J"] - first["J"]) == 0.0
+    v = np.random.default_rng(12).standard_normal(g.shape)
+    dJ = O.forward_cs_terminal(P, g, p0, u0, s0, pT, uT, sT, v)
+    assert abs(dJ - G["dJdgamma"] @ v) <= 1e-11 * abs(dJ)
+    assert np.abs(G["dJdgamma"] - first["dJdgamma"]).max() > 1e-6 * np.abs(first["dJdgamma"]).max()
