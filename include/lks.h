@@ -153,6 +153,16 @@ LKS_API int lks_adjoint(lks_handle* h, double seed, void* stream);
  * synchronisation. */
 LKS_API int lks_sensitivity(lks_handle* h, double* dJdgamma_dev, void* stream);
 
+/* Periodic warm start (Sec. 3.4): the last forward's final state and DOFs become the initial state
+ * of the next forward, and (with_adjoint != 0) the last adjoint's initial adjoint lambda(0) and
+ * dJ/ds(0) become the terminal adjoint of the next reverse sweep, which then differentiates
+ * J + lambda(0).state(N_t). The copies stay on the device (the DOFs pass through the host). The
+ * next lks_forward and lks_adjoint use them; lks_set_initial_state replaces the initial state
+ * (the terminal adjoint stays until the next lks_warm_start). Synchronises the stream.
+ * Errors: LKS_ERR_ORDER (no forward, or with_adjoint without an adjoint), LKS_ERR_UNSUPPORTED (the
+ * final DOFs start rotated but the workspace was sized for an axis-aligned box), LKS_ERR_CUDA. */
+LKS_API int lks_warm_start(lks_handle* h, int with_adjoint, void* stream);
+
 /* Volume constraint (Eq. constraint) of the design gamma_dev [N_D] (device): G = sum of gamma-bar over
  * the design domain / (v_min * its point count) - 1 into G_host, and dG/dgamma [N_D] (device, FP64,
  * through the design chain) into dGdgamma_dev if not NULL. Synchronises the stream to return G.

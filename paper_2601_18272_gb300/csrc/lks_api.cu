@@ -14,6 +14,7 @@
 // reverse kernel, then the transposed stencil.
 #include <algorithm>
 #include <climits>
+#include <cstddef>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -71,6 +72,10 @@ struct lks_handle {
   double *cg1 = nullptr, *cgtil = nullptr, *cgbar = nullptr, *cW = nullptr;
   double *kg1 = nullptr, *kgtil = nullptr, *kgbar = nullptr, *kW = nullptr;
   double *dv = nullptr, *dtmp = nullptr, *vol = nullptr;
+  // terminal adjoint of the next reverse sweep (periodic warm start): fields in the field type
+  void* term_L = nullptr;
+  double* term_s = nullptr;
+  bool has_term = false;
   Dof* it = nullptr;
   Ctrl* ctrl = nullptr;
   Moments* mom = nullptr;
@@ -534,7 +539,13 @@ int adjoint_impl(lks_handle* h, double seed, cudaStream_t st) {
   const int NT = h->P.n_steps;
   Launcher L0{h, st, false};
   CK(cudaMemsetAsync(h->L, 0, 2 * h->slot_elems * h->esz, st));
-  L0("init", [&](cudaStream_t s) { launch_adj_init(g, h->ctrl, h->it, h->P.n_steps, h->objw, seed, h->dkref, g.ND, s); });
+  if (h->has_term)  // lambda(N_t) sits in slot N_t mod 2 of the adjoint pair
+    CK(cudaMemcpyAsync((char*)h->L + (size_t)(NT & 1) * h->slot_elems * h->esz, h->term_L, h->slot_elems * h->esz,
+                       cudaMemcpyDeviceToDevice, st));
+  const double* term_s = h->has_term ? h->term_s : nullptr;
+  L0("init", [&](cudaStream_t s) {
+    launch_adj_init(g, h->ctrl, h->it, h->P.n_steps, h->objw, seed, term_s, h->dkref, g.ND, s);
+  });
   if (h->P.ckpt_policy == LKS_CKPT_BINOMIAL) {
     TRY(binomial_reverse<T>(h, st, 0, NT, h->P.ckpt_every, true, -1, 0));
   } else if (h->P.ckpt_policy == LKS_CKPT_STORE_ALL) {
@@ -613,6 +624,8 @@ int allocate(lks_handle* h) {
   double** chain_bufs[] = {&h->cg1, &h->cgtil, &h->cgbar, &h->cW, &h->kg1, &h->kgtil, &h->kgbar, &h->kW, &h->dv, &h->dtmp};
   for (double** b : chain_bufs) TRY(dalloc(h, (void**)b, (size_t)g.ND * sizeof(double)));
   TRY(dalloc(h, (void**)&h->vol, 2 * sizeof(double)));
+  TRY(dalloc(h, &h->term_L, slot_bytes));
+  TRY(dalloc(h, (void**)&h->term_s, kNdofFree * sizeof(double)));
   TRY(dalloc(h, (void**)&h->it, (size_t)(NT + 1) * (K + 1) * sizeof(Dof)));
   TRY(dalloc(h, (void**)&h->ctrl, sizeof(Ctrl)));
   TRY(dalloc(h, (void**)&h->mom, sizeof(Moments)));
@@ -855,6 +868,35 @@ int lks_sensitivity(lks_handle* h, double* out, void* stream) {
   h->launches += 4;
   CK(cudaGetLastError());
   return LKS_OK;
+}
+
+int lks_warm_start(lks_handle* h, int with_adjoint, void* stream) {
+  if (!h) return LKS_ERR_ARG;
+  if (!h->fwd_done || (with_adjoint && !h->adj_done)) return LKS_ERR_ORDER;
+  cudaStream_t st = (cudaStream_t)stream;
+  const Geo& g = h->g;
+  const int NT = h->P.n_steps;
+  const void* src = (h->P.ckpt_policy == LKS_CKPT_STORE_ALL)
+                        ? (const char*)h->ring + (size_t)NT * h->slot_elems * h->esz
+                        : (const char*)h->pp + (size_t)(NT & 1) * h->slot_elems * h->esz;
+  if (h->prec == LKS_FP64)
+    launch_state_to_double<double>(g, (const double*)src, h->init_p, h->init_u, st);
+  else
+    launch_state_to_double<float>(g, (const float*)src, h->init_p, h->init_u, st);
+  Dof last;
+  CK(cudaMemcpyAsync(&last, h->it + (size_t)NT * (g.K + 1), sizeof(Dof), cudaMemcpyDeviceToHost, st));
+  if (with_adjoint) {
+    CK(cudaMemcpyAsync(h->term_L, h->L, h->slot_elems * h->esz, cudaMemcpyDeviceToDevice, st));  // lambda(0)
+    CK(cudaMemcpyAsync(h->term_s, (const char*)h->ctrl + offsetof(Ctrl, lam_s0), g.ns * sizeof(double),
+                       cudaMemcpyDeviceToDevice, st));
+  }
+  CK(cudaStreamSynchronize(st));
+  h->launches += 1;
+  for (int a = 0; a < kNdofFree; ++a) h->host_s0[a] = (a < g.ns) ? last.s[a] : 0.0;
+  CK(cudaMemcpy(h->init_s, h->host_s0, g.ns * sizeof(double), cudaMemcpyHostToDevice));
+  h->has_term = with_adjoint != 0;
+  h->fwd_done = h->adj_done = false;
+  return refresh_box(h);
 }
 
 int lks_constraint(lks_handle* h, const double* gamma_dev, double* G_host, double* dGdgamma_dev, void* stream) {

@@ -845,10 +845,11 @@ __global__ void k_set_step(Ctrl* ctrl, int t0, int base) {
 
 // Seed of the reverse sweep: dJ/ds(N_t) = seed * w, then the EOM reverse of iteration N_itr of
 // step N_t (free rotation: from the iterates it[N_t - 1][0] and it[N_t - 1][N_itr]).
-__global__ void k_adj_init(Geo g, Ctrl* ctrl, const Dof* it, int nt, const double* objw, double seed) {
+__global__ void k_adj_init(Geo g, Ctrl* ctrl, const Dof* it, int nt, const double* objw, double seed,
+                           const double* term_s) {
   double ls[kNdofFree], lp[kNdofFree], nF[3], nT[3];
   for (int a = 0; a < kNdofFree; ++a) {
-    ls[a] = (a < g.ns) ? seed * objw[a] : 0.0;
+    ls[a] = (a < g.ns) ? seed * objw[a] + (term_s ? term_s[a] : 0.0) : 0.0;
     lp[a] = 0.0;
   }
   if (g.ax == AX_FREE) {
@@ -957,10 +958,10 @@ void launch_init_forward(const Geo& g, const Slots<T>& S, const double* p0, cons
 
 void launch_set_step(Ctrl* ctrl, int t0, int base, cudaStream_t st) { launch(k_set_step, 1, 1, 0, st, ctrl, t0, base); }
 
-void launch_adj_init(const Geo& g, Ctrl* ctrl, const Dof* it, int nt, const double* objw, double seed, double* dkref,
-                     int nd, cudaStream_t st) {
+void launch_adj_init(const Geo& g, Ctrl* ctrl, const Dof* it, int nt, const double* objw, double seed,
+                     const double* term_s, double* dkref, int nd, cudaStream_t st) {
   cudaMemsetAsync(dkref, 0, sizeof(double) * (size_t)nd, st);
-  launch(k_adj_init, 1, 1, 0, st, g, ctrl, it, nt, objw, seed);
+  launch(k_adj_init, 1, 1, 0, st, g, ctrl, it, nt, objw, seed, term_s);
 }
 
 void launch_sensitivity(const Geo& g, const double* gamma, const double* dkref, double kappa_max, double q,

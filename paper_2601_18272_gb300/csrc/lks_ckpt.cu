@@ -123,6 +123,15 @@ __global__ void k_state_from_double(Geo g, T* dst, const double* __restrict__ p0
   }
 }
 
+template <typename T>
+__global__ void k_state_to_double(Geo g, const T* __restrict__ src, double* p0, double* u0) {
+  const long long N = g.N;
+  for (long long n = blockIdx.x * (long long)blockDim.x + threadIdx.x; n < N; n += (long long)gridDim.x * blockDim.x) {
+    p0[n] = (double)src[n];
+    for (int a = 0; a < g.dim; ++a) u0[a * N + n] = (double)src[(a + 1) * N + n];
+  }
+}
+
 inline unsigned q_blocks(const Geo& g) {
   const long long nb = (g.N + kQB - 1) / kQB;
   return (unsigned)(nb < 1024 ? nb : 1024);
@@ -151,6 +160,14 @@ void launch_state_from_double(const Geo& g, T* dst, const double* p0, const doub
   launch(k_state_from_double<T>, (unsigned)(nb < 4096 ? nb : 4096), 256, 0, st, g, dst, p0, u0);
 }
 
+template <typename T>
+void launch_state_to_double(const Geo& g, const T* src, double* p0, double* u0, cudaStream_t st) {
+  const long long nb = (g.N + 255) / 256;
+  launch(k_state_to_double<T>, (unsigned)(nb < 4096 ? nb : 4096), 256, 0, st, g, src, p0, u0);
+}
+
+template void launch_state_to_double<float>(const Geo&, const float*, double*, double*, cudaStream_t);
+template void launch_state_to_double<double>(const Geo&, const double*, double*, double*, cudaStream_t);
 template void launch_state_from_double<float>(const Geo&, float*, const double*, const double*, cudaStream_t);
 template void launch_state_from_double<double>(const Geo&, double*, const double*, const double*, cudaStream_t);
 

@@ -109,8 +109,12 @@ void launch_init_forward(const Geo& g, const Slots<T>& S, const double* p0, cons
 void launch_set_step(Ctrl* ctrl, int t0, int base, cudaStream_t st);
 
 // Adjoint initialisation: dJ/ds(N_t) = seed * w, EOM reverse of iteration K, zero dJ/dkappa^ref.
-void launch_adj_init(const Geo& g, Ctrl* ctrl, const Dof* it, int nt, const double* objw, double seed, double* dkref,
-                     int nd, cudaStream_t st);
+// term_s (device, nullable): a terminal DOF adjoint added to seed * w (the periodic warm start).
+void launch_adj_init(const Geo& g, Ctrl* ctrl, const Dof* it, int nt, const double* objw, double seed,
+                     const double* term_s, double* dkref, int nd, cudaStream_t st);
+// A state slot (T) -> p0 [N], u0 [dim][N] as doubles.
+template <typename T>
+void launch_state_to_double(const Geo& g, const T* src, double* p0, double* u0, cudaStream_t st);
 
 // dJ/dgamma-bar = dJ/dkappa^ref * dkappa^ref/dgamma-bar at gamma-bar (Eq. brinkman_coefficient).
 void launch_sensitivity(const Geo& g, const double* gbar, const double* dkref, double kappa_max, double q,

@@ -110,6 +110,7 @@ def load() -> ctypes.CDLL:
     L.lks_step_noalloc.argtypes = [ctypes.POINTER(lks_problem), vp, vp, ctypes.c_int, dp, vp]
     L.lks_dof_count.argtypes = [ctypes.POINTER(lks_problem)]
     L.lks_constraint.argtypes = [hp, vp, dp, vp, vp]
+    L.lks_warm_start.argtypes = [hp, ctypes.c_int, vp]
     L.lks_problem_size.argtypes = []
     L.lks_problem_size.restype = ctypes.c_size_t
     if L.lks_problem_size() != ctypes.sizeof(lks_problem):
@@ -210,6 +211,10 @@ def lks_constraint(h, gamma_dev_ptr: int, dG_dev_ptr: int = 0, stream: int = 0) 
                                  ctypes.c_void_p(dG_dev_ptr) if dG_dev_ptr else None, ctypes.c_void_p(stream)),
            "lks_constraint")
     return G.value
+
+
+def lks_warm_start(h, with_adjoint: bool = True, stream: int = 0):
+    _check(load().lks_warm_start(h, int(bool(with_adjoint)), ctypes.c_void_p(stream)), "lks_warm_start")
 
 
 def lks_dof_count(problem: lks_problem) -> int:
@@ -318,6 +323,11 @@ class Solver:
     @property
     def n_dof(self) -> int:
         return lks_dof_count(self.struct)
+
+    def warm_start(self, with_adjoint: bool = True, stream=None):
+        import torch
+        st = torch.cuda.current_stream() if stream is None else stream
+        lks_warm_start(self.handle, with_adjoint, st.cuda_stream)
 
     def constraint(self, gamma, dG=None, stream=None) -> float:
         import torch

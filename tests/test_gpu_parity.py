@@ -367,3 +367,40 @@ def test_volume_constraint_matches_oracle():
         np.testing.assert_allclose(dG.cpu().numpy(), dGo, rtol=1e-12, atol=1e-15)
     finally:
         S.close()
+
+
+# ------------------------------------------------------- periodic warm start (Sec. 3.4) ----
+@pytest.mark.parametrize("policy", ["store_all_fp64", "uniform_fp32"])
+def test_periodic_warm_start_matches_oracle(policy):
+    """A second gradient after lks_warm_start starts from the first forward's final state and
+    reverses from the first adjoint's initial adjoint: the oracle's reverse sweep from that terminal
+    adjoint on the same initial state."""
+    torch = _torch()
+    from paper_2601_18272_gb300.lks import Solver
+    P, g = body2d(nt=8)
+    p0, u0, s0 = perturbed_state(P)
+    first = O.gradient(P, g, p0, u0, s0)
+    pf, uf, hf, _ = O.forward(P, g, p0, u0, s0)
+    second = O.gradient_terminal(P, g, pf, uf, hf[-1], first["lam_p0"], first["lam_u0"], first["lam_dof0"])
+    fp64 = policy.endswith("fp64")
+    kw = dict(precision=64, ckpt_policy=CKPT_STORE_ALL) if fp64 else \
+        dict(precision=32, ckpt_policy=CKPT_UNIFORM, ckpt_every=4)
+    S = Solver(P, **kw)
+    try:
+        S.set_initial_state(p0, u0, s0)
+        gam = torch.tensor(g, dtype=torch.float64, device="cuda")
+        dg = torch.empty_like(gam)
+        S.forward(gam)
+        S.adjoint(1.0)
+        S.sensitivity(dg)
+        S.warm_start(True)
+        J2 = S.forward(gam)
+        np.testing.assert_allclose(S.dof_history()[0], hf[-1], rtol=1e-11 if fp64 else 1e-5, atol=1e-12)
+        S.adjoint(1.0)
+        S.sensitivity(dg)
+        torch.cuda.synchronize()
+        tj, tg = (1e-11, 1e-9) if fp64 else (1e-4, 1e-3)
+        assert abs(J2 - second["J"]) <= tj * abs(second["J"])
+        assert rel(dg.cpu().numpy(), second["dJdgamma"]) < tg
+    finally:
+        S.close()
