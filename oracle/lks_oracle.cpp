@@ -57,6 +57,7 @@
 #include <cmath>
 #include <complex>
 #include <cstdint>
+#include <algorithm>
 #include <cstring>
 #include <vector>
 
@@ -1215,6 +1216,426 @@ int run_forward(Ctx& C, const std::vector<double>& kref, const double* p0, const
   return C.err;
 }
 
+// ------------------------------------------------------------------------------------------
+// The paper's adjoint, ALKS (Sec. 2.5, Appendix A): a discretised continuous adjoint, kept beside
+// the exact discrete adjoint above for comparison. Its variables are the moments of the adjoint
+// distribution, p~ = sum_i w_i f~_i, u~ = sum_i w_i c_i f~_i, s~ = sum_i w_i c_i c_i f~_i, and the
+// body multipliers x~G, u~G, theta~, omega~, with the paper's sign (the multipliers of the
+// residuals of the Lagrangian, minus the derivatives of J).
+//
+// Adjoint loop of Algorithm 1, per step t = N_t, ..., 1:
+//   with the converged DOFs s(t) and the state u(t): N_itr fixed-point iterations of Eq. au (p~ and
+//   s~ equal their star moments, Eqs. ap and as, since J has no field term) and of Eqs. axg, aug,
+//   atheta, aomega; then the step's term of Eq. design_sensitivity;
+//   the star moments at t - 1 from the adjoint equilibrium at t (Eqs. ap_tmp, au_tmp, as_tmp),
+//   with the boundary values prescribed.
+// Readings where the paper is silent:
+//   - the terminal values x~G = -dJ/dxG, M u~G = -dJ/duG, theta~ = -dJ/dtheta, I omega~ = -dJ/domega
+//     belong to a step N_t + 1, so that the equations hold at every coupled step 1..N_t; the fluid
+//     multipliers at N_t + 1 are zero (J has no field term);
+//   - iteration k evaluates Eq. au with the body multipliers of iteration k - 1, and the body
+//     equations with the fluid multiplier of iteration k and u~G, omega~ of iteration k - 1 (x~G and
+//     theta~ of iteration k enter Eqs. aug and aomega); iteration 0 takes the values of step t + 1;
+//   - the derivative in f~eq is the forward's velocity-gradient stencil, with a ghost node that
+//     copies the boundary node;
+//   - boundary values: a quantity the forward prescribes (inlet and wall velocity, outlet pressure,
+//     the pressure of a pressure boundary) has a zero multiplier; one the forward copies from the
+//     inward neighbour copies the neighbour's multiplier; s~ is copied on every boundary;
+//   - single rotation axis only (the paper's setting); the derivative of the lever arm and of the
+//     solid velocity with respect to theta follow Eqs. rigid_body_position and rigid_body_velocity.
+// ------------------------------------------------------------------------------------------
+
+// Adjoint moments p~ [N], u~ [d][N] and s~ [3 a + b][N] (a, b < d; stored in full).
+struct AdjMoments {
+  std::vector<double> p;
+  std::vector<double> u[3];
+  std::vector<double> s[9];
+  void alloc(const Ctx& C) {
+    p.assign(C.N, 0.0);
+    for (int a = 0; a < 3; ++a) u[a].assign(a < C.d ? C.N : 0, 0.0);
+    for (int k = 0; k < 9; ++k) s[k].assign((k / 3 < C.d && k % 3 < C.d) ? C.N : 0, 0.0);
+  }
+};
+
+// Neighbour x + c for the derivative in f~eq: wrapped on periodic axes, the boundary node itself
+// beyond a non-periodic boundary.
+inline size_t copy_nbr(const Ctx& C, const int* x, const int* c) {
+  int y[3] = {0, 0, 0};
+  for (int a = 0; a < C.d; ++a) {
+    int v = x[a] + c[a];
+    if (C.P.bc[a] == BC_PERIODIC)
+      v = wrap(v, C.n[a]);
+    else
+      v = std::min(std::max(v, 0), C.n[a] - 1);
+    y[a] = v;
+  }
+  return idx(C, y[0], y[1], y[2]);
+}
+
+// Adjoint equilibrium at every node (Sec. 2.5, Appendix A):
+//   f~eq_i = p~ + 3 c_ia (u~_a + 3 s~_ab u_b - p~ u_a) - A c_ia d_b (s~_ab + s~_ba),
+// with the forward's velocity u at the same node and time. F [Q][N].
+void alks_feq_field(const Ctx& C, const AdjMoments& a, const Fields<double>& st, std::vector<double>* F) {
+  const int d = C.d, Q = C.L.Q;
+  std::vector<double> Dv((size_t)d * C.N, 0.0);  // Dv_a = sum_b d_b (s~_ab + s~_ba)
+  int x[3];
+  for (size_t n = 0; n < C.N; ++n) {
+    coords(C, n, x);
+    for (int ia = 0; ia < d; ++ia) {
+      double acc = 0.0;
+      for (int b = 0; b < d; ++b) {
+        double g = 0.0;
+        for (int j = 0; j < Q; ++j) {
+          if (C.L.c[j][b] == 0) continue;
+          const size_t m = copy_nbr(C, x, C.L.c[j]);
+          g += (double)C.L.c[j][b] * (a.s[3 * ia + b][m] + a.s[3 * b + ia][m]);
+        }
+        acc += g / C.L.cn[b];
+      }
+      Dv[(size_t)ia * C.N + n] = acc;
+    }
+  }
+  F->assign((size_t)Q * C.N, 0.0);
+  for (size_t n = 0; n < C.N; ++n)
+    for (int i = 0; i < Q; ++i) {
+      const int* c = C.L.c[i];
+      double v = a.p[n];
+      for (int ia = 0; ia < d; ++ia) {
+        double su = 0.0;
+        for (int b = 0; b < d; ++b) su += a.s[3 * ia + b][n] * st.u[b][n];
+        v += 3.0 * c[ia] * (a.u[ia][n] + 3.0 * su - a.p[n] * st.u[ia][n]);
+        v -= C.A * c[ia] * Dv[(size_t)ia * C.N + n];
+      }
+      (*F)[(size_t)i * C.N + n] = v;
+    }
+}
+
+// Boundary values of the adjoint moments (reading above), in the forward's phase order.
+void alks_boundaries(const Ctx& C, AdjMoments* o) {
+  const int d = C.d;
+  int x[3];
+  auto copy_s = [&](size_t n, size_t m) {
+    for (int k = 0; k < 9; ++k)
+      if (!o->s[k].empty()) o->s[k][n] = o->s[k][m];
+  };
+  for (int wa = 1; wa < d; ++wa) {
+    if (C.P.bc[wa] != BC_WALL) continue;
+    for (size_t n = 0; n < C.N; ++n) {
+      coords(C, n, x);
+      if (!(x[wa] == 0 || x[wa] == C.n[wa] - 1)) continue;
+      if (on_boundary(C, 0, x[0])) continue;
+      if (wa == 1 && d == 3 && on_boundary(C, 2, x[2])) continue;
+      int y[3] = {x[0], x[1], x[2]};
+      y[wa] = (x[wa] == 0) ? 1 : C.n[wa] - 2;
+      const size_t m = idx(C, y[0], y[1], y[2]);
+      o->p[n] = o->p[m];                             // the wall pressure is copied
+      for (int a = 0; a < d; ++a) o->u[a][n] = 0.0;  // the wall velocity is prescribed
+      copy_s(n, m);
+    }
+  }
+  const int bcx = C.P.bc[0];
+  if (bcx == BC_PERIODIC) return;
+  for (size_t n = 0; n < C.N; ++n) {
+    coords(C, n, x);
+    if (!(x[0] == 0 || x[0] == C.n[0] - 1)) continue;
+    const bool inlet = (x[0] == 0);
+    const size_t m = idx(C, inlet ? 1 : C.n[0] - 2, x[1], x[2]);
+    const bool p_fixed = (bcx == BC_PRESSURE) || !inlet;      // outlet, or either pressure plane
+    const bool u_fixed = (bcx == BC_INFLOW_OUTFLOW) && inlet;  // inflow velocity
+    o->p[n] = p_fixed ? 0.0 : o->p[m];
+    for (int a = 0; a < d; ++a) o->u[a][n] = u_fixed ? 0.0 : o->u[a][m];
+    copy_s(n, m);
+  }
+}
+
+// Star moments at t - 1 from the adjoint equilibrium at t (Eqs. ap_tmp, au_tmp, as_tmp):
+//   p~*(x) = sum_i w_i f~eq_i(x + c_i), u~*_a(x) = sum_i w_i c_ia f~eq_i(x + c_i),
+//   s~*_ab(x) = sum_i w_i c_ia c_ib f~eq_i(x + c_i),
+// at the interior nodes; the boundary nodes by alks_boundaries. st is the state at t.
+void alks_gather(const Ctx& C, const AdjMoments& a, const Fields<double>& st, AdjMoments* o) {
+  const int d = C.d, Q = C.L.Q;
+  std::vector<double> F;
+  alks_feq_field(C, a, st, &F);
+  o->alloc(C);
+  int x[3];
+  for (size_t n = 0; n < C.N; ++n) {
+    coords(C, n, x);
+    if (!is_interior(C, x)) continue;
+    for (int i = 0; i < Q; ++i) {
+      const int* c = C.L.c[i];
+      const double fw = C.L.w[i] * F[(size_t)i * C.N + shift_nbr(C, x, c, +1)];
+      o->p[n] += fw;
+      for (int ia = 0; ia < d; ++ia) {
+        o->u[ia][n] += c[ia] * fw;
+        for (int b = 0; b < d; ++b) o->s[3 * ia + b][n] += (double)(c[ia] * c[b]) * fw;
+      }
+    }
+  }
+  alks_boundaries(C, o);
+}
+
+// (a x b) along the rotation axis ax.
+template <class T>
+T cross_axis(int ax, const T* a, const T* b) {
+  int bb, cc;
+  plane_axes(ax, &bb, &cc);
+  return a[bb] * b[cc] - a[cc] * b[bb];
+}
+
+// The coupling part of the paper's Lagrangian at one step (the forcing term of R_1, and R_3, R_5):
+//   Lambda = sum_n 3 kappa_n (u_n - uS_n) . u~_n - u~G . F - omega~ T,
+//   F = sum_m kappa_m (u^ref_m - uS,ref_m),  T = sum_m kappa_m (l_m x (u^ref_m - uS,ref_m))_axis,
+// with the multipliers u~, u~G, omega~ held fixed and kappa_n, uS_n, u^ref_m, l_m = x^ref_m - x^G
+// evaluated at the DOFs s. Eq. au and the coupling terms of Eqs. axg, aug, atheta, aomega and of
+// Eq. design_sensitivity are its derivatives (the tests check them by complex step).
+template <class T>
+T alks_lambda(Ctx& C, const std::vector<T>& kref, const T* s, const std::vector<T>* u, const std::vector<double>* ut,
+              const double* ug, double om) {
+  const int d = C.d, ax = C.P.rot_axis;
+  Geometry<T> geo;
+  transform(C, s, &geo);
+  std::vector<T> kap(C.N, T(0)), us[3], uref(3 * C.ND, T(0));
+  for (int a = 0; a < 3; ++a) us[a].assign(C.N, T(0));
+  std::vector<WindowNode> wn;
+  std::vector<T> wv, dwv;
+  for (size_t m = 0; m < C.ND; ++m) {
+    if (!C.dom[m]) continue;
+    window(C, &geo.xref[3 * m], &wn, &wv, &dwv);
+    for (size_t q = 0; q < wn.size(); ++q) {
+      const size_t n = wn[q].n;
+      kap[n] += wv[q] * kref[m];
+      for (int a = 0; a < d; ++a) {
+        us[a][n] += wv[q] * geo.usref[3 * m + a];
+        uref[3 * m + a] += wv[q] * u[a][n];
+      }
+    }
+  }
+  T L = T(0);
+  for (size_t n = 0; n < C.N; ++n)
+    for (int a = 0; a < d; ++a) L += 3.0 * kap[n] * (u[a][n] - us[a][n]) * ut[a][n];
+  for (size_t m = 0; m < C.ND; ++m) {
+    if (!C.dom[m]) continue;
+    T D[3] = {T(0), T(0), T(0)};
+    for (int a = 0; a < d; ++a) D[a] = uref[3 * m + a] - geo.usref[3 * m + a];
+    for (int a = 0; a < d; ++a) L -= ug[a] * kref[m] * D[a];
+    L -= om * kref[m] * cross_axis(ax, &geo.lev[3 * m], D);
+  }
+  return L;
+}
+
+// The spread quantities of one step at the converged DOFs s(t) and the state u(t).
+struct AlksGeom {
+  Geometry<double> geo;
+  std::vector<std::vector<WindowNode>> win;  // per design point: its support window
+  std::vector<std::vector<double>> W, dW;    // W(x_n, x^ref_m) and dW/dx^ref (3 per node)
+  std::vector<double> kap;                   // kappa(x_n) = sum_m kappa_m W
+  std::vector<double> us[3];                 // uS(x_n) = sum_m W uS,ref_m
+  std::vector<double> tq[3];                 // sum_m kappa_m W (e_axis x l_m), the omega~ source of Eq. au
+  std::vector<double> uref;                  // u^ref_m = sum_n W u(x_n)  [3 per m]
+};
+
+void alks_geometry(Ctx& C, const std::vector<double>& kref, const double* s, const Fields<double>& st, AlksGeom* G) {
+  const int d = C.d;
+  transform(C, s, &G->geo);
+  G->win.assign(C.ND, {});
+  G->W.assign(C.ND, {});
+  G->dW.assign(C.ND, {});
+  G->kap.assign(C.N, 0.0);
+  for (int a = 0; a < 3; ++a) {
+    G->us[a].assign(C.N, 0.0);
+    G->tq[a].assign(C.N, 0.0);
+  }
+  G->uref.assign(3 * C.ND, 0.0);
+  for (size_t m = 0; m < C.ND; ++m) {
+    if (!C.dom[m]) continue;
+    window(C, &G->geo.xref[3 * m], &G->win[m], &G->W[m], &G->dW[m]);
+    for (size_t q = 0; q < G->win[m].size(); ++q) {
+      const size_t n = G->win[m][q].n;
+      const double w = G->W[m][q];
+      G->kap[n] += w * kref[m];
+      for (int a = 0; a < d; ++a) {
+        G->us[a][n] += w * G->geo.usref[3 * m + a];
+        G->tq[a][n] += kref[m] * w * G->geo.dlev[3 * m + a];
+        G->uref[3 * m + a] += w * st.u[a][n];
+      }
+    }
+  }
+}
+
+// Eq. au: u~ = (u~* + (u~G kappa + omega~ sum_m kappa_m W (e_axis x l_m)) / 3) / (1 + kappa).
+void alks_fluid(const Ctx& C, const AlksGeom& G, const std::vector<double>* ustar, const double* ug, double om,
+                std::vector<double>* ut) {
+  for (int a = 0; a < C.d; ++a) {
+    ut[a].assign(C.N, 0.0);
+    for (size_t n = 0; n < C.N; ++n)
+      ut[a][n] = (ustar[a][n] + (G.kap[n] * ug[a] + om * G.tq[a][n]) / 3.0) / (1.0 + G.kap[n]);
+  }
+}
+
+// The coupling terms of the body equations at step t for the fluid multiplier ut and the body
+// multipliers ug (u~G) and om (omega~), written as printed (sums over the design points m and the
+// nodes n of their supports); omega_t is the state's omega(t):
+//   X  : Eq. axg without x~G(t+1) and dJ/dxG,   U  : the bracket of Eq. aug without x~G(t) and dJ/duG,
+//   Th : Eq. atheta without theta~(t+1) and dJ/dtheta,   Om : the bracket of Eq. aomega without
+//   theta~(t) and dJ/domega.
+void alks_terms(const Ctx& C, const std::vector<double>& kref, const AlksGeom& G, const Fields<double>& st,
+                const std::vector<double>* ut, const double* ug, double om, double omega_t, double* X, double* U,
+                double* Th, double* Om) {
+  const int d = C.d, ax = C.P.rot_axis;
+  int b, c;
+  plane_axes(ax, &b, &c);
+  for (int a = 0; a < 3; ++a) X[a] = U[a] = 0.0;
+  *Th = *Om = 0.0;
+  for (size_t m = 0; m < C.ND; ++m) {
+    if (!C.dom[m]) continue;
+    const double km = kref[m];
+    const double* l = &G.geo.lev[3 * m];     // x^ref - x^G
+    const double* pm = &G.geo.dlev[3 * m];   // dx^ref/dtheta = duS,ref/domega
+    const double* usr = &G.geo.usref[3 * m];
+    double dus[3] = {0.0, 0.0, 0.0};         // duS,ref/dtheta = -omega (l_b, l_c) in the plane
+    dus[b] = -omega_t * l[b];
+    dus[c] = -omega_t * l[c];
+    double D[3] = {0.0, 0.0, 0.0};
+    for (int a = 0; a < d; ++a) D[a] = G.uref[3 * m + a] - usr[a];
+    double ugdus = 0.0, ugp = 0.0;
+    for (int a = 0; a < d; ++a) {
+      double ea[3] = {0.0, 0.0, 0.0};
+      ea[a] = 1.0;
+      U[a] -= ug[a] * km;
+      U[a] -= om * cross_axis(ax, l, ea) * km;
+      ugdus += ug[a] * dus[a];
+      ugp += ug[a] * pm[a];
+    }
+    *Th -= ugdus * km;
+    *Th += om * cross_axis(ax, pm, D) * km;
+    *Th -= om * cross_axis(ax, l, dus) * km;
+    *Om -= ugp * km;
+    *Om -= om * cross_axis(ax, l, pm) * km;
+    for (size_t q = 0; q < G.win[m].size(); ++q) {
+      const size_t n = G.win[m][q].n;
+      const double w = G.W[m][q];
+      const double* dw = &G.dW[m][3 * q];
+      double un[3] = {0.0, 0.0, 0.0}, v_ut = 0.0, ut_usr = 0.0, ut_dus = 0.0, ut_p = 0.0, ugu = 0.0, dwp = 0.0;
+      for (int a = 0; a < d; ++a) {
+        un[a] = st.u[a][n];
+        v_ut += (un[a] - G.us[a][n]) * ut[a][n];
+        ut_usr += ut[a][n] * usr[a];
+        ut_dus += ut[a][n] * dus[a];
+        ut_p += ut[a][n] * pm[a];
+        ugu += ug[a] * un[a];
+        dwp += dw[a] * pm[a];
+      }
+      const double lu = cross_axis(ax, l, un);
+      const double kn = G.kap[n];
+      for (int al = 0; al < d; ++al) {
+        X[al] += -3.0 * km * dw[al] * v_ut + 3.0 * kn * ut_usr * dw[al] + ugu * km * dw[al] + om * lu * km * dw[al];
+        U[al] += 3.0 * kn * ut[al][n] * w;
+      }
+      *Th += -3.0 * km * dwp * v_ut + 3.0 * kn * ut_dus * w + 3.0 * kn * ut_usr * dwp + ugu * km * dwp +
+             om * lu * km * dwp;
+      *Om += 3.0 * kn * ut_p * w;
+    }
+  }
+}
+
+// The step's term of Eq. design_sensitivity per design point:
+//   sum_n 3 W (u - uS) . u~ - u~G . (u^ref - uS,ref) - omega~ (l x (u^ref - uS,ref))_axis.
+void alks_sens_step(const Ctx& C, const AlksGeom& G, const Fields<double>& st, const std::vector<double>* ut,
+                    const double* ug, double om, double* sens) {
+  const int d = C.d, ax = C.P.rot_axis;
+  for (size_t m = 0; m < C.ND; ++m) {
+    sens[m] = 0.0;
+    if (!C.dom[m]) continue;
+    double acc = 0.0;
+    for (size_t q = 0; q < G.win[m].size(); ++q) {
+      const size_t n = G.win[m][q].n;
+      for (int a = 0; a < d; ++a) acc += 3.0 * G.W[m][q] * (st.u[a][n] - G.us[a][n]) * ut[a][n];
+    }
+    double D[3] = {0.0, 0.0, 0.0};
+    for (int a = 0; a < d; ++a) D[a] = G.uref[3 * m + a] - G.geo.usref[3 * m + a];
+    for (int a = 0; a < d; ++a) acc -= ug[a] * D[a];
+    acc -= om * cross_axis(ax, &G.geo.lev[3 * m], D);
+    sens[m] = acc;
+  }
+}
+
+// One step of the paper's adjoint at the converged DOFs s = s(t) and the state st = (p, u)(t):
+// N_itr fixed-point iterations of Eq. au and Eqs. axg, aug, atheta, aomega, then the step's term of
+// Eq. design_sensitivity added to dk. nxt: the body multipliers at t + 1 (DOF-vector order x~G[3],
+// u~G[3], theta~, omega~); out_b: those at t; star: the star moments at t; out: the moments at t.
+void alks_body_step(Ctx& C, const std::vector<double>& kref, const double* s, const Fields<double>& st,
+                    const AdjMoments& star, const double* nxt, int K, AdjMoments* out, double* out_b,
+                    std::vector<double>* dk) {
+  AlksGeom G;
+  alks_geometry(C, kref, s, st, &G);
+  const int d = C.d, mask = C.P.dof_mask;
+  double cur[8];
+  for (int a = 0; a < 8; ++a) cur[a] = nxt[a];
+  *out = star;
+  for (int k = 1; k <= K; ++k) {
+    alks_fluid(C, G, star.u, &cur[3], cur[7], out->u);
+    double X[3], U[3], Th, Om;
+    alks_terms(C, kref, G, st, out->u, &cur[3], cur[7], s[7], X, U, &Th, &Om);
+    double nw[8] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
+    for (int a = 0; a < d; ++a) {
+      if (!(mask & (1 << a))) continue;
+      nw[a] = nxt[a] + X[a];                               // Eq. axg
+      nw[3 + a] = nxt[3 + a] + (nw[a] + U[a]) / C.P.mass;  // Eq. aug
+    }
+    if (mask & DOF_ROT) {
+      nw[6] = nxt[6] + Th;                                 // Eq. atheta
+      nw[7] = nxt[7] + (nw[6] + Om) / C.P.inertia;         // Eq. aomega
+    }
+    for (int a = 0; a < 8; ++a) cur[a] = nw[a];
+  }
+  for (int a = 0; a < 8; ++a) out_b[a] = cur[a];
+  std::vector<double> sens(C.ND, 0.0);
+  alks_sens_step(C, G, st, out->u, &cur[3], cur[7], sens.data());
+  for (size_t m = 0; m < C.ND; ++m) (*dk)[m] += sens[m];
+}
+
+// Terminal body multipliers for J = sum_d w_d s_d(N_t), at the step N_t + 1 (reading above).
+void alks_terminal(const Ctx& C, double* b) {
+  for (int a = 0; a < 8; ++a) b[a] = 0.0;
+  for (int a = 0; a < C.d; ++a) {
+    if (!(C.P.dof_mask & (1 << a))) continue;
+    b[a] = -C.P.obj_w[a];
+    b[3 + a] = -C.P.obj_w[3 + a] / C.P.mass;
+  }
+  if (C.P.dof_mask & DOF_ROT) {
+    b[6] = -C.P.obj_w[6];
+    b[7] = -C.P.obj_w[7] / C.P.inertia;
+  }
+}
+
+void alks_load_moments(const Ctx& C, const double* p, const double* u, const double* s, AdjMoments* a) {
+  a->alloc(C);
+  for (size_t n = 0; n < C.N; ++n) a->p[n] = p ? p[n] : 0.0;
+  for (int i = 0; i < C.d; ++i)
+    for (size_t n = 0; n < C.N; ++n) a->u[i][n] = u ? u[(size_t)i * C.N + n] : 0.0;
+  for (int i = 0; i < C.d; ++i)
+    for (int j = 0; j < C.d; ++j)
+      for (size_t n = 0; n < C.N; ++n) a->s[3 * i + j][n] = s ? s[((size_t)i * C.d + j) * C.N + n] : 0.0;
+}
+
+void alks_store_moments(const Ctx& C, const AdjMoments& a, double* p, double* u, double* s) {
+  if (p)
+    for (size_t n = 0; n < C.N; ++n) p[n] = a.p[n];
+  if (u)
+    for (int i = 0; i < C.d; ++i)
+      for (size_t n = 0; n < C.N; ++n) u[(size_t)i * C.N + n] = a.u[i][n];
+  if (s)
+    for (int i = 0; i < C.d; ++i)
+      for (int j = 0; j < C.d; ++j)
+        for (size_t n = 0; n < C.N; ++n) s[((size_t)i * C.d + j) * C.N + n] = a.s[3 * i + j][n];
+}
+
+void alks_load_velocity(const Ctx& C, const double* u, Fields<double>* st) {
+  st->alloc(C);
+  for (int a = 0; a < C.d; ++a)
+    for (size_t n = 0; n < C.N; ++n) st->u[a][n] = u[(size_t)a * C.N + n];
+}
+
 }  // namespace
 
 // ============================================================================================
@@ -1594,6 +2015,174 @@ int oracle_constraint(const OracleProblem* P, const double* gamma, double* G, do
 double oracle_weight(int kind, double r, double* dw) {
   if (dw) *dw = dwk<double>(kind, r);
   return wk<double>(kind, r);
+}
+
+
+// ------------------------------------------------------------------------------------------
+// The paper's adjoint (ALKS, Sec. 2.5): entry points. Adjoint moments: p~ [N], u~ [dim][N],
+// s~ [dim][dim][N]. Body multipliers: 8 doubles in the DOF-vector order (x~G[3], u~G[3], theta~,
+// omega~). Single rotation axis only (ORC_ERR_ARG with free rotation).
+// ------------------------------------------------------------------------------------------
+
+// Forward + the paper's adjoint with dJ = 1: J, dJ/dgamma [ND] (Eq. design_sensitivity through the
+// design chain), dJ/dkappa^ref [ND], the moments at t = 0 and the body multipliers at t = 1.
+int oracle_gradient_alks(const OracleProblem* P, const double* gamma, const double* p0, const double* u0,
+                         const double* dof0, double* J, double* dJdgamma, double* dJdkref, double* adj_p0,
+                         double* adj_u0, double* adj_s0, double* body1) {
+  Ctx C;
+  if (!make_ctx(P, &C) || C.free_rot) return ORC_ERR_ARG;
+  if (P->nu <= 0.0) return ORC_ERR_UNSTABLE;
+  Chain<double> chain;
+  std::vector<double> kref = brinkman(C, gamma, &chain);
+  Trajectory tr;
+  run_forward(C, kref, p0, u0, dof0, &tr, true);
+  if (C.err) return C.err;
+  const int NT = P->n_steps, ns = C.ns;
+  if (J) *J = objective(C, &tr.s[(size_t)NT * ns]);
+  double nxt[8];
+  alks_terminal(C, nxt);
+  AdjMoments star;
+  star.alloc(C);
+  std::vector<double> dk(C.ND, 0.0);
+  for (int t = NT; t >= 1; --t) {
+    AdjMoments at, prev;
+    double b[8];
+    alks_body_step(C, kref, &tr.s[(size_t)t * ns], tr.states[t], star, nxt, P->n_itr, &at, b, &dk);
+    alks_gather(C, at, tr.states[t], &prev);
+    star = prev;
+    for (int a = 0; a < 8; ++a) nxt[a] = b[a];
+  }
+  if (C.err) return C.err;
+  alks_store_moments(C, star, adj_p0, adj_u0, adj_s0);
+  if (body1)
+    for (int a = 0; a < 8; ++a) body1[a] = nxt[a];
+  std::vector<double> gb3(C.ND, 0.0);
+  for (size_t m = 0; m < C.ND; ++m) {
+    const double den = (1.0 - chain.g3[m]) + P->q;
+    gb3[m] = C.dom[m] ? dk[m] * P->kappa_max * P->q * (1.0 + P->q) / (den * den) : 0.0;
+    if (dJdkref) dJdkref[m] = dk[m];
+  }
+  if (dJdgamma) design_chain_vjp(C, chain, gb3, dJdgamma);
+  return ORC_OK;
+}
+
+// The adjoint equilibrium f~eq [Q][N] of the moments (ap, au, as_) at the velocity u [dim][N].
+int oracle_alks_feq(const OracleProblem* P, const double* ap, const double* au, const double* as_, const double* u,
+                    double* F) {
+  Ctx C;
+  if (!make_ctx(P, &C)) return ORC_ERR_ARG;
+  AdjMoments a;
+  alks_load_moments(C, ap, au, as_, &a);
+  Fields<double> st;
+  alks_load_velocity(C, u, &st);
+  std::vector<double> f;
+  alks_feq_field(C, a, st, &f);
+  std::memcpy(F, f.data(), f.size() * sizeof(double));
+  return ORC_OK;
+}
+
+// Complex-step derivative along df of sum_{n,j} phi_j(n) f^eq_j(n), where f^eq is the forward's
+// equilibrium of the moments p = sum_i f_i / 3, u = sum_i c_i f_i of the distributions f [Q][N].
+int oracle_feq_adjoint_cs(const OracleProblem* P, const double* f, const double* df, const double* phi, double h,
+                          double* out) {
+  Ctx C;
+  if (!make_ctx(P, &C)) return ORC_ERR_ARG;
+  const int Q = C.L.Q, d = C.d;
+  Fields<cplx> s;
+  s.alloc(C);
+  for (size_t n = 0; n < C.N; ++n)
+    for (int i = 0; i < Q; ++i) {
+      const cplx fi(f[(size_t)i * C.N + n], h * df[(size_t)i * C.N + n]);
+      s.p[n] += fi / 3.0;
+      for (int a = 0; a < d; ++a) s.u[a][n] += (double)C.L.c[i][a] * fi;
+    }
+  std::vector<cplx> G;
+  velocity_gradient(C, s, &G);
+  cplx acc(0.0, 0.0);
+  for (size_t n = 0; n < C.N; ++n)
+    for (int i = 0; i < Q; ++i) acc += phi[(size_t)i * C.N + n] * feq(C, i, s, G, n);
+  *out = acc.imag() / h;
+  return ORC_OK;
+}
+
+// Star moments at t - 1 (with the boundary values) from the moments at t and the velocity u(t).
+int oracle_alks_gather(const OracleProblem* P, const double* ap, const double* au, const double* as_,
+                       const double* u, double* op, double* ou, double* os) {
+  Ctx C;
+  if (!make_ctx(P, &C)) return ORC_ERR_ARG;
+  AdjMoments a, o;
+  alks_load_moments(C, ap, au, as_, &a);
+  Fields<double> st;
+  alks_load_velocity(C, u, &st);
+  alks_gather(C, a, st, &o);
+  alks_store_moments(C, o, op, ou, os);
+  return ORC_OK;
+}
+
+// One evaluation of the step's equations at the DOFs s [8] and the velocity u [dim][N], for given
+// star moment ustar [dim][N] and body multipliers ug [3], om: the fluid multiplier of Eq. au into
+// ut [dim][N], the coupling terms (X[3], U[3], Th, Om; see alks_terms) with that ut into terms [8],
+// and the step's term of Eq. design_sensitivity into sens [ND].
+int oracle_alks_parts(const OracleProblem* P, const double* gamma, const double* s, const double* u,
+                      const double* ustar, const double* ug, double om, double* ut, double* terms, double* sens) {
+  Ctx C;
+  if (!make_ctx(P, &C) || C.free_rot) return ORC_ERR_ARG;
+  std::vector<double> kref = brinkman(C, gamma);
+  Fields<double> st;
+  alks_load_velocity(C, u, &st);
+  AlksGeom G;
+  alks_geometry(C, kref, s, st, &G);
+  std::vector<double> us[3], uo[3];
+  for (int a = 0; a < C.d; ++a) us[a].assign(ustar + (size_t)a * C.N, ustar + (size_t)(a + 1) * C.N);
+  alks_fluid(C, G, us, ug, om, uo);
+  for (int a = 0; a < C.d; ++a) std::memcpy(ut + (size_t)a * C.N, uo[a].data(), C.N * sizeof(double));
+  alks_terms(C, kref, G, st, uo, ug, om, s[7], &terms[0], &terms[3], &terms[6], &terms[7]);
+  alks_sens_step(C, G, st, uo, ug, om, sens);
+  return C.err;
+}
+
+// Complex-step derivative of the step Lagrangian (alks_lambda) along dkref [ND], ds [8] and du
+// [dim][N] (each may be NULL), at kappa^ref(gamma), the DOFs s and the velocity u, with the
+// multipliers ut [dim][N], ug [3], om held fixed.
+int oracle_alks_lambda_cs(const OracleProblem* P, const double* gamma, const double* dkref, const double* s,
+                          const double* ds, const double* u, const double* du, const double* ut, const double* ug,
+                          double om, double h, double* out) {
+  Ctx C;
+  if (!make_ctx(P, &C) || C.free_rot) return ORC_ERR_ARG;
+  std::vector<double> kr = brinkman(C, gamma);
+  std::vector<cplx> kref(C.ND);
+  for (size_t m = 0; m < C.ND; ++m) kref[m] = cplx(kr[m], dkref ? h * dkref[m] : 0.0);
+  cplx sc[8];
+  for (int a = 0; a < 8; ++a) sc[a] = cplx(s[a], ds ? h * ds[a] : 0.0);
+  std::vector<cplx> uc[3];
+  std::vector<double> utv[3];
+  for (int a = 0; a < C.d; ++a) {
+    uc[a].resize(C.N);
+    utv[a].assign(ut + (size_t)a * C.N, ut + (size_t)(a + 1) * C.N);
+    for (size_t n = 0; n < C.N; ++n) uc[a][n] = cplx(u[(size_t)a * C.N + n], du ? h * du[(size_t)a * C.N + n] : 0.0);
+  }
+  const cplx L = alks_lambda(C, kref, sc, uc, utv, ug, om);
+  *out = L.imag() / h;
+  return C.err;
+}
+
+// One step of the paper's adjoint with K fixed-point iterations (alks_body_step): from the star
+// moment ustar [dim][N] and the body multipliers nxt [8] at t + 1 to u~ [dim][N] and out_b [8] at t,
+// and the step's design sensitivity sens [ND].
+int oracle_alks_body_step(const OracleProblem* P, const double* gamma, const double* s, const double* u,
+                          const double* ustar, const double* nxt, int K, double* ut, double* out_b, double* sens) {
+  Ctx C;
+  if (!make_ctx(P, &C) || C.free_rot || K < 1) return ORC_ERR_ARG;
+  std::vector<double> kref = brinkman(C, gamma);
+  Fields<double> st;
+  alks_load_velocity(C, u, &st);
+  AdjMoments star, out;
+  alks_load_moments(C, nullptr, ustar, nullptr, &star);
+  std::vector<double> dk(C.ND, 0.0);
+  alks_body_step(C, kref, s, st, star, nxt, K, &out, out_b, &dk);
+  for (int a = 0; a < C.d; ++a) std::memcpy(ut + (size_t)a * C.N, out.u[a].data(), C.N * sizeof(double));
+  if (sens) std::memcpy(sens, dk.data(), C.ND * sizeof(double));
+  return C.err;
 }
 
 }  // extern "C"

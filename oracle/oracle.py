@@ -74,6 +74,13 @@ def lib():
         L.oracle_constraint.argtypes = [pp, dp, dp, dp]
         L.oracle_gradient_terminal.argtypes = [pp, dp, dp, dp, dp, dp, dp, dp, dp, dp, dp, dp, dp, dp]
         L.oracle_forward_cs_terminal.argtypes = [pp, dp, dp, dp, dp, dp, dp, dp, dp, ctypes.c_double, dp]
+        L.oracle_gradient_alks.argtypes = [pp, dp, dp, dp, dp, dp, dp, dp, dp, dp, dp, dp]
+        L.oracle_alks_feq.argtypes = [pp, dp, dp, dp, dp, dp]
+        L.oracle_feq_adjoint_cs.argtypes = [pp, dp, dp, dp, ctypes.c_double, dp]
+        L.oracle_alks_gather.argtypes = [pp, dp, dp, dp, dp, dp, dp, dp]
+        L.oracle_alks_parts.argtypes = [pp, dp, dp, dp, dp, dp, ctypes.c_double, dp, dp, dp]
+        L.oracle_alks_lambda_cs.argtypes = [pp, dp, dp, dp, dp, dp, dp, dp, dp, ctypes.c_double, ctypes.c_double, dp]
+        L.oracle_alks_body_step.argtypes = [pp, dp, dp, dp, dp, dp, ctypes.c_int, dp, dp, dp]
         if L.oracle_sizeof_problem() != ctypes.sizeof(OracleProblem):
             raise RuntimeError("oracle problem record layout mismatch")
         _lib = L
@@ -305,3 +312,83 @@ def forward_cs_terminal(P, gamma, p0, u0, dof0, lam_pT, lam_uT, lam_sT, dgamma, 
                                             _ptr(_f64(p0)), _ptr(_f64(u0)), _ptr(_f64(dof0)), _ptr(_f64(lam_pT)),
                                             _ptr(_f64(lam_uT)), _ptr(_f64(lam_sT)), h, ctypes.byref(dJ)))
     return dJ.value
+
+
+# ---- the paper's adjoint (ALKS, Sec. 2.5) ----------------------------------------------------
+# Moments: p~ [N], u~ [dim, N], s~ [dim, dim, N]. Body multipliers: 8 values in the DOF-vector
+# order (x~G[3], u~G[3], theta~, omega~), the paper's sign (minus the derivatives of J).
+
+
+def gradient_alks(P, gamma, p0, u0, dof0, n_steps: Optional[int] = None):
+    """Forward + the paper's adjoint: J, dJdgamma, dJdkref, the moments at t = 0 (adj_p0, adj_u0,
+    adj_s0) and the body multipliers at t = 1 (body1)."""
+    rec = problem_record(P, n_steps)
+    N, ND, d = P.n_cells, P.n_design, P.dim
+    out = {"dJdgamma": np.zeros(ND), "dJdkref": np.zeros(ND), "adj_p0": np.zeros(N), "adj_u0": np.zeros((d, N)),
+           "adj_s0": np.zeros((d, d, N)), "body1": np.zeros(8)}
+    J = ctypes.c_double(0.0)
+    _check(lib().oracle_gradient_alks(ctypes.byref(rec), _ptr(_f64(gamma)), _ptr(_f64(p0)), _ptr(_f64(u0)),
+                                      _ptr(_f64(dof0)), ctypes.byref(J), _ptr(out["dJdgamma"]), _ptr(out["dJdkref"]),
+                                      _ptr(out["adj_p0"]), _ptr(out["adj_u0"]), _ptr(out["adj_s0"]),
+                                      _ptr(out["body1"])))
+    out["J"] = J.value
+    return out
+
+
+def alks_feq(P, ap, au, as_, u):
+    """The adjoint equilibrium f~eq [Q, N] of the moments at the velocity u."""
+    Q = 9 if P.dim == 2 else 15
+    F = np.zeros((Q, P.n_cells))
+    _check(lib().oracle_alks_feq(ctypes.byref(problem_record(P)), _ptr(_f64(ap)), _ptr(_f64(au)), _ptr(_f64(as_)),
+                                 _ptr(_f64(u)), _ptr(F)))
+    return F
+
+
+def feq_adjoint_cs(P, f, df, phi, h: float = 1e-30):
+    """d/dh of sum phi_j f^eq_j(moments of f + i h df) / h: the forward equilibrium's derivative."""
+    out = ctypes.c_double(0.0)
+    _check(lib().oracle_feq_adjoint_cs(ctypes.byref(problem_record(P)), _ptr(_f64(f)), _ptr(_f64(df)),
+                                       _ptr(_f64(phi)), h, ctypes.byref(out)))
+    return out.value
+
+
+def alks_gather(P, ap, au, as_, u):
+    """Star moments at t - 1 from the moments at t and the velocity u(t), boundary values included."""
+    N, d = P.n_cells, P.dim
+    op, ou, os_ = np.zeros(N), np.zeros((d, N)), np.zeros((d, d, N))
+    _check(lib().oracle_alks_gather(ctypes.byref(problem_record(P)), _ptr(_f64(ap)), _ptr(_f64(au)),
+                                    _ptr(_f64(as_)), _ptr(_f64(u)), _ptr(op), _ptr(ou), _ptr(os_)))
+    return op, ou, os_
+
+
+def alks_parts(P, gamma, s, u, ustar, ug, om):
+    """Eq. au's fluid multiplier, the coupling terms (X[3], U[3], Th, Om) and the step's design
+    sensitivity term, at the DOFs s [8], velocity u, star moment ustar, multipliers ug [3], om."""
+    ut = np.zeros((P.dim, P.n_cells))
+    terms = np.zeros(8)
+    sens = np.zeros(P.n_design)
+    _check(lib().oracle_alks_parts(ctypes.byref(problem_record(P)), _ptr(_f64(gamma)), _ptr(_f64(s)), _ptr(_f64(u)),
+                                   _ptr(_f64(ustar)), _ptr(_f64(ug)), float(om), _ptr(ut), _ptr(terms), _ptr(sens)))
+    return ut, terms, sens
+
+
+def alks_lambda_cs(P, gamma, s, u, ut, ug, om, dkref=None, ds=None, du=None, h: float = 1e-30):
+    """Complex-step derivative of the step Lagrangian along (dkref, ds, du), multipliers fixed."""
+    out = ctypes.c_double(0.0)
+    _check(lib().oracle_alks_lambda_cs(ctypes.byref(problem_record(P)), _ptr(_f64(gamma)),
+                                       _ptr(None if dkref is None else _f64(dkref)), _ptr(_f64(s)),
+                                       _ptr(None if ds is None else _f64(ds)), _ptr(_f64(u)),
+                                       _ptr(None if du is None else _f64(du)), _ptr(_f64(ut)), _ptr(_f64(ug)),
+                                       float(om), h, ctypes.byref(out)))
+    return out.value
+
+
+def alks_body_step(P, gamma, s, u, ustar, nxt, K: int):
+    """One step of the paper's adjoint with K fixed-point iterations: (u~ [dim, N], body [8], sens)."""
+    ut = np.zeros((P.dim, P.n_cells))
+    b = np.zeros(8)
+    sens = np.zeros(P.n_design)
+    _check(lib().oracle_alks_body_step(ctypes.byref(problem_record(P)), _ptr(_f64(gamma)), _ptr(_f64(s)),
+                                       _ptr(_f64(u)), _ptr(_f64(ustar)), _ptr(_f64(nxt)), int(K), _ptr(ut), _ptr(b),
+                                       _ptr(sens)))
+    return ut, b, sens
