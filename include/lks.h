@@ -146,6 +146,23 @@ LKS_API int lks_forward(lks_handle* h, const double* gamma_dev, double* J_host, 
  * no synchronisation. Requires a prior lks_forward (else LKS_ERR_ORDER). */
 LKS_API int lks_adjoint(lks_handle* h, double seed, void* stream);
 
+/* The paper's adjoint, ALKS (Sec. 2.5, Appendix A; Algorithm 1, adjoint loop), in place of the exact
+ * discrete adjoint: the moments p~, u~, s~ of the adjoint distribution (the star moments gathered
+ * from the adjoint equilibrium at x + c_i, Eqs. ap_tmp to as, with the boundary values prescribed)
+ * and the body multipliers (Eqs. axg, aug, atheta, aomega, N_itr fixed-point iterations per step),
+ * accumulating Eq. design_sensitivity; lks_sensitivity then returns its dJ/dgamma. A discretised
+ * continuous adjoint: it approaches the exact gradient of lks_adjoint but is not equal to it.
+ * Seeded with dJ = seed; enqueued on the stream. The first call allocates its buffers (about
+ * (2 (1 + dim + dim(dim+1)/2) + dim) N field values). Single rotation axis only.
+ * Errors: LKS_ERR_ORDER (no forward), LKS_ERR_UNSUPPORTED (free rotation, or a warm-start terminal
+ * adjoint is set), LKS_ERR_OOM / LKS_ERR_BUDGET, LKS_ERR_CUDA. */
+LKS_API int lks_adjoint_alks(lks_handle* h, double seed, void* stream);
+
+/* After lks_adjoint_alks: the moments at t = 0, p~ [N], u~ [dim][N], s~ [dim][dim][N], and the body
+ * multipliers at t = 1 (x~G[3], u~G[3], theta~, omega~; the paper's sign) as host doubles (any may
+ * be NULL). Synchronous. Errors: LKS_ERR_ORDER. */
+LKS_API int lks_get_alks_adjoint(lks_handle* h, double* p_host, double* u_host, double* s_host, double* body_host);
+
 /* dJ/dgamma [ndx*ndy*ndz] (device, FP64) from the last adjoint: the accumulated dJ/dkappa^ref
  * chained through dkappa^ref/dgamma-bar (Eq. brinkman_coefficient) and the transpose of the design
  * chain (projection, filter, cyclic expansion: only orbit representatives receive sensitivity).

@@ -76,6 +76,15 @@ struct lks_handle {
   void* term_L = nullptr;
   double* term_s = nullptr;
   bool has_term = false;
+  // the paper-form adjoint (allocated by its first call): moment slots, box spread, equilibrium
+  // vector Z, per-design-point sensitivity coefficients, design-CTA partials
+  void* al_A = nullptr;
+  void* al_box = nullptr;
+  void* al_z = nullptr;
+  void* al_sens = nullptr;
+  void* al_part = nullptr;
+  long long al_astride = 0;
+  bool alks_mode = false, alks_done = false;
   Dof* it = nullptr;
   Ctrl* ctrl = nullptr;
   Moments* mom = nullptr;
@@ -403,6 +412,18 @@ void enqueue_recompute(lks_handle* h, Launcher& L, const Slots<T>& S, int nsteps
 template <typename T>
 void enqueue_adj_steps(lks_handle* h, Launcher& L, const Slots<T>& S, int nsteps) {
   const Geo& g = h->g;
+  if (h->alks_mode) {  // the paper-form adjoint: body at t, then the equilibrium's star moments at t-1
+    for (int i = 0; i < nsteps; ++i) {
+      L.n("alks_body", 5, [&](cudaStream_t s) {
+        launch_alks_body<T>(g, S, h->ctrl, h->it, (const T*)h->kref, (T*)h->al_box, (T*)h->al_A, h->al_astride,
+                            (T*)h->al_sens, h->al_part, h->dkref, i, s);
+      });
+      L.n("alks_stencil", 2, [&](cudaStream_t s) {
+        launch_alks_stencil<T>(g, S, h->ctrl, (T*)h->al_A, h->al_astride, (T*)h->al_z, i, s);
+      });
+    }
+    return;
+  }
   for (int i = 0; i < nsteps; ++i) {
     for (int k = g.K; k >= 1; --k) {
       L("adj_cell", [&](cudaStream_t s) {
@@ -504,7 +525,7 @@ int binomial_reverse(lks_handle* h, cudaStream_t st, int t0, int n, int s, bool 
   };
   auto reverse_step = [&](int t) -> int {  // needs state(t-1) in the working pair (base t0)
     L0("init", [&](cudaStream_t x) { launch_set_step(h->ctrl, t, t0, x); });
-    return run_graph(h, "bin_rev1", st, [&](Launcher& L) {
+    return run_graph(h, h->alks_mode ? "alks_bin_rev1" : "bin_rev1", st, [&](Launcher& L) {
       enqueue_recompute<T>(h, L, W, 1);
       enqueue_adj_steps<T>(h, L, W, 1);
     });
@@ -538,14 +559,19 @@ int adjoint_impl(lks_handle* h, double seed, cudaStream_t st) {
   const Geo& g = h->g;
   const int NT = h->P.n_steps;
   Launcher L0{h, st, false};
-  CK(cudaMemsetAsync(h->L, 0, 2 * h->slot_elems * h->esz, st));
-  if (h->has_term)  // lambda(N_t) sits in slot N_t mod 2 of the adjoint pair
-    CK(cudaMemcpyAsync((char*)h->L + (size_t)(NT & 1) * h->slot_elems * h->esz, h->term_L, h->slot_elems * h->esz,
-                       cudaMemcpyDeviceToDevice, st));
-  const double* term_s = h->has_term ? h->term_s : nullptr;
-  L0("init", [&](cudaStream_t s) {
-    launch_adj_init(g, h->ctrl, h->it, h->P.n_steps, h->objw, seed, term_s, h->dkref, g.ND, s);
-  });
+  if (h->alks_mode) {  // fluid multipliers zero at N_t + 1, terminal body multipliers
+    CK(cudaMemsetAsync(h->al_A, 0, 2 * (size_t)h->al_astride * h->esz, st));
+    L0("init", [&](cudaStream_t s) { launch_alks_init(g, h->ctrl, h->objw, seed, h->dkref, s); });
+  } else {
+    CK(cudaMemsetAsync(h->L, 0, 2 * h->slot_elems * h->esz, st));
+    if (h->has_term)  // lambda(N_t) sits in slot N_t mod 2 of the adjoint pair
+      CK(cudaMemcpyAsync((char*)h->L + (size_t)(NT & 1) * h->slot_elems * h->esz, h->term_L, h->slot_elems * h->esz,
+                         cudaMemcpyDeviceToDevice, st));
+    const double* term_s = h->has_term ? h->term_s : nullptr;
+    L0("init", [&](cudaStream_t s) {
+      launch_adj_init(g, h->ctrl, h->it, h->P.n_steps, h->objw, seed, term_s, h->dkref, g.ND, s);
+    });
+  }
   if (h->P.ckpt_policy == LKS_CKPT_BINOMIAL) {
     TRY(binomial_reverse<T>(h, st, 0, NT, h->P.ckpt_every, true, -1, 0));
   } else if (h->P.ckpt_policy == LKS_CKPT_STORE_ALL) {
@@ -553,7 +579,8 @@ int adjoint_impl(lks_handle* h, double seed, cudaStream_t st) {
     for (int t1 = NT; t1 >= 1; t1 -= h->chunk) {
       const int n = std::min(h->chunk, t1);
       L0("init", [&](cudaStream_t s) { launch_set_step(h->ctrl, t1, 0, s); });
-      TRY(run_graph(h, "adj_sa_" + std::to_string(n), st, [&](Launcher& L) { enqueue_adj_steps<T>(h, L, S, n); }));
+      TRY(run_graph(h, (h->alks_mode ? "alks_sa_" : "adj_sa_") + std::to_string(n), st,
+                    [&](Launcher& L) { enqueue_adj_steps<T>(h, L, S, n); }));
     }
   } else {
     Slots<T> S = ring_slots<T>(h);
@@ -575,7 +602,8 @@ int adjoint_impl(lks_handle* h, double seed, cudaStream_t st) {
       L0("init", [&](cudaStream_t s) { launch_set_step(h->ctrl, t0 + 1, t0, s); });
       TRY(run_graph(h, "rec_" + std::to_string(n), st, [&](Launcher& L) { enqueue_recompute<T>(h, L, S, n); }));
       L0("init", [&](cudaStream_t s) { launch_set_step(h->ctrl, t0 + n, t0, s); });
-      TRY(run_graph(h, "adj_u_" + std::to_string(n), st, [&](Launcher& L) { enqueue_adj_steps<T>(h, L, S, n); }));
+      TRY(run_graph(h, (h->alks_mode ? "alks_u_" : "adj_u_") + std::to_string(n), st,
+                    [&](Launcher& L) { enqueue_adj_steps<T>(h, L, S, n); }));
     }
   }
   CK(cudaGetLastError());
@@ -855,6 +883,62 @@ int lks_adjoint(lks_handle* h, double seed, void* stream) {
     collect_timers(h);
   }
   h->adj_done = true;
+  return LKS_OK;
+}
+
+int lks_adjoint_alks(lks_handle* h, double seed, void* stream) {
+  if (!h) return LKS_ERR_ARG;
+  if (!h->fwd_done) return LKS_ERR_ORDER;
+  if (h->g.ax == AX_FREE || h->has_term) return LKS_ERR_UNSUPPORTED;
+  const Geo& g = h->g;
+  if (!h->al_A) {
+    h->al_astride = (long long)alks_planes(g.dim) * g.N;
+    TRY(dalloc(h, &h->al_A, 2 * (size_t)h->al_astride * h->esz));
+    TRY(dalloc(h, &h->al_box, (size_t)(1 + 2 * g.dim) * g.box_cells * h->esz));
+    TRY(dalloc(h, &h->al_z, (size_t)g.dim * g.N * h->esz));
+    TRY(dalloc(h, &h->al_sens, (size_t)alks_sens_values(g.dim) * g.ND * h->esz));
+    const long long nb = (g.ND + kDesignPointsPerCta - 1) / kDesignPointsPerCta;
+    TRY(dalloc(h, &h->al_part, (size_t)nb * alks_partial_values(g.dim) * 2 * sizeof(double)));
+  }
+  cudaStream_t st = (cudaStream_t)stream;
+  h->alks_mode = true;
+  int r = (h->prec == LKS_FP64) ? adjoint_impl<double>(h, seed, st) : adjoint_impl<float>(h, seed, st);
+  h->alks_mode = false;
+  if (r != LKS_OK) return r;
+  if (h->timing) {
+    CK(cudaStreamSynchronize(st));
+    collect_timers(h);
+  }
+  h->adj_done = h->alks_done = true;
+  return LKS_OK;
+}
+
+int lks_get_alks_adjoint(lks_handle* h, double* p, double* u, double* s, double* body) {
+  if (!h) return LKS_ERR_ARG;
+  if (!h->alks_done) return LKS_ERR_ORDER;
+  const int d = h->g.dim;
+  const long long N = h->g.N, M = h->al_astride;
+  std::vector<char> raw((size_t)M * h->esz);
+  CK(cudaDeviceSynchronize());
+  CK(cudaMemcpy(raw.data(), h->al_A, raw.size(), cudaMemcpyDeviceToHost));  // the moments at t = 0: slot 0
+  auto val = [&](long long i) {
+    return (h->esz == 8) ? ((const double*)raw.data())[i] : (double)((const float*)raw.data())[i];
+  };
+  for (long long n = 0; n < N; ++n) {
+    if (p) p[n] = val(n);
+    for (int a = 0; a < d; ++a) {
+      if (u) u[a * N + n] = val((1 + a) * N + n);
+      for (int b = 0; b < d; ++b) {
+        const int k = (a == b) ? a : (d == 2 ? 2 : (a + b == 1 ? 3 : (a + b == 2 ? 4 : 5)));
+        if (s) s[((long long)a * d + b) * N + n] = val((1 + d + k) * N + n);
+      }
+    }
+  }
+  if (body) {
+    Ctrl c;
+    CK(cudaMemcpy(&c, h->ctrl, sizeof(Ctrl), cudaMemcpyDeviceToHost));
+    for (int a = 0; a < 8; ++a) body[a] = c.al_b[a];
+  }
   return LKS_OK;
 }
 

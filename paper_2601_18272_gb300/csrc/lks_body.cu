@@ -26,38 +26,12 @@
 // partial per CTA (double-float pairs in the FP32 form) and a one-warp finish kernel that sums the
 // partials in a fixed order and applies the (reverse) EOM: the kernel boundary orders the partials, so no GPU-scope fence or counter is
 // needed, and the sums are deterministic.
-#include "lks_kernels.h"
+#include "lks_body_common.cuh"
 
 namespace lks {
 
 namespace {
 
-// Box-cell kernels: LN consecutive threads share one cell's gather (candidate rows split among
-// them), CX x CY cells per CTA. Design-point kernel: LN threads per point (rows, or planes in 3D,
-// of its support window), kDesignPointsPerCta points per CTA. The split multiplies the resident
-// warps of these latency-bound kernels by LN.
-constexpr int LN = kLanesPerCell;
-constexpr int CX = kBoxCtaCellsX, CY = kBoxCtaCellsY;
-constexpr int kCellThreads = CX * CY * LN;
-constexpr int kDesignBlock = kDesignPointsPerCta * LN;
-constexpr int kFinishThreads = 256;
-
-struct CellSlot {
-  int j0, j1, j2, lane;
-  bool active;  // inside the box
-};
-__device__ __forceinline__ CellSlot cell_slot(const Geo& g) {
-  CellSlot c;
-  const int q = threadIdx.x / LN;
-  c.lane = threadIdx.x % LN;
-  c.j0 = blockIdx.x * CX + q % CX;
-  c.j1 = blockIdx.y * CY + q / CX;
-  c.j2 = blockIdx.z;
-  c.active = c.j0 < g.B[0] && c.j1 < g.B[1];
-  return c;
-}
-
-__device__ __forceinline__ int block_linear() { return blockIdx.x + gridDim.x * (blockIdx.y + gridDim.y * blockIdx.z); }
 
 // Partial sums per CTA: the coupling reduces force and torque (one torque component about the
 // axis, or the torque vector with free rotation); the design-point reverse reduces dJ/ds^(k-1)
@@ -66,30 +40,6 @@ template <int AX>
 __host__ __device__ constexpr int nv_couple() { return AX == AX_FREE ? 6 : 4; }
 template <int AX>
 __host__ __device__ constexpr int nv_design() { return AX == AX_FREE ? 18 : 8; }
-
-// R and omega of a free-rotation iterate in the field type.
-template <typename T>
-struct FreeView;
-template <>
-struct FreeView<float> {
-  float R[9], om[3];
-  __device__ __forceinline__ explicit FreeView(const Dof& d) {
-#pragma unroll
-    for (int i = 0; i < 9; ++i) R[i] = d.Rf[i];
-#pragma unroll
-    for (int a = 0; a < 3; ++a) om[a] = d.omf[a];
-  }
-};
-template <>
-struct FreeView<double> {
-  double R[9], om[3];
-  __device__ __forceinline__ explicit FreeView(const Dof& d) {
-#pragma unroll
-    for (int i = 0; i < 9; ++i) R[i] = d.s[S_R + i];
-#pragma unroll
-    for (int a = 0; a < 3; ++a) om[a] = d.s[S_OM + a];
-  }
-};
 
 // dJ/dF and dJ/dT of the iteration being reversed, in the field type (dJ/dT about the axis in [0]).
 template <typename T>
@@ -115,30 +65,6 @@ __device__ __forceinline__ void lam_store(Ctrl* ctrl, const double* lF, const do
     ctrl->lam_Ff[a] = (float)lF[a];
     ctrl->lam_T[a] = lT[a];
     ctrl->lam_Tf[a] = (float)lT[a];
-  }
-}
-
-// Gather of the cell's design-point sums under the iterate's rotation, and from them the
-// rotational part of the solid velocity (omega R' sum W r, or omega x R sum W r) and the lever
-// sum L_n = R sum W kappa r.
-template <typename T, int D, int AX>
-__device__ __forceinline__ void gather_cell(const Geo& g, const T* __restrict__ kref, const Dof& sk,
-                                            const DofView<T>& V, const T (&d)[3], int lane, bool active, Acc<T>& A,
-                                            T (&rotv)[3], T (&L)[3]) {
-  if constexpr (AX == AX_FREE) {
-    const FreeView<T> FV(sk);
-    gather_free_lanes<T, LN>(g, kref, d, FV.R, lane, active, A);
-    T Rwr[3];
-    matvec3(FV.R, A.wr, Rwr);
-    cross3(FV.om, Rwr, rotv);
-    matvec3(FV.R, A.kr, L);
-  } else {
-    gather_lanes<T, D, AX, LN>(g, kref, d, V.cs, V.sn, lane, active, A);
-    T dwr[3];
-    drot<AX>(V.cs, V.sn, A.wr, dwr);
-#pragma unroll
-    for (int a = 0; a < 3; ++a) rotv[a] = V.om * dwr[a];
-    rot<AX>(V.cs, V.sn, A.kr, L);
   }
 }
 
@@ -880,26 +806,9 @@ __global__ void k_ckpt_pack(Geo g, Slots<T> S, T* ckpt, long long cstride, int e
     dst[i] = src[i];
 }
 
-inline dim3 box_grid(const Geo& g) {
-  return dim3((g.B[0] + CX - 1) / CX, (g.B[1] + CY - 1) / CY, g.dim == 3 ? g.B[2] : 1);
-}
 
 }  // namespace
 
-// Dispatch on the dimension and the (runtime) rotation axis to the compile-time instantiation.
-#define LKS_BOX_DISPATCH(KERNEL, GRID, BLOCK, ...)          \
-  do {                                                      \
-    if (g.dim == 2)                                         \
-      launch(KERNEL<T, 2, 2>, GRID, BLOCK, 0, st, __VA_ARGS__); \
-    else if (g.ax == 0)                                     \
-      launch(KERNEL<T, 3, 0>, GRID, BLOCK, 0, st, __VA_ARGS__); \
-    else if (g.ax == 1)                                     \
-      launch(KERNEL<T, 3, 1>, GRID, BLOCK, 0, st, __VA_ARGS__); \
-    else if (g.ax == 2)                                     \
-      launch(KERNEL<T, 3, 2>, GRID, BLOCK, 0, st, __VA_ARGS__); \
-    else                                                    \
-      launch(KERNEL<T, 3, AX_FREE>, GRID, BLOCK, 0, st, __VA_ARGS__); \
-  } while (0)
 
 
 template <typename T>

@@ -115,6 +115,11 @@ struct Ctrl {
   double lam_T[3];        // adjoint: dJ/dT (about the axis in [0], or the vector with free rotation)
   double lam_s0[kNdofFree];  // adjoint: dJ/ds(0) after the sweep
   float lam_Ff[3], lam_Tf[3];  // FP32 copies of lam_F, lam_T
+  // the paper-form adjoint (ALKS): body multipliers (x~G[3], u~G[3], theta~, omega~) of the step
+  // last finished, and its u~G[3], omega~ of fixed-point iterations N_itr - 1 and N_itr
+  double al_b[8];
+  double al_it[8];
+  float al_itf[8];  // FP32 copies of al_it
 };
 
 // Design-grid moments used by the closed-form design-side force and torque terms.

@@ -136,4 +136,23 @@ template <typename T>
 void launch_ckpt_pack(const Geo& g, const Slots<T>& S, T* ckpt, long long cstride, int every, const Ctrl* ctrl, int di,
                       cudaStream_t st);
 
+
+// The paper-form adjoint (ALKS; lks_alks.cu). Moment slots Ab[t & 1] hold p~, u~[dim] and the
+// distinct entries of s~ (alks_planes planes of N values); abox: kappa, u^S[dim], the omega~ source
+// [dim] per box cell; sstore: alks_sens_values per design point; partials: alks_partial_values per
+// design-point CTA.
+int alks_partial_values(int dim);
+int alks_sens_values(int dim);
+int alks_planes(int dim);
+void launch_alks_init(const Geo& g, Ctrl* ctrl, const double* objw, double seed, double* dkref, cudaStream_t st);
+// Step t = ctrl->t0 - di: spread, coupling sums, fixed-point iterations, u~(t) in the box, the
+// step's design sensitivity (5 kernels).
+template <typename T>
+void launch_alks_body(const Geo& g, const Slots<T>& S, Ctrl* ctrl, const Dof* it, const T* kref, T* abox, T* Ab,
+                      long long astride, T* sstore, void* partials, double* dkref, int di, cudaStream_t st);
+// Step t: the adjoint equilibrium at t and the star moments at t - 1 with boundary values (2 kernels).
+template <typename T>
+void launch_alks_stencil(const Geo& g, const Slots<T>& S, const Ctrl* ctrl, T* Ab, long long astride, T* zb, int di,
+                         cudaStream_t st);
+
 }  // namespace lks

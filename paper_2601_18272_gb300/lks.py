@@ -96,6 +96,8 @@ def load() -> ctypes.CDLL:
     L.lks_get_dof_history.argtypes = [hp, dp, sz]
     L.lks_get_state.argtypes = [hp, dp, dp]
     L.lks_get_initial_adjoint.argtypes = [hp, dp, dp, dp]
+    L.lks_adjoint_alks.argtypes = [hp, ctypes.c_double, vp]
+    L.lks_get_alks_adjoint.argtypes = [hp, dp, dp, dp, dp]
     L.lks_launch_count.argtypes = [hp]
     L.lks_launch_count.restype = ctypes.c_longlong
     L.lks_set_kernel_timing.argtypes = [hp, ctypes.c_int]
@@ -192,6 +194,19 @@ def lks_forward(h, gamma_dev_ptr: int, stream: int = 0) -> float:
 
 def lks_adjoint(h, seed: float = 1.0, stream: int = 0):
     _check(load().lks_adjoint(h, float(seed), ctypes.c_void_p(stream)), "lks_adjoint")
+
+
+def lks_adjoint_alks(h, seed: float = 1.0, stream: int = 0):
+    _check(load().lks_adjoint_alks(h, float(seed), ctypes.c_void_p(stream)), "lks_adjoint_alks")
+
+
+def lks_get_alks_adjoint(h, n_cells: int, dim: int):
+    p = np.zeros(n_cells)
+    u = np.zeros((dim, n_cells))
+    s = np.zeros((dim, dim, n_cells))
+    body = np.zeros(8)
+    _check(load().lks_get_alks_adjoint(h, _dptr(p), _dptr(u), _dptr(s), _dptr(body)), "lks_get_alks_adjoint")
+    return p, u, s, body
 
 
 def lks_sensitivity(h, out_dev_ptr: int, stream: int = 0):
@@ -305,6 +320,16 @@ class Solver:
         import torch
         st = torch.cuda.current_stream() if stream is None else stream
         lks_adjoint(self.handle, seed, st.cuda_stream)
+
+    def adjoint_alks(self, seed: float = 1.0, stream=None):
+        """The paper's adjoint (ALKS) in place of the exact one; sensitivity() then gives its dJ/dgamma."""
+        import torch
+        st = torch.cuda.current_stream() if stream is None else stream
+        lks_adjoint_alks(self.handle, seed, st.cuda_stream)
+
+    def alks_adjoint(self):
+        """(p~, u~, s~) at t = 0 and the body multipliers at t = 1 of the last adjoint_alks."""
+        return lks_get_alks_adjoint(self.handle, self.P.n_cells, self.P.dim)
 
     def sensitivity(self, out, stream=None):
         import torch
