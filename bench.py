@@ -166,7 +166,9 @@ def _family_times(solver, run):
     run()
     torch.cuda.synchronize()
     fams = {f: lks.lks_kernel_time(solver.handle, f)
-            for f in ("stencil_fwd", "couple", "recompute", "adj_cell", "adj_design", "stencil_adj")}
+            for f in ("stencil_fwd", "couple", "recompute", "adj_cell", "adj_design", "stencil_adj", "alks_body",
+                      "alks_stencil")}
+    fams = {f: v for f, v in fams.items() if v[1] > 0}
     lks.lks_set_kernel_timing(solver.handle, False)
     return fams
 
@@ -245,6 +247,75 @@ def gradient_throughput(dev, flush, index: int, n_steps: int = 0, plain_fp64: bo
                                        "workspace_gb": lks.lks_workspace_bytes(S.handle) / 1e9}
         out["dJdgamma_rel_l2_vs_fp64"] = float(torch.linalg.norm(g32 - grad) / torch.linalg.norm(grad))
         S.close()
+    return out
+
+
+def paper_adjoint_study(dev, flush) -> dict:
+    """The paper's adjoint (ALKS, lks_adjoint_alks) beside the exact discrete adjoint. On the 512x256
+    gradient workload: its time per gradient and its deviation from the exact gradient. On the 80x40
+    translation workload and the two sensitivity checks of Appendix B (FP64): its deviation from the
+    exact gradient and both against central differences along seeded random directions."""
+    import numpy as np
+    import torch
+    from paper_2601_18272_gb300.lks import Solver
+    from workloads import config, verification
+    stream = torch.cuda.current_stream(dev)
+    out = {}
+    P, g = config(2)
+    gamma = torch.tensor(g, dtype=torch.float64, device=dev)
+    gex, gpa = torch.empty_like(gamma), torch.empty_like(gamma)
+    S = Solver(P)
+
+    def paper():
+        S.forward(gamma)
+        S.adjoint_alks(1.0)
+        S.sensitivity(gpa)
+
+    S.forward(gamma)
+    S.adjoint(1.0)
+    S.sensitivity(gex)
+    paper()
+    torch.cuda.synchronize()
+    flush.zero_()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    paper()
+    e1.record(stream)
+    e1.synchronize()
+    ms = e0.elapsed_time(e1)
+    fams = _family_times(S, paper)
+    S.close()
+    a, b = gex.cpu().numpy(), gpa.cpu().numpy()
+    out[P.name] = {"ms_per_gradient": ms, "value": P.n_cells * P.n_steps / (ms / 1000.0), "unit": UNIT,
+                   "kernel_ms_per_gradient": {k: round(v[0], 3) for k, v in fams.items()},
+                   "launches_per_gradient": {k: v[1] for k, v in fams.items()},
+                   "rel_l2_vs_exact": float(np.linalg.norm(b - a) / np.linalg.norm(a)),
+                   "cosine_vs_exact": float(a @ b / (np.linalg.norm(a) * np.linalg.norm(b)))}
+    rng = np.random.default_rng(20260118)
+    for (P, g), ndir in ((config(1), 3), (verification("translation"), 2), (verification("rotation"), 2)):
+        S = Solver(P)
+        gam = torch.tensor(g, dtype=torch.float64, device=dev)
+        S.forward(gam)
+        S.adjoint(1.0)
+        S.sensitivity(gex)
+        S.adjoint_alks(1.0)
+        S.sensitivity(gpa)
+        torch.cuda.synchronize()
+        a, b = gex.cpu().numpy(), gpa.cpu().numpy()
+        h = 1e-5
+        dirs = []
+        for _ in range(ndir):
+            v = rng.standard_normal(P.n_design)
+            jp = S.forward(torch.tensor(g + h * v, dtype=torch.float64, device=dev))
+            jm = S.forward(torch.tensor(g - h * v, dtype=torch.float64, device=dev))
+            fd = (jp - jm) / (2 * h)
+            dirs.append({"fd": fd, "exact": float(a @ v), "paper": float(b @ v)})
+        S.close()
+        out[P.name] = {"n_steps": P.n_steps, "rel_l2_vs_exact": float(np.linalg.norm(b - a) / np.linalg.norm(a)),
+                       "cosine_vs_exact": float(a @ b / (np.linalg.norm(a) * np.linalg.norm(b))),
+                       "exact_vs_fd_max_rel": max(abs(d["exact"] - d["fd"]) / abs(d["fd"]) for d in dirs),
+                       "paper_vs_fd_max_rel": max(abs(d["paper"] - d["fd"]) / abs(d["fd"]) for d in dirs),
+                       "directions": dirs}
     return out
 
 
@@ -495,6 +566,7 @@ def main():
         line["body3d"] = gradient_throughput(dev, flush, 4)
         line["turbine3d_6dof"] = gradient_throughput(dev, flush, 5, n_steps=200, plain_fp64=True)
         line["ckpt_precision"] = ckpt_precision_study(dev)
+        line["paper_adjoint"] = paper_adjoint_study(dev, flush)
         line["cpu_baseline"] = cpu_baseline(args.cpu_sample_steps)
     solver.close()
     if rank == 0:

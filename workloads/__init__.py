@@ -31,4 +31,5 @@ from .synth import (  # noqa: F401
     initial_state,
     mass_properties,
     splitmix64_uniform,
+    verification,
 )

@@ -287,6 +287,31 @@ def _cfg5(**kw) -> tuple:
 _CONFIGS = {1: _cfg1, 2: _cfg2, 3: _cfg3, 4: _cfg4, 5: _cfg5}
 
 
+def verification(kind: str) -> tuple:
+    """(Problem, gamma) of the sensitivity checks of Appendix B with the paper's parameters and a
+    geometry of our own (the paper draws it only in a figure): a pressure-driven channel of 600x100
+    cells (inlet pressure dp, outlet 0, no-slip walls in y) and a 20x20 design grid, FP64, every
+    state stored.
+      translation: x-translation only, J = x^G_x(N_t); N_t = 3000, nu = 0.1, M = 1e3, dp = 1e-2,
+                   kappa_max = 300, q = 1e-2
+      rotation:    rotation only, J = theta(N_t); N_t = 10000, nu = 0.1, I = 1e6, dp = 1e-2,
+                   kappa_max = 200, q = 1e-2"""
+    nd, seed = 20, 20260118 + (11 if kind == "translation" else 12)
+    g = gamma_2d(nd, seed)
+    common = dict(dim=2, nx=600, ny=100, nz=1, ndx=nd, ndy=nd, ndz=1, rot_axis=2, nu=0.1, u_in=0.0, dp=1e-2,
+                  bc=(BC_PRESSURE, BC_WALL, BC_PERIODIC), weight_kind=W_COS4, n_itr=5, field_precision=64,
+                  ckpt_policy=CKPT_STORE_ALL, seed=seed)
+    if kind == "translation":
+        P = Problem(body_centre=(150.0, 50.0, 0.0), dof_mask=DOF_TX, mass=1e3, inertia=1.0, kappa_max=300.0, q=1e-2,
+                    n_steps=3000, obj_weights=_obj(0), name="verify_translation_600x100_d20", **common)
+    elif kind == "rotation":
+        P = Problem(body_centre=(150.0, 50.0, 0.0), dof_mask=DOF_ROT, mass=1.0, inertia=1e6, kappa_max=200.0,
+                    q=1e-2, n_steps=10000, obj_weights=_obj(6), name="verify_rotation_600x100_d20", **common)
+    else:
+        raise ValueError(kind)
+    return P, g
+
+
 def config_names() -> dict:
     return {k: v()[0].name for k, v in _CONFIGS.items() if k <= 2}
 
