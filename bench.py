@@ -295,6 +295,7 @@ def paper_adjoint_study(dev, flush) -> dict:
     for (P, g), ndir in ((config(1), 3), (verification("translation"), 2), (verification("rotation"), 2)):
         S = Solver(P)
         gam = torch.tensor(g, dtype=torch.float64, device=dev)
+        gex, gpa = torch.empty_like(gam), torch.empty_like(gam)
         S.forward(gam)
         S.adjoint(1.0)
         S.sensitivity(gex)

@@ -146,6 +146,12 @@ LKS_API int lks_forward(lks_handle* h, const double* gamma_dev, double* J_host, 
  * no synchronisation. Requires a prior lks_forward (else LKS_ERR_ORDER). */
 LKS_API int lks_adjoint(lks_handle* h, double seed, void* stream);
 
+/* Continuation step (Sec. 3.3): the convexity parameter q of Eq. brinkman_coefficient and the
+ * projection steepness beta of Eq. projection for the following forward and adjoint calls (beta 0
+ * turns the projection off; a positive beta needs 0 < proj_eta < 1 from lks_create). Synchronises
+ * the device; the next lks_adjoint needs a new lks_forward. Errors: LKS_ERR_ARG. */
+LKS_API int lks_set_continuation(lks_handle* h, double q, double proj_beta);
+
 /* The paper's adjoint, ALKS (Sec. 2.5, Appendix A; Algorithm 1, adjoint loop), in place of the exact
  * discrete adjoint: the moments p~, u~, s~ of the adjoint distribution (the star moments gathered
  * from the adjoint equilibrium at x + c_i, Eqs. ap_tmp to as, with the boundary values prescribed)

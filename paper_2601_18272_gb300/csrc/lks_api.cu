@@ -886,6 +886,19 @@ int lks_adjoint(lks_handle* h, double seed, void* stream) {
   return LKS_OK;
 }
 
+int lks_set_continuation(lks_handle* h, double q, double proj_beta) {
+  if (!h) return LKS_ERR_ARG;
+  if (!(q > 0.0) || !std::isfinite(q) || !(proj_beta >= 0.0) || !std::isfinite(proj_beta)) return LKS_ERR_ARG;
+  if (proj_beta > 0.0 && !(h->P.proj_eta > 0.0 && h->P.proj_eta < 1.0)) return LKS_ERR_ARG;
+  CK(cudaDeviceSynchronize());
+  h->P.q = q;
+  h->P.proj_beta = proj_beta;
+  h->g.pbeta = proj_beta;
+  clear_graphs(h);  // no captured launch may keep the old values
+  h->fwd_done = h->adj_done = h->alks_done = false;
+  return LKS_OK;
+}
+
 int lks_adjoint_alks(lks_handle* h, double seed, void* stream) {
   if (!h) return LKS_ERR_ARG;
   if (!h->fwd_done) return LKS_ERR_ORDER;

@@ -97,6 +97,7 @@ def load() -> ctypes.CDLL:
     L.lks_get_state.argtypes = [hp, dp, dp]
     L.lks_get_initial_adjoint.argtypes = [hp, dp, dp, dp]
     L.lks_adjoint_alks.argtypes = [hp, ctypes.c_double, vp]
+    L.lks_set_continuation.argtypes = [hp, ctypes.c_double, ctypes.c_double]
     L.lks_get_alks_adjoint.argtypes = [hp, dp, dp, dp, dp]
     L.lks_launch_count.argtypes = [hp]
     L.lks_launch_count.restype = ctypes.c_longlong
@@ -194,6 +195,10 @@ def lks_forward(h, gamma_dev_ptr: int, stream: int = 0) -> float:
 
 def lks_adjoint(h, seed: float = 1.0, stream: int = 0):
     _check(load().lks_adjoint(h, float(seed), ctypes.c_void_p(stream)), "lks_adjoint")
+
+
+def lks_set_continuation(h, q: float, proj_beta: float):
+    _check(load().lks_set_continuation(h, float(q), float(proj_beta)), "lks_set_continuation")
 
 
 def lks_adjoint_alks(h, seed: float = 1.0, stream: int = 0):
@@ -320,6 +325,10 @@ class Solver:
         import torch
         st = torch.cuda.current_stream() if stream is None else stream
         lks_adjoint(self.handle, seed, st.cuda_stream)
+
+    def set_continuation(self, q: float, proj_beta: float):
+        """Continuation step (Sec. 3.3): new q and Heaviside beta for the following calls."""
+        lks_set_continuation(self.handle, q, proj_beta)
 
     def adjoint_alks(self, seed: float = 1.0, stream=None):
         """The paper's adjoint (ALKS) in place of the exact one; sensitivity() then gives its dJ/dgamma."""
