@@ -22,7 +22,8 @@
 //   k_alks_gather   all nodes: the star moments at t - 1 (Eqs. ap_tmp, au_tmp, as_tmp),
 //                   p~* = sum_i w_i f~eq_i(x + c_i) and its first and second moments, with the boundary
 //                   values prescribed: a quantity the forward fixes has a zero multiplier, one it
-//                   copies from the inward neighbour copies the neighbour's, s~ is copied.
+//                   copies from the inward neighbour copies the neighbour's, except u~ at the outlet
+//                   plane, the adjoint's inflow plane, which is zero; s~ is copied.
 // The terminal multipliers (x~G = -dJ/dxG, M u~G = -dJ/duG, theta~ = -dJ/dtheta, I omega~ = -dJ/domega)
 // belong to a step N_t + 1; the fluid multipliers start at zero.
 #include "lks_body_common.cuh"
@@ -507,7 +508,7 @@ __global__ void __launch_bounds__(256) k_alks_gather(Geo g, const Ctrl* ctrl, T*
     int x[3];
     node_coords<D>(g, n, x);
     // boundary node: the value of its inward neighbour (through every boundary axis), with a zero
-    // multiplier for what the forward prescribes there
+    // multiplier for what the forward prescribes there and for u~ on the outlet plane
     bool zp = false, zu = false;
     if (g.bc[0] != BC_PERIODIC) {
       if (x[0] == 0) {
@@ -518,7 +519,7 @@ __global__ void __launch_bounds__(256) k_alks_gather(Geo g, const Ctrl* ctrl, T*
           zp = true;
       } else if (x[0] == g.n[0] - 1) {
         x[0] = g.n[0] - 2;
-        zp = true;
+        zp = zu = true;
       }
     }
 #pragma unroll
