@@ -1240,10 +1240,10 @@ int run_forward(Ctx& C, const std::vector<double>& kref, const double* p0, const
 //     copies the boundary node;
 //   - boundary values: a quantity the forward prescribes (inlet and wall velocity, outlet pressure,
 //     the pressure of a pressure boundary) has a zero multiplier; one the forward copies from the
-//     inward neighbour copies the neighbour's multiplier, except the velocity at the outlet plane:
-//     the adjoint travels upstream, so the outlet is its inflow plane and takes u~ = 0 (copying
-//     it there made the sweep grow without bound once the outflow was fast); s~ is copied on every
-//     boundary;
+//     inward neighbour copies the neighbour's multiplier, except the velocity at the outlet plane,
+//     which follows the outflow condition of the convective adjoint, (u . n) u~ + nu du~/dn = 0
+//     (a plain copy there made the sweep grow without bound once the outflow was fast); s~ is
+//     copied on every boundary;
 //   - single rotation axis only (the paper's setting); the derivative of the lever arm and of the
 //     solid velocity with respect to theta follow Eqs. rigid_body_position and rigid_body_velocity.
 // ------------------------------------------------------------------------------------------
@@ -1315,8 +1315,9 @@ void alks_feq_field(const Ctx& C, const AdjMoments& a, const Fields<double>& st,
 
 // Boundary values of the adjoint moments (reading above), in the forward's phase order: walls zero
 // u~ and copy p~, s~; the inlet copies p~ (inflow/outflow) or zeroes it (pressure), zeroes u~
-// (inflow/outflow) or copies it (pressure); the outlet zeroes p~ and u~; s~ is copied.
-void alks_boundaries(const Ctx& C, AdjMoments* o) {
+// (inflow/outflow) or copies it (pressure); the outlet zeroes p~ and scales the inward u~ by
+// nu / (nu + u_x) (the state's outflow velocity there); s~ is copied.
+void alks_boundaries(const Ctx& C, const Fields<double>& st, AdjMoments* o) {
   const int d = C.d;
   int x[3];
   auto copy_s = [&](size_t n, size_t m) {
@@ -1346,9 +1347,12 @@ void alks_boundaries(const Ctx& C, AdjMoments* o) {
     const bool inlet = (x[0] == 0);
     const size_t m = idx(C, inlet ? 1 : C.n[0] - 2, x[1], x[2]);
     const bool p_fixed = (bcx == BC_PRESSURE) || !inlet;      // outlet, or either pressure plane
-    const bool u_fixed = !inlet || bcx == BC_INFLOW_OUTFLOW;  // the adjoint's inflow plane, or the inflow velocity
+    const bool u_fixed = (bcx == BC_INFLOW_OUTFLOW) && inlet;
+    // outlet: the outflow condition of the convective adjoint, (u . n) u~ + nu du~/dn = 0, with a
+    // one-sided difference: u~(outlet) = nu / (nu + max(u_x, 0)) u~(inward neighbour)
+    const double fac = inlet ? 1.0 : C.P.nu / (C.P.nu + std::max(st.u[0][n], 0.0));
     o->p[n] = p_fixed ? 0.0 : o->p[m];
-    for (int a = 0; a < d; ++a) o->u[a][n] = u_fixed ? 0.0 : o->u[a][m];
+    for (int a = 0; a < d; ++a) o->u[a][n] = u_fixed ? 0.0 : fac * o->u[a][m];
     copy_s(n, m);
   }
 }
@@ -1376,7 +1380,7 @@ void alks_gather(const Ctx& C, const AdjMoments& a, const Fields<double>& st, Ad
       }
     }
   }
-  alks_boundaries(C, o);
+  alks_boundaries(C, st, o);
 }
 
 // (a x b) along the rotation axis ax.

@@ -22,8 +22,9 @@
 //   k_alks_gather   all nodes: the star moments at t - 1 (Eqs. ap_tmp, au_tmp, as_tmp),
 //                   p~* = sum_i w_i f~eq_i(x + c_i) and its first and second moments, with the boundary
 //                   values prescribed: a quantity the forward fixes has a zero multiplier, one it
-//                   copies from the inward neighbour copies the neighbour's, except u~ at the outlet
-//                   plane, the adjoint's inflow plane, which is zero; s~ is copied.
+//                   copies from the inward neighbour copies the neighbour's, except u~ on the
+//                   outlet plane, which follows the outflow condition of the convective adjoint,
+//                   (u . n) u~ + nu du~/dn = 0: u~ = nu / (nu + max(u_x, 0)) u~(inward); s~ is copied.
 // The terminal multipliers (x~G = -dJ/dxG, M u~G = -dJ/duG, theta~ = -dJ/dtheta, I omega~ = -dJ/domega)
 // belong to a step N_t + 1; the fluid multipliers start at zero.
 #include "lks_body_common.cuh"
@@ -497,10 +498,11 @@ __global__ void __launch_bounds__(256) k_alks_z(Geo g, const Ctrl* ctrl, Slots<T
 }
 
 template <typename T, int D>
-__global__ void __launch_bounds__(256) k_alks_gather(Geo g, const Ctrl* ctrl, T* Ab, long long astride,
-                                                     const T* __restrict__ zb, int di) {
+__global__ void __launch_bounds__(256) k_alks_gather(Geo g, const Ctrl* ctrl, Slots<T> S, T* Ab, long long astride,
+                                                     const T* __restrict__ zb, T nu, int di) {
   constexpr int NS = Lat<D>::NS;
   const int t = ctrl->t0 - di;
+  const T* __restrict__ st = slot_ptr(S, t, ctrl->base);
   const T* __restrict__ am = Ab + (long long)(t & 1) * astride;
   T* __restrict__ out = Ab + (long long)((t - 1) & 1) * astride;
   const long long N = g.N;
@@ -508,8 +510,9 @@ __global__ void __launch_bounds__(256) k_alks_gather(Geo g, const Ctrl* ctrl, T*
     int x[3];
     node_coords<D>(g, n, x);
     // boundary node: the value of its inward neighbour (through every boundary axis), with a zero
-    // multiplier for what the forward prescribes there and for u~ on the outlet plane
+    // multiplier for what the forward prescribes there and the outflow factor for u~ on the outlet
     bool zp = false, zu = false;
+    T fu = T(1);
     if (g.bc[0] != BC_PERIODIC) {
       if (x[0] == 0) {
         x[0] = 1;
@@ -519,7 +522,8 @@ __global__ void __launch_bounds__(256) k_alks_gather(Geo g, const Ctrl* ctrl, T*
           zp = true;
       } else if (x[0] == g.n[0] - 1) {
         x[0] = g.n[0] - 2;
-        zp = zu = true;
+        zp = true;
+        fu = nu / (nu + fmax(st[N + n], T(0)));  // u_x of the state on the outlet node
       }
     }
 #pragma unroll
@@ -551,7 +555,7 @@ __global__ void __launch_bounds__(256) k_alks_gather(Geo g, const Ctrl* ctrl, T*
     }
     out[n] = zp ? T(0) : P;
 #pragma unroll
-    for (int a = 0; a < D; ++a) out[(1 + a) * N + n] = zu ? T(0) : U[a];
+    for (int a = 0; a < D; ++a) out[(1 + a) * N + n] = zu ? T(0) : fu * U[a];
 #pragma unroll
     for (int k = 0; k < NS; ++k) out[(1 + D + k) * N + n] = Sv[k];
   }
@@ -626,12 +630,13 @@ void launch_alks_body(const Geo& g, const Slots<T>& S, Ctrl* ctrl, const Dof* it
 template <typename T>
 void launch_alks_stencil(const Geo& g, const Slots<T>& S, const Ctrl* ctrl, T* Ab, long long astride, T* zb, int di,
                          cudaStream_t st) {
+  const T nu = (T)(1.0 / 6.0 - 2.0 * g.A / 9.0);  // nu = 1/6 - 2A/9 (Sec. 2.2)
   if (g.dim == 2) {
     launch(k_alks_z<T, 2>, node_blocks(g), 256, 0, st, g, ctrl, S, (const T*)Ab, astride, zb, di);
-    launch(k_alks_gather<T, 2>, node_blocks(g), 256, 0, st, g, ctrl, Ab, astride, (const T*)zb, di);
+    launch(k_alks_gather<T, 2>, node_blocks(g), 256, 0, st, g, ctrl, S, Ab, astride, (const T*)zb, nu, di);
   } else {
     launch(k_alks_z<T, 3>, node_blocks(g), 256, 0, st, g, ctrl, S, (const T*)Ab, astride, zb, di);
-    launch(k_alks_gather<T, 3>, node_blocks(g), 256, 0, st, g, ctrl, Ab, astride, (const T*)zb, di);
+    launch(k_alks_gather<T, 3>, node_blocks(g), 256, 0, st, g, ctrl, S, Ab, astride, (const T*)zb, nu, di);
   }
 }
 

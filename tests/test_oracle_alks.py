@@ -81,29 +81,35 @@ def test_gather_differs_from_exact_transpose_in_a_flow():
 
 def test_gather_boundary_values():
     """Reading of the omitted boundary values: a prescribed quantity has a zero multiplier, a copied
-    one copies its neighbour's, except u~ on the outlet plane (the adjoint's inflow), which is zero;
-    s~ is always copied."""
+    one copies its neighbour's, except u~ on the outlet plane, where the outflow condition of the
+    convective adjoint (u . n) u~ + nu du~/dn = 0 scales it by nu / (nu + u_x); s~ is always
+    copied."""
     P = box(9, 7, bc=(BC_INFLOW_OUTFLOW, BC_WALL, BC_PERIODIC), nu=0.05)
     nx, ny, N = P.nx, P.ny, P.n_cells
     rng = np.random.default_rng(2)
+    vel = 0.03 * rng.standard_normal((2, N))
     op, ou, os_ = O.alks_gather(P, rng.standard_normal(N), rng.standard_normal((2, N)),
-                                rng.standard_normal((2, 2, N)), 0.03 * rng.standard_normal((2, N)))
+                                rng.standard_normal((2, 2, N)), vel)
     p, u, s = op.reshape(ny, nx), ou.reshape(2, ny, nx), os_.reshape(2, 2, ny, nx)
     assert np.all(u[:, 0, 1:-1] == 0) and np.all(u[:, -1, 1:-1] == 0)          # wall velocity
     np.testing.assert_array_equal(p[0, 1:-1], p[1, 1:-1])                      # wall pressure copied
     assert np.all(u[:, :, 0] == 0)                                             # inlet velocity
     np.testing.assert_array_equal(p[:, 0], p[:, 1])                            # inlet pressure copied
     assert np.all(p[:, -1] == 0)                                               # outlet pressure
-    assert np.all(u[:, :, -1] == 0)                                            # the adjoint's inflow plane
+    fac = 0.05 / (0.05 + np.maximum(vel[0].reshape(ny, nx)[:, -1], 0))
+    np.testing.assert_allclose(u[:, 1:-1, -1], fac[1:-1] * u[:, 1:-1, -2], rtol=1e-15, atol=0)  # outflow
+    assert np.all(u[:, [0, -1], -1] == 0)                                      # outlet corners on the walls
     np.testing.assert_array_equal(s[:, :, :, 0], s[:, :, :, 1])
     np.testing.assert_array_equal(s[:, :, :, -1], s[:, :, :, -2])
     Pp = box(9, 7, bc=(BC_PRESSURE, BC_PERIODIC, BC_PERIODIC), nu=0.05)
+    vel = 0.03 * rng.standard_normal((2, N))
     op, ou, _ = O.alks_gather(Pp, rng.standard_normal(N), rng.standard_normal((2, N)),
-                              rng.standard_normal((2, 2, N)), 0.03 * rng.standard_normal((2, N)))
+                              rng.standard_normal((2, 2, N)), vel)
     p, u = op.reshape(ny, nx), ou.reshape(2, ny, nx)
     assert np.all(p[:, 0] == 0) and np.all(p[:, -1] == 0)
     np.testing.assert_array_equal(u[:, :, 0], u[:, :, 1])
-    assert np.all(u[:, :, -1] == 0)
+    fac = 0.05 / (0.05 + np.maximum(vel[0].reshape(ny, nx)[:, -1], 0))
+    np.testing.assert_allclose(u[:, :, -1], fac * u[:, :, -2], rtol=1e-15, atol=0)
 
 
 def _case(name):
