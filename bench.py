@@ -413,7 +413,9 @@ def main():
     ap.add_argument("--skip-extras", action="store_true", help="only the timed region and e2e")
     ap.add_argument("--time-steps", type=int, default=0,
                     help="truncate N_t (profiling runs only: keeps the per-step kernel mix, shrinks the launch list)")
-    ap.add_argument("--case", choices=["fluid2d", "fluid3d", "alks"], default=None,
+    ap.add_argument("--config", type=int, default=0,
+                    help="profiling runs with --case gradient or alks: the workload index (default: the benchmark's)")
+    ap.add_argument("--case", choices=["fluid2d", "fluid3d", "alks", "gradient"], default=None,
                     help="profiling runs only: the stencil roofline of a fluid grid (--grid NXxNY[xNZ]) alone")
     ap.add_argument("--grid", default=None)
     ap.add_argument("--case-steps", type=int, default=4)
@@ -421,12 +423,12 @@ def main():
     ws, rank, local = _dist()
     if args.impl == "reference":
         return run_reference(args, ws, rank)
-    if args.case == "alks":  # profiling runs only: gradients of the benchmark workload with the paper's adjoint
+    if args.case in ("alks", "gradient"):  # profiling runs only: gradients (exact or the paper's adjoint)
         import torch
         from paper_2601_18272_gb300.lks import Solver
         from workloads import config
         torch.cuda.set_device(local)
-        P, g = config(CONFIG_INDEX)
+        P, g = config(args.config or CONFIG_INDEX)
         if args.time_steps:
             P = P.replace(n_steps=args.time_steps, ckpt_every=min(P.ckpt_every, max(1, args.time_steps // 2)))
         S = Solver(P)
@@ -434,11 +436,11 @@ def main():
         grad = torch.empty_like(gamma)
         for _ in range(args.warmup + args.steps):
             J = S.forward(gamma)
-            S.adjoint_alks(1.0)
+            (S.adjoint_alks if args.case == "alks" else S.adjoint)(1.0)
             S.sensitivity(grad)
         torch.cuda.synchronize()
         S.close()
-        print(json.dumps({"case": "alks", "workload": P.name, "n_steps": P.n_steps, "J": J}), flush=True)
+        print(json.dumps({"case": args.case, "workload": P.name, "n_steps": P.n_steps, "J": J}), flush=True)
         return 0
     if args.case:
         import torch

@@ -90,6 +90,35 @@ __device__ __forceinline__ double cross_ax(const double* a, const double* b) {
   return a[B] * b[C] - a[C] * b[B];
 }
 
+// Block sum of NV per-thread values into out[0..NV) (global, FP64), written by threads < NV. FP32:
+// a shuffle tree in FP32 within each warp, then the warps' totals summed in FP64 by NV threads (the
+// double-float tree of the exact reverse costs a dependent chain per value, too long for the 36 to
+// 56 values here); FP64: the fixed-order FP64 tree. smem: 32 * NV doubles.
+template <int NV>
+__device__ __forceinline__ void alks_block_sum(float (&v)[NV], double* out, double* smem) {
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31, nw = blockDim.x >> 5;
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1)
+#pragma unroll
+    for (int i = 0; i < NV; ++i) v[i] += __shfl_xor_sync(0xffffffffu, v[i], off);
+  if (lane == 0)
+#pragma unroll
+    for (int i = 0; i < NV; ++i) smem[warp * NV + i] = (double)v[i];
+  __syncthreads();
+  if (tid < NV) {
+    double acc = 0.0;
+    for (int w = 0; w < nw; ++w) acc += smem[w * NV + tid];
+    out[tid] = acc;
+  }
+}
+template <int NV>
+__device__ __forceinline__ void alks_block_sum(double (&v)[NV], double* out, double* smem) {
+  block_sum<NV>(v, smem);
+  if (threadIdx.x == 0)
+#pragma unroll
+    for (int i = 0; i < NV; ++i) out[i] = v[i];
+}
+
 // u~G, omega~ of iterations N_itr - 1 (k = 0) and N_itr (k = 1) in the field type.
 template <typename T>
 __device__ __forceinline__ T al_it(const Ctrl* ctrl, int i);
@@ -337,17 +366,32 @@ __global__ void __launch_bounds__(kDesignBlock) k_alks_design(Geo g, Slots<T> S,
     sm[2 + 2 * D] = cross_ax<AX>(l, Dm);
   }
   if (!inside && lane == 0 && valid) atomicOr(&ctrl->status, ST_BOX_OVERFLOW);
-  block_sum_partial<NV::N>(v, static_cast<typename Partial<T>::type*>(partials) + blockIdx.x * NV::N, red);
+  alks_block_sum<NV::N>(v, static_cast<double*>(partials) + blockIdx.x * NV::N, red);
 }
 
 // ---- Algorithm 1's adjoint fixed-point iterations on the reduced sums (one CTA) ----------------
 template <typename T, int D>
-__global__ void __launch_bounds__(kFinishThreads) k_alks_finish(Geo g, Ctrl* ctrl, const void* partials, int nparts) {
+__global__ void __launch_bounds__(kFinishThreads) k_alks_finish(Geo g, Ctrl* ctrl, const double* partials, int nparts) {
   using NV = NvA<D>;
-  __shared__ double red[32 * NV::N];
+  __shared__ double red[kFinishThreads];
   __shared__ double Sm[NV::N];
-  block_sum_partials<NV::N>(static_cast<const typename Partial<T>::type*>(partials), nparts, Sm, red);
-  if (threadIdx.x != 0) return;
+  // the partials [nparts][NV], column-parallel: thread (i, j) sums value i over rows j, j + G, ...
+  // (G groups of NV threads), then thread i sums its column's G results; fixed order, FP64
+  constexpr int G = kFinishThreads / NV::N;
+  const int tid = threadIdx.x, col = tid % NV::N, grp = tid / NV::N;
+  if (grp < G) {
+    double acc = 0.0;
+    for (int q = grp; q < nparts; q += G) acc += __ldcg(&partials[(long long)q * NV::N + col]);
+    red[grp * NV::N + col] = acc;
+  }
+  __syncthreads();
+  if (tid < NV::N) {
+    double acc = 0.0;
+    for (int j = 0; j < G; ++j) acc += red[j * NV::N + tid];
+    Sm[tid] = acc;
+  }
+  __syncthreads();
+  if (tid != 0) return;
   const int mask = g.dof_mask, K = g.K;
   double nxt[8], cur[8], k1[4];
   for (int i = 0; i < 8; ++i) nxt[i] = cur[i] = ctrl->al_b[i];
@@ -615,12 +659,12 @@ void launch_alks_body(const Geo& g, const Slots<T>& S, Ctrl* ctrl, const Dof* it
   const long long wb = (g.box_cells + 255) / 256;
   const unsigned sb = (unsigned)((g.ND + 255) / 256);
   if (g.dim == 2) {
-    launch(k_alks_finish<T, 2>, 1, kFinishThreads, 0, st, g, ctrl, (const void*)partials, (int)nb);
+    launch(k_alks_finish<T, 2>, 1, kFinishThreads, 0, st, g, ctrl, (const double*)partials, (int)nb);
     launch(k_alks_write<T, 2>, (unsigned)(wb < 4096 ? wb : 4096), 256, 0, st, g, (const Ctrl*)ctrl, it,
            (const T*)abox, Ab, astride, di);
     launch(k_alks_sens<T, 2>, sb, 256, 0, st, g, (const Ctrl*)ctrl, (const T*)sstore, dkref);
   } else {
-    launch(k_alks_finish<T, 3>, 1, kFinishThreads, 0, st, g, ctrl, (const void*)partials, (int)nb);
+    launch(k_alks_finish<T, 3>, 1, kFinishThreads, 0, st, g, ctrl, (const double*)partials, (int)nb);
     launch(k_alks_write<T, 3>, (unsigned)(wb < 4096 ? wb : 4096), 256, 0, st, g, (const Ctrl*)ctrl, it,
            (const T*)abox, Ab, astride, di);
     launch(k_alks_sens<T, 3>, sb, 256, 0, st, g, (const Ctrl*)ctrl, (const T*)sstore, dkref);

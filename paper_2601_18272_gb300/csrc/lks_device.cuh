@@ -293,11 +293,27 @@ __device__ __forceinline__ void gather_lanes(const Geo& g, const F* __restrict__
   if (!active) ib1 = ib0 - 1;
   int ia0 = 0, ia1 = 0;
   F xia = F(0);
+  // 3D: the axial factor of W, its offset and the axial domain term depend only on ia, at most 2s of
+  // them per cell: computed once here, not once per in-plane candidate
+  F wa[4] = {F(0), F(0), F(0), F(0)}, ra[4] = {F(0), F(0), F(0), F(0)};
+  int qa[4] = {0, 0, 0, 0};
+  bool va[4] = {false, false, false, false};
   if (D == 3) {
     xia = d[ax] + pivot<F>(g, ax);
     const int fa = (int)floor(xia);
     ia0 = max(0, fa - g.s + 1);
     ia1 = min(g.nd[ax] - 1, fa + g.s);
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const int ia = ia0 + q;
+      const F oa = (F)ia - xia;
+      va[q] = ia <= ia1 && fabs(oa) < S;
+      if (va[q]) {
+        wa[q] = wfun(g.wk, oa);
+        ra[q] = (F)ia - pivot<F>(g, ax);
+        qa[q] = dsq(ia, g.nd[ax]);
+      }
+    }
   }
   o.phi = o.kap = F(0);
 #pragma unroll
@@ -349,21 +365,26 @@ __device__ __forceinline__ void gather_lanes(const Geo& g, const F* __restrict__
         o.kr[b] += wkap * rb;
         o.kr[c] += wkap * rc;
       } else {
-        for (int ia = ia0; ia <= ia1; ++ia) {
-          const F oa = (F)ia - xia;
-          if (fabs(oa) >= S || qbc + dsq(ia, g.nd[ax]) > g.rad4) continue;
-          const F W = w2 * wfun(g.wk, oa);
-          const F wkap = W * kref[m2 + ia * sa];
-          const F ra = (F)ia - pivot<F>(g, ax);
-          o.phi += W;
-          o.kap += wkap;
-          o.wr[b] += W * rb;
-          o.wr[c] += W * rc;
-          o.wr[ax] += W * ra;
-          o.kr[b] += wkap * rb;
-          o.kr[c] += wkap * rc;
-          o.kr[ax] += wkap * ra;
+        // sums over this candidate's axial column, then the in-plane weight once
+        F s1 = F(0), s0 = F(0), s2 = F(0), s3 = F(0);
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+          if (!va[q] || qbc + qa[q] > g.rad4) continue;
+          const F wk = wa[q] * kref[m2 + (ia0 + q) * sa];
+          s1 += wa[q];
+          s0 += wk;
+          s2 += wa[q] * ra[q];
+          s3 += wk * ra[q];
         }
+        const F w1 = w2 * s1, wk0 = w2 * s0;
+        o.phi += w1;
+        o.kap += wk0;
+        o.wr[b] += w1 * rb;
+        o.wr[c] += w1 * rc;
+        o.wr[ax] += w2 * s2;
+        o.kr[b] += wk0 * rb;
+        o.kr[c] += wk0 * rc;
+        o.kr[ax] += w2 * s3;
       }
     }
   }
