@@ -391,7 +391,7 @@ void enqueue_fwd_steps(lks_handle* h, Launcher& L, const Slots<T>& S, int nsteps
   for (int i = 0; i < nsteps; ++i) {
     L("stencil_fwd", [&](cudaStream_t s) { launch_stencil_fwd<T>(g, S, h->ctrl, i, s); });
     for (int k = 1; k <= g.K; ++k)
-      L("couple", [&](cudaStream_t s) {
+      L.n("couple", couple_kernels(g), [&](cudaStream_t s) {
         launch_couple<T>(g, S, h->ctrl, h->it, (const T*)h->kref, h->mom, h->partials, h->pstride, k, bs, h->nbox, i,
                          s);
       });

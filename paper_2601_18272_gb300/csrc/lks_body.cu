@@ -530,7 +530,7 @@ template <typename T, int D, int AX>
 __global__ void __launch_bounds__(kCellThreads, 2) k_couple(Geo g, Slots<T> S, Ctrl* ctrl, Dof* it,
                                                           const T* __restrict__ kref, const Moments* __restrict__ mom,
                                                           void* partials, long long pstride, int nparts, int k,
-                                                          T* __restrict__ boxstore, int nbox, int di) {
+                                                          T* __restrict__ boxstore, int nbox, int pre, int di) {
   using PT = typename Partial<T>::type;
   constexpr int NV = nv_couple<AX>();
   constexpr int DW = (int)(sizeof(Dof) / sizeof(double));  // the iterate in 8-byte words
@@ -544,7 +544,15 @@ __global__ void __launch_bounds__(kCellThreads, 2) k_couple(Geo g, Slots<T> S, C
   PT* pout = static_cast<PT*>(partials) + (idx & 1) * pstride;
   double* sdw = reinterpret_cast<double*>(sd);
   const int tid = threadIdx.x;
-  if (idx > 0) {
+  if (idx > 0 && pre) {
+    // k_couple_pre has finished the previous iteration into the iterate rows
+    const double* g0 = reinterpret_cast<const double*>(row);
+    const double* gk = reinterpret_cast<const double*>(row + (k - 1));
+    if (tid < DW) {
+      sdw[tid] = g0[tid];
+      sdw[DW + tid] = gk[tid];
+    }
+  } else if (idx > 0) {
     // previous iteration kp of step tp: its EOM starts from prow[0] with the transform of
     // prow[kp - 1]; both are staged in shared memory by the block (thread 0 then reads only the
     // fields it needs, keeping its FP64 chain in registers)
@@ -590,6 +598,43 @@ __global__ void __launch_bounds__(kCellThreads, 2) k_couple(Geo g, Slots<T> S, C
   for (int a = 0; a < NV; ++a) v[a] = T(0);
   couple_cell<T, D, AX>(g, kref, sk, lo, cc, dst, bs, k == K, &ctrl->status, v);
   block_sum_partial<NV>(v, pout + block_linear() * NV, red);
+}
+
+// The previous iteration's finish (sum of its partials and the EOM) for coupling iteration k of
+// step t, once, for grids whose CTA count makes the fused per-CTA form of k_couple (every CTA sums
+// all partials: loads quadratic in the CTA count) the larger cost. Same thread count and summation
+// order as the fused form, so the iterates are the same to the bit.
+template <typename T, int D, int AX>
+__global__ void __launch_bounds__(kCellThreads) k_couple_pre(Geo g, Ctrl* ctrl, Dof* it, const Moments* __restrict__ mom,
+                                                             const void* __restrict__ partials, long long pstride,
+                                                             int nparts, int k, int di) {
+  using PT = typename Partial<T>::type;
+  constexpr int NV = nv_couple<AX>();
+  __shared__ double red[32 * NV];
+  const int t = ctrl->t0 + di, K = g.K;
+  Dof* row = it + (long long)(t - 1) * (K + 1);
+  const long long idx = (long long)(t - 1) * K + (k - 1);
+  if (idx == 0) return;
+  Dof* prow = (k > 1) ? row : row - (K + 1);
+  const int kp = (k > 1) ? k - 1 : K;
+  const PT* pin = static_cast<const PT*>(partials) + ((idx - 1) & 1) * pstride;
+  Dof s0, sk;
+  Moments m;
+  if (threadIdx.x == 0) {
+    s0 = prow[0];
+    sk = prow[kp - 1];
+    m = *mom;
+  }
+  double sm[NV];
+  block_sum_partials<NV>(pin, nparts, sm, red);
+  if (threadIdx.x == 0) {
+    Dof nx;
+    int st = 0;
+    couple_finish_any<D, AX>(g, &m, s0, sk, sm, &nx, &st);
+    if (st) ctrl->status |= st;
+    prow[kp] = nx;
+    if (kp == K) row[0] = nx;
+  }
 }
 
 // EOM of the last coupling iteration of the run (step t_last, iteration N_itr).
@@ -822,8 +867,16 @@ void launch_couple(const Geo& g, const Slots<T>& S, Ctrl* ctrl, Dof* it, const T
                    void* partials, long long pstride, int k, T* boxstore, int nbox, int di, cudaStream_t st) {
   const dim3 grid = box_grid(g);
   const int nparts = (int)(grid.x * grid.y * grid.z);
+  const int pre = nparts > kFusedFinishMaxParts ? 1 : 0;
+  if (pre)
+    LKS_BOX_DISPATCH(k_couple_pre, 1, kCellThreads, g, ctrl, it, mom, (const void*)partials, pstride, nparts, k, di);
   LKS_BOX_DISPATCH(k_couple, grid, kCellThreads, g, S, ctrl, it, kref, mom, partials, pstride, nparts, k, boxstore,
-                   nbox, di);
+                   nbox, pre, di);
+}
+
+int couple_kernels(const Geo& g) {
+  const dim3 grid = box_grid(g);
+  return (int)(grid.x * grid.y * grid.z) > kFusedFinishMaxParts ? 2 : 1;
 }
 
 template <typename T>

@@ -18,6 +18,10 @@ constexpr int CX = kBoxCtaCellsX, CY = kBoxCtaCellsY;
 constexpr int kCellThreads = CX * CY * LN;
 constexpr int kDesignBlock = kDesignPointsPerCta * LN;
 constexpr int kFinishThreads = 256;
+// Coupling: up to this many CTAs every CTA finishes the previous iteration itself (fused; saves a
+// launch); above it a one-CTA kernel does it once (the fused form loads every CTA's partials in
+// every CTA).
+constexpr int kFusedFinishMaxParts = 640;
 
 struct CellSlot {
   int j0, j1, j2, lane;

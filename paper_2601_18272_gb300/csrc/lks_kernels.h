@@ -63,6 +63,8 @@ void launch_prep(const Geo& g, const double* gamma, double kappa_max, double q, 
 // of the double-buffered partials, pstride elements apart), then spread, Brinkman, force/torque
 // partials (float2 double-float pairs for FP32 fields, doubles for FP64). On k == K writes u(t) into
 // slot(t) and optionally u* into the box store.
+// Kernels one launch_couple issues: 2 when the previous iteration's finish runs as its own CTA.
+int couple_kernels(const Geo& g);
 template <typename T>
 void launch_couple(const Geo& g, const Slots<T>& S, Ctrl* ctrl, Dof* it, const T* kref, const Moments* mom,
                    void* partials, long long pstride, int k, T* boxstore, int nbox, int di, cudaStream_t st);
