@@ -186,7 +186,14 @@ __global__ void __launch_bounds__(kDesignBlock) k_alks_design(Geo g, Slots<T> S,
   const T* __restrict__ am = Ab + (long long)(t & 1) * astride;
   int lo[3];
   box_origin<D>(g, s0, lo[0], lo[1], lo[2]);
-  const int m = blockIdx.x * kDesignPointsPerCta + threadIdx.x / LN, lane = threadIdx.x % LN;
+  const int lane = threadIdx.x % LN;
+  T v[NV::N];
+#pragma unroll
+  for (int i = 0; i < NV::N; ++i) v[i] = T(0);
+  bool inside = true;
+  // chunks of kDesignPointsPerCta points, grid-strided (design_ctas caps the grid)
+  for (int m0 = blockIdx.x * kDesignPointsPerCta; m0 < g.ND; m0 += gridDim.x * kDesignPointsPerCta) {
+  const int m = m0 + threadIdx.x / LN;
   const bool valid_m = m < g.ND;
   const int mm = valid_m ? m : 0;
   const int ix = mm % g.nd[0], iy = (mm / g.nd[0]) % g.nd[1], iz = mm / (g.nd[0] * g.nd[1]);
@@ -237,11 +244,7 @@ __global__ void __launch_bounds__(kDesignBlock) k_alks_design(Geo g, Slots<T> S,
       dwe = dwfun(g.wk, rr);
     }
   }
-  T v[NV::N];
-#pragma unroll
-  for (int i = 0; i < NV::N; ++i) v[i] = T(0);
   T uref[3] = {T(0), T(0), T(0)}, sG[3] = {T(0), T(0), T(0)}, sa = T(0), sW = T(0);
-  bool inside = true;
   const long long N = g.N, BC = g.box_cells;
   const int B0 = g.B[0], B1 = g.B[1], B2 = (D == 3) ? g.B[2] : 1;
 #pragma unroll
@@ -365,7 +368,8 @@ __global__ void __launch_bounds__(kDesignBlock) k_alks_design(Geo g, Slots<T> S,
     sm[1 + D] = sW;
     sm[2 + 2 * D] = cross_ax<AX>(l, Dm);
   }
-  if (!inside && lane == 0 && valid) atomicOr(&ctrl->status, ST_BOX_OVERFLOW);
+  }
+  if (!inside && lane == 0) atomicOr(&ctrl->status, ST_BOX_OVERFLOW);
   alks_block_sum<NV::N>(v, static_cast<double*>(partials) + blockIdx.x * NV::N, red);
 }
 
@@ -653,7 +657,7 @@ template <typename T>
 void launch_alks_body(const Geo& g, const Slots<T>& S, Ctrl* ctrl, const Dof* it, const T* kref, T* abox, T* Ab,
                       long long astride, T* sstore, void* partials, double* dkref, int di, cudaStream_t st) {
   ALKS_DISPATCH(k_alks_spread, box_grid(g), kCellThreads, g, ctrl, it, kref, abox, di);
-  const unsigned nb = (unsigned)((g.ND + kDesignPointsPerCta - 1) / kDesignPointsPerCta);
+  const unsigned nb = (unsigned)design_ctas(g);
   ALKS_DISPATCH(k_alks_design, nb, kDesignBlock, g, S, ctrl, it, kref, (const T*)abox, (const T*)Ab, astride, sstore,
                 partials, di);
   const long long wb = (g.box_cells + 255) / 256;

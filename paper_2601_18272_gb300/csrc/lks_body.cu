@@ -737,12 +737,17 @@ __global__ void __launch_bounds__(kDesignBlock) k_adj_design(Geo g, Ctrl* ctrl, 
   lam_load<T>(ctrl, lF, lT);
   int lo[3];
   box_origin<D>(g, s0, lo[0], lo[1], lo[2]);
-  const int m = blockIdx.x * kDesignPointsPerCta + threadIdx.x / LN, lane = threadIdx.x % LN;
+  const int lane = threadIdx.x % LN;
   T v[NV];
 #pragma unroll
   for (int a = 0; a < NV; ++a) v[a] = T(0);
-  if (!adj_design_point<T, D, AX>(g, kref, scratch, sk, lo, m, m < g.ND, lane, lF, lT, dkref, v))
-    atomicOr(&ctrl->status, ST_BOX_OVERFLOW);
+  bool inside = true;
+  // chunks of kDesignPointsPerCta points, grid-strided (the grid is capped: see design_ctas)
+  for (int m0 = blockIdx.x * kDesignPointsPerCta; m0 < g.ND; m0 += gridDim.x * kDesignPointsPerCta) {
+    const int m = m0 + threadIdx.x / LN;
+    inside = adj_design_point<T, D, AX>(g, kref, scratch, sk, lo, m, m < g.ND, lane, lF, lT, dkref, v) && inside;
+  }
+  if (!inside) atomicOr(&ctrl->status, ST_BOX_OVERFLOW);
   block_sum_partial<NV>(v, static_cast<typename Partial<T>::type*>(partials) + blockIdx.x * NV, red);
 }
 
@@ -903,7 +908,7 @@ void launch_adj_cell(const Geo& g, const Ctrl* ctrl, const Dof* it, const T* kre
 template <typename T>
 void launch_adj_design(const Geo& g, Ctrl* ctrl, const Dof* it, const T* kref, const T* scratch, double* dkref,
                        void* partials, int k, int di, cudaStream_t st) {
-  const unsigned nb = (unsigned)((g.ND + kDesignPointsPerCta - 1) / kDesignPointsPerCta);
+  const unsigned nb = (unsigned)design_ctas(g);
   LKS_BOX_DISPATCH(k_adj_design, nb, kDesignBlock, g, ctrl, it, kref, scratch, dkref, partials, k, di);
   if (g.ax == AX_FREE)
     launch(k_design_finish<T, true>, 1, kFinishThreads, 0, st, g, ctrl, it, (const void*)partials, (int)nb, k, di);

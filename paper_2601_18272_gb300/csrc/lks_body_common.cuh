@@ -88,6 +88,14 @@ __device__ __forceinline__ void gather_cell(const Geo& g, const T* __restrict__ 
   }
 }
 
+// Design-point kernels: one CTA per kDesignPointsPerCta points up to kMaxDesignCtas CTAs (two waves
+// at their occupancy), grid-strided beyond, so the one-CTA finish sums at most that many partials.
+constexpr int kMaxDesignCtas = 912;
+inline int design_ctas(const Geo& g) {
+  const int n = (g.ND + kDesignPointsPerCta - 1) / kDesignPointsPerCta;
+  return n < kMaxDesignCtas ? n : kMaxDesignCtas;
+}
+
 inline dim3 box_grid(const Geo& g) {
   return dim3((g.B[0] + CX - 1) / CX, (g.B[1] + CY - 1) / CY, g.dim == 3 ? g.B[2] : 1);
 }
