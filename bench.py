@@ -121,6 +121,11 @@ def _alg_bytes(family: str, P, box_cells: int, esz: int) -> float:
         return 11 * esz * box_cells   # read stored u*, acc r/w, scratch write (5 planes)
     if family == "adj_design":
         return 5 * esz * box_cells + 20 * ND  # read scratch once, dJ/dkappa^ref r/w + kappa^ref
+    if family == "alks_stencil":
+        # the paper's adjoint equilibrium and gather: read p~, u~, s~ (1 + d + d(d+1)/2 planes) and u
+        # (d), write Z (d); then read p~, Z (1 + d), write the star moments (1 + d + d(d+1)/2)
+        ns = 1 + d + d * (d + 1) // 2
+        return ((ns + 2 * d) + (1 + d + ns)) * esz * N
     return 0.0
 
 
@@ -187,12 +192,19 @@ def stencil_roofline(dev, peak: float, dim: int, n: tuple, name: str, n_steps: i
         S.adjoint(1.0)
         S.sensitivity(grad)
 
+    def run_paper():
+        S.forward(gamma)
+        S.adjoint_alks(1.0)
+        S.sensitivity(grad)
+
     run()
+    run_paper()
     torch.cuda.synchronize()
     fams = _family_times(S, run)
+    fams.update({k: v for k, v in _family_times(S, run_paper).items() if k == "alks_stencil"})
     S.close()
     out = {"workload": name, "grid": list(n), "cells": P.n_cells, "dtype": "f32"}
-    for fam in ("stencil_fwd", "stencil_adj"):
+    for fam in ("stencil_fwd", "stencil_adj", "alks_stencil"):
         ms, cnt = fams[fam]
         per = ms / 1000.0 / cnt
         alg = _alg_bytes(fam, P, 0, 4)
