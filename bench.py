@@ -122,9 +122,12 @@ def _alg_bytes(family: str, P, box_cells: int, esz: int) -> float:
     if family == "adj_design":
         return 5 * esz * box_cells + 20 * ND  # read scratch once, dJ/dkappa^ref r/w + kappa^ref
     if family == "alks_stencil":
-        # the paper's adjoint equilibrium and gather: read p~, u~, s~ (1 + d + d(d+1)/2 planes) and u
-        # (d), write Z (d); then read p~, Z (1 + d), write the star moments (1 + d + d(d+1)/2)
+        # the paper's adjoint equilibrium and gather. 2D, one tiled pass: read p~, u~, s~
+        # (1 + d + d(d+1)/2 planes) and u (d), write the star moments. 3D, two passes: read the
+        # moments and u, write Z (d); read p~, Z (1 + d), write the star moments
         ns = 1 + d + d * (d + 1) // 2
+        if d == 2:
+            return (ns + d + ns) * esz * N
         return ((ns + 2 * d) + (1 + d + ns)) * esz * N
     return 0.0
 

@@ -418,7 +418,7 @@ void enqueue_adj_steps(lks_handle* h, Launcher& L, const Slots<T>& S, int nsteps
         launch_alks_body<T>(g, S, h->ctrl, h->it, (const T*)h->kref, (T*)h->al_box, (T*)h->al_A, h->al_astride,
                             (T*)h->al_sens, h->al_part, h->dkref, i, s);
       });
-      L.n("alks_stencil", 2, [&](cudaStream_t s) {
+      L.n("alks_stencil", alks_stencil_kernels(g.dim), [&](cudaStream_t s) {
         launch_alks_stencil<T>(g, S, h->ctrl, (T*)h->al_A, h->al_astride, (T*)h->al_z, i, s);
       });
     }

@@ -146,6 +146,7 @@ void launch_ckpt_pack(const Geo& g, const Slots<T>& S, T* ckpt, long long cstrid
 int alks_partial_values(int dim);
 int alks_sens_values(int dim);
 int alks_planes(int dim);
+int alks_stencil_kernels(int dim);  // kernels one launch_alks_stencil issues
 void launch_alks_init(const Geo& g, Ctrl* ctrl, const double* objw, double seed, double* dkref, cudaStream_t st);
 // Step t = ctrl->t0 - di: spread, coupling sums, fixed-point iterations, u~(t) in the box, the
 // step's design sensitivity (5 kernels).
