@@ -831,7 +831,7 @@ StripPlan plan_strips(const Geo& g) {
   sp.ntx = (g.n[0] + sp.W - 1) / sp.W;
   const int want = 8 * 152 * 4;  // warps
   int ns = (want + sp.ntx - 1) / sp.ntx;
-  const int maxs = g.n[1] / 4;  // at least four rows per strip
+  const int maxs = g.n[1] / 2;  // at least two rows per strip (a wall row is built from the next)
   if (ns > maxs) ns = maxs;
   sp.nstrip = ns < 1 ? 1 : ns;
   return sp;
