@@ -129,7 +129,7 @@ __device__ __forceinline__ double al_it<double>(const Ctrl* ctrl, int i) { retur
 
 // ---- spread at s(t) -------------------------------------------------------------------------
 template <typename T, int D, int AX>
-__global__ void __launch_bounds__(kCellThreads, 2) k_alks_spread(Geo g, const Ctrl* ctrl, const Dof* it,
+__global__ void __launch_bounds__(BoxCta<D>::threads, BoxCta<D>::min_blocks) k_alks_spread(Geo g, const Ctrl* ctrl, const Dof* it,
                                                                  const T* __restrict__ kref, T* __restrict__ abox,
                                                                  int di) {
   const int t = ctrl->t0 - di, K = g.K;
@@ -137,7 +137,7 @@ __global__ void __launch_bounds__(kCellThreads, 2) k_alks_spread(Geo g, const Ct
   const Dof s0 = row[0], sk = row[K];
   int lo[3];
   box_origin<D>(g, s0, lo[0], lo[1], lo[2]);
-  const CellSlot cc = cell_slot(g);
+  const CellSlot cc = cell_slot<D>(g);
   const int px = lo[0] + cc.j0, py = lo[1] + cc.j1, pz = lo[2] + cc.j2;
   long long n = 0;
   const bool ing = cell_index<D>(g, px, py, pz, n);
@@ -756,7 +756,7 @@ void launch_alks_init(const Geo& g, Ctrl* ctrl, const double* objw, double seed,
 template <typename T>
 void launch_alks_body(const Geo& g, const Slots<T>& S, Ctrl* ctrl, const Dof* it, const T* kref, T* abox, T* Ab,
                       long long astride, T* sstore, void* partials, double* dkref, int di, cudaStream_t st) {
-  ALKS_DISPATCH(k_alks_spread, box_grid(g), kCellThreads, g, ctrl, it, kref, abox, di);
+  ALKS_DISPATCH(k_alks_spread, box_grid(g), box_threads(g), g, ctrl, it, kref, abox, di);
   const unsigned nb = (unsigned)design_ctas(g);
   ALKS_DISPATCH(k_alks_design, nb, kDesignBlock, g, S, ctrl, it, kref, (const T*)abox, (const T*)Ab, astride, sstore,
                 partials, di);

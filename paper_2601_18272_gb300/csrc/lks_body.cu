@@ -527,7 +527,7 @@ __global__ void __launch_bounds__(256) k_prep(Geo g, const double* __restrict__ 
 // the iterate. This removes a launch and a dependent round trip per iteration; the EOM of the run's
 // last iteration is k_couple_last.
 template <typename T, int D, int AX>
-__global__ void __launch_bounds__(kCellThreads, 2) k_couple(Geo g, Slots<T> S, Ctrl* ctrl, Dof* it,
+__global__ void __launch_bounds__(BoxCta<D>::threads, BoxCta<D>::min_blocks) k_couple(Geo g, Slots<T> S, Ctrl* ctrl, Dof* it,
                                                           const T* __restrict__ kref, const Moments* __restrict__ mom,
                                                           void* partials, long long pstride, int nparts, int k,
                                                           T* __restrict__ boxstore, int nbox, int pre, int di) {
@@ -592,7 +592,7 @@ __global__ void __launch_bounds__(kCellThreads, 2) k_couple(Geo g, Slots<T> S, C
   int lo[3];
   box_origin<D>(g, s0, lo[0], lo[1], lo[2]);
   T* bs = (boxstore && k == K) ? boxstore + (long long)((t - base - 1) % nbox) * g.box_cells * D : nullptr;
-  const CellSlot cc = cell_slot(g);
+  const CellSlot cc = cell_slot<D>(g);
   T v[NV];
 #pragma unroll
   for (int a = 0; a < NV; ++a) v[a] = T(0);
@@ -605,7 +605,7 @@ __global__ void __launch_bounds__(kCellThreads, 2) k_couple(Geo g, Slots<T> S, C
 // all partials: loads quadratic in the CTA count) the larger cost. Same thread count and summation
 // order as the fused form, so the iterates are the same to the bit.
 template <typename T, int D, int AX>
-__global__ void __launch_bounds__(kCellThreads) k_couple_pre(Geo g, Ctrl* ctrl, Dof* it, const Moments* __restrict__ mom,
+__global__ void __launch_bounds__(BoxCta<D>::threads) k_couple_pre(Geo g, Ctrl* ctrl, Dof* it, const Moments* __restrict__ mom,
                                                              const void* __restrict__ partials, long long pstride,
                                                              int nparts, int k, int di) {
   using PT = typename Partial<T>::type;
@@ -671,7 +671,7 @@ __global__ void __launch_bounds__(kFinishThreads, 1) k_couple_last(Geo g, Ctrl* 
 
 // Recompute of one step's Brinkman update from the stored iterate s^(K-1).
 template <typename T, int D, int AX>
-__global__ void __launch_bounds__(kCellThreads, 2) k_apply(Geo g, Slots<T> S, const Ctrl* ctrl, const Dof* it,
+__global__ void __launch_bounds__(BoxCta<D>::threads, BoxCta<D>::min_blocks) k_apply(Geo g, Slots<T> S, const Ctrl* ctrl, const Dof* it,
                                                    const T* __restrict__ kref, T* __restrict__ boxstore, int nbox,
                                                    int di) {
   const int t = ctrl->t0 + di, base = ctrl->base, K = g.K;
@@ -681,7 +681,7 @@ __global__ void __launch_bounds__(kCellThreads, 2) k_apply(Geo g, Slots<T> S, co
   const long long N = g.N;
   int lo[3];
   box_origin<D>(g, s0, lo[0], lo[1], lo[2]);
-  const CellSlot cc = cell_slot(g);
+  const CellSlot cc = cell_slot<D>(g);
   const int j0 = cc.j0, j1 = cc.j1, j2 = cc.j2;
   const int px = lo[0] + j0, py = lo[1] + j1, pz = lo[2] + j2;
   long long n = 0;
@@ -705,7 +705,7 @@ __global__ void __launch_bounds__(kCellThreads, 2) k_apply(Geo g, Slots<T> S, co
 }
 
 template <typename T, int D, int AX>
-__global__ void __launch_bounds__(kCellThreads, 2) k_adj_cell(Geo g, const Ctrl* ctrl, const Dof* it, const T* __restrict__ kref,
+__global__ void __launch_bounds__(BoxCta<D>::threads, BoxCta<D>::min_blocks) k_adj_cell(Geo g, const Ctrl* ctrl, const Dof* it, const T* __restrict__ kref,
                                                       const T* __restrict__ boxstore, int nbox, T* Lb,
                                                       long long lstride, T* __restrict__ acc, T* __restrict__ scratch,
                                                       int k, int di) {
@@ -717,7 +717,7 @@ __global__ void __launch_bounds__(kCellThreads, 2) k_adj_cell(Geo g, const Ctrl*
   T* Lcur = Lb + (long long)(t & 1) * lstride;
   int lo[3];
   box_origin<D>(g, s0, lo[0], lo[1], lo[2]);
-  const CellSlot cc = cell_slot(g);
+  const CellSlot cc = cell_slot<D>(g);
   const T* bs = boxstore + (long long)((t - base - 1) % nbox) * g.box_cells * D;
   adj_cell_work<T, D, AX>(g, kref, sk, lo, cc, bs, Lcur, acc, scratch, k, K, lF, lT);
 }
@@ -874,8 +874,8 @@ void launch_couple(const Geo& g, const Slots<T>& S, Ctrl* ctrl, Dof* it, const T
   const int nparts = (int)(grid.x * grid.y * grid.z);
   const int pre = nparts > kFusedFinishMaxParts ? 1 : 0;
   if (pre)
-    LKS_BOX_DISPATCH(k_couple_pre, 1, kCellThreads, g, ctrl, it, mom, (const void*)partials, pstride, nparts, k, di);
-  LKS_BOX_DISPATCH(k_couple, grid, kCellThreads, g, S, ctrl, it, kref, mom, partials, pstride, nparts, k, boxstore,
+    LKS_BOX_DISPATCH(k_couple_pre, 1, box_threads(g), g, ctrl, it, mom, (const void*)partials, pstride, nparts, k, di);
+  LKS_BOX_DISPATCH(k_couple, grid, box_threads(g), g, S, ctrl, it, kref, mom, partials, pstride, nparts, k, boxstore,
                    nbox, pre, di);
 }
 
@@ -895,13 +895,13 @@ void launch_couple_last(const Geo& g, Ctrl* ctrl, Dof* it, const Moments* mom, c
 template <typename T>
 void launch_apply(const Geo& g, const Slots<T>& S, const Ctrl* ctrl, const Dof* it, const T* kref, T* boxstore,
                   int nbox, int di, cudaStream_t st) {
-  LKS_BOX_DISPATCH(k_apply, box_grid(g), kCellThreads, g, S, ctrl, it, kref, boxstore, nbox, di);
+  LKS_BOX_DISPATCH(k_apply, box_grid(g), box_threads(g), g, S, ctrl, it, kref, boxstore, nbox, di);
 }
 
 template <typename T>
 void launch_adj_cell(const Geo& g, const Ctrl* ctrl, const Dof* it, const T* kref, const T* boxstore, int nbox, T* Lb,
                      long long lstride, T* acc, T* scratch, int k, int di, cudaStream_t st) {
-  LKS_BOX_DISPATCH(k_adj_cell, box_grid(g), kCellThreads, g, ctrl, it, kref, boxstore, nbox, Lb, lstride, acc,
+  LKS_BOX_DISPATCH(k_adj_cell, box_grid(g), box_threads(g), g, ctrl, it, kref, boxstore, nbox, Lb, lstride, acc,
                    scratch, k, di);
 }
 

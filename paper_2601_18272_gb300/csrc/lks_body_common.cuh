@@ -14,8 +14,15 @@ namespace {
 // of its support window), kDesignPointsPerCta points per CTA. The split multiplies the resident
 // warps of these latency-bound kernels by LN.
 constexpr int LN = kLanesPerCell;
-constexpr int CX = kBoxCtaCellsX, CY = kBoxCtaCellsY;
-constexpr int kCellThreads = CX * CY * LN;
+// Box-cell CTA shape: 16 x 16 cells in 2D (fewer CTAs: each runs the fused finish, its FP64 chain
+// and block reductions once; measured 763 against 772 ms on the 512x256 gradient), 16 x 8 in 3D
+// (where the larger CTAs measured 7 % slower).
+template <int D>
+struct BoxCta {
+  static constexpr int X = kBoxCtaCellsX, Y = (D == 2) ? kBoxCtaCellsY2D : kBoxCtaCellsY;
+  static constexpr int threads = X * Y * LN;
+  static constexpr int min_blocks = threads >= 1024 ? 1 : 2;  // resident CTAs the register budget allows
+};
 constexpr int kDesignBlock = kDesignPointsPerCta * LN;
 constexpr int kFinishThreads = 256;
 // Coupling: up to this many CTAs every CTA finishes the previous iteration itself (fused; saves a
@@ -27,7 +34,9 @@ struct CellSlot {
   int j0, j1, j2, lane;
   bool active;  // inside the box
 };
+template <int D>
 __device__ __forceinline__ CellSlot cell_slot(const Geo& g) {
+  constexpr int CX = BoxCta<D>::X, CY = BoxCta<D>::Y;
   CellSlot c;
   const int q = threadIdx.x / LN;
   c.lane = threadIdx.x % LN;
@@ -96,8 +105,10 @@ inline int design_ctas(const Geo& g) {
   return n < kMaxDesignCtas ? n : kMaxDesignCtas;
 }
 
+inline int box_threads(const Geo& g) { return kBoxCtaCellsX * (g.dim == 2 ? kBoxCtaCellsY2D : kBoxCtaCellsY) * LN; }
 inline dim3 box_grid(const Geo& g) {
-  return dim3((g.B[0] + CX - 1) / CX, (g.B[1] + CY - 1) / CY, g.dim == 3 ? g.B[2] : 1);
+  const int cx = kBoxCtaCellsX, cy = g.dim == 2 ? kBoxCtaCellsY2D : kBoxCtaCellsY;
+  return dim3((g.B[0] + cx - 1) / cx, (g.B[1] + cy - 1) / cy, g.dim == 3 ? g.B[2] : 1);
 }
 
 }  // namespace

@@ -28,7 +28,8 @@ struct StripPlan {
   int W, ntx, nstrip;
 };
 constexpr int kLanesPerCell = 4;                      // threads per box cell / design point in the body kernels
-constexpr int kBoxCtaCellsX = 16, kBoxCtaCellsY = 8;  // box cells per body-kernel CTA
+constexpr int kBoxCtaCellsX = 16, kBoxCtaCellsY = 8;  // box cells per body-kernel CTA in 3D (and for sizing)
+constexpr int kBoxCtaCellsY2D = 16;                   // in 2D: 1024-thread CTAs, one per SM
 constexpr int kDesignPointsPerCta = 64;               // design points per reverse design-side CTA
 
 // Kernels that work on one time step take di: the step is ctrl->t0 + di (forward kernels) or
