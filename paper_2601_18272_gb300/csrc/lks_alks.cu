@@ -17,14 +17,15 @@
 //                   previous iterate), in FP64
 //   k_alks_write    box cells: u~(t) of Eq. au with u~G, omega~ of iteration N_itr - 1
 //   k_alks_sens     design points: the step's term of Eq. design_sensitivity into dJ/dkappa^ref
-//   k_alks_z        all nodes: Z = u~ + 3 s~ u - p~ u - (A/3) sum_b d_b (s~ + s~^T), so that the
+//   k_alks_z        3D, all nodes: Z = u~ + 3 s~ u - p~ u - (A/3) sum_b d_b (s~ + s~^T), so that the
 //                   adjoint equilibrium is f~eq_i = p~ + 3 c_i . Z
-//   k_alks_gather   all nodes: the star moments at t - 1 (Eqs. ap_tmp, au_tmp, as_tmp),
+//   k_alks_gather   3D, all nodes: the star moments at t - 1 (Eqs. ap_tmp, au_tmp, as_tmp),
 //                   p~* = sum_i w_i f~eq_i(x + c_i) and its first and second moments, with the boundary
 //                   values prescribed: a quantity the forward fixes has a zero multiplier, one it
 //                   copies from the inward neighbour copies the neighbour's, except u~ on the
 //                   outlet plane, which follows the outflow condition of the convective adjoint,
 //                   (u . n) u~ + nu du~/dn = 0: u~ = nu / (nu + max(u_x, 0)) u~(inward); s~ is copied.
+//   k_alks_tile2d   2D: the two passes above in one tiled kernel (Z kept in shared memory).
 // The terminal multipliers (x~G = -dJ/dxG, M u~G = -dJ/duG, theta~ = -dJ/dtheta, I omega~ = -dJ/domega)
 // belong to a step N_t + 1; the fluid multipliers start at zero.
 #include "lks_body_common.cuh"
