@@ -1,0 +1,98 @@
+"""Edge cases of the CUDA path against the oracle: the shortest march (one step), an all-void and an
+all-solid design, a non-square design grid on a ragged analysis grid, a checkpoint interval longer
+than the march, and the empty march, which the library rejects."""
+from __future__ import annotations
+
+import numpy as np
+import pytest
+
+from oracle import oracle as O
+from tests.problems import BC_INFLOW_OUTFLOW, BC_WALL, body2d, body3d, perturbed_state
+from workloads import CKPT_STORE_ALL, CKPT_UNIFORM, gamma_2d
+
+pytestmark = pytest.mark.gpu
+
+
+def _run(P, g, p0, u0, s0, paper=False, **kw):
+    import torch
+    from paper_2601_18272_gb300.lks import Solver
+    S = Solver(P, **kw)
+    try:
+        S.set_initial_state(p0, u0, s0)
+        gam = torch.tensor(g, dtype=torch.float64, device="cuda")
+        J = S.forward(gam)
+        (S.adjoint_alks if paper else S.adjoint)(1.0)
+        dg = torch.empty_like(gam)
+        S.sensitivity(dg)
+        torch.cuda.synchronize()
+        return J, dg.cpu().numpy(), S.dof_history()
+    finally:
+        S.close()
+
+
+def _rel(a, b):
+    return np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300)
+
+
+@pytest.mark.parametrize("make", [lambda: body2d(nt=1), lambda: body3d(nx=24, ny=16, nz=16, centre=(9.3, 7.6, 8.2), nt=1)],
+                         ids=["2d", "3d"])
+def test_single_step(make):
+    """N_t = 1: the forward is one predictor and N_itr coupling iterations; both reverse sweeps
+    are one step."""
+    P, g = make()
+    p0, u0, s0 = perturbed_state(P)
+    G = O.gradient(P, g, p0, u0, s0)
+    Ga = O.gradient_alks(P, g, p0, u0, s0)
+    J, dg, hist = _run(P, g, p0, u0, s0, precision=64, ckpt_policy=CKPT_STORE_ALL)
+    assert hist.shape[0] == 2
+    assert abs(J - G["J"]) <= 1e-11 * abs(G["J"])
+    assert _rel(dg, G["dJdgamma"]) < 1e-9
+    _, dga, _ = _run(P, g, p0, u0, s0, paper=True, precision=64, ckpt_policy=CKPT_STORE_ALL)
+    assert _rel(dga, Ga["dJdgamma"]) < 1e-9
+
+
+@pytest.mark.parametrize("fill", [0.0, 1.0], ids=["void", "solid"])
+def test_uniform_design(fill):
+    """gamma = 0 everywhere (kappa^ref = 0: the body feels no fluid, yet dkappa^ref/dgamma is
+    finite) and gamma = 1 everywhere (kappa^ref = kappa_max)."""
+    P, g = body2d(nt=6)
+    g = np.full_like(g, fill)
+    p0, u0, s0 = perturbed_state(P)
+    G = O.gradient(P, g, p0, u0, s0)
+    J, dg, _ = _run(P, g, p0, u0, s0, precision=64, ckpt_policy=CKPT_STORE_ALL)
+    assert abs(J - G["J"]) <= 1e-11 * max(abs(G["J"]), 1e-12)
+    assert np.linalg.norm(G["dJdgamma"]) > 0
+    assert _rel(dg, G["dJdgamma"]) < 1e-9
+
+
+def test_non_square_design_on_ragged_grid():
+    """A 7 x 5 design grid (pivot at (3, 2)) on a 37 x 21 grid with walls: odd extents everywhere."""
+    P, _ = body2d(nx=37, ny=21, centre=(14.3, 10.4), bc=(BC_INFLOW_OUTFLOW, BC_WALL, BC_WALL), nt=6)
+    P = P.replace(ndx=7, ndy=5)
+    g = gamma_2d(7, 11)[:35]
+    p0, u0, s0 = perturbed_state(P)
+    G = O.gradient(P, g, p0, u0, s0)
+    J, dg, _ = _run(P, g, p0, u0, s0, precision=64, ckpt_policy=CKPT_STORE_ALL)
+    assert abs(J - G["J"]) <= 1e-11 * abs(G["J"])
+    assert _rel(dg, G["dJdgamma"]) < 1e-9
+    Ga = O.gradient_alks(P, g, p0, u0, s0)
+    _, dga, _ = _run(P, g, p0, u0, s0, paper=True, precision=64, ckpt_policy=CKPT_STORE_ALL)
+    assert _rel(dga, Ga["dJdgamma"]) < 1e-9
+
+
+def test_checkpoint_interval_longer_than_march():
+    """Uniform checkpoints every 50 steps on a 7-step march: one segment, the same gradient."""
+    P, g = body2d(nt=7)
+    p0, u0, s0 = perturbed_state(P)
+    a = _run(P, g, p0, u0, s0, precision=64, ckpt_policy=CKPT_STORE_ALL)
+    b = _run(P, g, p0, u0, s0, precision=64, ckpt_policy=CKPT_UNIFORM, ckpt_every=50)
+    assert a[0] == b[0]
+    assert _rel(b[1], a[1]) < 1e-12
+
+
+def test_empty_march_is_rejected():
+    from paper_2601_18272_gb300.lks import LksError, lks_create, problem_struct
+    bad = problem_struct(body2d()[0])
+    bad.n_steps = 0
+    with pytest.raises(LksError, match="LKS_ERR_ARG"):
+        lks_create(bad)
