@@ -149,3 +149,15 @@ def test_alks_free_rotation_is_unsupported():
             S.adjoint_alks(1.0)
     finally:
         S.close()
+
+
+def test_alks_sail2d_80x40_full_fp64():
+    """The 80x40 / 16x16 / 400-step translation workload at its full size, FP64, every state stored:
+    the paper's adjoint element by element against the oracle's."""
+    P, g = config(1)
+    p0, u0, s0 = initial_state(P)
+    G = O.gradient_alks(P, g, p0, u0, s0)
+    r = gpu_alks(P, g, p0, u0, s0)
+    assert abs(r["J"] - G["J"]) <= 1e-11 * abs(G["J"])
+    assert rel(r["dJdgamma"], G["dJdgamma"]) < 1e-8
+    np.testing.assert_allclose(r["body1"], G["body1"], rtol=1e-8, atol=1e-14)

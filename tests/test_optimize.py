@@ -103,3 +103,25 @@ def test_algorithm1_improves_the_rotation_angle():
     assert first[-1].J > first[0].J
     assert h[-1].feasible
     assert np.all((r.gamma >= 0) & (r.gamma <= 1))
+
+
+@pytest.mark.gpu
+def test_algorithm1_with_periodic_warm_start():
+    """Algorithm 1 with the periodic warm start (Sec. 3.4) on a periodic channel: each gradient
+    starts from the previous forward's final state and reverse sweep's initial adjoint; the loop
+    runs, keeps gamma in [0, 1] and raises the angle turned over its first iterations."""
+    from paper_2601_18272_gb300.lks import Solver
+    from paper_2601_18272_gb300.optimize import optimize
+    from tests.problems import BC_PERIODIC, DOF_ROT, body2d
+    P, g = body2d(nt=30, mask=DOF_ROT, obj=(0, 0, 0, 0, 0, 0, 1, 0), nx=40, ny=24, nd=8, centre=(14.3, 12.1),
+                  bc=(BC_PERIODIC,) * 3)
+    P = P.replace(filter_radius=1.5, v_min=0.4)
+    S = Solver(P, precision=64)
+    try:
+        r = optimize(S, g, q_steps=(0.1,), beta_steps=(0.0,), n_opt=5, move=0.1, warm_start=True)
+    finally:
+        S.close()
+    J = [rec.J for rec in r.history]
+    assert len(J) >= 3 and np.all(np.isfinite(J))
+    assert max(J[1:]) > J[0]
+    assert np.all((r.gamma >= 0) & (r.gamma <= 1))
