@@ -23,9 +23,13 @@
 // K2s = sum kappa_m |r_m|^2, K2 = sum kappa_m r_m r_m^T.
 //
 // Each iteration's global reduction is split into a kernel over all SMs that writes one FP64
-// partial per CTA (double-float pairs in the FP32 form) and a one-warp finish kernel that sums the
-// partials in a fixed order and applies the (reverse) EOM: the kernel boundary orders the partials, so no GPU-scope fence or counter is
-// needed, and the sums are deterministic.
+// partial per CTA (double-float pairs in the FP32 form) and a finish that sums the partials in a
+// fixed order and applies the (reverse) EOM: the kernel boundary orders the partials, so no
+// GPU-scope fence or counter is needed, and the sums are deterministic. In the forward the next
+// coupling kernel does the finish in every CTA (one launch per iteration) while the grid has at
+// most kFusedFinishMaxParts CTAs, and a one-CTA k_couple_pre does it once above that; in the
+// reverse the one-CTA k_design_finish does it after the design-point kernel, whose grid is capped
+// (design_ctas) so that it sums few partials.
 #include "lks_body_common.cuh"
 
 namespace lks {
