@@ -215,8 +215,9 @@ LKS_API long long lks_launch_count(const lks_handle* h);
 /* Kernel timing for the benchmark. enable = 1 runs later calls without CUDA graphs and brackets
  * every launch of the named kernel family with CUDA events on the launching stream.
  * lks_kernel_time returns the summed milliseconds and the launch count for the family
- * ("stencil_fwd", "stencil_adj", "couple", "adj_cell", "adj_design", "recompute"); the
- * coupling and design-side families include their one-CTA finish kernels. */
+ * ("stencil_fwd", "stencil_adj", "couple", "adj_cell", "adj_design", "recompute", and for
+ * lks_adjoint_alks "alks_body", "alks_stencil"); the coupling and design-side families include
+ * their one-CTA finish kernels. */
 LKS_API int lks_set_kernel_timing(lks_handle* h, int enable);
 LKS_API int lks_kernel_time(lks_handle* h, const char* family, double* ms_total, long long* launches);
 
