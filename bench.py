@@ -31,6 +31,18 @@ UNIT = "cell-updates/s"
 CONFIG_INDEX = 2
 
 
+def replica_totals(total_ms: float, launches: int, dist=None, device=None):
+    """Whole-job figures of N independent replicas: the slowest rank's time (max over ranks) and
+    the launches of all ranks (sum). Without a process group, the local figures."""
+    import torch
+    t = torch.tensor([float(total_ms)], dtype=torch.float64, device=device)
+    nl = torch.tensor([float(launches)], dtype=torch.float64, device=device)
+    if dist:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        dist.all_reduce(nl, op=dist.ReduceOp.SUM)
+    return float(t.item()), int(nl.item())
+
+
 def _dist():
     ws = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -516,14 +528,7 @@ def main():
         dist.barrier()
     torch.cuda.synchronize()
     clocks = sampler.stop()
-    launches = solver.launches() - l0
-    total_ms = sum(ms)
-    t = torch.tensor([total_ms], dtype=torch.float64, device=dev)
-    nl = torch.tensor([float(launches)], dtype=torch.float64, device=dev)
-    if dist:
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        dist.all_reduce(nl, op=dist.ReduceOp.SUM)
-    total_ms = float(t.item())
+    total_ms, all_launches = replica_totals(sum(ms), solver.launches() - l0, dist, dev)
     cell_steps = P.n_cells * P.n_steps
     value = ws * args.steps * cell_steps / (total_ms / 1000.0)
 
@@ -540,10 +545,8 @@ def main():
         J = lks.lks_gradient_host(solver.handle, gptr, dptr, stream.cuda_stream)
     torch.cuda.synchronize()
     e2e_s = time.perf_counter() - t0
-    te = torch.tensor([e2e_s], dtype=torch.float64, device=dev)
-    if dist:
-        dist.all_reduce(te, op=dist.ReduceOp.MAX)
-    e2e_value = ws * args.steps * cell_steps / float(te.item())
+    e2e_s, _ = replica_totals(e2e_s, 0, dist, dev)
+    e2e_value = ws * args.steps * cell_steps / e2e_s
 
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
@@ -555,7 +558,7 @@ def main():
             "clocks": clocks,
             "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": 8 * P.n_design,
                     "d2h_bytes_per_step": 8 * P.n_design + 8, "J": J},
-            "gpu_launches": int(nl.item())}
+            "gpu_launches": all_launches}
 
     if rank == 0 and not args.skip_extras:
         # dominant kernel: one more gradient with every launch bracketed by CUDA events
