@@ -131,8 +131,9 @@ LKS_API size_t lks_problem_size(void);
 
 /* Initial state for the next forward (Algorithm 1, "Initialize"). p [N], u [dim][N] and
  * s [lks_dof_count] are host arrays (copied). Any pointer may be NULL to keep the default: p = 0,
- * u = (u_in, 0, 0), body at rest at body_centre (R = identity with free rotation).
- * Errors: LKS_ERR_ARG; LKS_ERR_UNSUPPORTED if s starts the body rotated but the workspace was
+ * u = (u_in, 0, 0), body at rest at body_centre (R = identity with free rotation). The last
+ * forward and its adjoints become invalid (the reverse sweep restarts from the initial state), so
+ * lks_adjoint needs a new lks_forward. Errors: LKS_ERR_ARG; LKS_ERR_UNSUPPORTED if s starts the body rotated but the workspace was
  * sized for an axis-aligned box (see lks_create); LKS_ERR_CUDA. */
 LKS_API int lks_set_initial_state(lks_handle* h, const double* p_host, const double* u_host, const double* s_host);
 
@@ -158,7 +159,8 @@ LKS_API int lks_set_continuation(lks_handle* h, double q, double proj_beta);
  * and the body multipliers (Eqs. axg, aug, atheta, aomega, N_itr fixed-point iterations per step),
  * accumulating Eq. design_sensitivity; lks_sensitivity then returns its dJ/dgamma. A discretised
  * continuous adjoint: it approaches the exact gradient of lks_adjoint but is not equal to it.
- * Seeded with dJ = seed; enqueued on the stream. The first call allocates its buffers (about
+ * Seeded with dJ = seed; enqueued on the stream. The exact adjoint's lambda(0) of an earlier
+ * lks_adjoint of the same forward stays available. The first call allocates its buffers (about
  * (2 (1 + dim + dim(dim+1)/2) + dim) N field values). Single rotation axis only.
  * Errors: LKS_ERR_ORDER (no forward), LKS_ERR_UNSUPPORTED (free rotation, or a warm-start terminal
  * adjoint is set), LKS_ERR_OOM / LKS_ERR_BUDGET, LKS_ERR_CUDA. */
@@ -182,7 +184,8 @@ LKS_API int lks_sensitivity(lks_handle* h, double* dJdgamma_dev, void* stream);
  * J + lambda(0).state(N_t). The copies stay on the device (the DOFs pass through the host). The
  * next lks_forward and lks_adjoint use them; lks_set_initial_state replaces the initial state
  * (the terminal adjoint stays until the next lks_warm_start). Synchronises the stream.
- * Errors: LKS_ERR_ORDER (no forward, or with_adjoint without an adjoint), LKS_ERR_UNSUPPORTED (the
+ * Errors: LKS_ERR_ORDER (no forward, or with_adjoint without an lks_adjoint of that forward: the
+ * paper-form adjoint has no lambda(0) of the state), LKS_ERR_UNSUPPORTED (the
  * final DOFs start rotated but the workspace was sized for an axis-aligned box), LKS_ERR_CUDA. */
 LKS_API int lks_warm_start(lks_handle* h, int with_adjoint, void* stream);
 
@@ -206,7 +209,8 @@ LKS_API int lks_get_dof_history(lks_handle* h, double* host_buf, size_t n);
 LKS_API int lks_get_state(lks_handle* h, double* p_host, double* u_host);
 
 /* Adjoint of the initial state after the last lks_adjoint: dJ/dp0 [N], dJ/du0 [dim][N],
- * dJ/ds0 [lks_dof_count] (host, any may be NULL). Synchronous. */
+ * dJ/ds0 [lks_dof_count] (host, any may be NULL). Synchronous. Errors: LKS_ERR_ORDER (no
+ * lks_adjoint of the last forward; lks_adjoint_alks does not count). */
 LKS_API int lks_get_initial_adjoint(lks_handle* h, double* lam_p_host, double* lam_u_host, double* lam_s_host);
 
 /* Number of kernels this handle has launched (graph nodes counted per replay). */

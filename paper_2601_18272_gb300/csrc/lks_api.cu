@@ -101,7 +101,9 @@ struct lks_handle {
   std::map<std::string, cudaGraphExec_t> graphs;
   std::map<std::string, int> graph_kernels;
   bool box_rot_ok = true;  // buffers hold the rotated box
-  bool fwd_done = false, adj_done = false;
+  // what the last calls left valid: a forward, an adjoint of it (either form: dkref), the exact
+  // adjoint's lambda(0) and dJ/ds(0), the paper-form adjoint's moments
+  bool fwd_done = false, adj_done = false, exact_done = false;
   long long launches = 0;
   bool timing = false;
   std::map<std::string, TimerFamily> timers;
@@ -837,6 +839,8 @@ int lks_set_initial_state(lks_handle* h, const double* p, const double* u, const
     for (int a = 0; a < g.ns; ++a) h->host_s0[a] = s[a];
     CK(cudaMemcpy(h->init_s, h->host_s0, g.ns * sizeof(double), cudaMemcpyHostToDevice));
   }
+  // the reverse sweep restores its first segment from the initial state: a new one voids the forward
+  h->fwd_done = h->adj_done = h->exact_done = h->alks_done = false;
   return refresh_box(h);
 }
 
@@ -844,7 +848,7 @@ int lks_forward(lks_handle* h, const double* gamma_dev, double* J_host, void* st
   if (!h || !gamma_dev) return LKS_ERR_ARG;
   cudaStream_t st = (cudaStream_t)stream;
   const Geo& g = h->g;
-  h->fwd_done = h->adj_done = false;
+  h->fwd_done = h->adj_done = h->exact_done = h->alks_done = false;
   if ((const void*)gamma_dev != (const void*)h->gamma)
     CK(cudaMemcpyAsync(h->gamma, gamma_dev, (size_t)g.ND * sizeof(double), cudaMemcpyDeviceToDevice, st));
   Launcher L0{h, st, false};
@@ -876,13 +880,14 @@ int lks_adjoint(lks_handle* h, double seed, void* stream) {
   if (!h) return LKS_ERR_ARG;
   if (!h->fwd_done) return LKS_ERR_ORDER;
   cudaStream_t st = (cudaStream_t)stream;
+  h->adj_done = h->exact_done = false;
   int r = (h->prec == LKS_FP64) ? adjoint_impl<double>(h, seed, st) : adjoint_impl<float>(h, seed, st);
   if (r != LKS_OK) return r;
   if (h->timing) {
     CK(cudaStreamSynchronize(st));
     collect_timers(h);
   }
-  h->adj_done = true;
+  h->adj_done = h->exact_done = true;
   return LKS_OK;
 }
 
@@ -895,7 +900,7 @@ int lks_set_continuation(lks_handle* h, double q, double proj_beta) {
   h->P.proj_beta = proj_beta;
   h->g.pbeta = proj_beta;
   clear_graphs(h);  // no captured launch may keep the old values
-  h->fwd_done = h->adj_done = h->alks_done = false;
+  h->fwd_done = h->adj_done = h->exact_done = h->alks_done = false;
   return LKS_OK;
 }
 
@@ -914,6 +919,7 @@ int lks_adjoint_alks(lks_handle* h, double seed, void* stream) {
     TRY(dalloc(h, &h->al_part, (size_t)nb * alks_partial_values(g.dim) * 2 * sizeof(double)));
   }
   cudaStream_t st = (cudaStream_t)stream;
+  h->adj_done = h->alks_done = false;  // the exact adjoint's lambda(0) is untouched
   h->alks_mode = true;
   int r = (h->prec == LKS_FP64) ? adjoint_impl<double>(h, seed, st) : adjoint_impl<float>(h, seed, st);
   h->alks_mode = false;
@@ -969,7 +975,7 @@ int lks_sensitivity(lks_handle* h, double* out, void* stream) {
 
 int lks_warm_start(lks_handle* h, int with_adjoint, void* stream) {
   if (!h) return LKS_ERR_ARG;
-  if (!h->fwd_done || (with_adjoint && !h->adj_done)) return LKS_ERR_ORDER;
+  if (!h->fwd_done || (with_adjoint && !h->exact_done)) return LKS_ERR_ORDER;
   cudaStream_t st = (cudaStream_t)stream;
   const Geo& g = h->g;
   const int NT = h->P.n_steps;
@@ -992,7 +998,7 @@ int lks_warm_start(lks_handle* h, int with_adjoint, void* stream) {
   for (int a = 0; a < kNdofFree; ++a) h->host_s0[a] = (a < g.ns) ? last.s[a] : 0.0;
   CK(cudaMemcpy(h->init_s, h->host_s0, g.ns * sizeof(double), cudaMemcpyHostToDevice));
   h->has_term = with_adjoint != 0;
-  h->fwd_done = h->adj_done = false;
+  h->fwd_done = h->adj_done = h->exact_done = h->alks_done = false;
   return refresh_box(h);
 }
 
@@ -1072,7 +1078,7 @@ int lks_get_state(lks_handle* h, double* p, double* u) {
 
 int lks_get_initial_adjoint(lks_handle* h, double* lp, double* lu, double* ls) {
   if (!h) return LKS_ERR_ARG;
-  if (!h->adj_done) return LKS_ERR_ORDER;
+  if (!h->exact_done) return LKS_ERR_ORDER;
   const long long M = h->slot_elems, N = h->g.N;
   std::vector<char> raw((size_t)M * h->esz);
   CK(cudaDeviceSynchronize());

@@ -1,6 +1,7 @@
 """Edge cases of the CUDA path against the oracle: the shortest march (one step), an all-void and an
 all-solid design, a non-square design grid on a ragged analysis grid, a checkpoint interval longer
-than the march, and the empty march, which the library rejects."""
+than the march, the empty march, which the library rejects, and the order of the calls: what needs the
+exact adjoint refuses the paper-form one, and a new initial state voids the last forward."""
 from __future__ import annotations
 
 import numpy as np
@@ -96,3 +97,37 @@ def test_empty_march_is_rejected():
     bad.n_steps = 0
     with pytest.raises(LksError, match="LKS_ERR_ARG"):
         lks_create(bad)
+
+
+def test_call_order_rules():
+    """lks_get_initial_adjoint and lks_warm_start(with_adjoint) need an exact adjoint of the last
+    forward (the paper-form adjoint has no lambda(0) of the state); a new initial state voids the last
+    forward, since the reverse sweep restarts from the initial state."""
+    import torch
+    from paper_2601_18272_gb300.lks import LksError, Solver
+    P, g = body2d(nt=3)
+    p0, u0, s0 = perturbed_state(P)
+    S = Solver(P, precision=64, ckpt_policy=CKPT_UNIFORM, ckpt_every=2)
+    try:
+        gam = torch.tensor(g, dtype=torch.float64, device="cuda")
+        S.set_initial_state(p0, u0, s0)
+        S.forward(gam)
+        S.adjoint_alks(1.0)
+        with pytest.raises(LksError, match="LKS_ERR_ORDER"):
+            S.initial_adjoint()
+        with pytest.raises(LksError, match="LKS_ERR_ORDER"):
+            S.warm_start(True)
+        S.adjoint(1.0)
+        lp = S.initial_adjoint()[0]
+        S.adjoint_alks(1.0)  # leaves the exact adjoint's lambda(0) in place
+        assert np.array_equal(S.initial_adjoint()[0], lp)
+        S.alks_adjoint()
+        S.set_initial_state(p0, u0, s0)
+        for call in (lambda: S.adjoint(1.0), S.initial_adjoint, S.alks_adjoint, S.state):
+            with pytest.raises(LksError, match="LKS_ERR_ORDER"):
+                call()
+        S.forward(gam)
+        S.adjoint(1.0)
+        assert np.array_equal(S.initial_adjoint()[0], lp)
+    finally:
+        S.close()
