@@ -3,6 +3,10 @@
 forward : J(gamma) through lks_forward (LKS + rigid-body march, Algorithm 1 state loop)
 backward: dJ/dgamma through lks_adjoint (reverse sweep) and lks_sensitivity; torch only supplies
           the device tensors and the current stream.
+
+The solver keeps the history of its latest forward only, so a backward must come before the next
+forward on the same solver; an out-of-order backward raises instead of differentiating the wrong
+march.
 """
 from __future__ import annotations
 
@@ -17,6 +21,7 @@ class LKSObjective(torch.autograd.Function):
         g = gamma.detach().to(torch.float64).contiguous()
         J = solver.forward(g)
         ctx.solver = solver
+        ctx.forward_id = solver.forward_count
         ctx.gamma_shape = gamma.shape
         ctx.gamma_dtype = gamma.dtype
         return torch.tensor(J, dtype=torch.float64, device=gamma.device)
@@ -24,6 +29,9 @@ class LKSObjective(torch.autograd.Function):
     @staticmethod
     def backward(ctx, gJ: torch.Tensor):
         solver = ctx.solver
+        if solver.forward_count != ctx.forward_id:
+            raise RuntimeError("LKSObjective.backward: the solver ran another forward after this one and holds "
+                               "only the latest history; run each backward before the next forward")
         solver.adjoint(float(gJ.item()))
         out = torch.empty(solver.P.n_design, dtype=torch.float64, device=gJ.device)
         solver.sensitivity(out)

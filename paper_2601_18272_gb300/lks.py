@@ -307,6 +307,7 @@ class Solver:
         self.P = P
         self.struct = problem_struct(P, **overrides)
         self.handle = lks_create(self.struct)
+        self.forward_count = 0  # forwards run so far: a reverse sweep belongs to the latest one
 
     @property
     def n_steps(self) -> int:
@@ -319,6 +320,7 @@ class Solver:
         import torch
         assert gamma.is_cuda and gamma.dtype == torch.float64 and gamma.is_contiguous()
         st = torch.cuda.current_stream(gamma.device) if stream is None else stream
+        self.forward_count += 1
         return lks_forward(self.handle, gamma.data_ptr(), st.cuda_stream)
 
     def adjoint(self, seed: float = 1.0, stream=None):
