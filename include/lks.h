@@ -129,6 +129,23 @@ LKS_API int lks_dof_count(const lks_problem* problem);
 /* sizeof(lks_problem) as compiled into the library, for bindings that mirror the struct. */
 LKS_API size_t lks_problem_size(void);
 
+/* Actions of the binomial checkpoint schedule (LKS_CKPT_BINOMIAL), in the order the library runs them. */
+enum {
+  LKS_BIN_FWD_SNAPSHOT = 0, /* the forward keeps state(b) in snapshot slot a on its way */
+  LKS_BIN_RESTORE = 1,      /* the working state <- snapshot slot a (-1: the initial state), which holds state(b) */
+  LKS_BIN_ADVANCE = 2,      /* re-advance the working state from state(a) by b steps */
+  LKS_BIN_STORE = 3,        /* snapshot slot a <- the working state, state(b) (c steps past the last restore) */
+  LKS_BIN_REVERSE = 4       /* reverse step a (its recompute from state(a - 1), then its adjoint) */
+};
+
+/* The binomial schedule (Griewank's revolve: the least total re-advanced steps for the given number
+ * of snapshot slots, the initial state being restorable too) of an n_steps march with `snapshots`
+ * slots, as the library builds it for lks_create with LKS_CKPT_BINOMIAL and ckpt_every =
+ * snapshots. Host only (no device work). Writes min(count, capacity) actions as rows of four ints
+ * (kind, a, b, c) into ops (host, [capacity][4]; may be NULL if capacity is 0) and returns the
+ * action count, or -LKS_ERR_ARG for n_steps < 1, snapshots < 0 or capacity < 0. */
+LKS_API long long lks_binomial_plan(int n_steps, int snapshots, int* ops, long long capacity);
+
 /* Initial state for the next forward (Algorithm 1, "Initialize"). p [N], u [dim][N] and
  * s [lks_dof_count] are host arrays (copied). Any pointer may be NULL to keep the default: p = 0,
  * u = (u_in, 0, 0), body at rest at body_centre (R = identity with free rotation). The last

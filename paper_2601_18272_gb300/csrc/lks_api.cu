@@ -7,9 +7,10 @@
 //   uniform   : ping-pong state, a checkpoint every k steps; the adjoint restores a checkpoint,
 //               recomputes the segment (stencil + Brinkman update with the stored DOF iterates)
 //               into a segment ring, then reverses it.
-//   binomial  : s state snapshots placed along a binomial schedule (the classic optimal
-//               checkpointing recursion for a fixed number of snapshots); the reverse sweep
-//               re-advances from the nearest snapshot and reverses one step at a time.
+//   binomial  : s state snapshots placed along a binomial schedule (Griewank's optimal
+//               checkpointing recursion for a fixed number of snapshots), built once as a list of
+//               actions; the reverse sweep re-advances from the nearest snapshot and reverses one
+//               step at a time.
 // Adjoint (Algorithm 1, adjoint loop): per step, for k = N_itr..1 a cell-side and a design-side
 // reverse kernel, then the transposed stencil.
 #include <algorithm>
@@ -41,6 +42,12 @@ struct TimerFamily {
   long long launches = 0;
 };
 
+// One action of the binomial checkpoint schedule (kinds LKS_BIN_* of the C ABI), built on the host
+// once per handle and replayed by the forward (LKS_BIN_FWD_SNAPSHOT) and by the reverse sweep.
+struct BinOp {
+  int kind, a, b, c;
+};
+
 }  // namespace
 
 struct lks_handle {
@@ -56,7 +63,7 @@ struct lks_handle {
   unsigned short* ckq = nullptr;  // uniform, BF16/FP16: checkpoints at t = k, 2k, ... (t = 0 from init)
   unsigned* ckkeys = nullptr;     // their per-plane ranges
   int nckpt = 0;
-  std::vector<int> bin_pts;  // binomial: steps whose state the forward snapshots (slot j for entry j)
+  std::vector<BinOp> bin_plan;  // binomial: the schedule (the forward's snapshots, the reverse's actions)
   long long slot_elems = 0;
   void* boxstore = nullptr;  // u* in the body box, one slab per step of the resident segment
   int nbox = 0;
@@ -352,38 +359,67 @@ void clear_graphs(lks_handle* h) {
   h->graph_kernels.clear();
 }
 
-// Binomial checkpointing. beta(s, r) = C(s + r, s) is the longest march that s snapshots reverse
-// with each step advanced at most r + 1 times; a march of n steps with s snapshots is split after
-// m steps, the remaining n - m being reversed with s - 1 snapshots and r repetitions and the first
-// m with s snapshots and r - 1 (beta(s, r) = beta(s, r - 1) + beta(s - 1, r)).
-long long binomial_beta(int s, int r) {
+// Binomial checkpointing (Griewank's revolve schedule). The initial state and s snapshot slots are
+// the c = s + 1 states a reversal can restart from. beta(c, r) = C(c + r, c) is the longest march
+// that c such states reverse with each step advanced at most r times besides its own reverse
+// step. A march of n steps is split after m steps: the last n - m are reversed from a snapshot of
+// state(t0 + m) with one slot fewer, then the first m with all slots again. Every m in
+// [max(beta(c, r-2), n - beta(c-1, r-1) - beta(c-2, r)), min(beta(c, r-1), n - beta(c-1, r-1))]
+// (r the least with beta(c, r) >= n) gives the least total number of re-advanced steps,
+// r n - beta(c+1, r-1); the upper end also leaves the most work to the snapshots the forward
+// takes on its way (they cost no extra steps), so it is the split taken everywhere.
+long long binomial_beta(int c, int r) {
+  if (c < 0 || r < 0) return 0;
   long long b = 1;
-  for (int i = 1; i <= s; ++i) {
+  for (int i = 1; i <= c; ++i) {
     b = b * (r + i) / i;  // C(r + i, i), exact at every step
     if (b > (1LL << 50)) return 1LL << 50;
   }
   return b;
 }
 int binomial_split(int n, int s) {  // n >= 2, s >= 1
-  int r = 0;
-  while (binomial_beta(s, r) < n) ++r;
-  long long m = n - binomial_beta(s - 1, r);
+  const int c = s + 1;
+  int r = 1;
+  while (binomial_beta(c, r) < n) ++r;
+  long long m = std::min(binomial_beta(c, r - 1), (long long)n - binomial_beta(c - 1, r - 1));
   if (m < 1) m = 1;
   if (m > n - 1) m = n - 1;
   return (int)m;
 }
-// The snapshots of the first descent of the recursion, which the forward pass takes on its way.
-std::vector<int> binomial_first_descent(int n, int s) {
-  std::vector<int> pts;
-  int t = 0;
-  while (s > 0 && n > 1) {
-    const int m = binomial_split(n, s);
-    t += m;
-    pts.push_back(t);
-    n -= m;
-    --s;
+
+// Reverse of steps t0+1 .. t0+n with s free snapshot slots; state(t0) is the initial state (src < 0)
+// or snapshot src. first: the snapshots of this branch's first descent are the forward's. Snapshot
+// slot d belongs to recursion depth d.
+void binomial_plan_rec(std::vector<BinOp>& ops, int t0, int n, int s, bool first, int src, int depth) {
+  if (n <= 0) return;
+  if (n == 1) {
+    ops.push_back({LKS_BIN_RESTORE, src, t0, 0});
+    ops.push_back({LKS_BIN_REVERSE, t0 + 1, t0, 0});
+    return;
   }
-  return pts;
+  if (s == 0) {  // no snapshot left: re-advance for every step
+    for (int j = n; j >= 1; --j) {
+      ops.push_back({LKS_BIN_RESTORE, src, t0, 0});
+      if (j > 1) ops.push_back({LKS_BIN_ADVANCE, t0, j - 1, 0});
+      ops.push_back({LKS_BIN_REVERSE, t0 + j, t0, 0});
+    }
+    return;
+  }
+  const int m = binomial_split(n, s);
+  if (first) {
+    ops.push_back({LKS_BIN_FWD_SNAPSHOT, depth, t0 + m, 0});
+  } else {
+    ops.push_back({LKS_BIN_RESTORE, src, t0, 0});
+    ops.push_back({LKS_BIN_ADVANCE, t0, m, 0});
+    ops.push_back({LKS_BIN_STORE, depth, t0 + m, m});
+  }
+  binomial_plan_rec(ops, t0 + m, n - m, s - 1, first, depth, depth + 1);
+  binomial_plan_rec(ops, t0, m, s, false, src, depth);
+}
+std::vector<BinOp> binomial_plan(int n, int s) {
+  std::vector<BinOp> ops;
+  binomial_plan_rec(ops, 0, n, s, true, -1, 0);
+  return ops;
 }
 
 template <typename T>
@@ -450,17 +486,22 @@ int forward_impl(lks_handle* h, cudaStream_t st) {
     // march in pieces between the snapshot steps of the first descent, snapshotting each
     Slots<T> S = pp_slots<T>(h);
     L0("init", [&](cudaStream_t s) { launch_init_forward<T>(g, S, h->init_p, h->init_u, h->init_s, h->it, h->ctrl, s); });
+    std::vector<BinOp> stops;  // the forward's snapshots (ascending steps), then the end of the march
+    for (const BinOp& op : h->bin_plan)
+      if (op.kind == LKS_BIN_FWD_SNAPSHOT) stops.push_back(op);
+    stops.push_back({-1, -1, NT, 0});
     int t = 0;
-    for (size_t j = 0; j <= h->bin_pts.size(); ++j) {
-      const int t1 = (j < h->bin_pts.size()) ? h->bin_pts[j] : NT;
+    for (const BinOp& stop : stops) {
+      const int t1 = stop.b;
       const int n = t1 - t;
       if (n > 0) {
         L0("init", [&](cudaStream_t s) { launch_set_step(h->ctrl, t + 1, 0, s); });
         TRY(run_graph(h, "fwd_b_" + std::to_string(n), st, [&](Launcher& L) { enqueue_fwd_steps<T>(h, L, S, n, false); }));
       }
-      if (j < h->bin_pts.size())
-        CK(cudaMemcpyAsync((char*)h->ckpt + j * h->slot_elems * h->esz, (char*)h->pp + (t1 & 1) * h->slot_elems * h->esz,
-                           h->slot_elems * h->esz, cudaMemcpyDeviceToDevice, st));
+      if (stop.a >= 0)
+        CK(cudaMemcpyAsync((char*)h->ckpt + (size_t)stop.a * h->slot_elems * h->esz,
+                           (char*)h->pp + (t1 & 1) * h->slot_elems * h->esz, h->slot_elems * h->esz,
+                           cudaMemcpyDeviceToDevice, st));
       t = t1;
     }
   } else if (h->P.ckpt_policy == LKS_CKPT_STORE_ALL) {
@@ -502,58 +543,47 @@ int forward_impl(lks_handle* h, cudaStream_t st) {
   return LKS_OK;
 }
 
-// Reverse of steps t0+1 .. t0+n with s free snapshot slots; state(t0) is the initial state
-// (src < 0) or snapshot src. The working pair (ring) holds state(t0) in slot 0 after a restore, so
-// its slot base is t0. first: the snapshots of this branch's first descent exist (the forward took
-// them). Snapshot slot d belongs to recursion depth d.
+// The reverse sweep of the binomial schedule: its actions in order. The working pair (ring) holds
+// state(t0) in slot 0 after a restore, so its slot base is t0; an advance by m leaves state(t0 + m)
+// in slot m mod 2.
 template <typename T>
-int binomial_reverse(lks_handle* h, cudaStream_t st, int t0, int n, int s, bool first, int src, int depth) {
+int binomial_reverse(lks_handle* h, cudaStream_t st) {
   const Geo& g = h->g;
   Slots<T> W = ring_slots<T>(h);
   Launcher L0{h, st, false};
   const size_t sb = h->slot_elems * h->esz;
-  auto restore = [&]() -> int {
-    if (src < 0)
-      L0("ckpt", [&](cudaStream_t x) { launch_state_from_double<T>(g, (T*)h->ring, h->init_p, h->init_u, x); });
-    else
-      CK(cudaMemcpyAsync(h->ring, (char*)h->ckpt + (size_t)src * sb, sb, cudaMemcpyDeviceToDevice, st));
-    return LKS_OK;
-  };
-  auto advance = [&](int nadv) -> int {  // state(t0) -> state(t0 + nadv) in the working pair
-    if (nadv <= 0) return LKS_OK;
-    L0("init", [&](cudaStream_t x) { launch_set_step(h->ctrl, t0 + 1, t0, x); });
-    return run_graph(h, "bin_adv_" + std::to_string(nadv), st,
-                     [&](Launcher& L) { enqueue_recompute<T>(h, L, W, nadv); });
-  };
-  auto reverse_step = [&](int t) -> int {  // needs state(t-1) in the working pair (base t0)
-    L0("init", [&](cudaStream_t x) { launch_set_step(h->ctrl, t, t0, x); });
-    return run_graph(h, h->alks_mode ? "alks_bin_rev1" : "bin_rev1", st, [&](Launcher& L) {
-      enqueue_recompute<T>(h, L, W, 1);
-      enqueue_adj_steps<T>(h, L, W, 1);
-    });
-  };
-  if (n <= 0) return LKS_OK;
-  if (n == 1) {
-    TRY(restore());
-    return reverse_step(t0 + 1);
-  }
-  if (s == 0) {  // no snapshot left: re-advance for every step
-    for (int j = n; j >= 1; --j) {
-      TRY(restore());
-      TRY(advance(j - 1));
-      TRY(reverse_step(t0 + j));
+  for (const BinOp& op : h->bin_plan) {
+    switch (op.kind) {
+      case LKS_BIN_RESTORE:  // a: snapshot slot (-1: the initial state)
+        if (op.a < 0)
+          L0("ckpt", [&](cudaStream_t x) { launch_state_from_double<T>(g, (T*)h->ring, h->init_p, h->init_u, x); });
+        else
+          CK(cudaMemcpyAsync(h->ring, (char*)h->ckpt + (size_t)op.a * sb, sb, cudaMemcpyDeviceToDevice, st));
+        break;
+      case LKS_BIN_ADVANCE: {  // state(a) -> state(a + b)
+        const int t0 = op.a, n = op.b;
+        L0("init", [&](cudaStream_t x) { launch_set_step(h->ctrl, t0 + 1, t0, x); });
+        TRY(run_graph(h, "bin_adv_" + std::to_string(n), st, [&](Launcher& L) { enqueue_recompute<T>(h, L, W, n); }));
+        break;
+      }
+      case LKS_BIN_STORE:  // snapshot slot a <- state(b), c steps past the working pair's base
+        CK(cudaMemcpyAsync((char*)h->ckpt + (size_t)op.a * sb, (char*)h->ring + (size_t)(op.c & 1) * sb, sb,
+                           cudaMemcpyDeviceToDevice, st));
+        break;
+      case LKS_BIN_REVERSE: {  // step a from state(a - 1) in the working pair (base b)
+        const int t = op.a, t0 = op.b;
+        L0("init", [&](cudaStream_t x) { launch_set_step(h->ctrl, t, t0, x); });
+        TRY(run_graph(h, h->alks_mode ? "alks_bin_rev1" : "bin_rev1", st, [&](Launcher& L) {
+          enqueue_recompute<T>(h, L, W, 1);
+          enqueue_adj_steps<T>(h, L, W, 1);
+        }));
+        break;
+      }
+      default:  // LKS_BIN_FWD_SNAPSHOT: taken by the forward
+        break;
     }
-    return LKS_OK;
   }
-  const int m = binomial_split(n, s);
-  if (!first) {
-    TRY(restore());
-    TRY(advance(m));
-    CK(cudaMemcpyAsync((char*)h->ckpt + (size_t)depth * sb, (char*)h->ring + (size_t)(m & 1) * sb, sb,
-                       cudaMemcpyDeviceToDevice, st));
-  }
-  TRY(binomial_reverse<T>(h, st, t0 + m, n - m, s - 1, first, depth, depth + 1));
-  return binomial_reverse<T>(h, st, t0, m, s, false, src, depth);
+  return LKS_OK;
 }
 
 template <typename T>
@@ -575,7 +605,7 @@ int adjoint_impl(lks_handle* h, double seed, cudaStream_t st) {
     });
   }
   if (h->P.ckpt_policy == LKS_CKPT_BINOMIAL) {
-    TRY(binomial_reverse<T>(h, st, 0, NT, h->P.ckpt_every, true, -1, 0));
+    TRY(binomial_reverse<T>(h, st));
   } else if (h->P.ckpt_policy == LKS_CKPT_STORE_ALL) {
     Slots<T> S = ring_slots<T>(h);
     for (int t1 = NT; t1 >= 1; t1 -= h->chunk) {
@@ -626,8 +656,10 @@ int allocate(lks_handle* h) {
   } else if (P.ckpt_policy == LKS_CKPT_BINOMIAL) {
     h->nring = 2;  // working pair of the reverse sweep
     h->nbox = 1;
-    h->bin_pts = binomial_first_descent(NT, P.ckpt_every);
-    h->nckpt = (int)h->bin_pts.size();
+    h->bin_plan = binomial_plan(NT, P.ckpt_every);
+    h->nckpt = 0;  // the slots the schedule uses
+    for (const BinOp& op : h->bin_plan)
+      if (op.kind == LKS_BIN_FWD_SNAPSHOT || op.kind == LKS_BIN_STORE) h->nckpt = std::max(h->nckpt, op.a + 1);
     TRY(dalloc(h, &h->pp, 2 * slot_bytes));
     if (h->nckpt > 0) TRY(dalloc(h, &h->ckpt, (size_t)h->nckpt * slot_bytes));
   } else {
@@ -734,6 +766,19 @@ const char* lks_status_string(int s) {
 int lks_last_cuda_error(void) { return g_last_cuda_error; }
 
 size_t lks_problem_size(void) { return sizeof(lks_problem); }
+
+long long lks_binomial_plan(int n_steps, int snapshots, int* ops, long long capacity) {
+  if (n_steps < 1 || snapshots < 0 || capacity < 0 || (capacity > 0 && !ops)) return -(long long)LKS_ERR_ARG;
+  const std::vector<BinOp> plan = binomial_plan(n_steps, snapshots);
+  const long long n = (long long)plan.size();
+  for (long long i = 0; i < std::min(n, capacity); ++i) {
+    ops[4 * i] = plan[i].kind;
+    ops[4 * i + 1] = plan[i].a;
+    ops[4 * i + 2] = plan[i].b;
+    ops[4 * i + 3] = plan[i].c;
+  }
+  return n;
+}
 
 int lks_dof_count(const lks_problem* P) {
   if (!P) return 0;

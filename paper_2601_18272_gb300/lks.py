@@ -19,6 +19,7 @@ LKS_D2Q9, LKS_D3Q15 = 9, 15
 LKS_FP32, LKS_FP64 = 32, 64
 LKS_CKPT_STORE_ALL, LKS_CKPT_UNIFORM, LKS_CKPT_BINOMIAL = 0, 1, 2
 LKS_CKPT_NATIVE, LKS_CKPT_BF16, LKS_CKPT_FP16 = 0, 1, 2
+LKS_BIN_FWD_SNAPSHOT, LKS_BIN_RESTORE, LKS_BIN_ADVANCE, LKS_BIN_STORE, LKS_BIN_REVERSE = 0, 1, 2, 3, 4
 LKS_ROT_FREE = -1
 LKS_NDOF_AXIS, LKS_NDOF_FREE, LKS_MAX_DOF = 8, 21, 21
 STATUS = {0: "LKS_OK", 1: "LKS_ERR_ARG", 2: "LKS_ERR_OOM", 3: "LKS_ERR_BUDGET", 4: "LKS_ERR_UNSTABLE",
@@ -114,6 +115,8 @@ def load() -> ctypes.CDLL:
     L.lks_dof_count.argtypes = [ctypes.POINTER(lks_problem)]
     L.lks_constraint.argtypes = [hp, vp, dp, vp, vp]
     L.lks_warm_start.argtypes = [hp, ctypes.c_int, vp]
+    L.lks_binomial_plan.argtypes = [ctypes.c_int, ctypes.c_int, vp, ctypes.c_longlong]
+    L.lks_binomial_plan.restype = ctypes.c_longlong
     L.lks_problem_size.argtypes = []
     L.lks_problem_size.restype = ctypes.c_size_t
     if L.lks_problem_size() != ctypes.sizeof(lks_problem):
@@ -235,6 +238,18 @@ def lks_constraint(h, gamma_dev_ptr: int, dG_dev_ptr: int = 0, stream: int = 0) 
 
 def lks_warm_start(h, with_adjoint: bool = True, stream: int = 0):
     _check(load().lks_warm_start(h, int(bool(with_adjoint)), ctypes.c_void_p(stream)), "lks_warm_start")
+
+
+def lks_binomial_plan(n_steps: int, snapshots: int) -> np.ndarray:
+    """The binomial checkpoint schedule as rows (kind, a, b, c), kinds LKS_BIN_* (host only)."""
+    L = load()
+    n = L.lks_binomial_plan(int(n_steps), int(snapshots), None, 0)
+    if n < 0:
+        raise LksError(int(-n), "lks_binomial_plan")
+    ops = np.zeros((n, 4), dtype=np.int32)
+    if n:
+        L.lks_binomial_plan(int(n_steps), int(snapshots), ops.ctypes.data, n)
+    return ops
 
 
 def lks_dof_count(problem: lks_problem) -> int:
