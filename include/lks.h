@@ -221,8 +221,9 @@ LKS_API int lks_gradient_host(lks_handle* h, const double* gamma_host, double* J
  * doubles. */
 LKS_API int lks_get_dof_history(lks_handle* h, double* host_buf, size_t n);
 
-/* Final state of the last forward: p [N], u [dim][N] as doubles (host). Only for
- * LKS_CKPT_STORE_ALL or when n_steps is a multiple of ckpt_every. Synchronous. */
+/* Final state of the last forward: p [N], u [dim][N] as doubles (host), any checkpoint policy.
+ * Synchronous. Errors: LKS_ERR_ORDER (no forward since the last lks_create, lks_set_initial_state,
+ * lks_set_continuation or lks_warm_start). */
 LKS_API int lks_get_state(lks_handle* h, double* p_host, double* u_host);
 
 /* Adjoint of the initial state after the last lks_adjoint: dJ/dp0 [N], dJ/du0 [dim][N],

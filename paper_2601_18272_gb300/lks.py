@@ -133,8 +133,19 @@ def _check(code: int, where: str):
 def _dptr(a: Optional[np.ndarray]):
     if a is None:
         return None
-    assert a.dtype == np.float64 and a.flags.c_contiguous
+    if a.dtype != np.float64 or not a.flags.c_contiguous:
+        raise TypeError("host arrays passed to the library must be contiguous float64")
     return a.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+
+
+def check_design_tensor(t, n_design: int, name: str = "gamma"):
+    """Raise unless t is a contiguous float64 CUDA tensor of n_design values: the library reads or
+    writes exactly that many doubles at its address."""
+    import torch
+    if not isinstance(t, torch.Tensor) or not t.is_cuda or t.dtype != torch.float64 or not t.is_contiguous():
+        raise TypeError(f"{name} must be a contiguous float64 CUDA tensor")
+    if t.numel() != n_design:
+        raise ValueError(f"{name}: {t.numel()} values, expected {n_design}")
 
 
 def problem_struct(P, precision: Optional[int] = None, ckpt_policy: Optional[int] = None,
@@ -187,6 +198,14 @@ def lks_set_initial_state(h, p: Optional[np.ndarray] = None, u: Optional[np.ndar
     conv = lambda a: None if a is None else np.ascontiguousarray(a, dtype=np.float64)  # noqa: E731
     p, u, s = conv(p), conv(u), conv(s)
     _check(load().lks_set_initial_state(h, _dptr(p), _dptr(u), _dptr(s)), "lks_set_initial_state")
+
+
+def check_initial_state(n_cells: int, dim: int, n_dof: int, p=None, u=None, s=None):
+    """Raise ValueError unless each given array holds exactly the values lks_set_initial_state
+    reads: p [N], u [dim][N], s [n_dof] (the library reads that many, whatever the array holds)."""
+    for name, a, n in (("p", p, n_cells), ("u", u, dim * n_cells), ("s", s, n_dof)):
+        if a is not None and np.size(a) != n:
+            raise ValueError(f"initial state {name}: {np.size(a)} values, expected {n}")
 
 
 def lks_forward(h, gamma_dev_ptr: int, stream: int = 0) -> float:
@@ -329,11 +348,12 @@ class Solver:
         return self.struct.n_steps
 
     def set_initial_state(self, p=None, u=None, s=None):
+        check_initial_state(self.P.n_cells, self.P.dim, self.n_dof, p, u, s)
         lks_set_initial_state(self.handle, p, u, s)
 
     def forward(self, gamma, stream=None) -> float:
         import torch
-        assert gamma.is_cuda and gamma.dtype == torch.float64 and gamma.is_contiguous()
+        check_design_tensor(gamma, self.P.n_design)
         st = torch.cuda.current_stream(gamma.device) if stream is None else stream
         self.forward_count += 1
         return lks_forward(self.handle, gamma.data_ptr(), st.cuda_stream)
@@ -359,7 +379,7 @@ class Solver:
 
     def sensitivity(self, out, stream=None):
         import torch
-        assert out.is_cuda and out.dtype == torch.float64 and out.is_contiguous()
+        check_design_tensor(out, self.P.n_design, "out")
         st = torch.cuda.current_stream(out.device) if stream is None else stream
         lks_sensitivity(self.handle, out.data_ptr(), st.cuda_stream)
         return out
@@ -368,6 +388,8 @@ class Solver:
         import torch
         st = torch.cuda.current_stream() if stream is None else stream
         out = np.zeros(self.P.n_design)
+        if np.size(gamma) != self.P.n_design:
+            raise ValueError(f"gamma: {np.size(gamma)} values, expected {self.P.n_design}")
         J = lks_gradient_host(self.handle, np.ascontiguousarray(gamma, dtype=np.float64), out, st.cuda_stream)
         return J, out
 
@@ -382,7 +404,9 @@ class Solver:
 
     def constraint(self, gamma, dG=None, stream=None) -> float:
         import torch
-        assert gamma.is_cuda and gamma.dtype == torch.float64 and gamma.is_contiguous()
+        check_design_tensor(gamma, self.P.n_design)
+        if dG is not None:
+            check_design_tensor(dG, self.P.n_design, "dG")
         st = torch.cuda.current_stream(gamma.device) if stream is None else stream
         return lks_constraint(self.handle, gamma.data_ptr(), 0 if dG is None else dG.data_ptr(), st.cuda_stream)
 

@@ -1,6 +1,7 @@
-"""Host logic of the autograd wrapper, with a stand-in solver (no GPU): the backward seeds the
-reverse sweep with the incoming gradient and returns the sensitivity in gamma's shape and dtype,
-and a backward that comes after a later forward on the same solver raises."""
+"""Host logic of the Python layer (no GPU). The autograd wrapper, with a stand-in solver: the
+backward seeds the reverse sweep with the incoming gradient and returns the sensitivity in gamma's
+shape and dtype, and a backward that comes after a later forward on the same solver raises. The
+binding's size checks on host arrays the library reads by the problem's sizes."""
 from __future__ import annotations
 
 import numpy as np
@@ -58,3 +59,22 @@ def test_backward_after_a_later_forward_raises():
         J1.backward()
     J2.backward()
     np.testing.assert_array_equal(g2.grad.numpy(), np.arange(1.0, 7.0))
+
+
+def test_initial_state_sizes_are_checked_before_the_library_reads_them():
+    from paper_2601_18272_gb300.lks import check_initial_state
+    N, dim, ndof = 12, 2, 8
+    check_initial_state(N, dim, ndof, np.zeros(N), np.zeros((dim, N)), np.zeros(ndof))
+    check_initial_state(N, dim, ndof)  # all defaults
+    for bad in (dict(p=np.zeros(N - 1)), dict(u=np.zeros(N)), dict(s=np.zeros(ndof + 1))):
+        with pytest.raises(ValueError):
+            check_initial_state(N, dim, ndof, **bad)
+
+
+def test_design_tensors_are_checked_before_the_library_touches_them():
+    import torch
+    from paper_2601_18272_gb300.lks import check_design_tensor
+    with pytest.raises(TypeError):
+        check_design_tensor(torch.zeros(6, dtype=torch.float64), 6)  # host memory
+    with pytest.raises(TypeError):
+        check_design_tensor(np.zeros(6), 6)

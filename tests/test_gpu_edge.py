@@ -9,7 +9,7 @@ import pytest
 
 from oracle import oracle as O
 from tests.problems import BC_INFLOW_OUTFLOW, BC_WALL, body2d, body3d, perturbed_state
-from workloads import CKPT_STORE_ALL, CKPT_UNIFORM, gamma_2d
+from workloads import CKPT_BINOMIAL, CKPT_STORE_ALL, CKPT_UNIFORM, gamma_2d
 
 pytestmark = pytest.mark.gpu
 
@@ -131,3 +131,25 @@ def test_call_order_rules():
         assert np.array_equal(S.initial_adjoint()[0], lp)
     finally:
         S.close()
+
+
+@pytest.mark.parametrize("policy", [dict(ckpt_policy=CKPT_UNIFORM, ckpt_every=3), dict(ckpt_policy=CKPT_BINOMIAL, ckpt_every=2)],
+                         ids=["uniform", "binomial"])
+def test_final_state_of_a_ragged_checkpointed_march(policy):
+    """7 steps with checkpoints every 3 (a short last segment) or 2 binomial snapshots: the final
+    state read back equals the store-all forward's, bit for bit (the same kernels in the same order)."""
+    import torch
+    from paper_2601_18272_gb300.lks import Solver
+    P, g = body2d(nt=7)
+    p0, u0, s0 = perturbed_state(P)
+    out = []
+    for kw in (dict(ckpt_policy=CKPT_STORE_ALL), policy):
+        S = Solver(P, precision=64, **kw)
+        try:
+            S.set_initial_state(p0, u0, s0)
+            S.forward(torch.tensor(g, dtype=torch.float64, device="cuda"))
+            out.append(S.state())
+        finally:
+            S.close()
+    np.testing.assert_array_equal(out[1][0], out[0][0])
+    np.testing.assert_array_equal(out[1][1], out[0][1])
