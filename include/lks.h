@@ -150,8 +150,11 @@ LKS_API long long lks_binomial_plan(int n_steps, int snapshots, int* ops, long l
  * s [lks_dof_count] are host arrays (copied). Any pointer may be NULL to keep the default: p = 0,
  * u = (u_in, 0, 0), body at rest at body_centre (R = identity with free rotation). The last
  * forward and its adjoints become invalid (the reverse sweep restarts from the initial state), so
- * lks_adjoint needs a new lks_forward. Errors: LKS_ERR_ARG; LKS_ERR_UNSUPPORTED if s starts the body rotated but the workspace was
- * sized for an axis-aligned box (see lks_create); LKS_ERR_CUDA. */
+ * lks_adjoint needs a new lks_forward.
+ * Errors: LKS_ERR_ARG; LKS_ERR_NONFINITE if a given array holds a NaN or an infinity (checked on
+ * the host before anything is copied: the previous state and results stay); LKS_ERR_UNSUPPORTED
+ * if s starts the body rotated but the workspace was sized for an axis-aligned box (see
+ * lks_create); LKS_ERR_CUDA. */
 LKS_API int lks_set_initial_state(lks_handle* h, const double* p_host, const double* u_host, const double* s_host);
 
 /* Forward march over n_steps (Algorithm 1, state loop) for the design field gamma_dev

@@ -876,6 +876,14 @@ int lks_create(const lks_problem* P, lks_handle** out) {
 int lks_set_initial_state(lks_handle* h, const double* p, const double* u, const double* s) {
   if (!h) return LKS_ERR_ARG;
   const Geo& g = h->g;
+  // checked on the host before any device work: a NaN or an infinity is refused, not marched
+  auto finite = [](const double* a, long long n) {
+    for (long long i = 0; i < n; ++i)
+      if (!std::isfinite(a[i])) return false;
+    return true;
+  };
+  if ((p && !finite(p, g.N)) || (u && !finite(u, (long long)g.dim * g.N)) || (s && !finite(s, g.ns)))
+    return LKS_ERR_NONFINITE;
   int r = set_default_initial_state(h);
   if (r != LKS_OK) return r;
   if (p) CK(cudaMemcpy(h->init_p, p, (size_t)g.N * sizeof(double), cudaMemcpyHostToDevice));

@@ -1,7 +1,8 @@
 """Edge cases of the CUDA path against the oracle: the shortest march (one step), an all-void and an
 all-solid design, a non-square design grid on a ragged analysis grid, a checkpoint interval longer
-than the march, the empty march, which the library rejects, and the order of the calls: what needs the
-exact adjoint refuses the paper-form one, and a new initial state voids the last forward."""
+than the march, the final state of ragged checkpointed marches, the empty march and a non-finite
+initial state, which the library rejects, and the order of the calls: what needs the exact adjoint
+refuses the paper-form one, and a new initial state voids the last forward."""
 from __future__ import annotations
 
 import numpy as np
@@ -153,3 +154,28 @@ def test_final_state_of_a_ragged_checkpointed_march(policy):
             S.close()
     np.testing.assert_array_equal(out[1][0], out[0][0])
     np.testing.assert_array_equal(out[1][1], out[0][1])
+
+
+def test_nonfinite_initial_state_is_refused():
+    """A NaN or an infinity in a host-built initial state is refused on the host before any device
+    work (LKS_ERR_NONFINITE); the last forward and the handle stay usable."""
+    import torch
+    from paper_2601_18272_gb300.lks import LksError, Solver
+    P, g = body2d(nt=2)
+    p0, u0, s0 = perturbed_state(P)
+    S = Solver(P, precision=64, ckpt_policy=CKPT_STORE_ALL)
+    try:
+        gam = torch.tensor(g, dtype=torch.float64, device="cuda")
+        S.set_initial_state(p0, u0, s0)
+        J = S.forward(gam)
+        state = S.state()
+        for name, src, bad in (("p", p0, np.nan), ("u", u0, np.inf), ("s", s0, -np.inf)):
+            arr = np.array(src, dtype=np.float64)
+            arr.flat[3] = bad
+            with pytest.raises(LksError, match="LKS_ERR_NONFINITE"):
+                S.set_initial_state(**{name: arr})
+        np.testing.assert_array_equal(S.state()[0], state[0])
+        S.set_initial_state(p0, u0, s0)
+        assert S.forward(gam) == J
+    finally:
+        S.close()
