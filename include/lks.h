@@ -59,7 +59,7 @@ typedef enum lks_status {
   LKS_ERR_NONFINITE = 6,    /* a non-finite force, torque or state was produced */
   LKS_ERR_ORDER = 7,        /* adjoint or sensitivity requested before a forward / adjoint */
   LKS_ERR_CUDA = 8,         /* a CUDA runtime call failed */
-  LKS_ERR_UNSUPPORTED = 9   /* valid but not supported by this build (e.g. grid/tile shape) */
+  LKS_ERR_UNSUPPORTED = 9   /* valid but not supported by the library (e.g. grid/tile shape) */
 } lks_status;
 
 enum { LKS_D2Q9 = 9, LKS_D3Q15 = 15 };                   /* velocity sets (Sec. 2.2) */
