@@ -117,22 +117,30 @@ def _peaks():
 
 
 # Algorithmic bytes per launch of each kernel family. N = analysis cells, box_cells = body-box
-# cells, ND = design points, esz = bytes per field value.
-def _alg_bytes(family: str, P, box_cells: int, esz: int) -> float:
+# cells, ND = design points, esz = bytes per field value, K = N_itr (the persistent families
+# "couple" and "adj_body" run all K iterations of a step in one launch).
+def _alg_bytes(family: str, P, box_cells: int, esz: int, persistent: bool = True) -> float:
     N, ND = P.n_cells, P.n_design
-    d = P.dim
+    d, K = P.dim, P.n_itr
     if family == "stencil_fwd":
         return 2 * (d + 1) * esz * N  # read p, u; write p*, u*
     if family == "stencil_adj":
         return (3 * d + 2) * esz * N  # read the adjoint (d+1 planes) and u(t-1) (d planes); write d+1 planes
     if family == "couple":
-        return 2 * esz * box_cells + 4 * ND  # read u* in the box (+ kappa^ref)
+        per_iter = d * esz * box_cells + 4 * ND  # read u* in the box (+ kappa^ref)
+        if persistent:  # K iterations, then u(t) and the stored u* written once
+            return K * per_iter + 2 * d * esz * box_cells
+        return per_iter
     if family == "recompute":
-        return 6 * esz * box_cells + 4 * ND  # read u*, write u and the stored u*
+        return 3 * d * esz * box_cells + 4 * ND  # read u*, write u and the stored u*
+    cell = (5 * d + 1) * esz * box_cells      # read stored u*, acc r/w, scratch write (2d+1 planes)
+    design = (2 * d + 1) * esz * box_cells + 20 * ND  # read scratch once, dJ/dkappa^ref r/w + kappa^ref
     if family == "adj_cell":
-        return 11 * esz * box_cells   # read stored u*, acc r/w, scratch write (5 planes)
+        return cell
     if family == "adj_design":
-        return 5 * esz * box_cells + 20 * ND  # read scratch once, dJ/dkappa^ref r/w + kappa^ref
+        return design
+    if family == "adj_body":
+        return K * (cell + design)
     if family == "alks_stencil":
         # the paper's adjoint equilibrium and gather. 2D, one tiled pass: read p~, u~, s~
         # (1 + d + d(d+1)/2 planes) and u (d), write the star moments. 3D, two passes: read the
@@ -154,6 +162,7 @@ def _traffic(workload: str, family: str):
 
 
 def _box_cells(P) -> int:
+    """Body-box cells of a 2D problem whose body may rotate (circumscribed box, as the library sizes it)."""
     import math
     s = 1 if P.weight_kind == 1 else 2
     half = [(P.ndx - 1) / 2.0, (P.ndy - 1) / 2.0]
@@ -161,6 +170,18 @@ def _box_cells(P) -> int:
     hb = math.ceil(r - 1e-12)
     B = 2 * hb + 2 * s + 2 + 2
     return B * B
+
+
+def _handle_box_cells(solver, P) -> int:
+    """Body-box cells of the handle's workspace (lks_support_sets reports the box it uses)."""
+    from paper_2601_18272_gb300 import lks
+    _, B, _ = lks.lks_support_sets(solver.handle, _initial_dofs(P))
+    return int(np.prod(B))
+
+
+def _initial_dofs(P):
+    from workloads import initial_state
+    return initial_state(P)[2]
 
 
 def _fluid_problem(dim: int, n: tuple, name: str, n_steps: int = 20, every: int = 10):
@@ -186,8 +207,8 @@ def _family_times(solver, run):
     run()
     torch.cuda.synchronize()
     fams = {f: lks.lks_kernel_time(solver.handle, f)
-            for f in ("stencil_fwd", "couple", "recompute", "adj_cell", "adj_design", "stencil_adj", "alks_body",
-                      "alks_stencil")}
+            for f in ("stencil_fwd", "couple", "recompute", "adj_cell", "adj_design", "adj_body", "stencil_adj",
+                      "alks_body", "alks_stencil")}
     fams = {f: v for f, v in fams.items() if v[1] > 0}
     lks.lks_set_kernel_timing(solver.handle, False)
     return fams

@@ -59,7 +59,9 @@ typedef enum lks_status {
   LKS_ERR_NONFINITE = 6,    /* a non-finite force, torque or state was produced */
   LKS_ERR_ORDER = 7,        /* adjoint or sensitivity requested before a forward / adjoint */
   LKS_ERR_CUDA = 8,         /* a CUDA runtime call failed */
-  LKS_ERR_UNSUPPORTED = 9   /* valid but not supported by the library (e.g. grid/tile shape) */
+  LKS_ERR_UNSUPPORTED = 9,  /* valid but not supported by the library (e.g. grid/tile shape) */
+  LKS_ERR_TIMEOUT = 10      /* a grid barrier of the persistent coupling kernels waited longer than one
+                             * second; the kernels returned early and the results of the call are void */
 } lks_status;
 
 enum { LKS_D2Q9 = 9, LKS_D3Q15 = 15 };                   /* velocity sets (Sec. 2.2) */
@@ -160,11 +162,15 @@ LKS_API int lks_set_initial_state(lks_handle* h, const double* p_host, const dou
 /* Forward march over n_steps (Algorithm 1, state loop) for the design field gamma_dev
  * [ndx*ndy*ndz] (device, values in [0,1]). Stores the DOF history and the checkpoints the
  * adjoint needs. Synchronises the stream once to return J (host scalar).
- * Errors: LKS_ERR_ARG, LKS_ERR_BODY_OUTSIDE, LKS_ERR_NONFINITE, LKS_ERR_CUDA. */
+ * Errors: LKS_ERR_ARG, LKS_ERR_BODY_OUTSIDE, LKS_ERR_CUDA; LKS_ERR_NONFINITE if a force, torque or
+ * DOF became non-finite, or if gamma_dev holds a NaN or an infinity (found on the device; those
+ * points take part as void, kappa^ref = 0, so nothing non-finite enters the march). */
 LKS_API int lks_forward(lks_handle* h, const double* gamma_dev, double* J_host, void* stream);
 
-/* Reverse sweep (Algorithm 1, adjoint loop) seeded with dJ = seed. Enqueued on the stream,
- * no synchronisation. Requires a prior lks_forward (else LKS_ERR_ORDER). */
+/* Reverse sweep (Algorithm 1, adjoint loop) seeded with dJ = seed. Enqueued on the stream; with the
+ * persistent coupling kernels (lks_uses_persistent_coupling) it then synchronises the stream once to
+ * read the device status word. Requires a prior lks_forward (else LKS_ERR_ORDER).
+ * Errors: LKS_ERR_TIMEOUT, LKS_ERR_CUDA. */
 LKS_API int lks_adjoint(lks_handle* h, double seed, void* stream);
 
 /* Continuation step (Sec. 3.3): the convexity parameter q of Eq. brinkman_coefficient and the
@@ -234,33 +240,65 @@ LKS_API int lks_get_state(lks_handle* h, double* p_host, double* u_host);
  * lks_adjoint of the last forward; lks_adjoint_alks does not count). */
 LKS_API int lks_get_initial_adjoint(lks_handle* h, double* lam_p_host, double* lam_u_host, double* lam_s_host);
 
+/* For tests of the bit-exact integer indexing of the spread (Eqs. kappa_mapping, us_mapping,
+ * weight_function): for the DOF vector s_host [lks_dof_count] (host), the body box a march starting
+ * from s would use, box_host [6] = (unwrapped origin x, y, z; extent x, y, z) in cells, and, if
+ * stats_host is not NULL, for each box cell (x fastest) the design points the coupling's gather
+ * accepts (|x_n - x^ref_m| below the kernel's half-width on every axis, m in the design domain):
+ * stats_host [box cells][5] = (count, least linear design index or -1, largest index, sum of the
+ * indices, sum of their squares), capacity in values (at least 5 * box cells, else LKS_ERR_ARG).
+ * The acceptance is decided in the field precision of the handle. Synchronous (legacy default
+ * stream; allocates and frees a small device buffer). Errors: LKS_ERR_NONFINITE (s not finite),
+ * LKS_ERR_UNSUPPORTED (s rotated but the workspace holds an axis-aligned box), LKS_ERR_CUDA. */
+LKS_API int lks_support_sets(lks_handle* h, const double* s_host, int* box_host, long long* stats_host,
+                             size_t capacity);
+
+/* Test hook of the bounded grid barriers: skip != 0 makes the first CTA of every persistent coupling
+ * kernel skip its barrier arrivals, so the other CTAs' waits run out (after one second) and the
+ * forward or adjoint returns LKS_ERR_TIMEOUT; skip = 0 restores normal operation. Synchronises the
+ * device. Errors: LKS_ERR_ARG, LKS_ERR_CUDA. */
+LKS_API int lks_debug_sync_skip(lks_handle* h, int skip);
+
+/* How the handle runs each step's N_itr coupling iterations (Sec. 3.1) and their reverse: mode 1
+ * (the default) as one persistent cooperative launch per step when the device holds its grid, mode 0
+ * as one launch per iteration (with the finish kernels), mode -1 only asks. Returns 1 if the
+ * persistent kernels are in use after the call, 0 if not, or -status on error (LKS_ERR_ARG,
+ * LKS_ERR_CUDA). Changing the mode synchronises the device; results agree to rounding (the per-CTA
+ * partial sums are grouped differently). */
+LKS_API int lks_persistent_coupling(lks_handle* h, int mode);
+
 /* Number of kernels this handle has launched (graph nodes counted per replay). */
 LKS_API long long lks_launch_count(const lks_handle* h);
 
 /* Kernel timing for the benchmark. enable = 1 runs later calls without CUDA graphs and brackets
  * every launch of the named kernel family with CUDA events on the launching stream.
  * lks_kernel_time returns the summed milliseconds and the launch count for the family
- * ("stencil_fwd", "stencil_adj", "couple", "adj_cell", "adj_design", "recompute", and for
- * lks_adjoint_alks "alks_body", "alks_stencil"); the coupling and design-side families include
- * their one-CTA finish kernels. */
+ * ("stencil_fwd", "stencil_adj", "couple", "adj_cell", "adj_design", "recompute", "adj_body" (the
+ * persistent reverse coupling), and for lks_adjoint_alks "alks_body", "alks_stencil"); the coupling
+ * and design-side families include their one-CTA finish kernels. */
 LKS_API int lks_set_kernel_timing(lks_handle* h, int enable);
 LKS_API int lks_kernel_time(lks_handle* h, const char* family, double* ms_total, long long* launches);
 
 /* One time step of the march (LKS predictor, boundary values, N_itr coupling iterations) that
  * allocates no device memory. The paper has no counterpart: this is an interface for callers that
- * cannot allocate -- code inside a relaxed-mode CUDA graph capture, real-time loops with memory
- * fixed up front, frameworks that forbid libraries their own cudaMalloc. Its scratch is one fixed
- * device array (about 0.7 MB) that every GPU loading the library holds until exit.
- *   problem   : as for lks_create; dim 2 and LKS_FP64 only (else LKS_ERR_UNSUPPORTED); at most
- *               65536 design points, n_itr <= 16 and 4096 CTAs per reduction (else LKS_ERR_BUDGET)
- *   gamma_dev : design field [ndx*ndy] (device, caller-owned)
+ * cannot let a library allocate -- real-time loops whose device memory is fixed up front, and
+ * frameworks that own every device allocation and forbid libraries their own cudaMalloc. Its
+ * scratch is one fixed device array (about 0.7 MB) that every GPU loading the library holds until
+ * exit.
+ *   problem   : checked by the same rules as lks_create (same errors), and the body box derived the
+ *               same way; dim 2, LKS_FP64 and no design chain (filter_radius 0, proj_beta 0,
+ *               cyclic_order 1) only, else LKS_ERR_UNSUPPORTED; at most 65536 design points,
+ *               n_itr <= 16 and 4096 CTAs per reduction, else LKS_ERR_BUDGET
+ *   gamma_dev : design field [ndx*ndy] (device, caller-owned), used as gamma-bar directly
  *   state_dev : two state slots [2][3][nx*ny] doubles (device, caller-owned): step t reads slot
  *               (t-1) mod 2 and writes p*, u(t) into slot t mod 2
  *   t         : step index >= 1 (only its parity matters)
- *   s_host    : DOF vector [8] (host): s(t-1) in, s(t) out
- * The first call on a device looks up the scratch array's address with that device current; make
- * it before any stream capture. All calls share the array and each clears what must start at
- * zero; calls that overlap on the GPU race on it. Synchronises the stream before returning. */
+ *   s_host    : DOF vector [8] (host): s(t-1) in, s(t) out; LKS_ERR_NONFINITE if it holds a NaN
+ *               or an infinity
+ * The first call on a device looks up the scratch array's address with that device current. All
+ * calls share the array and each clears what must start at zero; calls that overlap on the GPU
+ * race on it, so serialise them. The call waits for the stream (it copies s(t) to the host) before
+ * it returns. */
 LKS_API int lks_step_noalloc(const lks_problem* problem, const double* gamma_dev, double* state_dev, int t,
                              double* s_host, void* stream);
 

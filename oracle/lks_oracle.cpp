@@ -1945,6 +1945,41 @@ int oracle_spread(const OracleProblem* P, const double* gamma, const double* s, 
   return C.err;
 }
 
+// Index sets of the spread at the DOF vector s (Eqs. kappa_mapping, weight_function): for every
+// analysis node n, the design points m of the design domain whose support window holds n, i.e.
+// |x_n - x^ref_m| < support on every axis, summarised as stats [N][5] = (count, least index or -1,
+// largest index, sum of the indices, sum of their squares). The windows are those of the scatter
+// per design point above.
+int oracle_support_sets(const OracleProblem* P, const double* s, long long* stats) {
+  Ctx C;
+  if (!make_ctx(P, &C)) return ORC_ERR_ARG;
+  Geometry<double> geo;
+  transform(C, s, &geo);
+  for (size_t n = 0; n < C.N; ++n) {
+    stats[5 * n + 0] = 0;
+    stats[5 * n + 1] = -1;
+    stats[5 * n + 2] = -1;
+    stats[5 * n + 3] = 0;
+    stats[5 * n + 4] = 0;
+  }
+  std::vector<WindowNode> wn;
+  std::vector<double> wv, dwv;
+  for (size_t m = 0; m < C.ND; ++m) {
+    if (!C.dom[m]) continue;
+    window(C, &geo.xref[3 * m], &wn, &wv, &dwv);
+    const long long mm = (long long)m;
+    for (size_t q = 0; q < wn.size(); ++q) {
+      long long* st = &stats[5 * wn[q].n];
+      if (st[0] == 0 || mm < st[1]) st[1] = mm;
+      if (mm > st[2]) st[2] = mm;
+      st[0] += 1;
+      st[3] += mm;
+      st[4] += mm * mm;
+    }
+  }
+  return C.err;
+}
+
 // Interpolation of an analysis-grid velocity to the design points (Eq. u_mapping): uref [ND][3].
 int oracle_interp(const OracleProblem* P, const double* s, const double* u, double* uref) {
   Ctx C;

@@ -64,6 +64,7 @@ def lib():
         L.oracle_step.argtypes = [pp, dp, dp, dp, dp, dp, dp, dp, dp]
         L.oracle_spread.argtypes = [pp, dp, dp, dp, dp, ip]
         L.oracle_interp.argtypes = [pp, dp, dp, dp]
+        L.oracle_support_sets.argtypes = [pp, dp, ctypes.c_void_p]
         L.oracle_weight.argtypes = [ctypes.c_int, ctypes.c_double, dp]
         L.oracle_weight.restype = ctypes.c_double
         L.oracle_lattice.argtypes = [ctypes.c_int, ip, dp]
@@ -234,6 +235,15 @@ def spread(P, gamma, s):
                              cnt.ctypes.data_as(ctypes.POINTER(ctypes.c_int)))
     _check(rc)
     return k, us, cnt
+
+
+def support_sets(P, s):
+    """Per analysis node, the design points whose support window holds it under the DOF vector s:
+    int64 [N, 5] = (count, least index or -1, largest index, sum of indices, sum of squares)."""
+    rec = problem_record(P)
+    out = np.zeros((P.n_cells, 5), dtype=np.int64)
+    _check(lib().oracle_support_sets(ctypes.byref(rec), _ptr(_f64(s)), out.ctypes.data))
+    return out
 
 
 def interp(P, s, u):

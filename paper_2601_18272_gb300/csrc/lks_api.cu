@@ -25,9 +25,194 @@
 #include <vector>
 
 #include "../../include/lks.h"
+#include "lks_geo.h"
 #include "lks_kernels.h"
 
 using namespace lks;
+
+// ---- problem validation and constants (shared with the allocation-free step: lks_geo.h) ----
+namespace lks {
+
+namespace {
+// Symmetric (to rounding) positive definite 3x3 matrix, by its leading minors.
+bool spd3(const double* A) {
+  double mx = 0.0;
+  for (int i = 0; i < 9; ++i) {
+    if (!std::isfinite(A[i])) return false;
+    mx = std::max(mx, std::fabs(A[i]));
+  }
+  for (int i = 0; i < 3; ++i)
+    for (int j = 0; j < i; ++j)
+      if (std::fabs(A[3 * i + j] - A[3 * j + i]) > 1e-12 * mx) return false;
+  const double m2 = A[0] * A[4] - A[1] * A[3];
+  const double det = A[0] * (A[4] * A[8] - A[5] * A[7]) - A[1] * (A[3] * A[8] - A[5] * A[6]) +
+                     A[2] * (A[3] * A[7] - A[4] * A[6]);
+  return A[0] > 0.0 && m2 > 0.0 && det > 0.0;
+}
+
+// Inverse of a symmetric 3x3 matrix: row i is c_(i+1) x c_(i+2) / det for the columns c.
+void inverse_sym3(const double* A, double* inv) {
+  const double c[3][3] = {{A[0], A[3], A[6]}, {A[1], A[4], A[7]}, {A[2], A[5], A[8]}};
+  double rows[3][3];
+  for (int i = 0; i < 3; ++i) {
+    const double* u = c[(i + 1) % 3];
+    const double* v = c[(i + 2) % 3];
+    rows[i][0] = u[1] * v[2] - u[2] * v[1];
+    rows[i][1] = u[2] * v[0] - u[0] * v[2];
+    rows[i][2] = u[0] * v[1] - u[1] * v[0];
+  }
+  const double det = c[0][0] * rows[0][0] + c[0][1] * rows[0][1] + c[0][2] * rows[0][2];
+  for (int i = 0; i < 3; ++i)
+    for (int j = 0; j < 3; ++j) inv[3 * i + j] = rows[i][j] / det;
+}
+
+}  // namespace
+
+int validate_problem(const lks_problem* P) {
+  if (!P) return LKS_ERR_ARG;
+  if (P->dim != 2 && P->dim != 3) return LKS_ERR_ARG;
+  if (P->dim == 2 && (P->velocity_set != LKS_D2Q9 || P->nz != 1 || P->ndz != 1 || P->rot_axis != 2)) return LKS_ERR_ARG;
+  if (P->dim == 3 && P->velocity_set != LKS_D3Q15) return LKS_ERR_ARG;
+  if (P->nx < 4 || P->ny < 4 || (P->dim == 3 && P->nz < 4)) return LKS_ERR_ARG;
+  if (P->ndx < 1 || P->ndy < 1 || P->ndz < 1) return LKS_ERR_ARG;
+  if (P->rot_axis == LKS_ROT_FREE) {
+    if (P->dim != 3 || !spd3(P->inertia_tensor)) return LKS_ERR_ARG;
+  } else if (P->rot_axis < 0 || P->rot_axis > 2) {
+    return LKS_ERR_ARG;
+  }
+  if (!(P->design_radius >= 0.0) || !std::isfinite(P->design_radius)) return LKS_ERR_ARG;
+  if (!(P->filter_radius >= 0.0) || !std::isfinite(P->filter_radius)) return LKS_ERR_ARG;
+  if (!(P->proj_beta >= 0.0) || !std::isfinite(P->proj_beta)) return LKS_ERR_ARG;
+  if (P->proj_beta > 0.0 && !(P->proj_eta > 0.0 && P->proj_eta < 1.0)) return LKS_ERR_ARG;
+  if (P->cyclic_order != 1 && P->cyclic_order != 2 && P->cyclic_order != 4) return LKS_ERR_ARG;
+  if (P->cyclic_order > 1) {
+    if (P->rot_axis == LKS_ROT_FREE) return LKS_ERR_ARG;
+    const int nd[3] = {P->ndx, P->ndy, P->dim == 3 ? P->ndz : 1};
+    const int b = (P->rot_axis + 1) % 3, c = (P->rot_axis + 2) % 3;
+    if (P->cyclic_order == 4 && nd[b] != nd[c]) return LKS_ERR_ARG;
+  }
+  if (P->bc[0] != LKS_BC_PERIODIC && P->bc[0] != LKS_BC_INFLOW_OUTFLOW && P->bc[0] != LKS_BC_PRESSURE) return LKS_ERR_ARG;
+  for (int a = 1; a < 3; ++a)
+    if (P->bc[a] != LKS_BC_PERIODIC && P->bc[a] != LKS_BC_WALL) return LKS_ERR_ARG;
+  if (!(P->nu > 0.0)) return LKS_ERR_UNSTABLE;
+  if (P->n_steps < 1 || P->n_itr < 1) return LKS_ERR_ARG;
+  if (P->weight_kind != LKS_W_COS4 && P->weight_kind != LKS_W_BILINEAR) return LKS_ERR_ARG;
+  if (!(P->mass > 0.0) || !(P->inertia > 0.0)) return LKS_ERR_ARG;
+  if (P->field_precision != LKS_FP32 && P->field_precision != LKS_FP64) return LKS_ERR_ARG;
+  if (P->ckpt_policy != LKS_CKPT_STORE_ALL && P->ckpt_policy != LKS_CKPT_UNIFORM &&
+      P->ckpt_policy != LKS_CKPT_BINOMIAL)
+    return LKS_ERR_ARG;
+  if (P->ckpt_policy != LKS_CKPT_STORE_ALL && P->ckpt_every < 1) return LKS_ERR_ARG;
+  if (P->ckpt_policy == LKS_CKPT_BINOMIAL && P->ckpt_format != LKS_CKPT_NATIVE) return LKS_ERR_UNSUPPORTED;
+  if (P->ckpt_format != LKS_CKPT_NATIVE && P->ckpt_format != LKS_CKPT_BF16 && P->ckpt_format != LKS_CKPT_FP16)
+    return LKS_ERR_ARG;
+  // reduced-precision checkpoints: FP32 fields with uniform checkpoints
+  if (P->ckpt_format != LKS_CKPT_NATIVE && (P->ckpt_policy != LKS_CKPT_UNIFORM || P->field_precision != LKS_FP32))
+    return LKS_ERR_UNSUPPORTED;
+  // 3D: boundary pairs (x = 0,1 and nx-2,nx-1; y walls likewise) must share a stencil column
+  // (2D strips choose their width so that they always do)
+  if (P->dim == 3 && P->bc[0] != LKS_BC_PERIODIC && P->nx % kTileX == 1) return LKS_ERR_UNSUPPORTED;
+  if (P->dim == 3 && P->bc[1] == LKS_BC_WALL && P->ny % kTileY3 == 1) return LKS_ERR_UNSUPPORTED;
+  return LKS_OK;
+}
+
+
+void setup_box(Geo* gp, double design_radius, bool rotated) {
+  Geo& g = *gp;
+  double half[3] = {0, 0, 0};
+  for (int a = 0; a < g.dim; ++a) half[a] = (g.nd[a] - 1) / 2.0;
+  if (rotated && g.ax == AX_FREE) {
+    const double r = std::sqrt(half[0] * half[0] + half[1] * half[1] + half[2] * half[2]);
+    half[0] = half[1] = half[2] = r;
+  } else if (rotated) {
+    const double r = std::sqrt(half[g.axb] * half[g.axb] + half[g.axc] * half[g.axc]);
+    half[g.axb] = half[g.axc] = r;
+  }
+  if (design_radius > 0.0)
+    for (int a = 0; a < g.dim; ++a) half[a] = std::min(half[a], design_radius);
+  g.margin = 1;
+  g.box_cells = 1;
+  for (int a = 0; a < 3; ++a) {
+    if (a < g.dim) {
+      g.hb[a] = (int)std::ceil(half[a] - 1e-12);
+      g.B[a] = 2 * g.hb[a] + 2 * g.s + 2 * g.margin + 2;
+    } else {
+      g.hb[a] = 0;
+      g.B[a] = 1;
+    }
+    g.box_cells *= g.B[a];
+  }
+}
+
+bool box_fits(const Geo& g) {
+  for (int a = 0; a < g.dim; ++a)
+    if (g.bc[a] == LKS_BC_PERIODIC && g.B[a] > g.n[a]) return false;
+  return true;
+}
+
+int make_geometry(const lks_problem* P, Geo* gp, bool* rot_ok) {
+  Geo& g = *gp;
+  std::memset(&g, 0, sizeof(g));
+  g.dim = P->dim;
+  g.n[0] = P->nx;
+  g.n[1] = P->ny;
+  g.n[2] = P->dim == 3 ? P->nz : 1;
+  g.N = (long long)g.n[0] * g.n[1] * g.n[2];
+  for (int a = 0; a < 3; ++a) g.bc[a] = (a < g.dim) ? P->bc[a] : LKS_BC_PERIODIC;
+  g.nd[0] = P->ndx;
+  g.nd[1] = P->ndy;
+  g.nd[2] = P->dim == 3 ? P->ndz : 1;
+  g.ND = g.nd[0] * g.nd[1] * g.nd[2];
+  for (int a = 0; a < 3; ++a) {
+    g.xic[a] = (a < g.dim) ? (g.nd[a] - 1) / 2.0 : 0.0;
+    g.xicf[a] = (float)g.xic[a];
+  }
+  if (P->rot_axis == LKS_ROT_FREE) {
+    g.ax = AX_FREE;
+    g.axb = 0;  // (unused with free rotation)
+    g.axc = 1;
+    g.ns = kNdofFree;
+    inverse_sym3(P->inertia_tensor, g.Jinv);
+  } else {
+    g.ax = P->rot_axis;
+    g.axb = (g.ax + 1) % 3;
+    g.axc = (g.ax + 2) % 3;
+    g.ns = kNdofAxis;
+  }
+  g.frad = P->filter_radius;
+  g.pbeta = P->proj_beta;
+  g.peta = P->proj_eta;
+  g.cyc = P->cyclic_order;
+  // design domain 4 |r_m|^2 <= rad4, compared in integers (4 |r_m|^2 is an integer)
+  g.rad4 = INT_MAX;
+  if (P->design_radius > 0.0) {
+    const double q = std::floor(4.0 * P->design_radius * P->design_radius);
+    g.rad4 = q < (double)INT_MAX ? (int)q : INT_MAX;
+  }
+  g.dof_mask = (int)P->dof_mask;
+  g.wk = P->weight_kind;
+  g.s = (P->weight_kind == LKS_W_BILINEAR) ? 1 : 2;
+  g.K = P->n_itr;
+  g.A = 4.5 * (1.0 / 6.0 - P->nu);
+  g.A2 = (float)(2.0 * g.A);
+  g.u_in = P->u_in;
+  g.dp = P->dp;
+  g.mass = P->mass;
+  g.inertia = P->inertia;
+  g.inv_mass = 1.0 / P->mass;
+  g.inv_inertia = 1.0 / P->inertia;
+  // the rotated (largest) box; a body without the rotational DOF whose rotated box would not fit a
+  // periodic extent gets the axis-aligned box and may not start rotated
+  setup_box(&g, P->design_radius, true);
+  *rot_ok = box_fits(g);
+  if (!*rot_ok) {
+    setup_box(&g, P->design_radius, false);
+    if ((g.dof_mask & LKS_DOF_ROT) || !box_fits(g)) return LKS_ERR_UNSUPPORTED;
+  }
+  return LKS_OK;
+}
+
+}  // namespace lks
 
 namespace {
 
@@ -108,6 +293,7 @@ struct lks_handle {
   std::map<std::string, cudaGraphExec_t> graphs;
   std::map<std::string, int> graph_kernels;
   bool box_rot_ok = true;  // buffers hold the rotated box
+  bool coop_enabled = false;  // persistent coupling kernels when the device holds their grid
   // what the last calls left valid: a forward, an adjoint of it (either form: dkref), the exact
   // adjoint's lambda(0) and dJ/ds(0), the paper-form adjoint's moments
   bool fwd_done = false, adj_done = false, exact_done = false;
@@ -152,116 +338,6 @@ int dalloc(lks_handle* h, void** p, size_t bytes) {
       return r_;            \
     }                       \
   } while (0)
-
-// Box extent from the design grid: circumscribed in the rotation plane if the body may rotate
-// (in every axis with free rotation), and within the design domain's radius when one is set.
-void setup_box(lks_handle* h, bool rotated) {
-  Geo& g = h->g;
-  double half[3] = {0, 0, 0};
-  for (int a = 0; a < g.dim; ++a) half[a] = (g.nd[a] - 1) / 2.0;
-  if (rotated && g.ax == AX_FREE) {
-    const double r = std::sqrt(half[0] * half[0] + half[1] * half[1] + half[2] * half[2]);
-    half[0] = half[1] = half[2] = r;
-  } else if (rotated) {
-    const double r = std::sqrt(half[g.axb] * half[g.axb] + half[g.axc] * half[g.axc]);
-    half[g.axb] = half[g.axc] = r;
-  }
-  const double rad = h->P.design_radius;
-  if (rad > 0.0)
-    for (int a = 0; a < g.dim; ++a) half[a] = std::min(half[a], rad);
-  g.margin = 1;
-  g.box_cells = 1;
-  for (int a = 0; a < 3; ++a) {
-    if (a < g.dim) {
-      g.hb[a] = (int)std::ceil(half[a] - 1e-12);
-      g.B[a] = 2 * g.hb[a] + 2 * g.s + 2 * g.margin + 2;
-    } else {
-      g.hb[a] = 0;
-      g.B[a] = 1;
-    }
-    g.box_cells *= g.B[a];
-  }
-}
-
-// Symmetric (to rounding) positive definite 3x3 matrix, by its leading minors.
-bool spd3(const double* A) {
-  double mx = 0.0;
-  for (int i = 0; i < 9; ++i) {
-    if (!std::isfinite(A[i])) return false;
-    mx = std::max(mx, std::fabs(A[i]));
-  }
-  for (int i = 0; i < 3; ++i)
-    for (int j = 0; j < i; ++j)
-      if (std::fabs(A[3 * i + j] - A[3 * j + i]) > 1e-12 * mx) return false;
-  const double m2 = A[0] * A[4] - A[1] * A[3];
-  const double det = A[0] * (A[4] * A[8] - A[5] * A[7]) - A[1] * (A[3] * A[8] - A[5] * A[6]) +
-                     A[2] * (A[3] * A[7] - A[4] * A[6]);
-  return A[0] > 0.0 && m2 > 0.0 && det > 0.0;
-}
-
-// Inverse of a symmetric 3x3 matrix: row i is c_(i+1) x c_(i+2) / det for the columns c.
-void inverse_sym3(const double* A, double* inv) {
-  const double c[3][3] = {{A[0], A[3], A[6]}, {A[1], A[4], A[7]}, {A[2], A[5], A[8]}};
-  double rows[3][3];
-  for (int i = 0; i < 3; ++i) {
-    const double* u = c[(i + 1) % 3];
-    const double* v = c[(i + 2) % 3];
-    rows[i][0] = u[1] * v[2] - u[2] * v[1];
-    rows[i][1] = u[2] * v[0] - u[0] * v[2];
-    rows[i][2] = u[0] * v[1] - u[1] * v[0];
-  }
-  const double det = c[0][0] * rows[0][0] + c[0][1] * rows[0][1] + c[0][2] * rows[0][2];
-  for (int i = 0; i < 3; ++i)
-    for (int j = 0; j < 3; ++j) inv[3 * i + j] = rows[i][j] / det;
-}
-
-int validate(const lks_problem* P) {
-  if (!P) return LKS_ERR_ARG;
-  if (P->dim != 2 && P->dim != 3) return LKS_ERR_ARG;
-  if (P->dim == 2 && (P->velocity_set != LKS_D2Q9 || P->nz != 1 || P->ndz != 1 || P->rot_axis != 2)) return LKS_ERR_ARG;
-  if (P->dim == 3 && P->velocity_set != LKS_D3Q15) return LKS_ERR_ARG;
-  if (P->nx < 4 || P->ny < 4 || (P->dim == 3 && P->nz < 4)) return LKS_ERR_ARG;
-  if (P->ndx < 1 || P->ndy < 1 || P->ndz < 1) return LKS_ERR_ARG;
-  if (P->rot_axis == LKS_ROT_FREE) {
-    if (P->dim != 3 || !spd3(P->inertia_tensor)) return LKS_ERR_ARG;
-  } else if (P->rot_axis < 0 || P->rot_axis > 2) {
-    return LKS_ERR_ARG;
-  }
-  if (!(P->design_radius >= 0.0) || !std::isfinite(P->design_radius)) return LKS_ERR_ARG;
-  if (!(P->filter_radius >= 0.0) || !std::isfinite(P->filter_radius)) return LKS_ERR_ARG;
-  if (!(P->proj_beta >= 0.0) || !std::isfinite(P->proj_beta)) return LKS_ERR_ARG;
-  if (P->proj_beta > 0.0 && !(P->proj_eta > 0.0 && P->proj_eta < 1.0)) return LKS_ERR_ARG;
-  if (P->cyclic_order != 1 && P->cyclic_order != 2 && P->cyclic_order != 4) return LKS_ERR_ARG;
-  if (P->cyclic_order > 1) {
-    if (P->rot_axis == LKS_ROT_FREE) return LKS_ERR_ARG;
-    const int nd[3] = {P->ndx, P->ndy, P->dim == 3 ? P->ndz : 1};
-    const int b = (P->rot_axis + 1) % 3, c = (P->rot_axis + 2) % 3;
-    if (P->cyclic_order == 4 && nd[b] != nd[c]) return LKS_ERR_ARG;
-  }
-  if (P->bc[0] != LKS_BC_PERIODIC && P->bc[0] != LKS_BC_INFLOW_OUTFLOW && P->bc[0] != LKS_BC_PRESSURE) return LKS_ERR_ARG;
-  for (int a = 1; a < 3; ++a)
-    if (P->bc[a] != LKS_BC_PERIODIC && P->bc[a] != LKS_BC_WALL) return LKS_ERR_ARG;
-  if (!(P->nu > 0.0)) return LKS_ERR_UNSTABLE;
-  if (P->n_steps < 1 || P->n_itr < 1) return LKS_ERR_ARG;
-  if (P->weight_kind != LKS_W_COS4 && P->weight_kind != LKS_W_BILINEAR) return LKS_ERR_ARG;
-  if (!(P->mass > 0.0) || !(P->inertia > 0.0)) return LKS_ERR_ARG;
-  if (P->field_precision != LKS_FP32 && P->field_precision != LKS_FP64) return LKS_ERR_ARG;
-  if (P->ckpt_policy != LKS_CKPT_STORE_ALL && P->ckpt_policy != LKS_CKPT_UNIFORM &&
-      P->ckpt_policy != LKS_CKPT_BINOMIAL)
-    return LKS_ERR_ARG;
-  if (P->ckpt_policy != LKS_CKPT_STORE_ALL && P->ckpt_every < 1) return LKS_ERR_ARG;
-  if (P->ckpt_policy == LKS_CKPT_BINOMIAL && P->ckpt_format != LKS_CKPT_NATIVE) return LKS_ERR_UNSUPPORTED;
-  if (P->ckpt_format != LKS_CKPT_NATIVE && P->ckpt_format != LKS_CKPT_BF16 && P->ckpt_format != LKS_CKPT_FP16)
-    return LKS_ERR_ARG;
-  // reduced-precision checkpoints: FP32 fields with uniform checkpoints
-  if (P->ckpt_format != LKS_CKPT_NATIVE && (P->ckpt_policy != LKS_CKPT_UNIFORM || P->field_precision != LKS_FP32))
-    return LKS_ERR_UNSUPPORTED;
-  // 3D: boundary pairs (x = 0,1 and nx-2,nx-1; y walls likewise) must share a stencil column
-  // (2D strips choose their width so that they always do)
-  if (P->dim == 3 && P->bc[0] != LKS_BC_PERIODIC && P->nx % kTileX == 1) return LKS_ERR_UNSUPPORTED;
-  if (P->dim == 3 && P->bc[1] == LKS_BC_WALL && P->ny % kTileY3 == 1) return LKS_ERR_UNSUPPORTED;
-  return LKS_OK;
-}
 
 template <typename T>
 Slots<T> ring_slots(lks_handle* h) {
@@ -428,6 +504,13 @@ void enqueue_fwd_steps(lks_handle* h, Launcher& L, const Slots<T>& S, int nsteps
   T* bs = store_box ? (T*)h->boxstore : nullptr;
   for (int i = 0; i < nsteps; ++i) {
     L("stencil_fwd", [&](cudaStream_t s) { launch_stencil_fwd<T>(g, S, h->ctrl, i, s); });
+    if (g.coop_fwd > 0) {  // all N_itr iterations and the last EOM in one persistent launch
+      L("couple", [&](cudaStream_t s) {
+        launch_couple_coop<T>(g, S, h->ctrl, h->it, (const T*)h->kref, h->mom, h->partials, h->pstride, bs, h->nbox,
+                              i, s);
+      });
+      continue;
+    }
     for (int k = 1; k <= g.K; ++k)
       L.n("couple", couple_kernels(g), [&](cudaStream_t s) {
         launch_couple<T>(g, S, h->ctrl, h->it, (const T*)h->kref, h->mom, h->partials, h->pstride, k, bs, h->nbox, i,
@@ -463,6 +546,14 @@ void enqueue_adj_steps(lks_handle* h, Launcher& L, const Slots<T>& S, int nsteps
     return;
   }
   for (int i = 0; i < nsteps; ++i) {
+    if (g.coop_adj > 0) {  // the N_itr reverse iterations in one persistent launch
+      L("adj_body", [&](cudaStream_t s) {
+        launch_adj_coop<T>(g, h->ctrl, h->it, (const T*)h->kref, (const T*)h->boxstore, h->nbox, (T*)h->L,
+                           h->slot_elems, (T*)h->acc, (T*)h->scratch, h->dkref, h->partials, h->pstride, i, s);
+      });
+      L("stencil_adj", [&](cudaStream_t s) { launch_stencil_adj<T>(g, S, (T*)h->L, h->slot_elems, h->ctrl, i, s); });
+      continue;
+    }
     for (int k = g.K; k >= 1; --k) {
       L("adj_cell", [&](cudaStream_t s) {
         launch_adj_cell<T>(g, h->ctrl, h->it, (const T*)h->kref, (const T*)h->boxstore, h->nbox, (T*)h->L,
@@ -482,6 +573,7 @@ int forward_impl(lks_handle* h, cudaStream_t st) {
   const Geo& g = h->g;
   const int NT = h->P.n_steps;
   Launcher L0{h, st, false};
+  CK(cudaMemsetAsync(&h->ctrl->sync_bar, 0, sizeof(unsigned), st));  // a barrier that timed out leaves it set
   if (h->P.ckpt_policy == LKS_CKPT_BINOMIAL) {
     // march in pieces between the snapshot steps of the first descent, snapshotting each
     Slots<T> S = pp_slots<T>(h);
@@ -537,7 +629,8 @@ int forward_impl(lks_handle* h, cudaStream_t st) {
       }));
     }
   }
-  L0("couple", [&](cudaStream_t s) { launch_couple_last<T>(g, h->ctrl, h->it, h->mom, h->partials, h->pstride, NT, s); });
+  if (g.coop_fwd == 0)  // the persistent kernel runs the last EOM itself
+    L0("couple", [&](cudaStream_t s) { launch_couple_last<T>(g, h->ctrl, h->it, h->mom, h->partials, h->pstride, NT, s); });
   CK(cudaGetLastError());
   if (h->launch_error) return LKS_ERR_CUDA;
   return LKS_OK;
@@ -591,6 +684,7 @@ int adjoint_impl(lks_handle* h, double seed, cudaStream_t st) {
   const Geo& g = h->g;
   const int NT = h->P.n_steps;
   Launcher L0{h, st, false};
+  CK(cudaMemsetAsync(&h->ctrl->sync_bar, 0, sizeof(unsigned), st));
   if (h->alks_mode) {  // fluid multipliers zero at N_t + 1, terminal body multipliers
     CK(cudaMemsetAsync(h->al_A, 0, 2 * (size_t)h->al_astride * h->esz, st));
     L0("init", [&](cudaStream_t s) { launch_alks_init(g, h->ctrl, h->objw, seed, h->dkref, s); });
@@ -694,10 +788,9 @@ int allocate(lks_handle* h) {
   const long long bx = ((g.B[0] + kBoxCtaCellsX - 1) / kBoxCtaCellsX) * (long long)((g.B[1] + kBoxCtaCellsY - 1) / kBoxCtaCellsY) * g.B[2];
   const long long bd = ((long long)g.ND + kDesignPointsPerCta - 1) / kDesignPointsPerCta;
   const long long nblk = std::max(bx, bd) + 1;
-  // per-CTA partials: up to 18 values (design-point reverse with free rotation); the coupling's
-  // double-buffered halves hold up to 6 values each
-  TRY(dalloc(h, (void**)&h->partials, (size_t)nblk * 18 * sizeof(double)));
-  h->pstride = 6 * nblk;
+  // per-CTA partials: up to 18 values (design-point reverse with free rotation), double-buffered
+  TRY(dalloc(h, (void**)&h->partials, (size_t)nblk * 36 * sizeof(double)));
+  h->pstride = 18 * nblk;  // two halves of up to 18 values per CTA (nblk >= the box tiles >= persistent CTAs)
   TRY(dalloc(h, (void**)&h->init_p, (size_t)g.N * sizeof(double)));
   TRY(dalloc(h, (void**)&h->init_u, (size_t)D * g.N * sizeof(double)));
   TRY(dalloc(h, (void**)&h->init_s, kNdofFree * sizeof(double)));
@@ -732,15 +825,13 @@ int refresh_box(lks_handle* h) {
   const bool rotated = (h->g.dof_mask & LKS_DOF_ROT) || start_rotated;
   if (rotated && !h->box_rot_ok) return LKS_ERR_UNSUPPORTED;
   const int old[3] = {h->g.B[0], h->g.B[1], h->g.B[2]};
-  setup_box(h, rotated);
+  setup_box(&h->g, h->P.design_radius, rotated);
+  if (h->coop_enabled)
+    setup_coop(&h->g, h->prec == LKS_FP64);
+  else
+    h->g.coop_fwd = h->g.coop_adj = 0;
   if (old[0] != h->g.B[0] || old[1] != h->g.B[1] || old[2] != h->g.B[2]) clear_graphs(h);
   return LKS_OK;
-}
-
-bool box_fits(const Geo& g) {
-  for (int a = 0; a < g.dim; ++a)
-    if (g.bc[a] == LKS_BC_PERIODIC && g.B[a] > g.n[a]) return false;
-  return true;
 }
 
 }  // namespace
@@ -759,6 +850,7 @@ const char* lks_status_string(int s) {
     case LKS_ERR_ORDER: return "call order (forward before adjoint before sensitivity)";
     case LKS_ERR_CUDA: return "CUDA runtime error";
     case LKS_ERR_UNSUPPORTED: return "unsupported configuration";
+    case LKS_ERR_TIMEOUT: return "a grid barrier wait timed out";
     default: return "unknown status";
   }
 }
@@ -788,74 +880,20 @@ int lks_dof_count(const lks_problem* P) {
 int lks_create(const lks_problem* P, lks_handle** out) {
   if (!out) return LKS_ERR_ARG;
   *out = nullptr;
-  int v = validate(P);
+  int v = validate_problem(P);
   if (v != LKS_OK) return v;
   lks_handle* h = new (std::nothrow) lks_handle();
   if (!h) return LKS_ERR_OOM;
   h->P = *P;
   h->prec = P->field_precision;
   h->esz = (h->prec == LKS_FP64) ? 8 : 4;
-  Geo& g = h->g;
-  std::memset(&g, 0, sizeof(g));
-  g.dim = P->dim;
-  g.n[0] = P->nx;
-  g.n[1] = P->ny;
-  g.n[2] = P->dim == 3 ? P->nz : 1;
-  g.N = (long long)g.n[0] * g.n[1] * g.n[2];
-  for (int a = 0; a < 3; ++a) g.bc[a] = (a < g.dim) ? P->bc[a] : LKS_BC_PERIODIC;
-  g.nd[0] = P->ndx;
-  g.nd[1] = P->ndy;
-  g.nd[2] = P->dim == 3 ? P->ndz : 1;
-  g.ND = g.nd[0] * g.nd[1] * g.nd[2];
-  for (int a = 0; a < 3; ++a) {
-    g.xic[a] = (a < g.dim) ? (g.nd[a] - 1) / 2.0 : 0.0;
-    g.xicf[a] = (float)g.xic[a];
+  bool rot_ok = true;
+  if (make_geometry(P, &h->g, &rot_ok) != LKS_OK) {
+    delete h;
+    return LKS_ERR_UNSUPPORTED;
   }
-  if (P->rot_axis == LKS_ROT_FREE) {
-    g.ax = AX_FREE;
-    g.axb = 0;  // (unused with free rotation)
-    g.axc = 1;
-    g.ns = kNdofFree;
-    inverse_sym3(P->inertia_tensor, g.Jinv);
-  } else {
-    g.ax = P->rot_axis;
-    g.axb = (g.ax + 1) % 3;
-    g.axc = (g.ax + 2) % 3;
-    g.ns = kNdofAxis;
-  }
-  g.frad = P->filter_radius;
-  g.pbeta = P->proj_beta;
-  g.peta = P->proj_eta;
-  g.cyc = P->cyclic_order;
-  // design domain 4 |r_m|^2 <= rad4, compared in integers (4 |r_m|^2 is an integer)
-  g.rad4 = INT_MAX;
-  if (P->design_radius > 0.0) {
-    const double q = std::floor(4.0 * P->design_radius * P->design_radius);
-    g.rad4 = q < (double)INT_MAX ? (int)q : INT_MAX;
-  }
-  g.dof_mask = (int)P->dof_mask;
-  g.wk = P->weight_kind;
-  g.s = (P->weight_kind == LKS_W_BILINEAR) ? 1 : 2;
-  g.K = P->n_itr;
-  g.A = 4.5 * (1.0 / 6.0 - P->nu);
-  g.A2 = (float)(2.0 * g.A);
-  g.u_in = P->u_in;
-  g.dp = P->dp;
-  g.mass = P->mass;
-  g.inertia = P->inertia;
-  g.inv_mass = 1.0 / P->mass;
-  g.inv_inertia = 1.0 / P->inertia;
-  // Allocate for the rotated (largest) box; a body without the rotational DOF whose rotated box
-  // would not fit a periodic extent gets the axis-aligned box and may not start rotated.
-  setup_box(h, true);
-  h->box_rot_ok = box_fits(g);
-  if (!h->box_rot_ok) {
-    setup_box(h, false);
-    if ((g.dof_mask & LKS_DOF_ROT) || !box_fits(g)) {
-      delete h;
-      return LKS_ERR_UNSUPPORTED;
-    }
-  }
+  h->box_rot_ok = rot_ok;
+  const Geo& g = h->g;
   int r = (h->prec == LKS_FP64) ? allocate<double>(h) : allocate<float>(h);
   if (r == LKS_OK) r = set_default_initial_state(h);
   if (r == LKS_OK && cudaStreamCreateWithFlags(&h->cap, cudaStreamNonBlocking) != cudaSuccess) r = LKS_ERR_CUDA;
@@ -905,6 +943,7 @@ int lks_forward(lks_handle* h, const double* gamma_dev, double* J_host, void* st
   if ((const void*)gamma_dev != (const void*)h->gamma)
     CK(cudaMemcpyAsync(h->gamma, gamma_dev, (size_t)g.ND * sizeof(double), cudaMemcpyDeviceToDevice, st));
   Launcher L0{h, st, false};
+  CK(cudaMemsetAsync((char*)h->ctrl + offsetof(Ctrl, prep_status), 0, sizeof(int), st));
   // design chain gamma -> gamma-bar (Sec. 3.2, 4.2), then kappa^ref of gamma-bar
   L0.n("prep", 2, [&](cudaStream_t s) { launch_design_chain(g, h->gamma, h->cg1, h->cgtil, h->cgbar, h->cW, s); });
   if (h->prec == LKS_FP64)
@@ -922,9 +961,10 @@ int lks_forward(lks_handle* h, const double* gamma_dev, double* J_host, void* st
   double J = 0.0;
   for (int a = 0; a < g.ns; ++a) J += h->P.obj_weights[a] * last.s[a];
   if (J_host) *J_host = J;
+  if (c.status & ST_SYNC_TIMEOUT) return LKS_ERR_TIMEOUT;
   if (c.status & ST_BODY_OUTSIDE) return LKS_ERR_BODY_OUTSIDE;
   if (c.status & ST_BOX_OVERFLOW) return LKS_ERR_BODY_OUTSIDE;
-  if ((c.status & ST_NONFINITE) || !std::isfinite(J)) return LKS_ERR_NONFINITE;
+  if ((c.status & ST_NONFINITE) || (c.prep_status & ST_NONFINITE) || !std::isfinite(J)) return LKS_ERR_NONFINITE;
   h->fwd_done = true;
   return LKS_OK;
 }
@@ -936,6 +976,13 @@ int lks_adjoint(lks_handle* h, double seed, void* stream) {
   h->adj_done = h->exact_done = false;
   int r = (h->prec == LKS_FP64) ? adjoint_impl<double>(h, seed, st) : adjoint_impl<float>(h, seed, st);
   if (r != LKS_OK) return r;
+  if (h->g.coop_adj > 0) {  // a grid barrier that timed out is reported through the status word
+    int status = 0;
+    CK(cudaMemcpyAsync(&status, (const char*)h->ctrl + offsetof(Ctrl, status), sizeof(int), cudaMemcpyDeviceToHost,
+                       st));
+    CK(cudaStreamSynchronize(st));
+    if (status & ST_SYNC_TIMEOUT) return LKS_ERR_TIMEOUT;
+  }
   if (h->timing) {
     CK(cudaStreamSynchronize(st));
     collect_timers(h);
@@ -1150,6 +1197,68 @@ int lks_get_initial_adjoint(lks_handle* h, double* lp, double* lu, double* ls) {
     for (int a = 0; a < h->g.ns; ++a) ls[a] = c.lam_s0[a];
   }
   return LKS_OK;
+}
+
+int lks_support_sets(lks_handle* h, const double* s_host, int* box_host, long long* stats_host, size_t capacity) {
+  if (!h || !s_host || !box_host) return LKS_ERR_ARG;
+  Geo g = h->g;
+  for (int a = 0; a < g.ns; ++a)
+    if (!std::isfinite(s_host[a])) return LKS_ERR_NONFINITE;
+  for (int a = 0; a < 3; ++a)
+    if (std::fabs(s_host[a]) > 1e9) return LKS_ERR_ARG;
+  Dof d;
+  const bool free_rot = g.ax == AX_FREE;
+  for (int a = 0; a < kNdofFree; ++a) d.s[a] = (a < g.ns) ? s_host[a] : 0.0;
+  d.cs = free_rot ? 1.0 : std::cos(d.s[6]);
+  d.sn = free_rot ? 0.0 : std::sin(d.s[6]);
+  dof_views(&d, free_rot);
+  // the box a march starting from s would use (as lks_set_initial_state chooses it)
+  bool start_rotated = !free_rot && d.s[6] != 0.0;
+  if (free_rot)
+    for (int i = 0; i < 9; ++i) start_rotated = start_rotated || d.s[S_R + i] != ((i % 4 == 0) ? 1.0 : 0.0);
+  const bool rotated = (g.dof_mask & LKS_DOF_ROT) || start_rotated;
+  if (rotated && !h->box_rot_ok) return LKS_ERR_UNSUPPORTED;
+  setup_box(&g, h->P.design_radius, rotated);
+  for (int a = 0; a < 3; ++a) {
+    box_host[a] = (a < g.dim) ? d.xi[a] - g.hb[a] - g.s - g.margin : 0;
+    box_host[3 + a] = g.B[a];
+  }
+  if (!stats_host) return LKS_OK;
+  if (capacity < (size_t)(5 * g.box_cells)) return LKS_ERR_ARG;
+  long long* out = nullptr;
+  CK(cudaMalloc((void**)&out, sizeof(long long) * 5 * (size_t)g.box_cells));
+  if (h->prec == LKS_FP64)
+    launch_support_sets<double>(g, d, (const double*)h->kref, out, 0);
+  else
+    launch_support_sets<float>(g, d, (const float*)h->kref, out, 0);
+  cudaError_t e = cudaMemcpy(stats_host, out, sizeof(long long) * 5 * (size_t)g.box_cells, cudaMemcpyDeviceToHost);
+  cudaFree(out);
+  if (e != cudaSuccess) {
+    g_last_cuda_error = (int)e;
+    return LKS_ERR_CUDA;
+  }
+  h->launches += 1;
+  return LKS_OK;
+}
+
+int lks_debug_sync_skip(lks_handle* h, int skip) {
+  if (!h) return LKS_ERR_ARG;
+  const int v = skip ? 1 : 0;
+  CK(cudaDeviceSynchronize());
+  CK(cudaMemcpy((char*)h->ctrl + offsetof(Ctrl, sync_skip), &v, sizeof(int), cudaMemcpyHostToDevice));
+  return LKS_OK;
+}
+
+int lks_persistent_coupling(lks_handle* h, int mode) {
+  if (!h || mode < -1 || mode > 1) return -LKS_ERR_ARG;
+  if (mode >= 0 && (mode == 1) != h->coop_enabled) {
+    if (cudaDeviceSynchronize() != cudaSuccess) return -LKS_ERR_CUDA;
+    h->coop_enabled = mode == 1;
+    const int r = refresh_box(h);
+    if (r != LKS_OK) return -r;
+    clear_graphs(h);
+  }
+  return (h->g.coop_fwd > 0 && h->g.coop_adj > 0) ? 1 : 0;
 }
 
 long long lks_launch_count(const lks_handle* h) { return h ? h->launches : 0; }

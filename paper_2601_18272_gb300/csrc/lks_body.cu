@@ -30,6 +30,8 @@
 // most kFusedFinishMaxParts CTAs, and a one-CTA k_couple_pre does it once above that; in the
 // reverse the one-CTA k_design_finish does it after the design-point kernel, whose grid is capped
 // (design_ctas) so that it sums few partials.
+#include <climits>
+
 #include "lks_body_common.cuh"
 
 namespace lks {
@@ -487,7 +489,10 @@ __global__ void __launch_bounds__(256) k_prep(Geo g, const double* __restrict__ 
     const int i[3] = {m % g.nd[0], (m / g.nd[0]) % g.nd[1], m / (g.nd[0] * g.nd[1])};
     const bool dom = dsq(i[0], g.nd[0]) + dsq(i[1], g.nd[1]) + dsq(i[2], g.nd[2]) <= g.rad4;
     const double gm = gamma[m];
-    const T k = dom ? (T)(kmax * q * gm / ((1.0 - gm) + q)) : T(0);
+    // a non-finite design value is reported through the status word and enters the march as void
+    const bool fin = isfinite(gm);
+    if (!fin) atomicOr(&ctrl->prep_status, ST_NONFINITE);
+    const T k = (dom && fin) ? (T)(kmax * q * gm / ((1.0 - gm) + q)) : T(0);
     kref[m] = k;
     const double kd = (double)k;
     double r[3];
@@ -860,10 +865,357 @@ __global__ void k_ckpt_pack(Geo g, Slots<T> S, T* ckpt, long long cstride, int e
     dst[i] = src[i];
 }
 
+// ---- persistent (cooperative) coupling ---------------------------------------------------------
+//
+// One launch per time step runs all N_itr coupling iterations (forward) or their reverse. Its CTAs
+// are co-resident (cooperative launch) and stride over the box tiles in a fixed assignment, so
+// every cell is handled by the same thread in every iteration; they meet at a grid barrier after
+// each iteration's per-CTA partial sums, after which every CTA sums the partials in the same fixed
+// order and runs the same FP64 EOM (or its reverse) on thread 0, so all CTAs hold the same iterate
+// without a second barrier. The partials are double-buffered by the parity of the iteration: a
+// buffer is rewritten only two barriers after it was read.
+
+constexpr unsigned long long kSyncTimeoutNs = 1000000000ull;  // one second
+
+__device__ __forceinline__ unsigned long long globaltimer_ns() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+__device__ __forceinline__ unsigned ld_acquire_gpu(const unsigned* p) {
+  unsigned v;
+  asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+
+// Grid barrier on one 32-bit word, sense-reversing: CTA 0 adds 2^31 - (G - 1) and every other CTA
+// adds 1, so the top bit flips exactly when the last of the G CTAs arrives and the low bits are
+// zero again for the next barrier. Each waiting CTA polls with acquire loads; the fence before the
+// arrival publishes the CTA's writes (ordered before it by the block barrier). Every wait is
+// bounded: after kSyncTimeoutNs, or as soon as another CTA has given up, the CTA sets
+// ST_SYNC_TIMEOUT and the call returns false, on which the kernel must return. skip (a test hook)
+// makes CTA 0 not arrive, so that the other CTAs' waits run out.
+__device__ __forceinline__ bool grid_sync(unsigned* bar, int* status, bool skip) {
+  __shared__ int sync_ok;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    const unsigned G = gridDim.x * gridDim.y * gridDim.z;
+    const bool first = block_linear() == 0;
+    const unsigned inc = first ? 0x80000000u - (G - 1u) : 1u;
+    __threadfence();
+    const unsigned old = (first && skip) ? ld_acquire_gpu(bar) : atomicAdd(bar, inc);
+    const unsigned long long t0 = globaltimer_ns();
+    int ok = 1;
+    while (((ld_acquire_gpu(bar) ^ old) & 0x80000000u) == 0u) {
+      if (*(volatile int*)status & ST_SYNC_TIMEOUT) {
+        ok = 0;
+        break;
+      }
+      if (globaltimer_ns() - t0 > kSyncTimeoutNs) {
+        atomicOr(status, ST_SYNC_TIMEOUT);
+        ok = 0;
+        break;
+      }
+      __nanosleep(20);
+    }
+    __threadfence();
+    sync_ok = ok;
+  }
+  __syncthreads();
+  return sync_ok != 0;
+}
+
+// Forward: the N_itr coupling iterations of step t and the EOM of the last one.
+template <typename T, int D, int AX>
+__global__ void __launch_bounds__(BoxCta<D>::threads, BoxCta<D>::min_blocks)
+    k_couple_coop(Geo g, Slots<T> S, Ctrl* ctrl, Dof* it, const T* __restrict__ kref, const Moments* __restrict__ mom,
+                  void* partials, long long pstride, T* __restrict__ boxstore, int nbox, int di) {
+  using PT = typename Partial<T>::type;
+  constexpr int NV = nv_couple<AX>();
+  constexpr int DW = (int)(sizeof(Dof) / sizeof(double));
+  __shared__ double red[32 * NV];
+  __shared__ Dof sd[3];  // s(t-1), the current iterate s^(k-1), the next iterate
+  if (*(volatile int*)&ctrl->status & ST_SYNC_TIMEOUT) return;  // an earlier launch gave up
+  const int t = ctrl->t0 + di, base = ctrl->base, K = g.K;
+  const bool skip = ctrl->sync_skip != 0;
+  Dof* row = it + (long long)(t - 1) * (K + 1);
+  double* sdw = reinterpret_cast<double*>(sd);
+  const int tid = threadIdx.x;
+  if (tid < DW) {
+    const double* g0 = reinterpret_cast<const double*>(row);
+    sdw[tid] = g0[tid];
+    sdw[DW + tid] = g0[tid];
+  }
+  __syncthreads();
+  T* __restrict__ dst = slot_ptr(S, t, base);
+  int lo[3];
+  box_origin<D>(g, sd[0], lo[0], lo[1], lo[2]);
+  T* bs = boxstore ? boxstore + (long long)((t - base - 1) % nbox) * g.box_cells * D : nullptr;
+  const dim3 bg = box_grid(g);
+  const int ntiles = (int)(bg.x * bg.y * bg.z);
+  const int G = (int)gridDim.x;
+  for (int k = 1; k <= K; ++k) {
+    const Dof sk = sd[1];
+    T v[NV];
+#pragma unroll
+    for (int a = 0; a < NV; ++a) v[a] = T(0);
+    for (int tile = blockIdx.x; tile < ntiles; tile += G) {
+      const CellSlot cc = cell_slot_tile<D>(g, tile, bg.x, bg.y);
+      couple_cell<T, D, AX>(g, kref, sk, lo, cc, dst, k == K ? bs : nullptr, k == K, &ctrl->status, v);
+    }
+    PT* part = static_cast<PT*>(partials) + (k & 1) * pstride;
+    block_sum_partial<NV>(v, part + blockIdx.x * NV, red);
+    if (!grid_sync(&ctrl->sync_bar, &ctrl->status, skip)) return;
+    if (k == K && blockIdx.x != 0) return;  // the last EOM is needed only for the DOF history
+    Moments m;
+    if (tid == 0) m = *mom;
+    double sm[NV];
+    block_sum_partials<NV>(part, G, sm, red);
+    if (tid == 0) {
+      int st = 0;
+      couple_finish_any<D, AX>(g, &m, sd[0], sd[1], sm, &sd[2], &st);
+      if (st && blockIdx.x == 0) atomicOr(&ctrl->status, st);
+    }
+    __syncthreads();
+    if (tid < DW) {
+      sdw[DW + tid] = sdw[2 * DW + tid];
+      if (blockIdx.x == 0) {
+        reinterpret_cast<double*>(row + k)[tid] = sdw[2 * DW + tid];
+        if (k == K) reinterpret_cast<double*>(row + K + 1)[tid] = sdw[2 * DW + tid];  // s(t): the next step's row 0
+      }
+    }
+    __syncthreads();
+  }
+}
+
+// Reverse: for k = N_itr..1 the cell phase (Brinkman and interpolation reverse), a barrier, the
+// design-point phase (spread and transform reverse, dJ/dkappa^ref, per-CTA partials of dJ/ds^(k-1)),
+// a barrier, then in every CTA the sum of the partials and the EOM reverse of the previous iteration
+// (adj_finish), whose dJ/dF, dJ/dT the next cell phase uses. CTA 0 stores the carried adjoint.
+template <typename T, int D, int AX>
+__global__ void __launch_bounds__(BoxCta<D>::threads, 1)
+    k_adj_coop(Geo g, Ctrl* ctrl, const Dof* it, const T* __restrict__ kref, const T* __restrict__ boxstore, int nbox,
+               T* Lb, long long lstride, T* __restrict__ acc, T* __restrict__ scratch, double* __restrict__ dkref,
+               void* partials, long long pstride, int di) {
+  using PT = typename Partial<T>::type;
+  constexpr bool FREE = AX == AX_FREE;
+  constexpr int NV = nv_design<AX>();
+  constexpr int NS = FREE ? kNdofFree : kNdofAxis;
+  constexpr int PPC = BoxCta<D>::threads / LN;  // design points per CTA pass
+  __shared__ double red[32 * NV];
+  // thread 0's FP64 finish works in shared memory (kept out of every thread's registers): the
+  // carried adjoint dJ/ds(t-1), dJ/ds(0) at step 1, dJ/dF and dJ/dT of the iteration to reverse
+  // next, and with free rotation the two iterates of the EOM being reversed
+  __shared__ double s_lp[NS], s_ls0[NS], slam[6];
+  __shared__ Dof s_e[FREE ? 2 : 1];
+  if (*(volatile int*)&ctrl->status & ST_SYNC_TIMEOUT) return;
+  const int t = ctrl->t0 - di, base = ctrl->base, K = g.K;
+  const bool skip = ctrl->sync_skip != 0;
+  const Dof* row = it + (long long)(t - 1) * (K + 1);
+  const int tid = threadIdx.x, lane = tid % LN;
+  T lF[3], lT[3];
+  lam_load<T>(ctrl, lF, lT);
+  if (tid < NS) {
+    s_lp[tid] = ctrl->lam_prev[tid];
+    s_ls0[tid] = 0.0;
+  }
+  if (tid < 6) slam[tid] = 0.0;
+  T* Lcur = Lb + (long long)(t & 1) * lstride;
+  int lo[3];
+  box_origin<D>(g, row[0], lo[0], lo[1], lo[2]);
+  const T* bs = boxstore + (long long)((t - base - 1) % nbox) * g.box_cells * D;
+  const dim3 bg = box_grid(g);
+  const int ntiles = (int)(bg.x * bg.y * bg.z);
+  const int G = (int)gridDim.x;
+  for (int k = K; k >= 1; --k) {
+    const Dof sk = row[k - 1];
+    for (int tile = blockIdx.x; tile < ntiles; tile += G) {
+      const CellSlot cc = cell_slot_tile<D>(g, tile, bg.x, bg.y);
+      adj_cell_work<T, D, AX>(g, kref, sk, lo, cc, bs, Lcur, acc, scratch, k, K, lF, lT);
+    }
+    if (!grid_sync(&ctrl->sync_bar, &ctrl->status, skip)) return;
+    T v[NV];
+#pragma unroll
+    for (int a = 0; a < NV; ++a) v[a] = T(0);
+    bool inside = true;
+    for (int m0 = blockIdx.x * PPC; m0 < g.ND; m0 += G * PPC) {
+      const int m = m0 + tid / LN;
+      inside = adj_design_point<T, D, AX>(g, kref, scratch, sk, lo, m, m < g.ND, lane, lF, lT, dkref, v) && inside;
+    }
+    if (!inside) atomicOr(&ctrl->status, ST_BOX_OVERFLOW);
+    PT* part = static_cast<PT*>(partials) + (k & 1) * pstride;
+    block_sum_partial<NV>(v, part + blockIdx.x * NV, red);
+    if (!grid_sync(&ctrl->sync_bar, &ctrl->status, skip)) return;
+    const int te = (k > 1) ? t : t - 1, ke = (k > 1) ? k - 1 : K;
+    if constexpr (FREE) {
+      constexpr int DW = (int)(sizeof(Dof) / sizeof(double));
+      if (te >= 1 && tid < DW) {  // the EOM being reversed maps s(te - 1) to iterate ke of step te
+        const Dof* erow = it + (long long)(te - 1) * (K + 1);
+        reinterpret_cast<double*>(&s_e[0])[tid] = reinterpret_cast<const double*>(erow)[tid];
+        reinterpret_cast<double*>(&s_e[1])[tid] = reinterpret_cast<const double*>(erow + ke)[tid];
+      }
+    }
+    double ls[NV];
+    block_sum_partials<NV>(static_cast<const PT*>(part), G, ls, red);  // its barriers order the staging
+    if (tid == 0) {
+      if constexpr (FREE)
+        adj_finish_free(g, k, ls, s_lp, slam, slam + 3, s_ls0, s_e[0], s_e[FREE ? 1 : 0], te >= 1);
+      else
+        adj_finish(g, k, ls, s_lp, slam, slam + 3, s_ls0);
+    }
+    __syncthreads();
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+      lF[a] = (T)slam[a];
+      lT[a] = (T)slam[3 + a];
+    }
+  }
+  if (blockIdx.x == 0 && tid == 0) {
+    for (int a = 0; a < NS; ++a) {
+      ctrl->lam_prev[a] = s_lp[a];
+      ctrl->lam_s0[a] = s_ls0[a];
+    }
+    lam_store(ctrl, slam, slam + 3);
+  }
+}
+
+// ---- index sets of the spread (test export) -------------------------------------------------
+
+// Per box cell: the number of design points the gather accepts, the least and largest of their
+// linear indices, and the sums of the indices and of their squares.
+struct SetStats {
+  long long c, lo, hi, s1, s2;
+};
+struct StatVisit {
+  SetStats* st;
+  __device__ __forceinline__ void operator()(int m) const {
+    st->c += 1;
+    st->lo = min(st->lo, (long long)m);
+    st->hi = max(st->hi, (long long)m);
+    st->s1 += m;
+    st->s2 += (long long)m * m;
+  }
+};
+
+// The box of the iterate s (the box a step starting from s would use), gathered as the coupling
+// gathers it, recording the accepted index sets into out[box cell][5].
+template <typename T, int D, int AX>
+__global__ void __launch_bounds__(BoxCta<D>::threads) k_support_sets(Geo g, Dof s, const T* __restrict__ kref,
+                                                                     long long* __restrict__ out) {
+  int lo[3];
+  box_origin<D>(g, s, lo[0], lo[1], lo[2]);
+  const CellSlot cc = cell_slot<D>(g);
+  const int px = lo[0] + cc.j0, py = lo[1] + cc.j1, pz = lo[2] + cc.j2;
+  const DofView<T> V(s);
+  const T d[3] = {V.rel(0, px), V.rel(1, py), D == 3 ? V.rel(2, pz) : T(0)};
+  SetStats st{0, LLONG_MAX, -1, 0, 0};
+  Acc<T> A;
+  if constexpr (AX == AX_FREE) {
+    const FreeView<T> FV(s);
+    gather_free_lanes<T, LN>(g, kref, d, FV.R, cc.lane, cc.active, A, StatVisit{&st});
+  } else {
+    gather_lanes<T, D, AX, LN>(g, kref, d, V.cs, V.sn, cc.lane, cc.active, A, StatVisit{&st});
+  }
+#pragma unroll
+  for (int off = 1; off < LN; off <<= 1) {
+    st.c += __shfl_xor_sync(0xffffffffu, st.c, off);
+    st.lo = min(st.lo, __shfl_xor_sync(0xffffffffu, st.lo, off));
+    st.hi = max(st.hi, __shfl_xor_sync(0xffffffffu, st.hi, off));
+    st.s1 += __shfl_xor_sync(0xffffffffu, st.s1, off);
+    st.s2 += __shfl_xor_sync(0xffffffffu, st.s2, off);
+  }
+  if (!cc.active || cc.lane != 0) return;
+  const long long bl = cc.j0 + (long long)g.B[0] * (cc.j1 + (long long)g.B[1] * cc.j2);
+  out[5 * bl + 0] = st.c;
+  out[5 * bl + 1] = st.c ? st.lo : -1;
+  out[5 * bl + 2] = st.hi;
+  out[5 * bl + 3] = st.s1;
+  out[5 * bl + 4] = st.s2;
+}
 
 }  // namespace
 
+template <typename T>
+void launch_couple_coop(const Geo& g, const Slots<T>& S, Ctrl* ctrl, Dof* it, const T* kref, const Moments* mom,
+                        void* partials, long long pstride, T* boxstore, int nbox, int di, cudaStream_t st) {
+  const dim3 grid((unsigned)g.coop_fwd), block((unsigned)box_threads(g));
+  if (g.dim == 2)
+    launch_coop(k_couple_coop<T, 2, 2>, grid, block, 0, st, g, S, ctrl, it, kref, mom, partials, pstride, boxstore,
+                nbox, di);
+  else if (g.ax == 0)
+    launch_coop(k_couple_coop<T, 3, 0>, grid, block, 0, st, g, S, ctrl, it, kref, mom, partials, pstride, boxstore,
+                nbox, di);
+  else if (g.ax == 1)
+    launch_coop(k_couple_coop<T, 3, 1>, grid, block, 0, st, g, S, ctrl, it, kref, mom, partials, pstride, boxstore,
+                nbox, di);
+  else if (g.ax == 2)
+    launch_coop(k_couple_coop<T, 3, 2>, grid, block, 0, st, g, S, ctrl, it, kref, mom, partials, pstride, boxstore,
+                nbox, di);
+  else
+    launch_coop(k_couple_coop<T, 3, AX_FREE>, grid, block, 0, st, g, S, ctrl, it, kref, mom, partials, pstride,
+                boxstore, nbox, di);
+}
 
+template <typename T>
+void launch_adj_coop(const Geo& g, Ctrl* ctrl, const Dof* it, const T* kref, const T* boxstore, int nbox, T* Lb,
+                     long long lstride, T* acc, T* scratch, double* dkref, void* partials, long long pstride, int di,
+                     cudaStream_t st) {
+  const dim3 grid((unsigned)g.coop_adj), block((unsigned)box_threads(g));
+  if (g.dim == 2)
+    launch_coop(k_adj_coop<T, 2, 2>, grid, block, 0, st, g, ctrl, it, kref, boxstore, nbox, Lb, lstride, acc, scratch,
+                dkref, partials, pstride, di);
+  else if (g.ax == 0)
+    launch_coop(k_adj_coop<T, 3, 0>, grid, block, 0, st, g, ctrl, it, kref, boxstore, nbox, Lb, lstride, acc, scratch,
+                dkref, partials, pstride, di);
+  else if (g.ax == 1)
+    launch_coop(k_adj_coop<T, 3, 1>, grid, block, 0, st, g, ctrl, it, kref, boxstore, nbox, Lb, lstride, acc, scratch,
+                dkref, partials, pstride, di);
+  else if (g.ax == 2)
+    launch_coop(k_adj_coop<T, 3, 2>, grid, block, 0, st, g, ctrl, it, kref, boxstore, nbox, Lb, lstride, acc, scratch,
+                dkref, partials, pstride, di);
+  else
+    launch_coop(k_adj_coop<T, 3, AX_FREE>, grid, block, 0, st, g, ctrl, it, kref, boxstore, nbox, Lb, lstride, acc,
+                scratch, dkref, partials, pstride, di);
+}
+
+namespace {
+template <typename T, int D, int AX>
+int coop_ctas(const Geo& g, int threads) {
+  int dev = 0, sms = 0, per_sm_f = 0, per_sm_a = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return 0;
+  if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm_f, k_couple_coop<T, D, AX>, threads, 0) != cudaSuccess)
+    return 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm_a, k_adj_coop<T, D, AX>, threads, 0) != cudaSuccess)
+    return 0;
+  const int per_sm = per_sm_f < per_sm_a ? per_sm_f : per_sm_a;
+  const dim3 bg = box_grid(g);
+  const long long ntiles = (long long)bg.x * bg.y * bg.z;
+  const long long cap = (long long)per_sm * sms;
+  return (int)(ntiles < cap ? ntiles : cap);
+}
+template <typename T>
+int coop_ctas_any(const Geo& g) {
+  const int th = box_threads(g);
+  if (g.dim == 2) return coop_ctas<T, 2, 2>(g, th);
+  if (g.ax == 0) return coop_ctas<T, 3, 0>(g, th);
+  if (g.ax == 1) return coop_ctas<T, 3, 1>(g, th);
+  if (g.ax == 2) return coop_ctas<T, 3, 2>(g, th);
+  return coop_ctas<T, 3, AX_FREE>(g, th);
+}
+}  // namespace
+
+void setup_coop(Geo* g, bool fp64) {
+  const int n = fp64 ? coop_ctas_any<double>(*g) : coop_ctas_any<float>(*g);
+  cudaGetLastError();  // an occupancy query that failed leaves the per-iteration kernels in use
+  g->coop_fwd = g->coop_adj = n;
+}
+
+template <typename T>
+void launch_support_sets(const Geo& g, const Dof& s, const T* kref, long long* out, cudaStream_t st) {
+  LKS_BOX_DISPATCH(k_support_sets, box_grid(g), box_threads(g), g, s, kref, out);
+}
 
 template <typename T>
 void launch_prep(const Geo& g, const double* gamma, double kappa_max, double q, T* kref, Moments* mom,
@@ -963,7 +1315,12 @@ void launch_ckpt_pack(const Geo& g, const Slots<T>& S, T* ckpt, long long cstrid
                                      cudaStream_t);                                                                 \
   template void launch_init_forward<T>(const Geo&, const Slots<T>&, const double*, const double*, const double*,     \
                                        Dof*, Ctrl*, cudaStream_t);                                                  \
-  template void launch_ckpt_pack<T>(const Geo&, const Slots<T>&, T*, long long, int, const Ctrl*, int, cudaStream_t);
+  template void launch_ckpt_pack<T>(const Geo&, const Slots<T>&, T*, long long, int, const Ctrl*, int, cudaStream_t); \
+  template void launch_support_sets<T>(const Geo&, const Dof&, const T*, long long*, cudaStream_t);             \
+  template void launch_couple_coop<T>(const Geo&, const Slots<T>&, Ctrl*, Dof*, const T*, const Moments*, void*,     \
+                                      long long, T*, int, int, cudaStream_t);                                       \
+  template void launch_adj_coop<T>(const Geo&, Ctrl*, const Dof*, const T*, const T*, int, T*, long long, T*, T*,    \
+                                   double*, void*, long long, int, cudaStream_t);
 
 LKS_INST(float)
 LKS_INST(double)

@@ -47,6 +47,22 @@ __device__ __forceinline__ CellSlot cell_slot(const Geo& g) {
   return c;
 }
 
+// The same for box tile `tile` of the box grid (x fastest) in the persistent kernels, whose CTAs
+// stride over the tiles.
+template <int D>
+__device__ __forceinline__ CellSlot cell_slot_tile(const Geo& g, int tile, int gx, int gy) {
+  constexpr int CX = BoxCta<D>::X, CY = BoxCta<D>::Y;
+  CellSlot c;
+  const int q = threadIdx.x / LN;
+  c.lane = threadIdx.x % LN;
+  const int bx = tile % gx, by = (tile / gx) % gy, bz = tile / (gx * gy);
+  c.j0 = bx * CX + q % CX;
+  c.j1 = by * CY + q / CX;
+  c.j2 = bz;
+  c.active = c.j0 < g.B[0] && c.j1 < g.B[1];
+  return c;
+}
+
 __device__ __forceinline__ int block_linear() { return blockIdx.x + gridDim.x * (blockIdx.y + gridDim.y * blockIdx.z); }
 
 // R and omega of a free-rotation iterate in the field type.
@@ -105,8 +121,8 @@ inline int design_ctas(const Geo& g) {
   return n < kMaxDesignCtas ? n : kMaxDesignCtas;
 }
 
-inline int box_threads(const Geo& g) { return kBoxCtaCellsX * (g.dim == 2 ? kBoxCtaCellsY2D : kBoxCtaCellsY) * LN; }
-inline dim3 box_grid(const Geo& g) {
+__host__ __device__ inline int box_threads(const Geo& g) { return kBoxCtaCellsX * (g.dim == 2 ? kBoxCtaCellsY2D : kBoxCtaCellsY) * LN; }
+__host__ __device__ inline dim3 box_grid(const Geo& g) {
   const int cx = kBoxCtaCellsX, cy = g.dim == 2 ? kBoxCtaCellsY2D : kBoxCtaCellsY;
   return dim3((g.B[0] + cx - 1) / cx, (g.B[1] + cy - 1) / cy, g.dim == 3 ? g.B[2] : 1);
 }

@@ -21,7 +21,7 @@ enum { BC_PERIODIC = 0, BC_INFLOW_OUTFLOW = 1, BC_WALL = 2, BC_PRESSURE = 3 };
 enum { W_COS4 = 0, W_BILINEAR = 1 };
 enum { DOF_TX = 1, DOF_TY = 2, DOF_TZ = 4, DOF_ROT = 8 };
 enum { CKQ_BF16 = 1, CKQ_FP16 = 2 };  // reduced-precision checkpoint formats
-enum { ST_BODY_OUTSIDE = 1, ST_NONFINITE = 2, ST_BOX_OVERFLOW = 4 };
+enum { ST_BODY_OUTSIDE = 1, ST_NONFINITE = 2, ST_BOX_OVERFLOW = 4, ST_SYNC_TIMEOUT = 8 };
 enum { CNT_COUPLE = 0, CNT_APPLY = 1, CNT_DESIGN = 2, CNT_ADJ_STENCIL = 3, CNT_PREP = 4, CNT_CKPT = 5, CNT_N = 8 };
 // Rotation modes (the AX template argument of the body kernels): 0, 1, 2 = one axis; free rotation.
 constexpr int AX_FREE = 3;
@@ -108,7 +108,9 @@ struct Ctrl {
   int t0;                 // forward: first step of the chunk; adjoint: last step of the chunk
   int base;               // step held in slot 0 of the resident segment
   int status;             // ST_* bits
-  int pad;
+  int prep_status;        // ST_NONFINITE if the design field held a NaN or an infinity (k_prep)
+  unsigned sync_bar;      // grid barrier word of the cooperative coupling kernels (grid_sync)
+  int sync_skip;          // test hook: non-zero makes CTA 0 skip its barrier arrivals (the waits time out)
   unsigned count[CNT_N];  // last-block counters, one per kernel family
   double lam_prev[kNdofFree];  // adjoint: direct EOM part of dJ/ds(t-1)
   double lam_F[3];        // adjoint: dJ/dF of the iteration being reversed
@@ -157,6 +159,7 @@ struct Geo {
   int hb[3];      // box half extent (ceil of the body's half extent)
   int margin;     // cells of drift allowed within one step
   long long box_cells;
+  int coop_fwd, coop_adj;  // CTAs of the cooperative coupling kernels (0: the per-iteration kernels)
 };
 
 // State slots.
@@ -274,15 +277,21 @@ __device__ __forceinline__ int dsq(int i, int nd) {
   return e * e;
 }
 
+// Visitor of the design points a gather accepts (their linear indices); the default does nothing,
+// a test export records the accepted index sets.
+struct NoVisit {
+  __device__ __forceinline__ void operator()(int) const {}
+};
+
 // Gather (Eqs. kappa_mapping, us_mapping) for the cell at d = x_n - x^G under rotation (cs, sn)
 // about AX, split over LANES consecutive threads of a warp. Candidates: the design points of the
 // design domain whose rotated position lies in the axis-aligned support square of the cell; in the
 // design frame they lie within s (|cos| + |sin|) of the cell's image. Lane j takes candidate rows
 // ib0 + j, ib0 + j + LANES, ...; the sums are combined with shuffles so every lane ends with the
 // cell's totals.
-template <typename F, int D, int AX, int LANES>
+template <typename F, int D, int AX, int LANES, typename Visit = NoVisit>
 __device__ __forceinline__ void gather_lanes(const Geo& g, const F* __restrict__ kref, const F (&d)[3], F cs, F sn,
-                                             int lane, bool active, Acc<F>& o) {
+                                             int lane, bool active, Acc<F>& o, Visit visit = Visit()) {
   constexpr int b = Axes<AX>::B, c = Axes<AX>::C, ax = Axes<AX>::A;
   const F S = (F)g.s;
   const F xib = cs * d[b] + sn * d[c] + pivot<F>(g, b);
@@ -357,6 +366,7 @@ __device__ __forceinline__ void gather_lanes(const Geo& g, const F* __restrict__
       const F rc = (F)ic - pivot<F>(g, c);
       const int m2 = ib * sb + ic * sc;
       if (D == 2) {
+        visit(m2);
         const F wkap = w2 * kref[m2];
         o.phi += w2;
         o.kap += wkap;
@@ -370,6 +380,7 @@ __device__ __forceinline__ void gather_lanes(const Geo& g, const F* __restrict__
 #pragma unroll
         for (int q = 0; q < 4; ++q) {
           if (!va[q] || qbc + qa[q] > g.rad4) continue;
+          visit(m2 + (ia0 + q) * sa);
           const F wk = wa[q] * kref[m2 + (ia0 + q) * sa];
           s1 += wa[q];
           s0 += wk;
@@ -407,9 +418,10 @@ __device__ __forceinline__ void gather_lanes(const Geo& g, const F* __restrict__
 // s sum_a |R_ab|. Rows (iy, iz) of that box are split over the lanes; within a row the three world
 // offsets are linear in ix, which bounds ix to the interval where all three lie in (-s, s)
 // (widened slightly; the exact test decides).
-template <typename F, int LANES>
+template <typename F, int LANES, typename Visit = NoVisit>
 __device__ __forceinline__ void gather_free_lanes(const Geo& g, const F* __restrict__ kref, const F (&d)[3],
-                                                  const F (&R)[9], int lane, bool active, Acc<F>& o) {
+                                                  const F (&R)[9], int lane, bool active, Acc<F>& o,
+                                                  Visit visit = Visit()) {
   const F S = (F)g.s;
   F xi[3];
   int lo[3], hi[3];
@@ -459,6 +471,7 @@ __device__ __forceinline__ void gather_free_lanes(const Geo& g, const F* __restr
       const F ex = (F)ix - xi[0];
       const F o0 = R[0] * ex + cw[0], o1 = R[3] * ex + cw[1], o2 = R[6] * ex + cw[2];
       if (fabs(o0) >= S || fabs(o1) >= S || fabs(o2) >= S || qyz + dsq(ix, g.nd[0]) > g.rad4) continue;
+      visit(mrow + ix);
       const F W = wfun(g.wk, o0) * wfun(g.wk, o1) * wfun(g.wk, o2);
       const F wkap = W * kref[mrow + ix];
       const F rx = (F)ix - pivot<F>(g, 0);

@@ -19,6 +19,24 @@ inline void launch(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t smem,
   cudaLaunchKernelEx(&cfg, kernel, args...);
 }
 
+// Cooperative launch (every CTA of the grid co-resident, or the launch fails): the persistent
+// coupling kernels, whose CTAs meet at grid barriers.
+template <typename... KArgs, typename... Args>
+inline void launch_coop(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t st,
+                        Args... args) {
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeCooperative;
+  attr[0].val.cooperative = 1;
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = grid;
+  cfg.blockDim = block;
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = st;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  cudaLaunchKernelEx(&cfg, kernel, args...);
+}
+
 constexpr int kTileX = 32;  // 3D stencil column width (cells); boundary pairs must not straddle columns
 constexpr int kTileY3 = 16;  // 3D stencil column height (the column marches over a chunk of z planes)
 constexpr int kStripWarps = 4;  // 2D stencil: warps per CTA, each streaming its own strip of rows
@@ -74,6 +92,24 @@ template <typename T>
 void launch_couple_last(const Geo& g, Ctrl* ctrl, Dof* it, const Moments* mom, const void* partials,
                         long long pstride, int t_last, cudaStream_t st);
 
+// Persistent form of the N_itr coupling iterations of step t (one cooperative launch of
+// g.coop_fwd CTAs that stride over the box tiles, with a bounded grid barrier after each
+// iteration's partial sums): the same cell work and fixed-order sums as launch_couple, and the EOM
+// of iteration N_itr too, so no finish kernel follows. Sets ctrl->coop fields through sync_bar.
+template <typename T>
+void launch_couple_coop(const Geo& g, const Slots<T>& S, Ctrl* ctrl, Dof* it, const T* kref, const Moments* mom,
+                        void* partials, long long pstride, T* boxstore, int nbox, int di, cudaStream_t st);
+// Persistent form of the reverse of the N_itr coupling iterations of step t (cell phase, barrier,
+// design-point phase, barrier, finish with the EOM reverse in every CTA), one cooperative launch of
+// g.coop_adj CTAs in place of launch_adj_cell + launch_adj_design for k = N_itr..1.
+template <typename T>
+void launch_adj_coop(const Geo& g, Ctrl* ctrl, const Dof* it, const T* kref, const T* boxstore, int nbox, T* Lb,
+                     long long lstride, T* acc, T* scratch, double* dkref, void* partials, long long pstride, int di,
+                     cudaStream_t st);
+// CTAs of the cooperative kernels for this geometry and field type: the box tiles, at most as many
+// as the device holds at once (0 if the kernel cannot be resident); sets g->coop_fwd, g->coop_adj.
+void setup_coop(Geo* g, bool fp64);
+
 // Recompute: Brinkman update with the stored iterate s^(K-1); writes u(t) and the box store of u*.
 template <typename T>
 void launch_apply(const Geo& g, const Slots<T>& S, const Ctrl* ctrl, const Dof* it, const T* kref, T* boxstore,
@@ -89,6 +125,11 @@ void launch_adj_cell(const Geo& g, const Ctrl* ctrl, const Dof* it, const T* kre
 template <typename T>
 void launch_adj_design(const Geo& g, Ctrl* ctrl, const Dof* it, const T* kref, const T* scratch, double* dkref,
                        void* partials, int k, int di, cudaStream_t st);
+
+// Test export: the design points the coupling's gather accepts for each cell of the box of the
+// iterate s, as out[box cell][5] = (count, least index or -1, largest index, sum, sum of squares).
+template <typename T>
+void launch_support_sets(const Geo& g, const Dof& s, const T* kref, long long* out, cudaStream_t st);
 
 // Design chain (cyclic expansion, density filter, Heaviside projection) gamma -> gbar, keeping the
 // filtered field gtil and the filter normaliser W for the transpose; active unless every step is off.

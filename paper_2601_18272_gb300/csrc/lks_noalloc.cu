@@ -1,28 +1,32 @@
 // One time step of the coupled LKS / rigid-body march that allocates no device memory.
 //
 // Who needs this: lks_create allocates a workspace with cudaMalloc, and some callers cannot let a
-// library do that -- code running inside a relaxed-mode CUDA graph capture on its own stream,
-// real-time loops whose device memory must be fixed before they start, and host frameworks that
-// own every device allocation and forbid libraries from making their own. For them,
-// lks_step_noalloc keeps all of its scratch (kappa^ref, the design moments, the DOF iterates, the
-// control block and the per-CTA partial sums of the force/torque reduction) in one fixed array
-// of device memory declared below. The caller still passes the design field and the state.
+// library do that -- real-time loops whose device memory must be fixed before they start, and
+// host frameworks that own every device allocation and forbid libraries from making their own.
+// For them, lks_step_noalloc keeps all of its scratch (kappa^ref, the design moments, the DOF
+// iterates, the control block and the per-CTA partial sums of the force/torque reduction) in one
+// fixed array of device memory declared below. The caller still passes the design field and the
+// state.
 //
 // Costs and rules:
 //   - every GPU that loads this library holds the array (kScratchBytes, about 0.7 MB) until the
 //     process exits;
 //   - the first call on a device looks up the array's device address (cudaGetSymbolAddress) with
-//     that device current and caches it; make that first call before any stream capture;
+//     that device current and caches it;
 //   - all calls share the one array, which keeps the last call's contents: each call clears the
 //     part that must start at zero, and calls that overlap on the GPU (two streams, two host
 //     threads) race on it -- serialise them;
-//   - sizes beyond the array's limits are rejected with LKS_ERR_BUDGET.
+//   - each call waits for its stream and copies the new DOFs to the host before it returns;
+//   - the problem is checked, and its geometry derived, by the same code as lks_create; sizes
+//     beyond the array's limits are rejected with LKS_ERR_BUDGET, and what the step does not do
+//     (3D, FP32 fields, the design chain) with LKS_ERR_UNSUPPORTED.
 #include <climits>
 #include <cmath>
 #include <cstring>
 #include <mutex>
 
 #include "../../include/lks.h"
+#include "lks_geo.h"
 #include "lks_kernels.h"
 
 using namespace lks;
@@ -70,65 +74,20 @@ __global__ void k_noalloc_seed(Ctrl* ctrl, Dof* it, Dof s0, int base) {
   it[0] = s0;
 }
 
-// Problem constants for one step (2D, FP64 fields), the same as the handle-based path computes.
-int make_geo(const lks_problem* P, Geo* g) {
+// Problem constants for one step (2D, FP64 fields) from the shared validation and geometry of
+// lks_create, with the body box lks_forward would use for a march starting from s(t-1).
+int make_geo(const lks_problem* P, const double* s_prev, Geo* g) {
   if (!P) return LKS_ERR_ARG;
-  if (P->dim != 2 || P->velocity_set != LKS_D2Q9 || P->nz != 1 || P->ndz != 1 || P->rot_axis != 2)
-    return P->dim == 3 ? LKS_ERR_UNSUPPORTED : LKS_ERR_ARG;
-  if (P->field_precision != LKS_FP64) return LKS_ERR_UNSUPPORTED;
-  if (P->nx < 4 || P->ny < 4 || P->ndx < 1 || P->ndy < 1) return LKS_ERR_ARG;
-  if (P->bc[0] != LKS_BC_PERIODIC && P->bc[0] != LKS_BC_INFLOW_OUTFLOW && P->bc[0] != LKS_BC_PRESSURE) return LKS_ERR_ARG;
-  if (P->bc[1] != LKS_BC_PERIODIC && P->bc[1] != LKS_BC_WALL) return LKS_ERR_ARG;
-  if (!(P->nu > 0.0)) return LKS_ERR_UNSTABLE;
-  if (P->n_itr < 1 || !(P->mass > 0.0) || !(P->inertia > 0.0)) return LKS_ERR_ARG;
-  if (P->weight_kind != LKS_W_COS4 && P->weight_kind != LKS_W_BILINEAR) return LKS_ERR_ARG;
-  if (P->design_radius != 0.0) return LKS_ERR_UNSUPPORTED;
-  std::memset(g, 0, sizeof(Geo));
-  g->dim = 2;
-  g->n[0] = P->nx;
-  g->n[1] = P->ny;
-  g->n[2] = 1;
-  g->N = (long long)P->nx * P->ny;
-  g->bc[0] = P->bc[0];
-  g->bc[1] = P->bc[1];
-  g->bc[2] = LKS_BC_PERIODIC;
-  g->nd[0] = P->ndx;
-  g->nd[1] = P->ndy;
-  g->nd[2] = 1;
-  g->ND = P->ndx * P->ndy;
-  g->xic[0] = (P->ndx - 1) / 2.0;
-  g->xic[1] = (P->ndy - 1) / 2.0;
-  g->xicf[0] = (float)g->xic[0];
-  g->xicf[1] = (float)g->xic[1];
-  g->ax = 2;
-  g->axb = 0;
-  g->axc = 1;
-  g->ns = kNdofAxis;
-  g->rad4 = INT_MAX;  // the whole design grid
-  g->dof_mask = (int)P->dof_mask;
-  g->wk = P->weight_kind;
-  g->s = (P->weight_kind == LKS_W_BILINEAR) ? 1 : 2;
-  g->K = P->n_itr;
-  g->A = 4.5 * (1.0 / 6.0 - P->nu);
-  g->A2 = (float)(2.0 * g->A);
-  g->u_in = P->u_in;
-  g->dp = P->dp;
-  g->mass = P->mass;
-  g->inertia = P->inertia;
-  g->inv_mass = 1.0 / P->mass;
-  g->inv_inertia = 1.0 / P->inertia;
-  // body box placed from x^G(t-1): circumscribed in the plane (the body may rotate)
-  const double hx = (P->ndx - 1) / 2.0, hy = (P->ndy - 1) / 2.0;
-  const int hb = (int)std::ceil(std::sqrt(hx * hx + hy * hy) - 1e-12);
-  g->margin = 1;
-  for (int a = 0; a < 2; ++a) {
-    g->hb[a] = hb;
-    g->B[a] = 2 * hb + 2 * g->s + 2 * g->margin + 2;
-    if (g->bc[a] == LKS_BC_PERIODIC && g->B[a] > g->n[a]) return LKS_ERR_UNSUPPORTED;
-  }
-  g->hb[2] = 0;
-  g->B[2] = 1;
-  g->box_cells = (long long)g->B[0] * g->B[1];
+  const int v = validate_problem(P);
+  if (v != LKS_OK) return v;
+  if (P->dim != 2 || P->field_precision != LKS_FP64) return LKS_ERR_UNSUPPORTED;
+  // the design chain (cyclic expansion, filter, projection) needs workspace of its own
+  if (P->filter_radius > 0.0 || P->proj_beta > 0.0 || P->cyclic_order > 1) return LKS_ERR_UNSUPPORTED;
+  bool rot_ok = true;
+  if (make_geometry(P, g, &rot_ok) != LKS_OK) return LKS_ERR_UNSUPPORTED;
+  const bool rotated = (g->dof_mask & LKS_DOF_ROT) || s_prev[6] != 0.0;
+  if (rotated && !rot_ok) return LKS_ERR_UNSUPPORTED;
+  setup_box(g, P->design_radius, rotated);
   return LKS_OK;
 }
 
@@ -137,8 +96,12 @@ int make_geo(const lks_problem* P, Geo* g) {
 extern "C" int lks_step_noalloc(const lks_problem* problem, const double* gamma_dev, double* state_dev, int t,
                                 double* s_host, void* stream) {
   if (!problem || !gamma_dev || !state_dev || !s_host || t < 1) return LKS_ERR_ARG;
+  for (int a = 0; a < kNdofAxis; ++a)
+    if (!std::isfinite(s_host[a])) return LKS_ERR_NONFINITE;
+  for (int a = 0; a < 3; ++a)
+    if (std::fabs(s_host[a]) > 1e9) return LKS_ERR_ARG;  // x^G far outside any grid
   Geo g;
-  int r = make_geo(problem, &g);
+  int r = make_geo(problem, s_host, &g);
   if (r != LKS_OK) return r;
   const long long box_blocks = (long long)((g.B[0] + kBoxCtaCellsX - 1) / kBoxCtaCellsX) * ((g.B[1] + kBoxCtaCellsY - 1) / kBoxCtaCellsY);
   const long long design_blocks = ((long long)g.ND * 4 + 255) / 256;
@@ -179,6 +142,6 @@ extern "C" int lks_step_noalloc(const lks_problem* problem, const double* gamma_
   if (cudaGetLastError() != cudaSuccess) return LKS_ERR_CUDA;
   for (int a = 0; a < 8; ++a) s_host[a] = out.s[a];
   if (c.status & (ST_BODY_OUTSIDE | ST_BOX_OVERFLOW)) return LKS_ERR_BODY_OUTSIDE;
-  if (c.status & ST_NONFINITE) return LKS_ERR_NONFINITE;
+  if ((c.status & ST_NONFINITE) || (c.prep_status & ST_NONFINITE)) return LKS_ERR_NONFINITE;
   return LKS_OK;
 }

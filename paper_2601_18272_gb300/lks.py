@@ -24,7 +24,7 @@ LKS_ROT_FREE = -1
 LKS_NDOF_AXIS, LKS_NDOF_FREE, LKS_MAX_DOF = 8, 21, 21
 STATUS = {0: "LKS_OK", 1: "LKS_ERR_ARG", 2: "LKS_ERR_OOM", 3: "LKS_ERR_BUDGET", 4: "LKS_ERR_UNSTABLE",
           5: "LKS_ERR_BODY_OUTSIDE", 6: "LKS_ERR_NONFINITE", 7: "LKS_ERR_ORDER", 8: "LKS_ERR_CUDA",
-          9: "LKS_ERR_UNSUPPORTED"}
+          9: "LKS_ERR_UNSUPPORTED", 10: "LKS_ERR_TIMEOUT"}
 
 
 class lks_problem(ctypes.Structure):  # noqa: N801  (mirrors the C struct name)
@@ -113,6 +113,9 @@ def load() -> ctypes.CDLL:
     L.lks_last_cuda_error.argtypes = []
     L.lks_step_noalloc.argtypes = [ctypes.POINTER(lks_problem), vp, vp, ctypes.c_int, dp, vp]
     L.lks_dof_count.argtypes = [ctypes.POINTER(lks_problem)]
+    L.lks_support_sets.argtypes = [hp, dp, vp, vp, sz]
+    L.lks_debug_sync_skip.argtypes = [hp, ctypes.c_int]
+    L.lks_persistent_coupling.argtypes = [hp, ctypes.c_int]
     L.lks_constraint.argtypes = [hp, vp, dp, vp, vp]
     L.lks_warm_start.argtypes = [hp, ctypes.c_int, vp]
     L.lks_binomial_plan.argtypes = [ctypes.c_int, ctypes.c_int, vp, ctypes.c_longlong]
@@ -328,6 +331,32 @@ def lks_step_noalloc(problem: lks_problem, gamma_dev_ptr: int, state_dev_ptr: in
                                    ctypes.c_void_p(state_dev_ptr), int(t), _dptr(s), ctypes.c_void_p(stream)),
            "lks_step_noalloc")
     return s
+
+
+def lks_support_sets(h, s: np.ndarray):
+    """Test export: (box origin [3], box extent [3], int64 stats [box cells, 5]) of the design points
+    the coupling's gather accepts for each box cell under the DOF vector s."""
+    s = np.ascontiguousarray(s, dtype=np.float64)
+    box = np.zeros(6, dtype=np.int32)
+    L = load()
+    _check(L.lks_support_sets(h, _dptr(s), box.ctypes.data, None, 0), "lks_support_sets")
+    n = int(np.prod(box[3:]))
+    stats = np.zeros((n, 5), dtype=np.int64)
+    _check(L.lks_support_sets(h, _dptr(s), box.ctypes.data, stats.ctypes.data, stats.size), "lks_support_sets")
+    return box[:3].copy(), box[3:].copy(), stats
+
+
+def lks_debug_sync_skip(h, skip: bool):
+    """Test hook: the persistent kernels' first CTA skips its grid-barrier arrivals (waits time out)."""
+    _check(load().lks_debug_sync_skip(h, int(bool(skip))), "lks_debug_sync_skip")
+
+
+def lks_persistent_coupling(h, mode: int = -1) -> bool:
+    """Set (mode 1 / 0) or ask (mode -1) whether each step's coupling runs as one persistent launch."""
+    r = int(load().lks_persistent_coupling(h, int(mode)))
+    if r < 0:
+        raise LksError(-r, "lks_persistent_coupling")
+    return r == 1
 
 
 def lks_status_string(code: int) -> str:

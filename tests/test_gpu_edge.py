@@ -179,3 +179,47 @@ def test_nonfinite_initial_state_is_refused():
         assert S.forward(gam) == J
     finally:
         S.close()
+
+
+@pytest.mark.parametrize("precision", [32, 64])
+def test_nonfinite_design_is_found_on_the_device(precision):
+    """A NaN or an infinity in the device design field is found by the kernel that forms kappa^ref:
+    it reports through the device status word (LKS_ERR_NONFINITE) and the march runs with that point
+    void, so nothing non-finite enters it; the handle stays usable and a finite design gives the
+    same J as before."""
+    import torch
+    from paper_2601_18272_gb300.lks import LksError, Solver
+    P, g = body2d(nt=3)
+    p0, u0, s0 = perturbed_state(P)
+    S = Solver(P, precision=precision, ckpt_policy=CKPT_STORE_ALL)
+    try:
+        S.set_initial_state(p0, u0, s0)
+        gam = torch.tensor(g, dtype=torch.float64, device="cuda")
+        J = S.forward(gam)
+        for bad in (np.nan, np.inf):
+            gb = gam.clone()
+            gb[7] = bad
+            with pytest.raises(LksError, match="LKS_ERR_NONFINITE"):
+                S.forward(gb)
+            with pytest.raises(LksError, match="LKS_ERR_ORDER"):
+                S.adjoint(1.0)  # a failed forward leaves nothing to reverse
+        assert S.forward(gam) == J
+    finally:
+        S.close()
+
+
+def test_workspace_budget():
+    """hbm_budget_bytes bounds the workspace: a budget below what the problem needs is refused at
+    creation (LKS_ERR_BUDGET) before any allocation is kept; one at the exact need is accepted."""
+    from paper_2601_18272_gb300 import lks
+    from paper_2601_18272_gb300.lks import LksError, Solver
+    P, _ = body2d(nt=20)
+    S = Solver(P, precision=32, ckpt_policy=CKPT_UNIFORM, ckpt_every=5)
+    need = lks.lks_workspace_bytes(S.handle)
+    S.close()
+    for budget in (1 << 10, need - 256):
+        with pytest.raises(LksError, match="LKS_ERR_BUDGET"):
+            Solver(P, precision=32, ckpt_policy=CKPT_UNIFORM, ckpt_every=5, hbm_budget_bytes=budget)
+    S = Solver(P, precision=32, ckpt_policy=CKPT_UNIFORM, ckpt_every=5, hbm_budget_bytes=need)
+    assert lks.lks_workspace_bytes(S.handle) == need
+    S.close()

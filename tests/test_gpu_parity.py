@@ -273,7 +273,9 @@ def test_body3d_128x64x64_truncated_fp32():
 
 # ---- reduced-precision checkpoints -----------------------------------------------------------
 
-@pytest.mark.parametrize("fmt,tol", [(CKPT_BF16, 5e-2), (CKPT_FP16, 5e-3)], ids=["bf16", "fp16"])
+# tolerances about ten times the largest error measured on these cases (BF16 1.1e-4, FP16 8.6e-6;
+# FP32 checkpoints 4e-7)
+@pytest.mark.parametrize("fmt,tol", [(CKPT_BF16, 1.2e-3), (CKPT_FP16, 1e-4)], ids=["bf16", "fp16"])
 @pytest.mark.parametrize("name,make", CASES_2D[:2] + CASES_3D[:1], ids=[c[0] for c in CASES_2D[:2] + CASES_3D[:1]])
 def test_reduced_precision_checkpoints(name, make, fmt, tol):
     """BF16 / FP16 checkpoints with a per-plane affine range: the forward (and J) is that of the
