@@ -250,9 +250,34 @@ def stencil_roofline(dev, peak: float, dim: int, n: tuple, name: str, n_steps: i
     return out
 
 
-def gradient_throughput(dev, flush, index: int, n_steps: int = 0, plain_fp64: bool = False) -> dict:
-    """Whole-gradient throughput of another workload (one warm-up, one timed gradient), optionally
-    truncated to n_steps time steps and compared with the plain FP64 form (every state stored)."""
+def _timed(stream, flush, fn) -> float:
+    """CUDA-event milliseconds of fn() on the stream, after an L2 flush."""
+    import torch
+    torch.cuda.synchronize()
+    flush.zero_()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    fn()
+    e1.record(stream)
+    e1.synchronize()
+    return e0.elapsed_time(e1)
+
+
+def _fwd_roofline(P, ms: float, peak: float) -> dict:
+    """Forward-only throughput and its HBM fraction from the full-grid stencil bytes per cell-update
+    (24 B in 2D, 32 B in 3D, FP32): what the march must move if nothing stays in L2."""
+    bpc = 2 * (P.dim + 1) * 4
+    value = P.n_cells * P.n_steps / (ms / 1000.0)
+    return {"value": value, "unit": UNIT, "ms": ms, "bytes_per_cell_update": bpc,
+            "hbm_frac": value * bpc / 1e9 / peak}
+
+
+def gradient_throughput(dev, flush, peak: float, index: int, n_steps: int = 0, plain_steps: int = 0,
+                        warm: bool = True) -> dict:
+    """Whole-gradient and forward-only throughput of a workload (optionally truncated to n_steps): one
+    timed gradient (after one warm-up gradient if warm), one timed forward, the kernel families of a
+    gradient; with plain_steps, the plain FP64 store-all form on the first plain_steps steps and this
+    form's gradient error against it there."""
     import torch
     from paper_2601_18272_gb300 import lks
     from paper_2601_18272_gb300.lks import Solver
@@ -264,38 +289,53 @@ def gradient_throughput(dev, flush, index: int, n_steps: int = 0, plain_fp64: bo
     grad = torch.empty_like(gamma)
     stream = torch.cuda.current_stream(dev)
 
-    def timed(S):
-        def run():
-            S.forward(gamma)
-            S.adjoint(1.0)
-            S.sensitivity(grad)
-        run()
-        torch.cuda.synchronize()
-        flush.zero_()
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        e0.record(stream)
-        run()
-        e1.record(stream)
-        e1.synchronize()
-        return e0.elapsed_time(e1), run
+    def run(S, out):
+        S.forward(gamma)
+        S.adjoint(1.0)
+        S.sensitivity(out)
 
     S = Solver(P)
-    ms, run = timed(S)
-    fams = _family_times(S, run)
-    g32 = grad.clone()
+    if warm:
+        run(S, grad)
+    ms = _timed(stream, flush, lambda: run(S, grad))
+    ms_fwd = _timed(stream, flush, lambda: S.forward(gamma))
     out = {"workload": P.name, "value": P.n_cells * P.n_steps / (ms / 1000.0), "unit": UNIT, "ms_per_gradient": ms,
-           "n_steps": P.n_steps, "dtype": "f32", "workspace_gb": lks.lks_workspace_bytes(S.handle) / 1e9,
-           "kernel_ms_per_gradient": {k: round(v[0], 3) for k, v in fams.items()}}
+           "n_steps": P.n_steps, "dtype": "f32", "checkpoints": _ckpt_desc(P),
+           "workspace_gb": lks.lks_workspace_bytes(S.handle) / 1e9,
+           "persistent_coupling": lks.lks_persistent_coupling(S.handle, -1),
+           "forward": _fwd_roofline(P, ms_fwd, peak)}
+    if warm:
+        fams = _family_times(S, lambda: run(S, grad))
+        out["kernel_ms_per_gradient"] = {k: round(v[0], 3) for k, v in fams.items()}
     S.close()
-    if plain_fp64:
-        S = Solver(P, precision=64, ckpt_policy=CKPT_STORE_ALL)
-        ms64, _ = timed(S)
-        out["plain_fp64_store_all"] = {"value": P.n_cells * P.n_steps / (ms64 / 1000.0), "unit": UNIT,
-                                       "ms_per_gradient": ms64,
+    if plain_steps:
+        Pp = P.replace(n_steps=plain_steps)
+        S = Solver(Pp)
+        g32 = torch.empty_like(gamma)
+        run(S, g32)
+        if not warm:
+            fams = _family_times(S, lambda: run(S, g32))
+            out["kernel_ms_first_steps"] = {"n_steps": plain_steps, **{k: round(v[0], 3) for k, v in fams.items()}}
+        S.close()
+        S = Solver(Pp, precision=64, ckpt_policy=CKPT_STORE_ALL)
+        g64 = torch.empty_like(gamma)
+        run(S, g64)
+        ms64 = _timed(stream, flush, lambda: run(S, g64))
+        out["plain_fp64_store_all"] = {"n_steps": plain_steps, "value": P.n_cells * plain_steps / (ms64 / 1000.0),
+                                       "unit": UNIT, "ms_per_gradient": ms64,
                                        "workspace_gb": lks.lks_workspace_bytes(S.handle) / 1e9}
-        out["dJdgamma_rel_l2_vs_fp64"] = float(torch.linalg.norm(g32 - grad) / torch.linalg.norm(grad))
+        out["dJdgamma_rel_l2_vs_fp64_first_steps"] = float(torch.linalg.norm(g32 - g64) / torch.linalg.norm(g64))
         S.close()
     return out
+
+
+def _ckpt_desc(P) -> str:
+    fmt = {0: "fp32", 1: "bf16", 2: "fp16"}.get(P.ckpt_format, "?")
+    if P.ckpt_policy == 2:
+        return f"binomial, {P.ckpt_every} snapshots, {fmt}"
+    if P.ckpt_policy == 0:
+        return "every state stored"
+    return f"uniform every {P.ckpt_every}, {fmt}"
 
 
 def paper_adjoint_study(dev, flush) -> dict:
@@ -368,40 +408,42 @@ def paper_adjoint_study(dev, flush) -> dict:
     return out
 
 
-def ckpt_precision_study(dev, n_steps: int = 400) -> dict:
-    """Gradient error of FP32 / BF16 / FP16 checkpoints against the FP64 store-all GPU form on the
-    1024x512 / 256x256 x-y-theta workload truncated to n_steps (checkpoints every 100)."""
+def ckpt_precision_study(dev, n_steps: int = 0) -> dict:
+    """Gradient error of FP32 / BF16 / FP16 checkpoints (FP32 fields, checkpoints every 100) on the
+    1024x512 / 256x256 x-y-theta workload, at its full 20000 steps unless n_steps is given, against
+    the FP64 form (FP64 fields and checkpoints every 100, which reproduces the FP64 store-all
+    gradient to rounding and fits in memory at this length)."""
     import torch
+    from paper_2601_18272_gb300 import lks
     from paper_2601_18272_gb300.lks import Solver
-    from workloads import CKPT_BF16, CKPT_FP16, CKPT_FP32, CKPT_STORE_ALL, CKPT_UNIFORM, config
+    from workloads import CKPT_BF16, CKPT_FP16, CKPT_FP32, CKPT_UNIFORM, config
     P, g = config(3)
-    P = P.replace(n_steps=n_steps)
+    if n_steps:
+        P = P.replace(n_steps=n_steps)
     gamma = torch.tensor(g, dtype=torch.float64, device=dev)
     stream = torch.cuda.current_stream(dev)
 
     def grad(S):
         out = torch.empty_like(gamma)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
         J = S.forward(gamma)
         S.adjoint(1.0)
         S.sensitivity(out)
-        torch.cuda.synchronize()
-        return J, out
-
-    ref = Solver(P, precision=64, ckpt_policy=CKPT_STORE_ALL)
-    J64, g64 = grad(ref)
-    ref.close()
-    out = {"workload": P.name + f"_first{n_steps}", "reference": "FP64 store-all GPU form"}
-    for name, fmt in (("fp32", CKPT_FP32), ("bf16", CKPT_BF16), ("fp16", CKPT_FP16)):
-        S = Solver(P, precision=32, ckpt_policy=CKPT_UNIFORM, ckpt_every=100, ckpt_format=fmt)
-        J, d = grad(S)
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        e0.record(stream)
-        grad(S)
         e1.record(stream)
         e1.synchronize()
-        from paper_2601_18272_gb300 import lks
+        return J, out, e0.elapsed_time(e1)
+
+    ref = Solver(P, precision=64, ckpt_policy=CKPT_UNIFORM, ckpt_every=100)
+    J64, g64, ms64 = grad(ref)
+    ref.close()
+    out = {"workload": P.name, "n_steps": P.n_steps, "reference": "FP64 fields, FP64 checkpoints every 100",
+           "reference_ms_per_gradient": ms64}
+    for name, fmt in (("fp32", CKPT_FP32), ("bf16", CKPT_BF16), ("fp16", CKPT_FP16)):
+        S = Solver(P, precision=32, ckpt_policy=CKPT_UNIFORM, ckpt_every=100, ckpt_format=fmt)
+        J, d, ms = grad(S)  # one gradient each (graphs captured in its first segment)
         out[name] = {"dJdgamma_rel_l2": float(torch.linalg.norm(d - g64) / torch.linalg.norm(g64)),
-                     "J_rel": abs(J - J64) / abs(J64), "ms_per_gradient": e0.elapsed_time(e1),
+                     "J_rel": abs(J - J64) / abs(J64), "ms_per_gradient": ms,
                      "workspace_gb": lks.lks_workspace_bytes(S.handle) / 1e9}
         S.close()
     return out
@@ -438,6 +480,8 @@ def run_reference(args, ws, rank):
 
 
 def cpu_baseline(sample_steps: int):
+    """The oracle (single-threaded FP64) on a bounded sample of the benchmark workload, and its OpenMP
+    timing build (the same arithmetic over all host cores) on the same sample."""
     from oracle import oracle as O
     from workloads import config, initial_state
     P, g = config(CONFIG_INDEX)
@@ -445,9 +489,23 @@ def cpu_baseline(sample_steps: int):
     t0 = time.perf_counter()
     O.gradient(P, g, p0, u0, s0, n_steps=sample_steps)
     dt = time.perf_counter() - t0
-    return {"value": P.n_cells * sample_steps / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
-            "sample": f"forward+adjoint of the first {sample_steps} of {P.n_steps} time steps of {P.name}, "
-                      f"single-threaded FP64 ({dt:.1f} s)"}
+    out = {"value": P.n_cells * sample_steps / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
+           "sample": f"forward+adjoint of the first {sample_steps} of {P.n_steps} time steps of {P.name}, "
+                     f"single-threaded FP64 ({dt:.1f} s)"}
+    try:
+        if O.set_variant("openmp"):
+            t0 = time.perf_counter()
+            O.gradient(P, g, p0, u0, s0, n_steps=sample_steps)
+            dto = time.perf_counter() - t0
+            out["openmp"] = {"value": P.n_cells * sample_steps / dto, "unit": UNIT, "cores": O.threads(),
+                             "nproc": os.cpu_count(), "sample": "the same sample; per-node loops over all cores, "
+                             "design-point scatter and reductions serial (results bitwise the single-threaded "
+                             f"oracle's) ({dto:.1f} s)"}
+        else:
+            out["openmp"] = {"unavailable": "the host compiler built no OpenMP variant"}
+    finally:
+        O.set_variant("serial")
+    return out
 
 
 def main():
@@ -588,13 +646,31 @@ def main():
         dom_ms, dom_n = fams[dom]
         peak, peak_kind = _peaks()
         per_launch_s = dom_ms / 1000.0 / dom_n
-        alg = _alg_bytes(dom, P, _box_cells(P), 4)
+        persistent = lks.lks_persistent_coupling(solver.handle, -1)
+        alg = _alg_bytes(dom, P, _box_cells(P), 4, persistent)
         achieved = alg / per_launch_s / 1e9
         line["roofline"] = {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peak, "unit": "GB/s",
                             "frac": achieved / peak, "traffic": _traffic(P.name, dom), "peak_source": peak_kind,
                             "alg_bytes_per_launch": alg, "avg_launch_us": per_launch_s * 1e6,
+                            "persistent_coupling": persistent,
                             "kernel_ms_per_gradient": {k: round(v[0], 3) for k, v in fams.items()},
                             "launches_per_gradient": {k: v[1] for k, v in fams.items()}}
+        # forward-only throughput of this workload (the march alone, lks_forward)
+        ms_fwd = _timed(stream, flush, lambda: solver.forward(gamma))
+        line["roofline"]["forward_only"] = {P.name: _fwd_roofline(P, ms_fwd, peak)}
+        # the benchmark spec's autograd form: LKSObjective.apply(gamma, solver).backward() (the backward
+        # reads the incoming gradient on the host: one synchronisation, as lks_forward already has)
+        from paper_2601_18272_gb300.autograd import objective
+        gam_ag = gamma.clone().requires_grad_(True)
+        def ag():
+            gam_ag.grad = None
+            objective(gam_ag, solver).backward()
+        ag()
+        ag_ms = [_timed(stream, flush, ag) for _ in range(3)]
+        line["e2e"]["autograd"] = {"ms_per_gradient": float(np.median(ag_ms)),
+                                   "value": cell_steps / (float(np.median(ag_ms)) / 1000.0), "unit": UNIT,
+                                   "form": "LKSObjective.apply(gamma, solver).backward()",
+                                   "max_abs_diff_vs_raw_calls": float((gam_ag.grad - grad).abs().max())}
         # accuracy of this FP32 checkpointed gradient against the FP64 store-all GPU form, and the
         # throughput of that plain FP64 form
         plain = Solver(P, precision=64, ckpt_policy=CKPT_STORE_ALL)
@@ -621,14 +697,31 @@ def main():
                                         "ms_per_step": plain_ms, "workspace_gb": lks.lks_workspace_bytes(plain.handle) / 1e9}
         line["workspace_gb"] = lks.lks_workspace_bytes(solver.handle) / 1e9
         plain.close()
-        # the full-grid kernels on grids far larger than L2, and the 3D workload
+        # the full-grid kernels on grids far larger than L2, and the 3D workloads
         line["stencil_roofline_2d"] = stencil_roofline(dev, peak, 2, (8192, 4096), "fluid2d_8192x4096")
         line["stencil_roofline_3d"] = stencil_roofline(dev, peak, 3, (512, 256, 256), "fluid3d_512x256x256")
-        line["body3d"] = gradient_throughput(dev, flush, 4)
-        line["turbine3d_6dof"] = gradient_throughput(dev, flush, 5, n_steps=200, plain_fp64=True)
+        line["body3d"] = gradient_throughput(dev, flush, peak, 4)
+        # the largest workload at its full 10000 steps: one timed gradient (graphs captured in its
+        # first segment) and one timed forward; the plain FP64 store-all form does not fit at this
+        # length (1.3 TB), so it is compared on the first 50 steps
+        line["turbine3d_6dof"] = gradient_throughput(dev, flush, peak, 5, plain_steps=50, warm=False)
         line["ckpt_precision"] = ckpt_precision_study(dev)
         line["paper_adjoint"] = paper_adjoint_study(dev, flush)
         line["cpu_baseline"] = cpu_baseline(args.cpu_sample_steps)
+        # short copies that keep the large-grid fractions and the other workloads' throughput with
+        # the roofline record
+        sr2, sr3 = line["stencil_roofline_2d"], line["stencil_roofline_3d"]
+        line["roofline"]["stencil_frac"] = {"2d_fwd": sr2["stencil_fwd"]["frac"], "2d_adj": sr2["stencil_adj"]["frac"],
+                                            "3d_fwd": sr3["stencil_fwd"]["frac"], "3d_adj": sr3["stencil_adj"]["frac"],
+                                            "grids": ["8192x4096", "512x256x256"]}
+        for key in ("body3d", "turbine3d_6dof"):
+            w = line[key]
+            line["roofline"]["forward_only"][w["workload"]] = w["forward"]
+            line["roofline"].setdefault("gradient", {})[w["workload"]] = {
+                "n_steps": w["n_steps"], "ms": w["ms_per_gradient"], "value": w["value"]}
+        cp = line["ckpt_precision"]
+        line["roofline"]["ckpt_precision"] = {"n_steps": cp["n_steps"],
+                                              **{k: cp[k]["dJdgamma_rel_l2"] for k in ("fp32", "bf16", "fp16")}}
     solver.close()
     if rank == 0:
         print(json.dumps(line), flush=True)

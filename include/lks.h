@@ -111,8 +111,11 @@ typedef struct lks_problem {
   int field_precision;    /* LKS_FP32 or LKS_FP64 */
   int ckpt_policy;        /* LKS_CKPT_STORE_ALL, LKS_CKPT_UNIFORM or LKS_CKPT_BINOMIAL */
   int ckpt_every;         /* UNIFORM: checkpoint interval k; BINOMIAL: number of state snapshots
-                           * (the reverse sweep recomputes along a binomial schedule) */
-  int ckpt_format;        /* LKS_CKPT_NATIVE, LKS_CKPT_BF16 or LKS_CKPT_FP16 (FP32 fields) */
+                           * (the reverse sweep recomputes along a binomial schedule), or 0 with
+                           * hbm_budget_bytes > 0: as many snapshots as the budget holds after the rest
+                           * of the workspace (at most n_steps - 1) */
+  int ckpt_format;        /* LKS_CKPT_NATIVE, LKS_CKPT_BF16 or LKS_CKPT_FP16 (FP32 fields; uniform
+                           * checkpoints or binomial snapshots, 2 bytes per value and a per-plane range) */
   size_t hbm_budget_bytes;/* workspace limit, 0 = no limit */
 } lks_problem;
 
@@ -259,12 +262,14 @@ LKS_API int lks_support_sets(lks_handle* h, const double* s_host, int* box_host,
  * device. Errors: LKS_ERR_ARG, LKS_ERR_CUDA. */
 LKS_API int lks_debug_sync_skip(lks_handle* h, int skip);
 
-/* How the handle runs each step's N_itr coupling iterations (Sec. 3.1) and their reverse: mode 1
- * (the default) as one persistent cooperative launch per step when the device holds its grid, mode 0
- * as one launch per iteration (with the finish kernels), mode -1 only asks. Returns 1 if the
- * persistent kernels are in use after the call, 0 if not, or -status on error (LKS_ERR_ARG,
- * LKS_ERR_CUDA). Changing the mode synchronises the device; results agree to rounding (the per-CTA
- * partial sums are grouped differently). */
+/* How the handle runs each step's N_itr coupling iterations (Sec. 3.1) and their reverse: mode 1 as
+ * one persistent cooperative launch per step (grid barriers between the iterations) when the device
+ * holds its grid, mode 0 as one launch per iteration (with the finish kernels), mode 2 (the default)
+ * the persistent launch only where it measured faster (2D bodies whose box has more tiles than the
+ * persistent grid has CTAs), mode -1 only asks. Returns 1 if the persistent kernels are in use after
+ * the call, 0 if not, or -status on error (LKS_ERR_ARG, LKS_ERR_CUDA). Changing the mode
+ * synchronises the device; results agree to rounding (the per-CTA partial sums are grouped
+ * differently). */
 LKS_API int lks_persistent_coupling(lks_handle* h, int mode);
 
 /* Number of kernels this handle has launched (graph nodes counted per replay). */
@@ -301,6 +306,10 @@ LKS_API int lks_kernel_time(lks_handle* h, const char* family, double* ms_total,
  * it returns. */
 LKS_API int lks_step_noalloc(const lks_problem* problem, const double* gamma_dev, double* state_dev, int t,
                              double* s_host, void* stream);
+
+/* State copies the handle keeps for the reverse sweep: binomial snapshot slots (as chosen for
+ * ckpt_every = 0), uniform checkpoints, or n_steps + 1 stored states; -LKS_ERR_ARG for NULL. */
+LKS_API int lks_checkpoint_slots(const lks_handle* h);
 
 /* Bytes of device workspace held by the handle. */
 LKS_API size_t lks_workspace_bytes(const lks_handle* h);

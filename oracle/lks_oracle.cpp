@@ -56,6 +56,17 @@
 
 #include <cmath>
 #include <complex>
+
+// A timing build (compiled with -fopenmp) spreads the independent per-node loops marked below over
+// the host's cores; every output is still computed by the same operations in the same order, so
+// its results are those of the single-threaded build, bit for bit. The plain build ignores it.
+#if defined(_OPENMP)
+#include <omp.h>
+#define LKS_ORACLE_PRAGMA(x) _Pragma(#x)
+#define LKS_ORACLE_PARALLEL_FOR LKS_ORACLE_PRAGMA(omp parallel for schedule(static))
+#else
+#define LKS_ORACLE_PARALLEL_FOR
+#endif
 #include <cstdint>
 #include <algorithm>
 #include <cstring>
@@ -335,6 +346,7 @@ template <class T>
 void velocity_gradient(const Ctx& C, const Fields<T>& s, std::vector<T>* G) {
   const int d = C.d;
   G->assign((size_t)d * d * C.N, T(0));
+  LKS_ORACLE_PARALLEL_FOR
   for (size_t n = 0; n < C.N; ++n) {
     int x[3];
     coords(C, n, x);
@@ -416,11 +428,13 @@ void stencil_fwd(const Ctx& C, const Fields<T>& s, Fields<T>* o) {
   std::vector<T> G;
   velocity_gradient(C, s, &G);
   std::vector<T> f((size_t)Q * C.N);
+  LKS_ORACLE_PARALLEL_FOR
   for (size_t n = 0; n < C.N; ++n)
     for (int i = 0; i < Q; ++i) f[(size_t)i * C.N + n] = feq(C, i, s, G, n);
   o->alloc(C);
-  int x[3];
+  LKS_ORACLE_PARALLEL_FOR
   for (size_t n = 0; n < C.N; ++n) {
+    int x[3];
     coords(C, n, x);
     if (!is_interior(C, x)) continue;
     T ps = T(0);
@@ -481,7 +495,10 @@ void stencil_vjp(const Ctx& C, const Fields<T>& s, const Fields<T>& lam_star, Fi
   }
   // interior gather transpose: fbar_i(x - c_i) += lps(x)/3 + c_i . lus(x)
   std::vector<T> fbar((size_t)Q * C.N, T(0));
+  // (for a fixed i, x -> x - c_i is one-to-one on the interior: each fbar entry has one writer)
+  LKS_ORACLE_PARALLEL_FOR
   for (size_t n = 0; n < C.N; ++n) {
+    int x[3];
     coords(C, n, x);
     if (!is_interior(C, x)) continue;
     for (int i = 0; i < Q; ++i) {
@@ -493,6 +510,7 @@ void stencil_vjp(const Ctx& C, const Fields<T>& s, const Fields<T>& lam_star, Fi
   // f^eq transpose (the gradient enters f^eq linearly, so only its adjoint is needed)
   lam->alloc(C);
   std::vector<T> lG((size_t)d * d * C.N, T(0));
+  LKS_ORACLE_PARALLEL_FOR
   for (size_t n = 0; n < C.N; ++n) {
     for (int i = 0; i < Q; ++i) {
       T fb = fbar[(size_t)i * C.N + n];
@@ -769,6 +787,7 @@ void coupling_iteration(Ctx& C, const std::vector<T>& kref, const T* s_prev_iter
     }
   }
   // Brinkman update (Eq. u); p = p* is untouched
+  LKS_ORACLE_PARALLEL_FOR
   for (size_t n = 0; n < N; ++n)
     for (int a = 0; a < d; ++a) rec->u[a][n] = (star.u[a][n] + rec->kap[n] * rec->us[a][n]) / (1.0 + rec->kap[n]);
   // interpolation to the design points (Eq. u_mapping)
@@ -1656,6 +1675,15 @@ void alks_load_velocity(const Ctx& C, const double* u, Fields<double>* st) {
 extern "C" {
 
 int oracle_abi_version(void) { return 1; }
+
+// Threads the per-node loops use: 1 in the plain build, the OpenMP team size in the timing build.
+int oracle_threads(void) {
+#if defined(_OPENMP)
+  return omp_get_max_threads();
+#else
+  return 1;
+#endif
+}
 
 int oracle_sizeof_problem(void) { return (int)sizeof(OracleProblem); }
 

@@ -6,6 +6,7 @@ CPU-baseline leg call it. It takes a ``workloads.Problem`` and numpy float64 arr
 from __future__ import annotations
 
 import ctypes
+import os
 from typing import Optional
 
 import numpy as np
@@ -45,12 +46,34 @@ class OracleProblem(ctypes.Structure):
 ERRORS = {0: "ok", 1: "bad argument", 2: "body outside the domain", 3: "non-finite state", 4: "unstable (nu <= 0)"}
 
 _lib = None
+_libs = {}
+_variant = "serial"
+
+
+def set_variant(name: str) -> bool:
+    """Select the build later calls use: "serial" (the oracle), or "openmp" (the timing build: the same
+    arithmetic over the host's cores, bitwise the same results). Returns False if that build is absent."""
+    global _variant, _lib
+    _build.build()
+    path = _build.LIB_OMP if name == "openmp" else _build.LIB
+    if not os.path.exists(path):
+        return False
+    _variant = name
+    _lib = _libs.get(name)
+    return True
+
+
+def threads() -> int:
+    """Threads of the selected build's per-node loops."""
+    return int(lib().oracle_threads())
 
 
 def lib():
     global _lib
     if _lib is None:
         path = _build.build()
+        if _variant == "openmp":
+            path = _build.LIB_OMP
         L = ctypes.CDLL(path)
         dp = ctypes.POINTER(ctypes.c_double)
         ip = ctypes.POINTER(ctypes.c_int)
@@ -82,9 +105,11 @@ def lib():
         L.oracle_alks_parts.argtypes = [pp, dp, dp, dp, dp, dp, ctypes.c_double, dp, dp, dp]
         L.oracle_alks_lambda_cs.argtypes = [pp, dp, dp, dp, dp, dp, dp, dp, dp, ctypes.c_double, ctypes.c_double, dp]
         L.oracle_alks_body_step.argtypes = [pp, dp, dp, dp, dp, dp, ctypes.c_int, dp, dp, dp]
+        L.oracle_threads.argtypes = []
         if L.oracle_sizeof_problem() != ctypes.sizeof(OracleProblem):
             raise RuntimeError("oracle problem record layout mismatch")
         _lib = L
+        _libs[_variant] = L
     return _lib
 
 

@@ -102,12 +102,13 @@ int validate_problem(const lks_problem* P) {
   if (P->ckpt_policy != LKS_CKPT_STORE_ALL && P->ckpt_policy != LKS_CKPT_UNIFORM &&
       P->ckpt_policy != LKS_CKPT_BINOMIAL)
     return LKS_ERR_ARG;
-  if (P->ckpt_policy != LKS_CKPT_STORE_ALL && P->ckpt_every < 1) return LKS_ERR_ARG;
-  if (P->ckpt_policy == LKS_CKPT_BINOMIAL && P->ckpt_format != LKS_CKPT_NATIVE) return LKS_ERR_UNSUPPORTED;
+  // binomial snapshots: a count, or 0 for as many as hbm_budget_bytes holds
+  const bool bin_auto = P->ckpt_policy == LKS_CKPT_BINOMIAL && P->ckpt_every == 0 && P->hbm_budget_bytes > 0;
+  if (P->ckpt_policy != LKS_CKPT_STORE_ALL && P->ckpt_every < 1 && !bin_auto) return LKS_ERR_ARG;
   if (P->ckpt_format != LKS_CKPT_NATIVE && P->ckpt_format != LKS_CKPT_BF16 && P->ckpt_format != LKS_CKPT_FP16)
     return LKS_ERR_ARG;
-  // reduced-precision checkpoints: FP32 fields with uniform checkpoints
-  if (P->ckpt_format != LKS_CKPT_NATIVE && (P->ckpt_policy != LKS_CKPT_UNIFORM || P->field_precision != LKS_FP32))
+  // reduced-precision checkpoints: FP32 fields with uniform checkpoints or binomial snapshots
+  if (P->ckpt_format != LKS_CKPT_NATIVE && (P->ckpt_policy == LKS_CKPT_STORE_ALL || P->field_precision != LKS_FP32))
     return LKS_ERR_UNSUPPORTED;
   // 3D: boundary pairs (x = 0,1 and nx-2,nx-1; y walls likewise) must share a stencil column
   // (2D strips choose their width so that they always do)
@@ -142,6 +143,11 @@ void setup_box(Geo* gp, double design_radius, bool rotated) {
     }
     g.box_cells *= g.B[a];
   }
+}
+
+long long box_tiles(const Geo& g) {
+  const long long cy = g.dim == 2 ? kBoxCtaCellsY2D : kBoxCtaCellsY;
+  return ((g.B[0] + kBoxCtaCellsX - 1) / kBoxCtaCellsX) * ((g.B[1] + cy - 1) / cy) * (long long)g.B[2];
 }
 
 bool box_fits(const Geo& g) {
@@ -249,6 +255,7 @@ struct lks_handle {
   unsigned* ckkeys = nullptr;     // their per-plane ranges
   int nckpt = 0;
   std::vector<BinOp> bin_plan;  // binomial: the schedule (the forward's snapshots, the reverse's actions)
+  int bin_snapshots = 0;        // binomial: snapshot slots of the schedule
   long long slot_elems = 0;
   void* boxstore = nullptr;  // u* in the body box, one slab per step of the resident segment
   int nbox = 0;
@@ -293,7 +300,7 @@ struct lks_handle {
   std::map<std::string, cudaGraphExec_t> graphs;
   std::map<std::string, int> graph_kernels;
   bool box_rot_ok = true;  // buffers hold the rotated box
-  bool coop_enabled = false;  // persistent coupling kernels when the device holds their grid
+  int coop_mode = 2;  // persistent coupling kernels: 0 off, 1 on (when the device holds their grid), 2 automatic
   // what the last calls left valid: a forward, an adjoint of it (either form: dkref), the exact
   // adjoint's lambda(0) and dJ/ds(0), the paper-form adjoint's moments
   bool fwd_done = false, adj_done = false, exact_done = false;
@@ -498,6 +505,19 @@ std::vector<BinOp> binomial_plan(int n, int s) {
   return ops;
 }
 
+// Binomial snapshot slot a <- the state at src: a copy in the field precision, or BF16 / FP16 with
+// the per-plane range of the reduced formats (FP32 fields).
+int bin_snapshot(lks_handle* h, const void* src, int a, cudaStream_t st) {
+  const size_t sb = h->slot_elems * h->esz;
+  if (h->P.ckpt_format == LKS_CKPT_NATIVE) {
+    CK(cudaMemcpyAsync((char*)h->ckpt + (size_t)a * sb, src, sb, cudaMemcpyDeviceToDevice, st));
+  } else {
+    launch_ckpt_pack_q_at(h->g, (const float*)src, h->ckq, h->ckkeys, h->P.ckpt_format, a, st);
+    h->launches += 3;
+  }
+  return LKS_OK;
+}
+
 template <typename T>
 void enqueue_fwd_steps(lks_handle* h, Launcher& L, const Slots<T>& S, int nsteps, bool store_box) {
   const Geo& g = h->g;
@@ -590,10 +610,7 @@ int forward_impl(lks_handle* h, cudaStream_t st) {
         L0("init", [&](cudaStream_t s) { launch_set_step(h->ctrl, t + 1, 0, s); });
         TRY(run_graph(h, "fwd_b_" + std::to_string(n), st, [&](Launcher& L) { enqueue_fwd_steps<T>(h, L, S, n, false); }));
       }
-      if (stop.a >= 0)
-        CK(cudaMemcpyAsync((char*)h->ckpt + (size_t)stop.a * h->slot_elems * h->esz,
-                           (char*)h->pp + (t1 & 1) * h->slot_elems * h->esz, h->slot_elems * h->esz,
-                           cudaMemcpyDeviceToDevice, st));
+      if (stop.a >= 0) TRY(bin_snapshot(h, (char*)h->pp + (t1 & 1) * h->slot_elems * h->esz, stop.a, st));
       t = t1;
     }
   } else if (h->P.ckpt_policy == LKS_CKPT_STORE_ALL) {
@@ -650,8 +667,12 @@ int binomial_reverse(lks_handle* h, cudaStream_t st) {
       case LKS_BIN_RESTORE:  // a: snapshot slot (-1: the initial state)
         if (op.a < 0)
           L0("ckpt", [&](cudaStream_t x) { launch_state_from_double<T>(g, (T*)h->ring, h->init_p, h->init_u, x); });
-        else
+        else if (h->P.ckpt_format == LKS_CKPT_NATIVE)
           CK(cudaMemcpyAsync(h->ring, (char*)h->ckpt + (size_t)op.a * sb, sb, cudaMemcpyDeviceToDevice, st));
+        else
+          L0("ckpt", [&](cudaStream_t x) {
+            launch_ckpt_restore_q(g, (float*)h->ring, h->ckq, h->ckkeys, h->P.ckpt_format, op.a, x);
+          });
         break;
       case LKS_BIN_ADVANCE: {  // state(a) -> state(a + b)
         const int t0 = op.a, n = op.b;
@@ -660,8 +681,7 @@ int binomial_reverse(lks_handle* h, cudaStream_t st) {
         break;
       }
       case LKS_BIN_STORE:  // snapshot slot a <- state(b), c steps past the working pair's base
-        CK(cudaMemcpyAsync((char*)h->ckpt + (size_t)op.a * sb, (char*)h->ring + (size_t)(op.c & 1) * sb, sb,
-                           cudaMemcpyDeviceToDevice, st));
+        TRY(bin_snapshot(h, (char*)h->ring + (size_t)(op.c & 1) * sb, op.a, st));
         break;
       case LKS_BIN_REVERSE: {  // step a from state(a - 1) in the working pair (base b)
         const int t = op.a, t0 = op.b;
@@ -737,6 +757,36 @@ int adjoint_impl(lks_handle* h, double seed, cudaStream_t st) {
   return LKS_OK;
 }
 
+// Binomial schedule and its snapshot slots (native slots, or BF16 / FP16 values with per-plane
+// ranges). ckpt_every snapshots, or with ckpt_every = 0 as many as hbm_budget_bytes holds after the
+// rest of the workspace (at most n_steps - 1, the count beyond which the schedule cannot use more).
+int allocate_snapshots(lks_handle* h, size_t slot_bytes) {
+  const lks_problem& P = h->P;
+  const int NT = P.n_steps, D = h->g.dim;
+  const bool native = P.ckpt_format == LKS_CKPT_NATIVE;
+  const size_t per_q = h->slot_elems * sizeof(unsigned short), per_keys = (size_t)(D + 1) * 2 * sizeof(unsigned);
+  int s = P.ckpt_every;
+  if (s == 0) {
+    const size_t round = 256;  // each allocation is rounded up to 256 bytes
+    const size_t have = P.hbm_budget_bytes > h->bytes + 2 * round ? P.hbm_budget_bytes - h->bytes - 2 * round : 0;
+    const size_t per = native ? slot_bytes : per_q + per_keys;
+    const size_t fit = have / per;
+    s = (int)std::min<size_t>(fit, (size_t)std::max(NT - 1, 0));
+  }
+  h->bin_snapshots = s;
+  h->bin_plan = binomial_plan(NT, s);
+  h->nckpt = 0;  // the slots the schedule uses
+  for (const BinOp& op : h->bin_plan)
+    if (op.kind == LKS_BIN_FWD_SNAPSHOT || op.kind == LKS_BIN_STORE) h->nckpt = std::max(h->nckpt, op.a + 1);
+  if (h->nckpt > 0 && native) {
+    TRY(dalloc(h, &h->ckpt, (size_t)h->nckpt * slot_bytes));
+  } else if (h->nckpt > 0) {  // snapshots in BF16 / FP16 with per-plane ranges
+    TRY(dalloc(h, (void**)&h->ckq, (size_t)h->nckpt * per_q));
+    TRY(dalloc(h, (void**)&h->ckkeys, (size_t)h->nckpt * per_keys));
+  }
+  return LKS_OK;
+}
+
 template <typename T>
 int allocate(lks_handle* h) {
   Geo& g = h->g;
@@ -750,12 +800,9 @@ int allocate(lks_handle* h) {
   } else if (P.ckpt_policy == LKS_CKPT_BINOMIAL) {
     h->nring = 2;  // working pair of the reverse sweep
     h->nbox = 1;
-    h->bin_plan = binomial_plan(NT, P.ckpt_every);
-    h->nckpt = 0;  // the slots the schedule uses
-    for (const BinOp& op : h->bin_plan)
-      if (op.kind == LKS_BIN_FWD_SNAPSHOT || op.kind == LKS_BIN_STORE) h->nckpt = std::max(h->nckpt, op.a + 1);
     TRY(dalloc(h, &h->pp, 2 * slot_bytes));
-    if (h->nckpt > 0) TRY(dalloc(h, &h->ckpt, (size_t)h->nckpt * slot_bytes));
+    // the snapshots come last (allocate_snapshots): with ckpt_every = 0 their count is what the
+    // budget holds after the rest of the workspace
   } else {
     h->nring = P.ckpt_every + 1;
     h->nbox = P.ckpt_every;
@@ -795,6 +842,7 @@ int allocate(lks_handle* h) {
   TRY(dalloc(h, (void**)&h->init_u, (size_t)D * g.N * sizeof(double)));
   TRY(dalloc(h, (void**)&h->init_s, kNdofFree * sizeof(double)));
   TRY(dalloc(h, (void**)&h->objw, kNdofFree * sizeof(double)));
+  if (P.ckpt_policy == LKS_CKPT_BINOMIAL) TRY(allocate_snapshots(h, slot_bytes));
   CK(cudaMemset(h->ctrl, 0, sizeof(Ctrl)));
   CK(cudaMemset(h->L, 0, 2 * slot_bytes));
   CK(cudaMemcpy(h->objw, P.obj_weights, g.ns * sizeof(double), cudaMemcpyHostToDevice));
@@ -826,10 +874,11 @@ int refresh_box(lks_handle* h) {
   if (rotated && !h->box_rot_ok) return LKS_ERR_UNSUPPORTED;
   const int old[3] = {h->g.B[0], h->g.B[1], h->g.B[2]};
   setup_box(&h->g, h->P.design_radius, rotated);
-  if (h->coop_enabled)
-    setup_coop(&h->g, h->prec == LKS_FP64);
-  else
-    h->g.coop_fwd = h->g.coop_adj = 0;
+  h->g.coop_fwd = h->g.coop_adj = 0;
+  if (h->coop_mode != 0) setup_coop(&h->g, h->prec == LKS_FP64);
+  if (h->coop_mode == 2 && (h->g.dim != 2 || box_tiles(h->g) <= h->g.coop_fwd))
+    h->g.coop_fwd = h->g.coop_adj = 0;  // measured slower there: a grid barrier costs about twice a
+                                         // kernel boundary in a graph; only multi-wave 2D boxes gain
   if (old[0] != h->g.B[0] || old[1] != h->g.B[1] || old[2] != h->g.B[2]) clear_graphs(h);
   return LKS_OK;
 }
@@ -1250,10 +1299,10 @@ int lks_debug_sync_skip(lks_handle* h, int skip) {
 }
 
 int lks_persistent_coupling(lks_handle* h, int mode) {
-  if (!h || mode < -1 || mode > 1) return -LKS_ERR_ARG;
-  if (mode >= 0 && (mode == 1) != h->coop_enabled) {
+  if (!h || mode < -1 || mode > 2) return -LKS_ERR_ARG;
+  if (mode >= 0 && mode != h->coop_mode) {
     if (cudaDeviceSynchronize() != cudaSuccess) return -LKS_ERR_CUDA;
-    h->coop_enabled = mode == 1;
+    h->coop_mode = mode;
     const int r = refresh_box(h);
     if (r != LKS_OK) return -r;
     clear_graphs(h);
@@ -1288,6 +1337,13 @@ int lks_kernel_time(lks_handle* h, const char* family, double* ms, long long* la
 }
 
 size_t lks_workspace_bytes(const lks_handle* h) { return h ? h->bytes : 0; }
+
+int lks_checkpoint_slots(const lks_handle* h) {
+  if (!h) return -LKS_ERR_ARG;
+  if (h->P.ckpt_policy == LKS_CKPT_BINOMIAL) return h->bin_snapshots;
+  if (h->P.ckpt_policy == LKS_CKPT_UNIFORM) return h->nckpt;
+  return h->P.n_steps + 1;
+}
 
 void lks_destroy(lks_handle* h) {
   if (!h) return;

@@ -606,7 +606,7 @@ __global__ void __launch_bounds__(BoxCta<D>::threads, BoxCta<D>::min_blocks) k_c
 #pragma unroll
   for (int a = 0; a < NV; ++a) v[a] = T(0);
   couple_cell<T, D, AX>(g, kref, sk, lo, cc, dst, bs, k == K, &ctrl->status, v);
-  block_sum_partial<NV>(v, pout + block_linear() * NV, red);
+  block_sum_partial<NV, LN>(v, pout + block_linear() * NV, red);
 }
 
 // The previous iteration's finish (sum of its partials and the EOM) for coupling iteration k of
@@ -757,7 +757,7 @@ __global__ void __launch_bounds__(kDesignBlock) k_adj_design(Geo g, Ctrl* ctrl, 
     inside = adj_design_point<T, D, AX>(g, kref, scratch, sk, lo, m, m < g.ND, lane, lF, lT, dkref, v) && inside;
   }
   if (!inside) atomicOr(&ctrl->status, ST_BOX_OVERFLOW);
-  block_sum_partial<NV>(v, static_cast<typename Partial<T>::type*>(partials) + blockIdx.x * NV, red);
+  block_sum_partial<NV, LN>(v, static_cast<typename Partial<T>::type*>(partials) + blockIdx.x * NV, red);
 }
 
 // Sum of the design-point partials and the EOM reverse (adj_finish, or adj_finish_free with the
@@ -965,7 +965,7 @@ __global__ void __launch_bounds__(BoxCta<D>::threads, BoxCta<D>::min_blocks)
       couple_cell<T, D, AX>(g, kref, sk, lo, cc, dst, k == K ? bs : nullptr, k == K, &ctrl->status, v);
     }
     PT* part = static_cast<PT*>(partials) + (k & 1) * pstride;
-    block_sum_partial<NV>(v, part + blockIdx.x * NV, red);
+    block_sum_partial<NV, LN>(v, part + blockIdx.x * NV, red);
     if (!grid_sync(&ctrl->sync_bar, &ctrl->status, skip)) return;
     if (k == K && blockIdx.x != 0) return;  // the last EOM is needed only for the DOF history
     Moments m;
@@ -1039,13 +1039,15 @@ __global__ void __launch_bounds__(BoxCta<D>::threads, 1)
 #pragma unroll
     for (int a = 0; a < NV; ++a) v[a] = T(0);
     bool inside = true;
-    for (int m0 = blockIdx.x * PPC; m0 < g.ND; m0 += G * PPC) {
+    // each CTA an equal contiguous share of the design points, PPC at a time
+    const int share = (g.ND + G - 1) / G, mb = blockIdx.x * share, me = min(g.ND, mb + share);
+    for (int m0 = mb; m0 < me; m0 += PPC) {
       const int m = m0 + tid / LN;
-      inside = adj_design_point<T, D, AX>(g, kref, scratch, sk, lo, m, m < g.ND, lane, lF, lT, dkref, v) && inside;
+      inside = adj_design_point<T, D, AX>(g, kref, scratch, sk, lo, m, m < me, lane, lF, lT, dkref, v) && inside;
     }
     if (!inside) atomicOr(&ctrl->status, ST_BOX_OVERFLOW);
     PT* part = static_cast<PT*>(partials) + (k & 1) * pstride;
-    block_sum_partial<NV>(v, part + blockIdx.x * NV, red);
+    block_sum_partial<NV, LN>(v, part + blockIdx.x * NV, red);
     if (!grid_sync(&ctrl->sync_bar, &ctrl->status, skip)) return;
     const int te = (k > 1) ? t : t - 1, ke = (k > 1) ? k - 1 : K;
     if constexpr (FREE) {
@@ -1180,36 +1182,40 @@ void launch_adj_coop(const Geo& g, Ctrl* ctrl, const Dof* it, const T* kref, con
 }
 
 namespace {
-template <typename T, int D, int AX>
-int coop_ctas(const Geo& g, int threads) {
-  int dev = 0, sms = 0, per_sm_f = 0, per_sm_a = 0;
+// CTAs of a persistent kernel: the box tiles, at most as many as the device holds at once (0 if
+// the query fails or none fits).
+template <typename K>
+int coop_ctas(const Geo& g, K kernel) {
+  int dev = 0, sms = 0, per_sm = 0;
   if (cudaGetDevice(&dev) != cudaSuccess) return 0;
   if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return 0;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm_f, k_couple_coop<T, D, AX>, threads, 0) != cudaSuccess)
-    return 0;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm_a, k_adj_coop<T, D, AX>, threads, 0) != cudaSuccess)
-    return 0;
-  const int per_sm = per_sm_f < per_sm_a ? per_sm_f : per_sm_a;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, box_threads(g), 0) != cudaSuccess) return 0;
   const dim3 bg = box_grid(g);
   const long long ntiles = (long long)bg.x * bg.y * bg.z;
   const long long cap = (long long)per_sm * sms;
   return (int)(ntiles < cap ? ntiles : cap);
 }
+template <typename T, int D, int AX>
+void coop_setup(Geo* g) {
+  g->coop_fwd = coop_ctas(*g, k_couple_coop<T, D, AX>);
+  g->coop_adj = coop_ctas(*g, k_adj_coop<T, D, AX>);
+}
 template <typename T>
-int coop_ctas_any(const Geo& g) {
-  const int th = box_threads(g);
-  if (g.dim == 2) return coop_ctas<T, 2, 2>(g, th);
-  if (g.ax == 0) return coop_ctas<T, 3, 0>(g, th);
-  if (g.ax == 1) return coop_ctas<T, 3, 1>(g, th);
-  if (g.ax == 2) return coop_ctas<T, 3, 2>(g, th);
-  return coop_ctas<T, 3, AX_FREE>(g, th);
+void coop_setup_any(Geo* g) {
+  if (g->dim == 2) coop_setup<T, 2, 2>(g);
+  else if (g->ax == 0) coop_setup<T, 3, 0>(g);
+  else if (g->ax == 1) coop_setup<T, 3, 1>(g);
+  else if (g->ax == 2) coop_setup<T, 3, 2>(g);
+  else coop_setup<T, 3, AX_FREE>(g);
 }
 }  // namespace
 
 void setup_coop(Geo* g, bool fp64) {
-  const int n = fp64 ? coop_ctas_any<double>(*g) : coop_ctas_any<float>(*g);
+  if (fp64)
+    coop_setup_any<double>(g);
+  else
+    coop_setup_any<float>(g);
   cudaGetLastError();  // an occupancy query that failed leaves the per-iteration kernels in use
-  g->coop_fwd = g->coop_adj = n;
 }
 
 template <typename T>

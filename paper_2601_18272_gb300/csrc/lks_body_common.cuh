@@ -34,6 +34,7 @@ struct CellSlot {
   int j0, j1, j2, lane;
   bool active;  // inside the box
 };
+
 template <int D>
 __device__ __forceinline__ CellSlot cell_slot(const Geo& g) {
   constexpr int CX = BoxCta<D>::X, CY = BoxCta<D>::Y;

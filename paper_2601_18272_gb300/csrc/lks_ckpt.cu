@@ -43,8 +43,7 @@ __device__ __forceinline__ float from_q(unsigned short b, int fmt) {
 // checkpoint index of the step the graph node works on
 __device__ __forceinline__ int ckpt_index(const Ctrl* ctrl, int di, int every) { return (ctrl->t0 + di) / every; }
 
-__global__ void k_ckq_init(unsigned* keys, int nplanes, int every, const Ctrl* ctrl, int di) {
-  const int c = ckpt_index(ctrl, di, every);
+__device__ __forceinline__ void ckq_init_body(unsigned* keys, int nplanes, int c) {
   const int a = threadIdx.x;
   if (a < nplanes) {
     keys[(c * nplanes + a) * 2 + 0] = 0xffffffffu;  // min
@@ -52,11 +51,13 @@ __global__ void k_ckq_init(unsigned* keys, int nplanes, int every, const Ctrl* c
   }
 }
 
-__global__ void __launch_bounds__(kQB) k_ckq_range(Geo g, Slots<float> S, unsigned* keys, int every,
-                                                   const Ctrl* ctrl, int di) {
+__global__ void k_ckq_init(unsigned* keys, int nplanes, int every, const Ctrl* ctrl, int di) {
+  ckq_init_body(keys, nplanes, ckpt_index(ctrl, di, every));
+}
+
+// Range of plane a of the state v (N values per plane) into its key pair kp.
+__device__ __forceinline__ void ckq_range_body(const Geo& g, const float* __restrict__ v, unsigned* kp) {
   __shared__ float smin[kQB / 32], smax[kQB / 32];
-  const int tn = ctrl->t0 + di, c = tn / every, a = blockIdx.y, nplanes = g.dim + 1;
-  const float* __restrict__ v = slot_ptr(S, tn, ctrl->base) + (long long)a * g.N;
   float lo = __int_as_float(0x7f800000), hi = -__int_as_float(0x7f800000);
   for (long long i = blockIdx.x * (long long)kQB + threadIdx.x; i < g.N; i += (long long)gridDim.x * kQB) {
     const float x = v[i];
@@ -79,9 +80,15 @@ __global__ void __launch_bounds__(kQB) k_ckq_range(Geo g, Slots<float> S, unsign
       lo = fminf(lo, smin[q]);
       hi = fmaxf(hi, smax[q]);
     }
-    atomicMin(&keys[(c * nplanes + a) * 2 + 0], fkey(lo));
-    atomicMax(&keys[(c * nplanes + a) * 2 + 1], fkey(hi));
+    atomicMin(&kp[0], fkey(lo));
+    atomicMax(&kp[1], fkey(hi));
   }
+}
+
+__global__ void __launch_bounds__(kQB) k_ckq_range(Geo g, Slots<float> S, unsigned* keys, int every,
+                                                   const Ctrl* ctrl, int di) {
+  const int tn = ctrl->t0 + di, c = tn / every, a = blockIdx.y, nplanes = g.dim + 1;
+  ckq_range_body(g, slot_ptr(S, tn, ctrl->base) + (long long)a * g.N, keys + (c * nplanes + a) * 2);
 }
 
 // m and s of a plane from its key pair; inv = 1/s (0 for a constant plane)
@@ -92,15 +99,34 @@ __device__ __forceinline__ void plane_scale(const unsigned* kp, float* m, float*
   *inv = *s > 0.0f ? 1.0f / *s : 0.0f;
 }
 
+// Plane values v -> q[] in the reduced format with the plane's scale from its key pair kp.
+__device__ __forceinline__ void ckq_store_body(const Geo& g, const float* __restrict__ v, const unsigned* kp,
+                                               unsigned short* __restrict__ out, int fmt) {
+  float m, s, inv;
+  plane_scale(kp, &m, &s, &inv);
+  for (long long i = blockIdx.x * (long long)kQB + threadIdx.x; i < g.N; i += (long long)gridDim.x * kQB)
+    out[i] = to_q((v[i] - m) * inv, fmt);
+}
+
 __global__ void __launch_bounds__(kQB) k_ckq_store(Geo g, Slots<float> S, const unsigned* keys, unsigned short* q,
                                                    int fmt, int every, const Ctrl* ctrl, int di) {
   const int tn = ctrl->t0 + di, c = tn / every, a = blockIdx.y, nplanes = g.dim + 1;
-  float m, s, inv;
-  plane_scale(keys + (c * nplanes + a) * 2, &m, &s, &inv);
-  const float* __restrict__ v = slot_ptr(S, tn, ctrl->base) + (long long)a * g.N;
-  unsigned short* __restrict__ out = q + ((long long)c * nplanes + a) * g.N;
-  for (long long i = blockIdx.x * (long long)kQB + threadIdx.x; i < g.N; i += (long long)gridDim.x * kQB)
-    out[i] = to_q((v[i] - m) * inv, fmt);
+  ckq_store_body(g, slot_ptr(S, tn, ctrl->base) + (long long)a * g.N, keys + (c * nplanes + a) * 2,
+                 q + ((long long)c * nplanes + a) * g.N, fmt);
+}
+
+// The same three steps for the state at src into checkpoint c (the binomial snapshots, whose slots
+// and steps the host schedule names).
+__global__ void k_ckq_init_at(unsigned* keys, int nplanes, int c) { ckq_init_body(keys, nplanes, c); }
+__global__ void __launch_bounds__(kQB) k_ckq_range_at(Geo g, const float* src, unsigned* keys, int c) {
+  const int a = blockIdx.y, nplanes = g.dim + 1;
+  ckq_range_body(g, src + (long long)a * g.N, keys + (c * nplanes + a) * 2);
+}
+__global__ void __launch_bounds__(kQB) k_ckq_store_at(Geo g, const float* src, const unsigned* keys,
+                                                      unsigned short* q, int fmt, int c) {
+  const int a = blockIdx.y, nplanes = g.dim + 1;
+  ckq_store_body(g, src + (long long)a * g.N, keys + (c * nplanes + a) * 2, q + ((long long)c * nplanes + a) * g.N,
+                 fmt);
 }
 
 __global__ void __launch_bounds__(kQB) k_ckq_restore(Geo g, float* dst, const unsigned* keys,
@@ -146,6 +172,15 @@ void launch_ckpt_pack_q(const Geo& g, const Slots<float>& S, unsigned short* q, 
   const dim3 grid(q_blocks(g), nplanes);
   launch(k_ckq_range, grid, kQB, 0, st, g, S, keys, every, ctrl, di);
   launch(k_ckq_store, grid, kQB, 0, st, g, S, (const unsigned*)keys, q, fmt, every, ctrl, di);
+}
+
+void launch_ckpt_pack_q_at(const Geo& g, const float* src, unsigned short* q, unsigned* keys, int fmt, int c,
+                           cudaStream_t st) {
+  const int nplanes = g.dim + 1;
+  launch(k_ckq_init_at, 1, 32, 0, st, keys, nplanes, c);
+  const dim3 grid(q_blocks(g), nplanes);
+  launch(k_ckq_range_at, grid, kQB, 0, st, g, src, keys, c);
+  launch(k_ckq_store_at, grid, kQB, 0, st, g, src, (const unsigned*)keys, q, fmt, c);
 }
 
 void launch_ckpt_restore_q(const Geo& g, float* dst, const unsigned short* q, const unsigned* keys, int fmt, int c,

@@ -532,15 +532,17 @@ __device__ __forceinline__ void drot(F cs, F sn, const F (&r)[3], F (&out)[3]) {
 }
 
 // Deterministic block sum of NV doubles (fixed shuffle tree, fixed warp order). Result in
-// thread 0. Requires blockDim a multiple of 32 and <= 1024; smem >= 32 * NV doubles.
-template <int NV>
+// thread 0. Requires blockDim a multiple of 32 and <= 1024; smem >= 32 * NV doubles. STRIDE: only
+// lanes whose index is a multiple of STRIDE hold values (the others zeros), so the warp tree skips
+// the levels that would only add zeros.
+template <int NV, int STRIDE = 1>
 __device__ __forceinline__ void block_sum(double* v, double* smem) {
   const int tid = threadIdx.x + blockDim.x * (threadIdx.y + blockDim.y * threadIdx.z);
   const int nthreads = blockDim.x * blockDim.y * blockDim.z;
 #pragma unroll
   for (int i = 0; i < NV; ++i)
 #pragma unroll
-    for (int off = 16; off > 0; off >>= 1) v[i] += __shfl_xor_sync(0xffffffffu, v[i], off);
+    for (int off = 16; off >= STRIDE; off >>= 1) v[i] += __shfl_xor_sync(0xffffffffu, v[i], off);
   const int warp = tid >> 5, lane = tid & 31, nw = nthreads >> 5;
   if (lane == 0)
 #pragma unroll
@@ -616,20 +618,28 @@ struct Partial<double> {
   using type = double;
 };
 
-// Fixed-order block tree of NV double-float pairs (shuffles within warps, then warp 0 over the
-// warps' results); the total is in thread 0's (hi, lo). Requires blockDim a multiple of 32 and
-// smem >= 32 * NV doubles. All threads of the block must call it.
-template <int NV>
-__device__ __forceinline__ void block_df_tree(float (&hi)[NV], float (&lo)[NV], double* smem) {
-  const int tid = threadIdx.x + blockDim.x * (threadIdx.y + blockDim.y * threadIdx.z);
-  const int nthreads = blockDim.x * blockDim.y * blockDim.z;
+// Fixed-order shuffle tree of NV double-float pairs within a warp over the lanes whose index is a
+// multiple of STRIDE (the other lanes hold zeros: the levels below STRIDE would only add zeros);
+// lane 0 ends with the warp's total.
+template <int NV, int STRIDE>
+__device__ __forceinline__ void warp_df_tree(float (&hi)[NV], float (&lo)[NV]) {
 #pragma unroll
-  for (int off = 16; off > 0; off >>= 1)
+  for (int off = 16; off >= STRIDE; off >>= 1)
 #pragma unroll
     for (int i = 0; i < NV; ++i) {
       const float bh = __shfl_xor_sync(0xffffffffu, hi[i], off), bl = __shfl_xor_sync(0xffffffffu, lo[i], off);
       df_add(hi[i], lo[i], bh, bl);
     }
+}
+
+// Fixed-order block tree of NV double-float pairs (shuffles within warps, then warp 0 over the
+// warps' results); the total is in thread 0's (hi, lo). Requires blockDim a multiple of 32 and
+// smem >= 32 * NV doubles. All threads of the block must call it. STRIDE as in warp_df_tree.
+template <int NV, int STRIDE = 1>
+__device__ __forceinline__ void block_df_tree(float (&hi)[NV], float (&lo)[NV], double* smem) {
+  const int tid = threadIdx.x + blockDim.x * (threadIdx.y + blockDim.y * threadIdx.z);
+  const int nthreads = blockDim.x * blockDim.y * blockDim.z;
+  warp_df_tree<NV, STRIDE>(hi, lo);
   float2* s2 = reinterpret_cast<float2*>(smem);
   const int warp = tid >> 5, lane = tid & 31, nw = nthreads >> 5;
   if (lane == 0)
@@ -646,18 +656,14 @@ __device__ __forceinline__ void block_df_tree(float (&hi)[NV], float (&lo)[NV], 
         lo[i] = s2[lane * NV + i].y;
       }
     }
-#pragma unroll
-    for (int off = 16; off > 0; off >>= 1)
-#pragma unroll
-      for (int i = 0; i < NV; ++i) {
-        const float bh = __shfl_xor_sync(0xffffffffu, hi[i], off), bl = __shfl_xor_sync(0xffffffffu, lo[i], off);
-        df_add(hi[i], lo[i], bh, bl);
-      }
+    warp_df_tree<NV, 1>(hi, lo);
   }
 }
 
 // Block sum of NV per-thread FP32 values as double-float pairs, written by thread 0 to out[0..NV).
-template <int NV>
+// STRIDE: only lanes whose index is a multiple of STRIDE hold values (the body kernels, where one
+// of the LN threads of a cell or design point does the accumulation).
+template <int NV, int STRIDE = 1>
 __device__ __forceinline__ void block_sum_partial(float (&v)[NV], float2* out, double* smem) {
   const int tid = threadIdx.x + blockDim.x * (threadIdx.y + blockDim.y * threadIdx.z);
   float hi[NV], lo[NV];
@@ -666,38 +672,62 @@ __device__ __forceinline__ void block_sum_partial(float (&v)[NV], float2* out, d
     hi[i] = v[i];
     lo[i] = 0.0f;
   }
-  block_df_tree<NV>(hi, lo, smem);
+  block_df_tree<NV, STRIDE>(hi, lo, smem);
   if (tid == 0)
 #pragma unroll
     for (int i = 0; i < NV; ++i) out[i] = make_float2(hi[i], lo[i]);
 }
-template <int NV>
+template <int NV, int STRIDE = 1>
 __device__ __forceinline__ void block_sum_partial(double (&v)[NV], double* out, double* smem) {
-  block_sum<NV>(v, smem);
+  block_sum<NV, STRIDE>(v, smem);
   const int tid = threadIdx.x + blockDim.x * (threadIdx.y + blockDim.y * threadIdx.z);
   if (tid == 0)
 #pragma unroll
     for (int i = 0; i < NV; ++i) out[i] = v[i];
 }
 
-// The block sums the partials [nblocks][NV] in a fixed order (thread-strided, then the fixed
-// block tree); the FP64 result is in thread 0. Double-float pairs are summed with FP32
-// instructions only.
+// The block sums the partials [nblocks][NV] in a fixed order; the FP64 result is in thread 0.
+// Only as many warps as one partial per lane needs take part (the partial sums are short; a
+// tree over every thread of a large block costs more issue slots than the loads): warp w, lane l
+// sums partials w * 32 + l + 32 W j in order, then its lanes by the shuffle tree, then warp 0 the
+// W warps' totals. Double-float pairs are summed with FP32 instructions only. All threads of the
+// block must call it; it starts with a block barrier (which also orders the callers' shared-memory
+// staging before thread 0 reads it).
 template <int NV>
 __device__ __forceinline__ void block_sum_partials(const float2* partials, int nblocks, double* out, double* smem) {
   const int tid = threadIdx.x + blockDim.x * (threadIdx.y + blockDim.y * threadIdx.z);
   const int nthreads = blockDim.x * blockDim.y * blockDim.z;
+  const int warp = tid >> 5, lane = tid & 31, nw = nthreads >> 5;
+  const int W = min(nw, max(1, (nblocks + 31) / 32));
   float hi[NV], lo[NV];
 #pragma unroll
   for (int a = 0; a < NV; ++a) hi[a] = lo[a] = 0.0f;
+  __syncthreads();
+  if (warp < W) {
 #pragma unroll 4
-  for (int q = tid; q < nblocks; q += nthreads)
+    for (int q = warp * 32 + lane; q < nblocks; q += W * 32)
 #pragma unroll
-    for (int a = 0; a < NV; ++a) {
-      const float2 p = __ldcg(&partials[q * NV + a]);
-      df_add(hi[a], lo[a], p.x, p.y);
+      for (int a = 0; a < NV; ++a) {
+        const float2 p = __ldcg(&partials[q * NV + a]);
+        df_add(hi[a], lo[a], p.x, p.y);
+      }
+    warp_df_tree<NV, 1>(hi, lo);
+  }
+  if (W > 1) {
+    float2* s2 = reinterpret_cast<float2*>(smem);
+    if (warp < W && lane == 0)
+#pragma unroll
+      for (int a = 0; a < NV; ++a) s2[warp * NV + a] = make_float2(hi[a], lo[a]);
+    __syncthreads();
+    if (warp == 0) {
+#pragma unroll
+      for (int a = 0; a < NV; ++a) {
+        hi[a] = lane < W ? s2[lane * NV + a].x : 0.0f;
+        lo[a] = lane < W ? s2[lane * NV + a].y : 0.0f;
+      }
+      warp_df_tree<NV, 1>(hi, lo);
     }
-  block_df_tree<NV>(hi, lo, smem);
+  }
   if (tid == 0)
 #pragma unroll
     for (int a = 0; a < NV; ++a) out[a] = (double)hi[a] + (double)lo[a];
@@ -706,13 +736,35 @@ template <int NV>
 __device__ __forceinline__ void block_sum_partials(const double* partials, int nblocks, double* out, double* smem) {
   const int tid = threadIdx.x + blockDim.x * (threadIdx.y + blockDim.y * threadIdx.z);
   const int nthreads = blockDim.x * blockDim.y * blockDim.z;
+  const int warp = tid >> 5, lane = tid & 31, nw = nthreads >> 5;
+  const int W = min(nw, max(1, (nblocks + 31) / 32));
   double v[NV];
 #pragma unroll
   for (int a = 0; a < NV; ++a) v[a] = 0.0;
-  for (int q = tid; q < nblocks; q += nthreads)
+  __syncthreads();
+  if (warp < W) {
+    for (int q = warp * 32 + lane; q < nblocks; q += W * 32)
 #pragma unroll
-    for (int a = 0; a < NV; ++a) v[a] += __ldcg(&partials[q * NV + a]);
-  block_sum<NV>(v, smem);
+      for (int a = 0; a < NV; ++a) v[a] += __ldcg(&partials[q * NV + a]);
+#pragma unroll
+    for (int a = 0; a < NV; ++a)
+#pragma unroll
+      for (int off = 16; off > 0; off >>= 1) v[a] += __shfl_xor_sync(0xffffffffu, v[a], off);
+  }
+  if (W > 1) {
+    if (warp < W && lane == 0)
+#pragma unroll
+      for (int a = 0; a < NV; ++a) smem[warp * NV + a] = v[a];
+    __syncthreads();
+    if (warp == 0) {
+#pragma unroll
+      for (int a = 0; a < NV; ++a) {
+        v[a] = lane < W ? smem[lane * NV + a] : 0.0;
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) v[a] += __shfl_xor_sync(0xffffffffu, v[a], off);
+      }
+    }
+  }
 #pragma unroll
   for (int a = 0; a < NV; ++a) out[a] = v[a];
 }

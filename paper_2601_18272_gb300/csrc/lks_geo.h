@@ -24,4 +24,7 @@ void setup_box(Geo* g, double design_radius, bool rotated);
 // True if the body box fits every periodic extent of the grid.
 bool box_fits(const Geo& g);
 
+// Tiles of box cells of the body kernels (16 x 16 cells in 2D, 16 x 8 per plane in 3D).
+long long box_tiles(const Geo& g);
+
 }  // namespace lks

@@ -168,6 +168,9 @@ void launch_sensitivity(const Geo& g, const double* gbar, const double* dkref, d
 // c = step / every: per-plane range keys[c][plane][2] and q[c][plane][N] in BF16 or FP16.
 void launch_ckpt_pack_q(const Geo& g, const Slots<float>& S, unsigned short* q, unsigned* keys, int fmt, int every,
                         const Ctrl* ctrl, int di, cudaStream_t st);
+// The same for the state at src ((dim+1) planes of N floats) into checkpoint c.
+void launch_ckpt_pack_q_at(const Geo& g, const float* src, unsigned short* q, unsigned* keys, int fmt, int c,
+                           cudaStream_t st);
 // Restore of checkpoint c into dst ((dim+1) planes of N floats).
 void launch_ckpt_restore_q(const Geo& g, float* dst, const unsigned short* q, const unsigned* keys, int fmt, int c,
                            cudaStream_t st);

@@ -116,6 +116,7 @@ def load() -> ctypes.CDLL:
     L.lks_support_sets.argtypes = [hp, dp, vp, vp, sz]
     L.lks_debug_sync_skip.argtypes = [hp, ctypes.c_int]
     L.lks_persistent_coupling.argtypes = [hp, ctypes.c_int]
+    L.lks_checkpoint_slots.argtypes = [hp]
     L.lks_constraint.argtypes = [hp, vp, dp, vp, vp]
     L.lks_warm_start.argtypes = [hp, ctypes.c_int, vp]
     L.lks_binomial_plan.argtypes = [ctypes.c_int, ctypes.c_int, vp, ctypes.c_longlong]
@@ -153,7 +154,7 @@ def check_design_tensor(t, n_design: int, name: str = "gamma"):
 
 def problem_struct(P, precision: Optional[int] = None, ckpt_policy: Optional[int] = None,
                    ckpt_every: Optional[int] = None, ckpt_format: Optional[int] = None,
-                   n_steps: Optional[int] = None, hbm_budget_bytes: int = 0) -> lks_problem:
+                   n_steps: Optional[int] = None, hbm_budget_bytes: Optional[int] = None) -> lks_problem:
     """lks_problem from a ``workloads.Problem`` (optionally overriding the run controls)."""
     s = lks_problem()
     s.dim = P.dim
@@ -185,7 +186,7 @@ def problem_struct(P, precision: Optional[int] = None, ckpt_policy: Optional[int
     s.ckpt_format = P.ckpt_format if ckpt_format is None else ckpt_format
     if s.ckpt_format != LKS_CKPT_NATIVE and s.field_precision == LKS_FP64:
         s.ckpt_format = LKS_CKPT_NATIVE
-    s.hbm_budget_bytes = hbm_budget_bytes
+    s.hbm_budget_bytes = int(getattr(P, "hbm_budget_bytes", 0) if hbm_budget_bytes is None else hbm_budget_bytes)
     return s
 
 
@@ -318,6 +319,13 @@ def lks_workspace_bytes(h) -> int:
     return int(load().lks_workspace_bytes(h))
 
 
+def lks_checkpoint_slots(h) -> int:
+    r = int(load().lks_checkpoint_slots(h))
+    if r < 0:
+        raise LksError(-r, "lks_checkpoint_slots")
+    return r
+
+
 def lks_destroy(h):
     if h:
         load().lks_destroy(h)
@@ -352,7 +360,8 @@ def lks_debug_sync_skip(h, skip: bool):
 
 
 def lks_persistent_coupling(h, mode: int = -1) -> bool:
-    """Set (mode 1 / 0) or ask (mode -1) whether each step's coupling runs as one persistent launch."""
+    """Set (1 on, 0 off, 2 automatic) or ask (-1) whether each step's coupling runs as one persistent
+    launch; returns whether it does after the call."""
     r = int(load().lks_persistent_coupling(h, int(mode)))
     if r < 0:
         raise LksError(-r, "lks_persistent_coupling")

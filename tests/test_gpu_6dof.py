@@ -123,3 +123,56 @@ def test_turbine3d_6dof_adjoint_from_rotated_state():
         r = gpu_run(P, g, p0, u0, s0, precision=32, ckpt_policy=CKPT_UNIFORM, ckpt_every=1, ckpt_format=fmt)
         assert abs(r["J"] - G["J"]) <= 1e-4 * abs(G["J"]), fmt
         assert rel(r["dJdgamma"], G["dJdgamma"]) <= 1e-3, fmt
+
+
+@pytest.mark.parametrize("fmt", ["bf16", "fp16"])
+def test_free_binomial_reduced_snapshots(fmt):
+    """Binomial checkpointing with BF16 / FP16 snapshots (the six-DOF workload's memory policy): the
+    forward is the FP32 run's bit for bit (snapshots are copies on the side); the gradient carries the
+    quantisation of the restored and re-stored states and stays within the reduced-precision tolerance
+    of the uniform policy (1.2e-3 BF16, 1e-4 FP16) of the oracle's."""
+    from workloads import CKPT_BF16, CKPT_FP16
+    P, g = b6(nt=9)
+    p0, u0, s0 = perturbed_state6(P)
+    G = O.gradient(P, g, p0, u0, s0)
+    code, tol = (CKPT_BF16, 1.2e-3) if fmt == "bf16" else (CKPT_FP16, 1e-4)
+    r32 = gpu_run(P, g, p0, u0, s0, precision=32, ckpt_policy=CKPT_BINOMIAL, ckpt_every=2)
+    rq = gpu_run(P, g, p0, u0, s0, precision=32, ckpt_policy=CKPT_BINOMIAL, ckpt_every=2, ckpt_format=code)
+    assert rq["J"] == r32["J"]
+    np.testing.assert_array_equal(rq["hist"], r32["hist"])
+    assert rel(r32["dJdgamma"], G["dJdgamma"]) <= 1e-3
+    assert rel(rq["dJdgamma"], G["dJdgamma"]) <= tol
+
+
+def test_binomial_snapshots_sized_by_the_budget():
+    """ckpt_every = 0 with a budget: the binomial schedule gets as many BF16 snapshots as the budget
+    holds after the rest of the workspace; the workspace stays within the budget and the gradient is
+    that of an explicit handle with the same snapshot count, bit for bit."""
+    import torch
+    from paper_2601_18272_gb300 import lks
+    from paper_2601_18272_gb300.lks import Solver
+    from workloads import CKPT_BF16
+    P, g = b6(nt=12)
+    gam = torch.tensor(g, dtype=torch.float64, device="cuda")
+    S3 = Solver(P, precision=32, ckpt_policy=CKPT_BINOMIAL, ckpt_every=3, ckpt_format=CKPT_BF16)
+    budget = lks.lks_workspace_bytes(S3.handle)
+    S3.close()
+    Sa = Solver(P, precision=32, ckpt_policy=CKPT_BINOMIAL, ckpt_every=0, ckpt_format=CKPT_BF16,
+                hbm_budget_bytes=budget)
+    n = lks.lks_checkpoint_slots(Sa.handle)
+    assert 2 <= n <= 3
+    assert lks.lks_workspace_bytes(Sa.handle) <= budget
+    Sn = Solver(P, precision=32, ckpt_policy=CKPT_BINOMIAL, ckpt_every=n, ckpt_format=CKPT_BF16)
+    out = []
+    for S in (Sa, Sn):
+        try:
+            J = S.forward(gam)
+            S.adjoint(1.0)
+            d = torch.empty_like(gam)
+            S.sensitivity(d)
+            torch.cuda.synchronize()
+            out.append((J, d.cpu().numpy()))
+        finally:
+            S.close()
+    assert out[0][0] == out[1][0]
+    assert np.array_equal(out[0][1], out[1][1])

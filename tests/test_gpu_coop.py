@@ -1,9 +1,9 @@
 """The persistent coupling kernels (one cooperative launch per time step for the N_itr coupling
 iterations of Sec. 3.1, and one for their reverse) through the C ABI.
 
-- They are the default wherever the device holds their grid (2D, 3D single axis, six DOFs).
-- They agree with the per-iteration kernels to rounding (FP64), and both with the oracle (the parity
-  tests of the other files run the default, persistent, path).
+- They run wherever the device holds their grid (2D, 3D single axis, six DOFs) when asked for, and
+  by default for 2D bodies whose box has more tiles than the persistent grid has CTAs.
+- They agree with the per-iteration kernels to rounding (FP64), and both with the oracle.
 - Their grid barriers are bounded: with the test hook that makes the first CTA skip its arrivals, the
   other CTAs' waits run out after one second, the forward or the adjoint returns LKS_ERR_TIMEOUT, and
   the handle stays usable: the next calls give the same results as before, bit for bit.
@@ -59,7 +59,7 @@ def test_persistent_matches_per_iteration_kernels_and_oracle(name, make, state):
         assert not lks.lks_persistent_coupling(S.handle, 0)
         Jk, dk = _grad(S, g, p0, u0, s0)
         hk = S.dof_history()
-        assert lks.lks_persistent_coupling(S.handle, 1)
+        assert lks.lks_persistent_coupling(S.handle, 2) is False  # a small box: one launch per iteration
     finally:
         S.close()
     assert abs(Jc - Jk) <= 1e-13 * abs(Jk)
@@ -105,3 +105,18 @@ def test_grid_barrier_timeout_is_reported_and_recoverable(precision):
         S.close()
     assert J1 == J0
     assert np.array_equal(d1, d0)
+
+
+def test_automatic_choice_on_a_large_2d_box():
+    """The default (automatic) mode takes the persistent kernels for the 1024x512 / 256x256 workload's
+    box (576 tiles) and the per-iteration kernels for the 512x256 / 128x128 one (144 tiles)."""
+    from paper_2601_18272_gb300 import lks
+    from paper_2601_18272_gb300.lks import Solver
+    from workloads import config
+    for idx, expect in ((3, True), (2, False)):
+        P, _ = config(idx)
+        S = Solver(P.replace(n_steps=4, ckpt_every=2))
+        try:
+            assert lks.lks_persistent_coupling(S.handle, -1) is expect, idx
+        finally:
+            S.close()

@@ -363,3 +363,26 @@ def test_terminal_adjoint_is_the_derivative_of_the_terminal_functional():
     dJ = O.forward_cs_terminal(P, g, p0, u0, s0, pT, uT, sT, v)
     assert abs(dJ - G["dJdgamma"] @ v) <= 1e-11 * abs(dJ)
     assert np.abs(G["dJdgamma"] - first["dJdgamma"]).max() > 1e-6 * np.abs(first["dJdgamma"]).max()
+
+
+def test_openmp_timing_build_is_bitwise_the_oracle():
+    """The OpenMP timing build of the oracle (used only to time the CPU baseline on all host cores)
+    gives the single-threaded oracle's results bit for bit: it only spreads independent per-node
+    loops, each output computed by the same operations in the same order."""
+    from tests.problems import body2d, body3d, perturbed_state
+    if not O.set_variant("openmp"):
+        pytest.skip("no OpenMP build on this host")
+    try:
+        outs = {}
+        for variant in ("openmp", "serial"):
+            assert O.set_variant(variant)
+            for name, (P, g) in (("2d", body2d(nt=4)), ("3d", body3d(nt=3))):
+                p0, u0, s0 = perturbed_state(P)
+                outs[(variant, name)] = O.gradient(P, g, p0, u0, s0)
+        for name in ("2d", "3d"):
+            a, b = outs[("openmp", name)], outs[("serial", name)]
+            assert a["J"] == b["J"]
+            for k in ("dJdgamma", "lam_p0", "lam_u0", "lam_dof0"):
+                assert np.array_equal(a[k], b[k]), (name, k)
+    finally:
+        O.set_variant("serial")

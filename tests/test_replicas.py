@@ -31,9 +31,9 @@ def _rank(rank: int, port: int, out):
 
 def test_replica_totals_take_the_slowest_rank_and_all_launches():
     port = _free_port()
-    with mp.Manager() as m:
+    ctx = mp.get_context("spawn")  # no fork of a process that may hold threads (an OpenMP oracle build)
+    with ctx.Manager() as m:
         out = m.dict()
-        ctx = mp.get_context("spawn")
         procs = [ctx.Process(target=_rank, args=(r, port, out)) for r in range(2)]
         for p in procs:
             p.start()

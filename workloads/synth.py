@@ -169,6 +169,7 @@ class Problem:
     proj_eta: float = 0.5               # Heaviside projection threshold
     v_min: float = 0.25                 # minimum volume ratio of the constraint
     cyclic_order: int = 1               # cyclic expansion of the design about the rotation axis: 1, 2, 4
+    hbm_budget_bytes: int = 0           # workspace limit (0: none); binomial with ckpt_every 0 fills it
 
     @property
     def n_cells(self) -> int:
@@ -272,13 +273,13 @@ def _cfg5(**kw) -> tuple:
     M, _ = mass_properties(g, (nd, nd, nd), 3, 0)
     It = inertia_tensor(g, (nd, nd, nd))
     # six DOFs (free rotation); the design domain is the ball of the sphere mask, radius nd/2 - 2;
-    # J = h_x(N_t), the angular momentum about the flow axis
+    # J = h_x(N_t), the angular momentum about the flow axis.
     P = Problem(dim=3, nx=256, ny=128, nz=128, ndx=nd, ndy=nd, ndz=nd, body_centre=(96.0, 64.0, 64.0),
                 rot_axis=ROT_FREE, dof_mask=DOF_TX | DOF_TY | DOF_TZ | DOF_ROT, mass=M, inertia=It[0],
                 nu=_nu_from_re(0.05, nd, 300), u_in=0.05, dp=0.0,
                 bc=(BC_INFLOW_OUTFLOW, BC_PERIODIC, BC_PERIODIC), kappa_max=1.0, q=0.1,
                 weight_kind=W_COS4, n_steps=10000, n_itr=5, obj_weights=_obj(6, 21), field_precision=32,
-                ckpt_policy=CKPT_UNIFORM, ckpt_every=200, ckpt_format=CKPT_BF16,
+                ckpt_policy=CKPT_BINOMIAL, ckpt_every=0, ckpt_format=CKPT_BF16, hbm_budget_bytes=150 * 10**9,
                 name="turbine3d_256x128x128_d96_6dof", seed=seed, inertia_tensor=It,
                 design_radius=nd / 2.0 - 2.0)
     return P, g
