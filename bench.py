@@ -300,7 +300,8 @@ def gradient_throughput(dev, flush, peak: float, index: int, n_steps: int = 0, p
     ms = _timed(stream, flush, lambda: run(S, grad))
     ms_fwd = _timed(stream, flush, lambda: S.forward(gamma))
     out = {"workload": P.name, "value": P.n_cells * P.n_steps / (ms / 1000.0), "unit": UNIT, "ms_per_gradient": ms,
-           "n_steps": P.n_steps, "dtype": "f32", "checkpoints": _ckpt_desc(P),
+           "n_steps": P.n_steps, "dtype": "f32",
+           "checkpoints": _ckpt_desc(P, lks.lks_checkpoint_slots(S.handle)),
            "workspace_gb": lks.lks_workspace_bytes(S.handle) / 1e9,
            "persistent_coupling": lks.lks_persistent_coupling(S.handle, -1),
            "forward": _fwd_roofline(P, ms_fwd, peak)}
@@ -329,10 +330,11 @@ def gradient_throughput(dev, flush, peak: float, index: int, n_steps: int = 0, p
     return out
 
 
-def _ckpt_desc(P) -> str:
+def _ckpt_desc(P, slots: int) -> str:
     fmt = {0: "fp32", 1: "bf16", 2: "fp16"}.get(P.ckpt_format, "?")
     if P.ckpt_policy == 2:
-        return f"binomial, {P.ckpt_every} snapshots, {fmt}"
+        budget = f" (as many as {P.hbm_budget_bytes / 1e9:.0f} GB hold)" if P.ckpt_every == 0 else ""
+        return f"binomial, {slots} snapshots{budget}, {fmt}"
     if P.ckpt_policy == 0:
         return "every state stored"
     return f"uniform every {P.ckpt_every}, {fmt}"
