@@ -1332,6 +1332,21 @@ void alks_feq_field(const Ctx& C, const AdjMoments& a, const Fields<double>& st,
     }
 }
 
+// The outlet multiplier of u~ (reading above). A test may plant another rule in its place, to check
+// that the tests of the paper-form adjoint tell the rules apart: 1 copies u~ (factor 1), 2 zeroes
+// it, 3 takes the complement max(u_x, 0) / (nu + max(u_x, 0)), 4 doubles the outflow speed.
+int g_alks_outlet_rule = 0;
+double alks_outlet_factor(double nu, double ux) {
+  const double up = std::max(ux, 0.0);
+  switch (g_alks_outlet_rule) {
+    case 1: return 1.0;
+    case 2: return 0.0;
+    case 3: return up / (nu + up);
+    case 4: return nu / (nu + 2.0 * up);
+    default: return nu / (nu + up);
+  }
+}
+
 // Boundary values of the adjoint moments (reading above), in the forward's phase order: walls zero
 // u~ and copy p~, s~; the inlet copies p~ (inflow/outflow) or zeroes it (pressure), zeroes u~
 // (inflow/outflow) or copies it (pressure); the outlet zeroes p~ and scales the inward u~ by
@@ -1369,7 +1384,7 @@ void alks_boundaries(const Ctx& C, const Fields<double>& st, AdjMoments* o) {
     const bool u_fixed = (bcx == BC_INFLOW_OUTFLOW) && inlet;
     // outlet: the outflow condition of the convective adjoint, (u . n) u~ + nu du~/dn = 0, with a
     // one-sided difference: u~(outlet) = nu / (nu + max(u_x, 0)) u~(inward neighbour)
-    const double fac = inlet ? 1.0 : C.P.nu / (C.P.nu + std::max(st.u[0][n], 0.0));
+    const double fac = inlet ? 1.0 : alks_outlet_factor(C.P.nu, st.u[0][n]);
     o->p[n] = p_fixed ? 0.0 : o->p[m];
     for (int a = 0; a < d; ++a) o->u[a][n] = u_fixed ? 0.0 : fac * o->u[a][m];
     copy_s(n, m);
@@ -1675,6 +1690,14 @@ void alks_load_velocity(const Ctx& C, const double* u, Fields<double>* st) {
 extern "C" {
 
 int oracle_abi_version(void) { return 1; }
+
+// Test hook: the outlet rule of the paper-form adjoint (0: the reading; 1..4: planted mistakes, see
+// alks_outlet_factor). Returns the previous rule.
+int oracle_set_alks_outlet_rule(int rule) {
+  const int prev = g_alks_outlet_rule;
+  g_alks_outlet_rule = rule;
+  return prev;
+}
 
 // Threads the per-node loops use: 1 in the plain build, the OpenMP team size in the timing build.
 int oracle_threads(void) {

@@ -63,6 +63,11 @@ def set_variant(name: str) -> bool:
     return True
 
 
+def set_alks_outlet_rule(rule: int) -> int:
+    """Test hook: plant another outlet rule in the paper-form adjoint (0 restores the reading)."""
+    return int(lib().oracle_set_alks_outlet_rule(int(rule)))
+
+
 def threads() -> int:
     """Threads of the selected build's per-node loops."""
     return int(lib().oracle_threads())
@@ -106,6 +111,7 @@ def lib():
         L.oracle_alks_lambda_cs.argtypes = [pp, dp, dp, dp, dp, dp, dp, dp, dp, ctypes.c_double, ctypes.c_double, dp]
         L.oracle_alks_body_step.argtypes = [pp, dp, dp, dp, dp, dp, ctypes.c_int, dp, dp, dp]
         L.oracle_threads.argtypes = []
+        L.oracle_set_alks_outlet_rule.argtypes = [ctypes.c_int]
         if L.oracle_sizeof_problem() != ctypes.sizeof(OracleProblem):
             raise RuntimeError("oracle problem record layout mismatch")
         _lib = L
