@@ -60,8 +60,10 @@ typedef enum lks_status {
   LKS_ERR_ORDER = 7,        /* adjoint or sensitivity requested before a forward / adjoint */
   LKS_ERR_CUDA = 8,         /* a CUDA runtime call failed */
   LKS_ERR_UNSUPPORTED = 9,  /* valid but not supported by the library (e.g. grid/tile shape) */
-  LKS_ERR_TIMEOUT = 10      /* a grid barrier of the persistent coupling kernels waited longer than one
-                             * second; the kernels returned early and the results of the call are void */
+  LKS_ERR_TIMEOUT = 10      /* a bounded wait on the device (a grid barrier of the persistent coupling
+                             * kernels, or a tile copy of the row-streamed 3D stencils) waited longer
+                             * than one second; the kernels returned early and the results of the call
+                             * are void */
 } lks_status;
 
 enum { LKS_D2Q9 = 9, LKS_D3Q15 = 15 };                   /* velocity sets (Sec. 2.2) */
@@ -171,8 +173,8 @@ LKS_API int lks_set_initial_state(lks_handle* h, const double* p_host, const dou
 LKS_API int lks_forward(lks_handle* h, const double* gamma_dev, double* J_host, void* stream);
 
 /* Reverse sweep (Algorithm 1, adjoint loop) seeded with dJ = seed. Enqueued on the stream; with the
- * persistent coupling kernels (lks_uses_persistent_coupling) it then synchronises the stream once to
- * read the device status word. Requires a prior lks_forward (else LKS_ERR_ORDER).
+ * persistent coupling kernels (lks_persistent_coupling) or the row-streamed 3D stencils
+ * (lks_stencil_form = 1) it then synchronises the stream once to read the device status word. Requires a prior lks_forward (else LKS_ERR_ORDER).
  * Errors: LKS_ERR_TIMEOUT, LKS_ERR_CUDA. */
 LKS_API int lks_adjoint(lks_handle* h, double seed, void* stream);
 
@@ -310,6 +312,14 @@ LKS_API int lks_step_noalloc(const lks_problem* problem, const double* gamma_dev
 /* State copies the handle keeps for the reverse sweep: binomial snapshot slots (as chosen for
  * ckpt_every = 0), uniform checkpoints, or n_steps + 1 stored states; -LKS_ERR_ARG for NULL. */
 LKS_API int lks_checkpoint_slots(const lks_handle* h);
+
+/* Form of the 3D predictor and transpose kernels the handle launches: 1 for the row-streamed FP32
+ * kernels (a 64-column window fed by one TMA box of 16 rows per plane, packed FP32x2 arithmetic;
+ * taken for FP32 fields on grids periodic in y and z with nx a multiple of 4 and at least 64 and
+ * ny at least 16), 0 for the general kernels (2D problems, FP64 fields, walls in y or z, other
+ * grids); -LKS_ERR_ARG for NULL. Both forms compute the predictor of Sec. 2.2 and its exact
+ * transpose. */
+LKS_API int lks_stencil_form(const lks_handle* h);
 
 /* Bytes of device workspace held by the handle. */
 LKS_API size_t lks_workspace_bytes(const lks_handle* h);

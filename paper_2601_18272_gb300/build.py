@@ -17,7 +17,7 @@ CSRC = os.path.join(HERE, "csrc")
 OBJ = os.path.join(HERE, "_build")
 LIBDIR = os.path.join(HERE, "lib")
 LIB = os.path.join(LIBDIR, "liblks_gb300.so")
-SOURCES = ["lks_api.cu", "lks_stencil.cu", "lks_stencil3d.cu", "lks_body.cu", "lks_ckpt.cu", "lks_design.cu", "lks_alks.cu", "lks_noalloc.cu"]
+SOURCES = ["lks_api.cu", "lks_stencil.cu", "lks_stencil3d.cu", "lks_stencil3d_q.cu", "lks_body.cu", "lks_ckpt.cu", "lks_design.cu", "lks_alks.cu", "lks_noalloc.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-fvisibility=hidden",
          "-I" + os.path.join(ROOT, "include")]

@@ -899,7 +899,7 @@ const char* lks_status_string(int s) {
     case LKS_ERR_ORDER: return "call order (forward before adjoint before sensitivity)";
     case LKS_ERR_CUDA: return "CUDA runtime error";
     case LKS_ERR_UNSUPPORTED: return "unsupported configuration";
-    case LKS_ERR_TIMEOUT: return "a grid barrier wait timed out";
+    case LKS_ERR_TIMEOUT: return "a bounded wait on the device timed out";
     default: return "unknown status";
   }
 }
@@ -1025,7 +1025,8 @@ int lks_adjoint(lks_handle* h, double seed, void* stream) {
   h->adj_done = h->exact_done = false;
   int r = (h->prec == LKS_FP64) ? adjoint_impl<double>(h, seed, st) : adjoint_impl<float>(h, seed, st);
   if (r != LKS_OK) return r;
-  if (h->g.coop_adj > 0) {  // a grid barrier that timed out is reported through the status word
+  // a grid barrier or tile copy whose wait timed out is reported through the status word
+  if (h->g.coop_adj > 0 || lks_stencil_form(h) == 1) {
     int status = 0;
     CK(cudaMemcpyAsync(&status, (const char*)h->ctrl + offsetof(Ctrl, status), sizeof(int), cudaMemcpyDeviceToHost,
                        st));
@@ -1343,6 +1344,11 @@ int lks_checkpoint_slots(const lks_handle* h) {
   if (h->P.ckpt_policy == LKS_CKPT_BINOMIAL) return h->bin_snapshots;
   if (h->P.ckpt_policy == LKS_CKPT_UNIFORM) return h->nckpt;
   return h->P.n_steps + 1;
+}
+
+int lks_stencil_form(const lks_handle* h) {
+  if (!h) return -LKS_ERR_ARG;
+  return (h->prec == LKS_FP32 && stencil3d_q_fits(h->g)) ? 1 : 0;
 }
 
 void lks_destroy(lks_handle* h) {

@@ -72,6 +72,15 @@ void launch_stencil3d_fwd(const Geo& g, const Slots<T>& S, const Ctrl* ctrl, int
 template <typename T>
 void launch_stencil3d_adj(const Geo& g, const Slots<T>& S, T* Lb, long long lstride, const Ctrl* ctrl, int di,
                           cudaStream_t st);
+// Row-streamed FP32 forms (TMA-fed, packed FP32x2) for grids periodic in y and z with nx a multiple
+// of 4 and at least 64 and ny at least 16: true if this geometry takes them. The launchers return false (launching
+// nothing) where it does not, or where a tensor map cannot be encoded. A copy whose wait runs out
+// (about a second) sets ST_SYNC_TIMEOUT in ctrl->status.
+bool stencil3d_q_fits(const Geo& g);
+void prepare_stencil3d_q();
+bool launch_stencil3d_q_fwd(const Geo& g, const Slots<float>& S, const Ctrl* ctrl, int di, cudaStream_t st);
+bool launch_stencil3d_q_adj(const Geo& g, const Slots<float>& S, float* Lb, long long lstride, const Ctrl* ctrl,
+                            int di, cudaStream_t st);
 
 // Design preparation: kappa^ref from gamma (Eq. brinkman_coefficient), moments.
 template <typename T>

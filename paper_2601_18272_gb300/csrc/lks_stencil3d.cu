@@ -704,10 +704,14 @@ template <typename T>
 void prepare_stencil3d() {
   cudaFuncSetAttribute(k_stencil3d<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(Fwd3Smem<T>));
   cudaFuncSetAttribute(k_stencil3d_adj<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(Adj3Smem<T>));
+  if (sizeof(T) == 4) prepare_stencil3d_q();
 }
 
 template <typename T>
 void launch_stencil3d_fwd(const Geo& g, const Slots<T>& S, const Ctrl* ctrl, int di, cudaStream_t st) {
+  if constexpr (sizeof(T) == 4) {
+    if (launch_stencil3d_q_fwd(g, S, ctrl, di, st)) return;
+  }
   const dim3 grid((g.n[0] + TX - 1) / TX, (g.n[1] + TY - 1) / TY, z_chunks(g, sizeof(T) == 4 ? 2 : 1));
   launch(k_stencil3d<T>, grid, NT, sizeof(Fwd3Smem<T>), st, g, S, ctrl, di);
 }
@@ -715,6 +719,9 @@ void launch_stencil3d_fwd(const Geo& g, const Slots<T>& S, const Ctrl* ctrl, int
 template <typename T>
 void launch_stencil3d_adj(const Geo& g, const Slots<T>& S, T* Lb, long long lstride, const Ctrl* ctrl, int di,
                           cudaStream_t st) {
+  if constexpr (sizeof(T) == 4) {
+    if (launch_stencil3d_q_adj(g, S, Lb, lstride, ctrl, di, st)) return;
+  }
   const dim3 grid((g.n[0] + TX - 1) / TX, (g.n[1] + TY - 1) / TY, z_chunks(g, sizeof(T) == 4 ? 2 : 1));
   launch(k_stencil3d_adj<T>, grid, NT, sizeof(Adj3Smem<T>), st, g, S, Lb, lstride, ctrl, di);
 }

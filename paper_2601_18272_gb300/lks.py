@@ -117,6 +117,7 @@ def load() -> ctypes.CDLL:
     L.lks_debug_sync_skip.argtypes = [hp, ctypes.c_int]
     L.lks_persistent_coupling.argtypes = [hp, ctypes.c_int]
     L.lks_checkpoint_slots.argtypes = [hp]
+    L.lks_stencil_form.argtypes = [hp]
     L.lks_constraint.argtypes = [hp, vp, dp, vp, vp]
     L.lks_warm_start.argtypes = [hp, ctypes.c_int, vp]
     L.lks_binomial_plan.argtypes = [ctypes.c_int, ctypes.c_int, vp, ctypes.c_longlong]
@@ -323,6 +324,13 @@ def lks_checkpoint_slots(h) -> int:
     r = int(load().lks_checkpoint_slots(h))
     if r < 0:
         raise LksError(-r, "lks_checkpoint_slots")
+    return r
+
+
+def lks_stencil_form(h) -> int:
+    r = int(load().lks_stencil_form(h))
+    if r < 0:
+        raise LksError(-r, "lks_stencil_form")
     return r
 
 
