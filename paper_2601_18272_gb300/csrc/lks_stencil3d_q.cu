@@ -180,8 +180,12 @@ struct QMaps {
 template <bool PX>
 __global__ void __launch_bounds__(QT, 1)
     k_stencil3d_q(const __grid_constant__ QMaps tm, Geo g, Slots<float> S, Ctrl* ctrl, int di) {
-  extern __shared__ unsigned char q_smem[];
-  QFwdSmem& s = *reinterpret_cast<QFwdSmem*>((reinterpret_cast<size_t>(q_smem) + 127) & ~size_t(127));
+  extern __shared__ __align__(128) unsigned char q_smem[];
+  QFwdSmem& s = *reinterpret_cast<QFwdSmem*>(q_smem);  // shared-space addresses throughout
+  if (smem_u32(q_smem) & 127u) {  // the copy engine needs 128-byte aligned slots
+    if (threadIdx.x == 0) atomicOr(&ctrl->status, ST_SYNC_TIMEOUT);
+    return;
+  }
   const int tid = threadIdx.x, w = tid >> 5, lane = tid & 31;
   const int t = ctrl->t0 + di, base = ctrl->base;
   int sslot = (t - 1 - base) % S.nslots;
@@ -427,8 +431,12 @@ template <bool PX>
 __global__ void __launch_bounds__(QT, 1)
     k_stencil3d_adj_q(const __grid_constant__ QMaps tl, const __grid_constant__ CUtensorMap tu, Geo g,
                       Slots<float> S, float* Lb, long long lstride, Ctrl* ctrl, int di) {
-  extern __shared__ unsigned char q_smem[];
-  QAdjSmem& s = *reinterpret_cast<QAdjSmem*>((reinterpret_cast<size_t>(q_smem) + 127) & ~size_t(127));
+  extern __shared__ __align__(128) unsigned char q_smem[];
+  QAdjSmem& s = *reinterpret_cast<QAdjSmem*>(q_smem);  // shared-space addresses throughout
+  if (smem_u32(q_smem) & 127u) {  // the copy engine needs 128-byte aligned slots
+    if (threadIdx.x == 0) atomicOr(&ctrl->status, ST_SYNC_TIMEOUT);
+    return;
+  }
   const int tid = threadIdx.x, w = tid >> 5, lane = tid & 31;
   const int t = ctrl->t0 - di, base = ctrl->base;
   int sslot = (t - 1 - base) % S.nslots;
@@ -780,7 +788,7 @@ int q_chunks(const Geo& g) {
   return best;
 }
 
-constexpr size_t kFwdSmem = sizeof(QFwdSmem) + 128, kAdjSmem = sizeof(QAdjSmem) + 128;
+constexpr size_t kFwdSmem = sizeof(QFwdSmem), kAdjSmem = sizeof(QAdjSmem);
 
 }  // namespace
 
