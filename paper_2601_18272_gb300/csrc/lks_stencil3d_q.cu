@@ -53,11 +53,30 @@ __device__ __forceinline__ float2 sub2(float2 a, float2 b) { return __ffma2_rn(b
 __device__ __forceinline__ float2 mul2(float2 a, float2 b) { return __fmul2_rn(a, b); }
 __device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
 
-// The value of a two-column quantity at x - 1 and at x + 1 (lane L holds columns 2L, 2L + 1 of the
-// window; lane 0's left and lane 31's right neighbours are not in the window and come back wrong,
-// which only the unused edge columns see).
-__device__ __forceinline__ float2 left_of(float2 v) { return make_float2(__shfl_up_sync(kFull, v.y, 1), v.x); }
-__device__ __forceinline__ float2 right_of(float2 v) { return make_float2(v.y, __shfl_down_sync(kFull, v.x, 1)); }
+// Neighbours along x of two-column quantities (lane L holds columns 2L, 2L + 1 of the window; lane
+// 0's left and lane 31's right neighbours are not in the window and come back wrong, which only the
+// unused edge columns see). The combinations are formed by scalar operations straight into the
+// result pair: a packed operation on a shifted value would first move it into a register pair.
+// D_x v = v(x + 1) - v(x - 1), S_x v = v(x + 1) + v(x - 1):
+__device__ __forceinline__ float2 dx2(float2 v) {
+  const float pv = __shfl_up_sync(kFull, v.y, 1), nv = __shfl_down_sync(kFull, v.x, 1);
+  return make_float2(v.y - pv, nv - v.x);
+}
+__device__ __forceinline__ float2 sx2(float2 v) {
+  const float pv = __shfl_up_sync(kFull, v.y, 1), nv = __shfl_down_sync(kFull, v.x, 1);
+  return make_float2(v.y + pv, nv + v.x);
+}
+// r(x + 1) + l(x - 1):
+__device__ __forceinline__ float2 rl2(float2 r, float2 l) {
+  const float nr = __shfl_down_sync(kFull, r.x, 1), pl = __shfl_up_sync(kFull, l.y, 1);
+  return make_float2(r.y + pl, nr + l.x);
+}
+// r(x + 1) + l(x - 1) and r(x + 1) - l(x - 1):
+__device__ __forceinline__ void rl2_sd(float2 r, float2 l, float2& sum, float2& diff) {
+  const float nr = __shfl_down_sync(kFull, r.x, 1), pl = __shfl_up_sync(kFull, l.y, 1);
+  sum = make_float2(r.y + pl, nr + l.x);
+  diff = make_float2(r.y - pl, nr - l.x);
+}
 
 // ---- mbarrier and TMA (inline PTX) -------------------------------------------------------------
 __device__ __forceinline__ unsigned smem_u32(const void* p) { return (unsigned)__cvta_generic_to_shared(p); }
@@ -274,9 +293,9 @@ __global__ void __launch_bounds__(QT, 1)
         const float2 Du = s.r1[6 + a][w + 1][lane], Dd = s.r1[6 + a][w - 1][lane];
         const float2 X1v = add2(U0[a], add2(Su, Sd));
         const float2 dysz = sub2(Su, Sd), sydz = add2(Du, Dd);
-        G[a][0] = sub2(right_of(X1v), left_of(X1v));
-        G[a][1] = add2(sub2(Uu, Ud), add2(right_of(dysz), left_of(dysz)));
-        G[a][2] = add2(Dz[a], add2(right_of(sydz), left_of(sydz)));
+        G[a][0] = dx2(X1v);
+        G[a][1] = add2(sub2(Uu, Ud), sx2(dysz));
+        G[a][2] = add2(Dz[a], sx2(sydz));
       }
       const float2 ux = U0[0], uy = U0[1], uz = U0[2];
       const float2 usq = fma2(uz, uz, fma2(uy, uy, mul2(ux, ux)));
@@ -310,10 +329,11 @@ __global__ void __launch_bounds__(QT, 1)
       }
       if (row_out) {  // the node's own values along x (plane zr) and z (planes zr + 1, zr - 1)
         const float2 f0 = mul2(a0, f2(2.0f / 9.0f));
-        const float2 L1 = left_of(add2(tx, bx)), R2 = right_of(sub2(tx, bx));
+        float2 sx, dx;  // f_2 (c = -x) from x + 1 and f_1 (c = +x) from x - 1: sum and difference
+        rl2_sd(sub2(tx, bx), add2(tx, bx), sx, dx);
         const float2 f5 = add2(tz, bz), f6 = sub2(tz, bz);
-        Ac[0] = add2(Ac[0], add2(f0, add2(L1, R2)));
-        Ac[1] = add2(Ac[1], sub2(L1, R2));
+        Ac[0] = add2(Ac[0], add2(f0, sx));
+        Ac[1] = sub2(Ac[1], dx);
         Ap[0] = add2(Ap[0], f5);
         Ap[3] = add2(Ap[3], f5);
         Am[0] = add2(Am[0], f6);
@@ -330,17 +350,18 @@ __global__ void __launch_bounds__(QT, 1)
         // (s_x, s_z) groups: from the row below (s_y = +1) and the row above (s_y = -1)
         const float2 dP = s.r2[2 + 2 * iz][w - 1][lane], dM = s.r2[3 + 2 * iz][w - 1][lane];
         const float2 uP = s.r2[6 + 2 * iz][w + 1][lane], uM = s.r2[7 + 2 * iz][w + 1][lane];
-        const float2 Apl = left_of(add2(dP, uP)), Bpl = left_of(sub2(dP, uP));     // s_x = +1: from x - 1
-        const float2 Amr = right_of(add2(dM, uM)), Bmr = right_of(sub2(dM, uM));  // s_x = -1: from x + 1
-        const float2 sA = add2(Apl, Amr), dA = sub2(Apl, Amr), sB = add2(Bpl, Bmr);
+        // s_x = +1 values from x - 1, s_x = -1 values from x + 1
+        float2 sA, mA;  // mA: the s_x = -1 values less the s_x = +1 ones
+        rl2_sd(add2(dM, uM), add2(dP, uP), sA, mA);
+        const float2 sB = rl2(sub2(dM, uM), sub2(dP, uP));
         if (iz == 0) {  // s_z = +1: output plane zr + 1
           Ap[0] = add2(Ap[0], sA);
-          Ap[1] = add2(Ap[1], dA);
+          Ap[1] = sub2(Ap[1], mA);
           Ap[2] = add2(Ap[2], sB);
           Ap[3] = add2(Ap[3], sA);
         } else {  // s_z = -1: output plane zr - 1
           Am[0] = add2(Am[0], sA);
-          Am[1] = add2(Am[1], dA);
+          Am[1] = sub2(Am[1], mA);
           Am[2] = add2(Am[2], sB);
           Am[3] = sub2(Am[3], sA);
         }
@@ -597,24 +618,24 @@ __global__ void __launch_bounds__(QT, 1)
       const float2 gpm = s.r1[6][w - 1][lane], gmm = s.r1[7][w - 1][lane];
       const float2 dpm = s.r1[8][w - 1][lane], dmm = s.r1[9][w - 1][lane];
       // x pass: s_x = +1 values from x + 1, s_x = -1 values from x - 1
-      const float2 RA = right_of(add2(gpp, gpm)), LA = left_of(add2(gmp, gmm));
-      const float2 RB = right_of(sub2(gpp, gpm)), LB = left_of(sub2(gmp, gmm));
-      const float2 RD = right_of(add2(dpp, dpm)), LD = left_of(add2(dmp, dmm));
-      const float2 RE = right_of(sub2(dpp, dpm)), LE = left_of(sub2(dmp, dmm));
-      const float2 Xp = right_of(add2(a0_, b0_[0])), Xm = left_of(sub2(a0_, b0_[0]));
+      float2 Pc, Uxc, Uyc, Sxyc, Uzc, Sxzc, sX, dX;
+      rl2_sd(add2(gpp, gpm), add2(gmp, gmm), Pc, Uxc);
+      rl2_sd(sub2(gpp, gpm), sub2(gmp, gmm), Uyc, Sxyc);
+      rl2_sd(add2(dpp, dpm), add2(dmp, dmm), Uzc, Sxzc);
+      const float2 Syzc = rl2(sub2(dpp, dpm), sub2(dmp, dmm));
+      rl2_sd(add2(a0_, b0_[0]), sub2(a0_, b0_[0]), sX, dX);
       const float2 Zp = add2(ap_, bp_[2]), Zm = sub2(am_, bm_[2]);
-      const float2 Pc = add2(RA, LA);
-      const float2 sX = add2(Xp, Xm), sY = add2(Yp, Ym), sZ = add2(Zp, Zm);
+      const float2 sY = add2(Yp, Ym), sZ = add2(Zp, Zm);
       P = fma2(w0, a0_, fma2(w1, add2(add2(sX, sY), sZ), mul2(w3, Pc)));
-      U[0] = fma2(w1, sub2(Xp, Xm), mul2(w3, sub2(RA, LA)));
-      U[1] = fma2(w1, sub2(Yp, Ym), mul2(w3, add2(RB, LB)));
-      U[2] = fma2(w1, sub2(Zp, Zm), mul2(w3, add2(RD, LD)));
+      U[0] = fma2(w1, dX, mul2(w3, Uxc));
+      U[1] = fma2(w1, sub2(Yp, Ym), mul2(w3, Uyc));
+      U[2] = fma2(w1, sub2(Zp, Zm), mul2(w3, Uzc));
       Sm[0] = fma2(w1, sX, mul2(w3, Pc));
       Sm[1] = fma2(w1, sY, mul2(w3, Pc));
       Sm[2] = fma2(w1, sZ, mul2(w3, Pc));
-      Sm[3] = mul2(w3, sub2(RB, LB));
-      Sm[4] = mul2(w3, sub2(RD, LD));
-      Sm[5] = mul2(w3, add2(RE, LE));
+      Sm[3] = mul2(w3, Sxyc);
+      Sm[4] = mul2(w3, Sxzc);
+      Sm[5] = mul2(w3, Syzc);
       if (!on0 || !on1) {  // the moments are zero off the grid (open x)
         if (!on0) {
           P.x = 0.0f;
@@ -663,11 +684,11 @@ __global__ void __launch_bounds__(QT, 1)
         const float2 sySaz = add2(Su[IZ[a]], Sd[IZ[a]]);
         const float2 Sax = Sm[IX[a]], Saz = Sm[IZ[a]];
         // plane zr: -(D_x S_ax + D_y S_ay)
-        const float2 h0 = sub2(sub2(left_of(Sax), right_of(Sax)), dySay);
+        const float2 h0 = sub2(f2(0.0f), add2(dx2(Sax), dySay));
         // planes zr +- 1: +-S_az - (D_x S_y S_ax + S_x D_y S_ay) +- S_x S_y S_az
         const float2 m = add2(sySax, dySay), n = sub2(dySay, sySax);
-        const float2 hp = add2(Saz, add2(right_of(sub2(sySaz, m)), left_of(sub2(sySaz, n))));
-        const float2 hm = sub2(f2(0.0f), add2(Saz, add2(right_of(add2(m, sySaz)), left_of(add2(n, sySaz)))));
+        const float2 hp = add2(Saz, rl2(sub2(sySaz, m), sub2(sySaz, n)));
+        const float2 hm = sub2(f2(0.0f), add2(Saz, rl2(add2(m, sySaz), add2(n, sySaz))));
         qc[1 + a] = fma2(kA, h0, qc[1 + a]);
         qp[1 + a] = fma2(kA, hp, qp[1 + a]);
         qm[1 + a] = fma2(kA, hm, qm[1 + a]);
