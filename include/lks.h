@@ -264,6 +264,14 @@ LKS_API int lks_support_sets(lks_handle* h, const double* s_host, int* box_host,
  * device. Errors: LKS_ERR_ARG, LKS_ERR_CUDA. */
 LKS_API int lks_debug_sync_skip(lks_handle* h, int skip);
 
+/* Test hook of the bounded copy waits of the row-streamed 3D stencils (lks_stencil_form = 1):
+ * skip != 0 makes every CTA of those kernels withhold the copy of the third plane of its chunk, so
+ * its wait runs out (after one second), the CTA waits (bounded) for the copies it did issue and
+ * returns, and the forward or adjoint returns LKS_ERR_TIMEOUT; later launches of the same call
+ * return at once. skip = 0 restores normal operation. Synchronises the device.
+ * Errors: LKS_ERR_ARG, LKS_ERR_CUDA. */
+LKS_API int lks_debug_copy_skip(lks_handle* h, int skip);
+
 /* How the handle runs each step's N_itr coupling iterations (Sec. 3.1) and their reverse: mode 1 as
  * one persistent cooperative launch per step (grid barriers between the iterations) when the device
  * holds its grid, mode 0 as one launch per iteration (with the finish kernels), mode 2 (the default)

@@ -1291,12 +1291,26 @@ int lks_support_sets(lks_handle* h, const double* s_host, int* box_host, long lo
   return LKS_OK;
 }
 
-int lks_debug_sync_skip(lks_handle* h, int skip) {
-  if (!h) return LKS_ERR_ARG;
-  const int v = skip ? 1 : 0;
+namespace {
+// Sets or clears one bit of the control block's test-hook word.
+int set_skip_bit(lks_handle* h, int bit, int on) {
+  int v = 0;
   CK(cudaDeviceSynchronize());
+  CK(cudaMemcpy(&v, (char*)h->ctrl + offsetof(Ctrl, sync_skip), sizeof(int), cudaMemcpyDeviceToHost));
+  v = on ? (v | bit) : (v & ~bit);
   CK(cudaMemcpy((char*)h->ctrl + offsetof(Ctrl, sync_skip), &v, sizeof(int), cudaMemcpyHostToDevice));
   return LKS_OK;
+}
+}  // namespace
+
+int lks_debug_sync_skip(lks_handle* h, int skip) {
+  if (!h) return LKS_ERR_ARG;
+  return set_skip_bit(h, 1, skip);
+}
+
+int lks_debug_copy_skip(lks_handle* h, int skip) {
+  if (!h) return LKS_ERR_ARG;
+  return set_skip_bit(h, 2, skip);
 }
 
 int lks_persistent_coupling(lks_handle* h, int mode) {

@@ -938,7 +938,7 @@ __global__ void __launch_bounds__(BoxCta<D>::threads, BoxCta<D>::min_blocks)
   __shared__ Dof sd[3];  // s(t-1), the current iterate s^(k-1), the next iterate
   if (*(volatile int*)&ctrl->status & ST_SYNC_TIMEOUT) return;  // an earlier launch gave up
   const int t = ctrl->t0 + di, base = ctrl->base, K = g.K;
-  const bool skip = ctrl->sync_skip != 0;
+  const bool skip = (ctrl->sync_skip & 1) != 0;
   Dof* row = it + (long long)(t - 1) * (K + 1);
   double* sdw = reinterpret_cast<double*>(sd);
   const int tid = threadIdx.x;
@@ -1011,7 +1011,7 @@ __global__ void __launch_bounds__(BoxCta<D>::threads, 1)
   __shared__ Dof s_e[FREE ? 2 : 1];
   if (*(volatile int*)&ctrl->status & ST_SYNC_TIMEOUT) return;
   const int t = ctrl->t0 - di, base = ctrl->base, K = g.K;
-  const bool skip = ctrl->sync_skip != 0;
+  const bool skip = (ctrl->sync_skip & 1) != 0;
   const Dof* row = it + (long long)(t - 1) * (K + 1);
   const int tid = threadIdx.x, lane = tid % LN;
   T lF[3], lT[3];

@@ -110,7 +110,8 @@ struct Ctrl {
   int status;             // ST_* bits
   int prep_status;        // ST_NONFINITE if the design field held a NaN or an infinity (k_prep)
   unsigned sync_bar;      // grid barrier word of the cooperative coupling kernels (grid_sync)
-  int sync_skip;          // test hook: non-zero makes CTA 0 skip its barrier arrivals (the waits time out)
+  int sync_skip;          // test hooks: bit 0 makes CTA 0 skip its grid-barrier arrivals, bit 1 makes the
+                          // row-streamed 3D stencils withhold one plane's copy (the waits time out)
   unsigned count[CNT_N];  // last-block counters, one per kernel family
   double lam_prev[kNdofFree];  // adjoint: direct EOM part of dJ/ds(t-1)
   double lam_F[3];        // adjoint: dJ/dF of the iteration being reversed

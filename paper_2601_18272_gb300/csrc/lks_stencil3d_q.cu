@@ -205,6 +205,8 @@ __global__ void __launch_bounds__(QT, 1)
     if (threadIdx.x == 0) atomicOr(&ctrl->status, ST_SYNC_TIMEOUT);
     return;
   }
+  if (ctrl->status & ST_SYNC_TIMEOUT) return;  // an earlier wait of this call timed out: results are void
+  const bool skip_copy = (ctrl->sync_skip & 2) != 0;  // test hook: withhold the copy of plane 2
   const int tid = threadIdx.x, w = tid >> 5, lane = tid & 31;
   const int t = ctrl->t0 + di, base = ctrl->base;
   int sslot = (t - 1 - base) % S.nslots;
@@ -235,6 +237,7 @@ __global__ void __launch_bounds__(QT, 1)
   const bool store_row = row_out && lane >= 1 && lane <= 30;
 
   auto issue = [&](int jq) {  // thread 0: plane za - 2 + jq into slot jq % QRF
+    if (skip_copy && jq == 2) return;  // its wait runs out; no copy is left in flight
     const int sl = jq % QRF, zq = wrapi(za - 2 + jq, nz);
     mbar_expect_tx(&s.bar[sl], plane_bytes);
     tma_load_5d(&s.ring[sl][0][0][0], &tm.main, xs, 0, rows.ys, zq, sslot, &s.bar[sl]);
@@ -247,6 +250,7 @@ __global__ void __launch_bounds__(QT, 1)
   auto read_plane = [&](int jq, float2& p, float2 (&u)[3]) -> bool {  // this row's values of plane jq
     const int sl = jq % QRF;
     const bool ok = mbar_wait_bounded(&s.bar[sl], (unsigned)(jq / QRF) & 1u);
+    if (!ok) atomicOr(&ctrl->status, ST_SYNC_TIMEOUT);
     const float* row = &s.ring[sl][srow][0][0];
     if (!edge) {
       p = *reinterpret_cast<const float2*>(row + 2 * lane);
@@ -458,6 +462,8 @@ __global__ void __launch_bounds__(QT, 1)
     if (threadIdx.x == 0) atomicOr(&ctrl->status, ST_SYNC_TIMEOUT);
     return;
   }
+  if (ctrl->status & ST_SYNC_TIMEOUT) return;  // an earlier wait of this call timed out: results are void
+  const bool skip_copy = (ctrl->sync_skip & 2) != 0;  // test hook: withhold the copy of plane 2
   const int tid = threadIdx.x, w = tid >> 5, lane = tid & 31;
   const int t = ctrl->t0 - di, base = ctrl->base;
   int sslot = (t - 1 - base) % S.nslots;
@@ -485,6 +491,7 @@ __global__ void __launch_bounds__(QT, 1)
   const int bx = g.bc[0];
 
   auto issue = [&](int jq) {
+    if (skip_copy && jq == 2) return;  // test hook: its wait runs out; no copy is left in flight
     const int sl = jq % QR, zq = wrapi(za - 2 + jq, nz);
     mbar_expect_tx(&s.bar[sl], plane_bytes);
     tma_load_5d(&s.ring[sl][0][0][0], &tl.main, xs, 0, rows.ys, zq, lslot, &s.bar[sl]);

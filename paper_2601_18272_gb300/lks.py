@@ -115,6 +115,7 @@ def load() -> ctypes.CDLL:
     L.lks_dof_count.argtypes = [ctypes.POINTER(lks_problem)]
     L.lks_support_sets.argtypes = [hp, dp, vp, vp, sz]
     L.lks_debug_sync_skip.argtypes = [hp, ctypes.c_int]
+    L.lks_debug_copy_skip.argtypes = [hp, ctypes.c_int]
     L.lks_persistent_coupling.argtypes = [hp, ctypes.c_int]
     L.lks_checkpoint_slots.argtypes = [hp]
     L.lks_stencil_form.argtypes = [hp]
@@ -365,6 +366,11 @@ def lks_support_sets(h, s: np.ndarray):
 def lks_debug_sync_skip(h, skip: bool):
     """Test hook: the persistent kernels' first CTA skips its grid-barrier arrivals (waits time out)."""
     _check(load().lks_debug_sync_skip(h, int(bool(skip))), "lks_debug_sync_skip")
+
+
+def lks_debug_copy_skip(h, skip: bool):
+    """Test hook: withhold one plane's tile copy in the row-streamed 3D stencils (the waits time out)."""
+    _check(load().lks_debug_copy_skip(h, int(bool(skip))), "lks_debug_copy_skip")
 
 
 def lks_persistent_coupling(h, mode: int = -1) -> bool:

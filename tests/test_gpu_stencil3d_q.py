@@ -96,3 +96,47 @@ def test_general_form_where_the_row_streamed_one_does_not_apply():
             assert lks.lks_stencil_form(S.handle) == 0
         finally:
             S.close()
+
+
+def test_tile_copy_timeout_is_reported_and_recoverable():
+    """A tile copy that never arrives (test hook: each CTA withholds one plane's copy) makes the
+    bounded waits run out: the forward and the adjoint return LKS_ERR_TIMEOUT, and after the hook is
+    cleared the handle gives the same gradient as before, bit for bit."""
+    import time
+    import torch
+    from paper_2601_18272_gb300 import lks
+    from paper_2601_18272_gb300.lks import LksError, Solver
+    P, g = CASES_Q[0][1]()
+    P = P.replace(n_steps=2)
+    p0, u0, s0 = perturbed_state(P)
+    S = Solver(P, precision=32, ckpt_policy=CKPT_STORE_ALL)
+    try:
+        assert lks.lks_stencil_form(S.handle) == 1
+        S.set_initial_state(p0, u0, s0)
+        gam = torch.tensor(g, dtype=torch.float64, device="cuda")
+
+        def grad():
+            J = S.forward(gam)
+            S.adjoint(1.0)
+            d = torch.empty_like(gam)
+            S.sensitivity(d)
+            torch.cuda.synchronize()
+            return J, d.cpu().numpy()
+
+        J0, d0 = grad()
+        lks.lks_debug_copy_skip(S.handle, True)
+        t0 = time.perf_counter()
+        with pytest.raises(LksError, match="LKS_ERR_TIMEOUT"):
+            S.forward(gam)
+        assert time.perf_counter() - t0 < 30.0
+        lks.lks_debug_copy_skip(S.handle, False)
+        assert S.forward(gam) == J0
+        lks.lks_debug_copy_skip(S.handle, True)
+        with pytest.raises(LksError, match="LKS_ERR_TIMEOUT"):
+            S.adjoint(1.0)
+        lks.lks_debug_copy_skip(S.handle, False)
+        J1, d1 = grad()
+        assert J1 == J0
+        np.testing.assert_array_equal(d1, d0)
+    finally:
+        S.close()
