@@ -30,7 +30,7 @@ CASES_Q = [
     ("inflow-64x20x16", lambda: body3d(nx=64, ny=20, nz=16, centre=(20.3, 9.6, 7.9), nt=3)),
     ("periodic-68x26x18-rotz", lambda: body3d(nx=68, ny=26, nz=18, centre=(40.3, 13.2, 8.8), bc=(BC_PERIODIC,) * 3,
                                               rot_axis=2, nt=3)),
-    ("pressure-124x18x14-rotx", lambda: body3d(nx=124, ny=18, nz=14, centre=(60.4, 8.7, 6.6),
+    ("pressure-124x20x14-rotx", lambda: body3d(nx=124, ny=20, nz=14, centre=(60.4, 9.7, 6.6),
                                                bc=(BC_PRESSURE, BC_PERIODIC, BC_PERIODIC), rot_axis=0, nt=3)),
     ("inflow-188x40x21", lambda: body3d(nx=188, ny=40, nz=21, centre=(90.3, 19.6, 10.4), nt=2)),
 ]
