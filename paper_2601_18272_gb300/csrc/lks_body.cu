@@ -142,6 +142,101 @@ __device__ __forceinline__ void couple_finish(const Geo& g, const Moments* mom, 
     if (fabs(nx->s[a] - s0.s[a]) > (double)g.margin) *status |= ST_BOX_OVERFLOW;
 }
 
+// couple_finish on the lanes of one warp (one rotation axis): lane a < 3 the force, velocity,
+// position and FP32 views of axis a, lane 3 the torque, angular velocity, angle and cos/sin, lane 4
+// the unused DOF entries, so the FP64 chain on the critical path is the rotation's alone. Each
+// quantity is computed by the same operations in the same order as couple_finish, so the iterate is
+// the same to the bit. Every lane of the warp calls it; s (the cell sums) is taken from lane 0; the
+// status bits are returned to every lane.
+template <int D, int AX>
+__device__ __forceinline__ int couple_finish_lanes(const Geo& g, const Moments& mom, const Dof& s0, const Dof& sk,
+                                                   const double* s_in, Dof* nx, int lane) {
+  constexpr int NS = D + 1;
+  double s[NS];
+#pragma unroll
+  for (int i = 0; i < NS; ++i) s[i] = __shfl_sync(0xffffffffu, s_in[i], 0);
+  constexpr int b = Axes<AX>::B, c = Axes<AX>::C;
+  const double cs = sk.cs, sn = sk.sn, om = sk.s[7];
+  const double K1[3] = {mom.K1[0], mom.K1[1], mom.K1[2]};
+  const double ug[3] = {sk.s[3], sk.s[4], sk.s[5]};
+  int st = 0;
+  if (lane < 3) {
+    const int a = lane;
+    double x = s0.s[a], u = s0.s[3 + a];
+    if (a < D) {
+      double K1d[3];
+      drot<AX>(cs, sn, K1, K1d);
+      const double F = s[a] - (mom.K0 * ug[a] + om * K1d[a]);
+      if (!isfinite(F)) st |= ST_NONFINITE;
+      if (g.dof_mask & (1 << a)) {
+        u = s0.s[3 + a] + F * g.inv_mass;
+        x = s0.s[a] + u;
+      }
+      if (fabs(x - s0.s[a]) > (double)g.margin) st |= ST_BOX_OVERFLOW;
+    }
+    nx->s[a] = x;
+    nx->s[3 + a] = u;
+    const double fl = floor(x);
+    nx->xi[a] = (int)fl;
+    nx->xf[a] = (float)(x - fl);
+    nx->ug[a] = (float)u;
+  } else if (lane == 3) {
+    double K1r[3];
+    rot<AX>(cs, sn, K1, K1r);
+    const double Tq = s[D] - (K1r[b] * ug[c] - K1r[c] * ug[b]) - om * mom.K2p;
+    if (!isfinite(Tq)) st |= ST_NONFINITE;
+    double w = s0.s[7], th = s0.s[6];
+    if (g.dof_mask & DOF_ROT) {
+      w = s0.s[7] + Tq * g.inv_inertia;
+      th = s0.s[6] + w;
+    }
+    nx->s[6] = th;
+    nx->s[7] = w;
+    double ncs, nsn;
+    rotate_angle(s0, th - s0.s[6], &ncs, &nsn);
+    nx->cs = ncs;
+    nx->sn = nsn;
+    nx->om = (float)w;
+    nx->csf = (float)ncs;
+    nx->snf = (float)nsn;
+  } else if (lane == 4) {
+#pragma unroll
+    for (int a = kNdofAxis; a < kNdofFree; ++a) nx->s[a] = 0.0;
+  }
+  return __reduce_or_sync(0xffffffffu, st);
+}
+
+// The one-block finish kernels' part (one rotation axis): stage s0 = base[0] and sk = base[kprev]
+// in shared memory, sum the partials, run couple_finish_lanes on warp 0 and store the new iterate
+// to out (and to out2 if not null). All threads of the block call it.
+template <int D, int AX, typename PT, int NV>
+__device__ __forceinline__ void finish_lanes_to(const Geo& g, Ctrl* ctrl, const Moments* __restrict__ mom,
+                                                const Dof* base, int kprev, const PT* pin, int nparts, double* red,
+                                                Dof (&sdd)[3], Dof* out, Dof* out2) {
+  constexpr int DW = sizeof(Dof) / sizeof(double);
+  const int tid = threadIdx.x;
+  double* sdw = reinterpret_cast<double*>(sdd);
+  if (tid < DW) {
+    sdw[tid] = reinterpret_cast<const double*>(base)[tid];
+    sdw[DW + tid] = reinterpret_cast<const double*>(base + kprev)[tid];
+  }
+  Moments m;
+  if (tid < 32) m = *mom;
+  double sm[NV];
+#pragma unroll
+  for (int a = 0; a < NV; ++a) sm[a] = 0.0;
+  block_sum_partials<NV>(pin, nparts, sm, red);  // its barriers order the staging copies
+  if (tid < 32) {
+    const int st = couple_finish_lanes<D, AX>(g, m, sdd[0], sdd[1], sm, &sdd[2], tid);
+    if (tid == 0 && st) ctrl->status |= st;
+  }
+  __syncthreads();
+  if (tid < DW) {
+    reinterpret_cast<double*>(out)[tid] = sdw[2 * DW + tid];
+    if (out2) reinterpret_cast<double*>(out2)[tid] = sdw[2 * DW + tid];
+  }
+}
+
 // The same with free rotation from the cell sums s[0..5] = (F_cell, T_cell).
 __device__ __forceinline__ void couple_finish_free(const Geo& g, const Moments* mom, const Dof& s0, const Dof& sk,
                                                    const double* s, Dof* nx, int* status) {
@@ -574,11 +669,15 @@ __global__ void __launch_bounds__(BoxCta<D>::threads, BoxCta<D>::min_blocks) k_c
       sdw[2 * DW + tid] = gk[tid];
     }
     Moments m;
-    if (tid == 0) m = *mom;
+    if (tid < 32) m = *mom;
     double sm[NV];
     block_sum_partials<NV>(pin, nparts, sm, red);  // its barriers order the staging copies
     int st = 0;
-    if (tid == 0) couple_finish_any<D, AX>(g, &m, sd[0], sd[2], sm, &sd[1], &st);
+    if constexpr (AX == AX_FREE) {
+      if (tid == 0) couple_finish_any<D, AX>(g, &m, sd[0], sd[2], sm, &sd[1], &st);
+    } else {
+      if (tid < 32) st = couple_finish_lanes<D, AX>(g, m, sd[0], sd[2], sm, &sd[1], tid);
+    }
     __syncthreads();
     if (k == 1 && tid < DW) sdw[tid] = sdw[DW + tid];  // s(t-1) is the new iterate
     if (blockIdx.x == 0 && blockIdx.y == 0 && blockIdx.z == 0) {
@@ -627,22 +726,27 @@ __global__ void __launch_bounds__(BoxCta<D>::threads) k_couple_pre(Geo g, Ctrl* 
   Dof* prow = (k > 1) ? row : row - (K + 1);
   const int kp = (k > 1) ? k - 1 : K;
   const PT* pin = static_cast<const PT*>(partials) + ((idx - 1) & 1) * pstride;
-  Dof s0, sk;
-  Moments m;
-  if (threadIdx.x == 0) {
-    s0 = prow[0];
-    sk = prow[kp - 1];
-    m = *mom;
-  }
-  double sm[NV];
-  block_sum_partials<NV>(pin, nparts, sm, red);
-  if (threadIdx.x == 0) {
-    Dof nx;
-    int st = 0;
-    couple_finish_any<D, AX>(g, &m, s0, sk, sm, &nx, &st);
-    if (st) ctrl->status |= st;
-    prow[kp] = nx;
-    if (kp == K) row[0] = nx;
+  if constexpr (AX == AX_FREE) {
+    Dof s0, sk;
+    Moments m;
+    if (threadIdx.x == 0) {
+      s0 = prow[0];
+      sk = prow[kp - 1];
+      m = *mom;
+    }
+    double sm[NV];
+    block_sum_partials<NV>(pin, nparts, sm, red);
+    if (threadIdx.x == 0) {
+      Dof nx;
+      int st = 0;
+      couple_finish_any<D, AX>(g, &m, s0, sk, sm, &nx, &st);
+      if (st) ctrl->status |= st;
+      prow[kp] = nx;
+      if (kp == K) row[0] = nx;
+    }
+  } else {
+    __shared__ Dof sdd[3];  // s0, s^(kp-1), the new iterate
+    finish_lanes_to<D, AX, PT, NV>(g, ctrl, mom, prow, kp - 1, pin, nparts, red, sdd, prow + kp, kp == K ? row : nullptr);
   }
 }
 
@@ -659,22 +763,27 @@ __global__ void __launch_bounds__(kFinishThreads, 1) k_couple_last(Geo g, Ctrl* 
   Dof* row = it + (long long)(t_last - 1) * (K + 1);
   const long long idx = (long long)(t_last - 1) * K + (K - 1);
   const PT* pin = static_cast<const PT*>(partials) + (idx & 1) * pstride;
-  Dof s0, sk;
-  Moments m;
-  if (threadIdx.x == 0) {
-    s0 = row[0];
-    sk = row[K - 1];
-    m = *mom;
-  }
-  double sm[NV];
-  block_sum_partials<NV>(pin, nparts, sm, red);
-  if (threadIdx.x == 0) {
-    Dof nx;
-    int st = 0;
-    couple_finish_any<D, AX>(g, &m, s0, sk, sm, &nx, &st);
-    if (st) ctrl->status |= st;
-    row[K] = nx;
-    it[(long long)t_last * (K + 1)] = nx;
+  if constexpr (AX == AX_FREE) {
+    Dof s0, sk;
+    Moments m;
+    if (threadIdx.x == 0) {
+      s0 = row[0];
+      sk = row[K - 1];
+      m = *mom;
+    }
+    double sm[NV];
+    block_sum_partials<NV>(pin, nparts, sm, red);
+    if (threadIdx.x == 0) {
+      Dof nx;
+      int st = 0;
+      couple_finish_any<D, AX>(g, &m, s0, sk, sm, &nx, &st);
+      if (st) ctrl->status |= st;
+      row[K] = nx;
+      it[(long long)t_last * (K + 1)] = nx;
+    }
+  } else {
+    __shared__ Dof sdd[3];
+    finish_lanes_to<D, AX, PT, NV>(g, ctrl, mom, row, K - 1, pin, nparts, red, sdd, row + K, it + (long long)t_last * (K + 1));
   }
 }
 
@@ -969,13 +1078,18 @@ __global__ void __launch_bounds__(BoxCta<D>::threads, BoxCta<D>::min_blocks)
     if (!grid_sync(&ctrl->sync_bar, &ctrl->status, skip)) return;
     if (k == K && blockIdx.x != 0) return;  // the last EOM is needed only for the DOF history
     Moments m;
-    if (tid == 0) m = *mom;
+    if (tid < 32) m = *mom;
     double sm[NV];
     block_sum_partials<NV>(part, G, sm, red);
-    if (tid == 0) {
-      int st = 0;
-      couple_finish_any<D, AX>(g, &m, sd[0], sd[1], sm, &sd[2], &st);
-      if (st && blockIdx.x == 0) atomicOr(&ctrl->status, st);
+    if constexpr (AX == AX_FREE) {
+      if (tid == 0) {
+        int st = 0;
+        couple_finish_any<D, AX>(g, &m, sd[0], sd[1], sm, &sd[2], &st);
+        if (st && blockIdx.x == 0) atomicOr(&ctrl->status, st);
+      }
+    } else if (tid < 32) {
+      const int st = couple_finish_lanes<D, AX>(g, m, sd[0], sd[1], sm, &sd[2], tid);
+      if (tid == 0 && st && blockIdx.x == 0) atomicOr(&ctrl->status, st);
     }
     __syncthreads();
     if (tid < DW) {
