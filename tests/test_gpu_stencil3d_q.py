@@ -3,8 +3,9 @@ and at least 64) with the oracle: the forward fields after the march, the adjoin
 (which pass through every transposed predictor of the sweep), J and dJ/dgamma.
 
 The grids give several 64-column windows with a ragged last one (the window after the grid's end
-holds wrapped or boundary columns), several 12-row tiles with a ragged last one, z chunks of
-unequal length, and the three x boundary kinds (inflow/outflow, pressure, periodic).
+holds wrapped or boundary columns), several 12-row tiles with a last one aligned to the grid's end,
+the fewest rows the form takes (16: both tiles wrap across y = 0), z chunks of unequal length, and
+the three x boundary kinds (inflow/outflow, pressure, periodic).
 
 Tolerances: FP32 fields carry about 1e-7 relative rounding per operation; after a few steps of
 the coupled march the field errors measured about 1e-7 (forward) and 1e-6 (adjoint), so the bars
@@ -33,6 +34,9 @@ CASES_Q = [
     ("pressure-124x20x14-rotx", lambda: body3d(nx=124, ny=20, nz=14, centre=(60.4, 9.7, 6.6),
                                                bc=(BC_PRESSURE, BC_PERIODIC, BC_PERIODIC), rot_axis=0, nt=3)),
     ("inflow-188x40x21", lambda: body3d(nx=188, ny=40, nz=21, centre=(90.3, 19.6, 10.4), nt=2)),
+    # the fewest rows the form takes: both row tiles wrap across y = 0 (one below, one above)
+    ("periodic-64x16x16-rotz", lambda: body3d(nx=64, ny=16, nz=16, centre=(30.2, 7.7, 8.1), bc=(BC_PERIODIC,) * 3,
+                                              rot_axis=2, nt=3)),
 ]
 
 
