@@ -336,7 +336,7 @@ __device__ __forceinline__ void adj_cell_work(const Geo& g, const T* __restrict_
 // takes one row, or in 3D one plane, of the support window; every thread of the warp must call it);
 // lane 0 finishes the point. Design points outside the design domain do nothing. Returns false if
 // the support window left the body box.
-template <typename T, int D, int AX>
+template <typename T, int D, int AX, bool COHERENT>
 __device__ __forceinline__ bool adj_design_point(const Geo& g, const T* __restrict__ kref, const T* scratch,
                                                  const Dof& sk, const int (&lo)[3], int m, bool valid_m, int lane,
                                                  const T (&lF)[3], const T (&lT)[3], double* __restrict__ dkref,
@@ -433,13 +433,16 @@ __device__ __forceinline__ bool adj_design_point(const Geo& g, const T* __restri
         continue;
       }
       const long long bl = p0 + (long long)B0 * (p1 + (long long)B1 * p2);
+      // scratch is read-only in a kernel of its own (neighbouring points share most of their
+      // windows, so through L1); the persistent kernel rewrites it between its barriers (L2 only)
+      auto ld = [&](long long i) { return COHERENT ? __ldcg(&scratch[i]) : __ldg(&scratch[i]); };
       T uk[3] = {T(0), T(0), T(0)}, lus[3] = {T(0), T(0), T(0)};
 #pragma unroll
       for (int a = 0; a < D; ++a) {
-        uk[a] = __ldcg(&scratch[a * BC + bl]);
-        lus[a] = __ldcg(&scratch[(D + 1 + a) * BC + bl]);
+        uk[a] = ld(a * BC + bl);
+        lus[a] = ld((D + 1 + a) * BC + bl);
       }
-      const T lk = __ldcg(&scratch[D * BC + bl]);
+      const T lk = ld(D * BC + bl);
       T qv = km * lk;
 #pragma unroll
       for (int a = 0; a < D; ++a) {
@@ -863,7 +866,7 @@ __global__ void __launch_bounds__(kDesignBlock) k_adj_design(Geo g, Ctrl* ctrl, 
   // chunks of kDesignPointsPerCta points, grid-strided (the grid is capped: see design_ctas)
   for (int m0 = blockIdx.x * kDesignPointsPerCta; m0 < g.ND; m0 += gridDim.x * kDesignPointsPerCta) {
     const int m = m0 + threadIdx.x / LN;
-    inside = adj_design_point<T, D, AX>(g, kref, scratch, sk, lo, m, m < g.ND, lane, lF, lT, dkref, v) && inside;
+    inside = adj_design_point<T, D, AX, false>(g, kref, scratch, sk, lo, m, m < g.ND, lane, lF, lT, dkref, v) && inside;
   }
   if (!inside) atomicOr(&ctrl->status, ST_BOX_OVERFLOW);
   block_sum_partial<NV, LN>(v, static_cast<typename Partial<T>::type*>(partials) + blockIdx.x * NV, red);
@@ -1157,7 +1160,7 @@ __global__ void __launch_bounds__(BoxCta<D>::threads, 1)
     const int share = (g.ND + G - 1) / G, mb = blockIdx.x * share, me = min(g.ND, mb + share);
     for (int m0 = mb; m0 < me; m0 += PPC) {
       const int m = m0 + tid / LN;
-      inside = adj_design_point<T, D, AX>(g, kref, scratch, sk, lo, m, m < me, lane, lF, lT, dkref, v) && inside;
+      inside = adj_design_point<T, D, AX, true>(g, kref, scratch, sk, lo, m, m < me, lane, lF, lT, dkref, v) && inside;
     }
     if (!inside) atomicOr(&ctrl->status, ST_BOX_OVERFLOW);
     PT* part = static_cast<PT*>(partials) + (k & 1) * pstride;
