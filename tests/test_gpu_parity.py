@@ -259,6 +259,26 @@ def test_3d_fp32_uniform_matches_oracle(name, make):
     assert rel(r["dJdgamma"], G["dJdgamma"]) <= 1e-3
 
 
+def test_sailturbine2d_1024x512_truncated_fp32():
+    """The 1024x512 / 256x256 rotating workload in its benchmark precision (FP32 fields, uniform
+    checkpoints, and the persistent coupling kernels the automatic choice takes for its 576 box
+    tiles), truncated to 8 steps so the oracle finishes in about half a minute."""
+    from paper_2601_18272_gb300 import lks
+    from paper_2601_18272_gb300.lks import Solver
+    P, g = config(3)
+    P = P.replace(n_steps=8, ckpt_every=4)
+    S = Solver(P)
+    try:
+        assert lks.lks_persistent_coupling(S.handle, -1) is True
+    finally:
+        S.close()
+    p0, u0, s0 = initial_state(P)
+    G = O.gradient(P, g, p0, u0, s0)
+    r = gpu_run(P, g, p0, u0, s0)
+    assert abs(r["J"] - G["J"]) <= 1e-4 * abs(G["J"])
+    assert rel(r["dJdgamma"], G["dJdgamma"]) <= 1e-3
+
+
 def test_body3d_128x64x64_truncated_fp32():
     """The 128x64x64 D3Q15 / 48^3 translating workload in its benchmark precision (FP32 fields,
     uniform checkpoints), truncated to 2 steps so the oracle finishes in about half a minute."""
