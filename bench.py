@@ -660,7 +660,7 @@ def main():
         # forward-only throughput of this workload (the march alone, lks_forward)
         ms_fwd = _timed(stream, flush, lambda: solver.forward(gamma))
         line["roofline"]["forward_only"] = {P.name: _fwd_roofline(P, ms_fwd, peak)}
-        # the benchmark spec's autograd form: LKSObjective.apply(gamma, solver).backward() (the backward
+        # the gradient in autograd form: LKSObjective.apply(gamma, solver).backward() (the backward
         # reads the incoming gradient on the host: one synchronisation, as lks_forward already has)
         from paper_2601_18272_gb300.autograd import objective
         gam_ag = gamma.clone().requires_grad_(True)
