@@ -174,7 +174,8 @@ LKS_API int lks_forward(lks_handle* h, const double* gamma_dev, double* J_host, 
 
 /* Reverse sweep (Algorithm 1, adjoint loop) seeded with dJ = seed. Enqueued on the stream; with the
  * persistent coupling kernels (lks_persistent_coupling) or the row-streamed 3D stencils
- * (lks_stencil_form = 1) it then synchronises the stream once to read the device status word. Requires a prior lks_forward (else LKS_ERR_ORDER).
+ * (lks_stencil_form = 1) it then synchronises the stream once to read the device status word.
+ * Requires a prior lks_forward (else LKS_ERR_ORDER).
  * Errors: LKS_ERR_TIMEOUT, LKS_ERR_CUDA. */
 LKS_API int lks_adjoint(lks_handle* h, double seed, void* stream);
 
@@ -324,7 +325,7 @@ LKS_API int lks_checkpoint_slots(const lks_handle* h);
 /* Form of the 3D predictor and transpose kernels the handle launches: 1 for the row-streamed FP32
  * kernels (a 64-column window fed by one TMA box of 16 rows per plane, packed FP32x2 arithmetic;
  * taken for FP32 fields on grids periodic in y and z with nx a multiple of 4 and at least 64 and
- * ny at least 16), 0 for the general kernels (2D problems, FP64 fields, walls in y or z, other
+ * ny at least 16, x not walled), 0 for the general kernels (2D problems, FP64 fields, walls, other
  * grids); -LKS_ERR_ARG for NULL. Both forms compute the predictor of Sec. 2.2 and its exact
  * transpose. */
 LKS_API int lks_stencil_form(const lks_handle* h);
