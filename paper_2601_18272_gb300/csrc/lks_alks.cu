@@ -494,8 +494,58 @@ __device__ __forceinline__ long long alks_nbr(const Geo& g, const int (&x)[3], i
   return (long long)y[0] + (long long)g.n[0] * ((long long)y[1] + (long long)g.n[1] * y[2]);
 }
 
+// D3Q15 vector components as compile-time values, in the order of c_cv3: rest, +-x, +-y, +-z,
+// then the corners with s_x alternating, s_y in pairs and s_z in fours.
+__host__ __device__ constexpr int cv3(int i, int a) {
+  return i == 0 ? 0 : (i < 7 ? ((i - 1) / 2 == a ? ((i & 1) ? 1 : -1) : 0) : ((((i - 7) >> a) & 1) ? -1 : 1));
+}
+constexpr int kCv3Order[15][3] = {{0, 0, 0},  {1, 0, 0},  {-1, 0, 0}, {0, 1, 0},   {0, -1, 0},
+                                  {0, 0, 1},  {0, 0, -1}, {1, 1, 1},  {-1, 1, 1},  {1, -1, 1},
+                                  {-1, -1, 1}, {1, 1, -1}, {-1, 1, -1}, {1, -1, -1}, {-1, -1, -1}};
+constexpr bool cv3_in_order() {
+  for (int i = 0; i < 15; ++i)
+    for (int a = 0; a < 3; ++a)
+      if (cv3(i, a) != kCv3Order[i][a]) return false;
+  return true;
+}
+static_assert(cv3_in_order(), "cv3 must list the D3Q15 vectors in the order of c_cv3");
+
+// The node indices alks_nbr gives for the D3Q15 vectors of node x, with the wrap or clamp done
+// once per axis and coordinate (components are -1, 0 or +1) instead of once per vector and axis:
+// o[a][k] is coordinate x_a + k - 1, wrapped or clamped, times the stride of axis a. Call with a
+// compile-time vector index (unrolled loops), so o stays in registers.
+struct NodeNbrs3 {
+  long long o[3][3];
+  __device__ __forceinline__ NodeNbrs3(const Geo& g, const int (&x)[3]) {
+    long long stride = 1;
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+#pragma unroll
+      for (int k = 0; k < 3; ++k) {
+        int v = x[a] + k - 1;
+        if (g.bc[a] == BC_PERIODIC)
+          v = v < 0 ? v + g.n[a] : (v >= g.n[a] ? v - g.n[a] : v);
+        else
+          v = min(max(v, 0), g.n[a] - 1);
+        o[a][k] = (long long)v * stride;
+      }
+      stride *= g.n[a];
+    }
+  }
+  __device__ __forceinline__ long long operator()(int j) const {
+    return o[0][cv3(j, 0) + 1] + o[1][cv3(j, 1) + 1] + o[2][cv3(j, 2) + 1];
+  }
+};
+
 template <int D>
 __device__ __forceinline__ void node_coords(const Geo& g, long long n, int (&x)[3]) {
+  if (n <= 0x7fffffffLL) {  // 32-bit division where the index allows it
+    const unsigned u = (unsigned)n, r = u / (unsigned)g.n[0];
+    x[0] = (int)(u - r * (unsigned)g.n[0]);
+    x[1] = (int)(r % (unsigned)g.n[1]);
+    x[2] = (D == 3) ? (int)(r / (unsigned)g.n[1]) : 0;
+    return;
+  }
   x[0] = (int)(n % g.n[0]);
   x[1] = (int)((n / g.n[0]) % g.n[1]);
   x[2] = (D == 3) ? (int)(n / ((long long)g.n[0] * g.n[1])) : 0;
@@ -518,9 +568,11 @@ __global__ void __launch_bounds__(256) k_alks_z(Geo g, const Ctrl* ctrl, Slots<T
     for (int a = 0; a < D; ++a)
 #pragma unroll
       for (int bb = 0; bb < D; ++bb) gs[a][bb] = T(0);
+    static_assert(D == 3, "the node kernels through Z are the 3D form");
+    const NodeNbrs3 nb(g, x);
 #pragma unroll
     for (int j = 1; j < Lat<D>::Q; ++j) {
-      const long long m = alks_nbr<D>(g, x, j);
+      const long long m = nb(j);
       T sv[NS];
 #pragma unroll
       for (int k = 0; k < NS; ++k) sv[k] = am[(1 + D + k) * N + m];
@@ -586,9 +638,11 @@ __global__ void __launch_bounds__(256) k_alks_gather(Geo g, const Ctrl* ctrl, Sl
     for (int a = 0; a < D; ++a) U[a] = T(0);
 #pragma unroll
     for (int k = 0; k < NS; ++k) Sv[k] = T(0);
+    static_assert(D == 3, "the node kernels through Z are the 3D form");
+    const NodeNbrs3 nb(g, x);  // x is interior on non-periodic axes: no clamping
 #pragma unroll
     for (int i = 0; i < Lat<D>::Q; ++i) {
-      const long long m = alks_nbr<D>(g, x, i);  // x is interior on non-periodic axes: no clamping
+      const long long m = nb(i);
       T F = am[m];
 #pragma unroll
       for (int a = 0; a < D; ++a) F += T(3) * (T)Lat<D>::c(i, a) * zb[a * N + m];
