@@ -552,7 +552,7 @@ __device__ __forceinline__ void node_coords(const Geo& g, long long n, int (&x)[
 }
 
 template <typename T, int D>
-__global__ void __launch_bounds__(256) k_alks_z(Geo g, const Ctrl* ctrl, Slots<T> S, const T* __restrict__ Ab,
+__global__ void __launch_bounds__(256, sizeof(T) == 4 ? 3 : 0) k_alks_z(Geo g, const Ctrl* ctrl, Slots<T> S, const T* __restrict__ Ab,
                                                 long long astride, T* __restrict__ zb, int di) {
   constexpr int NS = Lat<D>::NS;
   const int t = ctrl->t0 - di;
@@ -599,7 +599,7 @@ __global__ void __launch_bounds__(256) k_alks_z(Geo g, const Ctrl* ctrl, Slots<T
 }
 
 template <typename T, int D>
-__global__ void __launch_bounds__(256) k_alks_gather(Geo g, const Ctrl* ctrl, Slots<T> S, T* Ab, long long astride,
+__global__ void __launch_bounds__(256, sizeof(T) == 4 ? 3 : 0) k_alks_gather(Geo g, const Ctrl* ctrl, Slots<T> S, T* Ab, long long astride,
                                                      const T* __restrict__ zb, T nu, int di) {
   constexpr int NS = Lat<D>::NS;
   const int t = ctrl->t0 - di;
